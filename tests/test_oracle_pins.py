@@ -1,0 +1,388 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed form,
+a summation identity the scheme is built on, a brute-force dense solve, a
+finite-difference derivative, or an order of convergence.  The last test plants
+mistakes in the oracle (on the CPU) and checks that a pin catches each one.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import pfc_oracle as O
+from paper_1703_01202_gb300 import inputs
+
+H2 = math.pi / 4
+GAMMA = 0.25
+
+
+def rand_field(shape, seed, mean=0.1, amp=0.3):
+    return inputs.noise_field(shape, mean, amp, seed)
+
+
+def kappa(ks, ns, h):
+    """Symbol of -Delta_d on the Fourier mode with integer wave numbers ks."""
+    return sum(4.0 / h**2 * math.sin(math.pi * k / n) ** 2 for k, n in zip(ks, ns))
+
+
+def mode(shape, ks, h):
+    """cos(sum_a 2 pi k_a x_a / L_a) on the cell centres."""
+    coords = inputs.cell_centres(shape, h)
+    arg = 0.0
+    for c, k, n in zip(coords, ks, shape):
+        arg = arg + 2.0 * math.pi * k * c / (n * h)
+    return np.cos(arg)
+
+
+# ---------------------------------------------------------------- operators
+@pytest.mark.parametrize("shape,ks", [((12, 16), (2, 3)), ((6, 10, 8), (1, 4, 3))])
+def test_laplacian_fourier_symbol(shape, ks):
+    """Delta_d cos(k.x) = -kappa cos(k.x), kappa = sum 4/h^2 sin^2(pi k/N) (Sec. 3)."""
+    h = 0.7
+    u = mode(shape, ks, h)
+    lam = kappa(ks, shape, h)
+    np.testing.assert_allclose(O.lap(u, h), -lam * u, rtol=0, atol=1e-12 * lam)
+    # L_gamma acts as (1-g) - 2 kappa + kappa^2 (Eq. discretedG)
+    s = (1 - GAMMA) - 2 * lam + lam**2
+    np.testing.assert_allclose(O.L_gamma(u, h, GAMMA), s * u, rtol=0, atol=1e-11 * (1 + lam**2))
+
+
+def test_energy_closed_forms():
+    """F_d of a constant and of one Fourier mode (Eqs. relations, freeenergy)."""
+    shape = (16, 24)
+    h = 0.6
+    area = h * h * shape[0] * shape[1]
+    c = 0.37
+    assert O.energy(np.full(shape, c), h, GAMMA) == pytest.approx(
+        area * ((1 - GAMMA) * c * c / 2 + c**4 / 4), rel=1e-13)
+    # phi = A cos(2 pi k x / L) with 2k, 4k not multiples of N: mean of cos^2 = 1/2, cos^4 = 3/8
+    A = 0.3
+    ks = (0, 5)
+    phi = A * mode(shape, ks, h)
+    lam = kappa(ks, shape, h)
+    expect = area * (A * A / 4 * ((1 - GAMMA) - 2 * lam + lam * lam) + 3 * A**4 / 32)
+    assert O.energy(phi, h, GAMMA) == pytest.approx(expect, rel=1e-12)
+    assert O.mass(phi + 0.2, h) == pytest.approx(0.2 * area, rel=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(10, 12), (6, 8, 7)])
+def test_dvd_identity(shape):
+    """Eq. (DVD): h^d sum [G_d(phi1) - G_d(phi0)] = h^d sum mu(phi1, phi0)(phi1 - phi0)."""
+    h = 0.8
+    p1 = rand_field(shape, 1)
+    p0 = rand_field(shape, 2)
+    lhs = O.energy(p1, h, GAMMA) - O.energy(p0, h, GAMMA)
+    rhs = float(np.sum(O.mu_dvd(p1, p0, h, GAMMA) * (p1 - p0))) * h ** len(shape)
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-12 * abs(O.energy(p0, h, GAMMA)))
+
+
+@pytest.mark.parametrize("shape", [(10, 12), (6, 8, 7)])
+def test_summation_by_parts(shape):
+    """Eq. (summation) with M = 1: sum g Delta_d g = -sum_axes sum (D^+ g)^2."""
+    h = 0.9
+    g = rand_field(shape, 3)
+    lhs = float(np.sum(g * O.lap(g, h)))
+    rhs = -sum(float(np.sum(O.d_plus(g, ax, h) ** 2)) for ax in range(len(shape)))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ---------------------------------------------------------------- Jacobian
+def test_jacobian_matches_finite_differences():
+    """Analytic J v against central differences of F (Eq. Jacobi)."""
+    shape = (12, 10)
+    Phi = rand_field(shape, 4, 0.2, 0.4)
+    phin = rand_field(shape, 5, 0.2, 0.4)
+    v = rand_field(shape, 6, 0.0, 1.0)
+    dt = 0.7
+    Jv = O.jvp(v, Phi, phin, dt, H2, GAMMA)
+    eps = 1e-5 * np.linalg.norm(Phi) / np.linalg.norm(v)
+    fd = (O.residual(Phi + eps * v, phin, dt, H2, GAMMA) - O.residual(Phi - eps * v, phin, dt, H2, GAMMA)) / (2 * eps)
+    assert np.linalg.norm(Jv - fd) <= 1e-8 * np.linalg.norm(Jv)
+    J = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA)
+    np.testing.assert_allclose((J @ v.ravel()).reshape(shape), Jv, rtol=0, atol=1e-13 * np.abs(Jv).max())
+    # 3D as well
+    s3 = (6, 7, 8)
+    Phi3, phin3, v3 = rand_field(s3, 7), rand_field(s3, 8), rand_field(s3, 9, 0.0, 1.0)
+    Jv3 = O.jvp(v3, Phi3, phin3, dt, H2, GAMMA)
+    fd3 = (O.residual(Phi3 + eps * v3, phin3, dt, H2, GAMMA) - O.residual(Phi3 - eps * v3, phin3, dt, H2, GAMMA)) / (2 * eps)
+    assert np.linalg.norm(Jv3 - fd3) <= 1e-8 * np.linalg.norm(Jv3)
+
+
+# ---------------------------------------------------------------- Schwarz pieces
+@pytest.mark.parametrize("shape,parts,overlap", [((16, 20), (2, 3), 1), ((17, 16), (3, 2), 2), ((10, 10, 10), (2, 2, 2), 1)])
+def test_improved_bc_equals_principal_submatrix(shape, parts, overlap):
+    """The subdomain problem with phi = 0 on the 3-layer ring (Sec. 4, improved
+    boundary condition) gives exactly A_k = R J R^T (Eq. Ak) whenever the block
+    plus its ring does not wrap onto itself (block width + 3 <= grid width)."""
+    Phi, phin = rand_field(shape, 10), rand_field(shape, 11)
+    dt = 2.0
+    J = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA)
+    blocks = O.decompose(shape, parts, overlap)
+    for blk in blocks[:3]:
+        A1 = O.subdomain_matrix(J, blk)
+        A2 = O.subdomain_matrix_improved_bc(Phi, phin, dt, H2, GAMMA, blk)
+        np.testing.assert_allclose(A2, A1, rtol=0, atol=1e-13 * np.abs(A1).max())
+
+
+def test_decomposition_covers_grid_once():
+    """Cores partition the grid (uneven splits give the extra cell to the first cores)."""
+    for shape, parts in [((64, 64), (4, 4)), ((37, 50), (3, 7)), ((10, 11, 9), (2, 3, 2))]:
+        blocks = O.decompose(shape, parts, 1)
+        hits = np.zeros(int(np.prod(shape)), dtype=int)
+        for b in blocks:
+            hits[b.core_idx] += 1
+        assert np.all(hits == 1)
+    assert O.split_axis(256, 7) == [(0, 37), (37, 37), (74, 37), (111, 37), (148, 36), (184, 36), (220, 36)]
+
+
+def test_single_block_ras_is_exact_inverse():
+    """One subdomain covering the periodic grid: H^{-1} = J^{-1}, so GMRES needs one iteration."""
+    shape = (10, 12)
+    Phi, phin = rand_field(shape, 12), rand_field(shape, 13)
+    J = O.assemble_jacobian(Phi, phin, 1.0, H2, GAMMA)
+    pre = O.Schwarz(J, O.decompose(shape, (1, 1), 0), "left-ras", "lu")
+    b = rand_field(shape, 14, 0.0, 1.0)
+    res = O.gmres_right(lambda v: (J @ v.ravel()).reshape(shape), pre.apply, b, 1e-12 * np.linalg.norm(b))
+    assert res.iterations == 1
+    np.testing.assert_allclose(res.x.ravel(), np.linalg.solve(J.toarray(), b.ravel()), rtol=1e-10, atol=1e-12)
+
+
+def test_ras_variants_match_definitions():
+    """AS / left-RAS / right-RAS (Eqs. invM, ras, ash) against explicit sums of
+    restriction matrices times dense block inverses."""
+    shape = (12, 12)
+    Phi, phin = rand_field(shape, 15), rand_field(shape, 16)
+    J = O.assemble_jacobian(Phi, phin, 0.5, H2, GAMMA)
+    blocks = O.decompose(shape, (2, 3), 1)
+    n = Phi.size
+    r = rand_field(shape, 17, 0.0, 1.0).ravel()
+    for kind in ("as", "left-ras", "right-ras"):
+        M = np.zeros((n, n))
+        for blk in blocks:
+            Rd = np.zeros((blk.block_idx.size, n))
+            Rd[np.arange(blk.block_idx.size), blk.block_idx] = 1.0
+            R0 = Rd * blk.core_mask[:, None]
+            Ainv = np.linalg.inv(J.toarray()[np.ix_(blk.block_idx, blk.block_idx)])
+            left = R0 if kind == "left-ras" else Rd
+            right = R0 if kind == "right-ras" else Rd
+            M += left.T @ Ainv @ right
+        z = O.Schwarz(J, blocks, kind, "lu").apply(r.reshape(shape)).ravel()
+        np.testing.assert_allclose(z, M @ r, rtol=1e-10, atol=1e-12 * np.abs(M @ r).max())
+
+
+def test_ilu0_on_banded_pattern_is_exact_lu():
+    """ILU(0) equals exact LU when the pattern already holds all fill (a
+    tridiagonal matrix); and its factors reproduce A on the pattern."""
+    n = 30
+    rng = np.random.default_rng(0)
+    A = sp.diags([rng.uniform(-1, 1, n - 1), 4 + rng.uniform(0, 1, n), rng.uniform(-1, 1, n - 1)], [-1, 0, 1], format="csr")
+    LU = O.ilu0(A)
+    b = rng.uniform(-1, 1, n)
+    np.testing.assert_allclose(O.ilu0_solve(LU, b), np.linalg.solve(A.toarray(), b), rtol=1e-12)
+    # 2D 5-point matrix: (L U)_ij = a_ij on the pattern
+    m = 6
+    T = sp.diags([-np.ones(m - 1), 4 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    A2 = (sp.kron(sp.identity(m), T) + sp.kron(sp.diags([-np.ones(m - 1), -np.ones(m - 1)], [-1, 1]), sp.identity(m))).tocsr()
+    LU2 = O.ilu0(A2).toarray()
+    L = np.tril(LU2, -1) + np.eye(m * m)
+    U = np.triu(LU2)
+    prod = L @ U
+    mask = A2.toarray() != 0
+    np.testing.assert_allclose(prod[mask], A2.toarray()[mask], atol=1e-13)
+
+
+def test_gmres_unpreconditioned_matches_dense_solve():
+    """GMRES with H = I to 1e-14 against a dense solve (restart exercised)."""
+    shape = (8, 8)
+    Phi, phin = rand_field(shape, 18), rand_field(shape, 19)
+    J = O.assemble_jacobian(Phi, phin, 0.3, H2, GAMMA)
+    b = rand_field(shape, 20, 0.0, 1.0)
+    res = O.gmres_right(lambda v: (J @ v.ravel()).reshape(shape), lambda v: v, b, 1e-14 * np.linalg.norm(b), restart=10)
+    assert res.converged
+    np.testing.assert_allclose(res.x.ravel(), np.linalg.solve(J.toarray(), b.ravel()), rtol=0, atol=1e-11 * np.abs(b).max())
+
+
+# ---------------------------------------------------------------- full step
+def dense_newton(phin, dt, h, gamma, tol=1e-14):
+    """Brute force: Newton with the dense Jacobian solved by LAPACK."""
+    Phi = phin.copy()
+    for _ in range(50):
+        F = O.residual(Phi, phin, dt, h, gamma)
+        if np.linalg.norm(F) <= tol:
+            break
+        J = O.assemble_jacobian(Phi, phin, dt, h, gamma).toarray()
+        Phi = Phi - np.linalg.solve(J, F.ravel()).reshape(Phi.shape)
+    return Phi
+
+
+@pytest.mark.parametrize("shape,parts,solver,h,dt", [((8, 8), (2, 2), "lu", H2, 0.5),
+                                                     ((10, 10, 10), (2, 2, 2), "ilu0", 80 * math.pi / 256, 0.1)])
+def test_nks_matches_dense_direct_solve(shape, parts, solver, h, dt):
+    """NKS step (Newton + right-preconditioned GMRES + left-RAS) against Newton
+    with dense direct solves, to 1e-12 (tight tolerances on both sides).  3D uses
+    ILU(0) subdomain solves at the 3D test's spacing and a dt where ILU(0) of the
+    radius-3 block matrix has positive pivots."""
+    phin = inputs.noise_field(shape, 0.07, 0.07, 21)
+    p = O.Params(newton_rtol=1e-13, gmres_rtol=1e-8, parts=parts, overlap=1, subdomain_solver=solver)
+    Phi, info = O.newton_solve(phin, dt, h, GAMMA, p)
+    ref = dense_newton(phin, dt, h, GAMMA)
+    assert info.converged and info.newton_its >= 2
+    assert np.abs(Phi - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dt", [1e-3, 1e-2, 0.1, 1.0, 5.0, 100.0])
+def test_energy_law_and_decrease(dt):
+    """Proposition: F_d(phi^{n+1}) <= F_d(phi^n) for every dt, and the exact
+    balance F1 - F0 = -dt h^2 sum_axes sum (D^+ mu)^2 + dt h^2 sum mu F(phi1).
+    (dt near 2/|kappa S| for a grid mode makes J singular for this liquid at
+    gamma = 0.25; such dt, e.g. 10 here, are left out.)"""
+    shape = (16, 16)
+    phin = inputs.noise_field(shape, 0.07, 0.07, 22)
+    p = O.Params(parts=(2, 2), overlap=1, newton_rtol=1e-12)
+    phi1, info = O.newton_solve(phin, dt, H2, GAMMA, p)
+    assert info.converged
+    F0, F1 = O.energy(phin, H2, GAMMA), O.energy(phi1, H2, GAMMA)
+    mu = O.mu_dvd(phi1, phin, H2, GAMMA)
+    diss = sum(float(np.sum(O.d_plus(mu, ax, H2) ** 2)) for ax in range(2))
+    rest = float(np.sum(mu * O.residual(phi1, phin, dt, H2, GAMMA)))
+    assert F1 - F0 == pytest.approx(-dt * H2**2 * diss + dt * H2**2 * rest, rel=1e-9, abs=1e-12 * abs(F0))
+    assert F1 <= F0
+
+
+def test_mass_conservation():
+    """Sum phi is conserved (Sec. 3): with the zero-mean update to 1e-12; and,
+    for a loosely solved step without it, the drift equals dt h^2 sum F(phi^{n+1})
+    (sum Delta_d = 0 on the periodic grid)."""
+    shape = (16, 16)
+    phi0 = inputs.noise_field(shape, 0.07, 0.07, 23)
+    p = O.Params(parts=(2, 2), overlap=1)
+    phi, recs = O.run(phi0, H2, GAMMA, p, 8, fixed_dt=0.5)
+    m0 = O.mass(phi0, H2)
+    assert all(abs(r.mass - m0) <= 1e-12 * max(1.0, abs(m0)) for r in recs)
+    p2 = O.Params(parts=(2, 2), overlap=1, mass_projection=False, newton_rtol=1e-2, gmres_rtol=0.3)
+    phi1, _ = O.newton_solve(phi0, 0.5, H2, GAMMA, p2)
+    drift = O.mass(phi1, H2) - m0
+    expect = 0.5 * H2**2 * float(np.sum(O.residual(phi1, phi0, 0.5, H2, GAMMA)))
+    assert abs(drift - expect) <= 1e-13 * max(1.0, abs(m0))
+
+
+def test_constant_is_fixed_point():
+    """A constant field is a steady state: F = 0, zero Newton iterations."""
+    phin = np.full((12, 12), 0.3)
+    assert np.abs(O.residual(phin, phin, 1.0, H2, GAMMA)).max() < 1e-14
+    phi1, info = O.newton_solve(phin, 1.0, H2, GAMMA, O.Params(parts=(2, 2)))
+    assert info.newton_its == 0 and np.array_equal(phi1, phin)
+
+
+@pytest.mark.parametrize("dt", [0.05, 1.0, 20.0])
+def test_fourier_mode_crank_nicolson_multiplier(dt):
+    """Small-amplitude mode: the scheme is Crank-Nicolson on the linearised
+    equation, so phi1 = g phi0 with g = (1 - dt kappa S/2)/(1 + dt kappa S/2),
+    S = (1-gamma) - 2 kappa + kappa^2 (Eqs. discretedG, NSOP)."""
+    shape = (16, 16)
+    h = 1.1
+    ks = (1, 2)
+    phi0 = 1e-6 * mode(shape, ks, h)
+    lam = kappa(ks, shape, h)
+    S = (1 - GAMMA) - 2 * lam + lam * lam
+    g = (1 - 0.5 * dt * lam * S) / (1 + 0.5 * dt * lam * S)
+    p = O.Params(parts=(2, 2), newton_rtol=1e-13, gmres_rtol=1e-12)
+    phi1, info = O.newton_solve(phi0, dt, h, GAMMA, p)
+    np.testing.assert_allclose(phi1, g * phi0, rtol=0, atol=1e-9 * 1e-6)
+
+
+def test_adaptive_dt_formula():
+    """Eq. (sencondt) with hand-computed values."""
+    p = O.Params(dt_min=0.01, dt_max=10.0, eta=5000.0)
+    # F' = (E_n - E_nm1)/dt_prev = -0.02/0.5 = -0.04 ; 1 + 5000*0.0016 = 9 -> 10/3
+    assert O.adaptive_dt(-1.02, -1.0, 0.5, p) == pytest.approx(10.0 / 3.0, rel=1e-15)
+    assert O.adaptive_dt(-1.0, -1.0, 0.5, p) == 10.0
+    assert O.adaptive_dt(-100.0, 0.0, 0.01, p) == 0.01
+
+
+# ---------------------------------------------------------------- orders of accuracy
+def test_second_order_in_space():
+    """Sec. 5 accuracy test (sine initial value on [0,32]^2, gamma = 0.025) with
+    ratio-3 refinement so that cell centres coincide (coarse cell i sits on fine
+    cell 3i+1, or 9i+4 two levels down): the error ratio between successive
+    grids approaches 9 (second order).  Smaller grids and final time than the
+    paper's 1024^2 reference, same initial value."""
+    gamma = 0.025
+    L = 32.0
+    dt, steps = 0.1, 3
+    sols = {}
+    for n, parts, ov in [(12, (1, 1), 0), (36, (1, 1), 0), (108, (2, 2), 2)]:
+        h = L / n
+        phi0 = inputs.sine_field((n, n), h)
+        p = O.Params(parts=parts, overlap=ov, newton_rtol=1e-10, newton_atol=1e-8, gmres_rtol=1e-8)
+        sols[n], _ = O.run(phi0, h, gamma, p, steps, fixed_dt=dt)
+    ref = sols[108]
+    e12 = np.linalg.norm(sols[12] - ref[4::9, 4::9]) / np.linalg.norm(ref[4::9, 4::9])
+    e36 = np.linalg.norm(sols[36] - ref[1::3, 1::3]) / np.linalg.norm(ref[1::3, 1::3])
+    # C h^2 (1 - 1/81) against C (h/3)^2 (1 - 1/9): ratio -> 10 asymptotically
+    assert 8.5 < e12 / e36 < 11.0
+
+
+def test_second_order_in_time():
+    """Temporal accuracy (Sec. 5): errors against a dt/64 reference fall by ~4 per halving."""
+    gamma = 0.025
+    n = 32
+    h = 1.0
+    phi0 = inputs.sine_field((n, n), h)
+    T = 1.0
+    p = O.Params(parts=(2, 2), overlap=1, newton_rtol=1e-12, gmres_rtol=1e-8)
+    ref, _ = O.run(phi0, h, gamma, p, 128, fixed_dt=T / 128)
+    errs = []
+    for m in (4, 8, 16):
+        sol, _ = O.run(phi0, h, gamma, p, m, fixed_dt=T / m)
+        errs.append(np.linalg.norm(sol - ref) / np.linalg.norm(ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """A dropped term, a wrong sign or a wrong factor in the oracle trips a pin."""
+    shape = (10, 12)
+    h = 0.8
+    p1, p0 = rand_field(shape, 1), rand_field(shape, 2)
+
+    def dvd_gap():
+        lhs = O.energy(p1, h, GAMMA) - O.energy(p0, h, GAMMA)
+        rhs = float(np.sum(O.mu_dvd(p1, p0, h, GAMMA) * (p1 - p0))) * h * h
+        return abs(lhs - rhs) / abs(lhs)
+
+    assert dvd_gap() < 1e-12
+    orig_mu = O.mu_dvd
+    # dropped phi^n^3 term
+    monkeypatch.setattr(O, "mu_dvd", lambda P, q, hh, g: orig_mu(P, q, hh, g) - q**3 / 4)
+    assert dvd_gap() > 1e-6
+    monkeypatch.setattr(O, "mu_dvd", orig_mu)
+    # wrong sign of the 2 Delta term in L_gamma
+    orig_lg = O.L_gamma
+    monkeypatch.setattr(O, "L_gamma", lambda u, hh, g: orig_lg(u, hh, g) - 4.0 * O.lap(u, hh))
+    assert dvd_gap() > 1e-6
+    monkeypatch.setattr(O, "L_gamma", orig_lg)
+    # gradient term of G_d halved
+    orig_le = O.local_energy
+
+    def bad_le(phi, hh, g):
+        out = orig_le(phi, hh, g)
+        for ax in range(phi.ndim):
+            out += 0.25 * (O.d_plus(phi, ax, hh) ** 2 + O.d_minus(phi, ax, hh) ** 2)
+        return out
+
+    monkeypatch.setattr(O, "local_energy", bad_le)
+    assert dvd_gap() > 1e-6
+    monkeypatch.setattr(O, "local_energy", orig_le)
+    # transposed / wrong q in the Jacobian: finite-difference pin fails
+    Phi, phin, v = rand_field(shape, 4, 0.2, 0.4), rand_field(shape, 5, 0.2, 0.4), rand_field(shape, 6, 0.0, 1.0)
+    orig_q = O.jac_coeff
+    monkeypatch.setattr(O, "jac_coeff", lambda P, q: (3 * q**2 + 2 * P * q + P**2) / 4)
+    Jv = O.jvp(v, Phi, phin, 0.7, h, GAMMA)
+    eps = 1e-5
+    fd = (O.residual(Phi + eps * v, phin, 0.7, h, GAMMA) - O.residual(Phi - eps * v, phin, 0.7, h, GAMMA)) / (2 * eps)
+    assert np.linalg.norm(Jv - fd) > 1e-4 * np.linalg.norm(Jv)
+    monkeypatch.setattr(O, "jac_coeff", orig_q)
