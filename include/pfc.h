@@ -1,0 +1,180 @@
+/*
+ * pfc.h -- C ABI of the GB300 phase-field-crystal time stepper.
+ *
+ * One call of pfc_step advances the density field phi^n by one time step of
+ * the energy-stable DVDM semi-implicit scheme (Eq. NSOP with the discrete
+ * variational derivative of Eq. discretedG, mobility M = 1, periodic grid),
+ * solving the nonlinear system F(Phi) = 0 (Eq. NLS) by inexact Newton
+ * (Eq. newton) with right-preconditioned GMRES (Eq. hjacobi) and a restricted
+ * additive Schwarz preconditioner with the paper's "improved" subdomain
+ * boundary condition (Sec. 4, Eqs. ras, Ak).  pfc_run adds the adaptive time
+ * step of Eq. (sencondt).
+ *
+ * Conventions shared by every entry point
+ *  - Fields are float64, one value per cell of an Nx x Ny (x Nz) periodic
+ *    cell-centred grid with isotropic spacing h, row-major with x fastest:
+ *    idx = i + Nx * (j + Ny * k).
+ *  - The library never allocates device memory.  The caller allocates one
+ *    device workspace of pfc_workspace_size() bytes (256-byte aligned) and
+ *    passes it, together with the CUDA stream all work is queued on, to
+ *    pfc_create.  The workspace and the stream stay owned by the caller and
+ *    must outlive the state.  Host arrays are caller-owned and are never
+ *    retained past the call.
+ *  - Every function returns a pfc_status (0 = success).  On any error pfc_step
+ *    and pfc_run leave phi^n, phi^{n-1} and the energy history unchanged.
+ *  - Calls on one state are not thread-safe; distinct states are independent.
+ */
+#ifndef PFC_H
+#define PFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PFC_OK = 0,
+  PFC_EINVAL = -1,     /* bad argument (sizes, parameters, null pointers)        */
+  PFC_ENOMEM = -2,     /* workspace smaller than pfc_workspace_size()             */
+  PFC_ECUDA = -3,      /* a CUDA runtime call failed                              */
+  PFC_ENEWTON = -4,    /* Newton reached newton_max_it without meeting its test   */
+  PFC_EGMRES = -5,     /* GMRES reached gmres_max_it without meeting its test     */
+  PFC_ESINGULAR = -6,  /* a subdomain factorisation met a zero pivot              */
+  PFC_ENAN = -7,       /* a residual norm became NaN or Inf                       */
+  PFC_ETIMEOUT = -8    /* a bounded device-side wait ran out                      */
+} pfc_status;
+
+/* Subdomain factor storage precision. */
+enum { PFC_F64 = 0, PFC_F32 = 1, PFC_BF16 = 2 };
+/* Schwarz variant (Sec. 4): Eq. invM, Eq. ras, Eq. ash. */
+enum { PFC_AS = 0, PFC_LEFT_RAS = 1, PFC_RIGHT_RAS = 2 };
+/* Newton initial guess: phi^n (Sec. 4), linear extrapolation, caller-supplied. */
+enum { PFC_GUESS_PREV = 0, PFC_GUESS_EXTRAP = 1, PFC_GUESS_USER = 2 };
+
+typedef struct {
+  int dim;       /* 2 or 3                                        */
+  int64_t n[3];  /* Nx, Ny, Nz (n[2] = 1 when dim == 2)          */
+} pfc_grid;
+
+typedef struct {
+  /* Newton stop test ||F(Phi_{m+1})|| <= max(newton_rtol ||F(Phi_0)||, newton_atol)
+     (Sec. 4, Newton stopping condition); 2-norms. */
+  double newton_rtol, newton_atol;
+  int newton_max_it;
+  /* GMRES stop test ||r_m|| <= max(gmres_rtol ||F(Phi_m)||, gmres_atol) (Sec. 4). */
+  double gmres_rtol, gmres_atol;
+  int gmres_restart, gmres_max_it;
+  /* Decomposition: sub[a] cores along x, y, z (uneven splits give the first
+     cores one extra cell); overlap = cells added per side (Sec. 4). */
+  int sub[3];
+  int overlap;
+  int ras_kind;      /* PFC_LEFT_RAS (only kind built on the GPU)            */
+  int factor_prec;   /* PFC_F64 (plain path), PFC_F32 or PFC_BF16 storage    */
+  int guess;         /* PFC_GUESS_*                                          */
+  int mass_projection; /* 1: Newton update projected to zero mean            */
+  double ls_alpha;   /* Armijo constant of the backtracking line search      */
+  int ls_max_cuts;
+  /* Adaptive time step, Eq. (sencondt); energy_scaled = 1 feeds F_d/|Omega|. */
+  double dt_min, dt_max, eta;
+  int energy_scaled;
+} pfc_params;
+
+typedef struct {
+  int status;        /* pfc_status of the step                                */
+  int newton_its;    /* Newton iterations taken                               */
+  int gmres_its;     /* GMRES iterations summed over the Newton iterations    */
+  int ls_cuts;       /* line-search step reductions summed over the step      */
+  double dt;         /* time step used                                        */
+  double energy;     /* F_d(phi^{n+1}), Eq. (freeenergy)                      */
+  double mass;       /* h^d sum phi^{n+1}                                      */
+  double res_norm0;  /* ||F(Phi_0)||                                          */
+  double res_norm;   /* ||F(phi^{n+1})||                                      */
+} pfc_step_info;
+
+typedef struct pfc_state pfc_state;
+
+/* Fills *p with the defaults: Newton rtol 1e-10, GMRES rtol 1e-6, restart 30,
+   left-RAS, overlap 1, F64 factors, guess = phi^n, mass projection on,
+   Armijo 1e-4 with 10 cuts, dt in [1e-2, 10], eta 5000, scaled energy. */
+int pfc_default_params(pfc_params* p);
+
+/* Bytes of device workspace a state for this grid and these parameters needs.
+   Errors: PFC_EINVAL for an invalid grid or decomposition (a block, core plus
+   2*overlap, wider than the grid along an axis). */
+int pfc_workspace_size(const pfc_grid* g, const pfc_params* p, size_t* bytes);
+
+/* Creates a state on the current CUDA device.  h: grid spacing; eps: the
+   quench depth gamma of Eq. (GE).  dev_workspace: caller-owned device buffer
+   of `bytes` >= pfc_workspace_size (256-byte aligned); cuda_stream: a
+   cudaStream_t (NULL = legacy default stream).  phi^n starts at zero. */
+int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, void* dev_workspace,
+               size_t bytes, void* cuda_stream, pfc_state** out);
+void pfc_destroy(pfc_state* s);
+
+/* Sets phi^n = phi^{n-1} = phi (N values) and clears the energy history.
+   on_device = 1: phi is a device pointer; 0: a host pointer. */
+int pfc_set_field(pfc_state* s, const double* phi, int on_device);
+/* Copies phi^n out (N values) to a device (on_device = 1) or host buffer. */
+int pfc_get_field(pfc_state* s, double* out, int on_device);
+/* Caller-supplied Newton initial guess for the next pfc_step when
+   params.guess == PFC_GUESS_USER (N values, device or host). */
+int pfc_set_guess(pfc_state* s, const double* guess, int on_device);
+
+/* One time step of size dt (Eq. NSOP solved by NKS, Sec. 4).  On success
+   phi^{n-1} <- phi^n, phi^n <- phi^{n+1}.  info may be NULL. */
+int pfc_step(pfc_state* s, double dt, pfc_step_info* info);
+
+/* nsteps steps with dt from Eq. (sencondt); the first step of a fresh field
+   uses dt_min.  per_step: caller-owned array of nsteps records, or NULL.
+   Stops at the first failing step and returns its status. */
+int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step);
+
+/* F_d(phi^n) (Eq. freeenergy) and h^d sum phi^n. */
+int pfc_energy(pfc_state* s, double* F);
+int pfc_mass(pfc_state* s, double* m);
+
+/* Test hooks on caller device arrays of N values (no state change):
+   residual F(Phi) of Eq. (NSOP) for the given phi^n and dt; its 2-norm in
+   *norm (may be NULL). */
+int pfc_residual(pfc_state* s, const double* Phi, const double* phin, double dt, double* F_out,
+                 double* norm);
+/* J v = v/dt - Delta_d(L_gamma v / 2 + q v), q = (3 Phi^2 + 2 Phi phi^n + phi^n^2)/4 (Eq. Jacobi). */
+int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v, double dt,
+            double* Jv);
+/* Builds the subdomain factors of J(Phi, phi^n, dt) (Eq. Ak, improved BC) and
+   applies the Schwarz preconditioner (Eq. ras) to r: z = sum_k (R_k^0)^T A_k^{-1} R_k^delta r. */
+int pfc_precond_apply(pfc_state* s, const double* Phi, const double* phin, double dt, const double* r,
+                      double* z);
+
+/* The time step Eq. (sencondt) gives from the state's energy history:
+   max(dt_min, dt_max / sqrt(1 + eta F'^2)), F' = (E^n - E^{n-1}) / dt_{n-1}, E the
+   energy (or the energy density when energy_scaled); dt_min on a fresh field.
+   pfc_run uses exactly this value. */
+int pfc_next_dt(pfc_state* s, double* dt);
+
+/* One step through host buffers: copies phin_host (N values, pinned memory
+   recommended) into phi^n keeping the energy history -- pass the field the
+   previous step returned -- advances by dt as pfc_step does, and copies
+   phi^{n+1} back into out_host.  The copies run on the state's stream. */
+int pfc_step_host(pfc_state* s, const double* phin_host, double dt, double* out_host, pfc_step_info* info);
+
+/* Kernel timing for roofline reports.  pfc_profile(s, 1) creates CUDA events
+   and from then on brackets every executed Schwarz-apply launch with a pair of
+   events on the state's stream; pfc_profile(s, 0) releases them.
+   pfc_profile_read: launches and summed device milliseconds of the applies
+   since profiling was enabled, the algorithmic bytes one apply moves (factor
+   entries read + block gather + core write), and the number of kernels this
+   library launched in the process so far (all kinds). */
+int pfc_profile(pfc_state* s, int enable);
+int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
+                     long long* kernel_launches);
+
+/* Human-readable name of a status code (static string). */
+const char* pfc_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFC_H */

@@ -1,0 +1,750 @@
+// C ABI of libpfc (include/pfc.h): state, workspace layout and the host-side
+// control of one time step -- inexact Newton with backtracking line search
+// (Sec. 4, Eq. newton), right-preconditioned restarted GMRES (Eq. hjacobi)
+// whose Arnoldi bookkeeping lives on the device, the left-RAS preconditioner
+// with factors built once per step and reused by every Newton iteration
+// (Sec. 5.2), and the adaptive time step of Eq. (sencondt).
+//
+// Every numeric step runs in the CUDA kernels of this library; the host only
+// sequences launches on the caller's stream and reads back a few scalars
+// (residual norms, GMRES iteration counts) to take the Newton and GMRES
+// decisions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/pfc.h"
+#include "pfc_internal.cuh"
+
+using pfc::BlockDesc;
+using pfc::Geo;
+using pfc::GmresCtl;
+using pfc::VecList;
+
+struct pfc_state {
+  pfc_grid grid;
+  pfc_params p;
+  Geo g;
+  double h, gamma;
+  cudaStream_t st;
+  int dim;
+  // fields (device, N doubles each)
+  double *phin, *phinm1, *Phi, *F, *q, *Pt, *Ft, *qt, *S, *W, *guess;
+  double *Vbuf, *Zbuf;  // (m+1) x N and m x N
+  // preconditioner
+  BlockDesc* blocks_dev;
+  int nblocks;
+  pfc::FactorStore fs;
+  double* lin_dev;
+  // reductions and control
+  GmresCtl* ctl;
+  double* partial;
+  double* red;   // device scalars: [0..7] general, [8..15] axpy reductions
+  int* status_dev;
+  // host mirrors (pinned)
+  GmresCtl* ctl_h;
+  double* red_h;
+  int* status_h;
+  // history for the adaptive step and the extrapolated guess
+  bool have_E, have_Em1, have_prev_dt, have_user_guess;
+  double E_n, E_nm1, dt_prev;
+  // kernel timing (pfc_profile)
+  bool prof;
+  cudaEvent_t ev[2 * pfc::kMaxRestart];
+  long long apply_launches;
+  double apply_ms;
+  double apply_bytes;
+};
+
+namespace pfc {
+namespace {
+long long g_launches = 0;  // host-side count; launches come from the calling thread
+}
+void count_launches(long long n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
+long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+}  // namespace pfc
+
+namespace {
+
+#define CU(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      fprintf(stderr, "libpfc: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return PFC_ECUDA;                                  \
+    }                                                    \
+  } while (0)
+
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    size_t off = total;
+    total += (bytes + 255) & ~(size_t)255;
+    return off;
+  }
+};
+
+struct Split {
+  int start, size;
+};
+
+std::vector<Split> split_axis(int n, int p) {
+  std::vector<Split> out;
+  const int base = n / p, extra = n % p;
+  int s = 0;
+  for (int r = 0; r < p; ++r) {
+    const int sz = base + (r < extra ? 1 : 0);
+    out.push_back({s, sz});
+    s += sz;
+  }
+  return out;
+}
+
+int validate(const pfc_grid* g, const pfc_params* p) {
+  if (!g || !p) return PFC_EINVAL;
+  if (g->dim != 2) return PFC_EINVAL;  // 3D blocks are built by a later entry point
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < 1 || g->n[a] > (1 << 20)) return PFC_EINVAL;
+  if (p->gmres_restart < 1 || p->gmres_restart > pfc::kMaxRestart) return PFC_EINVAL;
+  if (p->newton_max_it < 0 || p->gmres_max_it < 1 || p->overlap < 0) return PFC_EINVAL;
+  if (p->ras_kind != PFC_LEFT_RAS) return PFC_EINVAL;
+  if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
+  for (int a = 0; a < g->dim; ++a) {
+    if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
+    const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
+    if (core_max + 2 * p->overlap > g->n[a]) return PFC_EINVAL;
+  }
+  return PFC_OK;
+}
+
+void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>* out, int* n_max, int* kl_max) {
+  auto sx = split_axis((int)g->n[0], p->sub[0]);
+  auto sy = split_axis((int)g->n[1], p->sub[1]);
+  const int ov = p->overlap;
+  *n_max = 0;
+  *kl_max = 0;
+  for (int by = 0; by < p->sub[1]; ++by)
+    for (int bx = 0; bx < p->sub[0]; ++bx) {
+      BlockDesc b{};
+      b.x0 = sx[bx].start - ov;
+      b.y0 = sy[by].start - ov;
+      b.z0 = 0;
+      b.bx = sx[bx].size + 2 * ov;
+      b.by = sy[by].size + 2 * ov;
+      b.bz = 1;
+      b.ox = ov;
+      b.oy = ov;
+      b.oz = 0;
+      b.cx = sx[bx].size;
+      b.cy = sy[by].size;
+      b.cz = 1;
+      out->push_back(b);
+      const int n = b.bx * b.by;
+      const int kl = std::min(3 * b.bx, n - 1);
+      *n_max = std::max(*n_max, n);
+      *kl_max = std::max(*kl_max, kl);
+    }
+}
+
+struct Plan {
+  size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status;
+  size_t total;
+  int nblocks, n_max, kl_max;
+  size_t sL, sU, sP;
+  int lrow, ucol;
+  size_t partial_len;
+};
+
+int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
+  int rc = validate(g, p);
+  if (rc) return rc;
+  const long long N = g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
+  std::vector<BlockDesc> blocks;
+  build_blocks(g, p, &blocks, &pl->n_max, &pl->kl_max);
+  pl->nblocks = (int)blocks.size();
+  const size_t es = p->factor_prec == PFC_F64 ? 8 : (p->factor_prec == PFC_F32 ? 4 : 2);
+  // rows of L and columns of U padded to 8 elements: every block, row and chunk
+  // of rows starts on a 16-byte boundary and spans a multiple of 16 bytes (bulk copies)
+  pl->lrow = (pl->kl_max + 7) / 8 * 8;
+  pl->ucol = (2 * pl->kl_max + 1 + 7) / 8 * 8;
+  pl->sL = (size_t)pl->n_max * pl->lrow;
+  pl->sU = (size_t)pl->n_max * pl->ucol;
+  pl->sP = ((size_t)pl->n_max + 15) / 16 * 16;
+  const size_t vec = (size_t)N * 8;
+  const int m = p->gmres_restart;
+  const size_t tiles = (size_t)((g->n[0] + 31) / 32) * ((g->n[1] + 15) / 16);
+  pl->partial_len = std::max<size_t>(tiles * 2, (size_t)pfc::kRedCtas * (pfc::kMaxVecs + 2));
+  Layout L;
+  pl->phin = L.take(vec);
+  pl->phinm1 = L.take(vec);
+  pl->Phi = L.take(vec);
+  pl->F = L.take(vec);
+  pl->q = L.take(vec);
+  pl->Pt = L.take(vec);
+  pl->Ft = L.take(vec);
+  pl->qt = L.take(vec);
+  pl->S = L.take(vec);
+  pl->W = L.take(vec);
+  pl->guess = L.take(vec);
+  pl->V = L.take(vec * (m + 1));
+  pl->Z = L.take(vec * m);
+  pl->L = L.take(pl->sL * es * pl->nblocks);
+  pl->U = L.take(pl->sU * es * pl->nblocks);
+  pl->piv = L.take(pl->sP * pl->nblocks);
+  pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
+  pl->lin = L.take(sizeof(double) * 49);
+  pl->ctl = L.take(sizeof(GmresCtl));
+  pl->partial = L.take(sizeof(double) * pl->partial_len);
+  pl->red = L.take(sizeof(double) * 16);
+  pl->status = L.take(sizeof(int) * 4);
+  pl->total = L.total;
+  return PFC_OK;
+}
+
+// -(1/2) Delta_d L_gamma as a 7x7 table (2D), L_gamma = (1-gamma) + 2 Delta_d + Delta_d^2.
+void lin_stencil_2d(double h, double gamma, double* out49) {
+  double P1[7][7] = {};
+  P1[3][3] = -4.0;
+  P1[2][3] = P1[4][3] = P1[3][2] = P1[3][4] = 1.0;
+  auto conv = [](const double (*a)[7], const double (*b)[7], double (*c)[7]) {
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < 7; ++j) c[i][j] = 0.0;
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < 7; ++j) {
+        if (a[i][j] == 0.0) continue;
+        for (int k = 0; k < 7; ++k)
+          for (int l = 0; l < 7; ++l) {
+            if (b[k][l] == 0.0) continue;
+            const int y = i + k - 3, x = j + l - 3;
+            if (y >= 0 && y < 7 && x >= 0 && x < 7) c[y][x] += a[i][j] * b[k][l];
+          }
+      }
+  };
+  double P2[7][7], P3[7][7];
+  conv(P1, P1, P2);
+  conv(P2, P1, P3);
+  const double ih2 = 1.0 / (h * h), ih4 = ih2 * ih2, ih6 = ih4 * ih2;
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; j < 7; ++j)
+      out49[i * 7 + j] = -0.5 * ((1.0 - gamma) * ih2 * P1[i][j] + 2.0 * ih4 * P2[i][j] + ih6 * P3[i][j]);
+}
+
+// ---------------------------------------------------------------- building blocks of a step
+int sync_read(pfc_state* s, void* dst, const void* src, size_t bytes) {
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  return PFC_OK;
+}
+
+// F, q at Phi (or at the trial point Phi + lam (S - mean S)); returns ||F||^2 on the device in red[slot].
+int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, bool project, const double* phin,
+                  double idt, double* F, double* Pout, double* qout, int slot) {
+  int np = 0;
+  pfc::launch_residual2d(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, phin, idt, F, Pout, qout, s->partial, &np,
+                         s->st);
+  pfc::launch_reduce(s->partial, 1, np, s->red + slot, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+int factor_blocks(pfc_state* s, const double* q, double idt) {
+  // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx): blocks at most 42 cells wide in x
+  if (2 * s->fs.kl_max + 2 > 256) return PFC_EINVAL;
+  CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
+  pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// Right-preconditioned restarted GMRES for J S = -F, x0 = 0 (Eq. hjacobi).
+// V_0 = -F/||F||, Z_j = H^{-1} V_j, S = sum_j y_j Z_j.  Leaves sum(S) in red[9].
+int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
+  const long long N = s->g.n;
+  const int m = s->p.gmres_restart;
+  const int* done = &s->ctl->done;
+  const int* reorth = &s->ctl->reorth;
+  int total = 0;
+  int np = 0;
+  CU(cudaMemsetAsync(s->S, 0, sizeof(double) * N, s->st));
+  CU(cudaMemsetAsync(s->red + 8, 0, 2 * sizeof(double), s->st));
+  // first cycle: V_0 = F scaled by -1/||F||
+  const double* v0 = s->F;
+  double f2 = fnorm * fnorm;
+  CU(cudaMemcpyAsync(s->red + 10, &f2, sizeof(double), cudaMemcpyHostToDevice, s->st));
+  pfc::launch_gmres_init(s->ctl, s->red + 10, -1.0, tol, s->st);
+  while (true) {
+    VecList V{};
+    V.p[0] = v0;
+    for (int i = 1; i <= m; ++i) V.p[i] = s->Vbuf + (size_t)i * N;
+    VecList Z{};
+    for (int i = 0; i < m; ++i) Z.p[i] = s->Zbuf + (size_t)i * N;
+    int j = 0;
+    const int chunk = 3;
+    while (j < m) {
+      const int jstart = j;
+      const int jend = std::min(m, j + chunk);
+      for (; j < jend; ++j) {
+        double* w = s->Vbuf + (size_t)(j + 1) * N;
+        if (s->prof) CU(cudaEventRecord(s->ev[2 * j], s->st));
+        pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, V.p[j], &s->ctl->scale[j],
+                                (double*)Z.p[j], done, s->status_dev + 1, s->st);
+        if (s->prof) CU(cudaEventRecord(s->ev[2 * j + 1], s->st));
+        pfc::launch_jvp2d(s->g, Z.p[j], nullptr, s->q, idt, w, done, s->st);
+        VecList D = V;
+        D.p[j + 1] = w;
+        for (int pass = 0; pass < 2; ++pass) {
+          pfc::launch_multidot(D, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, s->st, &np);
+          pfc::launch_reduce(s->partial, j + 2, np, s->ctl->red, s->st);
+          pfc::launch_gmres_after_dot(s->ctl, j, pass, s->st);
+          pfc::launch_multiaxpy(w, V, j + 1, s->ctl->coef, -1.0, N, s->partial, done, pass ? reorth : nullptr, s->st,
+                                &np);
+          pfc::launch_reduce(s->partial, 1, np, s->red + 8, s->st);
+          pfc::launch_gmres_after_axpy(s->ctl, s->red + 8, j, pass, m, s->st);
+        }
+      }
+      CU(cudaGetLastError());
+      int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
+      if (rc) return rc;
+      if (s->prof) {  // only applies that ran (not the ones skipped after convergence)
+        const int ran_to = s->ctl_h->done ? std::min(s->ctl_h->its, jend) : jend;
+        for (int t = jstart; t < ran_to; ++t) {
+          float ms = 0.f;
+          CU(cudaEventElapsedTime(&ms, s->ev[2 * t], s->ev[2 * t + 1]));
+          s->apply_ms += ms;
+          s->apply_launches += 1;
+        }
+      }
+      if (s->ctl_h->done) break;
+    }
+    const int its = s->ctl_h->its;
+    total += its;
+    if (its > 0) {
+      pfc::launch_gmres_solve(s->ctl, s->st);
+      pfc::launch_multiaxpy(s->S, Z, its, s->ctl->y, 1.0, N, s->partial, nullptr, nullptr, s->st, &np);
+      pfc::launch_reduce(s->partial, 2, np, s->red + 8, s->st);  // red[8] = |S|^2, red[9] = sum S
+      CU(cudaGetLastError());
+    }
+    const double est = s->ctl_h->est;
+    if (!(est == est)) return PFC_ENAN;
+    if (est <= s->ctl_h->tol || s->ctl_h->breakdown) break;
+    if (total >= s->p.gmres_max_it) {
+      *its_out = total;
+      return PFC_EGMRES;
+    }
+    // restart: r = -F - J S
+    pfc::launch_jvp2d(s->g, s->S, nullptr, s->q, idt, s->W, nullptr, s->st);
+    pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
+    VecList R{};
+    R.p[0] = s->W;
+    pfc::launch_multidot(R, 1, s->W, N, s->partial, nullptr, nullptr, s->st, &np);
+    pfc::launch_reduce(s->partial, 1, np, s->red + 10, s->st);
+    pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, s->st);
+    v0 = s->W;
+    CU(cudaGetLastError());
+  }
+  *its_out = total;
+  return PFC_OK;
+}
+
+// One Newton solve of F(Phi) = 0 from the initial guess in s->Phi.  On success s->Phi holds phi^{n+1}.
+int newton(pfc_state* s, double dt, pfc_step_info* info) {
+  const double idt = 1.0 / dt;
+  const pfc_params& p = s->p;
+  int rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->F, nullptr, s->q, 0);
+  if (rc) return rc;
+  if ((rc = sync_read(s, s->red_h, s->red, sizeof(double)))) return rc;
+  const double r0 = std::sqrt(s->red_h[0]);
+  if (!(r0 == r0) || std::isinf(r0)) return PFC_ENAN;
+  const double target = std::max(p.newton_rtol * r0, p.newton_atol);
+  double rnorm = r0;
+  info->res_norm0 = r0;
+  int m = 0, gm_total = 0, cuts_total = 0;
+  bool factored = false;
+  while (rnorm > target && m < p.newton_max_it) {
+    if (!factored) {  // factors of J(Phi_0) reused by every Newton iteration of the step
+      if ((rc = factor_blocks(s, s->q, idt))) return rc;
+      factored = true;
+    }
+    int its = 0;
+    rc = gmres(s, idt, rnorm, std::max(p.gmres_rtol * rnorm, p.gmres_atol), &its);
+    gm_total += its;
+    if (rc) {
+      info->gmres_its = gm_total;
+      return rc;
+    }
+    if ((rc = sync_read(s, s->status_h, s->status_dev, 2 * sizeof(int)))) return rc;
+    if (s->status_h[0]) return s->status_h[0];
+    if (s->status_h[1]) return s->status_h[1];
+    // backtracking line search on f = ||F||^2 / 2 (Armijo, quadratic model)
+    const double f0 = 0.5 * rnorm * rnorm;
+    double lam = 1.0, ft = 0.0;
+    for (int cut = 0;; ++cut) {
+      if ((rc = eval_residual(s, s->Phi, s->S, lam, p.mass_projection != 0, s->phin, idt, s->Ft, s->Pt, s->qt, 1)))
+        return rc;
+      if ((rc = sync_read(s, s->red_h, s->red, 2 * sizeof(double)))) return rc;
+      ft = 0.5 * s->red_h[1];
+      if (!(ft == ft) || std::isinf(ft)) return PFC_ENAN;
+      if (ft <= (1.0 - 2.0 * p.ls_alpha * lam) * f0 || cut == p.ls_max_cuts) break;
+      const double lq = lam * lam * f0 / (ft - f0 + 2.0 * lam * f0);
+      lam = std::min(std::max(lq, 0.1 * lam), 0.5 * lam);
+      ++cuts_total;
+    }
+    std::swap(s->Phi, s->Pt);
+    std::swap(s->F, s->Ft);
+    std::swap(s->q, s->qt);
+    rnorm = std::sqrt(2.0 * ft);
+    ++m;
+  }
+  info->newton_its = m;
+  info->gmres_its = gm_total;
+  info->ls_cuts = cuts_total;
+  info->res_norm = rnorm;
+  if (rnorm > target) return PFC_ENEWTON;
+  return PFC_OK;
+}
+
+int energy_mass(pfc_state* s, const double* phi, double* E, double* M) {
+  int np = 0;
+  pfc::launch_energy2d(s->g, phi, s->partial, &np, s->st);
+  pfc::launch_reduce(s->partial, 2, np, s->red + 4, s->st);
+  CU(cudaGetLastError());
+  int rc = sync_read(s, s->red_h + 4, s->red + 4, 2 * sizeof(double));
+  if (rc) return rc;
+  if (E) *E = s->red_h[4] * s->g.hd;
+  if (M) *M = s->red_h[5] * s->g.hd;
+  return PFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pfc_default_params(pfc_params* p) {
+  if (!p) return PFC_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->newton_rtol = 1e-10;
+  p->newton_atol = 0.0;
+  p->newton_max_it = 50;
+  p->gmres_rtol = 1e-6;
+  p->gmres_atol = 0.0;
+  p->gmres_restart = 30;
+  p->gmres_max_it = 10000;
+  p->sub[0] = p->sub[1] = p->sub[2] = 1;
+  p->overlap = 1;
+  p->ras_kind = PFC_LEFT_RAS;
+  p->factor_prec = PFC_F64;
+  p->guess = PFC_GUESS_PREV;
+  p->mass_projection = 1;
+  p->ls_alpha = 1e-4;
+  p->ls_max_cuts = 10;
+  p->dt_min = 1e-2;
+  p->dt_max = 10.0;
+  p->eta = 5000.0;
+  p->energy_scaled = 1;
+  return PFC_OK;
+}
+
+int pfc_workspace_size(const pfc_grid* g, const pfc_params* p, size_t* bytes) {
+  if (!bytes) return PFC_EINVAL;
+  Plan pl;
+  int rc = make_plan(g, p, &pl);
+  if (rc) return rc;
+  *bytes = pl.total;
+  return PFC_OK;
+}
+
+int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, void* ws, size_t bytes,
+               void* cuda_stream, pfc_state** out) {
+  if (!out || !ws || !(h > 0.0) || !(eps == eps)) return PFC_EINVAL;
+  *out = nullptr;
+  Plan pl;
+  int rc = make_plan(g, p, &pl);
+  if (rc) return rc;
+  if (bytes < pl.total) return PFC_ENOMEM;
+  if (((uintptr_t)ws & 255) != 0) return PFC_EINVAL;
+  pfc_state* s = new (std::nothrow) pfc_state();
+  if (!s) return PFC_ENOMEM;
+  s->grid = *g;
+  s->p = *p;
+  s->h = h;
+  s->gamma = eps;
+  s->dim = g->dim;
+  s->st = (cudaStream_t)cuda_stream;
+  s->g.nx = (int)g->n[0];
+  s->g.ny = (int)g->n[1];
+  s->g.nz = g->dim == 3 ? (int)g->n[2] : 1;
+  s->g.n = (long long)s->g.nx * s->g.ny * s->g.nz;
+  s->g.ih2 = 1.0 / (h * h);
+  s->g.gamma = eps;
+  s->g.hd = g->dim == 3 ? h * h * h : h * h;
+  char* base = (char*)ws;
+  auto at = [&](size_t off) { return (void*)(base + off); };
+  s->phin = (double*)at(pl.phin);
+  s->phinm1 = (double*)at(pl.phinm1);
+  s->Phi = (double*)at(pl.Phi);
+  s->F = (double*)at(pl.F);
+  s->q = (double*)at(pl.q);
+  s->Pt = (double*)at(pl.Pt);
+  s->Ft = (double*)at(pl.Ft);
+  s->qt = (double*)at(pl.qt);
+  s->S = (double*)at(pl.S);
+  s->W = (double*)at(pl.W);
+  s->guess = (double*)at(pl.guess);
+  s->Vbuf = (double*)at(pl.V);
+  s->Zbuf = (double*)at(pl.Z);
+  s->fs.L = at(pl.L);
+  s->fs.U = at(pl.U);
+  s->fs.piv = (uint8_t*)at(pl.piv);
+  s->fs.strideL = pl.sL;
+  s->fs.strideU = pl.sU;
+  s->fs.strideP = pl.sP;
+  s->fs.lrow = pl.lrow;
+  s->fs.ucol = pl.ucol;
+  s->fs.prec = p->factor_prec;
+  s->fs.kl_max = pl.kl_max;
+  s->fs.n_max = pl.n_max;
+  s->nblocks = pl.nblocks;
+  s->blocks_dev = (BlockDesc*)at(pl.blocks);
+  s->lin_dev = (double*)at(pl.lin);
+  s->ctl = (GmresCtl*)at(pl.ctl);
+  s->partial = (double*)at(pl.partial);
+  s->red = (double*)at(pl.red);
+  s->status_dev = (int*)at(pl.status);
+  if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess) {
+    pfc_destroy(s);
+    return PFC_ECUDA;
+  }
+  std::vector<BlockDesc> blocks;
+  int nm, km;
+  build_blocks(g, p, &blocks, &nm, &km);
+  {  // algorithmic bytes of one Schwarz apply: factors + pivots read, block gather, core write
+    const double es = p->factor_prec == PFC_F64 ? 8.0 : (p->factor_prec == PFC_F32 ? 4.0 : 2.0);
+    double bytes = 0.0;
+    for (const BlockDesc& b : blocks) {
+      const double n = (double)b.bx * b.by;
+      const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
+      const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
+      bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
+    }
+    s->apply_bytes = bytes;
+  }
+  double lin[49];
+  lin_stencil_2d(h, eps, lin);
+  if (cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
+                      s->st) != cudaSuccess ||
+      cudaMemcpyAsync(s->lin_dev, lin, sizeof(lin), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemsetAsync(s->phin, 0, sizeof(double) * s->g.n, s->st) != cudaSuccess ||
+      cudaMemsetAsync(s->phinm1, 0, sizeof(double) * s->g.n, s->st) != cudaSuccess ||
+      cudaMemsetAsync(s->red, 0, sizeof(double) * 16, s->st) != cudaSuccess ||
+      cudaStreamSynchronize(s->st) != cudaSuccess) {
+    pfc_destroy(s);
+    return PFC_ECUDA;
+  }
+  *out = s;
+  return PFC_OK;
+}
+
+void pfc_destroy(pfc_state* s) {
+  if (!s) return;
+  pfc_profile(s, 0);
+  if (s->ctl_h) cudaFreeHost(s->ctl_h);
+  if (s->red_h) cudaFreeHost(s->red_h);
+  if (s->status_h) cudaFreeHost(s->status_h);
+  delete s;
+}
+
+int pfc_set_field(pfc_state* s, const double* phi, int on_device) {
+  if (!s || !phi) return PFC_EINVAL;
+  const size_t b = sizeof(double) * s->g.n;
+  CU(cudaMemcpyAsync(s->phin, phi, b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+  CU(cudaMemcpyAsync(s->phinm1, s->phin, b, cudaMemcpyDeviceToDevice, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  s->have_E = s->have_Em1 = s->have_prev_dt = s->have_user_guess = false;
+  return PFC_OK;
+}
+
+int pfc_get_field(pfc_state* s, double* out, int on_device) {
+  if (!s || !out) return PFC_EINVAL;
+  CU(cudaMemcpyAsync(out, s->phin, sizeof(double) * s->g.n,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  return PFC_OK;
+}
+
+int pfc_set_guess(pfc_state* s, const double* guess, int on_device) {
+  if (!s || !guess) return PFC_EINVAL;
+  CU(cudaMemcpyAsync(s->guess, guess, sizeof(double) * s->g.n,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+  s->have_user_guess = true;
+  return PFC_OK;
+}
+
+int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
+  if (!s || !(dt > 0.0) || std::isinf(dt)) return PFC_EINVAL;
+  pfc_step_info info{};
+  info.dt = dt;
+  const size_t b = sizeof(double) * s->g.n;
+  // initial guess Phi_0
+  if (s->p.guess == PFC_GUESS_EXTRAP && s->have_prev_dt) {
+    pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, s->g.n, s->st);
+  } else if (s->p.guess == PFC_GUESS_USER && s->have_user_guess) {
+    CU(cudaMemcpyAsync(s->Phi, s->guess, b, cudaMemcpyDeviceToDevice, s->st));
+  } else {
+    CU(cudaMemcpyAsync(s->Phi, s->phin, b, cudaMemcpyDeviceToDevice, s->st));
+  }
+  CU(cudaGetLastError());
+  int rc = newton(s, dt, &info);
+  s->have_user_guess = false;
+  if (rc) {
+    info.status = rc;
+    if (info_out) *info_out = info;
+    return rc;
+  }
+  if (!s->have_E) {
+    if ((rc = energy_mass(s, s->phin, &s->E_n, nullptr))) return rc;
+    s->have_E = true;
+  }
+  // accept: phi^{n-1} <- phi^n, phi^n <- Phi
+  double* old = s->phinm1;
+  s->phinm1 = s->phin;
+  s->phin = s->Phi;
+  s->Phi = old;
+  double E = 0.0, M = 0.0;
+  if ((rc = energy_mass(s, s->phin, &E, &M))) return rc;
+  s->E_nm1 = s->E_n;
+  s->E_n = E;
+  s->have_Em1 = true;
+  s->dt_prev = dt;
+  s->have_prev_dt = true;
+  info.energy = E;
+  info.mass = M;
+  info.status = PFC_OK;
+  if (info_out) *info_out = info;
+  return PFC_OK;
+}
+
+int pfc_next_dt(pfc_state* s, double* dt_out) {
+  if (!s || !dt_out) return PFC_EINVAL;
+  const double area = s->g.hd * (double)s->g.n;
+  const double scale = s->p.energy_scaled ? 1.0 / area : 1.0;
+  double dt = s->p.dt_min;
+  if (s->have_Em1 && s->have_prev_dt) {  // Eq. (sencondt)
+    const double fp = (s->E_n - s->E_nm1) * scale / s->dt_prev;
+    dt = std::max(s->p.dt_min, s->p.dt_max / std::sqrt(1.0 + s->p.eta * fp * fp));
+  }
+  *dt_out = dt;
+  return PFC_OK;
+}
+
+int pfc_step_host(pfc_state* s, const double* phin_host, double dt, double* out_host, pfc_step_info* info) {
+  if (!s || !phin_host || !out_host) return PFC_EINVAL;
+  const size_t b = sizeof(double) * s->g.n;
+  CU(cudaMemcpyAsync(s->phin, phin_host, b, cudaMemcpyHostToDevice, s->st));
+  int rc = pfc_step(s, dt, info);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(out_host, s->phin, b, cudaMemcpyDeviceToHost, s->st));
+  CU(cudaStreamSynchronize(s->st));
+  return PFC_OK;
+}
+
+int pfc_profile(pfc_state* s, int enable) {
+  if (!s) return PFC_EINVAL;
+  if (enable && !s->prof) {
+    for (int i = 0; i < 2 * pfc::kMaxRestart; ++i) CU(cudaEventCreate(&s->ev[i]));
+    s->prof = true;
+  } else if (!enable && s->prof) {
+    cudaStreamSynchronize(s->st);
+    for (int i = 0; i < 2 * pfc::kMaxRestart; ++i) cudaEventDestroy(s->ev[i]);
+    s->prof = false;
+  }
+  s->apply_launches = 0;
+  s->apply_ms = 0.0;
+  return PFC_OK;
+}
+
+int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
+                     long long* kernel_launches) {
+  if (!s) return PFC_EINVAL;
+  if (apply_launches) *apply_launches = s->apply_launches;
+  if (apply_ms) *apply_ms = s->apply_ms;
+  if (apply_bytes) *apply_bytes = s->apply_bytes;
+  if (kernel_launches) *kernel_launches = pfc::launches_so_far();
+  return PFC_OK;
+}
+
+int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step) {
+  if (!s || nsteps < 0) return PFC_EINVAL;
+  for (int n = 0; n < nsteps; ++n) {
+    double dt = 0.0;
+    pfc_next_dt(s, &dt);
+    pfc_step_info info{};
+    int rc = pfc_step(s, dt, &info);
+    if (per_step) per_step[n] = info;
+    if (rc) return rc;
+  }
+  return PFC_OK;
+}
+
+int pfc_energy(pfc_state* s, double* F) {
+  if (!s || !F) return PFC_EINVAL;
+  return energy_mass(s, s->phin, F, nullptr);
+}
+
+int pfc_mass(pfc_state* s, double* m) {
+  if (!s || !m) return PFC_EINVAL;
+  return energy_mass(s, s->phin, nullptr, m);
+}
+
+int pfc_residual(pfc_state* s, const double* Phi, const double* phin, double dt, double* F_out, double* norm) {
+  if (!s || !Phi || !phin || !F_out || !(dt > 0.0)) return PFC_EINVAL;
+  int rc = eval_residual(s, Phi, nullptr, 0.0, false, phin, 1.0 / dt, F_out, nullptr, nullptr, 2);
+  if (rc) return rc;
+  if ((rc = sync_read(s, s->red_h + 2, s->red + 2, sizeof(double)))) return rc;
+  if (norm) *norm = std::sqrt(s->red_h[2]);
+  return PFC_OK;
+}
+
+int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v, double dt, double* Jv) {
+  if (!s || !Phi || !phin || !v || !Jv || !(dt > 0.0)) return PFC_EINVAL;
+  pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  pfc::launch_jvp2d(s->g, v, nullptr, s->qt, 1.0 / dt, Jv, nullptr, s->st);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s->st));
+  return PFC_OK;
+}
+
+int pfc_precond_apply(pfc_state* s, const double* Phi, const double* phin, double dt, const double* r, double* z) {
+  if (!s || !Phi || !phin || !r || !z || !(dt > 0.0)) return PFC_EINVAL;
+  pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  int rc = factor_blocks(s, s->qt, 1.0 / dt);
+  if (rc) return rc;
+  pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, nullptr, z, nullptr, s->status_dev + 1, s->st);
+  CU(cudaGetLastError());
+  if ((rc = sync_read(s, s->status_h, s->status_dev, 2 * sizeof(int)))) return rc;
+  if (s->status_h[0]) return s->status_h[0];
+  return s->status_h[1] ? s->status_h[1] : PFC_OK;
+}
+
+const char* pfc_status_str(int st) {
+  switch (st) {
+    case PFC_OK: return "ok";
+    case PFC_EINVAL: return "invalid argument";
+    case PFC_ENOMEM: return "workspace too small";
+    case PFC_ECUDA: return "CUDA error";
+    case PFC_ENEWTON: return "Newton did not converge";
+    case PFC_EGMRES: return "GMRES did not converge";
+    case PFC_ESINGULAR: return "zero pivot in a subdomain factorisation";
+    case PFC_ENAN: return "NaN or Inf in a residual norm";
+    case PFC_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

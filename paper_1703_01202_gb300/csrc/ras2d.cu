@@ -1,0 +1,401 @@
+// Restricted additive Schwarz preconditioner of Sec. 4 (left-RAS, Eq. ras) for
+// 2D grids: batched assembly + factorisation of every subdomain matrix A_k
+// (Eq. Ak with the improved boundary condition: phi = 0 on the 3-layer ring,
+// which makes A_k the principal submatrix of J on the block), and the batched
+// apply z = sum_k (R_k^0)^T A_k^{-1} R_k^delta r.
+//
+// Design (GB300): A_k of a bx x by block ordered x-fastest is banded with
+// half-bandwidth kl = 3 bx (the radius-3 stencil reaches 3 rows up/down).  LU
+// with partial pivoting keeps L inside kl sub-diagonals and U inside 2 kl
+// super-diagonals, so each block is factored by a sliding-window band LU: one
+// CTA holds only the kl+1 active rows in shared memory (columns in a ring of
+// RING slots), generating each new row of A_k on the fly from the stencil
+// table and q, and streams L (one row of lrow >= kl multipliers per step) and U
+// (one column of ucol >= 2kl+1 entries per step, diagonal stored inverted) out
+// in the storage precision, pivots as 8-bit offsets.  This is the dense LU with
+// partial pivoting of A_k restricted to its band: same pivots, same factors.
+//
+// The apply is a batched pair of banded triangular solves, one warp per block.
+// The solve itself is a chain of n dependent steps, so the factor stream is
+// decoupled from it: each warp runs a two-stage ring of TMA bulk copies
+// (cp.async.bulk global->shared, completion on an mbarrier) that fetches the
+// next chunk of L rows / U columns while the current chunk is consumed.  The
+// kernel is bound by the factor bytes it streams from HBM.
+#include <cuda_bf16.h>
+
+#include "../../include/pfc.h"
+#include "pfc_internal.cuh"
+
+namespace pfc {
+namespace {
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+template <typename T>
+__device__ __forceinline__ T to_store(double v);
+template <>
+__device__ __forceinline__ double to_store<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_store<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+
+template <typename TC, typename TS>
+__device__ __forceinline__ TC from_store(TS v) { return (TC)v; }
+template <>
+__device__ __forceinline__ float from_store<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---- TMA bulk copy + mbarrier helpers (PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity to complete; gives up after about
+// two seconds of SM clock and returns false (the caller records PFC_ETIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+  return true;
+}
+
+// Entry (r, c) of A_k = R_k J R_k^T, J = I/dt - (1/2) Delta_d L_gamma - Delta_d diag(q) (Eq. Jacobi).
+// qb: q on the block (block-local order), lin: the 7x7 table of -(1/2) Delta_d L_gamma.
+__device__ __forceinline__ double jac_entry(int bx, double ih2, const double* qb, double idt, const double* lin,
+                                            int r, int c) {
+  const int ar = r % bx, br = r / bx, ac = c % bx, bc = c / bx;
+  const int dx = ac - ar, dy = bc - br;
+  const int ad = abs(dx) + abs(dy);
+  if (ad > 3) return 0.0;
+  double v = lin[(dy + 3) * 7 + (dx + 3)];
+  if (ad <= 1) v -= (ad == 0 ? -4.0 * ih2 : ih2) * qb[c];
+  if (ad == 0) v += idt;
+  return v;
+}
+
+template <typename TC, typename TS, int RING>
+__global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
+                                                  const double* __restrict__ q, double idt,
+                                                  const double* __restrict__ lin, FactorStore fs,
+                                                  int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TC s_dinv;
+  const BlockDesc B = blocks[blockIdx.x];
+  const int n = B.bx * B.by;
+  const int kl = min(3 * B.bx, n - 1);
+  const int ku2 = min(2 * kl, n - 1);
+  const int W = kl + 1;
+  const int lrow = fs.lrow, ucol = fs.ucol;
+  double* qb = reinterpret_cast<double*>(smem);  // q on the block, block-local order
+  double* lin_s = qb + fs.n_max;                 // 7 x 7 stencil table
+  TC* A = reinterpret_cast<TC*>(lin_s + 49);     // W rows x RING column slots
+  TC* lv = A + (size_t)W * RING;                 // multipliers of the current step
+  TC* uv = lv + RING;                            // U row of the current step
+  int* slot = reinterpret_cast<int*>(uv + RING);  // window position (mod W) -> row slot
+  TS* L = (TS*)fs.L + blockIdx.x * fs.strideL;
+  TS* U = (TS*)fs.U + blockIdx.x * fs.strideU;
+  uint8_t* piv = fs.piv + blockIdx.x * fs.strideP;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int bx = B.bx;
+  const double ih2 = g.ih2;
+
+  for (int t = tid; t < n; t += nt)
+    qb[t] = q[wrap(B.x0 + t % bx, g.nx) + (long long)g.nx * wrap(B.y0 + t / bx, g.ny)];
+  for (int t = tid; t < 49; t += nt) lin_s[t] = lin[t];
+  for (int w = tid; w < W; w += nt) slot[w] = w;
+  __syncthreads();
+  for (int idx = tid; idx < W * RING; idx += nt) {
+    const int pos = idx / RING, col = idx - pos * RING;
+    A[idx] = (pos < n && col < n) ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, pos, col) : (TC)0;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < n; ++k) {
+    const int kw = k % RING;
+    const int last = min(k + kl, n - 1);
+    if (tid < 32) {  // partial pivoting: largest |a_ik| over the window, first on ties
+      TC best = (TC)-1;
+      int bp = k;
+      for (int pos = k + tid; pos <= last; pos += 32) {
+        const TC v = abs(A[slot[pos % W] * RING + kw]);
+        if (v > best) {
+          best = v;
+          bp = pos;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const TC ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ob > best || (ob == best && op < bp)) {
+          best = ob;
+          bp = op;
+        }
+      }
+      if (tid == 0) {
+        const int sk = slot[k % W], sp = slot[bp % W];
+        slot[k % W] = sp;
+        slot[bp % W] = sk;
+        piv[k] = (uint8_t)(bp - k);
+        TC d = A[sp * RING + kw];
+        if (d == (TC)0) {
+          atomicExch(status, PFC_ESINGULAR);
+          d = (TC)1;
+        }
+        s_dinv = (TC)1 / d;
+      }
+    }
+    __syncthreads();
+    const int sk = slot[k % W];
+    const TC dinv = s_dinv;
+    for (int i = tid; i < lrow; i += nt) {
+      const int pos = k + 1 + i;
+      TC l = (TC)0;
+      if (i < kl && pos < n) l = A[slot[pos % W] * RING + kw] * dinv;
+      L[(size_t)k * lrow + i] = to_store<TS>((double)l);
+      if (i < kl) lv[i] = l;
+    }
+    for (int j = tid; j < ucol; j += nt) {
+      const int col = k + j;
+      TC u = (TC)0;
+      if (j <= ku2 && col < n) {
+        u = A[sk * RING + col % RING];
+        U[(size_t)col * ucol + j] = to_store<TS>((double)(j == 0 ? dinv : u));
+      }
+      if (j <= ku2) uv[j] = u;
+    }
+    // U column k's entries above the band (j > ku2) stay zero for the bulk copies
+    for (int j = ku2 + 1 + tid; j < ucol; j += nt) U[(size_t)k * ucol + j] = to_store<TS>(0.0);
+    __syncthreads();
+    // rank-1 update of the active window
+    for (int j = 1 + tid; j <= ku2; j += nt) {
+      const TC u = uv[j];
+      if (u != (TC)0 && k + j < n) {
+        const int cw = (k + j) % RING;
+        const int rows = min(kl, n - 1 - k);
+        for (int i = 0; i < rows; ++i) {
+          TC* a = &A[slot[(k + 1 + i) % W] * RING + cw];
+          *a = *a - lv[i] * u;
+        }
+      }
+    }
+    // the column entering the band must start at zero in the rows that stay
+    const int cz = (k + 1 + ku2) % RING;
+    for (int i = tid; i < kl; i += nt) A[slot[(k + 1 + i) % W] * RING + cz] = (TC)0;
+    // next row of A_k enters the slot the pivot row leaves
+    const int rnew = k + 1 + kl;
+    if (rnew < n) {
+      TC* row = &A[sk * RING];
+      const int base = k + 1;
+      for (int t = tid; t < RING; t += nt) {
+        const int col = base + (((t - base) % RING) + RING) % RING;
+        row[t] = col < n ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, rnew, col) : (TC)0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Shared-memory carve-out of one warp of the apply kernel.
+struct ApplySmem {
+  size_t stage, buf, piv, total;
+};
+__host__ __device__ inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+template <typename TC, typename TS, int CH>
+__host__ __device__ inline ApplySmem apply_smem(int lrow, int ucol, int nmax) {
+  ApplySmem s;
+  const int row = lrow > ucol ? lrow : ucol;
+  s.stage = rup((size_t)CH * row * sizeof(TS), 128);
+  s.buf = rup((size_t)nmax * sizeof(TC), 16);
+  s.piv = rup((size_t)nmax, 16);
+  s.total = 2 * s.stage + s.buf + s.piv + 16;
+  s.total = rup(s.total, 128);
+  return s;
+}
+
+template <typename TC, typename TS, int CH, int WPC>
+__global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc* __restrict__ blocks, int nblocks,
+                                                          FactorStore fs, const double* __restrict__ r,
+                                                          const double* __restrict__ rscale, double* __restrict__ z,
+                                                          const int* __restrict__ skip, int* __restrict__ err) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * WPC + w;
+  if (b >= nblocks) return;  // warp-uniform; no CTA-wide barrier follows
+  const int lrow = fs.lrow, ucol = fs.ucol;
+  const ApplySmem lay = apply_smem<TC, TS, CH>(lrow, ucol, fs.n_max);
+  unsigned char* base = smem + (size_t)w * lay.total;
+  auto stage = [&](int st) { return reinterpret_cast<TS*>(base + st * lay.stage); };
+  TC* buf = reinterpret_cast<TC*>(base + 2 * lay.stage);
+  uint8_t* pv = base + 2 * lay.stage + lay.buf;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * lay.stage + lay.buf + lay.piv);
+
+  const BlockDesc B = blocks[b];
+  const int bx = B.bx, n = B.bx * B.by;
+  const int kl = min(3 * bx, n - 1), ku2 = min(2 * kl, n - 1);
+  const TS* L = (const TS*)fs.L + b * fs.strideL;
+  const TS* U = (const TS*)fs.U + b * fs.strideU;
+  const uint8_t* piv = fs.piv + b * fs.strideP;
+  const int nc = (n + CH - 1) / CH;
+  const int total = 2 * nc;  // forward chunks 0..nc-1, then backward chunks nc-1..0
+
+  auto issue = [&](int t) {  // lane 0: bulk-copy chunk t into stage t & 1
+    const int st = t & 1;
+    const int c = t < nc ? t : 2 * nc - 1 - t;
+    const int rows = min(CH, n - c * CH);
+    const TS* src = t < nc ? L + (size_t)c * CH * lrow : U + (size_t)c * CH * ucol;
+    const uint32_t bytes = (uint32_t)(rows * (t < nc ? lrow : ucol) * sizeof(TS));
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(stage(st), src, bytes, &bar[st]);
+  };
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    issue(0);
+    if (total > 1) issue(1);
+  }
+  for (int t = lane; t < n; t += 32) {  // restriction R_k^delta (periodic wrap) and pivots
+    const int a = t % bx, c = t / bx;
+    buf[t] = (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)];
+    pv[t] = piv[t];
+  }
+  __syncwarp();
+  uint32_t phase0 = 0, phase1 = 0;
+  for (int t = 0; t < total; ++t) {
+    const int st = t & 1;
+    const bool ok = mbar_wait_bounded(&bar[st], st ? phase1 : phase0);
+    if (st) phase1 ^= 1; else phase0 ^= 1;
+    if (!__all_sync(0xffffffffu, ok)) {  // give up: record, drain the other copy in flight, leave
+      if (lane == 0) {
+        atomicExch(err, PFC_ETIMEOUT);
+        mbar_wait_bounded(&bar[st], st ? phase1 ^ 1 : phase0 ^ 1);
+        if (t + 1 < total) mbar_wait_bounded(&bar[st ^ 1], st ? phase0 : phase1);
+      }
+      return;
+    }
+    const TS* data = stage(st);
+    if (t < nc) {  // forward: row interchange P_k, then elimination L_k
+      const int c = t, rows = min(CH, n - c * CH);
+      for (int kk = 0; kk < rows; ++kk) {
+        const int k = c * CH + kk;
+        const TS* lk = data + kk * lrow;
+        const int p = k + pv[k];
+        const TC bk = buf[k], bp = buf[p];
+        __syncwarp();
+        const int cnt = min(kl, n - 1 - k);
+        for (int i = lane; i < cnt; i += 32) {
+          const int tt = k + 1 + i;
+          const TC val = (tt == p) ? bk : buf[tt];
+          buf[tt] = val - from_store<TC, TS>(lk[i]) * bp;
+        }
+        if (lane == 0) buf[k] = bp;
+        __syncwarp();
+      }
+    } else {  // backward, column oriented: x_k = b_k / u_kk, b_{k-j} -= u_{k-j,k} x_k
+      const int c = 2 * nc - 1 - t, rows = min(CH, n - c * CH);
+      for (int kk = rows - 1; kk >= 0; --kk) {
+        const int k = c * CH + kk;
+        const TS* uk = data + kk * ucol;
+        const TC xk = buf[k] * from_store<TC, TS>(uk[0]);
+        __syncwarp();
+        const int top = min(ku2, k);
+        for (int j = 1 + lane; j <= top; j += 32) buf[k - j] -= from_store<TC, TS>(uk[j]) * xk;
+        if (lane == 0) buf[k] = xk;
+        __syncwarp();
+      }
+    }
+    if (lane == 0 && t + 2 < total) issue(t + 2);  // refill the stage just consumed
+  }
+  const double sc = rscale ? *rscale : 1.0;
+  for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
+    const int a = t % bx, c = t / bx;
+    if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
+      z[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] = sc * (double)buf[t];
+  }
+}
+
+template <typename TC, typename TS>
+void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
+                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
+  const int W = fs.kl_max + 1;
+  if (2 * fs.kl_max + 2 <= 128) {
+    const size_t smem = (size_t)(fs.n_max + 49) * 8 + (size_t)(W * 128 + 2 * 128) * sizeof(TC) + W * sizeof(int) + 16;
+    cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_factor2d<TC, TS, 128><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+  } else {
+    const size_t smem = (size_t)(fs.n_max + 49) * 8 + (size_t)(W * 256 + 2 * 256) * sizeof(TC) + W * sizeof(int) + 16;
+    cudaFuncSetAttribute(k_factor2d<TC, TS, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_factor2d<TC, TS, 256><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+  }
+  count_launches(1);
+}
+
+template <typename TC, typename TS, int CH>
+void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
+                    const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
+  constexpr int WPC = 4;
+  const ApplySmem lay = apply_smem<TC, TS, CH>(fs.lrow, fs.ucol, fs.n_max);
+  const size_t smem = WPC * lay.total;
+  cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ras_apply2d<TC, TS, CH, WPC><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale,
+                                                                                    z, skip, err);
+  count_launches(1);
+}
+
+}  // namespace
+
+size_t factor_smem_bytes(int prec, int kl) {
+  const int ring = (2 * kl + 2 <= 128) ? 128 : 256;
+  const size_t tc = prec == PFC_F64 ? 8 : 4;
+  return (size_t)((kl + 1) * ring + 2 * ring) * tc + (kl + 1) * sizeof(int) + 16;
+}
+
+void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
+                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
+  if (fs.prec == PFC_F64)
+    factor_dispatch<double, double>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+  else if (fs.prec == PFC_F32)
+    factor_dispatch<float, float>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+  else
+    factor_dispatch<float, __nv_bfloat16>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+}
+
+void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
+                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
+  // chunk length chosen so one stage is about 3.5 KB for every storage type
+  if (fs.prec == PFC_F64)
+    apply_dispatch<double, double, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+  else if (fs.prec == PFC_F32)
+    apply_dispatch<float, float, 8>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+  else
+    apply_dispatch<float, __nv_bfloat16, 16>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+}
+
+}  // namespace pfc

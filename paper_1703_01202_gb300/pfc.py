@@ -1,0 +1,283 @@
+"""ctypes binding of libpfc (include/pfc.h).
+
+Argument marshalling only: every numeric step runs in the CUDA kernels of
+libpfc.so.  PyTorch supplies the device workspace and the stream.  The library
+is loaded on first use; if it is missing or fails to load, the call raises --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_longlong, c_size_t, c_void_p
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpfc.so")
+
+PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA = 0, -1, -2, -3
+PFC_ENEWTON, PFC_EGMRES, PFC_ESINGULAR, PFC_ENAN, PFC_ETIMEOUT = -4, -5, -6, -7, -8
+PFC_F64, PFC_F32, PFC_BF16 = 0, 1, 2
+PFC_AS, PFC_LEFT_RAS, PFC_RIGHT_RAS = 0, 1, 2
+PFC_GUESS_PREV, PFC_GUESS_EXTRAP, PFC_GUESS_USER = 0, 1, 2
+
+
+class pfc_grid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int64 * 3)]
+
+
+class pfc_params(ctypes.Structure):
+    _fields_ = [
+        ("newton_rtol", c_double), ("newton_atol", c_double), ("newton_max_it", c_int),
+        ("gmres_rtol", c_double), ("gmres_atol", c_double), ("gmres_restart", c_int), ("gmres_max_it", c_int),
+        ("sub", c_int * 3), ("overlap", c_int), ("ras_kind", c_int), ("factor_prec", c_int), ("guess", c_int),
+        ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
+        ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
+    ]
+
+
+class pfc_step_info(ctypes.Structure):
+    _fields_ = [
+        ("status", c_int), ("newton_its", c_int), ("gmres_its", c_int), ("ls_cuts", c_int),
+        ("dt", c_double), ("energy", c_double), ("mass", c_double), ("res_norm0", c_double), ("res_norm", c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PfcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+# (name, restype, argtypes) of every entry point declared in include/pfc.h
+_SIGNATURES = [
+    ("pfc_default_params", c_int, [POINTER(pfc_params)]),
+    ("pfc_workspace_size", c_int, [POINTER(pfc_grid), POINTER(pfc_params), POINTER(c_size_t)]),
+    ("pfc_create", c_int, [POINTER(pfc_grid), c_double, c_double, POINTER(pfc_params), c_void_p, c_size_t, c_void_p,
+                           POINTER(c_void_p)]),
+    ("pfc_destroy", None, [c_void_p]),
+    ("pfc_set_field", c_int, [c_void_p, c_void_p, c_int]),
+    ("pfc_get_field", c_int, [c_void_p, c_void_p, c_int]),
+    ("pfc_set_guess", c_int, [c_void_p, c_void_p, c_int]),
+    ("pfc_step", c_int, [c_void_p, c_double, POINTER(pfc_step_info)]),
+    ("pfc_run", c_int, [c_void_p, c_int, POINTER(pfc_step_info)]),
+    ("pfc_energy", c_int, [c_void_p, POINTER(c_double)]),
+    ("pfc_mass", c_int, [c_void_p, POINTER(c_double)]),
+    ("pfc_residual", c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(c_double)]),
+    ("pfc_jvp", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_void_p]),
+    ("pfc_precond_apply", c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
+    ("pfc_next_dt", c_int, [c_void_p, POINTER(c_double)]),
+    ("pfc_step_host", c_int, [c_void_p, c_void_p, c_double, c_void_p, POINTER(pfc_step_info)]),
+    ("pfc_profile", c_int, [c_void_p, c_int]),
+    ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
+                                 POINTER(c_longlong)]),
+    ("pfc_status_str", c_char_p, [c_int]),
+]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libpfc.so (raises if it is absent: build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpfc.so not built ({LIB_PATH}); run paper_1703_01202_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(st: int) -> str:
+    try:
+        return lib().pfc_status_str(st).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(st: int, what: str):
+    if st != PFC_OK:
+        raise PfcError(st, what)
+
+
+def default_params(**over) -> pfc_params:
+    p = pfc_params()
+    _check(lib().pfc_default_params(ctypes.byref(p)), "pfc_default_params")
+    for k, v in over.items():
+        if k == "sub":
+            for a, s in enumerate(v):
+                p.sub[a] = int(s)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def make_grid(shape: Sequence[int]) -> pfc_grid:
+    """Grid from an array shape in array-axis order ((Ny, Nx) or (Nz, Ny, Nx))."""
+    g = pfc_grid()
+    g.dim = len(shape)
+    rev = list(shape)[::-1]
+    for a in range(3):
+        g.n[a] = int(rev[a]) if a < len(rev) else 1
+    return g
+
+
+def workspace_size(shape: Sequence[int], params: pfc_params) -> int:
+    out = c_size_t(0)
+    _check(lib().pfc_workspace_size(ctypes.byref(make_grid(shape)), ctypes.byref(params), ctypes.byref(out)),
+           "pfc_workspace_size")
+    return out.value
+
+
+class Solver:
+    """One PFC state on the current CUDA device: a thin owner of the workspace
+    (a torch uint8 tensor) and of the pfc_state handle."""
+
+    def __init__(self, shape: Sequence[int], h: float, gamma: float, params: Optional[pfc_params] = None,
+                 stream=None, device: str = "cuda"):
+        import torch
+
+        self.torch = torch
+        self.shape = tuple(int(s) for s in shape)
+        self.n = int(np.prod(self.shape))
+        self.params = params if params is not None else default_params()
+        self.grid = make_grid(self.shape)
+        size = workspace_size(self.shape, self.params)
+        self.device = torch.device(device)
+        self.ws = torch.empty(max(size, 256), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        handle = c_void_p()
+        _check(lib().pfc_create(ctypes.byref(self.grid), float(h), float(gamma), ctypes.byref(self.params),
+                                c_void_p(self.ws.data_ptr()), c_size_t(self.ws.numel()),
+                                c_void_p(self.stream.cuda_stream), ctypes.byref(handle)), "pfc_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().pfc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- fields
+    def _dev(self, x):
+        t = self.torch
+        if isinstance(x, np.ndarray):
+            x = t.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(self.device)
+        assert x.dtype == t.float64 and x.is_cuda and x.is_contiguous() and x.numel() == self.n
+        return x
+
+    def set_field(self, phi):
+        if isinstance(phi, np.ndarray):
+            a = np.ascontiguousarray(phi, dtype=np.float64)
+            assert a.size == self.n
+            _check(lib().pfc_set_field(self.handle, a.ctypes.data_as(c_void_p), 0), "pfc_set_field")
+        else:
+            d = self._dev(phi)
+            _check(lib().pfc_set_field(self.handle, c_void_p(d.data_ptr()), 1), "pfc_set_field")
+
+    def get_field(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(lib().pfc_get_field(self.handle, out.ctypes.data_as(c_void_p), 0), "pfc_get_field")
+        return out
+
+    def get_field_device(self, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty(self.shape, dtype=t.float64, device=self.device)
+        _check(lib().pfc_get_field(self.handle, c_void_p(out.data_ptr()), 1), "pfc_get_field")
+        return out
+
+    def set_guess(self, guess):
+        if isinstance(guess, np.ndarray):
+            a = np.ascontiguousarray(guess, dtype=np.float64)
+            _check(lib().pfc_set_guess(self.handle, a.ctypes.data_as(c_void_p), 0), "pfc_set_guess")
+        else:
+            d = self._dev(guess)
+            _check(lib().pfc_set_guess(self.handle, c_void_p(d.data_ptr()), 1), "pfc_set_guess")
+
+    # -- stepping
+    def step(self, dt: float) -> dict:
+        info = pfc_step_info()
+        _check(lib().pfc_step(self.handle, float(dt), ctypes.byref(info)), "pfc_step")
+        return info.as_dict()
+
+    def run(self, nsteps: int) -> List[dict]:
+        infos = (pfc_step_info * max(nsteps, 1))()
+        st = lib().pfc_run(self.handle, int(nsteps), infos)
+        out = [infos[i].as_dict() for i in range(nsteps)]
+        _check(st, "pfc_run")
+        return out
+
+    def energy(self) -> float:
+        v = c_double()
+        _check(lib().pfc_energy(self.handle, ctypes.byref(v)), "pfc_energy")
+        return v.value
+
+    def mass(self) -> float:
+        v = c_double()
+        _check(lib().pfc_mass(self.handle, ctypes.byref(v)), "pfc_mass")
+        return v.value
+
+    def next_dt(self) -> float:
+        v = c_double()
+        _check(lib().pfc_next_dt(self.handle, ctypes.byref(v)), "pfc_next_dt")
+        return v.value
+
+    def step_host(self, phin_host: np.ndarray, dt: float, out_host: np.ndarray) -> dict:
+        """One step through host buffers (float64, C-contiguous; pinned memory recommended)."""
+        assert phin_host.dtype == np.float64 and out_host.dtype == np.float64
+        assert phin_host.flags.c_contiguous and out_host.flags.c_contiguous
+        info = pfc_step_info()
+        _check(lib().pfc_step_host(self.handle, phin_host.ctypes.data_as(c_void_p), float(dt),
+                                   out_host.ctypes.data_as(c_void_p), ctypes.byref(info)), "pfc_step_host")
+        return info.as_dict()
+
+    def profile(self, enable: bool):
+        _check(lib().pfc_profile(self.handle, 1 if enable else 0), "pfc_profile")
+
+    def profile_read(self) -> dict:
+        a, k = c_longlong(), c_longlong()
+        ms, b = c_double(), c_double()
+        _check(lib().pfc_profile_read(self.handle, ctypes.byref(a), ctypes.byref(ms), ctypes.byref(b),
+                                      ctypes.byref(k)), "pfc_profile_read")
+        return {"apply_launches": a.value, "apply_ms": ms.value, "apply_bytes": b.value, "kernel_launches": k.value}
+
+    # -- test hooks on device tensors
+    def residual(self, Phi, phin, dt: float):
+        t = self.torch
+        P, N = self._dev(Phi), self._dev(phin)
+        F = t.empty(self.shape, dtype=t.float64, device=self.device)
+        nrm = c_double()
+        _check(lib().pfc_residual(self.handle, c_void_p(P.data_ptr()), c_void_p(N.data_ptr()), float(dt),
+                                  c_void_p(F.data_ptr()), ctypes.byref(nrm)), "pfc_residual")
+        return F, nrm.value
+
+    def jvp(self, Phi, phin, v, dt: float):
+        t = self.torch
+        P, N, V = self._dev(Phi), self._dev(phin), self._dev(v)
+        out = t.empty(self.shape, dtype=t.float64, device=self.device)
+        _check(lib().pfc_jvp(self.handle, c_void_p(P.data_ptr()), c_void_p(N.data_ptr()), c_void_p(V.data_ptr()),
+                             float(dt), c_void_p(out.data_ptr())), "pfc_jvp")
+        return out
+
+    def precond_apply(self, Phi, phin, dt: float, r):
+        t = self.torch
+        P, N, R = self._dev(Phi), self._dev(phin), self._dev(r)
+        out = t.zeros(self.shape, dtype=t.float64, device=self.device)
+        _check(lib().pfc_precond_apply(self.handle, c_void_p(P.data_ptr()), c_void_p(N.data_ptr()), float(dt),
+                                       c_void_p(R.data_ptr()), c_void_p(out.data_ptr())), "pfc_precond_apply")
+        return out

@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.  Tolerances: FP64 kernels to rounding (1e-12 relative
+for single operators); full steps to max|phi_gpu - phi_oracle| <= 1e-8 and
+relative energy error <= 1e-10 (plain FP64 path)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pfc_oracle as O
+from paper_1703_01202_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+H = math.pi / 4
+GAMMA = 0.25
+
+
+@pytest.fixture(scope="module")
+def pfc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_01202_gb300 import build, pfc as P
+
+    build.build()
+    P.lib()
+    return P
+
+
+def solver(P, shape, parts, prec=0, **kw):
+    params = P.default_params(sub=tuple(parts[::-1]), factor_prec=prec, **kw)
+    return P.Solver(shape, H, GAMMA, params)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (40, 70), (9, 13), (48, 200)])
+def test_residual_matches_oracle(pfc, shape):
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 1)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 2)
+    s = solver(pfc, shape, (1, 1), overlap=0)
+    F, nrm = s.residual(Phi, phin, 0.7)
+    ref = O.residual(Phi, phin, 0.7, H, GAMMA)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(F.cpu().numpy(), ref, rtol=0, atol=1e-12 * scale)
+    assert nrm == pytest.approx(np.linalg.norm(ref), rel=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (40, 70), (33, 31)])
+def test_jvp_matches_oracle(pfc, shape):
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 3)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 4)
+    v = inputs.noise_field(shape, 0.0, 1.0, 5)
+    s = solver(pfc, shape, (1, 1), overlap=0)
+    Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 2.5, H, GAMMA)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (37, 50)])
+def test_energy_mass_match_oracle(pfc, shape):
+    phi = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=6, seed=7) if shape == (64, 64) else \
+        inputs.noise_field(shape, 0.1, 0.3, 6)
+    s = solver(pfc, shape, (1, 1), overlap=0)
+    s.set_field(phi)
+    assert s.energy() == pytest.approx(O.energy(phi, H, GAMMA), rel=1e-12)
+    assert s.mass() == pytest.approx(O.mass(phi, H), rel=1e-12, abs=1e-12)
+
+
+# F64 factors: the same LU as the oracle's up to rounding.  F32 / BF16 storage
+# (unit roundoff 2^-24 / 2^-9 per factor entry) perturbs the banded solves by
+# that roundoff times the growth of the triangular factors; at dt = 10 the
+# blocks are near-indefinite and BF16 storage reaches ~0.1 relative.  An
+# error of order one would mean a wrong factor, not storage rounding.
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4), (2, 0.25)])
+@pytest.mark.parametrize("shape,parts,dt", [((64, 64), (4, 4), 0.1), ((50, 37), (3, 2), 10.0), ((96, 80), (5, 6), 1.0)])
+def test_precond_apply_matches_oracle(pfc, shape, parts, dt, prec, tol):
+    """Left-RAS with the improved-BC block factors (Eqs. ras, Ak) against the
+    oracle's dense-LU Schwarz apply; F32/BF16 factor storage within their rounding."""
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, parts, prec=prec, overlap=1)
+    z = s.precond_apply(Phi, phin, dt, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, dt, H, GAMMA)
+    pre = O.Schwarz(J, O.decompose(shape, parts, 1), "left-ras", "lu")
+    ref = pre.apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+def test_twenty_steps_noise64_match_oracle(pfc):
+    """64^2 liquid from noise, fixed dt = 0.1, 20 steps, left-RAS 4x4 cores of 16^2 with
+    one overlap cell per side (18^2 blocks): phi and energy per step against the oracle."""
+    w = inputs.workload("noise64")
+    s = solver(pfc, w["shape"], w["parts"], overlap=1)
+    s.set_field(w["phi"])
+    infos = [s.step(w["fixed_dt"]) for _ in range(w["steps"])]
+    got = s.get_field()
+    ref, recs = O.run(w["phi"], w["h"], w["gamma"], O.Params(parts=w["parts"], overlap=1), w["steps"],
+                      fixed_dt=w["fixed_dt"])
+    assert np.abs(got - ref).max() <= 1e-8
+    for inf, rec in zip(infos, recs):
+        assert abs(inf["energy"] - rec.energy) <= 1e-10 * abs(rec.energy)
+        assert abs(inf["mass"] - rec.mass) <= 1e-12 * max(1.0, abs(rec.mass))
+    E = [i["energy"] for i in infos]
+    assert all(b <= a for a, b in zip(E, E[1:]))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_factors_match_oracle(pfc, prec):
+    """F32 / BF16 factor storage changes only the preconditioner: the Newton
+    solution stays within 1e-7 (phi) and 1e-9 (relative energy) of the FP64 oracle."""
+    w = inputs.workload("noise64")
+    s = solver(pfc, w["shape"], w["parts"], prec=prec, overlap=1)
+    s.set_field(w["phi"])
+    infos = [s.step(w["fixed_dt"]) for _ in range(5)]
+    ref, recs = O.run(w["phi"], w["h"], w["gamma"], O.Params(parts=w["parts"], overlap=1), 5, fixed_dt=w["fixed_dt"])
+    assert np.abs(s.get_field() - ref).max() <= 1e-7
+    assert abs(infos[-1]["energy"] - recs[-1].energy) <= 1e-9 * abs(recs[-1].energy)
+
+
+def test_adaptive_run_matches_oracle(pfc):
+    """pfc_run with the adaptive step (Eq. sencondt) on a small crystal-growth
+    case (ragged 3x2 decomposition) against the oracle's time loop."""
+    shape = (48, 60)
+    phi0 = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=8, seed=11)
+    prm = dict(dt_min=0.01, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, shape, (3, 2), overlap=1, **prm)
+    s.set_field(phi0)
+    infos = s.run(12)
+    ref, recs = O.run(phi0, H, GAMMA, O.Params(parts=(3, 2), overlap=1, **prm), 12)
+    for inf, rec in zip(infos, recs):
+        assert inf["dt"] == pytest.approx(rec.dt, rel=1e-8)
+        assert abs(inf["energy"] - rec.energy) <= 1e-10 * abs(rec.energy)
+    assert np.abs(s.get_field() - ref).max() <= 1e-8
+
+
+def test_constant_field_takes_no_newton_iteration(pfc):
+    shape = (32, 32)
+    s = solver(pfc, shape, (2, 2), overlap=1)
+    s.set_field(np.full(shape, 0.3))
+    info = s.step(1.0)
+    assert info["newton_its"] == 0 and np.array_equal(s.get_field(), np.full(shape, 0.3))
+
+
+def test_invalid_arguments_and_small_workspace(pfc):
+    import ctypes
+
+    s = solver(pfc, (32, 32), (2, 2), overlap=1)
+    with pytest.raises(pfc.PfcError) as e:
+        s.step(-1.0)
+    assert e.value.status == pfc.PFC_EINVAL
+    g = pfc.make_grid((32, 32))
+    p = pfc.default_params(sub=(2, 2))
+    h = ctypes.c_void_p()
+    st = pfc.lib().pfc_create(ctypes.byref(g), H, GAMMA, ctypes.byref(p), ctypes.c_void_p(s.ws.data_ptr()),
+                              ctypes.c_size_t(1024), None, ctypes.byref(h))
+    assert st == pfc.PFC_ENOMEM
