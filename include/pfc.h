@@ -171,6 +171,23 @@ int pfc_profile(pfc_state* s, int enable);
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches);
 
+/* The 2D residual F(Phi) of pfc_residual, for callers that cannot allocate
+   device memory at all: it needs no pfc_state and no workspace.  (The paper
+   has no counterpart; this is a deployment convenience.)  The caller still
+   passes the inputs Phi, phin and the output F_out (device arrays of
+   Nx*Ny doubles) and the stream; *norm (may be NULL) receives ||F||_2.
+   Its scratch -- one partial sum per 32x16 tile plus the total -- is a
+   fixed array inside the library (65,536 tiles, 512 KiB, held on every GPU
+   that loads the library until the process exits), so grids with more than
+   65,536 tiles (more than 33,554,432 cells) are rejected with PFC_EINVAL.
+   The first call on a device looks up the array's device address (with that
+   device current); make that first call before any stream capture.  All
+   calls share the one array: calls that overlap on the GPU (other streams,
+   other threads) race and must be serialised by the caller.  The call
+   synchronises its stream to return the norm. */
+int pfc_residual_static(const pfc_grid* g, double h, double eps, const double* Phi, const double* phin,
+                        double dt, double* F_out, double* norm, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pfc_status_str(int status);
 

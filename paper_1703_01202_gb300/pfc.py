@@ -76,6 +76,8 @@ _SIGNATURES = [
     ("pfc_profile", c_int, [c_void_p, c_int]),
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
                                  POINTER(c_longlong)]),
+    ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
+                                    POINTER(c_double), c_void_p]),
     ("pfc_status_str", c_char_p, [c_int]),
 ]
 
