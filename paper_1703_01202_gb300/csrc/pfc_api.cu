@@ -254,7 +254,8 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
 
 int factor_blocks(pfc_state* s, const double* q, double idt) {
   // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx): blocks at most 42 cells wide in x
-  if (2 * s->fs.kl_max + 2 > 256) return PFC_EINVAL;
+  if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
+    return PFC_EINVAL;
   CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
   pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
   CU(cudaGetLastError());

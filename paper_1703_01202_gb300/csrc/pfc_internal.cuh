@@ -87,7 +87,7 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
-size_t factor_smem_bytes(int prec, int kl);
+size_t factor_smem_bytes(int prec, int kl, int n_max);
 
 // ---- Krylov vector kernels (krylov.cu)
 void launch_multidot(const VecList& V, int nv, const double* w, long long n, double* partial, const int* skip,

@@ -113,16 +113,19 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
   const int lrow = fs.lrow, ucol = fs.ucol;
   double* qb = reinterpret_cast<double*>(smem);  // q on the block, block-local order
   double* lin_s = qb + fs.n_max;                 // 7 x 7 stencil table
+  constexpr int PM = RING / 2 - 1;               // window positions (<= RING/2 of them) map by pos & PM
   TC* A = reinterpret_cast<TC*>(lin_s + 49);     // W rows x RING column slots
   TC* lv = A + (size_t)W * RING;                 // multipliers of the current step
   TC* uv = lv + RING;                            // U row of the current step
-  int* slot = reinterpret_cast<int*>(uv + RING);  // window position (mod W) -> row slot
+  int* slot = reinterpret_cast<int*>(uv + RING);  // window position & PM -> row slot
+  int* roff = slot + RING / 2;                    // row offsets (slot * RING) of positions k+1..k+kl
   TS* L = (TS*)fs.L + blockIdx.x * fs.strideL;
   TS* U = (TS*)fs.U + blockIdx.x * fs.strideU;
   uint8_t* piv = fs.piv + blockIdx.x * fs.strideP;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int bx = B.bx;
+  const int bx = B.bx, by = B.by;
   const double ih2 = g.ih2;
+  const float inv_bx = 1.0f / (float)bx;
 
   for (int t = tid; t < n; t += nt)
     qb[t] = q[wrap(B.x0 + t % bx, g.nx) + (long long)g.nx * wrap(B.y0 + t / bx, g.ny)];
@@ -136,13 +139,13 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
   __syncthreads();
 
   for (int k = 0; k < n; ++k) {
-    const int kw = k % RING;
+    const int kw = k & (RING - 1);
     const int last = min(k + kl, n - 1);
     if (tid < 32) {  // partial pivoting: largest |a_ik| over the window, first on ties
       TC best = (TC)-1;
       int bp = k;
       for (int pos = k + tid; pos <= last; pos += 32) {
-        const TC v = abs(A[slot[pos % W] * RING + kw]);
+        const TC v = abs(A[slot[pos & PM] * RING + kw]);
         if (v > best) {
           best = v;
           bp = pos;
@@ -157,9 +160,9 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
         }
       }
       if (tid == 0) {
-        const int sk = slot[k % W], sp = slot[bp % W];
-        slot[k % W] = sp;
-        slot[bp % W] = sk;
+        const int sk = slot[k & PM], sp = slot[bp & PM];
+        slot[k & PM] = sp;
+        slot[bp & PM] = sk;
         piv[k] = (uint8_t)(bp - k);
         TC d = A[sp * RING + kw];
         if (d == (TC)0) {
@@ -170,20 +173,24 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
       }
     }
     __syncthreads();
-    const int sk = slot[k % W];
+    const int sk = slot[k & PM];
     const TC dinv = s_dinv;
     for (int i = tid; i < lrow; i += nt) {
       const int pos = k + 1 + i;
       TC l = (TC)0;
-      if (i < kl && pos < n) l = A[slot[pos % W] * RING + kw] * dinv;
+      if (i < kl) {
+        const int off = slot[pos & PM] * RING;
+        roff[i] = off;
+        if (pos < n) l = A[off + kw] * dinv;
+        lv[i] = l;
+      }
       L[(size_t)k * lrow + i] = to_store<TS>((double)l);
-      if (i < kl) lv[i] = l;
     }
     for (int j = tid; j < ucol; j += nt) {
       const int col = k + j;
       TC u = (TC)0;
       if (j <= ku2 && col < n) {
-        u = A[sk * RING + col % RING];
+        u = A[sk * RING + (col & (RING - 1))];
         U[(size_t)col * ucol + j] = to_store<TS>((double)(j == 0 ? dinv : u));
       }
       if (j <= ku2) uv[j] = u;
@@ -192,28 +199,47 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
     for (int j = ku2 + 1 + tid; j < ucol; j += nt) U[(size_t)k * ucol + j] = to_store<TS>(0.0);
     __syncthreads();
     // rank-1 update of the active window
+    const int rows = min(kl, n - 1 - k);
     for (int j = 1 + tid; j <= ku2; j += nt) {
       const TC u = uv[j];
       if (u != (TC)0 && k + j < n) {
-        const int cw = (k + j) % RING;
-        const int rows = min(kl, n - 1 - k);
+        const int cw = (k + j) & (RING - 1);
         for (int i = 0; i < rows; ++i) {
-          TC* a = &A[slot[(k + 1 + i) % W] * RING + cw];
+          TC* a = &A[roff[i] + cw];
           *a = *a - lv[i] * u;
         }
       }
     }
     // the column entering the band must start at zero in the rows that stay
-    const int cz = (k + 1 + ku2) % RING;
-    for (int i = tid; i < kl; i += nt) A[slot[(k + 1 + i) % W] * RING + cz] = (TC)0;
+    const int cz = (k + 1 + ku2) & (RING - 1);
+    for (int i = tid; i < kl; i += nt) A[roff[i] + cz] = (TC)0;
     // next row of A_k enters the slot the pivot row leaves
     const int rnew = k + 1 + kl;
     if (rnew < n) {
+      if (tid == 0) slot[rnew & PM] = sk;
       TC* row = &A[sk * RING];
       const int base = k + 1;
+      const int ar = rnew % bx, br = rnew / bx;
       for (int t = tid; t < RING; t += nt) {
-        const int col = base + (((t - base) % RING) + RING) % RING;
-        row[t] = col < n ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, rnew, col) : (TC)0;
+        const int col = base + ((t - base) & (RING - 1));
+        TC v = (TC)0;
+        if (col < n) {
+          if (bx >= 7) {  // col - rnew = dx + bx dy has a unique split with |dx| <= 3
+            const int d = col - rnew;
+            const int dy = __float2int_rn((float)d * inv_bx);
+            const int dx = d - dy * bx;
+            const int ad = abs(dx) + abs(dy);
+            if (ad <= 3 && ar + dx >= 0 && ar + dx < bx && br + dy >= 0 && br + dy < by) {
+              double e = lin_s[(dy + 3) * 7 + (dx + 3)];
+              if (ad <= 1) e -= (ad == 0 ? -4.0 * ih2 : ih2) * qb[col];
+              if (ad == 0) e += idt;
+              v = (TC)e;
+            }
+          } else {
+            v = (TC)jac_entry(bx, ih2, qb, idt, lin_s, rnew, col);
+          }
+        }
+        row[t] = v;
       }
     }
     __syncthreads();
@@ -287,12 +313,25 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
     pv[t] = piv[t];
   }
   __syncwarp();
+  // The active window of each triangular solve lives in registers: lane l holds
+  // the entries congruent to l mod 32, one register per 32-entry block.  Forward
+  // window [k, k+kl] (kl <= 63): blocks mf..mf+2 in w0..w2, mf = k / 32.
+  // Backward window [k-ku2, k] (ku2 <= 127): blocks mb..mb-4 in v0..v4, mb = k / 32.
+  // The registers rotate when k crosses a block boundary; the pivot and x_k
+  // values reach every lane by warp shuffles, so no step needs a shared-memory
+  // round trip or a warp barrier.
+  const unsigned FULL = 0xffffffffu;
+  int mf = 0, mb = 0;
+  TC w0 = lane < n ? buf[lane] : (TC)0;
+  TC w1 = lane + 32 < n ? buf[lane + 32] : (TC)0;
+  TC w2 = lane + 64 < n ? buf[lane + 64] : (TC)0;
+  TC v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0;
   uint32_t phase0 = 0, phase1 = 0;
   for (int t = 0; t < total; ++t) {
     const int st = t & 1;
     const bool ok = mbar_wait_bounded(&bar[st], st ? phase1 : phase0);
     if (st) phase1 ^= 1; else phase0 ^= 1;
-    if (!__all_sync(0xffffffffu, ok)) {  // give up: record, drain the other copy in flight, leave
+    if (!__all_sync(FULL, ok)) {  // give up: record, drain the copies in flight, leave
       if (lane == 0) {
         atomicExch(err, PFC_ETIMEOUT);
         mbar_wait_bounded(&bar[st], st ? phase1 ^ 1 : phase0 ^ 1);
@@ -305,34 +344,74 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
       const int c = t, rows = min(CH, n - c * CH);
       for (int kk = 0; kk < rows; ++kk) {
         const int k = c * CH + kk;
+        if ((k >> 5) != mf) {  // entered block mf + 1
+          ++mf;
+          w0 = w1;
+          w1 = w2;
+          const int tn = 32 * (mf + 2) + lane;
+          w2 = tn < n ? buf[tn] : (TC)0;
+        }
         const TS* lk = data + kk * lrow;
         const int p = k + pv[k];
-        const TC bk = buf[k], bp = buf[p];
-        __syncwarp();
-        const int cnt = min(kl, n - 1 - k);
-        for (int i = lane; i < cnt; i += 32) {
-          const int tt = k + 1 + i;
-          const TC val = (tt == p) ? bk : buf[tt];
-          buf[tt] = val - from_store<TC, TS>(lk[i]) * bp;
-        }
-        if (lane == 0) buf[k] = bp;
-        __syncwarp();
+        const int dp = (p >> 5) - mf;
+        const TC bk = __shfl_sync(FULL, w0, k & 31);
+        const TC bp = __shfl_sync(FULL, dp == 0 ? w0 : (dp == 1 ? w1 : w2), p & 31);
+        if (lane == (k & 31)) buf[k] = bp;  // y_k
+        const int last = min(k + kl, n - 1);
+        int tt = 32 * mf + lane;
+        if (tt > k && tt <= last) w0 = ((tt == p) ? bk : w0) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
+        tt += 32;
+        if (tt > k && tt <= last) w1 = ((tt == p) ? bk : w1) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
+        tt += 32;
+        if (tt <= last) w2 = ((tt == p) ? bk : w2) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
       }
-    } else {  // backward, column oriented: x_k = b_k / u_kk, b_{k-j} -= u_{k-j,k} x_k
+    } else {  // backward, column oriented: x_k = y_k / u_kk, y_{k-j} -= u_{k-j,k} x_k
+      if (t == nc) {  // y complete: load the top of the backward window
+        __syncwarp();
+        mb = (n - 1) >> 5;
+        int tb = 32 * mb + lane;
+        v0 = (tb < n) ? buf[tb] : (TC)0;
+        tb -= 32;
+        v1 = (tb >= 0) ? buf[tb] : (TC)0;
+        tb -= 32;
+        v2 = (tb >= 0) ? buf[tb] : (TC)0;
+        tb -= 32;
+        v3 = (tb >= 0) ? buf[tb] : (TC)0;
+        tb -= 32;
+        v4 = (tb >= 0) ? buf[tb] : (TC)0;
+      }
       const int c = 2 * nc - 1 - t, rows = min(CH, n - c * CH);
       for (int kk = rows - 1; kk >= 0; --kk) {
         const int k = c * CH + kk;
+        if ((k >> 5) != mb) {  // entered block mb - 1
+          --mb;
+          v0 = v1;
+          v1 = v2;
+          v2 = v3;
+          v3 = v4;
+          const int tn = 32 * (mb - 4) + lane;
+          v4 = tn >= 0 ? buf[tn] : (TC)0;
+        }
         const TS* uk = data + kk * ucol;
-        const TC xk = buf[k] * from_store<TC, TS>(uk[0]);
-        __syncwarp();
-        const int top = min(ku2, k);
-        for (int j = 1 + lane; j <= top; j += 32) buf[k - j] -= from_store<TC, TS>(uk[j]) * xk;
-        if (lane == 0) buf[k] = xk;
-        __syncwarp();
+        const TC xk = __shfl_sync(FULL, v0, k & 31) * from_store<TC, TS>(uk[0]);
+        if (lane == (k & 31)) buf[k] = xk;
+        const int lo = max(0, k - ku2);
+        int tt = 32 * mb + lane;
+        if (tt < k && tt >= lo) v0 -= from_store<TC, TS>(uk[k - tt]) * xk;
+        tt -= 32;
+        if (tt >= lo) v1 -= from_store<TC, TS>(uk[k - tt]) * xk;
+        tt -= 32;
+        if (tt >= lo) v2 -= from_store<TC, TS>(uk[k - tt]) * xk;
+        tt -= 32;
+        if (tt >= lo) v3 -= from_store<TC, TS>(uk[k - tt]) * xk;
+        tt -= 32;
+        if (tt >= lo) v4 -= from_store<TC, TS>(uk[k - tt]) * xk;
       }
     }
-    if (lane == 0 && t + 2 < total) issue(t + 2);  // refill the stage just consumed
+    __syncwarp();  // every lane is done with this stage before it is refilled
+    if (lane == 0 && t + 2 < total) issue(t + 2);
   }
+  __syncwarp();
   const double sc = rscale ? *rscale : 1.0;
   for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
     const int a = t % bx, c = t / bx;
@@ -344,13 +423,11 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
-  const int W = fs.kl_max + 1;
+  const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max);
   if (2 * fs.kl_max + 2 <= 128) {
-    const size_t smem = (size_t)(fs.n_max + 49) * 8 + (size_t)(W * 128 + 2 * 128) * sizeof(TC) + W * sizeof(int) + 16;
     cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor2d<TC, TS, 128><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
   } else {
-    const size_t smem = (size_t)(fs.n_max + 49) * 8 + (size_t)(W * 256 + 2 * 256) * sizeof(TC) + W * sizeof(int) + 16;
     cudaFuncSetAttribute(k_factor2d<TC, TS, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor2d<TC, TS, 256><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
   }
@@ -371,10 +448,13 @@ void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Fa
 
 }  // namespace
 
-size_t factor_smem_bytes(int prec, int kl) {
+// Dynamic shared memory of the factor kernel: q on the block and the stencil
+// table (FP64), the (kl+1) x RING window plus the multiplier and U-row
+// buffers (compute type), the position map and the row offsets.
+size_t factor_smem_bytes(int prec, int kl, int n_max) {
   const int ring = (2 * kl + 2 <= 128) ? 128 : 256;
   const size_t tc = prec == PFC_F64 ? 8 : 4;
-  return (size_t)((kl + 1) * ring + 2 * ring) * tc + (kl + 1) * sizeof(int) + 16;
+  return (size_t)(n_max + 49) * 8 + (size_t)((kl + 1) * ring + 2 * ring) * tc + ring * sizeof(int) + 16;
 }
 
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
