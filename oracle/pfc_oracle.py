@@ -320,9 +320,14 @@ class Schwarz:
     kind 'as'        : sum_k (R_k^delta)^T inv(A_k) R_k^delta   (Eq. invM)
     kind 'left-ras'  : sum_k (R_k^0)^T     inv(A_k) R_k^delta   (Eq. ras)
     kind 'right-ras' : sum_k (R_k^delta)^T inv(A_k) R_k^0       (Eq. ash)
-    Subdomain solver: dense LU with partial pivoting ('lu') or ILU(0) ('ilu0')."""
+    Subdomain solver: dense LU with partial pivoting ('lu') or ILU(0) ('ilu0').
+    READING (3D): ILU(0) of the 63-point block matrices breaks down (negative
+    pivots) at the 3D workload's time steps, so 'ilu0' factors A_k + sigma I with
+    sigma = ilu_shift * mean |diag A_k| (a shifted incomplete factorisation);
+    ilu_shift = 0 is plain ILU(0)."""
 
-    def __init__(self, J: sp.csr_matrix, blocks: Sequence[Block], kind: str = "left-ras", solver: str = "lu"):
+    def __init__(self, J: sp.csr_matrix, blocks: Sequence[Block], kind: str = "left-ras", solver: str = "lu",
+                 ilu_shift: float = 0.0):
         if kind not in ("as", "left-ras", "right-ras"):
             raise ValueError(kind)
         self.blocks = list(blocks)
@@ -337,6 +342,7 @@ class Schwarz:
                 pattern = block_pattern(blk)
                 if np.any(A[~pattern] != 0.0):
                     raise ValueError("block couples to itself across the periodic wrap; grid too small")
+                A = A + ilu_shift * np.mean(np.abs(np.diag(A))) * np.eye(A.shape[0])
                 rows, cols = np.nonzero(pattern)
                 self.factors.append(ilu0(sp.csr_matrix((A[rows, cols], (rows, cols)), shape=A.shape)))
             else:
@@ -464,6 +470,7 @@ class Params:
     overlap: int = 1  # cells added per side (READING of '3 delta layers')
     ras_kind: str = "left-ras"
     subdomain_solver: str = "lu"  # 'lu' (2D) or 'ilu0' (3D)
+    ilu_shift: float = 0.1  # READING: relative diagonal shift of the 3D ILU(0) blocks
     precond: bool = True  # False: H = I
     mass_projection: bool = True  # READING: zero-mean Newton update
     ls_alpha: float = 1e-4  # Armijo constant of the backtracking line search
@@ -510,7 +517,8 @@ def newton_solve(
     while rnorm > target and m < p.newton_max_it:
         J = assemble_jacobian(Phi, phin, dt, h, gamma)
         if p.precond and pre is None:
-            pre = Schwarz(J, decompose(Phi.shape, p.parts, p.overlap), p.ras_kind, p.subdomain_solver)
+            pre = Schwarz(J, decompose(Phi.shape, p.parts, p.overlap), p.ras_kind, p.subdomain_solver,
+                          p.ilu_shift)
         precond = (lambda v: pre.apply(v)) if p.precond else (lambda v: v)
         matvec = lambda v: (J @ v.ravel()).reshape(v.shape)
         res = gmres_right(

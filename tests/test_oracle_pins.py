@@ -193,6 +193,28 @@ def test_ilu0_on_banded_pattern_is_exact_lu():
     np.testing.assert_allclose(prod[mask], A2.toarray()[mask], atol=1e-13)
 
 
+def test_shifted_ilu0_is_ilu0_of_the_shifted_block():
+    """The 3D reading: 'ilu0' with ilu_shift s factors A_k + s mean|diag A_k| I.  The
+    shift changes the apply, and the apply equals unshifted ILU(0) of the block
+    matrix with the shift added to its diagonal by hand."""
+    shape = (10, 10, 10)
+    Phi, phin = rand_field(shape, 30), rand_field(shape, 31)
+    J = O.assemble_jacobian(Phi, phin, 0.5, 80 * math.pi / 256, 0.3)
+    blocks = O.decompose(shape, (2, 2, 2), 1)
+    r = rand_field(shape, 32, 0.0, 1.0)
+    z0 = O.Schwarz(J, blocks, "left-ras", "ilu0", 0.0).apply(r)
+    z1 = O.Schwarz(J, blocks, "left-ras", "ilu0", 0.2).apply(r)
+    assert np.linalg.norm(z1 - z0) > 1e-3 * np.linalg.norm(z0)  # the shift changes the factors
+    # same block, shift folded into the matrix by hand, unshifted ILU(0): identical apply
+    blk = blocks[0]
+    A = O.subdomain_matrix(J, blk)
+    As = A + 0.2 * np.mean(np.abs(np.diag(A))) * np.eye(A.shape[0])
+    rows, cols = np.nonzero(O.block_pattern(blk))
+    LU = O.ilu0(sp.csr_matrix((As[rows, cols], (rows, cols)), shape=As.shape))
+    sol = O.ilu0_solve(LU, r.ravel()[blk.block_idx])
+    np.testing.assert_allclose(z1.ravel()[blk.core_idx], sol[blk.core_mask], rtol=1e-13, atol=1e-15)
+
+
 def test_gmres_unpreconditioned_matches_dense_solve():
     """GMRES with H = I to 1e-14 against a dense solve (restart exercised)."""
     shape = (8, 8)
