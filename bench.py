@@ -230,6 +230,35 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
     return out
 
 
+def kernel_loop(args):
+    """Runs one kernel family `steps` times on the workload's initial field
+    (each pfc_precond_apply factors and applies once), for ncu captures."""
+    import torch
+
+    from paper_1703_01202_gb300 import build, inputs, pfc
+
+    build.build()
+    w = inputs.workload(WORKLOAD)
+    prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2}[args.variant]
+    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec)
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
+    phi = torch.from_numpy(w["phi"]).cuda()
+    r = torch.from_numpy(inputs.noise_field(w["shape"], 0.0, 1.0, 7)).cuda()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        if args.kernel_loop == "apply":
+            s.precond_apply(phi, phi, 10.0, r)
+        elif args.kernel_loop == "jvp":
+            s.jvp(phi, phi, r, 10.0)
+        else:
+            s.residual(phi, phi, 10.0)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"kernel_loop": args.kernel_loop, "variant": args.variant, "calls": args.steps,
+                      "ms_per_call": [round(1e3 * t, 3) for t in times]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -239,7 +268,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16"],
                     help="run one factor-precision variant only (profiling runs)")
+    ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
+                    help="profiling aid: run one kernel family repeatedly on the workload (no bench line)")
     args = ap.parse_args()
+    if args.kernel_loop:
+        kernel_loop(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 

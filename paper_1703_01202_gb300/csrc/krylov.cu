@@ -1,9 +1,14 @@
 // FP64 vector kernels of right-preconditioned restarted GMRES (Sec. 4, Eq.
 // hjacobi): fused multi-dot products and multi-axpys for classical Gram-Schmidt
 // with one conditional re-orthogonalisation pass (Daniel-Gragg-Kaufman-Stewart
-// criterion), deterministic two-level reductions (per-CTA partial sums in a
-// fixed order, then one CTA per reduction), and the single-thread kernels that
-// keep the Arnoldi/Givens bookkeeping on the device.
+// criterion), and the Arnoldi/Givens bookkeeping, all on the device.
+//
+// Reductions are deterministic: every CTA writes its partial sums (fixed
+// order inside the CTA), and the last CTA to finish -- found with an atomic
+// ticket -- sums the partials in a fixed order and then runs the single-thread
+// bookkeeping step (Hessenberg column, Givens rotation, residual estimate,
+// convergence flag).  So one Gram-Schmidt pass costs one kernel per vector
+// sweep, with no separate reduction launch.
 //
 // The basis is kept unnormalised: V_i = scale_i * Vraw_i with scale_i held on
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
@@ -24,102 +29,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i]
-__global__ void __launch_bounds__(NT) k_multidot(VecList V, int nv, const double* __restrict__ w, long long n,
-                                                 double* __restrict__ partial, const int* __restrict__ skip,
-                                                 const int* __restrict__ only_if) {
-  if ((skip && *skip) || (only_if && !*only_if)) return;
-  __shared__ double red[NT / 32][G];
-  const int g0 = blockIdx.y * G;
-  const int cnt = min(G, nv - g0);
-  double acc[G];
-#pragma unroll
-  for (int k = 0; k < G; ++k) acc[k] = 0.0;
-  const long long stride = (long long)gridDim.x * NT;
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += stride) {
-    const double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < G; ++k)
-      if (k < cnt) acc[k] = fma(V.p[g0 + k][i], wi, acc[k]);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < G; ++k) {
-    const double s = warp_sum(acc[k]);
-    if (lane == 0) red[wid][k] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < cnt) {
-    double s = 0.0;
-    for (int q = 0; q < NT / 32; ++q) s += red[q][threadIdx.x];
-    partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
-  }
+// Vector i of a list: v0 for i = 0, tab[i] otherwise (tab is a device pointer table).
+__device__ __forceinline__ const double* vec_at(const double* v0, const double* const* tab, int i) {
+  return i == 0 ? v0 : tab[i];
 }
 
-// w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, partial[gridDim..] = sum w
-__global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, VecList X, int nx,
-                                                  const double* __restrict__ coef, double sign, long long n,
-                                                  double* __restrict__ partial, const int* __restrict__ skip,
-                                                  const int* __restrict__ only_if) {
-  if ((skip && *skip) || (only_if && !*only_if)) return;
-  __shared__ double red[2][NT / 32];
-  __shared__ double c[kMaxVecs];
-  for (int k = threadIdx.x; k < nx; k += NT) c[k] = sign * coef[k];
-  __syncthreads();
-  double s2 = 0.0, s1 = 0.0;
-  const long long stride = (long long)gridDim.x * NT;
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += stride) {
-    double acc = w[i];
-    for (int k = 0; k < nx; ++k) acc = fma(c[k], X.p[k][i], acc);
-    w[i] = acc;
-    s2 = fma(acc, acc, s2);
-    s1 += acc;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  s2 = warp_sum(s2);
-  s1 = warp_sum(s1);
-  if (lane == 0) {
-    red[0][wid] = s2;
-    red[1][wid] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int q = 0; q < NT / 32; ++q) s += red[threadIdx.x][q];
-    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
-  }
-}
+// ---- single-thread GMRES bookkeeping
 
-// out[v] = sum_p partial[v * nparts + p], fixed order.
-__global__ void __launch_bounds__(1024) k_reduce(const double* __restrict__ partial, int nvals, int nparts,
-                                                 double* __restrict__ out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int v = wid; v < nvals; v += 32) {
-    double s = 0.0;
-    for (int p = lane; p < nparts; p += 32) s += partial[(size_t)v * nparts + p];
-    s = warp_sum(s);
-    if (lane == 0) out[v] = s;
-  }
-}
-
-__global__ void k_gmres_init(GmresCtl* c, const double* __restrict__ nrm2, double sign, double tol) {
-  const double beta = sqrt(*nrm2);
-  c->done = 0;
-  c->its = 0;
-  c->reorth = 0;
-  c->breakdown = 0;
-  c->tol = tol;
-  c->beta = beta;
-  c->est = beta;
-  c->g[0] = beta;
-  c->scale[0] = beta > 0.0 ? sign / beta : 0.0;
-  if (!(beta > tol)) c->done = 1;
-}
-
-// After a multi-dot of V_0..V_j against w (red[0..j]) and w.w (red[j+1]).
-__global__ void k_gmres_after_dot(GmresCtl* c, int j, int pass) {
-  if (c->done) return;
-  if (pass == 1 && !c->reorth) return;
+// After a multi-dot of V_0..V_j against w (c->red[0..j]) and w.w (c->red[j+1]).
+__device__ void gmres_after_dot(GmresCtl* c, int j, int pass) {
   const int m1 = kMaxRestart + 1;
   for (int i = 0; i <= j; ++i) {
     const double h = c->scale[i] * c->red[i];
@@ -158,10 +76,8 @@ __device__ void gmres_finalize(GmresCtl* c, int j, int m, double wn2) {
   if (c->est <= c->tol || !(hn > 0.0) || j + 1 >= m || !(c->est == c->est)) c->done = 1;
 }
 
-// After the multi-axpy w -= sum coef_i Vraw_i; red[0] = w.w afterwards.
-__global__ void k_gmres_after_axpy(GmresCtl* c, const double* __restrict__ red2, int j, int pass, int m) {
-  if (c->done) return;
-  const double wn2 = red2[0];
+// After the multi-axpy w -= sum coef_i Vraw_i, with wn2 = w.w afterwards.
+__device__ void gmres_after_axpy(GmresCtl* c, int j, int pass, int m, double wn2) {
   if (pass == 0) {
     if (wn2 < 0.5 * c->wnorm2_before) {  // ||w'|| < ||w|| / sqrt(2): orthogonalise once more
       c->reorth = 1;
@@ -170,10 +86,179 @@ __global__ void k_gmres_after_axpy(GmresCtl* c, const double* __restrict__ red2,
     c->reorth = 0;
     gmres_finalize(c, j, m, wn2);
   } else {
-    if (!c->reorth) return;
     c->reorth = 0;
     gmres_finalize(c, j, m, wn2);
   }
+}
+
+// ---- fused last-CTA reduction
+
+// The last CTA of the grid (atomic ticket on t.counter) sums nvals partial rows
+// of nparts entries each, in a fixed order, then runs the tail step.
+__device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restrict__ partial, int nvals,
+                                          int nparts) {
+  __shared__ bool s_last;
+  __shared__ double s_sum[kMaxVecs + 2];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y;
+    s_last = atomicAdd(t.counter, 1u) == total - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < nvals; v += NT / 32) {
+    double s = 0.0;
+    for (int p = lane; p < nparts; p += 32) s += __ldcg(partial + (size_t)v * nparts + p);
+    s = warp_sum(s);
+    if (lane == 0) s_sum[v] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    GmresCtl* c = t.ctl;
+    if (t.kind == Tail::kDot) {
+      for (int v = 0; v < nvals; ++v) c->red[v] = s_sum[v];
+      gmres_after_dot(c, t.j, t.pass);
+    } else if (t.kind == Tail::kAxpy) {
+      gmres_after_axpy(c, t.j, t.pass, t.m, s_sum[0]);
+    } else {
+      for (int v = 0; v < nvals; ++v) t.out[v] = s_sum[v];
+    }
+    *t.counter = 0u;  // ready for the next kernel on this stream
+  }
+}
+
+// partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i]; pairs of points per
+// 16-byte load (every vector starts 256-byte aligned).
+__global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double* const* __restrict__ tab, int nv,
+                                                 const double* __restrict__ w, long long n,
+                                                 double* __restrict__ partial, const int* __restrict__ skip,
+                                                 const int* __restrict__ only_if, Tail tail) {
+  if ((skip && *skip) || (only_if && !*only_if)) return;
+  __shared__ double red[NT / 32][G];
+  __shared__ const double* sp[G];
+  const int g0 = blockIdx.y * G;
+  const int cnt = min(G, nv - g0);
+  if (threadIdx.x < G) sp[threadIdx.x] = threadIdx.x < cnt ? vec_at(v0, tab, g0 + threadIdx.x) : w;
+  __syncthreads();
+  const double* p[G];
+#pragma unroll
+  for (int k = 0; k < G; ++k) p[k] = sp[k];
+  double acc[G];
+#pragma unroll
+  for (int k = 0; k < G; ++k) acc[k] = 0.0;
+  const long long n2 = n >> 1;
+  const long long stride = (long long)gridDim.x * NT;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
+    const double2 wi = w2[i];
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+      if (k < cnt) {
+        const double2 a = reinterpret_cast<const double2*>(p[k])[i];
+        acc[k] = fma(a.y, wi.y, fma(a.x, wi.x, acc[k]));
+      }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
+    const double wi = w[n - 1];
+#pragma unroll
+    for (int k = 0; k < G; ++k)
+      if (k < cnt) acc[k] = fma(p[k][n - 1], wi, acc[k]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    const double s = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double s = 0.0;
+    for (int q = 0; q < NT / 32; ++q) s += red[q][threadIdx.x];
+    partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+  }
+  if (tail.counter) last_cta_tail(tail, partial, nv, gridDim.x);
+}
+
+// w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, partial[gridDim..] = sum w
+__global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const double* x0,
+                                                  const double* const* __restrict__ tab, int nx,
+                                                  const double* __restrict__ coef, double sign, long long n,
+                                                  double* __restrict__ partial, const int* __restrict__ skip,
+                                                  const int* __restrict__ only_if, Tail tail) {
+  if ((skip && *skip) || (only_if && !*only_if)) return;
+  __shared__ double red[2][NT / 32];
+  __shared__ double c[kMaxVecs];
+  __shared__ const double* sp[kMaxVecs];
+  for (int k = threadIdx.x; k < nx; k += NT) {
+    c[k] = sign * coef[k];
+    sp[k] = vec_at(x0, tab, k);
+  }
+  __syncthreads();
+  double s2 = 0.0, s1 = 0.0;
+  const long long n2 = n >> 1;
+  const long long stride = (long long)gridDim.x * NT;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
+    double2 acc = w2[i];
+    for (int k = 0; k < nx; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
+      acc.x = fma(c[k], a.x, acc.x);
+      acc.y = fma(c[k], a.y, acc.y);
+    }
+    w2[i] = acc;
+    s2 = fma(acc.y, acc.y, fma(acc.x, acc.x, s2));
+    s1 += acc.x + acc.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
+    double acc = w[n - 1];
+    for (int k = 0; k < nx; ++k) acc = fma(c[k], sp[k][n - 1], acc);
+    w[n - 1] = acc;
+    s2 = fma(acc, acc, s2);
+    s1 += acc;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  s2 = warp_sum(s2);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    red[0][wid] = s2;
+    red[1][wid] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int q = 0; q < NT / 32; ++q) s += red[threadIdx.x][q];
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+  if (tail.counter) last_cta_tail(tail, partial, 2, gridDim.x);
+}
+
+// out[v] = sum_p partial[v * nparts + p], fixed order.
+__global__ void __launch_bounds__(1024) k_reduce(const double* __restrict__ partial, int nvals, int nparts,
+                                                 double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < nvals; v += 32) {
+    double s = 0.0;
+    for (int p = lane; p < nparts; p += 32) s += partial[(size_t)v * nparts + p];
+    s = warp_sum(s);
+    if (lane == 0) out[v] = s;
+  }
+}
+
+__global__ void k_gmres_init(GmresCtl* c, const double* __restrict__ nrm2, double sign, double tol) {
+  const double beta = sqrt(*nrm2);
+  c->done = 0;
+  c->its = 0;
+  c->reorth = 0;
+  c->breakdown = 0;
+  c->tol = tol;
+  c->beta = beta;
+  c->est = beta;
+  c->g[0] = beta;
+  c->scale[0] = beta > 0.0 ? sign / beta : 0.0;
+  if (!(beta > tol)) c->done = 1;
 }
 
 // y = R^{-1} g over the completed iterations (R = rotated Hessenberg).
@@ -205,21 +290,20 @@ int red_ctas(long long n) {
 
 }  // namespace
 
-void launch_multidot(const VecList& V, int nv, const double* w, long long n, double* partial, const int* skip,
-                     const int* only_if, cudaStream_t st, int* nparts) {
-  const int bx = red_ctas(n);
+void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
+                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st) {
+  const int bx = red_ctas((n + 1) / 2);
   dim3 grid(bx, (nv + G - 1) / G);
-  k_multidot<<<grid, NT, 0, st>>>(V, nv, w, n, partial, skip, only_if);
+  k_multidot<<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
   count_launches(1);
-  *nparts = bx;
 }
 
-void launch_multiaxpy(double* w, const VecList& X, int nx, const double* coef, double sign, long long n,
-                      double* partial, const int* skip, const int* only_if, cudaStream_t st, int* nparts) {
-  const int bx = red_ctas(n);
-  k_multiaxpy<<<bx, NT, 0, st>>>(w, X, nx, coef, sign, n, partial, skip, only_if);
+void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
+                      long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
+                      cudaStream_t st) {
+  const int bx = red_ctas((n + 1) / 2);
+  k_multiaxpy<<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
   count_launches(1);
-  *nparts = bx;
 }
 
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st) {
@@ -231,16 +315,10 @@ void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double to
   k_gmres_init<<<1, 1, 0, st>>>(ctl, nrm2, sign, tol);
   count_launches(1);
 }
-void launch_gmres_after_dot(GmresCtl* ctl, int j, int pass, cudaStream_t st) {
-  k_gmres_after_dot<<<1, 1, 0, st>>>(ctl, j, pass);
+void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st) {
+  k_gmres_solve<<<1, 1, 0, st>>>(ctl);
   count_launches(1);
 }
-void launch_gmres_after_axpy(GmresCtl* ctl, const double* red2, int j, int pass, int m, cudaStream_t st) {
-  k_gmres_after_axpy<<<1, 1, 0, st>>>(ctl, red2, j, pass, m);
-  count_launches(1);
-}
-void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st) { k_gmres_solve<<<1, 1, 0, st>>>(ctl);
-  count_launches(1); }
 
 void launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
   k_axpby<<<red_ctas(n), NT, 0, st>>>(y, x, a, b, n);

@@ -36,11 +36,16 @@ struct pfc_state {
   // fields (device, N doubles each)
   double *phin, *phinm1, *Phi, *F, *q, *Pt, *Ft, *qt, *S, *W, *guess;
   double *Vbuf, *Zbuf;  // (m+1) x N and m x N
+  const double** vtab;  // device pointer tables: vtab[i] = Vbuf + i N, ztab[i] = Zbuf + i N
+  const double** ztab;
   // preconditioner
   BlockDesc* blocks_dev;
   int nblocks;
   pfc::FactorStore fs;
   double* lin_dev;
+  // 3D: scratch fields of the three-pass stencils and the ILU(0) Schwarz data
+  double *T1, *T2;
+  pfc::Ras3D r3;
   // reductions and control
   GmresCtl* ctl;
   double* partial;
@@ -107,9 +112,10 @@ std::vector<Split> split_axis(int n, int p) {
 
 int validate(const pfc_grid* g, const pfc_params* p) {
   if (!g || !p) return PFC_EINVAL;
-  if (g->dim != 2) return PFC_EINVAL;  // 3D blocks are built by a later entry point
+  if (g->dim != 2 && g->dim != 3) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a)
     if (g->n[a] < 1 || g->n[a] > (1 << 20)) return PFC_EINVAL;
+  if (g->dim == 2 && g->n[2] != 1) return PFC_EINVAL;
   if (p->gmres_restart < 1 || p->gmres_restart > pfc::kMaxRestart) return PFC_EINVAL;
   if (p->newton_max_it < 0 || p->gmres_max_it < 1 || p->overlap < 0) return PFC_EINVAL;
   if (p->ras_kind != PFC_LEFT_RAS) return PFC_EINVAL;
@@ -117,7 +123,13 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
+    const int core_min = (int)(g->n[a] / p->sub[a]);
     if (core_max + 2 * p->overlap > g->n[a]) return PFC_EINVAL;
+    if (g->dim == 3) {
+      // 3D blocks: at least 7 cells per axis (offset order = row order), and the
+      // block plus its 3-cell ring must not wrap onto itself (A_k = R J R^T pattern)
+      if (core_min + 2 * p->overlap < 7 || core_max + 2 * p->overlap + 3 > g->n[a]) return PFC_EINVAL;
+    }
   }
   return PFC_OK;
 }
@@ -125,60 +137,174 @@ int validate(const pfc_grid* g, const pfc_params* p) {
 void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>* out, int* n_max, int* kl_max) {
   auto sx = split_axis((int)g->n[0], p->sub[0]);
   auto sy = split_axis((int)g->n[1], p->sub[1]);
+  const int nz_parts = g->dim == 3 ? p->sub[2] : 1;
+  auto sz = split_axis(g->dim == 3 ? (int)g->n[2] : 1, nz_parts);
   const int ov = p->overlap;
+  const int ovz = g->dim == 3 ? ov : 0;
   *n_max = 0;
   *kl_max = 0;
-  for (int by = 0; by < p->sub[1]; ++by)
-    for (int bx = 0; bx < p->sub[0]; ++bx) {
-      BlockDesc b{};
-      b.x0 = sx[bx].start - ov;
-      b.y0 = sy[by].start - ov;
-      b.z0 = 0;
-      b.bx = sx[bx].size + 2 * ov;
-      b.by = sy[by].size + 2 * ov;
-      b.bz = 1;
-      b.ox = ov;
-      b.oy = ov;
-      b.oz = 0;
-      b.cx = sx[bx].size;
-      b.cy = sy[by].size;
-      b.cz = 1;
-      out->push_back(b);
-      const int n = b.bx * b.by;
-      const int kl = std::min(3 * b.bx, n - 1);
-      *n_max = std::max(*n_max, n);
-      *kl_max = std::max(*kl_max, kl);
+  for (int bz = 0; bz < nz_parts; ++bz)
+    for (int by = 0; by < p->sub[1]; ++by)
+      for (int bx = 0; bx < p->sub[0]; ++bx) {
+        BlockDesc b{};
+        b.x0 = sx[bx].start - ov;
+        b.y0 = sy[by].start - ov;
+        b.z0 = sz[bz].start - ovz;
+        b.bx = sx[bx].size + 2 * ov;
+        b.by = sy[by].size + 2 * ov;
+        b.bz = sz[bz].size + 2 * ovz;
+        b.ox = ov;
+        b.oy = ov;
+        b.oz = ovz;
+        b.cx = sx[bx].size;
+        b.cy = sy[by].size;
+        b.cz = sz[bz].size;
+        out->push_back(b);
+        const int n = b.bx * b.by * b.bz;
+        const int kl = std::min(3 * b.bx, n - 1);
+        *n_max = std::max(*n_max, n);
+        *kl_max = std::max(*kl_max, kl);
+      }
+}
+
+// 3D shape tables: one entry per distinct block extent.
+struct Shapes3 {
+  std::vector<pfc::Shape3> shapes;
+  std::vector<int> block_shape, lev_start, rowpad, rowlin, rowof;
+  int nrows_max = 0, pad_max = 0, max_level_rows = 0;
+};
+
+void offsets63(int off[63][3]) {
+  int idx = 0;
+  for (int c = -3; c <= 3; ++c)
+    for (int b = -3; b <= 3; ++b)
+      for (int a = -3; a <= 3; ++a)
+        if (std::abs(a) + std::abs(b) + std::abs(c) <= 3) {
+          off[idx][0] = a;
+          off[idx][1] = b;
+          off[idx][2] = c;
+          ++idx;
+        }
+}
+
+void build_shapes3(const std::vector<BlockDesc>& blocks, Shapes3* S) {
+  int off[63][3];
+  offsets63(off);
+  for (const BlockDesc& b : blocks) {
+    int found = -1;
+    for (size_t i = 0; i < S->shapes.size(); ++i)
+      if (S->shapes[i].bx == b.bx && S->shapes[i].by == b.by && S->shapes[i].bz == b.bz) found = (int)i;
+    if (found < 0) {
+      pfc::Shape3 sh{};
+      sh.bx = b.bx;
+      sh.by = b.by;
+      sh.bz = b.bz;
+      sh.px = b.bx + 6;
+      sh.py = b.by + 6;
+      sh.pz = b.bz + 6;
+      sh.nrows = b.bx * b.by * b.bz;
+      sh.nlev = (b.bx - 1) + 3 * (b.by - 1) + 7 * (b.bz - 1) + 1;
+      sh.lev_off = (int)S->lev_start.size();
+      sh.row_off = (int)S->rowpad.size();
+      sh.pad_off = (int)S->rowof.size();
+      for (int o = 0; o < 63; ++o) sh.poff[o] = off[o][0] + sh.px * (off[o][1] + sh.py * off[o][2]);
+      // rows in level order, ascending linear index inside a level
+      std::vector<std::vector<int>> bylev(sh.nlev);
+      for (int c = 0; c < b.bz; ++c)
+        for (int bb = 0; bb < b.by; ++bb)
+          for (int a = 0; a < b.bx; ++a) bylev[a + 3 * bb + 7 * c].push_back(a + b.bx * (bb + b.by * c));
+      std::vector<int> rowof((size_t)sh.px * sh.py * sh.pz, -1);
+      int r = 0;
+      for (int l = 0; l < sh.nlev; ++l) {
+        S->lev_start.push_back(r);
+        S->max_level_rows = std::max(S->max_level_rows, (int)bylev[l].size());
+        for (int li : bylev[l]) {
+          const int a = li % b.bx, bb = (li / b.bx) % b.by, c = li / (b.bx * b.by);
+          const int pp = (a + 3) + sh.px * ((bb + 3) + sh.py * (c + 3));
+          S->rowpad.push_back(pp);
+          S->rowlin.push_back(li);
+          rowof[pp] = r;
+          ++r;
+        }
+      }
+      S->lev_start.push_back(r);
+      S->rowof.insert(S->rowof.end(), rowof.begin(), rowof.end());
+      S->nrows_max = std::max(S->nrows_max, sh.nrows);
+      S->pad_max = std::max(S->pad_max, sh.px * sh.py * sh.pz);
+      found = (int)S->shapes.size();
+      S->shapes.push_back(sh);
     }
+    S->block_shape.push_back(found);
+  }
+}
+
+// ILU(0) update lists: for lower offset o1 and upper offset o2 of row k = i + o1,
+// the entry o3 = o1 + o2 of row i when |o3|_1 <= 3.
+void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
+  int off[63][3];
+  offsets63(off);
+  upd->assign(31 * 32, 0);
+  upd_n->assign(32, 0);
+  for (int o1 = 0; o1 < 31; ++o1) {
+    int cnt = 0;
+    for (int o2 = 32; o2 < 63; ++o2) {
+      const int a = off[o1][0] + off[o2][0], b = off[o1][1] + off[o2][1], c = off[o1][2] + off[o2][2];
+      if (std::abs(a) + std::abs(b) + std::abs(c) > 3) continue;
+      int o3 = -1;
+      for (int t = 0; t < 63; ++t)
+        if (off[t][0] == a && off[t][1] == b && off[t][2] == c) o3 = t;
+      (*upd)[o1 * 32 + cnt] = o2 | (o3 << 8);
+      ++cnt;
+    }
+    (*upd_n)[o1] = cnt;
+  }
 }
 
 struct Plan {
-  size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status;
+  size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
+      tabs;
+  // 3D
+  size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
   int nblocks, n_max, kl_max;
   size_t sL, sU, sP;
   int lrow, ucol;
   size_t partial_len;
+  Shapes3 sh3;
+  size_t sLU3, sWork3, sPad3;
 };
 
 int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   int rc = validate(g, p);
   if (rc) return rc;
-  const long long N = g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
+  const bool d3 = g->dim == 3;
+  const long long N = g->n[0] * g->n[1] * (d3 ? g->n[2] : 1);
   std::vector<BlockDesc> blocks;
   build_blocks(g, p, &blocks, &pl->n_max, &pl->kl_max);
   pl->nblocks = (int)blocks.size();
   const size_t es = p->factor_prec == PFC_F64 ? 8 : (p->factor_prec == PFC_F32 ? 4 : 2);
-  // rows of L and columns of U padded to 8 elements: every block, row and chunk
-  // of rows starts on a 16-byte boundary and spans a multiple of 16 bytes (bulk copies)
-  pl->lrow = (pl->kl_max + 7) / 8 * 8;
-  pl->ucol = (2 * pl->kl_max + 1 + 7) / 8 * 8;
-  pl->sL = (size_t)pl->n_max * pl->lrow;
-  pl->sU = (size_t)pl->n_max * pl->ucol;
-  pl->sP = ((size_t)pl->n_max + 15) / 16 * 16;
+  const size_t tc = p->factor_prec == PFC_F64 ? 8 : 4;
+  if (!d3) {
+    // rows of L and columns of U padded to 8 elements: every block, row and chunk
+    // of rows starts on a 16-byte boundary and spans a multiple of 16 bytes (bulk copies)
+    pl->lrow = (pl->kl_max + 7) / 8 * 8;
+    pl->ucol = (2 * pl->kl_max + 1 + 7) / 8 * 8;
+    pl->sL = (size_t)pl->n_max * pl->lrow;
+    pl->sU = (size_t)pl->n_max * pl->ucol;
+    pl->sP = ((size_t)pl->n_max + 15) / 16 * 16;
+  } else {
+    pl->lrow = pl->ucol = 0;
+    pl->sL = pl->sU = pl->sP = 0;
+    build_shapes3(blocks, &pl->sh3);
+    pl->sLU3 = (size_t)pl->sh3.nrows_max * 32;
+    pl->sWork3 = (size_t)pl->sh3.nrows_max * 64;
+    pl->sPad3 = ((size_t)pl->sh3.pad_max + 31) / 32 * 32;
+  }
   const size_t vec = (size_t)N * 8;
   const int m = p->gmres_restart;
   const size_t tiles = (size_t)((g->n[0] + 31) / 32) * ((g->n[1] + 15) / 16);
   pl->partial_len = std::max<size_t>(tiles * 2, (size_t)pfc::kRedCtas * (pfc::kMaxVecs + 2));
+  pl->partial_len = std::max<size_t>(pl->partial_len, 152 * 8 * 2);
   Layout L;
   pl->phin = L.take(vec);
   pl->phinm1 = L.take(vec);
@@ -197,41 +323,61 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->U = L.take(pl->sU * es * pl->nblocks);
   pl->piv = L.take(pl->sP * pl->nblocks);
   pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
-  pl->lin = L.take(sizeof(double) * 49);
+  pl->lin = L.take(sizeof(double) * 343);
   pl->ctl = L.take(sizeof(GmresCtl));
   pl->partial = L.take(sizeof(double) * pl->partial_len);
   pl->red = L.take(sizeof(double) * 16);
   pl->status = L.take(sizeof(int) * 4);
+  pl->tabs = L.take(sizeof(double*) * 2 * pfc::kMaxVecs);
+  if (d3) {
+    const Shapes3& S = pl->sh3;
+    pl->T1 = L.take(vec);
+    pl->T2 = L.take(vec);
+    pl->shapes = L.take(sizeof(pfc::Shape3) * S.shapes.size());
+    pl->block_shape = L.take(sizeof(int) * S.block_shape.size());
+    pl->lev_start = L.take(sizeof(int) * S.lev_start.size());
+    pl->rowpad = L.take(sizeof(int) * S.rowpad.size());
+    pl->rowlin = L.take(sizeof(int) * S.rowlin.size());
+    pl->rowof = L.take(sizeof(int) * S.rowof.size());
+    pl->upd = L.take(sizeof(int) * 31 * 32);
+    pl->upd_n = L.take(sizeof(int) * 32);
+    pl->Lp = L.take(pl->sLU3 * es * pl->nblocks);
+    pl->Up = L.take(pl->sLU3 * es * pl->nblocks);
+    pl->work = L.take(pl->sWork3 * tc * pl->nblocks);
+    pl->ypad = L.take(pl->sPad3 * tc * pl->nblocks);
+  }
   pl->total = L.total;
   return PFC_OK;
 }
 
-// -(1/2) Delta_d L_gamma as a 7x7 table (2D), L_gamma = (1-gamma) + 2 Delta_d + Delta_d^2.
-void lin_stencil_2d(double h, double gamma, double* out49) {
-  double P1[7][7] = {};
-  P1[3][3] = -4.0;
-  P1[2][3] = P1[4][3] = P1[3][2] = P1[3][4] = 1.0;
-  auto conv = [](const double (*a)[7], const double (*b)[7], double (*c)[7]) {
-    for (int i = 0; i < 7; ++i)
-      for (int j = 0; j < 7; ++j) c[i][j] = 0.0;
-    for (int i = 0; i < 7; ++i)
-      for (int j = 0; j < 7; ++j) {
-        if (a[i][j] == 0.0) continue;
-        for (int k = 0; k < 7; ++k)
-          for (int l = 0; l < 7; ++l) {
-            if (b[k][l] == 0.0) continue;
-            const int y = i + k - 3, x = j + l - 3;
-            if (y >= 0 && y < 7 && x >= 0 && x < 7) c[y][x] += a[i][j] * b[k][l];
-          }
-      }
-  };
-  double P2[7][7], P3[7][7];
-  conv(P1, P1, P2);
-  conv(P2, P1, P3);
+// 7-point (or 5-point) stencil convolution on a 7x7x7 table, centre (3,3,3).
+void conv3(const double* a, const double* b, double* c) {
+  for (int i = 0; i < 343; ++i) c[i] = 0.0;
+  for (int i = 0; i < 343; ++i) {
+    if (a[i] == 0.0) continue;
+    const int az = i / 49 - 3, ay = (i / 7) % 7 - 3, ax = i % 7 - 3;
+    for (int j = 0; j < 343; ++j) {
+      if (b[j] == 0.0) continue;
+      const int z = az + j / 49 - 3, y = ay + (j / 7) % 7 - 3, x = ax + j % 7 - 3;
+      if (std::abs(x) <= 3 && std::abs(y) <= 3 && std::abs(z) <= 3) c[(z + 3) * 49 + (y + 3) * 7 + (x + 3)] += a[i] * b[j];
+    }
+  }
+}
+
+// -(1/2) Delta_d L_gamma with L_gamma = (1-gamma) + 2 Delta_d + Delta_d^2, as a
+// 7x7x7 table (index (dz+3)*49 + (dy+3)*7 + dx+3); a 2D grid uses its dz = 0 plane.
+void lin_stencil(int dim, double h, double gamma, double* out343, double* out49) {
+  double P1[343] = {}, P2[343], P3[343];
+  const int c = 171;
+  P1[c] = -2.0 * dim;
+  P1[c - 1] = P1[c + 1] = P1[c - 7] = P1[c + 7] = 1.0;
+  if (dim == 3) P1[c - 49] = P1[c + 49] = 1.0;
+  conv3(P1, P1, P2);
+  conv3(P2, P1, P3);
   const double ih2 = 1.0 / (h * h), ih4 = ih2 * ih2, ih6 = ih4 * ih2;
-  for (int i = 0; i < 7; ++i)
-    for (int j = 0; j < 7; ++j)
-      out49[i * 7 + j] = -0.5 * ((1.0 - gamma) * ih2 * P1[i][j] + 2.0 * ih4 * P2[i][j] + ih6 * P3[i][j]);
+  for (int i = 0; i < 343; ++i)
+    out343[i] = -0.5 * ((1.0 - gamma) * ih2 * P1[i] + 2.0 * ih4 * P2[i] + ih6 * P3[i]);
+  for (int i = 0; i < 49; ++i) out49[i] = out343[3 * 49 + i];
 }
 
 // ---------------------------------------------------------------- building blocks of a step
@@ -245,19 +391,47 @@ int sync_read(pfc_state* s, void* dst, const void* src, size_t bytes) {
 int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, bool project, const double* phin,
                   double idt, double* F, double* Pout, double* qout, int slot) {
   int np = 0;
-  pfc::launch_residual2d(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, phin, idt, F, Pout, qout, s->partial, &np,
-                         s->st);
+  if (s->dim == 2) {
+    pfc::launch_residual2d(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, phin, idt, F, Pout, qout, s->partial,
+                           &np, s->st);
+  } else {
+    const double* P = Pb;
+    if (S) {  // the trial point is needed at neighbours: materialise it first
+      pfc::launch_trial(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, Pout, s->st);
+      P = Pout;
+    }
+    pfc::launch_residual3d(s->g, P, phin, idt, F, qout, s->T1, s->T2, s->partial, &np, s->st);
+  }
   pfc::launch_reduce(s->partial, 1, np, s->red + slot, s->st);
   CU(cudaGetLastError());
   return PFC_OK;
 }
 
+void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip) {
+  if (s->dim == 2)
+    pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st);
+  else
+    pfc::launch_jvp3d(s->g, v, nullptr, q, idt, out, s->T1, s->T2, skip, s->st);
+}
+
+void precond(pfc_state* s, const double* r, const double* rscale, double* z, const int* skip) {
+  if (s->dim == 2)
+    pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, rscale, z, skip, s->status_dev + 1, s->st);
+  else
+    pfc::launch_ras_apply3d(s->g, s->blocks_dev, s->nblocks, s->r3, r, rscale, z, skip, s->status_dev + 1, s->st);
+}
+
 int factor_blocks(pfc_state* s, const double* q, double idt) {
-  // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx): blocks at most 42 cells wide in x
-  if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
-    return PFC_EINVAL;
+  if (s->dim == 2) {
+    // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx): blocks at most 42 cells wide in x
+    if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
+      return PFC_EINVAL;
+  }
   CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
-  pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
+  if (s->dim == 2)
+    pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
+  else
+    pfc::launch_factor3d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->r3, s->status_dev, s->st);
   CU(cudaGetLastError());
   return PFC_OK;
 }
@@ -269,8 +443,8 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
   const int m = s->p.gmres_restart;
   const int* done = &s->ctl->done;
   const int* reorth = &s->ctl->reorth;
+  unsigned int* counter = reinterpret_cast<unsigned int*>(s->status_dev + 2);  // last-CTA ticket
   int total = 0;
-  int np = 0;
   CU(cudaMemsetAsync(s->S, 0, sizeof(double) * N, s->st));
   CU(cudaMemsetAsync(s->red + 8, 0, 2 * sizeof(double), s->st));
   // first cycle: V_0 = F scaled by -1/||F||
@@ -279,33 +453,26 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
   CU(cudaMemcpyAsync(s->red + 10, &f2, sizeof(double), cudaMemcpyHostToDevice, s->st));
   pfc::launch_gmres_init(s->ctl, s->red + 10, -1.0, tol, s->st);
   while (true) {
-    VecList V{};
-    V.p[0] = v0;
-    for (int i = 1; i <= m; ++i) V.p[i] = s->Vbuf + (size_t)i * N;
-    VecList Z{};
-    for (int i = 0; i < m; ++i) Z.p[i] = s->Zbuf + (size_t)i * N;
+    // basis V_0 = v0, V_i = Vbuf + i N (pointer table s->vtab); Z_i = Zbuf + i N (s->ztab)
     int j = 0;
     const int chunk = 3;
     while (j < m) {
       const int jstart = j;
       const int jend = std::min(m, j + chunk);
       for (; j < jend; ++j) {
+        const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * N;
+        double* zj = s->Zbuf + (size_t)j * N;
         double* w = s->Vbuf + (size_t)(j + 1) * N;
         if (s->prof) CU(cudaEventRecord(s->ev[2 * j], s->st));
-        pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, V.p[j], &s->ctl->scale[j],
-                                (double*)Z.p[j], done, s->status_dev + 1, s->st);
+        precond(s, vj, &s->ctl->scale[j], zj, done);
         if (s->prof) CU(cudaEventRecord(s->ev[2 * j + 1], s->st));
-        pfc::launch_jvp2d(s->g, Z.p[j], nullptr, s->q, idt, w, done, s->st);
-        VecList D = V;
-        D.p[j + 1] = w;
-        for (int pass = 0; pass < 2; ++pass) {
-          pfc::launch_multidot(D, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, s->st, &np);
-          pfc::launch_reduce(s->partial, j + 2, np, s->ctl->red, s->st);
-          pfc::launch_gmres_after_dot(s->ctl, j, pass, s->st);
-          pfc::launch_multiaxpy(w, V, j + 1, s->ctl->coef, -1.0, N, s->partial, done, pass ? reorth : nullptr, s->st,
-                                &np);
-          pfc::launch_reduce(s->partial, 1, np, s->red + 8, s->st);
-          pfc::launch_gmres_after_axpy(s->ctl, s->red + 8, j, pass, m, s->st);
+        jvp(s, zj, s->q, idt, w, done);
+        for (int pass = 0; pass < 2; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
+          const pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
+          pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st);
+          const pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
+          pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
+                                pass ? reorth : nullptr, ta, s->st);
         }
       }
       CU(cudaGetLastError());
@@ -326,8 +493,10 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     total += its;
     if (its > 0) {
       pfc::launch_gmres_solve(s->ctl, s->st);
-      pfc::launch_multiaxpy(s->S, Z, its, s->ctl->y, 1.0, N, s->partial, nullptr, nullptr, s->st, &np);
-      pfc::launch_reduce(s->partial, 2, np, s->red + 8, s->st);  // red[8] = |S|^2, red[9] = sum S
+      // red[8] = |S|^2, red[9] = sum S
+      const pfc::Tail tsum{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 8};
+      pfc::launch_multiaxpy(s->S, s->Zbuf, s->ztab, its, s->ctl->y, 1.0, N, s->partial, nullptr, nullptr, tsum,
+                            s->st);
       CU(cudaGetLastError());
     }
     const double est = s->ctl_h->est;
@@ -338,12 +507,10 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
       return PFC_EGMRES;
     }
     // restart: r = -F - J S
-    pfc::launch_jvp2d(s->g, s->S, nullptr, s->q, idt, s->W, nullptr, s->st);
+    jvp(s, s->S, s->q, idt, s->W, nullptr);
     pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
-    VecList R{};
-    R.p[0] = s->W;
-    pfc::launch_multidot(R, 1, s->W, N, s->partial, nullptr, nullptr, s->st, &np);
-    pfc::launch_reduce(s->partial, 1, np, s->red + 10, s->st);
+    const pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 10};
+    pfc::launch_multidot(s->W, s->vtab, 1, s->W, N, s->partial, nullptr, nullptr, tnrm, s->st);
     pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, s->st);
     v0 = s->W;
     CU(cudaGetLastError());
@@ -411,7 +578,10 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
 
 int energy_mass(pfc_state* s, const double* phi, double* E, double* M) {
   int np = 0;
-  pfc::launch_energy2d(s->g, phi, s->partial, &np, s->st);
+  if (s->dim == 2)
+    pfc::launch_energy2d(s->g, phi, s->partial, &np, s->st);
+  else
+    pfc::launch_energy3d(s->g, phi, s->partial, &np, s->st);
   pfc::launch_reduce(s->partial, 2, np, s->red + 4, s->st);
   CU(cudaGetLastError());
   int rc = sync_read(s, s->red_h + 4, s->red + 4, 2 * sizeof(double));
@@ -529,21 +699,78 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     const double es = p->factor_prec == PFC_F64 ? 8.0 : (p->factor_prec == PFC_F32 ? 4.0 : 2.0);
     double bytes = 0.0;
     for (const BlockDesc& b : blocks) {
-      const double n = (double)b.bx * b.by;
-      const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
-      const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
-      bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
+      if (g->dim == 2) {
+        const double n = (double)b.bx * b.by;
+        const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
+        const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
+        bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
+      } else {  // 63 ILU(0) entries per row, row tables, gather, core write
+        const double n = (double)b.bx * b.by * b.bz;
+        bytes += n * 63.0 * es + n * 8.0 + n * 8.0 + (double)b.cx * b.cy * b.cz * 8.0;
+      }
     }
     s->apply_bytes = bytes;
   }
-  double lin[49];
-  lin_stencil_2d(h, eps, lin);
+  if (g->dim == 3) {
+    const Shapes3& S = pl.sh3;
+    s->T1 = (double*)at(pl.T1);
+    s->T2 = (double*)at(pl.T2);
+    pfc::Ras3D& R = s->r3;
+    R.shapes = (const pfc::Shape3*)at(pl.shapes);
+    R.block_shape = (const int*)at(pl.block_shape);
+    R.lev_start = (const int*)at(pl.lev_start);
+    R.rowpad = (const int*)at(pl.rowpad);
+    R.rowlin = (const int*)at(pl.rowlin);
+    R.rowof = (const int*)at(pl.rowof);
+    R.upd = (const int*)at(pl.upd);
+    R.upd_n = (const int*)at(pl.upd_n);
+    R.Lp = at(pl.Lp);
+    R.Up = at(pl.Up);
+    R.work = at(pl.work);
+    R.ypad = at(pl.ypad);
+    R.sLU = pl.sLU3;
+    R.sWork = pl.sWork3;
+    R.sPad = pl.sPad3;
+    R.prec = p->factor_prec;
+    R.max_level_rows = S.max_level_rows;
+    R.shift = 0.1;  // fraction of the block's mean |a_ii| added to the diagonal before ILU(0)
+    std::vector<int> upd, upd_n;
+    update_lists(&upd, &upd_n);
+    const size_t tc = p->factor_prec == PFC_F64 ? 8 : 4;
+    auto put = [&](const void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync((void*)dst, src, bytes, cudaMemcpyHostToDevice, s->st) == cudaSuccess;
+    };
+    if (!put(R.shapes, S.shapes.data(), sizeof(pfc::Shape3) * S.shapes.size()) ||
+        !put(R.block_shape, S.block_shape.data(), sizeof(int) * S.block_shape.size()) ||
+        !put(R.lev_start, S.lev_start.data(), sizeof(int) * S.lev_start.size()) ||
+        !put(R.rowpad, S.rowpad.data(), sizeof(int) * S.rowpad.size()) ||
+        !put(R.rowlin, S.rowlin.data(), sizeof(int) * S.rowlin.size()) ||
+        !put(R.rowof, S.rowof.data(), sizeof(int) * S.rowof.size()) ||
+        !put(R.upd, upd.data(), sizeof(int) * upd.size()) || !put(R.upd_n, upd_n.data(), sizeof(int) * upd_n.size()) ||
+        cudaMemsetAsync(R.ypad, 0, pl.sPad3 * tc * pl.nblocks, s->st) != cudaSuccess ||
+        cudaStreamSynchronize(s->st) != cudaSuccess) {
+      pfc_destroy(s);
+      return PFC_ECUDA;
+    }
+  }
+  double lin343[343], lin49[49];
+  lin_stencil(g->dim, h, eps, lin343, lin49);
+  const double* lin = g->dim == 2 ? lin49 : lin343;
+  const size_t lin_bytes = sizeof(double) * (g->dim == 2 ? 49 : 343);
+  s->vtab = (const double**)at(pl.tabs);
+  s->ztab = s->vtab + pfc::kMaxVecs;
+  std::vector<const double*> tabs(2 * pfc::kMaxVecs, nullptr);
+  for (int i = 0; i <= p->gmres_restart; ++i) tabs[i] = s->Vbuf + (size_t)i * s->g.n;
+  for (int i = 0; i < p->gmres_restart; ++i) tabs[pfc::kMaxVecs + i] = s->Zbuf + (size_t)i * s->g.n;
   if (cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
                       s->st) != cudaSuccess ||
-      cudaMemcpyAsync(s->lin_dev, lin, sizeof(lin), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemcpyAsync(s->lin_dev, lin, lin_bytes, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)s->vtab, tabs.data(), sizeof(double*) * tabs.size(), cudaMemcpyHostToDevice, s->st) !=
+          cudaSuccess ||
       cudaMemsetAsync(s->phin, 0, sizeof(double) * s->g.n, s->st) != cudaSuccess ||
       cudaMemsetAsync(s->phinm1, 0, sizeof(double) * s->g.n, s->st) != cudaSuccess ||
       cudaMemsetAsync(s->red, 0, sizeof(double) * 16, s->st) != cudaSuccess ||
+      cudaMemsetAsync(s->status_dev, 0, sizeof(int) * 4, s->st) != cudaSuccess ||
       cudaStreamSynchronize(s->st) != cudaSuccess) {
     pfc_destroy(s);
     return PFC_ECUDA;
@@ -715,7 +942,7 @@ int pfc_residual(pfc_state* s, const double* Phi, const double* phin, double dt,
 int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v, double dt, double* Jv) {
   if (!s || !Phi || !phin || !v || !Jv || !(dt > 0.0)) return PFC_EINVAL;
   pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
-  pfc::launch_jvp2d(s->g, v, nullptr, s->qt, 1.0 / dt, Jv, nullptr, s->st);
+  jvp(s, v, s->qt, 1.0 / dt, Jv, nullptr);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(s->st));
   return PFC_OK;
@@ -726,7 +953,7 @@ int pfc_precond_apply(pfc_state* s, const double* Phi, const double* phin, doubl
   pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
   int rc = factor_blocks(s, s->qt, 1.0 / dt);
   if (rc) return rc;
-  pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, nullptr, z, nullptr, s->status_dev + 1, s->st);
+  precond(s, r, nullptr, z, nullptr);
   CU(cudaGetLastError());
   if ((rc = sync_read(s, s->status_h, s->status_dev, 2 * sizeof(int)))) return rc;
   if (s->status_h[0]) return s->status_h[0];

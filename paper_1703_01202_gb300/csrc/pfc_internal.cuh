@@ -89,15 +89,73 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
 size_t factor_smem_bytes(int prec, int kl, int n_max);
 
+// ---- 3D stencils (stencil3d.cu)
+void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, const double* ssum, double* Pout,
+                  cudaStream_t st);
+void launch_residual3d(const Geo& g, const double* P, const double* phin, double idt, double* F, double* q_out,
+                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st);
+void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
+                  double* T1, double* T2, const int* skip, cudaStream_t st);
+void launch_energy3d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
+
+// ---- 3D Schwarz preconditioner with shifted ILU(0) subdomain solves (ras3d.cu)
+// The 63 offsets (da, db, dc) with |da|+|db|+|dc| <= 3 in lexicographic (dc, db, da)
+// order: 0..30 lower, 31 the diagonal, 32..62 upper.
+constexpr int kNOff = 63;
+// Blocks of equal extent share one shape: rows in level order (level = a + 3b + 7c,
+// which every lower offset strictly decreases), padded positions (3-cell zero ring).
+struct Shape3 {
+  int bx, by, bz, px, py, pz;
+  int nrows, nlev;
+  int lev_off;  // level starts: lev_start[lev_off .. lev_off + nlev]
+  int row_off;  // rowpad / rowlin: [row_off .. row_off + nrows)
+  int pad_off;  // rowof: [pad_off .. pad_off + px*py*pz)
+  int poff[kNOff];
+};
+struct Ras3D {
+  const Shape3* shapes;
+  const int* block_shape;
+  const int* lev_start;
+  const int* rowpad;  // padded linear position of each row
+  const int* rowlin;  // block-local linear index of each row
+  const int* rowof;   // padded position -> row (-1 on the ring)
+  const int* upd;     // update lists: upd[o1 * 32 + t] = o2 | (o3 << 8), count in upd_n[o1]
+  const int* upd_n;
+  void* Lp;           // per block nrows_max x 32: L multipliers of offsets 0..30 (storage type)
+  void* Up;           // per block nrows_max x 32: [0] inverted diagonal, [1..31] offsets 32..62
+  void* work;         // per block nrows_max x 64 working rows (compute type)
+  void* ypad;         // per block pad_max (compute type): solve vector with zero ring
+  size_t sLU, sWork, sPad;
+  int prec;
+  int max_level_rows;
+  double shift;       // diagonal shift, relative to the block's mean |a_ii|
+};
+void launch_factor3d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
+                     const double* lin343, const Ras3D& R, int* status, cudaStream_t st);
+void launch_ras_apply3d(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
+                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
+
 // ---- Krylov vector kernels (krylov.cu)
-void launch_multidot(const VecList& V, int nv, const double* w, long long n, double* partial, const int* skip,
-                     const int* only_if, cudaStream_t st, int* nparts);
-void launch_multiaxpy(double* w, const VecList& X, int nx, const double* coef, double sign, long long n,
-                      double* partial, const int* skip, const int* only_if, cudaStream_t st, int* nparts);
+// What the last CTA of a multi-dot / multi-axpy does after the fixed-order
+// reduction of all CTAs' partial sums (counter: a device ticket that is zero
+// between launches; a null counter means "partials only").
+struct Tail {
+  enum { kSums = 0, kDot = 1, kAxpy = 2 };
+  int kind;
+  int j, pass, m;           // Arnoldi column, Gram-Schmidt pass, restart length
+  GmresCtl* ctl;
+  unsigned int* counter;
+  double* out;              // kSums: reduced values
+};
+
+// Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
+void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
+                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st);
+void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
+                      long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
+                      cudaStream_t st);
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st);
 void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, cudaStream_t st);
-void launch_gmres_after_dot(GmresCtl* ctl, int j, int pass, cudaStream_t st);
-void launch_gmres_after_axpy(GmresCtl* ctl, const double* red2, int j, int pass, int m, cudaStream_t st);
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
 void launch_extrapolate(double* out, const double* a, const double* b, double ratio, long long n,

@@ -1,0 +1,202 @@
+// FP64 stencil kernels of the 3D scheme: the DVDM residual (Eq. NSOP with the
+// variational derivative of Eq. discretedG), the Jacobian-vector product (Eq.
+// Jacobi), the discrete energy (Eqs. relations, freeenergy) and mass, on a
+// periodic nx x ny x nz grid (x fastest).
+//
+// The radius-3 composed operators are evaluated in three 7-point passes with
+// two scratch fields (T1, T2): a Laplacian pass, a pass that forms mu (or the
+// JVP's w) from it, and a final Laplacian pass that writes F (or J v).  Every
+// pass reads its neighbours through L1/L2; the FP64 issue rate, not HBM, bounds
+// them on GB300, so the extra passes cost little next to a fused 3D tile.
+#include "pfc_internal.cuh"
+
+namespace pfc {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+__device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+
+// unscaled 7-point Laplacian of u (+ u2 if given) at point idx = (x, y, z)
+__device__ __forceinline__ double lap7(const double* __restrict__ u, const double* __restrict__ u2, const Geo& g,
+                                       int x, int y, int z) {
+  const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+  const long long c = x + sy * y + sz * z;
+  const long long xp = c + (wrap_up(x, g.nx) - x) * sx, xm = c + (wrap_dn(x, g.nx) - x) * sx;
+  const long long yp = c + (wrap_up(y, g.ny) - y) * sy, ym = c + (wrap_dn(y, g.ny) - y) * sy;
+  const long long zp = c + (wrap_up(z, g.nz) - z) * sz, zm = c + (wrap_dn(z, g.nz) - z) * sz;
+  if (u2) {
+    const double cc = u[c] + u2[c];
+    return ((u[xp] + u2[xp]) + (u[xm] + u2[xm])) + ((u[yp] + u2[yp]) + (u[ym] + u2[ym])) +
+           ((u[zp] + u2[zp]) + (u[zm] + u2[zm])) - 6.0 * cc;
+  }
+  return (u[xp] + u[xm]) + (u[yp] + u[ym]) + (u[zp] + u[zm]) - 6.0 * u[c];
+}
+
+__device__ __forceinline__ void coords(const Geo& g, long long i, int* x, int* y, int* z) {
+  const long long nxy = (long long)g.nx * g.ny;
+  *z = (int)(i / nxy);
+  const long long r = i - (long long)(*z) * nxy;
+  *y = (int)(r / g.nx);
+  *x = (int)(r - (long long)(*y) * g.nx);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];  // fixed order: deterministic
+  return s;
+}
+
+// out = scale * Lap_u(a [+ b])   (scale applied to the unscaled Laplacian)
+__global__ void __launch_bounds__(NT) k_lap3d(Geo g, const double* __restrict__ a, const double* __restrict__ b,
+                                              const double* __restrict__ ascale, double* __restrict__ out,
+                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const double sc = ascale ? *ascale : 1.0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
+    int x, y, z;
+    coords(g, i, &x, &y, &z);
+    out[i] = sc * lap7(a, b, g, x, y, z);
+  }
+}
+
+// mode 0 (residual): out = mu = c0 s + ih2 T1 + ih4/2 Lap(T1) + (P^2 + N^2) s / 4, s = P + N
+// mode 1 (JVP):      out = w  = c0 v + ih2 T1 + ih4/2 Lap(T1) + q v,  v = sc * P
+__global__ void __launch_bounds__(NT) k_mid3d(Geo g, int mode, const double* __restrict__ P,
+                                              const double* __restrict__ N, const double* __restrict__ vscale,
+                                              const double* __restrict__ T1, double* __restrict__ out,
+                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const double ih2 = g.ih2, ih4 = g.ih2 * g.ih2, c0 = 0.5 * (1.0 - g.gamma);
+  const double sc = vscale ? *vscale : 1.0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
+    int x, y, z;
+    coords(g, i, &x, &y, &z);
+    const double L1 = T1[i];
+    const double LL = lap7(T1, nullptr, g, x, y, z);
+    if (mode == 0) {
+      const double p = P[i], nn = N[i], s = p + nn;
+      out[i] = fma(0.25 * fma(p, p, nn * nn), s, fma(0.5 * ih4, LL, fma(ih2, L1, c0 * s)));
+    } else {
+      const double v = sc * P[i];
+      out[i] = fma(N[i], v, fma(0.5 * ih4, LL, fma(ih2, L1, c0 * v)));
+    }
+  }
+}
+
+// F = (P - N) idt - ih2 Lap(mu); q = (3P^2 + 2PN + N^2)/4; per-CTA sum of F^2.
+__global__ void __launch_bounds__(NT) k_res_out3d(Geo g, const double* __restrict__ P, const double* __restrict__ N,
+                                                  const double* __restrict__ mu, double idt, double* __restrict__ F,
+                                                  double* __restrict__ qout, double* __restrict__ partial) {
+  __shared__ double red[NT / 32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
+    int x, y, z;
+    coords(g, i, &x, &y, &z);
+    const double p = P[i], nn = N[i];
+    const double f = fma(-g.ih2, lap7(mu, nullptr, g, x, y, z), (p - nn) * idt);
+    F[i] = f;
+    if (qout) qout[i] = 0.25 * fma(3.0 * p, p, nn * fma(2.0, p, nn));
+    acc = fma(f, f, acc);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// J v = sc v idt - ih2 Lap(w)
+__global__ void __launch_bounds__(NT) k_jvp_out3d(Geo g, const double* __restrict__ v,
+                                                  const double* __restrict__ vscale, const double* __restrict__ w,
+                                                  double idt, double* __restrict__ Jv, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const double sc = vscale ? *vscale : 1.0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
+    int x, y, z;
+    coords(g, i, &x, &y, &z);
+    Jv[i] = fma(-g.ih2, lap7(w, nullptr, g, x, y, z), sc * v[i] * idt);
+  }
+}
+
+// trial point Pout = Pb + lam (S - mean S)
+__global__ void k_trial(long long n, const double* __restrict__ Pb, const double* __restrict__ S, double lam,
+                        const double* __restrict__ ssum, double* __restrict__ Pout) {
+  const double sm = ssum ? *ssum / (double)n : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    Pout[i] = Pb[i] + lam * (S[i] - sm);
+}
+
+// Per-CTA sums of G_d (Eq. relations, three axes) and of phi.
+__global__ void __launch_bounds__(NT) k_energy3d(Geo g, const double* __restrict__ phi,
+                                                 double* __restrict__ partial) {
+  __shared__ double red[NT / 32];
+  const double c0 = 0.5 * (1.0 - g.gamma), ih2 = g.ih2;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  double e = 0.0, m = 0.0;
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
+    int x, y, z;
+    coords(g, i, &x, &y, &z);
+    const double p = phi[i];
+    const double xp = phi[i + (wrap_up(x, g.nx) - x)], xm = phi[i + (wrap_dn(x, g.nx) - x)];
+    const double yp = phi[i + (wrap_up(y, g.ny) - y) * sy], ym = phi[i + (wrap_dn(y, g.ny) - y) * sy];
+    const double zp = phi[i + (wrap_up(z, g.nz) - z) * sz], zm = phi[i + (wrap_dn(z, g.nz) - z) * sz];
+    const double lap = ih2 * ((xp + xm) + (yp + ym) + (zp + zm) - 6.0 * p);
+    const double grad = (xp - p) * (xp - p) + (p - xm) * (p - xm) + (yp - p) * (yp - p) + (p - ym) * (p - ym) +
+                        (zp - p) * (zp - p) + (p - zm) * (p - zm);
+    const double p2 = p * p;
+    e += c0 * p2 + 0.25 * p2 * p2 + 0.5 * lap * lap - 0.5 * ih2 * grad;
+    m += p;
+  }
+  const double se = block_sum(e, red);
+  __syncthreads();
+  const double sm = block_sum(m, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = se;
+    partial[gridDim.x + blockIdx.x] = sm;
+  }
+}
+
+int ctas(long long n) {
+  long long b = (n + NT - 1) / NT;
+  const long long cap = 152LL * 8;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+}  // namespace
+
+void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, const double* ssum, double* Pout,
+                  cudaStream_t st) {
+  k_trial<<<ctas(g.n), NT, 0, st>>>(g.n, Pb, S, lam, ssum, Pout);
+  count_launches(1);
+}
+
+void launch_residual3d(const Geo& g, const double* P, const double* phin, double idt, double* F, double* q_out,
+                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st) {
+  const int b = ctas(g.n);
+  k_lap3d<<<b, NT, 0, st>>>(g, P, phin, nullptr, T1, nullptr);
+  k_mid3d<<<b, NT, 0, st>>>(g, 0, P, phin, nullptr, T1, T2, nullptr);
+  k_res_out3d<<<b, NT, 0, st>>>(g, P, phin, T2, idt, F, q_out, partial);
+  count_launches(3);
+  *nparts = b;
+}
+
+void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
+                  double* T1, double* T2, const int* skip, cudaStream_t st) {
+  const int b = ctas(g.n);
+  k_lap3d<<<b, NT, 0, st>>>(g, v, nullptr, vscale, T1, skip);
+  k_mid3d<<<b, NT, 0, st>>>(g, 1, v, q, vscale, T1, T2, skip);
+  k_jvp_out3d<<<b, NT, 0, st>>>(g, v, vscale, T2, idt, Jv, skip);
+  count_launches(3);
+}
+
+void launch_energy3d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st) {
+  const int b = ctas(g.n);
+  k_energy3d<<<b, NT, 0, st>>>(g, phi, partial);
+  count_launches(1);
+  *nparts = b;
+}
+
+}  // namespace pfc
