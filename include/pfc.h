@@ -50,8 +50,9 @@ typedef enum {
 enum { PFC_F64 = 0, PFC_F32 = 1, PFC_BF16 = 2 };
 /* Schwarz variant (Sec. 4): Eq. invM, Eq. ras, Eq. ash. */
 enum { PFC_AS = 0, PFC_LEFT_RAS = 1, PFC_RIGHT_RAS = 2 };
-/* Newton initial guess: phi^n (Sec. 4), linear extrapolation, caller-supplied. */
-enum { PFC_GUESS_PREV = 0, PFC_GUESS_EXTRAP = 1, PFC_GUESS_USER = 2 };
+/* Newton initial guess: phi^n (Sec. 4), linear extrapolation, caller-supplied,
+   or the learned network (pfc_set_guess_net) with the extrapolation as fallback. */
+enum { PFC_GUESS_PREV = 0, PFC_GUESS_EXTRAP = 1, PFC_GUESS_USER = 2, PFC_GUESS_LEARNED = 3 };
 
 typedef struct {
   int dim;       /* 2 or 3                                        */
@@ -91,7 +92,10 @@ typedef struct {
   double mass;       /* h^d sum phi^{n+1}                                      */
   double res_norm0;  /* ||F(Phi_0)||                                          */
   double res_norm;   /* ||F(phi^{n+1})||                                      */
+  int guess_used;    /* PFC_GUESS_* actually used for Phi_0 (learned may fall back) */
 } pfc_step_info;
+
+typedef struct pfc_cnn pfc_cnn;
 
 typedef struct pfc_state pfc_state;
 
@@ -170,6 +174,41 @@ int pfc_step_host(pfc_state* s, const double* phin_host, double dt, double* out_
 int pfc_profile(pfc_state* s, int enable);
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches);
+
+/* ---- Learned Newton initial guess (2D).  The paper starts Newton from phi^n
+   (Sec. 4); the learned form adds a periodic 3x3 convolutional network
+   (channels 3 -> 32 -> 32 -> 32 -> 1, GELU, BF16 weights and activations,
+   FP32 accumulation) on the features
+     c0 = phi^n - mean(phi^n), c1 = r (phi^n - phi^{n-1}), c2 = dt / dt_max,
+   r = dt / dt_prev, and takes Phi_0 = phi^n + c1 + s_out * net(c), shifted to
+   the mass of phi^n.  Parameters: one flat FP32 vector, layer by layer
+   [W (Cout, Cin, 3, 3) row-major, b (Cout)].  Fields on device, planar. */
+int pfc_cnn_param_count(void);
+/* Workspace bytes of a network object for an nx x ny grid (activations,
+   gradients, Adam state). */
+int pfc_cnn_workspace_size(int64_t nx, int64_t ny, size_t* bytes);
+int pfc_cnn_create(int64_t nx, int64_t ny, void* dev_workspace, size_t bytes, void* cuda_stream, pfc_cnn** out);
+void pfc_cnn_destroy(pfc_cnn* c);
+/* Host arrays of pfc_cnn_param_count() floats; set also clears the Adam moments. */
+int pfc_cnn_set_params(pfc_cnn* c, const float* theta);
+int pfc_cnn_get_params(pfc_cnn* c, float* theta);
+/* out (N doubles) = net(feat), feat = 3 planes of N doubles. */
+int pfc_cnn_forward(pfc_cnn* c, const double* feat, double* out);
+/* Mean squared error against target (N doubles) and its gradient (host array
+   of pfc_cnn_param_count() floats, may be NULL). */
+int pfc_cnn_loss_grad(pfc_cnn* c, const double* feat, const double* target, double* loss, float* grad);
+/* One Adam step (lr, step count t >= 1) on one sample; *loss (may be NULL) is
+   the loss before the step. */
+int pfc_cnn_train_step(pfc_cnn* c, const double* feat, const double* target, double lr, int t, double* loss);
+/* One training sample from three consecutive fields of a trajectory (device
+   arrays of N doubles): feat (3 x N) = the features above with r = dt / dt_prev
+   and c2 = dt / dt_max, target (N) = (phi^{n+1} - phi^n - c1) / s_out. */
+int pfc_cnn_sample(pfc_cnn* c, const double* phinm1, const double* phin, const double* phinp1, double r,
+                   double c2, double s_out, double* feat, double* target);
+/* Lets PFC_GUESS_LEARNED use network c (same grid as s; c stays owned by the
+   caller and must outlive its use).  Each step compares the residual norms of
+   the learned and the extrapolated guess and starts Newton from the smaller. */
+int pfc_set_guess_net(pfc_state* s, pfc_cnn* c, double s_out);
 
 /* The 2D residual F(Phi) of pfc_residual, for callers that cannot allocate
    device memory at all: it needs no pfc_state and no workspace.  (The paper

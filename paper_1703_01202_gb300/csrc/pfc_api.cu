@@ -46,6 +46,10 @@ struct pfc_state {
   // 3D: scratch fields of the three-pass stencils and the ILU(0) Schwarz data
   double *T1, *T2;
   pfc::Ras3D r3;
+  // learned initial guess
+  pfc_cnn* cnn;
+  double s_out;
+  double* feat;  // 3 x N feature planes
   // reductions and control
   GmresCtl* ctl;
   double* partial;
@@ -262,7 +266,7 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs;
+      tabs, feat;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -329,6 +333,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->red = L.take(sizeof(double) * 16);
   pl->status = L.take(sizeof(int) * 4);
   pl->tabs = L.take(sizeof(double*) * 2 * pfc::kMaxVecs);
+  pl->feat = d3 ? 0 : L.take(vec * 3);
   if (d3) {
     const Shapes3& S = pl->sh3;
     pl->T1 = L.take(vec);
@@ -576,6 +581,37 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
   return PFC_OK;
 }
 
+int energy_mass(pfc_state* s, const double* phi, double* E, double* M);
+
+// Learned guess with fallback: Phi_L = phi^n + c1 + s_out net(c) (mass of phi^n)
+// against Phi_E = phi^n + c1 (the extrapolation); Newton starts from the one with
+// the smaller residual norm.  Leaves the choice in s->Phi.
+int learned_guess(pfc_state* s, double dt, int* used) {
+  const long long N = s->g.n;
+  int rc = energy_mass(s, s->phin, nullptr, nullptr);  // red[5] = sum phi^n
+  if (rc) return rc;
+  pfc::launch_cnn_features(N, s->phin, s->phinm1, s->red + 5, dt / s->dt_prev, dt / s->p.dt_max, s->feat, s->st);
+  pfc::Cnn* c = reinterpret_cast<pfc::Cnn*>(s->cnn);
+  pfc::cnn_forward(c, s->feat);
+  int np = 0;
+  pfc::launch_cnn_delta(N, s->feat, pfc::cnn_output(c), s->s_out, s->W, s->partial, &np, s->st);
+  pfc::launch_reduce(s->partial, 1, np, s->red + 11, s->st);
+  pfc::launch_add_centered(N, s->phin, s->W, s->red + 11, s->Pt, s->st);  // learned
+  pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, N, s->st);  // extrapolated
+  const double idt = 1.0 / dt;
+  if ((rc = eval_residual(s, s->Pt, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 2))) return rc;
+  if ((rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 3))) return rc;
+  if ((rc = sync_read(s, s->red_h + 2, s->red + 2, 2 * sizeof(double)))) return rc;
+  const double rl = s->red_h[2], re = s->red_h[3];
+  if (rl == rl && rl < re) {
+    std::swap(s->Phi, s->Pt);
+    *used = PFC_GUESS_LEARNED;
+  } else {
+    *used = PFC_GUESS_EXTRAP;
+  }
+  return PFC_OK;
+}
+
 int energy_mass(pfc_state* s, const double* phi, double* E, double* M) {
   int np = 0;
   if (s->dim == 2)
@@ -686,6 +722,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->partial = (double*)at(pl.partial);
   s->red = (double*)at(pl.red);
   s->status_dev = (int*)at(pl.status);
+  s->feat = g->dim == 2 ? (double*)at(pl.feat) : nullptr;
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess) {
@@ -820,15 +857,21 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
   info.dt = dt;
   const size_t b = sizeof(double) * s->g.n;
   // initial guess Phi_0
-  if (s->p.guess == PFC_GUESS_EXTRAP && s->have_prev_dt) {
+  int rc = PFC_OK;
+  info.guess_used = PFC_GUESS_PREV;
+  if (s->p.guess == PFC_GUESS_LEARNED && s->have_prev_dt && s->cnn) {
+    if ((rc = learned_guess(s, dt, &info.guess_used))) return rc;
+  } else if ((s->p.guess == PFC_GUESS_EXTRAP || s->p.guess == PFC_GUESS_LEARNED) && s->have_prev_dt) {
     pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, s->g.n, s->st);
+    info.guess_used = PFC_GUESS_EXTRAP;
   } else if (s->p.guess == PFC_GUESS_USER && s->have_user_guess) {
     CU(cudaMemcpyAsync(s->Phi, s->guess, b, cudaMemcpyDeviceToDevice, s->st));
+    info.guess_used = PFC_GUESS_USER;
   } else {
     CU(cudaMemcpyAsync(s->Phi, s->phin, b, cudaMemcpyDeviceToDevice, s->st));
   }
   CU(cudaGetLastError());
-  int rc = newton(s, dt, &info);
+  rc = newton(s, dt, &info);
   s->have_user_guess = false;
   if (rc) {
     info.status = rc;
@@ -855,6 +898,17 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
   info.mass = M;
   info.status = PFC_OK;
   if (info_out) *info_out = info;
+  return PFC_OK;
+}
+
+int pfc_set_guess_net(pfc_state* s, pfc_cnn* c, double s_out) {
+  if (!s || s->dim != 2 || !(s_out > 0.0)) return PFC_EINVAL;
+  if (c) {
+    const pfc::Cnn* cc = reinterpret_cast<const pfc::Cnn*>(c);
+    if (pfc::cnn_nx(cc) != s->g.nx || pfc::cnn_ny(cc) != s->g.ny) return PFC_EINVAL;
+  }
+  s->cnn = c;
+  s->s_out = s_out;
   return PFC_OK;
 }
 

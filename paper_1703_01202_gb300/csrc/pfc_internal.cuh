@@ -135,6 +135,29 @@ void launch_factor3d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 void launch_ras_apply3d(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
 
+// ---- learned initial guess network (cnn.cu)
+struct Cnn;
+size_t cnn_workspace_bytes(long long n);
+void cnn_bind(Cnn* c, void* ws);
+void cnn_forward(Cnn* c, const double* feat);
+int cnn_backward(Cnn* c, const double* feat, const double* target, int* nparts);
+void cnn_adam(Cnn* c, float lr, int t);
+void cnn_refresh_bf16(Cnn* c);
+void cnn_out_to_f64(Cnn* c, double* out);
+const float* cnn_output(const Cnn* c);
+int cnn_nx(const Cnn* c);
+int cnn_ny(const Cnn* c);
+// features (phi^n - mean, r (phi^n - phi^{n-1}), dt / dt_max) as 3 planes; guess pieces
+void launch_cnn_features(long long n, const double* phin, const double* phinm1, const double* mass_sum, double r,
+                         double c2, double* feat, cudaStream_t st);
+void launch_cnn_delta(long long n, const double* feat, const float* out, double s_out, double* delta,
+                      double* partial, int* nparts, cudaStream_t st);
+void launch_add_centered(long long n, const double* base, const double* delta, const double* dsum, double* out,
+                         cudaStream_t st);
+void launch_sum(long long n, const double* x, double* partial, int* nparts, cudaStream_t st);
+void launch_cnn_target(long long n, const double* phinp1, const double* phin, const double* feat, double s_out,
+                       double* target, cudaStream_t st);
+
 // ---- Krylov vector kernels (krylov.cu)
 // What the last CTA of a multi-dot / multi-axpy does after the fixed-order
 // reduction of all CTAs' partial sums (counter: a device ticket that is zero

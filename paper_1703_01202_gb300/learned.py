@@ -1,0 +1,137 @@
+"""Training and evaluation of the learned Newton initial guess.
+
+Trajectories come from the solver itself (plain NKS, F32 factors) on
+hexagonal-seed crystal-growth fields like the 1024^2 workload's, on a smaller
+grid; every step after the first gives one sample (features of phi^n, phi^{n-1},
+dt and the target correction toward phi^{n+1}), built on the device by
+pfc_cnn_sample.  Training runs pfc_cnn_train_step (the library's forward,
+backward and Adam kernels), one sample per Adam step.  All arithmetic runs in
+libpfc; this module only sequences calls and keeps samples in device memory.
+"""
+from __future__ import annotations
+
+import math
+import time
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import inputs, pfc
+
+H = math.pi / 4
+GAMMA = 0.25
+DT_MIN, DT_MAX, ETA = 1e-2, 10.0, 5000.0
+
+
+def generate(n_traj: int, steps: int, shape=(512, 512), seed0: int = 2000, s_out: Optional[float] = None,
+             sub: Optional[Tuple[int, int]] = None) -> Dict:
+    """Runs n_traj trajectories of `steps` adaptive steps from seeded hexagonal
+    crystal fields and returns the device samples and the output scale."""
+    import torch
+
+    ny, nx = shape
+    sub = sub or (nx // 16, ny // 16)
+    params = pfc.default_params(sub=sub, overlap=1, factor_prec=pfc.PFC_F32, dt_min=DT_MIN, dt_max=DT_MAX, eta=ETA)
+    solver = pfc.Solver(shape, H, GAMMA, params)
+    net = pfc.GuessNet(shape)
+    feats: List = []
+    targets: List = []
+    raw: List[Tuple] = []
+    t0 = time.perf_counter()
+    for tr in range(n_traj):
+        phi0 = inputs.hex_seeds_2d(shape, H, seed=seed0 + tr)
+        solver.set_field(phi0)
+        hist = [solver.get_field_device()]
+        dts = []
+        for _ in range(steps):
+            dt = solver.next_dt()
+            solver.step(dt)
+            dts.append(dt)
+            hist.append(solver.get_field_device())
+        for k in range(1, steps):  # sample: phi^{k-1}, phi^k -> phi^{k+1}, dt_k, dt_{k-1}
+            raw.append((hist[k - 1], hist[k], hist[k + 1], dts[k] / dts[k - 1], dts[k] / DT_MAX))
+    if s_out is None:  # output scale: rms of the extrapolation error over the first trajectory's samples
+        errs = []
+        for a, b, c, r, _ in raw[: max(1, steps - 1)]:
+            e = (c - b - r * (b - a)).cpu().numpy()
+            errs.append(float(np.sqrt(np.mean(e * e))))
+        s_out = float(np.mean(errs)) or 1e-3
+    for a, b, c, r, c2 in raw:
+        f = torch.empty((3,) + tuple(shape), dtype=torch.float64, device="cuda")
+        t = torch.empty(tuple(shape), dtype=torch.float64, device="cuda")
+        net.sample(a, b, c, r, c2, s_out, f, t)
+        feats.append(f)
+        targets.append(t)
+    return {"feat": feats, "target": targets, "s_out": s_out, "shape": tuple(shape), "gen_seconds":
+            time.perf_counter() - t0, "net": net}
+
+
+def _init_params(seed: int) -> np.ndarray:
+    """He-style uniform initialisation; the last layer starts near zero so the
+    first guesses are the extrapolation."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    layers = [(3, 32), (32, 32), (32, 32), (32, 1)]
+    for li, (ci, co) in enumerate(layers):
+        bound = math.sqrt(6.0 / (ci * 9))
+        w = rng.uniform(-bound, bound, co * ci * 9)
+        if li == len(layers) - 1:
+            w *= 0.01
+        parts.append(w)
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
+              theta0: Optional[np.ndarray] = None) -> Tuple[np.ndarray, List[float]]:
+    """Adam on single samples in a seeded random order; returns the parameters and the per-epoch mean loss."""
+    net: pfc.GuessNet = data["net"]
+    net.set_params(theta0 if theta0 is not None else _init_params(seed))
+    rng = np.random.default_rng(seed)
+    n = len(data["feat"])
+    t = 0
+    history = []
+    for _ in range(epochs):
+        order = rng.permutation(n)
+        tot = 0.0
+        for i in order:
+            t += 1
+            tot += net.train_step(data["feat"][i], data["target"][i], lr, t)
+        history.append(tot / max(n, 1))
+    return net.get_params(), history
+
+
+def evaluate(theta: np.ndarray, s_out: float, shape=(1024, 1024), steps: int = 12, warmup: int = 3,
+             seed: int = 1001, factor_prec: int = pfc.PFC_BF16) -> Dict:
+    """Newton / GMRES iterations and time per step with the extrapolated guess
+    and with the learned guess (fallback included) on a hexagonal-seed field."""
+    import torch
+
+    ny, nx = shape
+    out = {}
+    phi0 = inputs.hex_seeds_2d(shape, H, seed=seed)
+    for mode in ("extrap", "learned"):
+        guess = pfc.PFC_GUESS_EXTRAP if mode == "extrap" else pfc.PFC_GUESS_LEARNED
+        params = pfc.default_params(sub=(nx // 16, ny // 16), overlap=1, factor_prec=factor_prec, guess=guess,
+                                    dt_min=DT_MIN, dt_max=DT_MAX, eta=ETA)
+        s = pfc.Solver(shape, H, GAMMA, params)
+        net = None
+        if mode == "learned":
+            net = pfc.GuessNet(shape)
+            net.set_params(theta)
+            pfc.set_guess_net(s, net, s_out)
+        s.set_field(phi0)
+        s.run(warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = s.run(steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[mode] = {"steps_per_s": steps / el, "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
+                     "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
+                     "learned_used": sum(1 for i in infos if i["guess_used"] == pfc.PFC_GUESS_LEARNED),
+                     "energy_last": infos[-1]["energy"], "field": s.get_field()}
+        s.close()
+        if net is not None:
+            net.close()
+    return out

@@ -21,7 +21,7 @@ PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA = 0, -1, -2, -3
 PFC_ENEWTON, PFC_EGMRES, PFC_ESINGULAR, PFC_ENAN, PFC_ETIMEOUT = -4, -5, -6, -7, -8
 PFC_F64, PFC_F32, PFC_BF16 = 0, 1, 2
 PFC_AS, PFC_LEFT_RAS, PFC_RIGHT_RAS = 0, 1, 2
-PFC_GUESS_PREV, PFC_GUESS_EXTRAP, PFC_GUESS_USER = 0, 1, 2
+PFC_GUESS_PREV, PFC_GUESS_EXTRAP, PFC_GUESS_USER, PFC_GUESS_LEARNED = 0, 1, 2, 3
 
 
 class pfc_grid(ctypes.Structure):
@@ -42,6 +42,7 @@ class pfc_step_info(ctypes.Structure):
     _fields_ = [
         ("status", c_int), ("newton_its", c_int), ("gmres_its", c_int), ("ls_cuts", c_int),
         ("dt", c_double), ("energy", c_double), ("mass", c_double), ("res_norm0", c_double), ("res_norm", c_double),
+        ("guess_used", c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -78,6 +79,18 @@ _SIGNATURES = [
                                  POINTER(c_longlong)]),
     ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
                                     POINTER(c_double), c_void_p]),
+    ("pfc_cnn_param_count", c_int, []),
+    ("pfc_cnn_workspace_size", c_int, [c_int64, c_int64, POINTER(c_size_t)]),
+    ("pfc_cnn_create", c_int, [c_int64, c_int64, c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
+    ("pfc_cnn_destroy", None, [c_void_p]),
+    ("pfc_cnn_set_params", c_int, [c_void_p, c_void_p]),
+    ("pfc_cnn_get_params", c_int, [c_void_p, c_void_p]),
+    ("pfc_cnn_forward", c_int, [c_void_p, c_void_p, c_void_p]),
+    ("pfc_cnn_loss_grad", c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p]),
+    ("pfc_cnn_train_step", c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_double)]),
+    ("pfc_cnn_sample", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_void_p,
+                               c_void_p]),
+    ("pfc_set_guess_net", c_int, [c_void_p, c_void_p, c_double]),
     ("pfc_status_str", c_char_p, [c_int]),
 ]
 
@@ -283,3 +296,83 @@ class Solver:
         _check(lib().pfc_precond_apply(self.handle, c_void_p(P.data_ptr()), c_void_p(N.data_ptr()), float(dt),
                                        c_void_p(R.data_ptr()), c_void_p(out.data_ptr())), "pfc_precond_apply")
         return out
+
+
+class GuessNet:
+    """The learned-initial-guess network on one grid (workspace owned by a torch tensor)."""
+
+    def __init__(self, shape: Sequence[int], stream=None, device: str = "cuda"):
+        import torch
+
+        self.torch = torch
+        self.shape = tuple(int(s) for s in shape)
+        assert len(self.shape) == 2
+        ny, nx = self.shape
+        self.n = nx * ny
+        size = c_size_t(0)
+        _check(lib().pfc_cnn_workspace_size(nx, ny, ctypes.byref(size)), "pfc_cnn_workspace_size")
+        self.device = torch.device(device)
+        self.ws = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = c_void_p()
+        _check(lib().pfc_cnn_create(nx, ny, c_void_p(self.ws.data_ptr()), c_size_t(self.ws.numel()),
+                                    c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "pfc_cnn_create")
+        self.handle = h
+
+    @staticmethod
+    def param_count() -> int:
+        return lib().pfc_cnn_param_count()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().pfc_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta: np.ndarray):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.param_count()
+        _check(lib().pfc_cnn_set_params(self.handle, a.ctypes.data_as(c_void_p)), "pfc_cnn_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().pfc_cnn_get_params(self.handle, a.ctypes.data_as(c_void_p)), "pfc_cnn_get_params")
+        return a
+
+    def forward(self, feat):
+        """feat: device float64 tensor (3, ny, nx); returns (ny, nx) float64."""
+        t = self.torch
+        out = t.empty(self.shape, dtype=t.float64, device=self.device)
+        _check(lib().pfc_cnn_forward(self.handle, c_void_p(feat.data_ptr()), c_void_p(out.data_ptr())),
+               "pfc_cnn_forward")
+        return out
+
+    def loss_grad(self, feat, target):
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = c_double()
+        _check(lib().pfc_cnn_loss_grad(self.handle, c_void_p(feat.data_ptr()), c_void_p(target.data_ptr()),
+                                       ctypes.byref(loss), g.ctypes.data_as(c_void_p)), "pfc_cnn_loss_grad")
+        return loss.value, g
+
+    def sample(self, phinm1, phin, phinp1, r: float, c2: float, s_out: float, feat, target):
+        """Fills feat (3, ny, nx) and target (ny, nx) device tensors from three consecutive fields."""
+        _check(lib().pfc_cnn_sample(self.handle, c_void_p(phinm1.data_ptr()), c_void_p(phin.data_ptr()),
+                                    c_void_p(phinp1.data_ptr()), float(r), float(c2), float(s_out),
+                                    c_void_p(feat.data_ptr()), c_void_p(target.data_ptr())), "pfc_cnn_sample")
+
+    def train_step(self, feat, target, lr: float, t: int, want_loss: bool = True) -> float:
+        loss = c_double(float("nan"))
+        _check(lib().pfc_cnn_train_step(self.handle, c_void_p(feat.data_ptr()), c_void_p(target.data_ptr()),
+                                        float(lr), int(t), ctypes.byref(loss) if want_loss else None),
+               "pfc_cnn_train_step")
+        return loss.value
+
+
+def set_guess_net(solver: "Solver", net: Optional[GuessNet], s_out: float):
+    _check(lib().pfc_set_guess_net(solver.handle, net.handle if net is not None else None, float(s_out)),
+           "pfc_set_guess_net")

@@ -1,0 +1,99 @@
+"""GPU parity of the learned-guess network kernels (BF16 weights and
+activations, FP32 accumulation) against the FP64 reference, and the learned
+guess inside the time step."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+from oracle import pfc_oracle as O
+from paper_1703_01202_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_01202_gb300 import build, pfc as P
+
+    build.build()
+    P.lib()
+    return P, torch
+
+
+def sample(shape, seed):
+    rng = np.random.default_rng(seed)
+    feat = np.stack([rng.normal(scale=0.3, size=shape), rng.normal(scale=0.05, size=shape), np.full(shape, 0.7)])
+    tgt = rng.normal(size=shape)
+    theta = C.init_params(seed)
+    theta[-(32 * 9 + 1):] = rng.normal(scale=0.1, size=32 * 9 + 1)
+    return feat, tgt, theta
+
+
+@pytest.mark.parametrize("shape", [(24, 20), (33, 17)])
+def test_forward_matches_fp64_reference(env, shape):
+    P, torch = env
+    feat, _, theta = sample(shape, 1)
+    net = P.GuessNet(shape)
+    net.set_params(theta)
+    out = net.forward(torch.from_numpy(feat).cuda()).cpu().numpy()
+    ref, _ = C.forward(theta.astype(np.float32).astype(np.float64), feat)
+    # BF16 storage of weights and activations: ~2^-9 relative per entry
+    assert np.linalg.norm(out - ref) <= 2e-2 * np.linalg.norm(ref)
+
+
+def test_gradient_matches_fp64_reference(env):
+    P, torch = env
+    shape = (32, 24)
+    feat, tgt, theta = sample(shape, 2)
+    net = P.GuessNet(shape)
+    net.set_params(theta)
+    loss, g = net.loss_grad(torch.from_numpy(feat).cuda(), torch.from_numpy(tgt).cuda())
+    rl, rg = C.loss_and_grad(theta.astype(np.float32).astype(np.float64), feat, tgt)
+    assert loss == pytest.approx(rl, rel=2e-2)
+    for li, (ci, co) in enumerate(C.LAYERS):  # per layer, the weight and bias gradients
+        lo = sum(c2 * c1 * 9 + c2 for c1, c2 in C.LAYERS[:li])
+        hi = lo + co * ci * 9 + co
+        assert np.linalg.norm(g[lo:hi] - rg[lo:hi]) <= 5e-2 * np.linalg.norm(rg[lo:hi]), li
+
+
+def test_adam_training_reduces_the_loss(env):
+    P, torch = env
+    shape = (32, 32)
+    feat, _, theta = sample(shape, 3)
+    # a target the network can represent: a smooth function of the inputs
+    tgt = np.tanh(3.0 * feat[0]) + 0.5 * feat[1] / 0.05
+    net = P.GuessNet(shape)
+    net.set_params(theta)
+    f, t = torch.from_numpy(feat).cuda(), torch.from_numpy(tgt).cuda()
+    losses = [net.train_step(f, t, 3e-3, i + 1) for i in range(60)]
+    assert losses[-1] < 0.5 * losses[0]
+
+
+def test_learned_guess_with_zero_network_is_the_extrapolation(env):
+    """All-zero parameters make the network output zero, so the learned guess
+    equals the extrapolated one and the step matches the extrapolation run."""
+    P, torch = env
+    shape = (48, 48)
+    h, gamma = math.pi / 4, 0.25
+    phi0 = inputs.hex_seeds_2d(shape, h, nseeds=1, radius_cells=8, seed=4)
+    prm = dict(sub=(3, 3), overlap=1, dt_min=0.01, dt_max=10.0, eta=5000.0)
+    a = P.Solver(shape, h, gamma, P.default_params(guess=P.PFC_GUESS_LEARNED, **prm))
+    b = P.Solver(shape, h, gamma, P.default_params(guess=P.PFC_GUESS_EXTRAP, **prm))
+    net = P.GuessNet(shape)
+    net.set_params(np.zeros(P.GuessNet.param_count(), dtype=np.float32))
+    P.set_guess_net(a, net, 0.01)
+    a.set_field(phi0)
+    b.set_field(phi0)
+    ia, ib = a.run(4), b.run(4)
+    # step 0 has no history (phi^n); afterwards the two guesses tie and the fallback keeps the extrapolation
+    assert [i["guess_used"] for i in ia] == [P.PFC_GUESS_PREV] + [P.PFC_GUESS_EXTRAP] * 3
+    np.testing.assert_allclose(a.get_field(), b.get_field(), rtol=0, atol=1e-10)
+    # the oracle's run with the extrapolated guess agrees too
+    ref, _ = O.run(phi0, h, gamma, O.Params(parts=(3, 3), overlap=1, dt_min=0.01, dt_max=10.0, eta=5000.0), 4,
+                   guess="extrap")
+    assert np.abs(a.get_field() - ref).max() <= 1e-8
