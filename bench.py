@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "hex1024"
+EXTRA_3D_STEPS = 2
 METRIC = "PFC time steps/s (1024^2 2D crystal growth, adaptive dt)"
 
 
@@ -162,7 +163,8 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
-def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, measure_e2e: bool):
+def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, measure_e2e: bool,
+                apply_variant: int = -1):
     import numpy as np
     import torch
 
@@ -170,10 +172,11 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
 
     w = inputs.workload(WORKLOAD)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"])
+                                dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
     s.set_field(w["phi"])
     s.run(warmup)
+    tuning = s.tuning()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -205,6 +208,7 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
         "apply_bytes": prof["apply_bytes"],
         "gpu_launches": prof["kernel_launches"] - k0,
         "clocks": ck,
+        "tuning": tuning,
     }
     if measure_e2e:
         # same metric through the C ABI with host buffers: every step copies phi^n in
@@ -230,6 +234,80 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
     return out
 
 
+def run_batch32(steps: int, warmup: int, prec: int = 2):
+    """The ensemble workload: 32 independent 256^2 noise runs (gamma_i drawn
+    U(0.1, 0.35)), each on its own stream, stepped together by pfc_run_batch.
+    Returns aggregate steps/s (all runs) and one run's steps/s alone."""
+    import torch
+
+    from paper_1703_01202_gb300 import inputs, pfc
+
+    w = inputs.workload("batch32x256")
+
+    def make(g, st):
+        params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
+                                    dt_max=w["dt_max"], eta=w["eta"])
+        return pfc.Solver(w["shape"], w["h"], g, params, stream=st)
+
+    solvers = [make(g, torch.cuda.Stream()) for g in w["gammas"]]
+    for s, phi in zip(solvers, w["phis"]):
+        s.set_field(phi)
+    pfc.run_batch(solvers, warmup)
+    torch.cuda.synchronize()
+    k0 = solvers[0].profile_read()["kernel_launches"]
+    t0 = time.perf_counter()
+    recs = pfc.run_batch(solvers, steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    launches = solvers[0].profile_read()["kernel_launches"] - k0
+    for s in solvers:
+        s.close()
+    one = make(w["gammas"][0], None)
+    one.set_field(w["phis"][0])
+    one.run(warmup)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    one.run(steps)
+    torch.cuda.synchronize()
+    el1 = time.perf_counter() - t1
+    one.close()
+    torch.cuda.empty_cache()
+    return {"runs": len(solvers), "steps_per_run": steps, "steps_per_s": len(solvers) * steps / el,
+            "single_run_steps_per_s": steps / el1, "gpu_launches": launches,
+            "newton_per_step": sum(r["newton_its"] for rr in recs for r in rr) / (len(recs) * steps),
+            "gmres_per_step": sum(r["gmres_its"] for rr in recs for r in rr) / (len(recs) * steps),
+            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
+
+
+def run_bcc256(steps: int, warmup: int, prec: int):
+    """The 3D workload: 256^3 BCC growth, 7 x 7 x 7 uneven cores, ILU(0) blocks."""
+    import torch
+
+    from paper_1703_01202_gb300 import inputs, pfc
+
+    w = inputs.workload("bcc256")
+    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
+                                dt_max=w["dt_max"], eta=w["eta"])
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
+    s.set_field(w["phi"])
+    s.run(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    infos = s.run(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"steps": steps, "steps_per_s": steps / (ms / 1e3),
+            "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
+            "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
+            "dt_last": infos[-1]["dt"], "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
+
+
 def kernel_loop(args):
     """Runs one kernel family `steps` times on the workload's initial field
     (each pfc_precond_apply factors and applies once), for ncu captures."""
@@ -240,7 +318,8 @@ def kernel_loop(args):
     build.build()
     w = inputs.workload(WORKLOAD)
     prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2}[args.variant]
-    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec)
+    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec,
+                                apply_variant=args.apply_variant)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
     phi = torch.from_numpy(w["phi"]).cuda()
     r = torch.from_numpy(inputs.noise_field(w["shape"], 0.0, 1.0, 7)).cuda()
@@ -256,7 +335,7 @@ def kernel_loop(args):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     print(json.dumps({"kernel_loop": args.kernel_loop, "variant": args.variant, "calls": args.steps,
-                      "ms_per_call": [round(1e3 * t, 3) for t in times]}))
+                      "ms_per_call": [round(1e3 * t, 3) for t in times], "tuning": s.tuning()}))
 
 
 def main():
@@ -268,6 +347,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16"],
                     help="run one factor-precision variant only (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
+    ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="2D Schwarz apply kernel (-1: autotuned at the first factorisation)")
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
                     help="profiling aid: run one kernel family repeatedly on the workload (no bench line)")
     args = ap.parse_args()
@@ -305,7 +388,8 @@ def main():
     for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
         if args.variant in ("all", name):
             variants[name] = run_variant(prec, args.steps, args.warmup, world, local,
-                                         measure_e2e=(name == "bf16" or args.variant != "all"))
+                                         measure_e2e=(name == "bf16" or args.variant != "all"),
+                                         apply_variant=args.apply_variant if prec else min(args.apply_variant, 0))
     head = variants["bf16" if "bf16" in variants else args.variant]
     peak, peak_kind = measured_peaks()
     achieved = head["apply_bytes"] / (head["apply_ms_avg"] * 1e-3) / 1e9
@@ -333,6 +417,14 @@ def main():
         "iterations": {"newton_per_step": head["newton_per_step"], "gmres_per_step": head["gmres_per_step"]},
         "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks", "e2e")} for k, v in variants.items()},
     }
+    if not args.no_extras:
+        # the other workloads of the metric, each on this rank's GPU: the 32-run 256^2 ensemble
+        # (pfc_run_batch) and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
+        line["workloads"] = {
+            "batch32x256_bf16": run_batch32(max(2, args.steps // 2), 2),
+            "bcc256_f32": run_bcc256(EXTRA_3D_STEPS, 1, 1),
+            "bcc256_bf16": run_bcc256(EXTRA_3D_STEPS, 1, 2),
+        }
     if rank == 0 and not args.no_cpu_baseline:
         r = oracle_sample(1, 1)
         line["cpu_baseline"] = {"value": r["steps"] / r["seconds"], "unit": "steps/s", "cores": 1, "kind": "oracle",

@@ -51,7 +51,10 @@ enum { PFC_F64 = 0, PFC_F32 = 1, PFC_BF16 = 2 };
 /* Schwarz variant (Sec. 4): Eq. invM, Eq. ras, Eq. ash. */
 enum { PFC_AS = 0, PFC_LEFT_RAS = 1, PFC_RIGHT_RAS = 2 };
 /* Newton initial guess: phi^n (Sec. 4), linear extrapolation, caller-supplied,
-   or the learned network (pfc_set_guess_net) with the extrapolation as fallback. */
+   or the learned network (pfc_set_guess_net).  EXTRAP and LEARNED are
+   safeguarded: the residual norm of every candidate (phi^n, the extrapolation,
+   and the network's guess for LEARNED) is evaluated and Newton starts from the
+   smallest; pfc_step_info.guess_used reports the pick. */
 enum { PFC_GUESS_PREV = 0, PFC_GUESS_EXTRAP = 1, PFC_GUESS_USER = 2, PFC_GUESS_LEARNED = 3 };
 
 typedef struct {
@@ -61,7 +64,9 @@ typedef struct {
 
 typedef struct {
   /* Newton stop test ||F(Phi_{m+1})|| <= max(newton_rtol ||F(Phi_0)||, newton_atol)
-     (Sec. 4, Newton stopping condition); 2-norms. */
+     (Sec. 4, Newton stopping condition); 2-norms.  With the EXTRAP / LEARNED
+     guesses ||F(Phi_0)|| is that of Phi_0 = phi^n, the paper's start, so the
+     tolerance does not depend on the guess. */
   double newton_rtol, newton_atol;
   int newton_max_it;
   /* GMRES stop test ||r_m|| <= max(gmres_rtol ||F(Phi_m)||, gmres_atol) (Sec. 4). */
@@ -80,6 +85,12 @@ typedef struct {
   /* Adaptive time step, Eq. (sencondt); energy_scaled = 1 feeds F_d/|Omega|. */
   double dt_min, dt_max, eta;
   int energy_scaled;
+  /* 2D Schwarz apply launch shape (steps per bulk copy x warps per CTA):
+     0 default, 1 half-length copies, 2 half-length copies and 2-warp CTAs,
+     3 double-length copies; -1 (default) times every shape on the first
+     factorisation and keeps the fastest (pfc_get_tuning reports the pick).
+     Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0. */
+  int apply_variant;
 } pfc_params;
 
 typedef struct {
@@ -92,7 +103,7 @@ typedef struct {
   double mass;       /* h^d sum phi^{n+1}                                      */
   double res_norm0;  /* ||F(Phi_0)||                                          */
   double res_norm;   /* ||F(phi^{n+1})||                                      */
-  int guess_used;    /* PFC_GUESS_* actually used for Phi_0 (learned may fall back) */
+  int guess_used;    /* PFC_GUESS_* actually used for Phi_0 (safeguard pick)   */
 } pfc_step_info;
 
 typedef struct pfc_cnn pfc_cnn;
@@ -135,6 +146,16 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info);
    Stops at the first failing step and returns its status. */
 int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step);
 
+/* Batched form (independent runs, e.g. an ensemble of small grids): runs
+   pfc_run(states[i], nsteps, ...) for every i concurrently, one host thread per
+   state, so that states created on distinct streams overlap on the GPU.  The
+   paper runs one problem at a time; this entry point has no counterpart there.
+   per_step: count x nsteps records (state i at per_step[i * nsteps + n]) or
+   NULL; status: count ints or NULL.  Returns PFC_OK when every run succeeded,
+   else the status of the lowest-numbered failing state.  No two entries may be
+   the same state. */
+int pfc_run_batch(pfc_state** states, int count, int nsteps, pfc_step_info* per_step, int* status);
+
 /* F_d(phi^n) (Eq. freeenergy) and h^d sum phi^n. */
 int pfc_energy(pfc_state* s, double* F);
 int pfc_mass(pfc_state* s, double* m);
@@ -175,6 +196,13 @@ int pfc_profile(pfc_state* s, int enable);
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches);
 
+/* Autotuner report (2D).  *apply_variant: the Schwarz apply kernel in use
+   (pfc_params.apply_variant numbering).  apply_ms (optional, 4 floats): the
+   mean device milliseconds of one apply measured per kernel at the first
+   factorisation, -1 for kernels not timed (not tuned yet, an explicit variant,
+   or one that cannot run the blocks).  Not part of the paper's method. */
+int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms);
+
 /* ---- Learned Newton initial guess (2D).  The paper starts Newton from phi^n
    (Sec. 4); the learned form adds a periodic 3x3 convolutional network
    (channels 3 -> 32 -> 32 -> 32 -> 1, GELU, BF16 weights and activations,
@@ -207,7 +235,8 @@ int pfc_cnn_sample(pfc_cnn* c, const double* phinm1, const double* phin, const d
                    double c2, double s_out, double* feat, double* target);
 /* Lets PFC_GUESS_LEARNED use network c (same grid as s; c stays owned by the
    caller and must outlive its use).  Each step compares the residual norms of
-   the learned and the extrapolated guess and starts Newton from the smaller. */
+   the learned guess, the extrapolated guess and phi^n and starts Newton from
+   the smallest. */
 int pfc_set_guess_net(pfc_state* s, pfc_cnn* c, double s_out);
 
 /* The 2D residual F(Phi) of pfc_residual, for callers that cannot allocate

@@ -492,7 +492,8 @@ class StepInfo:
 
 
 def newton_solve(
-    phin: np.ndarray, dt: float, h: float, gamma: float, p: Params, guess: Optional[np.ndarray] = None
+    phin: np.ndarray, dt: float, h: float, gamma: float, p: Params, guess: Optional[np.ndarray] = None,
+    ref_norm: Optional[float] = None,
 ) -> Tuple[np.ndarray, StepInfo]:
     """One time step: solve F(Phi) = 0 (Eq. NLS) by inexact Newton (Eq. newton)
     Phi_{m+1} = Phi_m + lambda_m S_m, with S_m from right-preconditioned GMRES
@@ -500,6 +501,8 @@ def newton_solve(
     ||F(Phi_{m+1})|| <= max(eps_r ||F(Phi_0)||, eps_a).  Initial guess: phi^n
     (Sec. 4) unless `guess` is given.  The Schwarz factors are built once per
     step at the first Newton iteration and reused (Sec. 5.2, factor reuse).
+    READING: with another initial guess the tolerance stays the plain method's,
+    eps_r ||F(phi^n)|| (`ref_norm`), so a better guess cannot tighten it.
 
     READINGS: 2-norms throughout; backtracking line search on f = ||F||^2/2 with
     the Armijo test f(Phi + lam S) <= (1 - 2 alpha lam) f(Phi) and quadratic
@@ -508,7 +511,7 @@ def newton_solve(
     Phi = (phin if guess is None else guess).copy()
     F = residual(Phi, phin, dt, h, gamma)
     r0 = float(np.linalg.norm(F))
-    target = max(p.newton_rtol * r0, p.newton_atol)
+    target = max(p.newton_rtol * (r0 if ref_norm is None else ref_norm), p.newton_atol)
     rnorm = r0
     m = 0
     gm_total = 0
@@ -603,8 +606,16 @@ def run(
             dt = adaptive_dt(E_n * scale, E_nm1 * scale, dt_prev, p)
         g = None
         if guess == "extrap" and dt_prev is not None:
+            # READING (safeguard): the extrapolation is used only when its residual norm
+            # is not larger than that of phi^n, the paper's own starting point (Sec. 4);
+            # after a step-size jump dt/dt_prev is large and the extrapolation poor.
             g = extrapolated_guess(phin, phinm1, dt, dt_prev)
-        phi1, info = newton_solve(phin, dt, h, gamma, p, g)
+            ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma)))
+            if ref < np.linalg.norm(residual(g, phin, dt, h, gamma)):
+                g = None
+            phi1, info = newton_solve(phin, dt, h, gamma, p, g, ref_norm=ref)
+        else:
+            phi1, info = newton_solve(phin, dt, h, gamma, p, g)
         if not info.converged:
             raise RuntimeError(f"Newton did not converge at step {n}")
         phinm1, phin = phin, phi1

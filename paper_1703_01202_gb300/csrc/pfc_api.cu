@@ -11,10 +11,12 @@
 // decisions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -68,6 +70,12 @@ struct pfc_state {
   long long apply_launches;
   double apply_ms;
   double apply_bytes;
+  // apply kernel picked by timing at the first 2D factorisation (apply_variant = -1)
+  bool tuned;
+  float tune_ms[pfc::kApplyVariants];
+  // ||F(phi^n)|| of the current step when a safeguarded guess was chosen (< 0: none)
+  double ref_norm;
+  int device;  // CUDA device current at pfc_create
 };
 
 namespace pfc {
@@ -124,6 +132,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->newton_max_it < 0 || p->gmres_max_it < 1 || p->overlap < 0) return PFC_EINVAL;
   if (p->ras_kind != PFC_LEFT_RAS) return PFC_EINVAL;
   if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
+  if (p->apply_variant < -1 || p->apply_variant >= pfc::kApplyVariants) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -426,11 +435,59 @@ void precond(pfc_state* s, const double* r, const double* rscale, double* z, con
     pfc::launch_ras_apply3d(s->g, s->blocks_dev, s->nblocks, s->r3, r, rscale, z, skip, s->status_dev + 1, s->st);
 }
 
+// Times every apply kernel that can run the blocks on the factors just made
+// (r = F, z = W: both free at this point) and keeps the fastest.
+int tune_apply(pfc_state* s) {
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  int rc = PFC_OK;
+  for (int v = 0; v < pfc::kApplyVariants && rc == PFC_OK; ++v) {
+    s->tune_ms[v] = -1.f;
+    if (!pfc::apply_variant_ok(v, s->fs.prec, s->fs.kl_max)) continue;
+    s->fs.variant = v;
+    precond(s, s->F, nullptr, s->W, nullptr);  // warm-up
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s->st);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      precond(s, s->F, nullptr, s->W, nullptr);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      fprintf(stderr, "libpfc: timing apply kernel %d failed: %s\n", v, cudaGetErrorString(e));
+      rc = PFC_ECUDA;
+      break;
+    }
+    s->tune_ms[v] = ms / 3.f;
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PFC_OK) return rc;
+  if (best < 0) return PFC_EINVAL;
+  s->fs.variant = best;
+  s->tuned = true;
+  return PFC_OK;
+}
+
 int factor_blocks(pfc_state* s, const double* q, double idt) {
   if (s->dim == 2) {
-    // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx): blocks at most 42 cells wide in x
+    // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx: blocks at most 42 cells
+    // wide in x); blocks wider than 21 cells run the wide-window apply kernel in its default shape
     if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
       return PFC_EINVAL;
+    if (s->p.apply_variant >= 0 && !pfc::apply_variant_ok(s->p.apply_variant, s->fs.prec, s->fs.kl_max))
+      return PFC_EINVAL;
+    if (s->p.apply_variant < 0 && !pfc::apply_variant_ok(0, s->fs.prec, s->fs.kl_max)) return PFC_EINVAL;
   }
   CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
   if (s->dim == 2)
@@ -438,6 +495,7 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
   else
     pfc::launch_factor3d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->r3, s->status_dev, s->st);
   CU(cudaGetLastError());
+  if (s->dim == 2 && s->p.apply_variant < 0 && !s->tuned) return tune_apply(s);
   return PFC_OK;
 }
 
@@ -533,7 +591,8 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
   if ((rc = sync_read(s, s->red_h, s->red, sizeof(double)))) return rc;
   const double r0 = std::sqrt(s->red_h[0]);
   if (!(r0 == r0) || std::isinf(r0)) return PFC_ENAN;
-  const double target = std::max(p.newton_rtol * r0, p.newton_atol);
+  // the plain method's tolerance (relative to ||F(phi^n)||) also for other initial guesses
+  const double target = std::max(p.newton_rtol * (s->ref_norm >= 0.0 ? s->ref_norm : r0), p.newton_atol);
   double rnorm = r0;
   info->res_norm0 = r0;
   int m = 0, gm_total = 0, cuts_total = 0;
@@ -583,32 +642,42 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
 
 int energy_mass(pfc_state* s, const double* phi, double* E, double* M);
 
-// Learned guess with fallback: Phi_L = phi^n + c1 + s_out net(c) (mass of phi^n)
-// against Phi_E = phi^n + c1 (the extrapolation); Newton starts from the one with
-// the smaller residual norm.  Leaves the choice in s->Phi.
-int learned_guess(pfc_state* s, double dt, int* used) {
+// Safeguarded initial guess.  Candidates: phi^n (the paper's start, Sec. 4), the
+// extrapolation Phi_E = phi^n + c1, c1 = (dt / dt_prev)(phi^n - phi^{n-1}), and in
+// the learned form Phi_L = phi^n + c1 + s_out net(c) shifted to the mass of phi^n.
+// Newton starts from the candidate with the smallest ||F|| (ties keep Phi_E, then
+// phi^n): a step-size jump makes c1 large, and the extrapolation can then be far
+// worse than phi^n.  Leaves the choice in s->Phi.
+int safeguarded_guess(pfc_state* s, double dt, bool learned, int* used) {
   const long long N = s->g.n;
-  int rc = energy_mass(s, s->phin, nullptr, nullptr);  // red[5] = sum phi^n
-  if (rc) return rc;
-  pfc::launch_cnn_features(N, s->phin, s->phinm1, s->red + 5, dt / s->dt_prev, dt / s->p.dt_max, s->feat, s->st);
-  pfc::Cnn* c = reinterpret_cast<pfc::Cnn*>(s->cnn);
-  pfc::cnn_forward(c, s->feat);
-  int np = 0;
-  pfc::launch_cnn_delta(N, s->feat, pfc::cnn_output(c), s->s_out, s->W, s->partial, &np, s->st);
-  pfc::launch_reduce(s->partial, 1, np, s->red + 11, s->st);
-  pfc::launch_add_centered(N, s->phin, s->W, s->red + 11, s->Pt, s->st);  // learned
-  pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, N, s->st);  // extrapolated
   const double idt = 1.0 / dt;
-  if ((rc = eval_residual(s, s->Pt, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 2))) return rc;
-  if ((rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 3))) return rc;
-  if ((rc = sync_read(s, s->red_h + 2, s->red + 2, 2 * sizeof(double)))) return rc;
-  const double rl = s->red_h[2], re = s->red_h[3];
-  if (rl == rl && rl < re) {
-    std::swap(s->Phi, s->Pt);
-    *used = PFC_GUESS_LEARNED;
-  } else {
-    *used = PFC_GUESS_EXTRAP;
+  int rc = PFC_OK;
+  if (learned) {
+    if ((rc = energy_mass(s, s->phin, nullptr, nullptr))) return rc;  // red[5] = sum phi^n
+    pfc::launch_cnn_features(N, s->phin, s->phinm1, s->red + 5, dt / s->dt_prev, dt / s->p.dt_max, s->feat, s->st);
+    pfc::Cnn* c = reinterpret_cast<pfc::Cnn*>(s->cnn);
+    pfc::cnn_forward(c, s->feat);
+    int np = 0;
+    pfc::launch_cnn_delta(N, s->feat, pfc::cnn_output(c), s->s_out, s->W, s->partial, &np, s->st);
+    pfc::launch_reduce(s->partial, 1, np, s->red + 11, s->st);
+    pfc::launch_add_centered(N, s->phin, s->W, s->red + 11, s->Pt, s->st);  // Phi_L
+    if ((rc = eval_residual(s, s->Pt, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 2))) return rc;
   }
+  pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, N, s->st);  // Phi_E
+  if ((rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 3))) return rc;
+  if ((rc = eval_residual(s, s->phin, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 6))) return rc;
+  if ((rc = sync_read(s, s->red_h + 2, s->red + 2, 5 * sizeof(double)))) return rc;
+  const double rl = learned ? s->red_h[2] : NAN, re = s->red_h[3], rp = s->red_h[6];
+  s->ref_norm = std::sqrt(rp);
+  double best = re;
+  *used = PFC_GUESS_EXTRAP;
+  if (rp < best) {
+    best = rp;
+    *used = PFC_GUESS_PREV;
+  }
+  if (rl == rl && rl < best) *used = PFC_GUESS_LEARNED;
+  if (*used == PFC_GUESS_LEARNED) std::swap(s->Phi, s->Pt);
+  if (*used == PFC_GUESS_PREV) CU(cudaMemcpyAsync(s->Phi, s->phin, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
   return PFC_OK;
 }
 
@@ -653,6 +722,7 @@ int pfc_default_params(pfc_params* p) {
   p->dt_max = 10.0;
   p->eta = 5000.0;
   p->energy_scaled = 1;
+  p->apply_variant = -1;
   return PFC_OK;
 }
 
@@ -715,6 +785,14 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.prec = p->factor_prec;
   s->fs.kl_max = pl.kl_max;
   s->fs.n_max = pl.n_max;
+  s->fs.variant = p->apply_variant >= 0 ? p->apply_variant : 0;
+  s->tuned = false;
+  s->ref_norm = -1.0;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    pfc_destroy(s);
+    return PFC_ECUDA;
+  }
+  for (int v = 0; v < pfc::kApplyVariants; ++v) s->tune_ms[v] = -1.f;
   s->nblocks = pl.nblocks;
   s->blocks_dev = (BlockDesc*)at(pl.blocks);
   s->lin_dev = (double*)at(pl.lin);
@@ -816,6 +894,14 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   return PFC_OK;
 }
 
+int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms) {
+  if (!s || !apply_variant) return PFC_EINVAL;
+  *apply_variant = s->fs.variant;
+  if (apply_ms)
+    for (int v = 0; v < pfc::kApplyVariants; ++v) apply_ms[v] = s->tune_ms[v];
+  return PFC_OK;
+}
+
 void pfc_destroy(pfc_state* s) {
   if (!s) return;
   pfc_profile(s, 0);
@@ -859,11 +945,9 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
   // initial guess Phi_0
   int rc = PFC_OK;
   info.guess_used = PFC_GUESS_PREV;
-  if (s->p.guess == PFC_GUESS_LEARNED && s->have_prev_dt && s->cnn) {
-    if ((rc = learned_guess(s, dt, &info.guess_used))) return rc;
-  } else if ((s->p.guess == PFC_GUESS_EXTRAP || s->p.guess == PFC_GUESS_LEARNED) && s->have_prev_dt) {
-    pfc::launch_extrapolate(s->Phi, s->phin, s->phinm1, dt / s->dt_prev, s->g.n, s->st);
-    info.guess_used = PFC_GUESS_EXTRAP;
+  s->ref_norm = -1.0;
+  if ((s->p.guess == PFC_GUESS_EXTRAP || s->p.guess == PFC_GUESS_LEARNED) && s->have_prev_dt) {
+    if ((rc = safeguarded_guess(s, dt, s->p.guess == PFC_GUESS_LEARNED && s->cnn, &info.guess_used))) return rc;
   } else if (s->p.guess == PFC_GUESS_USER && s->have_user_guess) {
     CU(cudaMemcpyAsync(s->Phi, s->guess, b, cudaMemcpyDeviceToDevice, s->st));
     info.guess_used = PFC_GUESS_USER;
@@ -972,6 +1056,30 @@ int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step) {
     if (rc) return rc;
   }
   return PFC_OK;
+}
+
+int pfc_run_batch(pfc_state** states, int count, int nsteps, pfc_step_info* per_step, int* status) {
+  if (!states || count < 1 || nsteps < 0) return PFC_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!states[i]) return PFC_EINVAL;
+  std::vector<int> rc(count, PFC_OK);
+  std::vector<std::thread> pool;
+  pool.reserve(count);
+  for (int i = 0; i < count; ++i)
+    pool.emplace_back([&, i]() {
+      if (cudaSetDevice(states[i]->device) != cudaSuccess) {
+        rc[i] = PFC_ECUDA;
+        return;
+      }
+      rc[i] = pfc_run(states[i], nsteps, per_step ? per_step + (size_t)i * nsteps : nullptr);
+    });
+  for (std::thread& t : pool) t.join();
+  int first = PFC_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = rc[i];
+    if (first == PFC_OK) first = rc[i];
+  }
+  return first;
 }
 
 int pfc_energy(pfc_state* s, double* F) {

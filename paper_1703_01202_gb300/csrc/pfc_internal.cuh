@@ -82,12 +82,16 @@ struct FactorStore {
   int prec;                          // PFC_F64 / PFC_F32 / PFC_BF16
   int kl_max;
   int n_max;
+  int variant;       // apply launch shape, 0 .. kApplyVariants - 1
 };
+constexpr int kApplyVariants = 4;
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
 size_t factor_smem_bytes(int prec, int kl, int n_max);
+// Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec.
+bool apply_variant_ok(int v, int prec, int kl_max);
 
 // ---- 3D stencils (stencil3d.cu)
 void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, const double* ssum, double* Pout,

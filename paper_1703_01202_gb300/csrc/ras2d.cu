@@ -263,7 +263,7 @@ __host__ __device__ inline ApplySmem apply_smem(int lrow, int ucol, int nmax) {
   return s;
 }
 
-template <typename TC, typename TS, int CH, int WPC>
+template <typename TC, typename TS, int CH, int WPC, int NW>
 __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc* __restrict__ blocks, int nblocks,
                                                           FactorStore fs, const double* __restrict__ r,
                                                           const double* __restrict__ rscale, double* __restrict__ z,
@@ -315,17 +315,19 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   __syncwarp();
   // The active window of each triangular solve lives in registers: lane l holds
   // the entries congruent to l mod 32, one register per 32-entry block.  Forward
-  // window [k, k+kl] (kl <= 63): blocks mf..mf+2 in w0..w2, mf = k / 32.
-  // Backward window [k-ku2, k] (ku2 <= 127): blocks mb..mb-4 in v0..v4, mb = k / 32.
-  // The registers rotate when k crosses a block boundary; the pivot and x_k
-  // values reach every lane by warp shuffles, so no step needs a shared-memory
-  // round trip or a warp barrier.
+  // window [k, k+kl] (kl <= 32 (NW - 1)): blocks mf..mf+NW-1 in wf[], mf = k / 32.
+  // Backward window [k-ku2, k] (ku2 <= 32 (NB - 1)): blocks mb..mb-NB+1 in wb[],
+  // mb = k / 32.  The registers rotate when k crosses a block boundary; the pivot
+  // and x_k values reach every lane by warp shuffles, so no step needs a
+  // shared-memory round trip or a warp barrier.
+  constexpr int NB = 2 * NW - 1;
   const unsigned FULL = 0xffffffffu;
   int mf = 0, mb = 0;
-  TC w0 = lane < n ? buf[lane] : (TC)0;
-  TC w1 = lane + 32 < n ? buf[lane + 32] : (TC)0;
-  TC w2 = lane + 64 < n ? buf[lane + 64] : (TC)0;
-  TC v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0;
+  TC wf[NW], wb[NB];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) wf[q] = lane + 32 * q < n ? buf[lane + 32 * q] : (TC)0;
+#pragma unroll
+  for (int q = 0; q < NB; ++q) wb[q] = (TC)0;
   uint32_t phase0 = 0, phase1 = 0;
   for (int t = 0; t < total; ++t) {
     const int st = t & 1;
@@ -346,66 +348,58 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
         const int k = c * CH + kk;
         if ((k >> 5) != mf) {  // entered block mf + 1
           ++mf;
-          w0 = w1;
-          w1 = w2;
-          const int tn = 32 * (mf + 2) + lane;
-          w2 = tn < n ? buf[tn] : (TC)0;
+#pragma unroll
+          for (int q = 0; q < NW - 1; ++q) wf[q] = wf[q + 1];
+          const int tn = 32 * (mf + NW - 1) + lane;
+          wf[NW - 1] = tn < n ? buf[tn] : (TC)0;
         }
         const TS* lk = data + kk * lrow;
         const int p = k + pv[k];
         const int dp = (p >> 5) - mf;
-        const TC bk = __shfl_sync(FULL, w0, k & 31);
-        const TC bp = __shfl_sync(FULL, dp == 0 ? w0 : (dp == 1 ? w1 : w2), p & 31);
+        const TC bk = __shfl_sync(FULL, wf[0], k & 31);
+        TC src = wf[0];
+#pragma unroll
+        for (int q = 1; q < NW; ++q)
+          if (dp == q) src = wf[q];
+        const TC bp = __shfl_sync(FULL, src, p & 31);
         if (lane == (k & 31)) buf[k] = bp;  // y_k
         const int last = min(k + kl, n - 1);
-        int tt = 32 * mf + lane;
-        if (tt > k && tt <= last) w0 = ((tt == p) ? bk : w0) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
-        tt += 32;
-        if (tt > k && tt <= last) w1 = ((tt == p) ? bk : w1) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
-        tt += 32;
-        if (tt <= last) w2 = ((tt == p) ? bk : w2) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {  // rows of blocks mf+1.. lie below k by construction
+          const int tt = 32 * (mf + q) + lane;
+          if ((q > 0 || tt > k) && tt <= last)
+            wf[q] = ((tt == p) ? bk : wf[q]) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
+        }
       }
     } else {  // backward, column oriented: x_k = y_k / u_kk, y_{k-j} -= u_{k-j,k} x_k
       if (t == nc) {  // y complete: load the top of the backward window
         __syncwarp();
         mb = (n - 1) >> 5;
-        int tb = 32 * mb + lane;
-        v0 = (tb < n) ? buf[tb] : (TC)0;
-        tb -= 32;
-        v1 = (tb >= 0) ? buf[tb] : (TC)0;
-        tb -= 32;
-        v2 = (tb >= 0) ? buf[tb] : (TC)0;
-        tb -= 32;
-        v3 = (tb >= 0) ? buf[tb] : (TC)0;
-        tb -= 32;
-        v4 = (tb >= 0) ? buf[tb] : (TC)0;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int tb = 32 * (mb - q) + lane;
+          wb[q] = (tb >= 0 && tb < n) ? buf[tb] : (TC)0;
+        }
       }
       const int c = 2 * nc - 1 - t, rows = min(CH, n - c * CH);
       for (int kk = rows - 1; kk >= 0; --kk) {
         const int k = c * CH + kk;
         if ((k >> 5) != mb) {  // entered block mb - 1
           --mb;
-          v0 = v1;
-          v1 = v2;
-          v2 = v3;
-          v3 = v4;
-          const int tn = 32 * (mb - 4) + lane;
-          v4 = tn >= 0 ? buf[tn] : (TC)0;
+#pragma unroll
+          for (int q = 0; q < NB - 1; ++q) wb[q] = wb[q + 1];
+          const int tn = 32 * (mb - NB + 1) + lane;
+          wb[NB - 1] = tn >= 0 ? buf[tn] : (TC)0;
         }
         const TS* uk = data + kk * ucol;
-        const TC xk = __shfl_sync(FULL, v0, k & 31) * from_store<TC, TS>(uk[0]);
+        const TC xk = __shfl_sync(FULL, wb[0], k & 31) * from_store<TC, TS>(uk[0]);
         if (lane == (k & 31)) buf[k] = xk;
         const int lo = max(0, k - ku2);
-        int tt = 32 * mb + lane;
-        if (tt < k && tt >= lo) v0 -= from_store<TC, TS>(uk[k - tt]) * xk;
-        tt -= 32;
-        if (tt >= lo) v1 -= from_store<TC, TS>(uk[k - tt]) * xk;
-        tt -= 32;
-        if (tt >= lo) v2 -= from_store<TC, TS>(uk[k - tt]) * xk;
-        tt -= 32;
-        if (tt >= lo) v3 -= from_store<TC, TS>(uk[k - tt]) * xk;
-        tt -= 32;
-        if (tt >= lo) v4 -= from_store<TC, TS>(uk[k - tt]) * xk;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {  // rows of blocks mb-1.. lie above k by construction
+          const int tt = 32 * (mb - q) + lane;
+          if ((q > 0 || tt < k) && tt >= lo) wb[q] -= from_store<TC, TS>(uk[k - tt]) * xk;
+        }
       }
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
@@ -434,19 +428,24 @@ void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const d
   count_launches(1);
 }
 
-template <typename TC, typename TS, int CH>
+template <typename TC, typename TS, int CH, int WPC, int NW = 3>
 void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                     const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
-  constexpr int WPC = 4;
   const ApplySmem lay = apply_smem<TC, TS, CH>(fs.lrow, fs.ucol, fs.n_max);
   const size_t smem = WPC * lay.total;
-  cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ras_apply2d<TC, TS, CH, WPC><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale,
+  cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ras_apply2d<TC, TS, CH, WPC, NW><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale,
                                                                                     z, skip, err);
   count_launches(1);
 }
 
 }  // namespace
+
+bool apply_variant_ok(int v, int prec, int kl_max) {
+  (void)prec;
+  if (kl_max <= 64) return v >= 0 && v < kApplyVariants;  // 3 + 5 window registers per lane
+  return v == 0 && kl_max <= 128;                          // 5 + 9 window registers, default shape
+}
 
 // Dynamic shared memory of the factor kernel: q on the block and the stencil
 // table (FP64), the (kl+1) x RING window plus the multiplier and U-row
@@ -469,13 +468,40 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
-  // chunk length chosen so one stage is about 3.5 KB for every storage type
-  if (fs.prec == PFC_F64)
-    apply_dispatch<double, double, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
-  else if (fs.prec == PFC_F32)
-    apply_dispatch<float, float, 8>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
-  else
-    apply_dispatch<float, __nv_bfloat16, 16>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+  // Launch shapes (chunk length CH = steps per bulk copy, WPC = warps per CTA):
+  // variant 0: stages of about 3.5 KB for every storage type, 4 warps per CTA;
+  // 1: half the chunk (twice the resident warps per SM), 2: half the chunk and
+  // 2 warps per CTA (finer packing), 3: twice the chunk (fewer, larger copies).
+  if (fs.kl_max > 64) {  // blocks wider than 21 cells: the wide-window kernel, default shape
+    if (fs.prec == PFC_F64)
+      apply_dispatch<double, double, 4, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+    else if (fs.prec == PFC_F32)
+      apply_dispatch<float, float, 8, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+    else
+      apply_dispatch<float, __nv_bfloat16, 16, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+  } else if (fs.prec == PFC_F64) {
+    switch (fs.variant) {
+      case 1: apply_dispatch<double, double, 2, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 2: apply_dispatch<double, double, 2, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 3: apply_dispatch<double, double, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      default: apply_dispatch<double, double, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+    }
+  } else if (fs.prec == PFC_F32) {
+    switch (fs.variant) {
+      case 1: apply_dispatch<float, float, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 2: apply_dispatch<float, float, 4, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 3: apply_dispatch<float, float, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      default: apply_dispatch<float, float, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+    }
+  } else {
+    using B16 = __nv_bfloat16;
+    switch (fs.variant) {
+      case 1: apply_dispatch<float, B16, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 2: apply_dispatch<float, B16, 8, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      case 3: apply_dispatch<float, B16, 32, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
+      default: apply_dispatch<float, B16, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+    }
+  }
 }
 
 }  // namespace pfc

@@ -102,16 +102,16 @@ def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
 
 
 def evaluate(theta: np.ndarray, s_out: float, shape=(1024, 1024), steps: int = 12, warmup: int = 3,
-             seed: int = 1001, factor_prec: int = pfc.PFC_BF16) -> Dict:
-    """Newton / GMRES iterations and time per step with the extrapolated guess
-    and with the learned guess (fallback included) on a hexagonal-seed field."""
+             seed: int = 1001, factor_prec: int = pfc.PFC_BF16, modes=("prev", "extrap", "learned")) -> Dict:
+    """Newton / GMRES iterations and time per step with phi^n, the extrapolated
+    guess and the learned guess (safeguards included) on a hexagonal-seed field."""
     import torch
 
     ny, nx = shape
     out = {}
     phi0 = inputs.hex_seeds_2d(shape, H, seed=seed)
-    for mode in ("extrap", "learned"):
-        guess = pfc.PFC_GUESS_EXTRAP if mode == "extrap" else pfc.PFC_GUESS_LEARNED
+    for mode in modes:
+        guess = {"prev": pfc.PFC_GUESS_PREV, "extrap": pfc.PFC_GUESS_EXTRAP, "learned": pfc.PFC_GUESS_LEARNED}[mode]
         params = pfc.default_params(sub=(nx // 16, ny // 16), overlap=1, factor_prec=factor_prec, guess=guess,
                                     dt_min=DT_MIN, dt_max=DT_MAX, eta=ETA)
         s = pfc.Solver(shape, H, GAMMA, params)
@@ -129,7 +129,8 @@ def evaluate(theta: np.ndarray, s_out: float, shape=(1024, 1024), steps: int = 1
         el = time.perf_counter() - t0
         out[mode] = {"steps_per_s": steps / el, "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
                      "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
-                     "learned_used": sum(1 for i in infos if i["guess_used"] == pfc.PFC_GUESS_LEARNED),
+                     "guess_used": [i["guess_used"] for i in infos],
+                     "newton_its": [i["newton_its"] for i in infos], "dt": [i["dt"] for i in infos],
                      "energy_last": infos[-1]["energy"], "field": s.get_field()}
         s.close()
         if net is not None:

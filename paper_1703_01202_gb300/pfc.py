@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_longlong, c_size_t, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int64, c_longlong, c_size_t, c_void_p
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -35,6 +35,7 @@ class pfc_params(ctypes.Structure):
         ("sub", c_int * 3), ("overlap", c_int), ("ras_kind", c_int), ("factor_prec", c_int), ("guess", c_int),
         ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
+        ("apply_variant", c_int),
     ]
 
 
@@ -75,6 +76,8 @@ _SIGNATURES = [
     ("pfc_next_dt", c_int, [c_void_p, POINTER(c_double)]),
     ("pfc_step_host", c_int, [c_void_p, c_void_p, c_double, c_void_p, POINTER(pfc_step_info)]),
     ("pfc_profile", c_int, [c_void_p, c_int]),
+    ("pfc_run_batch", c_int, [POINTER(c_void_p), c_int, c_int, c_void_p, POINTER(c_int)]),
+    ("pfc_get_tuning", c_int, [c_void_p, POINTER(c_int), POINTER(c_float)]),
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
                                  POINTER(c_longlong)]),
     ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
@@ -134,6 +137,19 @@ def default_params(**over) -> pfc_params:
         else:
             setattr(p, k, v)
     return p
+
+
+def run_batch(solvers: Sequence["Solver"], nsteps: int) -> List[List[dict]]:
+    """pfc_run_batch over independent solvers (create each on its own stream so
+    their kernels overlap); returns the per-step records of every solver."""
+    n = len(solvers)
+    handles = (c_void_p * n)(*[s.handle.value for s in solvers])
+    infos = (pfc_step_info * max(n * nsteps, 1))()
+    status = (c_int * n)()
+    st = lib().pfc_run_batch(handles, n, int(nsteps), ctypes.cast(infos, c_void_p), status)
+    out = [[infos[i * nsteps + k].as_dict() for k in range(nsteps)] for i in range(n)]
+    _check(st, "pfc_run_batch")
+    return out
 
 
 def make_grid(shape: Sequence[int]) -> pfc_grid:
@@ -270,6 +286,12 @@ class Solver:
         _check(lib().pfc_profile_read(self.handle, ctypes.byref(a), ctypes.byref(ms), ctypes.byref(b),
                                       ctypes.byref(k)), "pfc_profile_read")
         return {"apply_launches": a.value, "apply_ms": ms.value, "apply_bytes": b.value, "kernel_launches": k.value}
+
+    def tuning(self) -> dict:
+        v = c_int()
+        ms = (c_float * 4)()
+        _check(lib().pfc_get_tuning(self.handle, ctypes.byref(v), ms), "pfc_get_tuning")
+        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(4)]}
 
     # -- test hooks on device tensors
     def residual(self, Phi, phin, dt: float):

@@ -90,8 +90,10 @@ def test_learned_guess_with_zero_network_is_the_extrapolation(env):
     a.set_field(phi0)
     b.set_field(phi0)
     ia, ib = a.run(4), b.run(4)
-    # step 0 has no history (phi^n); afterwards the two guesses tie and the fallback keeps the extrapolation
-    assert [i["guess_used"] for i in ia] == [P.PFC_GUESS_PREV] + [P.PFC_GUESS_EXTRAP] * 3
+    # step 0 has no history (phi^n); afterwards the learned and extrapolated guesses tie,
+    # the tie keeps the extrapolation, and the safeguard picks as in the extrapolation run
+    ga, gb = [i["guess_used"] for i in ia], [i["guess_used"] for i in ib]
+    assert ga[0] == P.PFC_GUESS_PREV and ga == gb and P.PFC_GUESS_LEARNED not in ga
     np.testing.assert_allclose(a.get_field(), b.get_field(), rtol=0, atol=1e-10)
     # the oracle's run with the extrapolated guess agrees too
     ref, _ = O.run(phi0, h, gamma, O.Params(parts=(3, 3), overlap=1, dt_min=0.01, dt_max=10.0, eta=5000.0), 4,

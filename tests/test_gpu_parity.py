@@ -88,6 +88,64 @@ def test_precond_apply_matches_oracle(pfc, shape, parts, dt, prec, tol):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape,parts,dt", [((50, 37), (3, 2), 10.0), ((96, 80), (5, 6), 1.0)])
+def test_apply_launch_shapes_agree(pfc, shape, parts, dt, prec):
+    """Every apply launch shape (chunk length, warps per CTA) runs the same
+    eliminations in the same order: identical results on ragged decompositions."""
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    z = {}
+    for v in (0, 1, 2, 3):
+        s = solver(pfc, shape, parts, prec=prec, overlap=1, apply_variant=v)
+        z[v] = s.precond_apply(Phi, phin, dt, r).cpu().numpy()
+        assert s.tuning()["apply_variant"] == v
+    for v in (1, 2, 3):
+        np.testing.assert_array_equal(z[v], z[0])
+
+
+def test_apply_autotuner_picks_a_timed_kernel(pfc):
+    """apply_variant = -1 times every kernel that fits at the first factorisation
+    and keeps the fastest; the step result does not depend on the pick."""
+    w = inputs.workload("noise64")
+    out = {}
+    for v in (-1, 0):
+        s = solver(pfc, w["shape"], w["parts"], prec=2, overlap=1, apply_variant=v)
+        s.set_field(w["phi"])
+        for _ in range(2):
+            s.step(w["fixed_dt"])
+        out[v] = s.get_field()
+        t = s.tuning()
+        if v == -1:
+            assert t["apply_variant"] in (0, 1, 2, 3)
+            assert all(ms > 0 for ms in t["apply_ms"])
+            assert t["apply_ms"][t["apply_variant"]] == min(t["apply_ms"])
+        else:
+            assert t["apply_ms"] == [-1.0] * 4
+    assert np.abs(out[-1] - out[0]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+def test_wide_blocks_use_the_wide_window_kernel(pfc, prec, tol):
+    """24-cell-wide blocks (kl = 72 > 64) run the wide-window apply kernel: same
+    oracle parity; launch shapes other than the default are refused."""
+    shape = (44, 44)
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, (2, 2), prec=prec, overlap=1)
+    z = s.precond_apply(Phi, phin, 1.0, r).cpu().numpy()
+    assert s.tuning()["apply_variant"] == 0
+    J = O.assemble_jacobian(Phi, phin, 1.0, H, GAMMA)
+    ref = O.Schwarz(J, O.decompose(shape, (2, 2), 1), "left-ras", "lu").apply(r)
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= tol
+    s2 = solver(pfc, shape, (2, 2), prec=prec, overlap=1, apply_variant=1)
+    with pytest.raises(pfc.PfcError) as e:
+        s2.precond_apply(Phi, phin, 1.0, r)
+    assert e.value.status == pfc.PFC_EINVAL
+
+
 def test_twenty_steps_noise64_match_oracle(pfc):
     """64^2 liquid from noise, fixed dt = 0.1, 20 steps, left-RAS 4x4 cores of 16^2 with
     one overlap cell per side (18^2 blocks): phi and energy per step against the oracle."""

@@ -408,3 +408,16 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     fd = (O.residual(Phi + eps * v, phin, 0.7, h, GAMMA) - O.residual(Phi - eps * v, phin, 0.7, h, GAMMA)) / (2 * eps)
     assert np.linalg.norm(Jv - fd) > 1e-4 * np.linalg.norm(Jv)
     monkeypatch.setattr(O, "jac_coeff", orig_q)
+
+
+def test_safeguarded_extrapolation_reaches_the_plain_solution():
+    """With the extrapolated (safeguarded) guess the Newton tolerance stays the
+    plain method's, eps_r ||F(phi^n)||: both runs reach the same discrete
+    solution within that tolerance, and the guess never costs iterations here."""
+    h, gamma = math.pi / 4, 0.25
+    phi0 = inputs.noise_field((24, 24), 0.07, 0.07, 31)
+    p = O.Params(parts=(2, 2), overlap=1)
+    a, ra = O.run(phi0, h, gamma, p, 4, fixed_dt=0.5, guess="prev")
+    b, rb = O.run(phi0, h, gamma, p, 4, fixed_dt=0.5, guess="extrap")
+    assert np.abs(a - b).max() <= 1e-9
+    assert sum(r.newton_its for r in rb) <= sum(r.newton_its for r in ra)
