@@ -164,16 +164,24 @@ def max_over_ranks(world, x: float) -> float:
 
 
 def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, measure_e2e: bool,
-                apply_variant: int = -1):
+                apply_variant: int = -1, learned: bool = False):
     import numpy as np
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
+    from paper_1703_01202_gb300 import learned as lrn
 
     w = inputs.workload(WORKLOAD)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant)
+                                dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant,
+                                guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
+    net = None
+    if learned:  # the committed network, trained on 512^2 trajectories of this workload's distribution
+        theta, s_out = lrn.load()
+        net = pfc.GuessNet(w["shape"])
+        net.set_params(theta)
+        pfc.set_guess_net(s, net, s_out)
     s.set_field(w["phi"])
     s.run(warmup)
     tuning = s.tuning()
@@ -201,6 +209,7 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
         "steps_per_s": steps / (ms / 1e3),
         "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
         "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
+        "learned_guess_used": sum(1 for i in infos if i["guess_used"] == pfc.PFC_GUESS_LEARNED),
         "dt_last": infos[-1]["dt"],
         "energy_last": infos[-1]["energy"],
         "apply_launches": prof["apply_launches"],
@@ -230,6 +239,8 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
                       "d2h_bytes_per_step": int(a_out.nbytes)}
     s.close()
     del s
+    if net is not None:
+        net.close()
     torch.cuda.empty_cache()
     return out
 
@@ -317,7 +328,7 @@ def kernel_loop(args):
 
     build.build()
     w = inputs.workload(WORKLOAD)
-    prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2}[args.variant]
+    prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2, "bf16_learned": 2}[args.variant]
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec,
                                 apply_variant=args.apply_variant)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
@@ -345,7 +356,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16"],
+    ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16", "bf16_learned"],
                     help="run one factor-precision variant only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
@@ -385,12 +396,12 @@ def main():
         build.build()
     barrier(world)
     variants = {}
-    for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
+    for name, prec, lg in (("f64", 0, False), ("f32", 1, False), ("bf16", 2, False), ("bf16_learned", 2, True)):
         if args.variant in ("all", name):
             variants[name] = run_variant(prec, args.steps, args.warmup, world, local,
-                                         measure_e2e=(name == "bf16" or args.variant != "all"),
-                                         apply_variant=args.apply_variant if prec else min(args.apply_variant, 0))
-    head = variants["bf16" if "bf16" in variants else args.variant]
+                                         measure_e2e=(name == "bf16_learned" or args.variant != "all"),
+                                         apply_variant=args.apply_variant, learned=lg)
+    head = variants["bf16_learned" if "bf16_learned" in variants else args.variant]
     peak, peak_kind = measured_peaks()
     achieved = head["apply_bytes"] / (head["apply_ms_avg"] * 1e-3) / 1e9
     line = {
@@ -404,9 +415,10 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (subdomain factors stored bf16, applied in f32)",
+        "dtype": "f64 (subdomain factors stored bf16 and applied in f32; guess network bf16/f32)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [1024, 1024], "subdomains": [64, 64], "overlap_per_side": 1,
+                   "guess": "learned network (safeguarded by phi^n and the extrapolation)",
                    "l2": "inputs larger than L2 (factors 0.45-1.7 GB per apply)", "replicas": world},
         "roofline": {"bound": "hbm", "kernel": "ras_apply (left-RAS banded triangular solves)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

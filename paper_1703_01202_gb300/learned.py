@@ -10,7 +10,9 @@ libpfc; this module only sequences calls and keeps samples in device memory.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 import time
 from typing import Dict, List, Optional, Tuple
 
@@ -83,12 +85,17 @@ def _init_params(seed: int) -> np.ndarray:
 
 
 def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
-              theta0: Optional[np.ndarray] = None) -> Tuple[np.ndarray, List[float]]:
-    """Adam on single samples in a seeded random order; returns the parameters and the per-epoch mean loss."""
+              theta0: Optional[np.ndarray] = None, lr_min: Optional[float] = None,
+              holdout: int = 0) -> Tuple[np.ndarray, List[float]]:
+    """Adam on single samples in a seeded random order, the step size following
+    a cosine from lr to lr_min (constant when lr_min is None).  The last
+    `holdout` samples are not trained on; the history holds per epoch the mean
+    training loss and, with a hold-out, the mean hold-out loss."""
     net: pfc.GuessNet = data["net"]
     net.set_params(theta0 if theta0 is not None else _init_params(seed))
     rng = np.random.default_rng(seed)
-    n = len(data["feat"])
+    n = len(data["feat"]) - holdout
+    total = epochs * n
     t = 0
     history = []
     for _ in range(epochs):
@@ -96,9 +103,60 @@ def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
         tot = 0.0
         for i in order:
             t += 1
-            tot += net.train_step(data["feat"][i], data["target"][i], lr, t)
-        history.append(tot / max(n, 1))
+            a = lr if lr_min is None else lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * (t - 1) / total))
+            tot += net.train_step(data["feat"][i], data["target"][i], a, t)
+        rec = {"train": tot / max(n, 1)}
+        if holdout:
+            rec["holdout"] = sum(net.loss_grad(data["feat"][i], data["target"][i])[0]
+                                 for i in range(n, n + holdout)) / holdout
+        history.append(rec)
     return net.get_params(), history
+
+
+# The committed network: trajectories of the 1024^2 workload's distribution
+# (three hexagonal seeds, gamma 0.25, adaptive dt) on 512^2 grids.
+DEFAULT_RECIPE = dict(n_traj=48, steps=25, size=512, epochs=12, lr=3e-4, lr_min=3e-5, seed=0, seed0=2000)
+WEIGHTS = "guess_net.npz"
+
+
+def train_default(out_path: str, **over) -> Dict:
+    """Generates the trajectories, trains, and saves theta, s_out and the recipe to out_path (.npz)."""
+    import torch
+
+    rc = dict(DEFAULT_RECIPE, **over)
+    t0 = time.perf_counter()
+    data = generate(rc["n_traj"], rc["steps"], shape=(rc["size"], rc["size"]), seed0=rc["seed0"])
+    hold = rc["steps"] - 1  # the last trajectory's samples
+    theta, hist = train_net(data, epochs=rc["epochs"], lr=rc["lr"], lr_min=rc["lr_min"], seed=rc["seed"],
+                            holdout=hold)
+    info = {"recipe": rc, "s_out": data["s_out"], "history": hist, "samples": len(data["feat"]) - hold,
+            "seconds": time.perf_counter() - t0}
+    np.savez(out_path, theta=theta.astype(np.float32), s_out=np.array([data["s_out"]]),
+             info=np.array(json.dumps(info)))
+    data["net"].close()
+    del data
+    torch.cuda.empty_cache()
+    return info
+
+
+def load(path: Optional[str] = None) -> Tuple[np.ndarray, float]:
+    """theta and s_out of a saved network (default: the committed one)."""
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", WEIGHTS)
+    z = np.load(path)
+    return z["theta"].astype(np.float32), float(z["s_out"][0])
+
+
+if __name__ == "__main__":
+    import argparse
+
+    ap = argparse.ArgumentParser(description="train the learned Newton initial guess on solver trajectories")
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", WEIGHTS))
+    for k, v in DEFAULT_RECIPE.items():
+        ap.add_argument("--" + k.replace("_", "-"), type=type(v), default=v)
+    args = ap.parse_args()
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    over = {k: getattr(args, k) for k in DEFAULT_RECIPE}
+    print(json.dumps(train_default(args.out, **over)))
 
 
 def evaluate(theta: np.ndarray, s_out: float, shape=(1024, 1024), steps: int = 12, warmup: int = 3,
