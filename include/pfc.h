@@ -91,6 +91,10 @@ typedef struct {
      factorisation and keeps the fastest (pfc_get_tuning reports the pick).
      Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0. */
   int apply_variant;
+  /* pfc_run only: a step whose Newton or GMRES iteration fails (PFC_ENEWTON,
+     PFC_EGMRES) is retried with half the time step, at most dt_halvings times
+     (default 0: the failure is returned).  The paper is silent on failures. */
+  int dt_halvings;
 } pfc_params;
 
 typedef struct {
@@ -104,6 +108,7 @@ typedef struct {
   double res_norm0;  /* ||F(Phi_0)||                                          */
   double res_norm;   /* ||F(phi^{n+1})||                                      */
   int guess_used;    /* PFC_GUESS_* actually used for Phi_0 (safeguard pick)   */
+  int dt_cuts;       /* pfc_run: halvings of the controller's dt before success */
 } pfc_step_info;
 
 typedef struct pfc_cnn pfc_cnn;

@@ -479,6 +479,7 @@ class Params:
     dt_max: float = 10.0
     eta: float = 5000.0
     energy_scaled: bool = True  # READING: controller uses F_d / |Omega|
+    dt_halvings: int = 0  # READING: a step whose Newton iteration fails is retried with dt / 2
 
 
 @dataclass
@@ -577,6 +578,20 @@ class RunRecord:
     gmres_its: int
 
 
+def _step_with_guess(phin, phinm1, dt, dt_prev, h, gamma, p, guess):
+    """One Newton solve from phi^n or, for guess == "extrap", the safeguarded extrapolation."""
+    if guess == "extrap" and dt_prev is not None:
+        # READING (safeguard): the extrapolation is used only when its residual norm
+        # is not larger than that of phi^n, the paper's own starting point (Sec. 4);
+        # after a step-size jump dt/dt_prev is large and the extrapolation poor.
+        g = extrapolated_guess(phin, phinm1, dt, dt_prev)
+        ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma)))
+        if ref < np.linalg.norm(residual(g, phin, dt, h, gamma)):
+            g = None
+        return newton_solve(phin, dt, h, gamma, p, g, ref_norm=ref)
+    return newton_solve(phin, dt, h, gamma, p, None)
+
+
 def run(
     phi0: np.ndarray,
     h: float,
@@ -604,18 +619,11 @@ def run(
             dt = p.dt_min
         else:
             dt = adaptive_dt(E_n * scale, E_nm1 * scale, dt_prev, p)
-        g = None
-        if guess == "extrap" and dt_prev is not None:
-            # READING (safeguard): the extrapolation is used only when its residual norm
-            # is not larger than that of phi^n, the paper's own starting point (Sec. 4);
-            # after a step-size jump dt/dt_prev is large and the extrapolation poor.
-            g = extrapolated_guess(phin, phinm1, dt, dt_prev)
-            ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma)))
-            if ref < np.linalg.norm(residual(g, phin, dt, h, gamma)):
-                g = None
-            phi1, info = newton_solve(phin, dt, h, gamma, p, g, ref_norm=ref)
-        else:
-            phi1, info = newton_solve(phin, dt, h, gamma, p, g)
+        for cut in range(p.dt_halvings + 1):
+            phi1, info = _step_with_guess(phin, phinm1, dt, dt_prev, h, gamma, p, guess)
+            if info.converged:
+                break
+            dt *= 0.5
         if not info.converged:
             raise RuntimeError(f"Newton did not converge at step {n}")
         phinm1, phin = phin, phi1

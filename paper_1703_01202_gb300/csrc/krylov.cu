@@ -14,6 +14,7 @@
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
 // the cycle's "done" flag and returns at once when it is set, which lets the
 // host queue several iterations ahead and synchronise rarely.
+#include <algorithm>
 #include <cmath>
 
 #include "pfc_internal.cuh"
@@ -130,6 +131,21 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
   }
 }
 
+// acc[k] += sum over this thread's pairs of points of V_k . w, for exactly C vectors
+// (a compile-time count: no predicated-off FP64 work for a partial group).
+template <int C>
+__device__ __forceinline__ void dot_sweep(const double* const* p, const double2* __restrict__ w2, long long n2,
+                                          long long start, long long stride, double* acc) {
+  for (long long i = start; i < n2; i += stride) {
+    const double2 wi = w2[i];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(p[k])[i];
+      acc[k] = fma(a.y, wi.y, fma(a.x, wi.x, acc[k]));
+    }
+  }
+}
+
 // partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i]; pairs of points per
 // 16-byte load (every vector starts 256-byte aligned).
 __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double* const* __restrict__ tab, int nv,
@@ -152,14 +168,16 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   const long long n2 = n >> 1;
   const long long stride = (long long)gridDim.x * NT;
   const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
-    const double2 wi = w2[i];
-#pragma unroll
-    for (int k = 0; k < G; ++k)
-      if (k < cnt) {
-        const double2 a = reinterpret_cast<const double2*>(p[k])[i];
-        acc[k] = fma(a.y, wi.y, fma(a.x, wi.x, acc[k]));
-      }
+  const long long start = blockIdx.x * (long long)NT + threadIdx.x;
+  switch (cnt) {  // block-uniform
+    case 1: dot_sweep<1>(p, w2, n2, start, stride, acc); break;
+    case 2: dot_sweep<2>(p, w2, n2, start, stride, acc); break;
+    case 3: dot_sweep<3>(p, w2, n2, start, stride, acc); break;
+    case 4: dot_sweep<4>(p, w2, n2, start, stride, acc); break;
+    case 5: dot_sweep<5>(p, w2, n2, start, stride, acc); break;
+    case 6: dot_sweep<6>(p, w2, n2, start, stride, acc); break;
+    case 7: dot_sweep<7>(p, w2, n2, start, stride, acc); break;
+    default: dot_sweep<G>(p, w2, n2, start, stride, acc);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
     const double wi = w[n - 1];
@@ -167,12 +185,37 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
     for (int k = 0; k < G; ++k)
       if (k < cnt) acc[k] = fma(p[k][n - 1], wi, acc[k]);
   }
+  // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
+  // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
+  // finishes one value over the remaining 4 lanes of its quarter (9 FP64 adds
+  // per lane instead of 8 full butterflies).  Lane l ends with the sum of value
+  // 4 b4 + 2 b3 + b2 (b_i = bit i of l).
+  static_assert(G == 8, "reduce-scatter written for 8 values");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
 #pragma unroll
-  for (int k = 0; k < G; ++k) {
-    const double s = warp_sum(acc[k]);
-    if (lane == 0) red[wid][k] = s;
+  for (int i = 0; i < 4; ++i) {
+    const bool up = lane & 16;
+    const double send = up ? acc[i] : acc[i + 4];
+    const double keep = up ? acc[i + 4] : acc[i];
+    acc[i] = keep + __shfl_xor_sync(FULL, send, 16);
   }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool up = lane & 8;
+    const double send = up ? acc[i] : acc[i + 2];
+    const double keep = up ? acc[i + 2] : acc[i];
+    acc[i] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const double send = up ? acc[0] : acc[1];
+    const double keep = up ? acc[1] : acc[0];
+    acc[0] = keep + __shfl_xor_sync(FULL, send, 4);
+  }
+  acc[0] += __shfl_xor_sync(FULL, acc[0], 2);
+  acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
+  if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
   __syncthreads();
   if (threadIdx.x < cnt) {
     double s = 0.0;
@@ -182,7 +225,8 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   if (tail.counter) last_cta_tail(tail, partial, nv, gridDim.x);
 }
 
-// w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, partial[gridDim..] = sum w
+// w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w
+template <bool SUM>
 __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const double* x0,
                                                   const double* const* __restrict__ tab, int nx,
                                                   const double* __restrict__ coef, double sign, long long n,
@@ -203,6 +247,7 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
   double2* w2 = reinterpret_cast<double2*>(w);
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
     double2 acc = w2[i];
+#pragma unroll 4
     for (int k = 0; k < nx; ++k) {
       const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
       acc.x = fma(c[k], a.x, acc.x);
@@ -210,7 +255,7 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
     }
     w2[i] = acc;
     s2 = fma(acc.y, acc.y, fma(acc.x, acc.x, s2));
-    s1 += acc.x + acc.y;
+    if (SUM) s1 += acc.x + acc.y;
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
     double acc = w[n - 1];
@@ -227,12 +272,12 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
     red[1][wid] = s1;
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x < (SUM ? 2 : 1)) {
     double s = 0.0;
     for (int q = 0; q < NT / 32; ++q) s += red[threadIdx.x][q];
     partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
-  if (tail.counter) last_cta_tail(tail, partial, 2, gridDim.x);
+  if (tail.counter) last_cta_tail(tail, partial, SUM ? 2 : 1, gridDim.x);
 }
 
 // out[v] = sum_p partial[v * nparts + p], fixed order.
@@ -292,7 +337,9 @@ int red_ctas(long long n) {
 
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st) {
-  const int bx = red_ctas((n + 1) / 2);
+  // half the CTAs of the other sweeps: each thread covers twice the points, so the
+  // per-CTA reduction of 8 sums is a smaller share of the FP64 work
+  const int bx = std::max(1, red_ctas((n + 1) / 2) / 2);
   dim3 grid(bx, (nv + G - 1) / G);
   k_multidot<<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
   count_launches(1);
@@ -302,7 +349,11 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st) {
   const int bx = red_ctas((n + 1) / 2);
-  k_multiaxpy<<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+  // the sum of w is read only by the kSums tail (and by callers of partials-only sweeps)
+  if (tail.counter && tail.kind != Tail::kSums)
+    k_multiaxpy<false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+  else
+    k_multiaxpy<true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
   count_launches(1);
 }
 

@@ -133,6 +133,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->ras_kind != PFC_LEFT_RAS) return PFC_EINVAL;
   if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
   if (p->apply_variant < -1 || p->apply_variant >= pfc::kApplyVariants) return PFC_EINVAL;
+  if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -1051,7 +1052,17 @@ int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step) {
     double dt = 0.0;
     pfc_next_dt(s, &dt);
     pfc_step_info info{};
-    int rc = pfc_step(s, dt, &info);
+    int rc = PFC_OK, cuts = 0;
+    for (;;) {  // a failed step leaves the state unchanged: retry with dt / 2
+      rc = pfc_step(s, dt, &info);
+      if ((rc == PFC_ENEWTON || rc == PFC_EGMRES) && cuts < s->p.dt_halvings) {
+        dt *= 0.5;
+        ++cuts;
+        continue;
+      }
+      break;
+    }
+    info.dt_cuts = cuts;
     if (per_step) per_step[n] = info;
     if (rc) return rc;
   }

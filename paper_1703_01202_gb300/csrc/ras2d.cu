@@ -317,10 +317,16 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   // the entries congruent to l mod 32, one register per 32-entry block.  Forward
   // window [k, k+kl] (kl <= 32 (NW - 1)): blocks mf..mf+NW-1 in wf[], mf = k / 32.
   // Backward window [k-ku2, k] (ku2 <= 32 (NB - 1)): blocks mb..mb-NB+1 in wb[],
-  // mb = k / 32.  The registers rotate when k crosses a block boundary; the pivot
-  // and x_k values reach every lane by warp shuffles, so no step needs a
-  // shared-memory round trip or a warp barrier.
+  // mb = k / 32.  A chunk of CH steps never crosses a 32-step block (CH divides
+  // 32), so the registers rotate only between chunks, when the finished block
+  // (final y or x values) goes to shared memory.  Inside a block, step k = 32 m + s
+  // touches register q of lane l exactly when l passes one threshold in s, and
+  // the row interchange is one predicated write into the lane holding the pivot
+  // row; the pivot and y_k / x_k values reach every lane by warp shuffles.
+  // Entries past n - 1 (forward) or below 0 (backward) may hold junk: no step
+  // reads them into a valid entry and they are never stored.
   constexpr int NB = 2 * NW - 1;
+  static_assert(32 % CH == 0, "a chunk stays inside one 32-step block");
   const unsigned FULL = 0xffffffffu;
   int mf = 0, mb = 0;
   TC wf[NW], wb[NB];
@@ -343,35 +349,45 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
     }
     const TS* data = stage(st);
     if (t < nc) {  // forward: row interchange P_k, then elimination L_k
-      const int c = t, rows = min(CH, n - c * CH);
-      for (int kk = 0; kk < rows; ++kk) {
-        const int k = c * CH + kk;
-        if ((k >> 5) != mf) {  // entered block mf + 1
-          ++mf;
+      const int c = t, k0 = c * CH, rows = min(CH, n - k0);
+      if ((k0 >> 5) != mf) {  // entered block mf + 1: block mf holds final y
+        if (32 * mf + lane < n) buf[32 * mf + lane] = wf[0];
+        ++mf;
 #pragma unroll
-          for (int q = 0; q < NW - 1; ++q) wf[q] = wf[q + 1];
-          const int tn = 32 * (mf + NW - 1) + lane;
-          wf[NW - 1] = tn < n ? buf[tn] : (TC)0;
-        }
-        const TS* lk = data + kk * lrow;
-        const int p = k + pv[k];
-        const int dp = (p >> 5) - mf;
-        const TC bk = __shfl_sync(FULL, wf[0], k & 31);
+        for (int q = 0; q < NW - 1; ++q) wf[q] = wf[q + 1];
+        const int tn = 32 * (mf + NW - 1) + lane;
+        wf[NW - 1] = tn < n ? buf[tn] : (TC)0;
+      }
+      const int s0 = k0 & 31;
+      for (int kk = 0; kk < rows; ++kk) {
+        const int s = s0 + kk, k = k0 + kk;
+        const TS* lk = data + kk * lrow - s - 1;  // lk[32 q + lane] multiplies row 32 (mf + q) + lane
+        const int sp = s + pv[k];                 // pivot row p = 32 mf + sp
+        const int dp = sp >> 5, lp = sp & 31;
+        const TC bk = __shfl_sync(FULL, wf[0], s);
         TC src = wf[0];
 #pragma unroll
         for (int q = 1; q < NW; ++q)
           if (dp == q) src = wf[q];
-        const TC bp = __shfl_sync(FULL, src, p & 31);
-        if (lane == (k & 31)) buf[k] = bp;  // y_k
-        const int last = min(k + kl, n - 1);
+        const TC bp = __shfl_sync(FULL, src, lp);
+        if (lane == lp) {  // interchange: row p receives b_k
 #pragma unroll
-        for (int q = 0; q < NW; ++q) {  // rows of blocks mf+1.. lie below k by construction
-          const int tt = 32 * (mf + q) + lane;
-          if ((q > 0 || tt > k) && tt <= last)
-            wf[q] = ((tt == p) ? bk : wf[q]) - from_store<TC, TS>(lk[tt - k - 1]) * bp;
+          for (int q = 0; q < NW; ++q)
+            if (dp == q) wf[q] = bk;
         }
+        if (lane == s) wf[0] = bp;  // y_k
+        if (lane > s && lane <= s + kl) wf[0] -= from_store<TC, TS>(lk[lane]) * bp;
+#pragma unroll
+        for (int q = 1; q < NW; ++q)
+          if (lane <= s + kl - 32 * q) wf[q] -= from_store<TC, TS>(lk[32 * q + lane]) * bp;
+      }
+      if (t == nc - 1) {  // forward done: the remaining blocks are final
+#pragma unroll
+        for (int q = 0; q < NW; ++q)
+          if (32 * (mf + q) + lane < n) buf[32 * (mf + q) + lane] = wf[q];
       }
     } else {  // backward, column oriented: x_k = y_k / u_kk, y_{k-j} -= u_{k-j,k} x_k
+      const int c = 2 * nc - 1 - t, k0 = c * CH, rows = min(CH, n - k0);
       if (t == nc) {  // y complete: load the top of the backward window
         __syncwarp();
         mb = (n - 1) >> 5;
@@ -380,27 +396,26 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
           const int tb = 32 * (mb - q) + lane;
           wb[q] = (tb >= 0 && tb < n) ? buf[tb] : (TC)0;
         }
+      } else if ((k0 >> 5) != mb) {  // entered block mb - 1: block mb holds final x
+        if (32 * mb + lane < n) buf[32 * mb + lane] = wb[0];
+        --mb;
+#pragma unroll
+        for (int q = 0; q < NB - 1; ++q) wb[q] = wb[q + 1];
+        const int tn = 32 * (mb - NB + 1) + lane;
+        wb[NB - 1] = tn >= 0 ? buf[tn] : (TC)0;
       }
-      const int c = 2 * nc - 1 - t, rows = min(CH, n - c * CH);
+      const int s0 = k0 & 31;
       for (int kk = rows - 1; kk >= 0; --kk) {
-        const int k = c * CH + kk;
-        if ((k >> 5) != mb) {  // entered block mb - 1
-          --mb;
+        const int s = s0 + kk;
+        const TS* uk = data + kk * ucol + s;  // uk[32 q - lane] multiplies row 32 (mb - q) + lane
+        const TC xk = __shfl_sync(FULL, wb[0], s) * from_store<TC, TS>(uk[-s]);
+        if (lane == s) wb[0] = xk;
+        if (lane < s && lane >= s - ku2) wb[0] -= from_store<TC, TS>(uk[-lane]) * xk;
 #pragma unroll
-          for (int q = 0; q < NB - 1; ++q) wb[q] = wb[q + 1];
-          const int tn = 32 * (mb - NB + 1) + lane;
-          wb[NB - 1] = tn >= 0 ? buf[tn] : (TC)0;
-        }
-        const TS* uk = data + kk * ucol;
-        const TC xk = __shfl_sync(FULL, wb[0], k & 31) * from_store<TC, TS>(uk[0]);
-        if (lane == (k & 31)) buf[k] = xk;
-        const int lo = max(0, k - ku2);
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {  // rows of blocks mb-1.. lie above k by construction
-          const int tt = 32 * (mb - q) + lane;
-          if ((q > 0 || tt < k) && tt >= lo) wb[q] -= from_store<TC, TS>(uk[k - tt]) * xk;
-        }
+        for (int q = 1; q < NB; ++q)
+          if (lane >= s + 32 * q - ku2) wb[q] -= from_store<TC, TS>(uk[32 * q - lane]) * xk;
       }
+      if (t == total - 1 && lane < n) buf[lane] = wb[0];  // block 0
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
     if (lane == 0 && t + 2 < total) issue(t + 2);

@@ -35,7 +35,7 @@ class pfc_params(ctypes.Structure):
         ("sub", c_int * 3), ("overlap", c_int), ("ras_kind", c_int), ("factor_prec", c_int), ("guess", c_int),
         ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
-        ("apply_variant", c_int),
+        ("apply_variant", c_int), ("dt_halvings", c_int),
     ]
 
 
@@ -43,7 +43,7 @@ class pfc_step_info(ctypes.Structure):
     _fields_ = [
         ("status", c_int), ("newton_its", c_int), ("gmres_its", c_int), ("ls_cuts", c_int),
         ("dt", c_double), ("energy", c_double), ("mass", c_double), ("res_norm0", c_double), ("res_norm", c_double),
-        ("guess_used", c_int),
+        ("guess_used", c_int), ("dt_cuts", c_int),
     ]
 
     def as_dict(self) -> dict:

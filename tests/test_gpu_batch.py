@@ -73,3 +73,33 @@ def test_batch_rejects_bad_arguments(env):
     P, torch = env
     with pytest.raises(P.PfcError):
         P.run_batch([], 1)
+
+
+def test_failed_steps_are_retried_with_half_the_step(env):
+    """With GMRES capped at 8 iterations the larger controller steps fail; pfc_run
+    halves dt (dt_halvings) until the step converges, and the accepted phi^{n+1}
+    satisfies the scheme at the dt actually used (oracle residual)."""
+    P, torch = env
+    shape = (48, 48)
+    params = P.default_params(sub=(3, 3), overlap=1, factor_prec=0, dt_min=0.01, dt_max=10.0, eta=5000.0,
+                              gmres_max_it=8, dt_halvings=12)
+    s = P.Solver(shape, H, 0.33, params)
+    phi = inputs.noise_field(shape, 0.07, 0.07, 1020)
+    s.set_field(phi)
+    prev = phi
+    cuts = 0
+    for _ in range(4):
+        rec = s.run(1)[0]
+        cur = s.get_field()
+        cuts += rec["dt_cuts"]
+        r_new = np.linalg.norm(O.residual(cur, prev, rec["dt"], H, 0.33))
+        r_ref = np.linalg.norm(O.residual(prev, prev, rec["dt"], H, 0.33))
+        assert r_new <= 1e-10 * r_ref * 1.01
+        prev = cur
+    assert cuts > 0
+    s0 = P.Solver(shape, H, 0.33, P.default_params(sub=(3, 3), overlap=1, dt_min=0.01, dt_max=10.0, eta=5000.0,
+                                                   gmres_max_it=8))
+    s0.set_field(phi)
+    with pytest.raises(P.PfcError) as e:
+        s0.run(4)
+    assert e.value.status == P.PFC_EGMRES
