@@ -32,6 +32,12 @@ EXTRA_3D_STEPS = 2
 METRIC = "PFC time steps/s (1024^2 2D crystal growth, adaptive dt)"
 
 
+# DRAM bytes (read + write) of one 2D Schwarz apply launch on this workload from one ncu capture
+# (profiles/ras_apply2d_hex1024_bf16.md), keyed by (factor precision, apply launch shape); a shape
+# or kernel not captured since its last change reports null.
+APPLY_TRAFFIC = {(2, 1): 456.193792e6 + 7.248384e6}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -451,7 +457,8 @@ def main():
                    "l2": "inputs larger than L2 (factors 0.45-1.7 GB per apply)", "replicas": world},
         "roofline": {"bound": "hbm", "kernel": "ras_apply (left-RAS banded triangular solves)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": None},
+                     "peak_source": peak_kind,
+                     "traffic": APPLY_TRAFFIC.get((2, head["tuning"]["apply_variant"]))},
         "clocks": head["clocks"],
         "gpu_launches": head["gpu_launches"],
         "e2e": head["e2e"],

@@ -475,6 +475,11 @@ int tune_apply(pfc_state* s) {
   cudaEventDestroy(e1);
   if (rc != PFC_OK) return rc;
   if (best < 0) return PFC_EINVAL;
+  for (int v = 0; v < best; ++v)  // timing noise: prefer the lowest-numbered shape within 1 % of the best
+    if (s->tune_ms[v] > 0.f && s->tune_ms[v] <= 1.01f * s->tune_ms[best]) {
+      best = v;
+      break;
+    }
   s->fs.variant = best;
   s->tuned = true;
   return PFC_OK;

@@ -120,7 +120,9 @@ def test_apply_autotuner_picks_a_timed_kernel(pfc):
         if v == -1:
             assert t["apply_variant"] in (0, 1, 2, 3)
             assert all(ms > 0 for ms in t["apply_ms"])
-            assert t["apply_ms"][t["apply_variant"]] == min(t["apply_ms"])
+            # the fastest shape, or a lower-numbered one within 1 % of it
+            assert t["apply_ms"][t["apply_variant"]] <= 1.01 * min(t["apply_ms"])
+            assert all(ms > 1.01 * min(t["apply_ms"]) for ms in t["apply_ms"][:t["apply_variant"]])
         else:
             assert t["apply_ms"] == [-1.0] * 4
     assert np.abs(out[-1] - out[0]).max() <= 1e-9
