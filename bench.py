@@ -204,7 +204,8 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
                                 dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant,
                                 guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV)
-    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
+    # a stream of its own: GMRES cycles run as captured graphs whenever per-apply timing is off
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
     net = None
     if learned:  # the committed network, trained on 512^2 trajectories of this workload's distribution
         theta, s_out = lrn.load()

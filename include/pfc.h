@@ -95,6 +95,17 @@ typedef struct {
      PFC_EGMRES) is retried with half the time step, at most dt_halvings times
      (default 0: the failure is returned).  The paper is silent on failures. */
   int dt_halvings;
+  /* Classical Gram-Schmidt re-orthogonalisation test (Daniel-Gragg-Kaufman-
+     Stewart): a second pass when ||w'|| < gmres_reorth_eta ||w||; default 0.3
+     (a second pass only under strong cancellation); 1/sqrt(2) is the classical
+     choice; 0 = one pass only.  Both sweeps are FP64. */
+  double gmres_reorth_eta;
+  /* 2D: run every GMRES cycle as one CUDA graph launch (default 1): a captured
+     conditional while loop over the Arnoldi iterations, one host synchronisation
+     per cycle instead of one per 3 iterations.  Used only on a stream other
+     than the legacy default stream and while pfc_profile is off; otherwise, or
+     if the graph cannot be built, the host-driven loop runs. */
+  int use_graph;
 } pfc_params;
 
 typedef struct {
@@ -205,8 +216,10 @@ int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, 
    (pfc_params.apply_variant numbering).  apply_ms (optional, 4 floats): the
    mean device milliseconds of one apply measured per kernel at the first
    factorisation, -1 for kernels not timed (not tuned yet, an explicit variant,
-   or one that cannot run the blocks).  Not part of the paper's method. */
-int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms);
+   or one that cannot run the blocks).  *graph (optional): 1 once GMRES cycles
+   run as captured CUDA graphs (use_graph), 0 otherwise.  Not part of the
+   paper's method. */
+int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms, int* graph);
 
 /* ---- Learned Newton initial guess (2D).  The paper starts Newton from phi^n
    (Sec. 4); the learned form adds a periodic 3x3 convolutional network
@@ -239,7 +252,8 @@ int pfc_cnn_train_step(pfc_cnn* c, const double* feat, const double* target, dou
 int pfc_cnn_sample(pfc_cnn* c, const double* phinm1, const double* phin, const double* phinp1, double r,
                    double c2, double s_out, double* feat, double* target);
 /* Lets PFC_GUESS_LEARNED use network c (same grid as s; c stays owned by the
-   caller and must outlive its use).  Each step compares the residual norms of
+   caller and must outlive its use; during a step its forward pass runs on the
+   state's stream, so c must not be used concurrently on another stream).  Each step compares the residual norms of
    the learned guess, the extrapolated guess and phi^n and starts Newton from
    the smallest. */
 int pfc_set_guess_net(pfc_state* s, pfc_cnn* c, double s_out);

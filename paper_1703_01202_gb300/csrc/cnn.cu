@@ -504,6 +504,11 @@ void launch_cnn_target(long long n, const double* phinp1, const double* phin, co
 const float* cnn_output(const Cnn* c) { return c->out; }
 int cnn_nx(const Cnn* c) { return c->nx; }
 int cnn_ny(const Cnn* c) { return c->ny; }
+cudaStream_t cnn_swap_stream(Cnn* c, cudaStream_t st) {
+  const cudaStream_t old = c->st;
+  c->st = st;
+  return old;
+}
 
 void launch_cnn_features(long long n, const double* phin, const double* phinm1, const double* mass_sum, double r,
                          double c2, double* feat, cudaStream_t st) {

@@ -80,7 +80,7 @@ __device__ void gmres_finalize(GmresCtl* c, int j, int m, double wn2) {
 // After the multi-axpy w -= sum coef_i Vraw_i, with wn2 = w.w afterwards.
 __device__ void gmres_after_axpy(GmresCtl* c, int j, int pass, int m, double wn2) {
   if (pass == 0) {
-    if (wn2 < 0.5 * c->wnorm2_before) {  // ||w'|| < ||w|| / sqrt(2): orthogonalise once more
+    if (wn2 < c->reorth_eta2 * c->wnorm2_before) {  // ||w'|| < eta ||w||: orthogonalise once more
       c->reorth = 1;
       return;
     }
@@ -119,11 +119,12 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
   __syncthreads();
   if (threadIdx.x == 0) {
     GmresCtl* c = t.ctl;
+    const int j = t.ia ? t.ia->j : t.j;
     if (t.kind == Tail::kDot) {
       for (int v = 0; v < nvals; ++v) c->red[v] = s_sum[v];
-      gmres_after_dot(c, t.j, t.pass);
+      gmres_after_dot(c, j, t.pass);
     } else if (t.kind == Tail::kAxpy) {
-      gmres_after_axpy(c, t.j, t.pass, t.m, s_sum[0]);
+      gmres_after_axpy(c, j, t.pass, t.m, s_sum[0]);
     } else {
       for (int v = 0; v < nvals; ++v) t.out[v] = s_sum[v];
     }
@@ -153,10 +154,14 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
                                                  double* __restrict__ partial, const int* __restrict__ skip,
                                                  const int* __restrict__ only_if, Tail tail) {
   if ((skip && *skip) || (only_if && !*only_if)) return;
+  if (tail.ia) {  // graph mode: this iteration's vector count and w
+    nv = tail.ia->j + 2;
+    w = tail.ia->w;
+  }
   __shared__ double red[NT / 32][G];
   __shared__ const double* sp[G];
   const int g0 = blockIdx.y * G;
-  const int cnt = min(G, nv - g0);
+  const int cnt = min(G, nv - g0);  // <= 0 for spare groups of a graph-mode grid: they only take a ticket
   if (threadIdx.x < G) sp[threadIdx.x] = threadIdx.x < cnt ? vec_at(v0, tab, g0 + threadIdx.x) : w;
   __syncthreads();
   const double* p[G];
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   const double2* w2 = reinterpret_cast<const double2*>(w);
   const long long start = blockIdx.x * (long long)NT + threadIdx.x;
   switch (cnt) {  // block-uniform
+    case 0: break;
     case 1: dot_sweep<1>(p, w2, n2, start, stride, acc); break;
     case 2: dot_sweep<2>(p, w2, n2, start, stride, acc); break;
     case 3: dot_sweep<3>(p, w2, n2, start, stride, acc); break;
@@ -177,7 +183,8 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
     case 5: dot_sweep<5>(p, w2, n2, start, stride, acc); break;
     case 6: dot_sweep<6>(p, w2, n2, start, stride, acc); break;
     case 7: dot_sweep<7>(p, w2, n2, start, stride, acc); break;
-    default: dot_sweep<G>(p, w2, n2, start, stride, acc);
+    default:
+      if (cnt > 0) dot_sweep<G>(p, w2, n2, start, stride, acc);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
     const double wi = w[n - 1];
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
   if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
   __syncthreads();
-  if (threadIdx.x < cnt) {
+  if ((int)threadIdx.x < cnt) {
     double s = 0.0;
     for (int q = 0; q < NT / 32; ++q) s += red[q][threadIdx.x];
     partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
@@ -233,6 +240,10 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
                                                   double* __restrict__ partial, const int* __restrict__ skip,
                                                   const int* __restrict__ only_if, Tail tail) {
   if ((skip && *skip) || (only_if && !*only_if)) return;
+  if (tail.ia) {  // graph mode: this iteration's vector count and w
+    nx = tail.ia->j + 1;
+    w = tail.ia->w;
+  }
   __shared__ double red[2][NT / 32];
   __shared__ double c[kMaxVecs];
   __shared__ const double* sp[kMaxVecs];
@@ -292,13 +303,14 @@ __global__ void __launch_bounds__(1024) k_reduce(const double* __restrict__ part
   }
 }
 
-__global__ void k_gmres_init(GmresCtl* c, const double* __restrict__ nrm2, double sign, double tol) {
+__global__ void k_gmres_init(GmresCtl* c, const double* __restrict__ nrm2, double sign, double tol, double eta2) {
   const double beta = sqrt(*nrm2);
   c->done = 0;
   c->its = 0;
   c->reorth = 0;
   c->breakdown = 0;
   c->tol = tol;
+  c->reorth_eta2 = eta2;
   c->beta = beta;
   c->est = beta;
   c->g[0] = beta;
@@ -326,6 +338,22 @@ __global__ void k_extrapolate(double* __restrict__ out, const double* __restrict
                               double ratio, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = fma(ratio, a[i] - b[i], a[i]);
+}
+
+__global__ void k_iter_setup(const GmresCtl* __restrict__ ctl, const double* const* __restrict__ vtab,
+                             const double* const* __restrict__ ztab, IterArgs* __restrict__ ia) {
+  const int j = ctl->its;
+  ia->j = j;
+  ia->v = vtab[j];
+  ia->z = const_cast<double*>(ztab[j]);
+  ia->w = const_cast<double*>(vtab[j + 1]);
+  ia->scale = &ctl->scale[j];
+}
+
+// Keeps the graph's while loop running until the cycle is done (converged, broken
+// down or at the restart length).
+__global__ void k_cycle_cond(const GmresCtl* __restrict__ ctl, int m, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (!ctl->done && ctl->its < m) ? 1u : 0u);
 }
 
 int red_ctas(long long n) {
@@ -357,13 +385,25 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
   count_launches(1);
 }
 
+void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
+                       cudaStream_t st) {
+  k_iter_setup<<<1, 1, 0, st>>>(ctl, vtab, ztab, ia);
+  count_launches(1);
+}
+
+void launch_cycle_cond(const GmresCtl* ctl, int m, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_cycle_cond<<<1, 1, 0, st>>>(ctl, m, h);
+  count_launches(1);
+}
+
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st) {
   k_reduce<<<1, 1024, 0, st>>>(partial, nvals, nparts, out);
   count_launches(1);
 }
 
-void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, cudaStream_t st) {
-  k_gmres_init<<<1, 1, 0, st>>>(ctl, nrm2, sign, tol);
+void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, double reorth_eta2,
+                       cudaStream_t st) {
+  k_gmres_init<<<1, 1, 0, st>>>(ctl, nrm2, sign, tol, reorth_eta2);
   count_launches(1);
 }
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st) {

@@ -76,6 +76,13 @@ struct pfc_state {
   // ||F(phi^n)|| of the current step when a safeguarded guess was chosen (< 0: none)
   double ref_norm;
   int device;  // CUDA device current at pfc_create
+  // graph mode (2D): one captured GMRES cycle, a conditional while node over the Arnoldi iterations
+  pfc::IterArgs* ia;    // device
+  pfc::IterArgs* ia_h;  // pinned host copy of the host-set fields
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  int graph_body;       // kernels in one iteration of the body
+  bool graph_failed;    // capture or instantiation failed once: keep the host-driven loop
 };
 
 namespace pfc {
@@ -134,6 +141,8 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
   if (p->apply_variant < -1 || p->apply_variant >= pfc::kApplyVariants) return PFC_EINVAL;
   if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
+  if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
+  if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -276,7 +285,7 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat;
+      tabs, feat, iargs;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -343,6 +352,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->red = L.take(sizeof(double) * 16);
   pl->status = L.take(sizeof(int) * 4);
   pl->tabs = L.take(sizeof(double*) * 2 * pfc::kMaxVecs);
+  pl->iargs = L.take(sizeof(pfc::IterArgs));
   pl->feat = d3 ? 0 : L.take(vec * 3);
   if (d3) {
     const Shapes3& S = pl->sh3;
@@ -422,16 +432,21 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
   return PFC_OK;
 }
 
-void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip) {
-  if (s->dim == 2)
-    pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st);
+void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
+         const pfc::IterArgs* ia = nullptr) {
+  if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
+    pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
+  else if (s->dim == 2)
+    pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
   else
     pfc::launch_jvp3d(s->g, v, nullptr, q, idt, out, s->T1, s->T2, skip, s->st);
 }
 
-void precond(pfc_state* s, const double* r, const double* rscale, double* z, const int* skip) {
+void precond(pfc_state* s, const double* r, const double* rscale, double* z, const int* skip,
+             const pfc::IterArgs* ia = nullptr) {
   if (s->dim == 2)
-    pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, rscale, z, skip, s->status_dev + 1, s->st);
+    pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, rscale, z, skip, s->status_dev + 1, s->st,
+                            ia);
   else
     pfc::launch_ras_apply3d(s->g, s->blocks_dev, s->nblocks, s->r3, r, rscale, z, skip, s->status_dev + 1, s->st);
 }
@@ -505,6 +520,67 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
   return PFC_OK;
 }
 
+// Captures one GMRES cycle as a graph: a conditional while node whose body is one
+// Arnoldi iteration (iteration setup, Schwarz apply, JVP, the Gram-Schmidt
+// passes) and the loop test.  Every pointer and count that changes between
+// iterations or solves is read from s->ia, V_0 lives in Vbuf[0].  Returns false
+// (and leaves nothing captured) when the graph cannot be built.
+bool build_cycle_graph(pfc_state* s) {
+  const long long N = s->g.n;
+  const int m = s->p.gmres_restart;
+  const int passes = s->p.gmres_reorth_eta > 0.0 ? 2 : 1;
+  unsigned int* counter = reinterpret_cast<unsigned int*>(s->status_dev + 2);
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  // kernels of one body iteration: setup, apply, JVP, a multi-dot and a multi-axpy per pass, loop test
+  // (counted here rather than from the process-wide counter, which other threads also move)
+  const int body = 4 + 2 * passes;
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s->st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const double* v0 = s->Vbuf;
+    const int* reorth = &s->ctl->reorth;
+    const int* done = &s->ctl->done;  // a cycle that converged at its start runs the body once, all skipped
+    pfc::launch_iter_setup(s->ctl, s->vtab, s->ztab, s->ia, s->st);
+    precond(s, nullptr, nullptr, nullptr, done, s->ia);
+    jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
+    for (int pass = 0; pass < passes; ++pass) {
+      const pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st);
+      const pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done,
+                            pass ? reorth : nullptr, ta, s->st);
+    }
+    pfc::launch_cycle_cond(s->ctl, m, h, s->st);
+    cudaGraph_t body = nullptr;
+    ok = cudaStreamEndCapture(s->st, &body) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  }
+  s->graph_body = body;
+  if (ok) pfc::count_launches(-(long long)body);  // the capture counted them once; replays count below
+  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return false;
+  }
+  s->graph = g;
+  s->gexec = ge;
+  return true;
+}
+
 // Right-preconditioned restarted GMRES for J S = -F, x0 = 0 (Eq. hjacobi).
 // V_0 = -F/||F||, Z_j = H^{-1} V_j, S = sum_j y_j Z_j.  Leaves sum(S) in red[9].
 int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
@@ -512,18 +588,41 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
   const int m = s->p.gmres_restart;
   const int* done = &s->ctl->done;
   const int* reorth = &s->ctl->reorth;
+  const double eta2 = s->p.gmres_reorth_eta * s->p.gmres_reorth_eta;
+  const int passes = eta2 > 0.0 ? 2 : 1;  // the second pass only exists with a DGKS threshold
   unsigned int* counter = reinterpret_cast<unsigned int*>(s->status_dev + 2);  // last-CTA ticket
   int total = 0;
   CU(cudaMemsetAsync(s->S, 0, sizeof(double) * N, s->st));
   CU(cudaMemsetAsync(s->red + 8, 0, 2 * sizeof(double), s->st));
+  // graph mode: 2D, a stream that can be captured, no per-apply event timing
+  bool graph = s->p.use_graph && s->dim == 2 && s->st != nullptr && !s->prof && !s->graph_failed;
+  if (graph && !s->gexec && !build_cycle_graph(s)) {
+    s->graph_failed = true;
+    graph = false;
+  }
+  if (graph) {
+    s->ia_h->q = s->q;
+    s->ia_h->idt = idt;
+    CU(cudaMemcpyAsync(s->ia, s->ia_h, sizeof(pfc::IterArgs), cudaMemcpyHostToDevice, s->st));
+  }
   // first cycle: V_0 = F scaled by -1/||F||
   const double* v0 = s->F;
+  if (graph) {
+    CU(cudaMemcpyAsync(s->Vbuf, s->F, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
+    v0 = s->Vbuf;
+  }
   double f2 = fnorm * fnorm;
   CU(cudaMemcpyAsync(s->red + 10, &f2, sizeof(double), cudaMemcpyHostToDevice, s->st));
-  pfc::launch_gmres_init(s->ctl, s->red + 10, -1.0, tol, s->st);
+  pfc::launch_gmres_init(s->ctl, s->red + 10, -1.0, tol, eta2, s->st);
   while (true) {
+    if (graph) {  // the whole cycle: one graph launch, one host synchronisation
+      CU(cudaGraphLaunch(s->gexec, s->st));
+      int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
+      if (rc) return rc;
+      pfc::count_launches((long long)s->graph_body * std::max(1, s->ctl_h->its));
+    }
     // basis V_0 = v0, V_i = Vbuf + i N (pointer table s->vtab); Z_i = Zbuf + i N (s->ztab)
-    int j = 0;
+    int j = graph ? m : 0;
     const int chunk = 3;
     while (j < m) {
       const int jstart = j;
@@ -536,7 +635,7 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
         precond(s, vj, &s->ctl->scale[j], zj, done);
         if (s->prof) CU(cudaEventRecord(s->ev[2 * j + 1], s->st));
         jvp(s, zj, s->q, idt, w, done);
-        for (int pass = 0; pass < 2; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
+        for (int pass = 0; pass < passes; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
           const pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
           pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st);
           const pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
@@ -580,8 +679,12 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
     const pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 10};
     pfc::launch_multidot(s->W, s->vtab, 1, s->W, N, s->partial, nullptr, nullptr, tnrm, s->st);
-    pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, s->st);
+    pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, eta2, s->st);
     v0 = s->W;
+    if (graph) {
+      CU(cudaMemcpyAsync(s->Vbuf, s->W, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
+      v0 = s->Vbuf;
+    }
     CU(cudaGetLastError());
   }
   *its_out = total;
@@ -662,7 +765,9 @@ int safeguarded_guess(pfc_state* s, double dt, bool learned, int* used) {
     if ((rc = energy_mass(s, s->phin, nullptr, nullptr))) return rc;  // red[5] = sum phi^n
     pfc::launch_cnn_features(N, s->phin, s->phinm1, s->red + 5, dt / s->dt_prev, dt / s->p.dt_max, s->feat, s->st);
     pfc::Cnn* c = reinterpret_cast<pfc::Cnn*>(s->cnn);
+    const cudaStream_t own = pfc::cnn_swap_stream(c, s->st);  // the forward pass joins the step's stream
     pfc::cnn_forward(c, s->feat);
+    pfc::cnn_swap_stream(c, own);
     int np = 0;
     pfc::launch_cnn_delta(N, s->feat, pfc::cnn_output(c), s->s_out, s->W, s->partial, &np, s->st);
     pfc::launch_reduce(s->partial, 1, np, s->red + 11, s->st);
@@ -729,6 +834,8 @@ int pfc_default_params(pfc_params* p) {
   p->eta = 5000.0;
   p->energy_scaled = 1;
   p->apply_variant = -1;
+  p->gmres_reorth_eta = 0.3;
+  p->use_graph = 1;
   return PFC_OK;
 }
 
@@ -807,9 +914,11 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->red = (double*)at(pl.red);
   s->status_dev = (int*)at(pl.status);
   s->feat = g->dim == 2 ? (double*)at(pl.feat) : nullptr;
+  s->ia = (pfc::IterArgs*)at(pl.iargs);
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->ia_h, sizeof(pfc::IterArgs)) != cudaSuccess) {
     pfc_destroy(s);
     return PFC_ECUDA;
   }
@@ -900,9 +1009,10 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   return PFC_OK;
 }
 
-int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms) {
+int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms, int* graph) {
   if (!s || !apply_variant) return PFC_EINVAL;
   *apply_variant = s->fs.variant;
+  if (graph) *graph = s->gexec != nullptr;
   if (apply_ms)
     for (int v = 0; v < pfc::kApplyVariants; ++v) apply_ms[v] = s->tune_ms[v];
   return PFC_OK;
@@ -914,6 +1024,9 @@ void pfc_destroy(pfc_state* s) {
   if (s->ctl_h) cudaFreeHost(s->ctl_h);
   if (s->red_h) cudaFreeHost(s->red_h);
   if (s->status_h) cudaFreeHost(s->status_h);
+  if (s->ia_h) cudaFreeHost(s->ia_h);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
   delete s;
 }
 

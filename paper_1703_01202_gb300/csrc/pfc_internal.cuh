@@ -37,11 +37,26 @@ struct GmresCtl {
   int breakdown;
   double tol, beta, est;
   double wnorm2_before;
+  double reorth_eta2;  // second pass when ||w'||^2 < reorth_eta2 ||w||^2 (0: never)
   double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
   double scale[kMaxRestart + 2];  // V_i = scale_i * Vraw_i
   double coef[kMaxRestart + 2];   // coefficients of the pending multi-axpy
   double red[kMaxVecs + 2];       // reduced sums of the last multi-dot / axpy
+};
+
+// Arguments of one Arnoldi iteration read from device memory, so that a captured
+// CUDA graph can loop over iterations: j and the vectors of step j are written by
+// k_iter_setup at the start of every iteration; q and idt by the host once per
+// GMRES solve.
+struct IterArgs {
+  int j;
+  const double* v;      // V_j (preconditioner input)
+  double* z;            // Z_j = M^-1 V_j
+  double* w;            // V_{j+1} = J Z_j before orthogonalisation
+  const double* scale;  // &scale[j]
+  const double* q;      // Jacobian coefficient of this Newton iteration
+  double idt;           // 1 / dt
 };
 
 // Scalars the host reads back after a reduction.
@@ -68,8 +83,11 @@ void launch_residual2d(const Geo& g, const double* Phi_base, const double* S, do
                        const double* phin, double idt, double* F, double* Phi_out, double* q_out, double* partial,
                        int* nparts, cudaStream_t st);
 void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  const int* skip, cudaStream_t st);
+                  const int* skip, cudaStream_t st, const IterArgs* ia = nullptr);
 void launch_energy2d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
+// The same JVP in float-float arithmetic on the FP32 pipe (jvp_ff.cu), for the mixed path.
+void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
+                     const int* skip, cudaStream_t st, const IterArgs* ia = nullptr);
 void launch_qcoef(const Geo& g, const double* Phi, const double* phin, double* q, cudaStream_t st);
 
 // ---- Schwarz preconditioner (ras2d.cu)
@@ -88,7 +106,8 @@ constexpr int kApplyVariants = 4;
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
-                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st);
+                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
+                        const IterArgs* ia = nullptr);
 size_t factor_smem_bytes(int prec, int kl, int n_max);
 // Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec.
 bool apply_variant_ok(int v, int prec, int kl_max);
@@ -150,6 +169,7 @@ void cnn_refresh_bf16(Cnn* c);
 void cnn_out_to_f64(Cnn* c, double* out);
 const float* cnn_output(const Cnn* c);
 int cnn_nx(const Cnn* c);
+cudaStream_t cnn_swap_stream(Cnn* c, cudaStream_t st);  // returns the previous stream
 int cnn_ny(const Cnn* c);
 // features (phi^n - mean, r (phi^n - phi^{n-1}), dt / dt_max) as 3 planes; guess pieces
 void launch_cnn_features(long long n, const double* phin, const double* phinm1, const double* mass_sum, double r,
@@ -173,16 +193,24 @@ struct Tail {
   GmresCtl* ctl;
   unsigned int* counter;
   double* out;              // kSums: reduced values
+  const IterArgs* ia;       // when set, j comes from ia->j (graph mode)
 };
 
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
+// With tail.ia set (graph mode) the vector count is ia->j + 2 (dot) / ia->j + 1 (axpy), w is
+// ia->w, and nv / nx only bound the grid.
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st);
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st);
+// Graph-mode helpers: ia <- the vectors of iteration j = ctl->its; loop condition of a GMRES cycle.
+void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
+                       cudaStream_t st);
+void launch_cycle_cond(const GmresCtl* ctl, int m, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st);
-void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, cudaStream_t st);
+void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, double reorth_eta2,
+                       cudaStream_t st);
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
 void launch_extrapolate(double* out, const double* a, const double* b, double ratio, long long n,

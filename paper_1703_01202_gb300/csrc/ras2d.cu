@@ -267,8 +267,14 @@ template <typename TC, typename TS, int CH, int WPC, int NW>
 __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc* __restrict__ blocks, int nblocks,
                                                           FactorStore fs, const double* __restrict__ r,
                                                           const double* __restrict__ rscale, double* __restrict__ z,
-                                                          const int* __restrict__ skip, int* __restrict__ err) {
+                                                          const int* __restrict__ skip, int* __restrict__ err,
+                                                          const IterArgs* __restrict__ ia) {
   if (skip && *skip) return;
+  if (ia) {  // graph mode: this Arnoldi iteration's vectors
+    r = ia->v;
+    rscale = ia->scale;
+    z = ia->z;
+  }
   extern __shared__ __align__(128) unsigned char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * WPC + w;
@@ -445,12 +451,13 @@ void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 
 template <typename TC, typename TS, int CH, int WPC, int NW = 3>
 void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
-                    const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
+                    const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
+                    const IterArgs* ia) {
   const ApplySmem lay = apply_smem<TC, TS, CH>(fs.lrow, fs.ucol, fs.n_max);
   const size_t smem = WPC * lay.total;
   cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ras_apply2d<TC, TS, CH, WPC, NW><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale,
-                                                                                    z, skip, err);
+                                                                                    z, skip, err, ia);
   count_launches(1);
 }
 
@@ -482,39 +489,40 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 }
 
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
-                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
+                        const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
+                        const IterArgs* ia) {
   // Launch shapes (chunk length CH = steps per bulk copy, WPC = warps per CTA):
   // variant 0: stages of about 3.5 KB for every storage type, 4 warps per CTA;
   // 1: half the chunk (twice the resident warps per SM), 2: half the chunk and
   // 2 warps per CTA (finer packing), 3: twice the chunk (fewer, larger copies).
   if (fs.kl_max > 64) {  // blocks wider than 21 cells: the wide-window kernel, default shape
     if (fs.prec == PFC_F64)
-      apply_dispatch<double, double, 4, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      apply_dispatch<double, double, 4, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     else if (fs.prec == PFC_F32)
-      apply_dispatch<float, float, 8, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      apply_dispatch<float, float, 8, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     else
-      apply_dispatch<float, __nv_bfloat16, 16, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      apply_dispatch<float, __nv_bfloat16, 16, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
   } else if (fs.prec == PFC_F64) {
     switch (fs.variant) {
-      case 1: apply_dispatch<double, double, 2, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 2: apply_dispatch<double, double, 2, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 3: apply_dispatch<double, double, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      default: apply_dispatch<double, double, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      case 1: apply_dispatch<double, double, 2, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 2: apply_dispatch<double, double, 2, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 3: apply_dispatch<double, double, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      default: apply_dispatch<double, double, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   } else if (fs.prec == PFC_F32) {
     switch (fs.variant) {
-      case 1: apply_dispatch<float, float, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 2: apply_dispatch<float, float, 4, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 3: apply_dispatch<float, float, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      default: apply_dispatch<float, float, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      case 1: apply_dispatch<float, float, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 2: apply_dispatch<float, float, 4, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 3: apply_dispatch<float, float, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      default: apply_dispatch<float, float, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   } else {
     using B16 = __nv_bfloat16;
     switch (fs.variant) {
-      case 1: apply_dispatch<float, B16, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 2: apply_dispatch<float, B16, 8, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      case 3: apply_dispatch<float, B16, 32, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st); break;
-      default: apply_dispatch<float, B16, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st);
+      case 1: apply_dispatch<float, B16, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 2: apply_dispatch<float, B16, 8, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 3: apply_dispatch<float, B16, 32, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      default: apply_dispatch<float, B16, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   }
 }

@@ -105,8 +105,15 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
 // J v = v/dt - Delta_d w,  w = L_gamma v / 2 + q v (Eq. Jacobi).
 __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ v,
                                               const double* __restrict__ vscale, const double* __restrict__ q,
-                                              double idt, double* __restrict__ Jv, const int* __restrict__ skip) {
+                                              double idt, double* __restrict__ Jv, const int* __restrict__ skip,
+                                              const IterArgs* __restrict__ ia) {
   if (skip && *skip) return;
+  if (ia) {  // graph mode: J Z_j into V_(j+1)
+    v = ia->z;
+    q = ia->q;
+    idt = ia->idt;
+    Jv = ia->w;
+  }
   __shared__ double sV[AY][AX];
   __shared__ double sQ[AY - 4][AX - 4];
   __shared__ double sL[AY - 2][AX - 2];
@@ -201,9 +208,9 @@ void launch_residual2d(const Geo& g, const double* Pb, const double* S, double l
 }
 
 void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  const int* skip, cudaStream_t st) {
+                  const int* skip, cudaStream_t st, const IterArgs* ia) {
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-  k_jvp2d<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip);
+  k_jvp2d<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia);
   count_launches(1);
 }
 

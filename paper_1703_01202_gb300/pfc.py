@@ -35,7 +35,8 @@ class pfc_params(ctypes.Structure):
         ("sub", c_int * 3), ("overlap", c_int), ("ras_kind", c_int), ("factor_prec", c_int), ("guess", c_int),
         ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
-        ("apply_variant", c_int), ("dt_halvings", c_int),
+        ("apply_variant", c_int), ("dt_halvings", c_int), ("gmres_reorth_eta", c_double),
+        ("use_graph", c_int),
     ]
 
 
@@ -77,7 +78,7 @@ _SIGNATURES = [
     ("pfc_step_host", c_int, [c_void_p, c_void_p, c_double, c_void_p, POINTER(pfc_step_info)]),
     ("pfc_profile", c_int, [c_void_p, c_int]),
     ("pfc_run_batch", c_int, [POINTER(c_void_p), c_int, c_int, c_void_p, POINTER(c_int)]),
-    ("pfc_get_tuning", c_int, [c_void_p, POINTER(c_int), POINTER(c_float)]),
+    ("pfc_get_tuning", c_int, [c_void_p, POINTER(c_int), POINTER(c_float), POINTER(c_int)]),
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
                                  POINTER(c_longlong)]),
     ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
@@ -288,10 +289,10 @@ class Solver:
         return {"apply_launches": a.value, "apply_ms": ms.value, "apply_bytes": b.value, "kernel_launches": k.value}
 
     def tuning(self) -> dict:
-        v = c_int()
+        v, gr = c_int(), c_int()
         ms = (c_float * 4)()
-        _check(lib().pfc_get_tuning(self.handle, ctypes.byref(v), ms), "pfc_get_tuning")
-        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(4)]}
+        _check(lib().pfc_get_tuning(self.handle, ctypes.byref(v), ms, ctypes.byref(gr)), "pfc_get_tuning")
+        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(4)], "graph": gr.value}
 
     # -- test hooks on device tensors
     def residual(self, Phi, phin, dt: float):

@@ -103,3 +103,24 @@ def test_failed_steps_are_retried_with_half_the_step(env):
     with pytest.raises(P.PfcError) as e:
         s0.run(4)
     assert e.value.status == P.PFC_EGMRES
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_graph_cycles_match_the_host_loop(env, prec):
+    """GMRES cycles captured as CUDA graphs (a conditional while loop over the Arnoldi
+    iterations, use_graph = 1, on a non-default stream) run the same kernels in the
+    same order as the host-driven loop: identical records and fields."""
+    P, torch = env
+    shape = (64, 64)
+    phi = inputs.noise_field(shape, 0.07, 0.07, 1030)
+    out = {}
+    for ug in (0, 1):
+        params = P.default_params(sub=(4, 4), overlap=1, factor_prec=prec, dt_min=0.01, dt_max=10.0, eta=5000.0,
+                                  use_graph=ug)
+        s = P.Solver(shape, H, 0.25, params, stream=torch.cuda.Stream())
+        s.set_field(phi)
+        recs = s.run(4)
+        out[ug] = (recs, s.get_field(), s.tuning()["graph"])
+    assert out[1][2] == 1 and out[0][2] == 0
+    assert [r["gmres_its"] for r in out[0][0]] == [r["gmres_its"] for r in out[1][0]]
+    np.testing.assert_array_equal(out[0][1], out[1][1])

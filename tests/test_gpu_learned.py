@@ -38,11 +38,11 @@ def _field(shape):
     return inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=8, seed=3001)
 
 
-def _run(P, shape, guess, theta, s_out, steps, prec=2, parts=None):
+def _run(P, shape, guess, theta, s_out, steps, prec=2, parts=None, stream=None):
     ny, nx = shape
     parts = parts or (nx // 16, ny // 16)
     params = P.default_params(sub=parts, overlap=1, factor_prec=prec, guess=guess, **PRM)
-    s = P.Solver(shape, H, GAMMA, params)
+    s = P.Solver(shape, H, GAMMA, params, stream=stream)
     net = None
     if guess == P.PFC_GUESS_LEARNED:
         net = P.GuessNet(shape)
@@ -83,3 +83,7 @@ def test_learned_run_matches_oracle(env):
                       O.Params(parts=(4, 4), overlap=1, **PRM), 4)
     assert np.abs(phi_l - ref).max() <= 1e-7
     assert abs(inf_l[-1]["energy"] - recs[-1].energy) <= 1e-9 * abs(recs[-1].energy)
+    # the same run on a side stream (network on the default stream, GMRES cycles as graphs)
+    phi_s, inf_s = _run(P, shape, P.PFC_GUESS_LEARNED, theta, s_out, 4, stream=torch.cuda.Stream())
+    np.testing.assert_array_equal(phi_s, phi_l)
+    assert [i["guess_used"] for i in inf_s] == [i["guess_used"] for i in inf_l]

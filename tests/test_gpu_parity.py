@@ -45,15 +45,32 @@ def test_residual_matches_oracle(pfc, shape):
     assert nrm == pytest.approx(np.linalg.norm(ref), rel=1e-12)
 
 
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("shape", [(64, 64), (40, 70), (33, 31)])
-def test_jvp_matches_oracle(pfc, shape):
+def test_jvp_matches_oracle(pfc, shape, prec):
+    """FP64 JVP (plain path) and the float-float JVP of the mixed path (F32/BF16
+    factors): both within 1e-12 of the oracle, relative to the largest entry."""
     Phi = inputs.noise_field(shape, 0.2, 0.4, 3)
     phin = inputs.noise_field(shape, 0.2, 0.4, 4)
     v = inputs.noise_field(shape, 0.0, 1.0, 5)
-    s = solver(pfc, shape, (1, 1), overlap=0)
+    s = solver(pfc, shape, (1, 1), prec=prec, overlap=0)
     Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
     ref = O.jvp(v, Phi, phin, 2.5, H, GAMMA)
     np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_float_float_jvp_on_a_smooth_vector(pfc):
+    """A smooth v makes the stencil terms cancel (J v ~ v / dt at dt = 10 while the
+    Delta_d^3 terms are ~ 1e2 |v|): the float-float JVP must still agree with the
+    oracle to 1e-11 of max |J v|."""
+    shape = (64, 64)
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 3)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 4)
+    v = inputs.sine_field(shape, H, 1.0, 32.0 * H)
+    s = solver(pfc, shape, (1, 1), prec=2, overlap=0)
+    Jv = s.jvp(Phi, phin, v, 10.0).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 10.0, H, GAMMA)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("shape", [(64, 64), (37, 50)])
