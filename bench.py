@@ -35,7 +35,7 @@ METRIC = "PFC time steps/s (1024^2 2D crystal growth, adaptive dt)"
 # DRAM bytes (read + write) of one 2D Schwarz apply launch on this workload from one ncu capture
 # (profiles/ras_apply2d_hex1024_bf16.md), keyed by (factor precision, apply launch shape); a shape
 # or kernel not captured since its last change reports null.
-APPLY_TRAFFIC = {(2, 1): 456.193792e6 + 7.248384e6}
+APPLY_TRAFFIC = {}
 
 
 def measured_peaks():

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
         wf[NW - 1] = tn < n ? buf[tn] : (TC)0;
       }
       const int s0 = k0 & 31;
-      for (int kk = 0; kk < rows; ++kk) {
+      auto fstep = [&](int kk) {
         const int s = s0 + kk, k = k0 + kk;
         const TS* lk = data + kk * lrow - s - 1;  // lk[32 q + lane] multiplies row 32 (mf + q) + lane
         const int sp = s + pv[k];                 // pivot row p = 32 mf + sp
@@ -385,7 +385,15 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
         if (lane > s && lane <= s + kl) wf[0] -= from_store<TC, TS>(lk[lane]) * bp;
 #pragma unroll
         for (int q = 1; q < NW; ++q)
-          if (lane <= s + kl - 32 * q) wf[q] -= from_store<TC, TS>(lk[32 * q + lane]) * bp;
+          if (s + kl - 32 * q >= 0) {  // warp-uniform: the band reaches register q at all
+            if (lane <= s + kl - 32 * q) wf[q] -= from_store<TC, TS>(lk[32 * q + lane]) * bp;
+          }
+      };
+      if (rows == CH) {
+#pragma unroll
+        for (int kk = 0; kk < CH; ++kk) fstep(kk);
+      } else {
+        for (int kk = 0; kk < rows; ++kk) fstep(kk);
       }
       if (t == nc - 1) {  // forward done: the remaining blocks are final
 #pragma unroll
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
         wb[NB - 1] = tn >= 0 ? buf[tn] : (TC)0;
       }
       const int s0 = k0 & 31;
-      for (int kk = rows - 1; kk >= 0; --kk) {
+      auto bstep = [&](int kk) {
         const int s = s0 + kk;
         const TS* uk = data + kk * ucol + s;  // uk[32 q - lane] multiplies row 32 (mb - q) + lane
         const TC xk = __shfl_sync(FULL, wb[0], s) * from_store<TC, TS>(uk[-s]);
@@ -419,7 +427,15 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
         if (lane < s && lane >= s - ku2) wb[0] -= from_store<TC, TS>(uk[-lane]) * xk;
 #pragma unroll
         for (int q = 1; q < NB; ++q)
-          if (lane >= s + 32 * q - ku2) wb[q] -= from_store<TC, TS>(uk[32 * q - lane]) * xk;
+          if (s + 32 * q - ku2 <= 31) {  // warp-uniform: the band reaches register q at all
+            if (lane >= s + 32 * q - ku2) wb[q] -= from_store<TC, TS>(uk[32 * q - lane]) * xk;
+          }
+      };
+      if (rows == CH) {
+#pragma unroll
+        for (int kk = CH - 1; kk >= 0; --kk) bstep(kk);
+      } else {
+        for (int kk = rows - 1; kk >= 0; --kk) bstep(kk);
       }
       if (t == total - 1 && lane < n) buf[lane] = wb[0];  // block 0
     }
