@@ -193,7 +193,7 @@ def max_over_ranks(world, x: float) -> float:
 
 
 def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, measure_e2e: bool,
-                apply_variant: int = -1, learned: bool = False):
+                apply_variant: int = -1, learned: bool = False, use_graph: int = 1):
     import numpy as np
     import torch
 
@@ -203,7 +203,7 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
     w = inputs.workload(WORKLOAD)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
                                 dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant,
-                                guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV)
+                                guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV, use_graph=use_graph)
     # a stream of its own: GMRES cycles run as captured graphs whenever per-apply timing is off
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
     net = None
@@ -391,6 +391,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16", "bf16_learned"],
                     help="run one factor-precision variant only (profiling runs)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="profiling aid: run GMRES cycles from the host loop (every launch visible to ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
     ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
@@ -436,7 +438,8 @@ def main():
         if args.variant in ("all", name):
             variants[name] = run_variant(prec, args.steps, args.warmup, world, local,
                                          measure_e2e=(name == "bf16_learned" or args.variant != "all"),
-                                         apply_variant=args.apply_variant, learned=lg)
+                                         apply_variant=args.apply_variant, learned=lg,
+                                         use_graph=0 if args.no_graph else 1)
     head = variants["bf16_learned" if "bf16_learned" in variants else args.variant]
     peak, peak_kind = measured_peaks()
     achieved = head["apply_bytes"] / (head["apply_ms_avg"] * 1e-3) / 1e9

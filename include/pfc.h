@@ -87,8 +87,9 @@ typedef struct {
   int energy_scaled;
   /* 2D Schwarz apply launch shape (steps per bulk copy x warps per CTA):
      0 default, 1 half-length copies, 2 half-length copies and 2-warp CTAs,
-     3 double-length copies; -1 (default) times every shape on the first
-     factorisation and keeps the fastest (pfc_get_tuning reports the pick).
+     3 double-length copies, 4 two subdomains per warp (16 lanes each);
+     -1 (default) times every shape on the first factorisation and keeps the
+     fastest (pfc_get_tuning reports the pick).
      Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0. */
   int apply_variant;
   /* pfc_run only: a step whose Newton or GMRES iteration fails (PFC_ENEWTON,
@@ -213,7 +214,7 @@ int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, 
                      long long* kernel_launches);
 
 /* Autotuner report (2D).  *apply_variant: the Schwarz apply kernel in use
-   (pfc_params.apply_variant numbering).  apply_ms (optional, 4 floats): the
+   (pfc_params.apply_variant numbering).  apply_ms (optional, 5 floats): the
    mean device milliseconds of one apply measured per kernel at the first
    factorisation, -1 for kernels not timed (not tuned yet, an explicit variant,
    or one that cannot run the blocks).  *graph (optional): 1 once GMRES cycles

@@ -6,10 +6,11 @@
 // bound by the FP64 pipe; here every value is an unevaluated sum hi + lo of two
 // floats (48 significand bits, relative rounding about 2^-48 per operation) and
 // the stencil runs on the FP32 pipe with error-free transformations: Knuth's
-// two-sum for additions and an FMA-based two-product for products.  Only the
-// conversions of the FP64 inputs and the output use the FP64 pipe (3 operations
-// per value).  All primitives use the _rn intrinsics so that the compiler
-// cannot contract or reassociate them.
+// two-sum for additions and an FMA-based two-product for products.  The FP64
+// inputs are split into hi + lo by integer operations on their bit patterns (the
+// hardware's double-float conversions run on the FP64 pipe, as slowly as the FP64
+// stencil itself); the output takes one FP64 addition.  All primitives use the
+// _rn intrinsics so that the compiler cannot contract or reassociate them.
 //
 // The plain FP64 path keeps k_jvp2d; this kernel serves F32/BF16-factor solves.
 #include "pfc_internal.cuh"
@@ -30,11 +31,34 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// hi = x with its significand cut to 24 bits (toward zero), lo = the remaining 29
+// bits rounded to 24: hi + lo = x to 48 bits.  Values below 2^-126 in magnitude
+// (far below any the scheme produces) become 0; |lo| below 2^-126 becomes 0.
 __device__ __forceinline__ ff ff_of(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7ffu) - 1023;  // unbiased exponent
+  if (e < -126) return {0.0f, 0.0f};
+  const unsigned frac23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | frac23);
+  const unsigned rest = l32 & 0x1fffffffu;  // 29 bits worth 2^(e - 52) each
+  float lo = 0.0f;
+  if (rest != 0u && e - 52 >= -126)  // the scale 2^(e - 52) is a normal float
+    lo = __fmul_rn(__uint2float_rn(rest), __uint_as_float((unsigned)(e - 52 + 127) << 23));
+  return {hi, sign ? -lo : lo};
 }
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+// Exact widening of a float by its bit pattern (no FP64-pipe conversion).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u) return 0.0;  // zero (no subnormals here: see ff_of)
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ ff two_sum(float a, float b) {

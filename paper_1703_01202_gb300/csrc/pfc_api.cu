@@ -285,7 +285,7 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs;
+      tabs, feat, iargs, order;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -353,6 +353,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->status = L.take(sizeof(int) * 4);
   pl->tabs = L.take(sizeof(double*) * 2 * pfc::kMaxVecs);
   pl->iargs = L.take(sizeof(pfc::IterArgs));
+  pl->order = L.take(sizeof(int) * (pl->nblocks + 16));
   pl->feat = d3 ? 0 : L.take(vec * 3);
   if (d3) {
     const Shapes3& S = pl->sh3;
@@ -915,6 +916,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->status_dev = (int*)at(pl.status);
   s->feat = g->dim == 2 ? (double*)at(pl.feat) : nullptr;
   s->ia = (pfc::IterArgs*)at(pl.iargs);
+  s->fs.order = (const int*)at(pl.order);
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess ||
@@ -925,6 +927,23 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   std::vector<BlockDesc> blocks;
   int nm, km;
   build_blocks(g, p, &blocks, &nm, &km);
+  // two-subdomains-per-warp order: blocks grouped by extent, each group padded to an even count with -1,
+  // so the first slot of every warp is a real block and both slots of a warp share the extent
+  std::vector<int> order;
+  {
+    std::vector<int> idx(blocks.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+      return std::make_pair(blocks[a].by, blocks[a].bx) < std::make_pair(blocks[b].by, blocks[b].bx);
+    });
+    for (size_t i = 0; i < idx.size(); ++i) {
+      order.push_back(idx[i]);
+      const bool last = i + 1 == idx.size() || blocks[idx[i + 1]].bx != blocks[idx[i]].bx ||
+                        blocks[idx[i + 1]].by != blocks[idx[i]].by;
+      if (last && order.size() % 2) order.push_back(-1);
+    }
+  }
+  s->fs.norder = (int)order.size();
   {  // algorithmic bytes of one Schwarz apply: factors + pivots read, block gather, core write
     const double es = p->factor_prec == PFC_F64 ? 8.0 : (p->factor_prec == PFC_F32 ? 4.0 : 2.0);
     double bytes = 0.0;
@@ -994,6 +1013,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   for (int i = 0; i < p->gmres_restart; ++i) tabs[pfc::kMaxVecs + i] = s->Zbuf + (size_t)i * s->g.n;
   if (cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
                       s->st) != cudaSuccess ||
+      cudaMemcpyAsync((void*)s->fs.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s->st) !=
+          cudaSuccess ||
       cudaMemcpyAsync(s->lin_dev, lin, lin_bytes, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
       cudaMemcpyAsync((void*)s->vtab, tabs.data(), sizeof(double*) * tabs.size(), cudaMemcpyHostToDevice, s->st) !=
           cudaSuccess ||

@@ -101,8 +101,10 @@ struct FactorStore {
   int kl_max;
   int n_max;
   int variant;       // apply launch shape, 0 .. kApplyVariants - 1
+  const int* order;  // two-per-warp shape: blocks grouped by extent, each group padded to an even count with -1
+  int norder;
 };
-constexpr int kApplyVariants = 4;
+constexpr int kApplyVariants = 5;
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,

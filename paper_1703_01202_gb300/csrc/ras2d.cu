@@ -84,6 +84,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+__host__ __device__ inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Four consecutive values from a 16-byte aligned shared-memory address.
+__device__ __forceinline__ void load4(const float* p, float* out) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  out[0] = v.x;
+  out[1] = v.y;
+  out[2] = v.z;
+  out[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* out) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  out[0] = a.x;
+  out[1] = a.y;
+  out[2] = b.x;
+  out[3] = b.y;
+}
+
 // Entry (r, c) of A_k = R_k J R_k^T, J = I/dt - (1/2) Delta_d L_gamma - Delta_d diag(q) (Eq. Jacobi).
 // qb: q on the block (block-local order), lin: the 7x7 table of -(1/2) Delta_d L_gamma.
 __device__ __forceinline__ double jac_entry(int bx, double ih2, const double* qb, double idt, const double* lin,
@@ -114,7 +132,8 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
   double* qb = reinterpret_cast<double*>(smem);  // q on the block, block-local order
   double* lin_s = qb + fs.n_max;                 // 7 x 7 stencil table
   constexpr int PM = RING / 2 - 1;               // window positions (<= RING/2 of them) map by pos & PM
-  TC* A = reinterpret_cast<TC*>(lin_s + 49);     // W rows x RING column slots
+  // W rows x RING column slots, 16-byte aligned so that lv / roff (below) can be read 4 at a time
+  TC* A = reinterpret_cast<TC*>(smem + rup((size_t)(fs.n_max + 49) * sizeof(double), 16));
   TC* lv = A + (size_t)W * RING;                 // multipliers of the current step
   TC* uv = lv + RING;                            // U row of the current step
   int* slot = reinterpret_cast<int*>(uv + RING);  // window position & PM -> row slot
@@ -198,16 +217,24 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
     // U column k's entries above the band (j > ku2) stay zero for the bulk copies
     for (int j = ku2 + 1 + tid; j < ucol; j += nt) U[(size_t)k * ucol + j] = to_store<TS>(0.0);
     __syncthreads();
-    // rank-1 update of the active window
+    // rank-1 update of the active window; multipliers and row offsets are read four at a time
+    // (16-byte loads), so shared memory carries about half the traffic of one load per row
     const int rows = min(kl, n - 1 - k);
+    const int rows4 = rows & ~3;
     for (int j = 1 + tid; j <= ku2; j += nt) {
       const TC u = uv[j];
       if (u != (TC)0 && k + j < n) {
         const int cw = (k + j) & (RING - 1);
-        for (int i = 0; i < rows; ++i) {
-          TC* a = &A[roff[i] + cw];
-          *a = *a - lv[i] * u;
+        for (int i = 0; i < rows4; i += 4) {
+          const int4 o = *reinterpret_cast<const int4*>(roff + i);
+          TC l[4];
+          load4(lv + i, l);
+          A[o.x + cw] -= l[0] * u;
+          A[o.y + cw] -= l[1] * u;
+          A[o.z + cw] -= l[2] * u;
+          A[o.w + cw] -= l[3] * u;
         }
+        for (int i = rows4; i < rows; ++i) A[roff[i] + cw] -= lv[i] * u;
       }
     }
     // the column entering the band must start at zero in the rows that stay
@@ -250,7 +277,6 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
 struct ApplySmem {
   size_t stage, buf, piv, total;
 };
-__host__ __device__ inline size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 template <typename TC, typename TS, int CH>
 __host__ __device__ inline ApplySmem apply_smem(int lrow, int ucol, int nmax) {
   ApplySmem s;
@@ -263,12 +289,14 @@ __host__ __device__ inline ApplySmem apply_smem(int lrow, int ucol, int nmax) {
   return s;
 }
 
-template <typename TC, typename TS, int CH, int WPC, int NW>
+template <typename TC, typename TS, int CH, int WPC, int NW, int LB>
 __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc* __restrict__ blocks, int nblocks,
                                                           FactorStore fs, const double* __restrict__ r,
                                                           const double* __restrict__ rscale, double* __restrict__ z,
                                                           const int* __restrict__ skip, int* __restrict__ err,
                                                           const IterArgs* __restrict__ ia) {
+  constexpr int G = 32 / LB;  // subdomains per warp, LB lanes each
+  static_assert(G * LB == 32 && (G == 1 || G == 2), "one or two subdomains per warp");
   if (skip && *skip) return;
   if (ia) {  // graph mode: this Arnoldi iteration's vectors
     r = ia->v;
@@ -277,11 +305,27 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   }
   extern __shared__ __align__(128) unsigned char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * WPC + w;
-  if (b >= nblocks) return;  // warp-uniform; no CTA-wide barrier follows
+  const int gi = lane / LB, li = lane % LB;
+  // subdomain of this lane group: consecutive blocks for one per warp; for two per warp the
+  // order of fs.order (blocks grouped by extent, every group padded to an even count with -1)
+  const int wslot = (blockIdx.x * WPC + w) * G;
+  int b;
+  bool valid = true;
+  if (G == 1) {
+    b = wslot;
+    if (b >= nblocks) return;  // warp-uniform; no CTA-wide barrier follows
+  } else {
+    if (wslot >= fs.norder || fs.order[wslot] < 0) return;  // warp-uniform
+    b = fs.order[wslot + gi];
+    valid = b >= 0;
+    if (!valid) b = fs.order[wslot];  // a padding group shadows its partner (same extent), stores nothing
+  }
   const int lrow = fs.lrow, ucol = fs.ucol;
   const ApplySmem lay = apply_smem<TC, TS, CH>(lrow, ucol, fs.n_max);
-  unsigned char* base = smem + (size_t)w * lay.total;
+  // groups of one warp are skewed by LB storage elements: their lanes read the same row
+  // offsets and would otherwise hit the same shared-memory banks
+  const size_t gstride = lay.total + (G > 1 ? LB * sizeof(TS) : 0);
+  unsigned char* base = smem + (size_t)w * rup(G * gstride, 128) + gi * gstride;
   auto stage = [&](int st) { return reinterpret_cast<TS*>(base + st * lay.stage); };
   TC* buf = reinterpret_cast<TC*>(base + 2 * lay.stage);
   uint8_t* pv = base + 2 * lay.stage + lay.buf;
@@ -296,7 +340,7 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   const int nc = (n + CH - 1) / CH;
   const int total = 2 * nc;  // forward chunks 0..nc-1, then backward chunks nc-1..0
 
-  auto issue = [&](int t) {  // lane 0: bulk-copy chunk t into stage t & 1
+  auto issue = [&](int t) {  // group lane 0: bulk-copy chunk t into stage t & 1
     const int st = t & 1;
     const int c = t < nc ? t : 2 * nc - 1 - t;
     const int rows = min(CH, n - c * CH);
@@ -306,47 +350,48 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
     mbar_expect_tx(&bar[st], bytes);
     bulk_g2s(stage(st), src, bytes, &bar[st]);
   };
-  if (lane == 0) {
+  if (valid && li == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
     issue(0);
     if (total > 1) issue(1);
   }
-  for (int t = lane; t < n; t += 32) {  // restriction R_k^delta (periodic wrap) and pivots
+  for (int t = li; t < n; t += LB) {  // restriction R_k^delta (periodic wrap) and pivots
     const int a = t % bx, c = t / bx;
-    buf[t] = (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)];
-    pv[t] = piv[t];
+    buf[t] = valid ? (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] : (TC)0;
+    pv[t] = valid ? piv[t] : (uint8_t)0;
   }
   __syncwarp();
-  // The active window of each triangular solve lives in registers: lane l holds
-  // the entries congruent to l mod 32, one register per 32-entry block.  Forward
-  // window [k, k+kl] (kl <= 32 (NW - 1)): blocks mf..mf+NW-1 in wf[], mf = k / 32.
-  // Backward window [k-ku2, k] (ku2 <= 32 (NB - 1)): blocks mb..mb-NB+1 in wb[],
-  // mb = k / 32.  A chunk of CH steps never crosses a 32-step block (CH divides
-  // 32), so the registers rotate only between chunks, when the finished block
-  // (final y or x values) goes to shared memory.  Inside a block, step k = 32 m + s
-  // touches register q of lane l exactly when l passes one threshold in s, and
-  // the row interchange is one predicated write into the lane holding the pivot
-  // row; the pivot and y_k / x_k values reach every lane by warp shuffles.
-  // Entries past n - 1 (forward) or below 0 (backward) may hold junk: no step
-  // reads them into a valid entry and they are never stored.
+  // The active window of each triangular solve lives in registers: lane li of a group
+  // holds the entries congruent to li mod LB, one register per LB-entry block.  Forward
+  // window [k, k+kl] (kl <= LB (NW - 1)): blocks mf..mf+NW-1 in wf[], mf = k / LB.
+  // Backward window [k-ku2, k] (ku2 <= LB (NB - 1)): blocks mb..mb-NB+1 in wb[],
+  // mb = k / LB.  A chunk of CH steps never crosses an LB-step block (CH divides LB),
+  // so the registers rotate only between chunks, when the finished block (final y or
+  // x values) goes to shared memory.  Inside a block, step k = LB m + s touches
+  // register q of lane li exactly when li passes one threshold in s, and the row
+  // interchange is one predicated write into the lane holding the pivot row; the
+  // pivot and y_k / x_k values reach the group's lanes by shuffles of width LB.
+  // Entries past n - 1 (forward) or below 0 (backward) may hold junk: no step reads
+  // them into a valid entry and they are never stored.  A padding group (valid ==
+  // false) runs the same instructions on zeros and unread stage memory.
   constexpr int NB = 2 * NW - 1;
-  static_assert(32 % CH == 0, "a chunk stays inside one 32-step block");
+  static_assert(LB % CH == 0, "a chunk stays inside one LB-step block");
   const unsigned FULL = 0xffffffffu;
   int mf = 0, mb = 0;
   TC wf[NW], wb[NB];
 #pragma unroll
-  for (int q = 0; q < NW; ++q) wf[q] = lane + 32 * q < n ? buf[lane + 32 * q] : (TC)0;
+  for (int q = 0; q < NW; ++q) wf[q] = li + LB * q < n ? buf[li + LB * q] : (TC)0;
 #pragma unroll
   for (int q = 0; q < NB; ++q) wb[q] = (TC)0;
   uint32_t phase0 = 0, phase1 = 0;
   for (int t = 0; t < total; ++t) {
     const int st = t & 1;
-    const bool ok = mbar_wait_bounded(&bar[st], st ? phase1 : phase0);
+    const bool ok = valid ? mbar_wait_bounded(&bar[st], st ? phase1 : phase0) : true;
     if (st) phase1 ^= 1; else phase0 ^= 1;
     if (!__all_sync(FULL, ok)) {  // give up: record, drain the copies in flight, leave
-      if (lane == 0) {
+      if (valid && li == 0) {
         atomicExch(err, PFC_ETIMEOUT);
         mbar_wait_bounded(&bar[st], st ? phase1 ^ 1 : phase0 ^ 1);
         if (t + 1 < total) mbar_wait_bounded(&bar[st ^ 1], st ? phase0 : phase1);
@@ -356,37 +401,37 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
     const TS* data = stage(st);
     if (t < nc) {  // forward: row interchange P_k, then elimination L_k
       const int c = t, k0 = c * CH, rows = min(CH, n - k0);
-      if ((k0 >> 5) != mf) {  // entered block mf + 1: block mf holds final y
-        if (32 * mf + lane < n) buf[32 * mf + lane] = wf[0];
+      if (k0 / LB != mf) {  // entered block mf + 1: block mf holds final y
+        if (LB * mf + li < n) buf[LB * mf + li] = wf[0];
         ++mf;
 #pragma unroll
         for (int q = 0; q < NW - 1; ++q) wf[q] = wf[q + 1];
-        const int tn = 32 * (mf + NW - 1) + lane;
+        const int tn = LB * (mf + NW - 1) + li;
         wf[NW - 1] = tn < n ? buf[tn] : (TC)0;
       }
-      const int s0 = k0 & 31;
+      const int s0 = k0 % LB;
       auto fstep = [&](int kk) {
         const int s = s0 + kk, k = k0 + kk;
-        const TS* lk = data + kk * lrow - s - 1;  // lk[32 q + lane] multiplies row 32 (mf + q) + lane
-        const int sp = s + pv[k];                 // pivot row p = 32 mf + sp
-        const int dp = sp >> 5, lp = sp & 31;
-        const TC bk = __shfl_sync(FULL, wf[0], s);
+        const TS* lk = data + kk * lrow - s - 1;  // lk[LB q + li] multiplies row LB (mf + q) + li
+        const int sp = s + pv[k];                 // pivot row p = LB mf + sp
+        const int dp = sp / LB, lp = sp % LB;
+        const TC bk = __shfl_sync(FULL, wf[0], s, LB);
         TC src = wf[0];
 #pragma unroll
         for (int q = 1; q < NW; ++q)
           if (dp == q) src = wf[q];
-        const TC bp = __shfl_sync(FULL, src, lp);
-        if (lane == lp) {  // interchange: row p receives b_k
+        const TC bp = __shfl_sync(FULL, src, lp, LB);
+        if (li == lp) {  // interchange: row p receives b_k
 #pragma unroll
           for (int q = 0; q < NW; ++q)
             if (dp == q) wf[q] = bk;
         }
-        if (lane == s) wf[0] = bp;  // y_k
-        if (lane > s && lane <= s + kl) wf[0] -= from_store<TC, TS>(lk[lane]) * bp;
+        if (li == s) wf[0] = bp;  // y_k
+        if (li > s && li <= s + kl) wf[0] -= from_store<TC, TS>(lk[li]) * bp;
 #pragma unroll
         for (int q = 1; q < NW; ++q)
-          if (s + kl - 32 * q >= 0) {  // warp-uniform: the band reaches register q at all
-            if (lane <= s + kl - 32 * q) wf[q] -= from_store<TC, TS>(lk[32 * q + lane]) * bp;
+          if (s + kl - LB * q >= 0) {  // warp-uniform: the band reaches register q at all
+            if (li <= s + kl - LB * q) wf[q] -= from_store<TC, TS>(lk[LB * q + li]) * bp;
           }
       };
       if (rows == CH) {
@@ -398,37 +443,37 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
       if (t == nc - 1) {  // forward done: the remaining blocks are final
 #pragma unroll
         for (int q = 0; q < NW; ++q)
-          if (32 * (mf + q) + lane < n) buf[32 * (mf + q) + lane] = wf[q];
+          if (LB * (mf + q) + li < n) buf[LB * (mf + q) + li] = wf[q];
       }
     } else {  // backward, column oriented: x_k = y_k / u_kk, y_{k-j} -= u_{k-j,k} x_k
       const int c = 2 * nc - 1 - t, k0 = c * CH, rows = min(CH, n - k0);
       if (t == nc) {  // y complete: load the top of the backward window
         __syncwarp();
-        mb = (n - 1) >> 5;
+        mb = (n - 1) / LB;
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-          const int tb = 32 * (mb - q) + lane;
+          const int tb = LB * (mb - q) + li;
           wb[q] = (tb >= 0 && tb < n) ? buf[tb] : (TC)0;
         }
-      } else if ((k0 >> 5) != mb) {  // entered block mb - 1: block mb holds final x
-        if (32 * mb + lane < n) buf[32 * mb + lane] = wb[0];
+      } else if (k0 / LB != mb) {  // entered block mb - 1: block mb holds final x
+        if (LB * mb + li < n) buf[LB * mb + li] = wb[0];
         --mb;
 #pragma unroll
         for (int q = 0; q < NB - 1; ++q) wb[q] = wb[q + 1];
-        const int tn = 32 * (mb - NB + 1) + lane;
+        const int tn = LB * (mb - NB + 1) + li;
         wb[NB - 1] = tn >= 0 ? buf[tn] : (TC)0;
       }
-      const int s0 = k0 & 31;
+      const int s0 = k0 % LB;
       auto bstep = [&](int kk) {
         const int s = s0 + kk;
-        const TS* uk = data + kk * ucol + s;  // uk[32 q - lane] multiplies row 32 (mb - q) + lane
-        const TC xk = __shfl_sync(FULL, wb[0], s) * from_store<TC, TS>(uk[-s]);
-        if (lane == s) wb[0] = xk;
-        if (lane < s && lane >= s - ku2) wb[0] -= from_store<TC, TS>(uk[-lane]) * xk;
+        const TS* uk = data + kk * ucol + s;  // uk[LB q - li] multiplies row LB (mb - q) + li
+        const TC xk = __shfl_sync(FULL, wb[0], s, LB) * from_store<TC, TS>(uk[-s]);
+        if (li == s) wb[0] = xk;
+        if (li < s && li >= s - ku2) wb[0] -= from_store<TC, TS>(uk[-li]) * xk;
 #pragma unroll
         for (int q = 1; q < NB; ++q)
-          if (s + 32 * q - ku2 <= 31) {  // warp-uniform: the band reaches register q at all
-            if (lane >= s + 32 * q - ku2) wb[q] -= from_store<TC, TS>(uk[32 * q - lane]) * xk;
+          if (s + LB * q - ku2 <= LB - 1) {  // warp-uniform: the band reaches register q at all
+            if (li >= s + LB * q - ku2) wb[q] -= from_store<TC, TS>(uk[LB * q - li]) * xk;
           }
       };
       if (rows == CH) {
@@ -437,14 +482,15 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
       } else {
         for (int kk = rows - 1; kk >= 0; --kk) bstep(kk);
       }
-      if (t == total - 1 && lane < n) buf[lane] = wb[0];  // block 0
+      if (t == total - 1 && li < n) buf[li] = wb[0];  // block 0
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
-    if (lane == 0 && t + 2 < total) issue(t + 2);
+    if (valid && li == 0 && t + 2 < total) issue(t + 2);
   }
   __syncwarp();
+  if (!valid) return;
   const double sc = rscale ? *rscale : 1.0;
-  for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
+  for (int t = li; t < n; t += LB) {  // extension (R_k^0)^T: core points only
     const int a = t % bx, c = t / bx;
     if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
       z[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] = sc * (double)buf[t];
@@ -465,15 +511,19 @@ void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const d
   count_launches(1);
 }
 
-template <typename TC, typename TS, int CH, int WPC, int NW = 3>
+template <typename TC, typename TS, int CH, int WPC, int NW = 3, int LB = 32>
 void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                     const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
                     const IterArgs* ia) {
+  constexpr int G = 32 / LB;
   const ApplySmem lay = apply_smem<TC, TS, CH>(fs.lrow, fs.ucol, fs.n_max);
-  const size_t smem = WPC * lay.total;
-  cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ras_apply2d<TC, TS, CH, WPC, NW><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale,
-                                                                                    z, skip, err, ia);
+  const size_t gstride = lay.total + (G > 1 ? LB * sizeof(TS) : 0);
+  const size_t smem = WPC * rup(G * gstride, 128);
+  const int warps = G == 1 ? nblocks : fs.norder / G;
+  cudaFuncSetAttribute(k_ras_apply2d<TC, TS, CH, WPC, NW, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_ras_apply2d<TC, TS, CH, WPC, NW, LB><<<(warps + WPC - 1) / WPC, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r,
+                                                                                       rscale, z, skip, err, ia);
   count_launches(1);
 }
 
@@ -491,7 +541,7 @@ bool apply_variant_ok(int v, int prec, int kl_max) {
 size_t factor_smem_bytes(int prec, int kl, int n_max) {
   const int ring = (2 * kl + 2 <= 128) ? 128 : 256;
   const size_t tc = prec == PFC_F64 ? 8 : 4;
-  return (size_t)(n_max + 49) * 8 + (size_t)((kl + 1) * ring + 2 * ring) * tc + ring * sizeof(int) + 16;
+  return rup((size_t)(n_max + 49) * 8, 16) + (size_t)((kl + 1) * ring + 2 * ring) * tc + ring * sizeof(int) + 16;
 }
 
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
@@ -510,7 +560,8 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
   // Launch shapes (chunk length CH = steps per bulk copy, WPC = warps per CTA):
   // variant 0: stages of about 3.5 KB for every storage type, 4 warps per CTA;
   // 1: half the chunk (twice the resident warps per SM), 2: half the chunk and
-  // 2 warps per CTA (finer packing), 3: twice the chunk (fewer, larger copies).
+  // 2 warps per CTA (finer packing), 3: twice the chunk (fewer, larger copies);
+  // 4: two subdomains per warp, 16 lanes each (5 + 9 window registers per lane).
   if (fs.kl_max > 64) {  // blocks wider than 21 cells: the wide-window kernel, default shape
     if (fs.prec == PFC_F64)
       apply_dispatch<double, double, 4, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
@@ -523,6 +574,8 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
       case 1: apply_dispatch<double, double, 2, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 2: apply_dispatch<double, double, 2, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 3: apply_dispatch<double, double, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 4: apply_dispatch<double, double, 4, 4, 5, 16>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
+        break;
       default: apply_dispatch<double, double, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   } else if (fs.prec == PFC_F32) {
@@ -530,6 +583,8 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
       case 1: apply_dispatch<float, float, 4, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 2: apply_dispatch<float, float, 4, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 3: apply_dispatch<float, float, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 4: apply_dispatch<float, float, 8, 4, 5, 16>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
+        break;
       default: apply_dispatch<float, float, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   } else {
@@ -538,6 +593,8 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
       case 1: apply_dispatch<float, B16, 8, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 2: apply_dispatch<float, B16, 8, 2>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
       case 3: apply_dispatch<float, B16, 32, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia); break;
+      case 4: apply_dispatch<float, B16, 8, 4, 5, 16>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
+        break;
       default: apply_dispatch<float, B16, 16, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     }
   }

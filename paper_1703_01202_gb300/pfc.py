@@ -290,9 +290,9 @@ class Solver:
 
     def tuning(self) -> dict:
         v, gr = c_int(), c_int()
-        ms = (c_float * 4)()
+        ms = (c_float * 5)()
         _check(lib().pfc_get_tuning(self.handle, ctypes.byref(v), ms, ctypes.byref(gr)), "pfc_get_tuning")
-        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(4)], "graph": gr.value}
+        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(5)], "graph": gr.value}
 
     # -- test hooks on device tensors
     def residual(self, Phi, phin, dt: float):
