@@ -150,6 +150,17 @@ void pfc_destroy(pfc_state* s);
 int pfc_set_field(pfc_state* s, const double* phi, int on_device);
 /* Copies phi^n out (N values) to a device (on_device = 1) or host buffer. */
 int pfc_get_field(pfc_state* s, double* out, int on_device);
+/* Checkpoint and resume of the time stepping: pfc_save writes phi^n,
+   phi^{n-1} and the adaptive-step history (energies of the last two steps,
+   previous dt) with the grid, h and eps to the host file `path` (binary, host
+   byte order); pfc_load restores them into a state created with the same grid,
+   h and eps, so that the following steps equal those of the saved run.
+   PFC_EINVAL on a file that cannot be written or read, a foreign or corrupt
+   file, or a different grid / h / eps (pfc_load then changes nothing).  Not
+   part of the paper's method. */
+int pfc_save(pfc_state* s, const char* path);
+int pfc_load(pfc_state* s, const char* path);
+
 /* Caller-supplied Newton initial guess for the next pfc_step when
    params.guess == PFC_GUESS_USER (N values, device or host). */
 int pfc_set_guess(pfc_state* s, const double* guess, int on_device);

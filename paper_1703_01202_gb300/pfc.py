@@ -77,6 +77,8 @@ _SIGNATURES = [
     ("pfc_next_dt", c_int, [c_void_p, POINTER(c_double)]),
     ("pfc_step_host", c_int, [c_void_p, c_void_p, c_double, c_void_p, POINTER(pfc_step_info)]),
     ("pfc_profile", c_int, [c_void_p, c_int]),
+    ("pfc_save", c_int, [c_void_p, c_char_p]),
+    ("pfc_load", c_int, [c_void_p, c_char_p]),
     ("pfc_run_batch", c_int, [POINTER(c_void_p), c_int, c_int, c_void_p, POINTER(c_int)]),
     ("pfc_get_tuning", c_int, [c_void_p, POINTER(c_int), POINTER(c_float), POINTER(c_int)]),
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
@@ -220,6 +222,12 @@ class Solver:
         else:
             d = self._dev(phi)
             _check(lib().pfc_set_field(self.handle, c_void_p(d.data_ptr()), 1), "pfc_set_field")
+
+    def save(self, path: str):
+        _check(lib().pfc_save(self.handle, os.fsencode(path)), "pfc_save")
+
+    def load(self, path: str):
+        _check(lib().pfc_load(self.handle, os.fsencode(path)), "pfc_load")
 
     def get_field(self) -> np.ndarray:
         out = np.empty(self.shape, dtype=np.float64)

@@ -235,3 +235,27 @@ def test_invalid_arguments_and_small_workspace(pfc):
     st = pfc.lib().pfc_create(ctypes.byref(g), H, GAMMA, ctypes.byref(p), ctypes.c_void_p(s.ws.data_ptr()),
                               ctypes.c_size_t(1024), None, ctypes.byref(h))
     assert st == pfc.PFC_ENOMEM
+
+
+def test_checkpoint_resume_continues_the_same_run(pfc, tmp_path):
+    """pfc_save after 3 adaptive steps, pfc_load into a fresh state: the next 2
+    steps equal those of the uninterrupted run (fields bitwise, same dt); a state
+    of another grid refuses the file."""
+    shape = (48, 60)
+    phi0 = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=8, seed=11)
+    prm = dict(dt_min=0.01, dt_max=10.0, eta=5000.0)
+    a = solver(pfc, shape, (3, 2), overlap=1, **prm)
+    a.set_field(phi0)
+    a.run(3)
+    path = str(tmp_path / "state.pfc")
+    a.save(path)
+    ra = a.run(2)
+    b = solver(pfc, shape, (3, 2), overlap=1, **prm)
+    b.load(path)
+    rb = b.run(2)
+    assert [r["dt"] for r in ra] == [r["dt"] for r in rb]
+    np.testing.assert_array_equal(a.get_field(), b.get_field())
+    c = solver(pfc, (48, 48), (3, 3), overlap=1, **prm)
+    with pytest.raises(pfc.PfcError) as e:
+        c.load(path)
+    assert e.value.status == pfc.PFC_EINVAL
