@@ -119,6 +119,118 @@ __global__ void __launch_bounds__(NT) k_conv_fwd(int nx, int ny, const TI* __res
   }
 }
 
+// The 32 -> 32 convolutions of the forward pass as an implicit GEMM on the tensor
+// cores: per 16 x 16 tile, D (256 pixels x 32 channels) = sum over the 9 taps of
+// A_tap (256 x 32 input channels, the tile shifted by the tap) times W_tap (32 x 32),
+// in BF16 with FP32 accumulation (mma.sync m16n8k16).  Warp w owns tile rows 2w and
+// 2w+1 (two 16-pixel M tiles) and all 32 output channels (four N tiles); K runs over
+// tap x 32 channels in 18 steps of 16.  The input tile with its periodic halo sits in
+// shared memory pixel-major with channels contiguous (pixel stride 40 elements = 80
+// bytes, so the eight rows of an ldmatrix phase fall on distinct banks); the weights
+// sit tap-major [tap][co][ci] with the same stride.  z and GELU(z) are staged back
+// through shared memory and written as coalesced 16-pixel rows of each channel plane.
+constexpr int kMmaStride = 40;  // BF16 elements per pixel row / per weight row in shared memory
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(NT) k_conv32_fwd_mma(int nx, int ny, const __nv_bfloat16* __restrict__ in,
+                                                       const __nv_bfloat16* __restrict__ W,
+                                                       const float* __restrict__ b, __nv_bfloat16* __restrict__ z,
+                                                       __nv_bfloat16* __restrict__ a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* s_in = reinterpret_cast<__nv_bfloat16*>(smraw);      // [TH][TH][kMmaStride]
+  __nv_bfloat16* s_w = s_in + TH * TH * kMmaStride;                   // [9][32][kMmaStride]
+  float* s_b = reinterpret_cast<float*>(s_w + 9 * 32 * kMmaStride);    // [32]
+  const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
+  const long long N = (long long)nx * ny;
+  for (int i = threadIdx.x; i < 32 * TH * TH; i += NT) {  // input planes -> pixel-major tile
+    const int c = i / (TH * TH), r = i - c * TH * TH;
+    const int ly = r / TH, lx = r - ly * TH;
+    const long long p = wrapi(x0 + lx - 1, nx) + (long long)nx * wrapi(y0 + ly - 1, ny);
+    s_in[(ly * TH + lx) * kMmaStride + c] = in[c * N + p];
+  }
+  for (int i = threadIdx.x; i < 32 * 32 * 9; i += NT) {  // W[co][ci][tap] -> s_w[tap][co][ci]
+    const int co = i / (32 * 9), r = i - co * 32 * 9;
+    const int ci = r / 9, tap = r - ci * 9;
+    s_w[(tap * 32 + co) * kMmaStride + ci] = W[i];
+  }
+  if (threadIdx.x < 32) s_b[threadIdx.x] = b[threadIdx.x];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {  // input channels 16 kc .. 16 kc + 15
+      uint32_t bf[4][2];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {  // two N tiles per ldmatrix.x4
+        const int co = 16 * np + (lane & 7) + ((lane >> 4) << 3);
+        const int ci = 16 * kc + ((lane >> 3) & 1) * 8;
+        ldsm_x4(smem_addr(s_w + (tap * 32 + co) * kMmaStride + ci), bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0],
+                bf[2 * np + 1][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int ty = 2 * warp + mt;  // tile row of this M tile; pixel x = row of the fragment
+        const int px = lane & 15, ci = 16 * kc + (lane >> 4) * 8;
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_addr(s_in + ((ty + 1 + dy) * TH + (px + 1 + dx)) * kMmaStride + ci), a0, a1, a2, a3);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+      }
+    }
+  }
+  __syncthreads();  // the input tile is done: reuse it for the output staging
+  __nv_bfloat16* s_z = s_in;                // [32][256]
+  __nv_bfloat16* s_a = s_in + 32 * NT;      // [32][256]
+  const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int ty = 2 * warp + mt;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int px = gid + (e >> 1) * 8, co = 8 * nt + 2 * tig + (e & 1);
+        const float v = acc[mt][nt][e] + s_b[co];
+        s_z[co * NT + ty * T + px] = __float2bfloat16(v);
+        s_a[co * NT + ty * T + px] = __float2bfloat16(gelu_f(v));
+      }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * NT; i += NT) {  // coalesced 16-pixel rows of every plane
+    const int co = i / NT, r = i - co * NT;
+    const int ty = r / T, tx = r - ty * T;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx < nx && gy < ny) {
+      const long long p = co * N + gx + (long long)nx * gy;
+      z[p] = s_z[i];
+      a[p] = s_a[i];
+    }
+  }
+}
+
 // Gradient through a convolution to its input, times GELU'(z_prev):
 // dz_prev[ci][p] = GELU'(z_prev[ci][p]) * sum_{co,tap} W[co][ci][tap] dz[co][p - off(tap)]
 template <int CIN, int COUT, typename TD>
@@ -282,6 +394,14 @@ void conv_fwd(int nx, int ny, const TI* in, const __nv_bfloat16* W, const float*
   count_launches(1);
 }
 
+void conv32_fwd_mma(int nx, int ny, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* b,
+                    __nv_bfloat16* z, __nv_bfloat16* a, cudaStream_t st) {
+  const size_t smem = sizeof(__nv_bfloat16) * (TH * TH + 9 * 32) * kMmaStride + sizeof(float) * 32;
+  cudaFuncSetAttribute(k_conv32_fwd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_conv32_fwd_mma<<<dim3((nx + T - 1) / T, (ny + T - 1) / T), NT, smem, st>>>(nx, ny, in, W, b, z, a);
+  count_launches(1);
+}
+
 template <int CIN, int COUT, typename TD>
 void conv_bwd_data(int nx, int ny, const TD* dz, const __nv_bfloat16* W, const __nv_bfloat16* zprev, float* dzprev,
                    cudaStream_t st) {
@@ -366,10 +486,8 @@ void cnn_forward(Cnn* c, const double* feat) {
   const float* th = c->theta;
   conv_fwd<3, 32, true, double, __nv_bfloat16>(nx, ny, feat, W + layer_offset(0), th + layer_offset(0) + 32 * 3 * 9,
                                                c->z[0], c->a[0], c->st);
-  conv_fwd<32, 32, true, __nv_bfloat16, __nv_bfloat16>(nx, ny, c->a[0], W + layer_offset(1),
-                                                       th + layer_offset(1) + 32 * 32 * 9, c->z[1], c->a[1], c->st);
-  conv_fwd<32, 32, true, __nv_bfloat16, __nv_bfloat16>(nx, ny, c->a[1], W + layer_offset(2),
-                                                       th + layer_offset(2) + 32 * 32 * 9, c->z[2], c->a[2], c->st);
+  conv32_fwd_mma(nx, ny, c->a[0], W + layer_offset(1), th + layer_offset(1) + 32 * 32 * 9, c->z[1], c->a[1], c->st);
+  conv32_fwd_mma(nx, ny, c->a[1], W + layer_offset(2), th + layer_offset(2) + 32 * 32 * 9, c->z[2], c->a[2], c->st);
   conv_fwd<32, 1, false, __nv_bfloat16, float>(nx, ny, c->a[2], W + layer_offset(3), th + layer_offset(3) + 32 * 9,
                                                c->out, nullptr, c->st);
 }

@@ -117,7 +117,7 @@ __device__ __forceinline__ double jac_entry(int bx, double ih2, const double* qb
 }
 
 template <typename TC, typename TS, int RING>
-__global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
                                                   const double* __restrict__ q, double idt,
                                                   const double* __restrict__ lin, FactorStore fs,
                                                   int* __restrict__ status) {
@@ -132,12 +132,15 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
   double* qb = reinterpret_cast<double*>(smem);  // q on the block, block-local order
   double* lin_s = qb + fs.n_max;                 // 7 x 7 stencil table
   constexpr int PM = RING / 2 - 1;               // window positions (<= RING/2 of them) map by pos & PM
-  // W rows x RING column slots, 16-byte aligned so that lv / roff (below) can be read 4 at a time
-  TC* A = reinterpret_cast<TC*>(smem + rup((size_t)(fs.n_max + 49) * sizeof(double), 16));
-  TC* lv = A + (size_t)W * RING;                 // multipliers of the current step
-  TC* uv = lv + RING;                            // U row of the current step
+  // Row stride RS = RING + 1 (odd): the column walks (pivot search, multipliers, zeroing) touch
+  // one entry per row and would otherwise put every lane on the same shared-memory bank.
+  constexpr int RS = RING + 1;
+  // lv / roff 16-byte aligned so that the rank-1 update can read them 4 at a time
+  TC* lv = reinterpret_cast<TC*>(smem + rup((size_t)(fs.n_max + 49) * sizeof(double), 16));  // multipliers
+  TC* uv = lv + RING;                             // U row of the current step
   int* slot = reinterpret_cast<int*>(uv + RING);  // window position & PM -> row slot
-  int* roff = slot + RING / 2;                    // row offsets (slot * RING) of positions k+1..k+kl
+  int* roff = slot + RING / 2;                    // row offsets (slot * RS) of positions k+1..k+kl
+  TC* A = reinterpret_cast<TC*>(roff + RING / 2);  // W rows x RING column slots, stride RS
   TS* L = (TS*)fs.L + blockIdx.x * fs.strideL;
   TS* U = (TS*)fs.U + blockIdx.x * fs.strideU;
   uint8_t* piv = fs.piv + blockIdx.x * fs.strideP;
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
   __syncthreads();
   for (int idx = tid; idx < W * RING; idx += nt) {
     const int pos = idx / RING, col = idx - pos * RING;
-    A[idx] = (pos < n && col < n) ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, pos, col) : (TC)0;
+    A[pos * RS + col] = (pos < n && col < n) ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, pos, col) : (TC)0;
   }
   __syncthreads();
 
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
       TC best = (TC)-1;
       int bp = k;
       for (int pos = k + tid; pos <= last; pos += 32) {
-        const TC v = abs(A[slot[pos & PM] * RING + kw]);
+        const TC v = abs(A[slot[pos & PM] * RS + kw]);
         if (v > best) {
           best = v;
           bp = pos;
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
         slot[k & PM] = sp;
         slot[bp & PM] = sk;
         piv[k] = (uint8_t)(bp - k);
-        TC d = A[sp * RING + kw];
+        TC d = A[sp * RS + kw];
         if (d == (TC)0) {
           atomicExch(status, PFC_ESINGULAR);
           d = (TC)1;
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
       const int pos = k + 1 + i;
       TC l = (TC)0;
       if (i < kl) {
-        const int off = slot[pos & PM] * RING;
+        const int off = slot[pos & PM] * RS;
         roff[i] = off;
         if (pos < n) l = A[off + kw] * dinv;
         lv[i] = l;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
       const int col = k + j;
       TC u = (TC)0;
       if (j <= ku2 && col < n) {
-        u = A[sk * RING + (col & (RING - 1))];
+        u = A[sk * RS + (col & (RING - 1))];
         U[(size_t)col * ucol + j] = to_store<TS>((double)(j == 0 ? dinv : u));
       }
       if (j <= ku2) uv[j] = u;
@@ -219,13 +222,17 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
     __syncthreads();
     // rank-1 update of the active window; multipliers and row offsets are read four at a time
     // (16-byte loads), so shared memory carries about half the traffic of one load per row
+    // threads split the (row, column) rectangle: 128 column lanes x nt / 128 row bands
     const int rows = min(kl, n - 1 - k);
-    const int rows4 = rows & ~3;
-    for (int j = 1 + tid; j <= ku2; j += nt) {
+    const int bands = nt / 128, band = tid / 128;
+    const int per = ((rows + bands - 1) / bands + 3) & ~3;  // rows per band, a multiple of 4
+    const int i0 = min(rows, band * per), i1 = min(rows, i0 + per);
+    const int i4 = i0 + ((i1 - i0) & ~3);
+    for (int j = 1 + (tid & 127); j <= ku2; j += 128) {
       const TC u = uv[j];
       if (u != (TC)0 && k + j < n) {
         const int cw = (k + j) & (RING - 1);
-        for (int i = 0; i < rows4; i += 4) {
+        for (int i = i0; i < i4; i += 4) {
           const int4 o = *reinterpret_cast<const int4*>(roff + i);
           TC l[4];
           load4(lv + i, l);
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
           A[o.z + cw] -= l[2] * u;
           A[o.w + cw] -= l[3] * u;
         }
-        for (int i = rows4; i < rows; ++i) A[roff[i] + cw] -= lv[i] * u;
+        for (int i = i4; i < i1; ++i) A[roff[i] + cw] -= lv[i] * u;
       }
     }
     // the column entering the band must start at zero in the rows that stay
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(128) k_factor2d(Geo g, const BlockDesc* __rest
     const int rnew = k + 1 + kl;
     if (rnew < n) {
       if (tid == 0) slot[rnew & PM] = sk;
-      TC* row = &A[sk * RING];
+      TC* row = &A[sk * RS];
       const int base = k + 1;
       const int ar = rnew % bx, br = rnew / bx;
       for (int t = tid; t < RING; t += nt) {
@@ -503,10 +510,10 @@ void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const d
   const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max);
   if (2 * fs.kl_max + 2 <= 128) {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d<TC, TS, 128><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    k_factor2d<TC, TS, 128><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status);
   } else {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d<TC, TS, 256><<<nblocks, 128, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    k_factor2d<TC, TS, 256><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status);
   }
   count_launches(1);
 }
@@ -536,12 +543,13 @@ bool apply_variant_ok(int v, int prec, int kl_max) {
 }
 
 // Dynamic shared memory of the factor kernel: q on the block and the stencil
-// table (FP64), the (kl+1) x RING window plus the multiplier and U-row
+// table (FP64), the (kl+1) x (RING+1) window plus the multiplier and U-row
 // buffers (compute type), the position map and the row offsets.
 size_t factor_smem_bytes(int prec, int kl, int n_max) {
   const int ring = (2 * kl + 2 <= 128) ? 128 : 256;
   const size_t tc = prec == PFC_F64 ? 8 : 4;
-  return rup((size_t)(n_max + 49) * 8, 16) + (size_t)((kl + 1) * ring + 2 * ring) * tc + ring * sizeof(int) + 16;
+  return rup((size_t)(n_max + 49) * 8, 16) + (size_t)((kl + 1) * (ring + 1) + 2 * ring) * tc + ring * sizeof(int) +
+         16;
 }
 
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
