@@ -115,7 +115,7 @@ def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
 
 # The committed network: trajectories of the 1024^2 workload's distribution
 # (three hexagonal seeds, gamma 0.25, adaptive dt) on 512^2 grids.
-DEFAULT_RECIPE = dict(n_traj=48, steps=25, size=512, epochs=12, lr=3e-4, lr_min=3e-5, seed=0, seed0=2000)
+DEFAULT_RECIPE = dict(n_traj=96, steps=25, size=512, epochs=20, lr=3e-4, lr_min=3e-5, seed=0, seed0=2000)
 WEIGHTS = "guess_net.npz"
 
 
