@@ -401,7 +401,7 @@ def main():
                     help="profiling aid: run GMRES cycles from the host loop (every launch visible to ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
-    ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+    ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
                     help="2D Schwarz apply kernel (-1: autotuned at the first factorisation)")
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
                     help="profiling aid: run one kernel family repeatedly on the workload (no bench line)")

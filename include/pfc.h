@@ -85,12 +85,16 @@ typedef struct {
   /* Adaptive time step, Eq. (sencondt); energy_scaled = 1 feeds F_d/|Omega|. */
   double dt_min, dt_max, eta;
   int energy_scaled;
-  /* 2D Schwarz apply launch shape (steps per bulk copy x warps per CTA):
-     0 default, 1 half-length copies, 2 half-length copies and 2-warp CTAs,
-     3 double-length copies, 4 two subdomains per warp (16 lanes each);
-     -1 (default) times every shape on the first factorisation and keeps the
+  /* 2D Schwarz apply kernel.  Per-step triangular solves (steps per bulk copy
+     x warps per CTA): 0 default, 1 half-length copies, 2 half-length copies and
+     2-warp CTAs, 3 double-length copies, 4 two subdomains per warp (16 lanes
+     each); these five give bitwise identical results.  5: chunked solves, the
+     same factors regrouped 8 elimination steps at a time (a row permutation and
+     a dense 8-column product per group, built after each factorisation; equal
+     to 0-4 up to rounding in the storage type).
+     -1 (default) times every kernel on the first factorisation and keeps the
      fastest (pfc_get_tuning reports the pick).
-     Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0. */
+     Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0 and 5. */
   int apply_variant;
   /* pfc_run only: a step whose Newton or GMRES iteration fails (PFC_ENEWTON,
      PFC_EGMRES) is retried with half the time step, at most dt_halvings times
@@ -225,7 +229,7 @@ int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, 
                      long long* kernel_launches);
 
 /* Autotuner report (2D).  *apply_variant: the Schwarz apply kernel in use
-   (pfc_params.apply_variant numbering).  apply_ms (optional, 5 floats): the
+   (pfc_params.apply_variant numbering).  apply_ms (optional, 6 floats): the
    mean device milliseconds of one apply measured per kernel at the first
    factorisation, -1 for kernels not timed (not tuned yet, an explicit variant,
    or one that cannot run the blocks).  *graph (optional): 1 once GMRES cycles

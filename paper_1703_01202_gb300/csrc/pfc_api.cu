@@ -69,7 +69,8 @@ struct pfc_state {
   cudaEvent_t ev[2 * pfc::kMaxRestart];
   long long apply_launches;
   double apply_ms;
-  double apply_bytes;
+  double apply_bytes;        // per-step factors (apply variants 0-4)
+  double apply_bytes_chunk;  // chunked records (variant 5)
   // apply kernel picked by timing at the first 2D factorisation (apply_variant = -1)
   bool tuned;
   float tune_ms[pfc::kApplyVariants];
@@ -285,13 +286,15 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs, order;
+      tabs, feat, iargs, order, X;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
   int nblocks, n_max, kl_max;
   size_t sL, sU, sP;
   int lrow, ucol;
+  size_t sX;   // bytes of chunked records per block (2D)
+  int xstage;  // bytes of the largest chunked record
   size_t partial_len;
   Shapes3 sh3;
   size_t sLU3, sWork3, sPad3;
@@ -315,9 +318,19 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
     pl->sL = (size_t)pl->n_max * pl->lrow;
     pl->sU = (size_t)pl->n_max * pl->ucol;
     pl->sP = ((size_t)pl->n_max + 15) / 16 * 16;
+    pl->sX = 0;
+    pl->xstage = 0;
+    for (const BlockDesc& b : blocks) {
+      const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es);
+      pl->sX = std::max(pl->sX, (size_t)cg.nc * (cg.fwd + cg.bwd));
+      pl->xstage = std::max(pl->xstage, (int)std::max(cg.fwd, cg.bwd));
+    }
+    pl->sX = (pl->sX + 127) / 128 * 128;
   } else {
     pl->lrow = pl->ucol = 0;
     pl->sL = pl->sU = pl->sP = 0;
+    pl->sX = 0;
+    pl->xstage = 0;
     build_shapes3(blocks, &pl->sh3);
     pl->sLU3 = (size_t)pl->sh3.nrows_max * 32;
     pl->sWork3 = (size_t)pl->sh3.nrows_max * 64;
@@ -345,6 +358,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->L = L.take(pl->sL * es * pl->nblocks);
   pl->U = L.take(pl->sU * es * pl->nblocks);
   pl->piv = L.take(pl->sP * pl->nblocks);
+  pl->X = L.take(pl->sX * pl->nblocks);
   pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
   pl->lin = L.take(sizeof(double) * 343);
   pl->ctl = L.take(sizeof(GmresCtl));
@@ -454,6 +468,10 @@ void precond(pfc_state* s, const double* r, const double* rscale, double* z, con
 
 // Times every apply kernel that can run the blocks on the factors just made
 // (r = F, z = W: both free at this point) and keeps the fastest.
+bool variant_ok(const pfc_state* s, int v) {
+  return pfc::apply_variant_ok(v, s->fs.prec, s->fs.kl_max, s->fs.xstage, s->fs.n_max);
+}
+
 int tune_apply(pfc_state* s) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
@@ -463,7 +481,7 @@ int tune_apply(pfc_state* s) {
   int rc = PFC_OK;
   for (int v = 0; v < pfc::kApplyVariants && rc == PFC_OK; ++v) {
     s->tune_ms[v] = -1.f;
-    if (!pfc::apply_variant_ok(v, s->fs.prec, s->fs.kl_max)) continue;
+    if (!variant_ok(s, v) || (v == pfc::kChunkedVariant && !s->fs.x_valid)) continue;
     s->fs.variant = v;
     precond(s, s->F, nullptr, s->W, nullptr);  // warm-up
     cudaError_t e = cudaGetLastError();
@@ -504,12 +522,12 @@ int tune_apply(pfc_state* s) {
 int factor_blocks(pfc_state* s, const double* q, double idt) {
   if (s->dim == 2) {
     // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx: blocks at most 42 cells
-    // wide in x); blocks wider than 21 cells run the wide-window apply kernel in its default shape
+    // wide in x); blocks wider than 21 cells run the wide-window apply kernel in its default shape or
+    // the chunked apply
     if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
       return PFC_EINVAL;
-    if (s->p.apply_variant >= 0 && !pfc::apply_variant_ok(s->p.apply_variant, s->fs.prec, s->fs.kl_max))
-      return PFC_EINVAL;
-    if (s->p.apply_variant < 0 && !pfc::apply_variant_ok(0, s->fs.prec, s->fs.kl_max)) return PFC_EINVAL;
+    if (s->p.apply_variant >= 0 && !variant_ok(s, s->p.apply_variant)) return PFC_EINVAL;
+    if (s->p.apply_variant < 0 && !variant_ok(s, 0)) return PFC_EINVAL;
   }
   CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
   if (s->dim == 2)
@@ -517,6 +535,15 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
   else
     pfc::launch_factor3d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->r3, s->status_dev, s->st);
   CU(cudaGetLastError());
+  if (s->dim == 2) {  // chunked records for the chunked apply (in use, or about to be timed)
+    const bool tuning = s->p.apply_variant < 0 && !s->tuned && variant_ok(s, pfc::kChunkedVariant);
+    s->fs.x_valid = 0;
+    if (tuning || s->fs.variant == pfc::kChunkedVariant) {
+      pfc::launch_chunk2d(s->blocks_dev, s->nblocks, s->fs, s->st);
+      CU(cudaGetLastError());
+      s->fs.x_valid = 1;
+    }
+  }
   if (s->dim == 2 && s->p.apply_variant < 0 && !s->tuned) return tune_apply(s);
   return PFC_OK;
 }
@@ -896,6 +923,10 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.strideP = pl.sP;
   s->fs.lrow = pl.lrow;
   s->fs.ucol = pl.ucol;
+  s->fs.X = (unsigned char*)at(pl.X);
+  s->fs.strideX = pl.sX;
+  s->fs.xstage = pl.xstage;
+  s->fs.x_valid = 0;
   s->fs.prec = p->factor_prec;
   s->fs.kl_max = pl.kl_max;
   s->fs.n_max = pl.n_max;
@@ -946,19 +977,22 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.norder = (int)order.size();
   {  // algorithmic bytes of one Schwarz apply: factors + pivots read, block gather, core write
     const double es = p->factor_prec == PFC_F64 ? 8.0 : (p->factor_prec == PFC_F32 ? 4.0 : 2.0);
-    double bytes = 0.0;
+    double bytes = 0.0, bytes_chunk = 0.0;
     for (const BlockDesc& b : blocks) {
       if (g->dim == 2) {
         const double n = (double)b.bx * b.by;
         const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
         const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
         bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
+        const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es);
+        bytes_chunk += (double)cg.nc * (cg.fwd + cg.bwd) + n * 8.0 + (double)b.cx * b.cy * 8.0;
       } else {  // 63 ILU(0) entries per row, row tables, gather, core write
         const double n = (double)b.bx * b.by * b.bz;
         bytes += n * 63.0 * es + n * 8.0 + n * 8.0 + (double)b.cx * b.cy * b.cz * 8.0;
       }
     }
     s->apply_bytes = bytes;
+    s->apply_bytes_chunk = bytes_chunk;
   }
   if (g->dim == 3) {
     const Shapes3& S = pl.sh3;
@@ -1254,7 +1288,8 @@ int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, 
   if (!s) return PFC_EINVAL;
   if (apply_launches) *apply_launches = s->apply_launches;
   if (apply_ms) *apply_ms = s->apply_ms;
-  if (apply_bytes) *apply_bytes = s->apply_bytes;
+  if (apply_bytes)
+    *apply_bytes = s->dim == 2 && s->fs.variant == pfc::kChunkedVariant ? s->apply_bytes_chunk : s->apply_bytes;
   if (kernel_launches) *kernel_launches = pfc::launches_so_far();
   return PFC_OK;
 }

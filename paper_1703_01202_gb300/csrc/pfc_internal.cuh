@@ -103,16 +103,53 @@ struct FactorStore {
   int variant;       // apply launch shape, 0 .. kApplyVariants - 1
   const int* order;  // two-per-warp shape: blocks grouped by extent, each group padded to an even count with -1
   int norder;
+  // Chunked form of the same factors (apply variant kChunkedVariant), one record stream per
+  // block in the order the apply consumes it; built from L, U, piv by launch_chunk2d.
+  unsigned char* X;
+  size_t strideX;  // bytes per block
+  int xstage;      // bytes of the largest record (one TMA stage)
+  int x_valid;     // X holds the chunks of the current factors
 };
-constexpr int kApplyVariants = 5;
+constexpr int kApplyVariants = 6;
+constexpr int kChunkedVariant = 5;
+
+// Chunked triangular solves.  The forward solve P/L of a block advances kChunk
+// elimination steps at a time: the steps k0 .. k0+bc-1 (bc = min(kChunk, n-k0))
+// act on the window of positions [k0, k0+W), W = kChunk + kl, as y <- (I + E) P y,
+// where P is their row interchanges combined and E (W x kChunk, zero on and above
+// the diagonal) collects the multipliers; the backward solve with U takes the
+// same chunks from the bottom: x_c = M1 y_c and y_a += M2 y_c on the ku2 rows
+// above the chunk (M1 = inverse of the chunk's diagonal block of U).
+// Records (16-byte multiples): forward = W permutation bytes rounded up to 16,
+// then W rows of kChunk entries; backward = kChunk + ku2 rows of kChunk entries
+// (rows of M1, then rows of M2 for positions k0-ku2 .. k0-1).
+constexpr int kChunk = 8;
+struct ChunkGeom {
+  int n, kl, ku2, nc, W, H;
+  size_t fwd, bwd;  // record bytes
+};
+__host__ __device__ inline ChunkGeom chunk_geom(int bx, int by, int es) {
+  ChunkGeom c;
+  c.n = bx * by;
+  c.kl = 3 * bx < c.n - 1 ? 3 * bx : c.n - 1;
+  c.ku2 = 2 * c.kl < c.n - 1 ? 2 * c.kl : c.n - 1;
+  c.nc = (c.n + kChunk - 1) / kChunk;
+  c.W = kChunk + c.kl;
+  c.H = kChunk + c.ku2;
+  c.fwd = (size_t)(c.W + 15) / 16 * 16 + (size_t)c.W * kChunk * es;
+  c.bwd = (size_t)c.H * kChunk * es;
+  return c;
+}
+void launch_chunk2d(const BlockDesc* blocks, int nblocks, const FactorStore& fs, cudaStream_t st);
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
                         const IterArgs* ia = nullptr);
 size_t factor_smem_bytes(int prec, int kl, int n_max);
-// Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec.
-bool apply_variant_ok(int v, int prec, int kl_max);
+// Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec
+// (xstage: bytes of the largest chunk record, n_max: rows of the largest block).
+bool apply_variant_ok(int v, int prec, int kl_max, int xstage, int n_max);
 
 // ---- 3D stencils (stencil3d.cu)
 void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, const double* ssum, double* Pout,

@@ -504,6 +504,277 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   }
 }
 
+// ---- Chunked form of the factors and the chunked apply.
+//
+// The per-step solves above carry one dependent step per row.  Grouping kChunk
+// elimination steps removes the chain inside a group: the forward steps
+// k0 .. k0+bc-1 change only the window [k0, k0 + kChunk + kl) of the vector, and
+// their composition is a row permutation followed by I + E with E nonzero in
+// the first kChunk columns only (strictly below the diagonal), so applying them
+// is one gather and one (W x kChunk) matrix-vector product.  Likewise the
+// backward steps of a chunk map its kChunk values to the finished x values (M1)
+// and to updates of the ku2 rows above it (M2).  k_chunk2d obtains P, E, M1 and
+// M2 by running the per-step recurrences of the factors on kChunk unit vectors,
+// in the compute type; the records are stored in the storage type.
+
+// One warp per chunk (warps of a CTA take chunks c = w, w + WPC, ...; one CTA per block).
+template <typename TC, typename TS, int WPC>
+__global__ void __launch_bounds__(32 * WPC) k_chunk2d(const BlockDesc* __restrict__ blocks, FactorStore fs) {
+  constexpr int KC = kChunk;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x;
+  const BlockDesc B = blocks[b];
+  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS));
+  const int n = cg.n, kl = cg.kl, ku2 = cg.ku2;
+  const size_t xrows = (size_t)(KC + 2 * fs.kl_max);  // >= H >= W
+  TC* X = reinterpret_cast<TC*>(smem) + (size_t)w * xrows * KC;
+  int* perm = reinterpret_cast<int*>(reinterpret_cast<TC*>(smem) + (size_t)WPC * xrows * KC) + (size_t)w * xrows;
+  const TS* L = (const TS*)fs.L + b * fs.strideL;
+  const TS* U = (const TS*)fs.U + b * fs.strideU;
+  const uint8_t* piv = fs.piv + b * fs.strideP;
+  unsigned char* rec0 = fs.X + (size_t)b * fs.strideX;
+  for (int c = w; c < cg.nc; c += WPC) {
+    const int k0 = c * KC, bc = min(KC, n - k0), W = cg.W, H = cg.H;
+    // forward: the combined interchange (perm[p] = window row whose value ends at p)
+    if (lane == 0) {
+      for (int p = 0; p < W; ++p) perm[p] = p;
+      for (int m = 0; m < bc; ++m) {
+        const int sp = m + piv[k0 + m], tmp = perm[m];
+        perm[m] = perm[sp];
+        perm[sp] = tmp;
+      }
+    }
+    __syncwarp();
+    // probe j starts as the unit vector at window row perm[j]; after the chunk's steps it is column j of I + E
+    for (int idx = lane; idx < W * KC; idx += 32) {
+      const int p = idx / KC, j = idx % KC;
+      X[idx] = (j < bc && p == perm[j]) ? (TC)1 : (TC)0;
+    }
+    __syncwarp();
+    for (int m = 0; m < bc; ++m) {
+      const int sp = m + piv[k0 + m];
+      if (sp != m && lane < KC) {
+        const TC tmp = X[m * KC + lane];
+        X[m * KC + lane] = X[sp * KC + lane];
+        X[sp * KC + lane] = tmp;
+      }
+      __syncwarp();
+      const TS* lk = L + (size_t)(k0 + m) * fs.lrow;  // lk[i] multiplies window row m + 1 + i
+      for (int idx = lane; idx < kl * KC; idx += 32) {
+        const int i = idx / KC, j = idx % KC, p = m + 1 + i;
+        if (k0 + p < n) X[p * KC + j] -= from_store<TC, TS>(lk[i]) * X[m * KC + j];
+      }
+      __syncwarp();
+    }
+    if (lane < bc) X[lane * KC + lane] -= (TC)1;  // the unit diagonal (exactly 1) is implied
+    __syncwarp();
+    unsigned char* rec = rec0 + (size_t)c * cg.fwd;
+    const int wp = (W + 15) & ~15;
+    for (int p = lane; p < wp; p += 32) rec[p] = p < W ? (unsigned char)perm[p] : (unsigned char)0;
+    TS* E = reinterpret_cast<TS*>(rec + wp);
+    for (int idx = lane; idx < W * KC; idx += 32) E[idx] = to_store<TS>((double)X[idx]);
+    __syncwarp();
+    // backward: local row rho <-> position k0 - ku2 + rho; probe j starts at the chunk's row j
+    for (int idx = lane; idx < H * KC; idx += 32) {
+      const int rho = idx / KC, j = idx % KC;
+      X[idx] = (j < bc && rho == ku2 + j) ? (TC)1 : (TC)0;
+    }
+    __syncwarp();
+    for (int kk = bc - 1; kk >= 0; --kk) {
+      const int k = k0 + kk, rk = ku2 + kk;
+      const TS* uk = U + (size_t)k * fs.ucol;  // uk[0] = 1 / u_kk, uk[jj] = u_{k-jj, k}
+      if (lane < KC) X[rk * KC + lane] *= from_store<TC, TS>(uk[0]);
+      __syncwarp();
+      for (int idx = lane; idx < ku2 * KC; idx += 32) {
+        const int jj = idx / KC + 1, j = idx % KC;
+        if (k - jj >= 0) X[(rk - jj) * KC + j] -= from_store<TC, TS>(uk[jj]) * X[rk * KC + j];
+      }
+      __syncwarp();
+    }
+    TS* M = reinterpret_cast<TS*>(rec0 + (size_t)cg.nc * cg.fwd + (size_t)(cg.nc - 1 - c) * cg.bwd);
+    for (int idx = lane; idx < H * KC; idx += 32) {
+      const int R = idx / KC, j = idx % KC;
+      M[idx] = to_store<TS>((double)X[(R < KC ? ku2 + R : R - KC) * KC + j]);
+    }
+    __syncwarp();
+  }
+}
+
+// One row of kChunk stored entries in the compute type.
+template <typename TC, typename TS>
+__device__ __forceinline__ void load_row8(const TS* row, TC* e);
+template <>
+__device__ __forceinline__ void load_row8<float, __nv_bfloat16>(const __nv_bfloat16* row, float* e) {
+  const uint4 v = *reinterpret_cast<const uint4*>(row);
+  const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    e[2 * i] = __uint_as_float(u[i] << 16);
+    e[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+  }
+}
+template <>
+__device__ __forceinline__ void load_row8<float, float>(const float* row, float* e) {
+  load4(row, e);
+  load4(row + 4, e + 4);
+}
+template <>
+__device__ __forceinline__ void load_row8<double, double>(const double* row, double* e) {
+  load4(row, e);
+  load4(row + 4, e + 4);
+}
+
+// Shared memory of one warp of the chunked apply: STAGES record buffers, the
+// block vector (rounded up to whole chunks), the stage barriers.
+struct ChunkSmem {
+  size_t stage, ybytes, total;
+};
+template <typename TC, int STAGES>
+__host__ __device__ inline ChunkSmem chunk_smem(int xstage, int n_max) {
+  ChunkSmem c;
+  c.stage = rup((size_t)xstage, 128);
+  c.ybytes = rup((size_t)((n_max + kChunk - 1) / kChunk * kChunk) * sizeof(TC), 16);
+  c.total = rup(STAGES * c.stage + c.ybytes + 8 * STAGES, 128);
+  return c;
+}
+
+// z = sum_k (R_k^0)^T A_k^{-1} R_k^delta r with the chunked factors: one warp per
+// block, the block's records streamed through a ring of STAGES bulk copies; the
+// forward chunk is a gather through P and W rows of E, the backward chunk H rows
+// of [M1; M2], one row per lane and round (QF >= W / 32 rounds forward).
+template <typename TC, typename TS, int WPC, int STAGES, int QF>
+__global__ void __launch_bounds__(32 * WPC)
+    k_ras_apply2d_chunked(Geo g, const BlockDesc* __restrict__ blocks, int nblocks, FactorStore fs,
+                          const double* __restrict__ r, const double* __restrict__ rscale, double* __restrict__ z,
+                          const int* __restrict__ skip, int* __restrict__ err, const IterArgs* __restrict__ ia) {
+  constexpr int KC = kChunk;
+  static_assert(KC == 8, "rows of 8 entries (16-byte loads)");
+  if (skip && *skip) return;
+  if (ia) {  // graph mode: this Arnoldi iteration's vectors
+    r = ia->v;
+    rscale = ia->scale;
+    z = ia->z;
+  }
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * WPC + w;
+  if (b >= nblocks) return;  // warp-uniform; no CTA-wide barrier follows
+  const ChunkSmem lay = chunk_smem<TC, STAGES>(fs.xstage, fs.n_max);
+  unsigned char* base = smem + (size_t)w * lay.total;
+  TC* y = reinterpret_cast<TC*>(base + STAGES * lay.stage);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + STAGES * lay.stage + lay.ybytes);
+  const BlockDesc B = blocks[b];
+  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS));
+  const int n = cg.n, nc = cg.nc, total = 2 * nc;
+  const unsigned char* src = fs.X + (size_t)b * fs.strideX;
+  auto issue = [&](int t) {  // lane 0: record t into stage t % STAGES
+    const int st = t % STAGES;
+    const size_t off = t < nc ? (size_t)t * cg.fwd : (size_t)nc * cg.fwd + (size_t)(t - nc) * cg.bwd;
+    const uint32_t bytes = (uint32_t)(t < nc ? cg.fwd : cg.bwd);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(base + st * lay.stage, src + off, bytes, &bar[st]);
+  };
+  if (lane == 0) {
+#pragma unroll
+    for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
+    fence_mbar_init();
+    for (int t = 0; t < STAGES && t < total; ++t) issue(t);
+  }
+  for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta; zeros past n
+    const int a = t % B.bx, c = t / B.bx;
+    y[t] = t < n ? (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] : (TC)0;
+  }
+  __syncwarp();
+  const unsigned FULL = 0xffffffffu;
+  for (int t = 0; t < total; ++t) {
+    const int st = t % STAGES;
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((t / STAGES) & 1));
+    if (!__all_sync(FULL, ok)) {  // give up: record, drain the copies in flight, leave
+      if (lane == 0) {
+        atomicExch(err, PFC_ETIMEOUT);
+        for (int u = t; u < t + STAGES && u < total; ++u)
+          mbar_wait_bounded(&bar[u % STAGES], (uint32_t)((u / STAGES) & 1));
+      }
+      return;
+    }
+    const unsigned char* rec = base + st * lay.stage;
+    if (t < nc) {  // forward chunk t: y_w <- (I + E) P y_w on the window w = [k0, k0 + W)
+      const int k0 = t * KC, W = cg.W;
+      const unsigned char* perm = rec;
+      const TS* E = reinterpret_cast<const TS*>(rec + ((W + 15) & ~15));
+      TC tv[QF];
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        const int R = lane + 32 * q;
+        tv[q] = (R < W && k0 + R < n) ? y[min(k0 + (int)perm[R], n - 1)] : (TC)0;
+      }
+      TC t1[KC];  // the chunk's pivot values: rows 0 .. KC-1 of the permuted window
+#pragma unroll
+      for (int j = 0; j < KC; ++j) t1[j] = __shfl_sync(FULL, tv[0], j);
+      __syncwarp();  // every gather is done before any row is written
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        const int R = lane + 32 * q;
+        if (R < W && k0 + R < n) {
+          TC e[KC];
+          load_row8<TC, TS>(E + R * KC, e);
+          TC acc = tv[q];
+#pragma unroll
+          for (int j = 0; j < KC; ++j) acc = fma(e[j], t1[j], acc);
+          y[k0 + R] = acc;
+        }
+      }
+    } else {  // backward chunk c: x_c = M1 y_c, y_a += M2 y_c (a = the ku2 rows above)
+      const int c = 2 * nc - 1 - t, k0 = c * KC, ku2 = cg.ku2, H = cg.H;
+      const TS* M = reinterpret_cast<const TS*>(rec);
+      TC t1[KC];
+      load_row8<TC, TC>(y + k0, t1);  // zeros past n
+      __syncwarp();                   // every lane holds y_c before x_c overwrites it
+      for (int R = lane; R < H; R += 32) {
+        const int pos = R < KC ? k0 + R : k0 - ku2 + (R - KC);
+        if (pos >= 0 && pos < n) {
+          TC e[KC];
+          load_row8<TC, TS>(M + R * KC, e);
+          TC acc = R < KC ? (TC)0 : y[pos];
+#pragma unroll
+          for (int j = 0; j < KC; ++j) acc = fma(e[j], t1[j], acc);
+          y[pos] = acc;
+        }
+      }
+    }
+    __syncwarp();  // every lane is done with this stage (and with y) before it is refilled
+    if (lane == 0 && t + STAGES < total) issue(t + STAGES);
+  }
+  const double sc = rscale ? *rscale : 1.0;
+  for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
+    const int a = t % B.bx, c = t / B.bx;
+    if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
+      z[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] = sc * (double)y[t];
+  }
+}
+
+template <typename TC, typename TS, int WPC, int STAGES>
+void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
+                      const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
+                      const IterArgs* ia) {
+  const size_t smem = WPC * chunk_smem<TC, STAGES>(fs.xstage, fs.n_max).total;
+  const int grid = (nblocks + WPC - 1) / WPC;
+  if (kChunk + fs.kl_max <= 96) {
+    cudaFuncSetAttribute(k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 3><<<grid, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale, z,
+                                                                              skip, err, ia);
+  } else {
+    cudaFuncSetAttribute(k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 5><<<grid, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale, z,
+                                                                              skip, err, ia);
+  }
+  count_launches(1);
+}
+
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
@@ -536,10 +807,44 @@ void apply_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Fa
 
 }  // namespace
 
-bool apply_variant_ok(int v, int prec, int kl_max) {
-  (void)prec;
-  if (kl_max <= 64) return v >= 0 && v < kApplyVariants;  // 3 + 5 window registers per lane
-  return v == 0 && kl_max <= 128;                          // 5 + 9 window registers, default shape
+// Chunked apply shapes per storage type (warps per CTA, stages).
+constexpr int kChunkWpcF64 = 2, kChunkStF64 = 2;
+constexpr int kChunkWpcF32 = 4, kChunkStF32 = 2;
+constexpr int kChunkWpcB16 = 4, kChunkStB16 = 3;
+
+size_t chunked_smem_bytes(int prec, int xstage, int n_max) {
+  if (prec == PFC_F64) return kChunkWpcF64 * chunk_smem<double, kChunkStF64>(xstage, n_max).total;
+  if (prec == PFC_F32) return kChunkWpcF32 * chunk_smem<float, kChunkStF32>(xstage, n_max).total;
+  return kChunkWpcB16 * chunk_smem<float, kChunkStB16>(xstage, n_max).total;
+}
+
+static size_t chunk_build_smem(int prec, int kl_max) {
+  const size_t tc = prec == PFC_F64 ? 8 : 4;
+  return (size_t)4 * (kChunk + 2 * kl_max) * (kChunk * tc + sizeof(int));
+}
+
+bool apply_variant_ok(int v, int prec, int kl_max, int xstage, int n_max) {
+  if (v == kChunkedVariant)
+    return kl_max <= 128 && chunked_smem_bytes(prec, xstage, n_max) <= 227 * 1024 &&
+           chunk_build_smem(prec, kl_max) <= 227 * 1024;
+  if (kl_max <= 64) return v >= 0 && v < kChunkedVariant;  // 3 + 5 window registers per lane
+  return v == 0 && kl_max <= 128;                           // 5 + 9 window registers, default shape
+}
+
+void launch_chunk2d(const BlockDesc* blocks, int nblocks, const FactorStore& fs, cudaStream_t st) {
+  const size_t smem = chunk_build_smem(fs.prec, fs.kl_max);
+  if (fs.prec == PFC_F64) {
+    cudaFuncSetAttribute(k_chunk2d<double, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chunk2d<double, double, 4><<<nblocks, 128, smem, st>>>(blocks, fs);
+  } else if (fs.prec == PFC_F32) {
+    cudaFuncSetAttribute(k_chunk2d<float, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chunk2d<float, float, 4><<<nblocks, 128, smem, st>>>(blocks, fs);
+  } else {
+    cudaFuncSetAttribute(k_chunk2d<float, __nv_bfloat16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_chunk2d<float, __nv_bfloat16, 4><<<nblocks, 128, smem, st>>>(blocks, fs);
+  }
+  count_launches(1);
 }
 
 // Dynamic shared memory of the factor kernel: q on the block and the stencil
@@ -569,8 +874,19 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
   // variant 0: stages of about 3.5 KB for every storage type, 4 warps per CTA;
   // 1: half the chunk (twice the resident warps per SM), 2: half the chunk and
   // 2 warps per CTA (finer packing), 3: twice the chunk (fewer, larger copies);
-  // 4: two subdomains per warp, 16 lanes each (5 + 9 window registers per lane).
-  if (fs.kl_max > 64) {  // blocks wider than 21 cells: the wide-window kernel, default shape
+  // 4: two subdomains per warp, 16 lanes each (5 + 9 window registers per lane);
+  // 5: the chunked solves (one warp per block, records of kChunk steps).
+  if (fs.variant == kChunkedVariant) {
+    if (fs.prec == PFC_F64)
+      chunked_dispatch<double, double, kChunkWpcF64, kChunkStF64>(g, blocks, nblocks, fs, r, rscale, z, skip, err,
+                                                                   st, ia);
+    else if (fs.prec == PFC_F32)
+      chunked_dispatch<float, float, kChunkWpcF32, kChunkStF32>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st,
+                                                                 ia);
+    else
+      chunked_dispatch<float, __nv_bfloat16, kChunkWpcB16, kChunkStB16>(g, blocks, nblocks, fs, r, rscale, z, skip,
+                                                                         err, st, ia);
+  } else if (fs.kl_max > 64) {  // blocks wider than 21 cells: the wide-window kernel, default shape
     if (fs.prec == PFC_F64)
       apply_dispatch<double, double, 4, 4, 5>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia);
     else if (fs.prec == PFC_F32)

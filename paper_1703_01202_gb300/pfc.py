@@ -22,6 +22,8 @@ PFC_ENEWTON, PFC_EGMRES, PFC_ESINGULAR, PFC_ENAN, PFC_ETIMEOUT = -4, -5, -6, -7,
 PFC_F64, PFC_F32, PFC_BF16 = 0, 1, 2
 PFC_AS, PFC_LEFT_RAS, PFC_RIGHT_RAS = 0, 1, 2
 PFC_GUESS_PREV, PFC_GUESS_EXTRAP, PFC_GUESS_USER, PFC_GUESS_LEARNED = 0, 1, 2, 3
+N_APPLY_VARIANTS = 6  # apply kernels 0-4 (per-step solves, bitwise equal) and 5 (chunked solves)
+APPLY_CHUNKED = 5
 
 
 class pfc_grid(ctypes.Structure):
@@ -298,9 +300,9 @@ class Solver:
 
     def tuning(self) -> dict:
         v, gr = c_int(), c_int()
-        ms = (c_float * 5)()
+        ms = (c_float * N_APPLY_VARIANTS)()
         _check(lib().pfc_get_tuning(self.handle, ctypes.byref(v), ms, ctypes.byref(gr)), "pfc_get_tuning")
-        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(5)], "graph": gr.value}
+        return {"apply_variant": v.value, "apply_ms": [ms[i] for i in range(N_APPLY_VARIANTS)], "graph": gr.value}
 
     # -- test hooks on device tensors
     def residual(self, Phi, phin, dt: float):

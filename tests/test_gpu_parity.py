@@ -137,34 +137,74 @@ def test_apply_autotuner_picks_a_timed_kernel(pfc):
         out[v] = s.get_field()
         t = s.tuning()
         if v == -1:
-            assert t["apply_variant"] in (0, 1, 2, 3, 4)
+            assert t["apply_variant"] in range(pfc.N_APPLY_VARIANTS)
             assert all(ms > 0 for ms in t["apply_ms"])
             # the fastest shape, or a lower-numbered one within 1 % of it
             assert t["apply_ms"][t["apply_variant"]] <= 1.01 * min(t["apply_ms"])
             assert all(ms > 1.01 * min(t["apply_ms"]) for ms in t["apply_ms"][:t["apply_variant"]])
         else:
-            assert t["apply_ms"] == [-1.0] * 5
+            assert t["apply_ms"] == [-1.0] * pfc.N_APPLY_VARIANTS
     assert np.abs(out[-1] - out[0]).max() <= 1e-9
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
 def test_wide_blocks_use_the_wide_window_kernel(pfc, prec, tol):
-    """24-cell-wide blocks (kl = 72 > 64) run the wide-window apply kernel: same
-    oracle parity; launch shapes other than the default are refused."""
+    """24-cell-wide blocks (kl = 72 > 64) run the wide-window apply kernel or the
+    chunked one: same oracle parity; the other launch shapes are refused."""
     shape = (44, 44)
     Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
     phin = inputs.noise_field(shape, 0.285, 0.3, 9)
     r = inputs.noise_field(shape, 0.0, 1.0, 10)
-    s = solver(pfc, shape, (2, 2), prec=prec, overlap=1)
-    z = s.precond_apply(Phi, phin, 1.0, r).cpu().numpy()
-    assert s.tuning()["apply_variant"] == 0
     J = O.assemble_jacobian(Phi, phin, 1.0, H, GAMMA)
     ref = O.Schwarz(J, O.decompose(shape, (2, 2), 1), "left-ras", "lu").apply(r)
-    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= tol
+    for v in (-1, 0, pfc.APPLY_CHUNKED):
+        s = solver(pfc, shape, (2, 2), prec=prec, overlap=1, apply_variant=v)
+        z = s.precond_apply(Phi, phin, 1.0, r).cpu().numpy()
+        assert s.tuning()["apply_variant"] in (0, pfc.APPLY_CHUNKED)
+        assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= tol
     s2 = solver(pfc, shape, (2, 2), prec=prec, overlap=1, apply_variant=1)
     with pytest.raises(pfc.PfcError) as e:
         s2.precond_apply(Phi, phin, 1.0, r)
     assert e.value.status == pfc.PFC_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4), (2, 0.25)])
+@pytest.mark.parametrize("shape,parts,dt", [((50, 37), (3, 2), 10.0), ((96, 80), (5, 6), 1.0),
+                                            ((21, 27), (3, 3), 10.0)])
+def test_chunked_apply_matches_oracle(pfc, shape, parts, dt, prec, tol):
+    """The chunked solves (apply variant 5: the factors regrouped 8 elimination
+    steps at a time, a row permutation and an 8-column product per group) against
+    the oracle's dense-LU Schwarz apply, on ragged decompositions (block sizes
+    360 ... 399 and 315 ... 352 cells, most with a partial last chunk, and 99)."""
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, parts, prec=prec, overlap=1, apply_variant=pfc.APPLY_CHUNKED)
+    z = s.precond_apply(Phi, phin, dt, r).cpu().numpy()
+    assert s.tuning()["apply_variant"] == pfc.APPLY_CHUNKED
+    J = O.assemble_jacobian(Phi, phin, dt, H, GAMMA)
+    ref = O.Schwarz(J, O.decompose(shape, parts, 1), "left-ras", "lu").apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+    if prec == 0:  # the per-step solves on the same FP64 factors agree to rounding
+        s0 = solver(pfc, shape, parts, prec=0, overlap=1, apply_variant=0)
+        z0 = s0.precond_apply(Phi, phin, dt, r).cpu().numpy()
+        assert np.abs(z - z0).max() <= 1e-12 * np.abs(z0).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
+def test_chunked_apply_steps_match_oracle(pfc, prec, tol):
+    """Five adaptive steps of the 64^2 noise field with the chunked apply: the
+    Newton solutions against the oracle's (the preconditioner only changes the
+    path, not the discrete solution)."""
+    w = inputs.workload("noise64")
+    prm = dict(dt_min=1e-2, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, w["shape"], w["parts"], prec=prec, overlap=1, apply_variant=pfc.APPLY_CHUNKED, **prm)
+    s.set_field(w["phi"])
+    recs = s.run(5)
+    ref, orecs = O.run(w["phi"], w["h"], w["gamma"], O.Params(parts=w["parts"], overlap=1, **prm), 5)
+    assert np.abs(s.get_field() - ref).max() <= tol
+    assert [r["dt"] for r in recs] == pytest.approx([o.dt for o in orecs], rel=1e-9)
 
 
 def test_twenty_steps_noise64_match_oracle(pfc):
