@@ -293,8 +293,9 @@ struct Plan {
   int nblocks, n_max, kl_max;
   size_t sL, sU, sP;
   int lrow, ucol;
-  size_t sX;   // bytes of chunked records per block (2D)
-  int xstage;  // bytes of the largest chunked record
+  size_t xfw, xbw;  // strides of the chunked forward / backward records (2D)
+  int xnc;          // chunks of the largest block
+  int xstage;       // bytes of the largest chunked record
   size_t partial_len;
   Shapes3 sh3;
   size_t sLU3, sWork3, sPad3;
@@ -318,18 +319,20 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
     pl->sL = (size_t)pl->n_max * pl->lrow;
     pl->sU = (size_t)pl->n_max * pl->ucol;
     pl->sP = ((size_t)pl->n_max + 15) / 16 * 16;
-    pl->sX = 0;
-    pl->xstage = 0;
+    pl->xfw = pl->xbw = 0;
+    pl->xnc = 0;
     for (const BlockDesc& b : blocks) {
-      const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es);
-      pl->sX = std::max(pl->sX, (size_t)cg.nc * (cg.fwd + cg.bwd));
-      pl->xstage = std::max(pl->xstage, (int)std::max(cg.fwd, cg.bwd));
+      const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es, (int)tc);
+      pl->xfw = std::max(pl->xfw, cg.fwd);
+      pl->xbw = std::max(pl->xbw, cg.bwd);
+      pl->xnc = std::max(pl->xnc, cg.nc);
     }
-    pl->sX = (pl->sX + 127) / 128 * 128;
+    pl->xstage = (int)std::max(pl->xfw, pl->xbw);
   } else {
     pl->lrow = pl->ucol = 0;
     pl->sL = pl->sU = pl->sP = 0;
-    pl->sX = 0;
+    pl->xfw = pl->xbw = 0;
+    pl->xnc = 0;
     pl->xstage = 0;
     build_shapes3(blocks, &pl->sh3);
     pl->sLU3 = (size_t)pl->sh3.nrows_max * 32;
@@ -358,7 +361,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->L = L.take(pl->sL * es * pl->nblocks);
   pl->U = L.take(pl->sU * es * pl->nblocks);
   pl->piv = L.take(pl->sP * pl->nblocks);
-  pl->X = L.take(pl->sX * pl->nblocks);
+  pl->X = L.take((size_t)pl->xnc * pl->nblocks * (pl->xfw + pl->xbw));
   pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
   pl->lin = L.take(sizeof(double) * 343);
   pl->ctl = L.take(sizeof(GmresCtl));
@@ -472,6 +475,8 @@ bool variant_ok(const pfc_state* s, int v) {
   return pfc::apply_variant_ok(v, s->fs.prec, s->fs.kl_max, s->fs.xstage, s->fs.n_max);
 }
 
+constexpr int kTuneReps = 10;  // timed applies per kernel
+
 int tune_apply(pfc_state* s) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
@@ -483,10 +488,10 @@ int tune_apply(pfc_state* s) {
     s->tune_ms[v] = -1.f;
     if (!variant_ok(s, v) || (v == pfc::kChunkedVariant && !s->fs.x_valid)) continue;
     s->fs.variant = v;
-    precond(s, s->F, nullptr, s->W, nullptr);  // warm-up
+    for (int i = 0; i < 2; ++i) precond(s, s->F, nullptr, s->W, nullptr);  // warm-up
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(e0, s->st);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < kTuneReps && e == cudaSuccess; ++i) {
       precond(s, s->F, nullptr, s->W, nullptr);
       e = cudaGetLastError();
     }
@@ -499,7 +504,7 @@ int tune_apply(pfc_state* s) {
       rc = PFC_ECUDA;
       break;
     }
-    s->tune_ms[v] = ms / 3.f;
+    s->tune_ms[v] = ms / kTuneReps;
     if (best < 0 || ms < best_ms) {
       best = v;
       best_ms = ms;
@@ -924,7 +929,10 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.lrow = pl.lrow;
   s->fs.ucol = pl.ucol;
   s->fs.X = (unsigned char*)at(pl.X);
-  s->fs.strideX = pl.sX;
+  s->fs.xfw = pl.xfw;
+  s->fs.xbw = pl.xbw;
+  s->fs.xnc = pl.xnc;
+  s->fs.nblk = pl.nblocks;
   s->fs.xstage = pl.xstage;
   s->fs.x_valid = 0;
   s->fs.prec = p->factor_prec;
@@ -984,7 +992,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
         const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
         const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
         bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
-        const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es);
+        const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es, p->factor_prec == PFC_F64 ? 8 : 4);
         bytes_chunk += (double)cg.nc * (cg.fwd + cg.bwd) + n * 8.0 + (double)b.cx * b.cy * 8.0;
       } else {  // 63 ILU(0) entries per row, row tables, gather, core write
         const double n = (double)b.bx * b.by * b.bz;

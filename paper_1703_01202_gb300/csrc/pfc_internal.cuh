@@ -103,42 +103,56 @@ struct FactorStore {
   int variant;       // apply launch shape, 0 .. kApplyVariants - 1
   const int* order;  // two-per-warp shape: blocks grouped by extent, each group padded to an even count with -1
   int norder;
-  // Chunked form of the same factors (apply variant kChunkedVariant), one record stream per
-  // block in the order the apply consumes it; built from L, U, piv by launch_chunk2d.
+  // Chunked form of the same factors (apply variant kChunkedVariant); built from L, U, piv
+  // by launch_chunk2d.  Record-major: record t of every block (in the order the apply
+  // consumes them: forward chunks 0 .. nc-1, then backward chunks nc-1 .. 0) lies next to
+  // record t of the neighbouring blocks, so the warps of one apply stream through
+  // memory together.
   unsigned char* X;
-  size_t strideX;  // bytes per block
-  int xstage;      // bytes of the largest record (one TMA stage)
-  int x_valid;     // X holds the chunks of the current factors
+  size_t xfw, xbw;  // stride of the forward / backward records (the largest of each)
+  int xnc;          // chunks of the largest block
+  int nblk;         // blocks
+  int xstage;       // bytes of the largest record (one TMA stage)
+  int x_valid;      // X holds the chunks of the current factors
 };
 constexpr int kApplyVariants = 6;
 constexpr int kChunkedVariant = 5;
 
 // Chunked triangular solves.  The forward solve P/L of a block advances kChunk
 // elimination steps at a time: the steps k0 .. k0+bc-1 (bc = min(kChunk, n-k0))
-// act on the window of positions [k0, k0+W), W = kChunk + kl, as y <- (I + E) P y,
-// where P is their row interchanges combined and E (W x kChunk, zero on and above
-// the diagonal) collects the multipliers; the backward solve with U takes the
-// same chunks from the bottom: x_c = M1 y_c and y_a += M2 y_c on the ku2 rows
-// above the chunk (M1 = inverse of the chunk's diagonal block of U).
+// act on the window of positions [k0, k0+W), W = kChunk + kl, as a row permutation
+// (their interchanges combined) followed by the unit lower triangular factor with
+// the chunk's multipliers, each moved by the interchanges after its own step:
+// y_c = E11 t_c on the chunk's rows (E11 = inverse of its kChunk x kChunk block)
+// and y_b = t_b - L21 y_c on the kl rows below.  The backward solve takes the same
+// chunks from the bottom: x_c = U11^{-1} y_c, then y_a -= U_a x_c on the ku2 rows
+// above.  L21 and U_a are entries of the factors themselves (storage type); the
+// small inverses are kept in the compute type.
 // Records (16-byte multiples): forward = W permutation bytes rounded up to 16,
-// then W rows of kChunk entries; backward = kChunk + ku2 rows of kChunk entries
-// (rows of M1, then rows of M2 for positions k0-ku2 .. k0-1).
+// E11 (kChunk^2, compute type, row-major), -L21 (kl rows of kChunk); backward =
+// U11^{-1} (kChunk^2, compute type), -U_a (ku2 rows of kChunk, positions
+// k0-ku2 .. k0-1).
 constexpr int kChunk = 8;
 struct ChunkGeom {
-  int n, kl, ku2, nc, W, H;
+  int n, kl, ku2, nc, W;
   size_t fwd, bwd;  // record bytes
 };
-__host__ __device__ inline ChunkGeom chunk_geom(int bx, int by, int es) {
+// es: bytes of a stored factor entry; tc: bytes of the compute type
+__host__ __device__ inline ChunkGeom chunk_geom(int bx, int by, int es, int tc) {
   ChunkGeom c;
   c.n = bx * by;
   c.kl = 3 * bx < c.n - 1 ? 3 * bx : c.n - 1;
   c.ku2 = 2 * c.kl < c.n - 1 ? 2 * c.kl : c.n - 1;
   c.nc = (c.n + kChunk - 1) / kChunk;
   c.W = kChunk + c.kl;
-  c.H = kChunk + c.ku2;
-  c.fwd = (size_t)(c.W + 15) / 16 * 16 + (size_t)c.W * kChunk * es;
-  c.bwd = (size_t)c.H * kChunk * es;
+  c.fwd = (size_t)(c.W + 15) / 16 * 16 + (size_t)kChunk * kChunk * tc + (size_t)c.kl * kChunk * es;
+  c.bwd = (size_t)kChunk * kChunk * tc + (size_t)c.ku2 * kChunk * es;
   return c;
+}
+// Byte offset in X of record t (consumption order) of block b with nc chunks.
+__host__ __device__ inline size_t chunk_rec_off(const FactorStore& fs, int b, int nc, int t) {
+  if (t < nc) return ((size_t)t * fs.nblk + b) * fs.xfw;
+  return (size_t)fs.xnc * fs.nblk * fs.xfw + ((size_t)(t - nc) * fs.nblk + b) * fs.xbw;
 }
 void launch_chunk2d(const BlockDesc* blocks, int nblocks, const FactorStore& fs, cudaStream_t st);
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,

@@ -507,15 +507,11 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
 // ---- Chunked form of the factors and the chunked apply.
 //
 // The per-step solves above carry one dependent step per row.  Grouping kChunk
-// elimination steps removes the chain inside a group: the forward steps
-// k0 .. k0+bc-1 change only the window [k0, k0 + kChunk + kl) of the vector, and
-// their composition is a row permutation followed by I + E with E nonzero in
-// the first kChunk columns only (strictly below the diagonal), so applying them
-// is one gather and one (W x kChunk) matrix-vector product.  Likewise the
-// backward steps of a chunk map its kChunk values to the finished x values (M1)
-// and to updates of the ku2 rows above it (M2).  k_chunk2d obtains P, E, M1 and
-// M2 by running the per-step recurrences of the factors on kChunk unit vectors,
-// in the compute type; the records are stored in the storage type.
+// elimination steps removes the chain inside a group except for a kChunk x
+// kChunk triangle, which is applied as a small dense product with its inverse;
+// the rest of the group's work is one gather (the group's row interchanges) and
+// one product with the factor entries of the group's columns.  k_chunk2d
+// rearranges L, U and the pivots into these records after each factorisation.
 
 // One warp per chunk (warps of a CTA take chunks c = w, w + WPC, ...; one CTA per block).
 template <typename TC, typename TS, int WPC>
@@ -525,77 +521,84 @@ __global__ void __launch_bounds__(32 * WPC) k_chunk2d(const BlockDesc* __restric
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x;
   const BlockDesc B = blocks[b];
-  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS));
-  const int n = cg.n, kl = cg.kl, ku2 = cg.ku2;
-  const size_t xrows = (size_t)(KC + 2 * fs.kl_max);  // >= H >= W
+  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS), (int)sizeof(TC));
+  const int n = cg.n, kl = cg.kl, ku2 = cg.ku2, W = cg.W;
+  const size_t xrows = (size_t)(KC + fs.kl_max);  // >= W
   TC* X = reinterpret_cast<TC*>(smem) + (size_t)w * xrows * KC;
   int* perm = reinterpret_cast<int*>(reinterpret_cast<TC*>(smem) + (size_t)WPC * xrows * KC) + (size_t)w * xrows;
   const TS* L = (const TS*)fs.L + b * fs.strideL;
   const TS* U = (const TS*)fs.U + b * fs.strideU;
   const uint8_t* piv = fs.piv + b * fs.strideP;
-  unsigned char* rec0 = fs.X + (size_t)b * fs.strideX;
   for (int c = w; c < cg.nc; c += WPC) {
-    const int k0 = c * KC, bc = min(KC, n - k0), W = cg.W, H = cg.H;
-    // forward: the combined interchange (perm[p] = window row whose value ends at p)
-    if (lane == 0) {
+    const int k0 = c * KC, bc = min(KC, n - k0);
+    // forward: perm[p] = window row whose value ends at p after the chunk's interchanges;
+    // column m of X = the multipliers of step m, moved by the interchanges of steps > m
+    if (lane == 0)
       for (int p = 0; p < W; ++p) perm[p] = p;
-      for (int m = 0; m < bc; ++m) {
-        const int sp = m + piv[k0 + m], tmp = perm[m];
-        perm[m] = perm[sp];
-        perm[sp] = tmp;
-      }
-    }
-    __syncwarp();
-    // probe j starts as the unit vector at window row perm[j]; after the chunk's steps it is column j of I + E
-    for (int idx = lane; idx < W * KC; idx += 32) {
-      const int p = idx / KC, j = idx % KC;
-      X[idx] = (j < bc && p == perm[j]) ? (TC)1 : (TC)0;
-    }
+    for (int idx = lane; idx < W * KC; idx += 32) X[idx] = (TC)0;
     __syncwarp();
     for (int m = 0; m < bc; ++m) {
       const int sp = m + piv[k0 + m];
-      if (sp != m && lane < KC) {
-        const TC tmp = X[m * KC + lane];
-        X[m * KC + lane] = X[sp * KC + lane];
-        X[sp * KC + lane] = tmp;
+      if (sp != m) {
+        if (lane < m) {  // interchange m moves the multipliers of the earlier steps
+          const TC tmp = X[m * KC + lane];
+          X[m * KC + lane] = X[sp * KC + lane];
+          X[sp * KC + lane] = tmp;
+        }
+        if (lane == 0) {
+          const int tmp = perm[m];
+          perm[m] = perm[sp];
+          perm[sp] = tmp;
+        }
       }
       __syncwarp();
       const TS* lk = L + (size_t)(k0 + m) * fs.lrow;  // lk[i] multiplies window row m + 1 + i
-      for (int idx = lane; idx < kl * KC; idx += 32) {
-        const int i = idx / KC, j = idx % KC, p = m + 1 + i;
-        if (k0 + p < n) X[p * KC + j] -= from_store<TC, TS>(lk[i]) * X[m * KC + j];
-      }
+      for (int i = lane; i < kl; i += 32)
+        if (k0 + m + 1 + i < n) X[(m + 1 + i) * KC + m] = from_store<TC, TS>(lk[i]);
       __syncwarp();
     }
-    if (lane < bc) X[lane * KC + lane] -= (TC)1;  // the unit diagonal (exactly 1) is implied
-    __syncwarp();
-    unsigned char* rec = rec0 + (size_t)c * cg.fwd;
+    unsigned char* rec = fs.X + chunk_rec_off(fs, b, cg.nc, c);
     const int wp = (W + 15) & ~15;
     for (int p = lane; p < wp; p += 32) rec[p] = p < W ? (unsigned char)perm[p] : (unsigned char)0;
-    TS* E = reinterpret_cast<TS*>(rec + wp);
-    for (int idx = lane; idx < W * KC; idx += 32) E[idx] = to_store<TS>((double)X[idx]);
-    __syncwarp();
-    // backward: local row rho <-> position k0 - ku2 + rho; probe j starts at the chunk's row j
-    for (int idx = lane; idx < H * KC; idx += 32) {
-      const int rho = idx / KC, j = idx % KC;
-      X[idx] = (j < bc && rho == ku2 + j) ? (TC)1 : (TC)0;
-    }
-    __syncwarp();
-    for (int kk = bc - 1; kk >= 0; --kk) {
-      const int k = k0 + kk, rk = ku2 + kk;
-      const TS* uk = U + (size_t)k * fs.ucol;  // uk[0] = 1 / u_kk, uk[jj] = u_{k-jj, k}
-      if (lane < KC) X[rk * KC + lane] *= from_store<TC, TS>(uk[0]);
-      __syncwarp();
-      for (int idx = lane; idx < ku2 * KC; idx += 32) {
-        const int jj = idx / KC + 1, j = idx % KC;
-        if (k - jj >= 0) X[(rk - jj) * KC + j] -= from_store<TC, TS>(uk[jj]) * X[rk * KC + j];
+    TC* E11 = reinterpret_cast<TC*>(rec + wp);
+    if (lane < KC) {  // column lane of the inverse of the unit lower KC x KC block
+      TC e[KC];
+#pragma unroll
+      for (int r = 0; r < KC; ++r) {
+        TC v = r == lane ? (TC)1 : (TC)0;
+        for (int q = 0; q < r; ++q) v -= X[r * KC + q] * e[q];
+        e[r] = v;
       }
-      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < KC; ++r) E11[r * KC + lane] = e[r];
     }
-    TS* M = reinterpret_cast<TS*>(rec0 + (size_t)cg.nc * cg.fwd + (size_t)(cg.nc - 1 - c) * cg.bwd);
-    for (int idx = lane; idx < H * KC; idx += 32) {
-      const int R = idx / KC, j = idx % KC;
-      M[idx] = to_store<TS>((double)X[(R < KC ? ku2 + R : R - KC) * KC + j]);
+    TS* L21 = reinterpret_cast<TS*>(rec + wp + KC * KC * sizeof(TC));
+    for (int idx = lane; idx < kl * KC; idx += 32) L21[idx] = to_store<TS>(-(double)X[KC * KC + idx]);
+    // backward: U11^{-1} (column lane by back substitution with the stored 1 / u_kk) and -U_a
+    TC* U11i = reinterpret_cast<TC*>(fs.X + chunk_rec_off(fs, b, cg.nc, 2 * cg.nc - 1 - c));
+    if (lane < KC) {
+      TC x[KC];
+#pragma unroll
+      for (int r = KC - 1; r >= 0; --r) {
+        TC v = r == lane ? (TC)1 : (TC)0;
+        if (r < bc) {
+          const TS* ur = U + (size_t)(k0 + r) * fs.ucol;  // ur[0] = 1 / u_rr
+#pragma unroll
+          for (int q = r + 1; q < KC; ++q)
+            if (q < bc) v -= from_store<TC, TS>(U[(size_t)(k0 + q) * fs.ucol + (q - r)]) * x[q];
+          v *= from_store<TC, TS>(ur[0]);
+        }
+        x[r] = v;
+      }
+#pragma unroll
+      for (int r = 0; r < KC; ++r) U11i[r * KC + lane] = x[r];
+    }
+    TS* Ua = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(U11i) + KC * KC * sizeof(TC));
+    for (int idx = lane; idx < ku2 * KC; idx += 32) {
+      const int i = idx / KC, j = idx % KC, jj = ku2 + j - i;  // u(k0 - ku2 + i, k0 + j) at U column k0 + j
+      double v = 0.0;
+      if (j < bc && jj <= ku2 && k0 - ku2 + i >= 0) v = -(double)from_store<TC, TS>(U[(size_t)(k0 + j) * fs.ucol + jj]);
+      Ua[idx] = to_store<TS>(v);
     }
     __syncwarp();
   }
@@ -639,11 +642,15 @@ __host__ __device__ inline ChunkSmem chunk_smem(int xstage, int n_max) {
   return c;
 }
 
+// Periodic index for -n <= i < 2n (a block is never wider than the grid).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 // z = sum_k (R_k^0)^T A_k^{-1} R_k^delta r with the chunked factors: one warp per
-// block, the block's records streamed through a ring of STAGES bulk copies; the
-// forward chunk is a gather through P and W rows of E, the backward chunk H rows
-// of [M1; M2], one row per lane and round (QF >= W / 32 rounds forward).
-template <typename TC, typename TS, int WPC, int STAGES, int QF>
+// block, the block's records streamed through a ring of STAGES bulk copies.  Lanes
+// 0..KC-1 apply the chunk's small inverse; then every lane takes one of the kl rows
+// below (forward) or ku2 rows above (backward) per round (QF >= kl / 32 rounds,
+// QB >= ku2 / 32).
+template <typename TC, typename TS, int WPC, int STAGES, int QF, int QB>
 __global__ void __launch_bounds__(32 * WPC)
     k_ras_apply2d_chunked(Geo g, const BlockDesc* __restrict__ blocks, int nblocks, FactorStore fs,
                           const double* __restrict__ r, const double* __restrict__ rscale, double* __restrict__ z,
@@ -665,16 +672,15 @@ __global__ void __launch_bounds__(32 * WPC)
   TC* y = reinterpret_cast<TC*>(base + STAGES * lay.stage);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + STAGES * lay.stage + lay.ybytes);
   const BlockDesc B = blocks[b];
-  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS));
+  const ChunkGeom cg = chunk_geom(B.bx, B.by, (int)sizeof(TS), (int)sizeof(TC));
   const int n = cg.n, nc = cg.nc, total = 2 * nc;
-  const unsigned char* src = fs.X + (size_t)b * fs.strideX;
   auto issue = [&](int t) {  // lane 0: record t into stage t % STAGES
     const int st = t % STAGES;
-    const size_t off = t < nc ? (size_t)t * cg.fwd : (size_t)nc * cg.fwd + (size_t)(t - nc) * cg.bwd;
+    const unsigned char* src = fs.X + chunk_rec_off(fs, b, nc, t);
     const uint32_t bytes = (uint32_t)(t < nc ? cg.fwd : cg.bwd);
     fence_proxy_async();
     mbar_expect_tx(&bar[st], bytes);
-    bulk_g2s(base + st * lay.stage, src + off, bytes, &bar[st]);
+    bulk_g2s(base + st * lay.stage, src, bytes, &bar[st]);
   };
   if (lane == 0) {
 #pragma unroll
@@ -682,9 +688,19 @@ __global__ void __launch_bounds__(32 * WPC)
     fence_mbar_init();
     for (int t = 0; t < STAGES && t < total; ++t) issue(t);
   }
-  for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta; zeros past n
-    const int a = t % B.bx, c = t / B.bx;
-    y[t] = t < n ? (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] : (TC)0;
+  // block-local (a, c) of element t = lane + 32 i, advanced without divisions
+  const int da = 32 % B.bx, dc = 32 / B.bx, a0 = lane % B.bx, c0 = lane / B.bx;
+  {
+    int a = a0, c = c0;
+    for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta; zeros past n
+      y[t] = t < n ? (TC)r[wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny)] : (TC)0;
+      a += da;
+      c += dc;
+      if (a >= B.bx) {
+        a -= B.bx;
+        ++c;
+      }
+    }
   }
   __syncwarp();
   const unsigned FULL = 0xffffffffu;
@@ -700,59 +716,104 @@ __global__ void __launch_bounds__(32 * WPC)
       return;
     }
     const unsigned char* rec = base + st * lay.stage;
-    if (t < nc) {  // forward chunk t: y_w <- (I + E) P y_w on the window w = [k0, k0 + W)
-      const int k0 = t * KC, W = cg.W;
+    if (t < nc) {  // forward chunk t on the window [k0, k0 + W): gather, y_c = E11 t_c, y_b = t_b - L21 y_c
+      const int k0 = t * KC, W = cg.W, kl = cg.kl;
       const unsigned char* perm = rec;
-      const TS* E = reinterpret_cast<const TS*>(rec + ((W + 15) & ~15));
-      TC tv[QF];
+      const TC* E11 = reinterpret_cast<const TC*>(rec + ((W + 15) & ~15));
+      const TS* L21 = reinterpret_cast<const TS*>(E11 + KC * KC);  // negated
+      const TC tc = (lane < KC && k0 + lane < n) ? y[min(k0 + (int)perm[lane], n - 1)] : (TC)0;
+      TC tv[QF];  // rows KC + i of the window, i = lane + 32 q
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
-        const int R = lane + 32 * q;
-        tv[q] = (R < W && k0 + R < n) ? y[min(k0 + (int)perm[R], n - 1)] : (TC)0;
+        const int i = lane + 32 * q, R = KC + i;
+        tv[q] = (i < kl && k0 + R < n) ? y[min(k0 + (int)perm[R], n - 1)] : (TC)0;
       }
-      TC t1[KC];  // the chunk's pivot values: rows 0 .. KC-1 of the permuted window
+      TC t1[KC];
 #pragma unroll
-      for (int j = 0; j < KC; ++j) t1[j] = __shfl_sync(FULL, tv[0], j);
+      for (int j = 0; j < KC; ++j) t1[j] = __shfl_sync(FULL, tc, j);
+      TC yc = (TC)0;
+      if (lane < KC) {
+        TC e[KC];
+        load_row8<TC, TC>(E11 + lane * KC, e);
+#pragma unroll
+        for (int j = 0; j < KC; ++j) yc = fma(e[j], t1[j], yc);
+      }
+      TC y1[KC];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) y1[j] = __shfl_sync(FULL, yc, j);
       __syncwarp();  // every gather is done before any row is written
+      if (lane < KC && k0 + lane < n) y[k0 + lane] = yc;
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
-        const int R = lane + 32 * q;
-        if (R < W && k0 + R < n) {
+        const int i = lane + 32 * q, R = KC + i;
+        if (i < kl && k0 + R < n) {
           TC e[KC];
-          load_row8<TC, TS>(E + R * KC, e);
+          load_row8<TC, TS>(L21 + i * KC, e);
           TC acc = tv[q];
 #pragma unroll
-          for (int j = 0; j < KC; ++j) acc = fma(e[j], t1[j], acc);
+          for (int j = 0; j < KC; ++j) acc = fma(e[j], y1[j], acc);
           y[k0 + R] = acc;
         }
       }
-    } else {  // backward chunk c: x_c = M1 y_c, y_a += M2 y_c (a = the ku2 rows above)
-      const int c = 2 * nc - 1 - t, k0 = c * KC, ku2 = cg.ku2, H = cg.H;
-      const TS* M = reinterpret_cast<const TS*>(rec);
+    } else {  // backward chunk c: x_c = U11^{-1} y_c, y_a -= U_a x_c (a = the ku2 rows above)
+      const int c = 2 * nc - 1 - t, k0 = c * KC, ku2 = cg.ku2;
+      const TC* U11i = reinterpret_cast<const TC*>(rec);
+      const TS* Ua = reinterpret_cast<const TS*>(U11i + KC * KC);  // negated
       TC t1[KC];
       load_row8<TC, TC>(y + k0, t1);  // zeros past n
-      __syncwarp();                   // every lane holds y_c before x_c overwrites it
-      for (int R = lane; R < H; R += 32) {
-        const int pos = R < KC ? k0 + R : k0 - ku2 + (R - KC);
-        if (pos >= 0 && pos < n) {
-          TC e[KC];
-          load_row8<TC, TS>(M + R * KC, e);
-          TC acc = R < KC ? (TC)0 : y[pos];
+      TC xc = (TC)0;
+      if (lane < KC) {
+        TC e[KC];
+        load_row8<TC, TC>(U11i + lane * KC, e);
 #pragma unroll
-          for (int j = 0; j < KC; ++j) acc = fma(e[j], t1[j], acc);
-          y[pos] = acc;
-        }
+        for (int j = 0; j < KC; ++j) xc = fma(e[j], t1[j], xc);
       }
+      TC x1[KC];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) x1[j] = __shfl_sync(FULL, xc, j);
+      __syncwarp();  // every lane holds y_c before x_c overwrites it
+      if (lane < KC && k0 + lane < n) y[k0 + lane] = xc;
+      // one row per lane and round; written as a loop over the lane's rows of the round
+      // (at most one), which measured faster than the equivalent predicated body
+#pragma unroll
+      for (int qb = 0; qb < QB; ++qb)
+        for (int i = lane + 32 * qb; i < ku2; i += 1 << 20) {
+          const int pos = k0 - ku2 + i;
+          if (pos >= 0) {
+            TC e[KC];
+            load_row8<TC, TS>(Ua + i * KC, e);
+            TC acc = y[pos];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) acc = fma(e[j], x1[j], acc);
+            y[pos] = acc;
+          }
+        }
     }
     __syncwarp();  // every lane is done with this stage (and with y) before it is refilled
     if (lane == 0 && t + STAGES < total) issue(t + STAGES);
   }
   const double sc = rscale ? *rscale : 1.0;
+  int a = a0, c = c0;
   for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
-    const int a = t % B.bx, c = t / B.bx;
     if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
-      z[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] = sc * (double)y[t];
+      z[wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny)] = sc * (double)y[t];
+    a += da;
+    c += dc;
+    if (a >= B.bx) {
+      a -= B.bx;
+      ++c;
+    }
   }
+}
+
+template <typename TC, typename TS, int WPC, int STAGES, int QF, int QB>
+void chunked_launch(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
+                    const double* rscale, double* z, const int* skip, int* err, cudaStream_t st, const IterArgs* ia,
+                    size_t smem) {
+  cudaFuncSetAttribute(k_ras_apply2d_chunked<TC, TS, WPC, STAGES, QF, QB>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ras_apply2d_chunked<TC, TS, WPC, STAGES, QF, QB><<<(nblocks + WPC - 1) / WPC, 32 * WPC, smem, st>>>(
+      g, blocks, nblocks, fs, r, rscale, z, skip, err, ia);
 }
 
 template <typename TC, typename TS, int WPC, int STAGES>
@@ -760,18 +821,13 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
                       const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
                       const IterArgs* ia) {
   const size_t smem = WPC * chunk_smem<TC, STAGES>(fs.xstage, fs.n_max).total;
-  const int grid = (nblocks + WPC - 1) / WPC;
-  if (kChunk + fs.kl_max <= 96) {
-    cudaFuncSetAttribute(k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 3><<<grid, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale, z,
-                                                                              skip, err, ia);
-  } else {
-    cudaFuncSetAttribute(k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_ras_apply2d_chunked<TC, TS, WPC, STAGES, 5><<<grid, 32 * WPC, smem, st>>>(g, blocks, nblocks, fs, r, rscale, z,
-                                                                              skip, err, ia);
-  }
+  // rounds of 32 rows: kl rows forward, ku2 <= 2 kl rows backward
+  if (fs.kl_max <= 64)
+    chunked_launch<TC, TS, WPC, STAGES, 2, 4>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia, smem);
+  else if (fs.kl_max <= 96)
+    chunked_launch<TC, TS, WPC, STAGES, 3, 6>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia, smem);
+  else
+    chunked_launch<TC, TS, WPC, STAGES, 4, 8>(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia, smem);
   count_launches(1);
 }
 
@@ -820,7 +876,7 @@ size_t chunked_smem_bytes(int prec, int xstage, int n_max) {
 
 static size_t chunk_build_smem(int prec, int kl_max) {
   const size_t tc = prec == PFC_F64 ? 8 : 4;
-  return (size_t)4 * (kChunk + 2 * kl_max) * (kChunk * tc + sizeof(int));
+  return (size_t)4 * (kChunk + kl_max) * (kChunk * tc + sizeof(int));
 }
 
 bool apply_variant_ok(int v, int prec, int kl_max, int xstage, int n_max) {
