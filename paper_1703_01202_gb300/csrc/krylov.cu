@@ -10,6 +10,12 @@
 // convergence flag).  So one Gram-Schmidt pass costs one kernel per vector
 // sweep, with no separate reduction launch.
 //
+// On the mixed path (F32/BF16 factors) the Arnoldi sweeps run in the float-float
+// arithmetic of ff.cuh on the FP32 pipe (FF = true): the multi-dot products and the
+// multi-axpy w -= sum c_k V_k carry 48-bit significands and the new w is stored
+// in FP64.  The Arnoldi relation J Z_j = V H holds to that accuracy whatever the
+// coefficients, so GMRES sees FP64-grade vectors at FP32-pipe cost.
+//
 // The basis is kept unnormalised: V_i = scale_i * Vraw_i with scale_i held on
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
 // the cycle's "done" flag and returns at once when it is set, which lets the
@@ -17,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "ff.cuh"
 #include "pfc_internal.cuh"
 
 namespace pfc {
@@ -147,8 +154,30 @@ __device__ __forceinline__ void dot_sweep(const double* const* p, const double2*
   }
 }
 
+// The same sweep in float-float: acc[k] (hi) and accl[k] (lo).
+template <int C>
+__device__ __forceinline__ void dot_sweep_ff(const double* const* p, const double2* __restrict__ w2, long long n2,
+                                             long long start, long long stride, double* acc) {
+  ff a[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) a[k] = {0.0f, 0.0f};
+  for (long long i = start; i < n2; i += stride) {
+    const double2 wi = w2[i];
+    const ff wx = ff_of(wi.x), wy = ff_of(wi.y);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const double2 v = reinterpret_cast<const double2*>(p[k])[i];
+      a[k] = ff_acc(a[k], ff_prod(ff_of(v.x), wx));
+      a[k] = ff_acc(a[k], ff_prod(ff_of(v.y), wy));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < C; ++k) acc[k] = ff_to_double(a[k]);
+}
+
 // partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i]; pairs of points per
 // 16-byte load (every vector starts 256-byte aligned).
+template <bool FF>
 __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double* const* __restrict__ tab, int nv,
                                                  const double* __restrict__ w, long long n,
                                                  double* __restrict__ partial, const int* __restrict__ skip,
@@ -174,17 +203,32 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   const long long stride = (long long)gridDim.x * NT;
   const double2* w2 = reinterpret_cast<const double2*>(w);
   const long long start = blockIdx.x * (long long)NT + threadIdx.x;
-  switch (cnt) {  // block-uniform
-    case 0: break;
-    case 1: dot_sweep<1>(p, w2, n2, start, stride, acc); break;
-    case 2: dot_sweep<2>(p, w2, n2, start, stride, acc); break;
-    case 3: dot_sweep<3>(p, w2, n2, start, stride, acc); break;
-    case 4: dot_sweep<4>(p, w2, n2, start, stride, acc); break;
-    case 5: dot_sweep<5>(p, w2, n2, start, stride, acc); break;
-    case 6: dot_sweep<6>(p, w2, n2, start, stride, acc); break;
-    case 7: dot_sweep<7>(p, w2, n2, start, stride, acc); break;
-    default:
-      if (cnt > 0) dot_sweep<G>(p, w2, n2, start, stride, acc);
+  if (FF) {
+    switch (cnt) {  // block-uniform
+      case 0: break;
+      case 1: dot_sweep_ff<1>(p, w2, n2, start, stride, acc); break;
+      case 2: dot_sweep_ff<2>(p, w2, n2, start, stride, acc); break;
+      case 3: dot_sweep_ff<3>(p, w2, n2, start, stride, acc); break;
+      case 4: dot_sweep_ff<4>(p, w2, n2, start, stride, acc); break;
+      case 5: dot_sweep_ff<5>(p, w2, n2, start, stride, acc); break;
+      case 6: dot_sweep_ff<6>(p, w2, n2, start, stride, acc); break;
+      case 7: dot_sweep_ff<7>(p, w2, n2, start, stride, acc); break;
+      default:
+        if (cnt > 0) dot_sweep_ff<G>(p, w2, n2, start, stride, acc);
+    }
+  } else {
+    switch (cnt) {  // block-uniform
+      case 0: break;
+      case 1: dot_sweep<1>(p, w2, n2, start, stride, acc); break;
+      case 2: dot_sweep<2>(p, w2, n2, start, stride, acc); break;
+      case 3: dot_sweep<3>(p, w2, n2, start, stride, acc); break;
+      case 4: dot_sweep<4>(p, w2, n2, start, stride, acc); break;
+      case 5: dot_sweep<5>(p, w2, n2, start, stride, acc); break;
+      case 6: dot_sweep<6>(p, w2, n2, start, stride, acc); break;
+      case 7: dot_sweep<7>(p, w2, n2, start, stride, acc); break;
+      default:
+        if (cnt > 0) dot_sweep<G>(p, w2, n2, start, stride, acc);
+    }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
     const double wi = w[n - 1];
@@ -233,7 +277,8 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
 }
 
 // w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w
-template <bool SUM>
+// (FF: the sum over k in float-float, one FP64 addition per point to store w)
+template <bool SUM, bool FF>
 __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const double* x0,
                                                   const double* const* __restrict__ tab, int nx,
                                                   const double* __restrict__ coef, double sign, long long n,
@@ -246,9 +291,11 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
   }
   __shared__ double red[2][NT / 32];
   __shared__ double c[kMaxVecs];
+  __shared__ ff cf[kMaxVecs];
   __shared__ const double* sp[kMaxVecs];
   for (int k = threadIdx.x; k < nx; k += NT) {
     c[k] = sign * coef[k];
+    cf[k] = ff_of(sign * coef[k]);
     sp[k] = vec_at(x0, tab, k);
   }
   __syncthreads();
@@ -258,11 +305,24 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
   double2* w2 = reinterpret_cast<double2*>(w);
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
     double2 acc = w2[i];
+    if (FF) {
+      ff ax = ff_of(acc.x), ay = ff_of(acc.y);
 #pragma unroll 4
-    for (int k = 0; k < nx; ++k) {
-      const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
-      acc.x = fma(c[k], a.x, acc.x);
-      acc.y = fma(c[k], a.y, acc.y);
+      for (int k = 0; k < nx; ++k) {
+        const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
+        const ff ck = cf[k];
+        ax = ff_acc(ax, ff_prod(ck, ff_of(a.x)));
+        ay = ff_acc(ay, ff_prod(ck, ff_of(a.y)));
+      }
+      acc.x = ff_to_double(ax);
+      acc.y = ff_to_double(ay);
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < nx; ++k) {
+        const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
+        acc.x = fma(c[k], a.x, acc.x);
+        acc.y = fma(c[k], a.y, acc.y);
+      }
     }
     w2[i] = acc;
     s2 = fma(acc.y, acc.y, fma(acc.x, acc.x, s2));
@@ -364,24 +424,33 @@ int red_ctas(long long n) {
 }  // namespace
 
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
-                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st) {
+                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
+                     bool ff) {
   // half the CTAs of the other sweeps: each thread covers twice the points, so the
   // per-CTA reduction of 8 sums is a smaller share of the FP64 work
   const int bx = std::max(1, red_ctas((n + 1) / 2) / 2);
   dim3 grid(bx, (nv + G - 1) / G);
-  k_multidot<<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+  if (ff)
+    k_multidot<true><<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+  else
+    k_multidot<false><<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
   count_launches(1);
 }
 
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool ff) {
   const int bx = red_ctas((n + 1) / 2);
   // the sum of w is read only by the kSums tail (and by callers of partials-only sweeps)
-  if (tail.counter && tail.kind != Tail::kSums)
-    k_multiaxpy<false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+  const bool sum = !(tail.counter && tail.kind != Tail::kSums);
+  if (sum && ff)
+    k_multiaxpy<true, true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+  else if (sum)
+    k_multiaxpy<true, false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+  else if (ff)
+    k_multiaxpy<false, true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
   else
-    k_multiaxpy<true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+    k_multiaxpy<false, false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
   count_launches(1);
 }
 

@@ -450,6 +450,9 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
   return PFC_OK;
 }
 
+// The mixed path (F32/BF16 factors) runs the Arnoldi sweeps in float-float arithmetic.
+bool ff_sweeps(const pfc_state* s) { return s->p.factor_prec != PFC_F64; }
+
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
          const pfc::IterArgs* ia = nullptr) {
   if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
@@ -591,10 +594,11 @@ bool build_cycle_graph(pfc_state* s) {
     jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
     for (int pass = 0; pass < passes; ++pass) {
       const pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
-      pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st);
+      pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
+                           ff_sweeps(s));
       const pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
       pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done,
-                            pass ? reorth : nullptr, ta, s->st);
+                            pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
     }
     pfc::launch_cycle_cond(s->ctl, m, h, s->st);
     cudaGraph_t body = nullptr;
@@ -670,10 +674,11 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
         jvp(s, zj, s->q, idt, w, done);
         for (int pass = 0; pass < passes; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
           const pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
-          pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st);
+          pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
+                               ff_sweeps(s));
           const pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
           pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
-                                pass ? reorth : nullptr, ta, s->st);
+                                pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
         }
       }
       CU(cudaGetLastError());

@@ -252,11 +252,13 @@ struct Tail {
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
 // With tail.ia set (graph mode) the vector count is ia->j + 2 (dot) / ia->j + 1 (axpy), w is
 // ia->w, and nv / nx only bound the grid.
+// ff: float-float arithmetic on the FP32 pipe (the mixed path's Arnoldi sweeps)
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
-                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st);
+                     double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
+                     bool ff = false);
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
-                      cudaStream_t st);
+                      cudaStream_t st, bool ff = false);
 // Graph-mode helpers: ia <- the vectors of iteration j = ctl->its; loop condition of a GMRES cycle.
 void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
                        cudaStream_t st);
