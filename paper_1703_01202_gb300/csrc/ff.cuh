@@ -74,6 +74,31 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 }
 __device__ __forceinline__ ff ff_scale(ff a, float c) { return {__fmul_rn(a.hi, c), __fmul_rn(a.lo, c)}; }  // c a power of 2
 
+// A faster split for streaming kernels: hi = x cut to 24 significand bits, lo =
+// the next 23 bits, read as 2^(e-23) (1 + m) - 2^(e-23) (one float subtraction, exact):
+// hi + lo = x to 2^-46 relative for |x| >= 2^-102; below that lo = 0, and below
+// 2^-126 hi = 0 as well.
+__device__ __forceinline__ ff ff_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int fexp = (int)((h32 >> 20) & 0x7ffu) - 896;  // float exponent field of hi
+  const unsigned mant = __funnelshift_l(l32, h32, 3) & 0x7fffffu;
+  if (fexp <= 0) return {0.0f, 0.0f};
+  const float hi = __uint_as_float(sign | ((unsigned)fexp << 23) | mant);
+  if (fexp <= 23) return {hi, 0.0f};
+  const unsigned eb = sign | ((unsigned)(fexp - 23) << 23);
+  return {hi, __fsub_rn(__uint_as_float(eb | ((l32 >> 6) & 0x7fffffu)), __uint_as_float(eb))};
+}
+// x cut to a float (24 significand bits, toward zero; 0 below 2^-126).
+__device__ __forceinline__ float f32_cut(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const int fexp = (int)((h32 >> 20) & 0x7ffu) - 896;
+  if (fexp <= 0) return 0.0f;
+  return __uint_as_float((h32 & 0x80000000u) | ((unsigned)fexp << 23) | (__funnelshift_l(l32, h32, 3) & 0x7fffffu));
+}
+
 // Product a * b as an unnormalised pair (p, e): p = fl(a.hi b.hi), e = its exact
 // error plus the cross terms (a.lo b.lo, about 2^-48 of the product, is dropped).
 __device__ __forceinline__ ff ff_prod(ff a, ff b) {

@@ -10,11 +10,14 @@
 // convergence flag).  So one Gram-Schmidt pass costs one kernel per vector
 // sweep, with no separate reduction launch.
 //
-// On the mixed path (F32/BF16 factors) the Arnoldi sweeps run in the float-float
-// arithmetic of ff.cuh on the FP32 pipe (FF = true): the multi-dot products and the
-// multi-axpy w -= sum c_k V_k carry 48-bit significands and the new w is stored
-// in FP64.  The Arnoldi relation J Z_j = V H holds to that accuracy whatever the
-// coefficients, so GMRES sees FP64-grade vectors at FP32-pipe cost.
+// On the mixed path (F32/BF16 factors) the Arnoldi sweeps run on the FP32 pipe
+// (FF = true).  The multi-axpy w -= sum c_k V_k uses the float-float arithmetic of
+// ff.cuh (about 2^-46 relative) and stores w in FP64: the Arnoldi relation
+// J Z_j = V H holds to that accuracy whatever the coefficients are.  The
+// coefficients themselves (the multi-dot products) then only decide how
+// orthogonal the new vector comes out, so they are summed in FP32 from the
+// vectors cut to 24-bit significands (about 2^-24 of |V_i| |w| per product);
+// the conditional second pass (DGKS) restores orthogonality where it matters.
 //
 // The basis is kept unnormalised: V_i = scale_i * Vraw_i with scale_i held on
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
@@ -23,8 +26,10 @@
 #include <algorithm>
 #include <cmath>
 
+#include "../../include/pfc.h"
 #include "ff.cuh"
 #include "pfc_internal.cuh"
+#include "pfc_tma.cuh"
 
 namespace pfc {
 namespace {
@@ -139,102 +144,134 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
   }
 }
 
-// acc[k] += sum over this thread's pairs of points of V_k . w, for exactly C vectors
-// (a compile-time count: no predicated-off FP64 work for a partial group).
-template <int C>
-__device__ __forceinline__ void dot_sweep(const double* const* p, const double2* __restrict__ w2, long long n2,
-                                          long long start, long long stride, double* acc) {
-  for (long long i = start; i < n2; i += stride) {
-    const double2 wi = w2[i];
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-      const double2 a = reinterpret_cast<const double2*>(p[k])[i];
-      acc[k] = fma(a.y, wi.y, fma(a.x, wi.x, acc[k]));
-    }
-  }
+// ---- Streamed sweeps.  Each CTA takes tiles of kTile points round-robin and
+// brings every vector's tile into shared memory with one bulk copy (TMA,
+// completion on an mbarrier) through a ring of kStages buffers, so a CTA keeps
+// up to kStages x 8 KB in flight without holding them in registers; the threads
+// then work from shared memory (kPts points each).  Element q of a CTA's copy
+// sequence is (local tile q / per, vector q % per).
+constexpr int kTile = 1024;
+constexpr int kStages = 6;
+constexpr int kPts = kTile / NT;
+constexpr int kSweepMinCtas = 4;  // CTAs per SM the register budget allows (__launch_bounds__)
+
+struct Ring {
+  double* buf;    // kStages x kTile
+  uint64_t* bar;  // kStages
+};
+
+// Thread 0: copy of sequence element q of this CTA (vector vp, local tile lt).
+__device__ __forceinline__ void ring_issue(const Ring& rg, int q, const double* vp, long long n, int lt) {
+  const int st = q % kStages;
+  const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+  const long long cnt = min((long long)kTile, n - base);
+  const uint32_t bytes = (uint32_t)((cnt * 8 + 15) & ~15ll);  // an odd count reads the 8-byte pad
+  fence_proxy_async();
+  mbar_expect_tx(&rg.bar[st], bytes);
+  bulk_g2s(rg.buf + (size_t)st * kTile, vp + base, bytes, &rg.bar[st]);
 }
 
-// The same sweep in float-float: acc[k] (hi) and accl[k] (lo).
-template <int C>
-__device__ __forceinline__ void dot_sweep_ff(const double* const* p, const double2* __restrict__ w2, long long n2,
-                                             long long start, long long stride, double* acc) {
-  ff a[C];
-#pragma unroll
-  for (int k = 0; k < C; ++k) a[k] = {0.0f, 0.0f};
-  for (long long i = start; i < n2; i += stride) {
-    const double2 wi = w2[i];
-    const ff wx = ff_of(wi.x), wy = ff_of(wi.y);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-      const double2 v = reinterpret_cast<const double2*>(p[k])[i];
-      a[k] = ff_acc(a[k], ff_prod(ff_of(v.x), wx));
-      a[k] = ff_acc(a[k], ff_prod(ff_of(v.y), wy));
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < C; ++k) acc[k] = ff_to_double(a[k]);
+// Every thread waits for element q; false (all threads) when a wait ran out.
+__device__ __forceinline__ bool ring_wait(const Ring& rg, int q) {
+  const bool ok = mbar_wait_bounded(&rg.bar[q % kStages], (uint32_t)((q / kStages) & 1));
+  return __syncthreads_and(ok) != 0;
 }
 
-// partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i]; pairs of points per
-// 16-byte load (every vector starts 256-byte aligned).
+// The multi-dot of this CTA's group of up to G vectors against w.  FF: FP32 products.
 template <bool FF>
-__global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double* const* __restrict__ tab, int nv,
-                                                 const double* __restrict__ w, long long n,
-                                                 double* __restrict__ partial, const int* __restrict__ skip,
-                                                 const int* __restrict__ only_if, Tail tail) {
+__device__ __forceinline__ void dot_tile(const double* tb, int cntp, const double* wv, const float* wf, double* acc,
+                                         float* af, int k) {
+#pragma unroll
+  for (int p = 0; p < kPts; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (i < cntp) {
+      const double v = tb[i];
+      if (FF)
+        af[k] = __fmaf_rn(f32_cut(v), wf[p], af[k]);
+      else
+        acc[k] = fma(v, wv[p], acc[k]);
+    }
+  }
+}
+
+// partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles.
+template <bool FF>
+__global__ void __launch_bounds__(NT, kSweepMinCtas)
+    k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
+               double* __restrict__ partial, const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
   if ((skip && *skip) || (only_if && !*only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nv = tail.ia->j + 2;
     w = tail.ia->w;
   }
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ring rg{reinterpret_cast<double*>(smem),
+                reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kTile * sizeof(double))};
   __shared__ double red[NT / 32][G];
-  __shared__ const double* sp[G];
+  __shared__ const double* sp[G + 1];
   const int g0 = blockIdx.y * G;
-  const int cnt = min(G, nv - g0);  // <= 0 for spare groups of a graph-mode grid: they only take a ticket
-  if (threadIdx.x < G) sp[threadIdx.x] = threadIdx.x < cnt ? vec_at(v0, tab, g0 + threadIdx.x) : w;
+  const int cnt = max(0, min(G, nv - g0));  // 0 for spare groups of a graph-mode grid: they only take a ticket
+  const int tid = threadIdx.x;
+  if (tid <= G) sp[tid] = tid == 0 ? w : (tid - 1 < cnt ? vec_at(v0, tab, g0 + tid - 1) : w);
+  const long long ntile = (n + kTile - 1) / kTile;
+  const int my_tiles = cnt > 0 && blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int per = 1 + cnt, total = my_tiles * per;
   __syncthreads();
-  const double* p[G];
-#pragma unroll
-  for (int k = 0; k < G; ++k) p[k] = sp[k];
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&rg.bar[st], 1);
+    fence_mbar_init();
+    for (int q = 0; q < kStages && q < total; ++q) ring_issue(rg, q, sp[q % per], n, q / per);
+  }
+  __syncthreads();
   double acc[G];
+  float af[G];
 #pragma unroll
-  for (int k = 0; k < G; ++k) acc[k] = 0.0;
-  const long long n2 = n >> 1;
-  const long long stride = (long long)gridDim.x * NT;
-  const double2* w2 = reinterpret_cast<const double2*>(w);
-  const long long start = blockIdx.x * (long long)NT + threadIdx.x;
-  if (FF) {
-    switch (cnt) {  // block-uniform
-      case 0: break;
-      case 1: dot_sweep_ff<1>(p, w2, n2, start, stride, acc); break;
-      case 2: dot_sweep_ff<2>(p, w2, n2, start, stride, acc); break;
-      case 3: dot_sweep_ff<3>(p, w2, n2, start, stride, acc); break;
-      case 4: dot_sweep_ff<4>(p, w2, n2, start, stride, acc); break;
-      case 5: dot_sweep_ff<5>(p, w2, n2, start, stride, acc); break;
-      case 6: dot_sweep_ff<6>(p, w2, n2, start, stride, acc); break;
-      case 7: dot_sweep_ff<7>(p, w2, n2, start, stride, acc); break;
-      default:
-        if (cnt > 0) dot_sweep_ff<G>(p, w2, n2, start, stride, acc);
+  for (int k = 0; k < G; ++k) {
+    acc[k] = 0.0;
+    af[k] = 0.0f;
+  }
+  bool ok = true;
+  int q = 0;
+  for (int lt = 0; lt < my_tiles && ok; ++lt) {
+    const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+    const int cntp = (int)min((long long)kTile, n - base);
+    double wv[kPts];
+    float wf[kPts];
+    if (!(ok = ring_wait(rg, q))) break;
+    {
+      const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
+#pragma unroll
+      for (int p = 0; p < kPts; ++p) {
+        const int i = tid + p * NT;
+        wv[p] = i < cntp ? tb[i] : 0.0;
+        if (FF) wf[p] = f32_cut(wv[p]);
+      }
     }
-  } else {
-    switch (cnt) {  // block-uniform
-      case 0: break;
-      case 1: dot_sweep<1>(p, w2, n2, start, stride, acc); break;
-      case 2: dot_sweep<2>(p, w2, n2, start, stride, acc); break;
-      case 3: dot_sweep<3>(p, w2, n2, start, stride, acc); break;
-      case 4: dot_sweep<4>(p, w2, n2, start, stride, acc); break;
-      case 5: dot_sweep<5>(p, w2, n2, start, stride, acc); break;
-      case 6: dot_sweep<6>(p, w2, n2, start, stride, acc); break;
-      case 7: dot_sweep<7>(p, w2, n2, start, stride, acc); break;
-      default:
-        if (cnt > 0) dot_sweep<G>(p, w2, n2, start, stride, acc);
+    __syncthreads();  // the buffer is free
+    if (tid == 0 && q + kStages < total) ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
+    ++q;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      if (k < cnt) {  // block-uniform
+        if (!(ok = ring_wait(rg, q))) break;
+        dot_tile<FF>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wf, acc, af, k);
+        __syncthreads();
+        if (tid == 0 && q + kStages < total)
+          ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
+        ++q;
+      }
     }
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
-    const double wi = w[n - 1];
+  if (!ok) {  // a copy never arrived: record, drain what is in flight, and still take the ticket
+    if (tid == 0) {
+      if (tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
+      for (int u = q; u < q + kStages && u < total; ++u)
+        mbar_wait_bounded(&rg.bar[u % kStages], (uint32_t)((u / kStages) & 1));
+    }
+  }
+  if (FF) {
 #pragma unroll
-    for (int k = 0; k < G; ++k)
-      if (k < cnt) acc[k] = fma(p[k][n - 1], wi, acc[k]);
+    for (int k = 0; k < G; ++k) acc[k] = f2d_bits(af[k]);
   }
   // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
   // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
@@ -242,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   // per lane instead of 8 full butterflies).  Lane l ends with the sum of value
   // 4 b4 + 2 b3 + b2 (b_i = bit i of l).
   static_assert(G == 8, "reduce-scatter written for 8 values");
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = tid & 31, wid = tid >> 5;
   const unsigned FULL = 0xffffffffu;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -268,74 +305,106 @@ __global__ void __launch_bounds__(NT) k_multidot(const double* v0, const double*
   acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
   if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
   __syncthreads();
-  if ((int)threadIdx.x < cnt) {
+  if (tid < cnt) {
     double s = 0.0;
-    for (int q = 0; q < NT / 32; ++q) s += red[q][threadIdx.x];
-    partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    for (int qq = 0; qq < NT / 32; ++qq) s += red[qq][tid];
+    partial[(size_t)(g0 + tid) * gridDim.x + blockIdx.x] = s;
   }
   if (tail.counter) last_cta_tail(tail, partial, nv, gridDim.x);
 }
 
-// w = w + sign * sum_k coef[k] X_k ; partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w
-// (FF: the sum over k in float-float, one FP64 addition per point to store w)
+// w = w + sign * sum_k coef[k] X_k over this CTA's tiles (the tile of w comes last);
+// partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w.  FF: the sum over
+// k in float-float, one FP64 addition per point to store w.
 template <bool SUM, bool FF>
-__global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const double* x0,
-                                                  const double* const* __restrict__ tab, int nx,
-                                                  const double* __restrict__ coef, double sign, long long n,
-                                                  double* __restrict__ partial, const int* __restrict__ skip,
-                                                  const int* __restrict__ only_if, Tail tail) {
+__global__ void __launch_bounds__(NT, kSweepMinCtas)
+    k_multiaxpy(double* __restrict__ w, const double* x0, const double* const* __restrict__ tab, int nx,
+                const double* __restrict__ coef, double sign, long long n, double* __restrict__ partial,
+                const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
   if ((skip && *skip) || (only_if && !*only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nx = tail.ia->j + 1;
     w = tail.ia->w;
   }
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ring rg{reinterpret_cast<double*>(smem),
+                reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kTile * sizeof(double))};
   __shared__ double red[2][NT / 32];
   __shared__ double c[kMaxVecs];
   __shared__ ff cf[kMaxVecs];
-  __shared__ const double* sp[kMaxVecs];
-  for (int k = threadIdx.x; k < nx; k += NT) {
-    c[k] = sign * coef[k];
-    cf[k] = ff_of(sign * coef[k]);
-    sp[k] = vec_at(x0, tab, k);
+  __shared__ const double* sp[kMaxVecs + 1];
+  const int tid = threadIdx.x;
+  for (int k = tid; k <= nx; k += NT) {
+    if (k < nx) {
+      c[k] = sign * coef[k];
+      cf[k] = ff_of(sign * coef[k]);
+    }
+    sp[k] = k < nx ? vec_at(x0, tab, k) : w;
+  }
+  const long long ntile = (n + kTile - 1) / kTile;
+  const int my_tiles = blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int per = nx + 1, total = my_tiles * per;
+  __syncthreads();
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&rg.bar[st], 1);
+    fence_mbar_init();
+    for (int q = 0; q < kStages && q < total; ++q) ring_issue(rg, q, sp[q % per], n, q / per);
   }
   __syncthreads();
   double s2 = 0.0, s1 = 0.0;
-  const long long n2 = n >> 1;
-  const long long stride = (long long)gridDim.x * NT;
-  double2* w2 = reinterpret_cast<double2*>(w);
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n2; i += stride) {
-    double2 acc = w2[i];
-    if (FF) {
-      ff ax = ff_of(acc.x), ay = ff_of(acc.y);
-#pragma unroll 4
-      for (int k = 0; k < nx; ++k) {
-        const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
-        const ff ck = cf[k];
-        ax = ff_acc(ax, ff_prod(ck, ff_of(a.x)));
-        ay = ff_acc(ay, ff_prod(ck, ff_of(a.y)));
-      }
-      acc.x = ff_to_double(ax);
-      acc.y = ff_to_double(ay);
-    } else {
-#pragma unroll 4
-      for (int k = 0; k < nx; ++k) {
-        const double2 a = reinterpret_cast<const double2*>(sp[k])[i];
-        acc.x = fma(c[k], a.x, acc.x);
-        acc.y = fma(c[k], a.y, acc.y);
-      }
+  bool ok = true;
+  int q = 0;
+  for (int lt = 0; lt < my_tiles && ok; ++lt) {
+    const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+    const int cntp = (int)min((long long)kTile, n - base);
+    double acc[kPts];
+    ff af[kPts];
+#pragma unroll
+    for (int p = 0; p < kPts; ++p) {
+      acc[p] = 0.0;
+      af[p] = {0.0f, 0.0f};
     }
-    w2[i] = acc;
-    s2 = fma(acc.y, acc.y, fma(acc.x, acc.x, s2));
-    if (SUM) s1 += acc.x + acc.y;
+    for (int k = 0; k <= nx; ++k) {
+      if (!(ok = ring_wait(rg, q))) break;
+      const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
+      if (k < nx) {
+        const double ck = c[k];
+        const ff cfk = cf[k];
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          const int i = tid + p * NT;
+          if (i < cntp) {
+            if (FF)
+              af[p] = ff_acc(af[p], ff_prod(cfk, ff_split(tb[i])));
+            else
+              acc[p] = fma(ck, tb[i], acc[p]);
+          }
+        }
+      } else {  // the tile of w: add and store
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          const int i = tid + p * NT;
+          if (i < cntp) {
+            const double wn = FF ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
+            w[base + i] = wn;
+            s2 = fma(wn, wn, s2);
+            if (SUM) s1 += wn;
+          }
+        }
+      }
+      __syncthreads();  // the buffer is free
+      if (tid == 0 && q + kStages < total) ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
+      ++q;
+    }
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail
-    double acc = w[n - 1];
-    for (int k = 0; k < nx; ++k) acc = fma(c[k], sp[k][n - 1], acc);
-    w[n - 1] = acc;
-    s2 = fma(acc, acc, s2);
-    s1 += acc;
+  if (!ok) {  // a copy never arrived: record, drain what is in flight, and still take the ticket
+    if (tid == 0) {
+      if (tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
+      for (int u = q; u < q + kStages && u < total; ++u)
+        mbar_wait_bounded(&rg.bar[u % kStages], (uint32_t)((u / kStages) & 1));
+    }
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = tid & 31, wid = tid >> 5;
   s2 = warp_sum(s2);
   s1 = warp_sum(s1);
   if (lane == 0) {
@@ -343,10 +412,10 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(double* __restrict__ w, const 
     red[1][wid] = s1;
   }
   __syncthreads();
-  if (threadIdx.x < (SUM ? 2 : 1)) {
+  if (tid < (SUM ? 2 : 1)) {
     double s = 0.0;
-    for (int q = 0; q < NT / 32; ++q) s += red[threadIdx.x][q];
-    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    for (int qq = 0; qq < NT / 32; ++qq) s += red[tid][qq];
+    partial[(size_t)tid * gridDim.x + blockIdx.x] = s;
   }
   if (tail.counter) last_cta_tail(tail, partial, SUM ? 2 : 1, gridDim.x);
 }
@@ -426,31 +495,44 @@ int red_ctas(long long n) {
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
                      bool ff) {
-  // half the CTAs of the other sweeps: each thread covers twice the points, so the
-  // per-CTA reduction of 8 sums is a smaller share of the FP64 work
-  const int bx = std::max(1, red_ctas((n + 1) / 2) / 2);
-  dim3 grid(bx, (nv + G - 1) / G);
-  if (ff)
-    k_multidot<true><<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
-  else
-    k_multidot<false><<<grid, NT, 0, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+  // groups of G vectors in y; about kSweepMinCtas CTAs per SM in all
+  const int gy = (nv + G - 1) / G;
+  const long long ntile = (n + kTile - 1) / kTile;
+  const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
+  const dim3 grid(bx, gy);
+  const size_t smem = (size_t)kStages * kTile * sizeof(double) + kStages * 8;
+  if (ff) {
+    cudaFuncSetAttribute(k_multidot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_multidot<true><<<grid, NT, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+  } else {
+    cudaFuncSetAttribute(k_multidot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_multidot<false><<<grid, NT, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+  }
   count_launches(1);
 }
 
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st, bool ff) {
-  const int bx = red_ctas((n + 1) / 2);
+  const long long ntile = (n + kTile - 1) / kTile;
+  const int bx = (int)std::max(1ll, std::min(ntile, (long long)kRedCtas));
+  const size_t smem = (size_t)kStages * kTile * sizeof(double) + kStages * 8;
   // the sum of w is read only by the kSums tail (and by callers of partials-only sweeps)
   const bool sum = !(tail.counter && tail.kind != Tail::kSums);
+#define PFC_AXPY(S, F)                                                                                  \
+  do {                                                                                                  \
+    cudaFuncSetAttribute(k_multiaxpy<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    k_multiaxpy<S, F><<<bx, NT, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail); \
+  } while (0)
   if (sum && ff)
-    k_multiaxpy<true, true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+    PFC_AXPY(true, true);
   else if (sum)
-    k_multiaxpy<true, false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+    PFC_AXPY(true, false);
   else if (ff)
-    k_multiaxpy<false, true><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+    PFC_AXPY(false, true);
   else
-    k_multiaxpy<false, false><<<bx, NT, 0, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail);
+    PFC_AXPY(false, false);
+#undef PFC_AXPY
   count_launches(1);
 }
 

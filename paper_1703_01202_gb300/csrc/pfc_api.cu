@@ -37,8 +37,9 @@ struct pfc_state {
   int dim;
   // fields (device, N doubles each)
   double *phin, *phinm1, *Phi, *F, *q, *Pt, *Ft, *qt, *S, *W, *guess;
-  double *Vbuf, *Zbuf;  // (m+1) x N and m x N
-  const double** vtab;  // device pointer tables: vtab[i] = Vbuf + i N, ztab[i] = Zbuf + i N
+  double *Vbuf, *Zbuf;  // (m+1) and m vectors of vstride doubles
+  size_t vstride;       // N rounded up to 32 doubles: every basis vector starts 256-byte aligned
+  const double** vtab;  // device pointer tables: vtab[i] = Vbuf + i vstride, ztab[i] = Zbuf + i vstride
   const double** ztab;
   // preconditioner
   BlockDesc* blocks_dev;
@@ -284,6 +285,12 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
   }
 }
 
+// Doubles between consecutive Krylov basis vectors: N rounded up to 32 (every vector
+// 256-byte aligned, for 16-byte loads and bulk copies) plus 17 x 256 bytes, so that
+// the vectors of a power-of-two grid do not all start at the same offset modulo a
+// large power of two (the Gram-Schmidt sweeps read all of them at the same offsets).
+size_t basis_stride(long long N) { return ((size_t)N + 31) / 32 * 32 + 17 * 32; }
+
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
       tabs, feat, iargs, order, X;
@@ -356,8 +363,9 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->S = L.take(vec);
   pl->W = L.take(vec);
   pl->guess = L.take(vec);
-  pl->V = L.take(vec * (m + 1));
-  pl->Z = L.take(vec * m);
+  const size_t vstride = basis_stride(N);
+  pl->V = L.take(vstride * 8 * (m + 1));
+  pl->Z = L.take(vstride * 8 * m);
   pl->L = L.take(pl->sL * es * pl->nblocks);
   pl->U = L.take(pl->sU * es * pl->nblocks);
   pl->piv = L.take(pl->sP * pl->nblocks);
@@ -593,10 +601,12 @@ bool build_cycle_graph(pfc_state* s) {
     precond(s, nullptr, nullptr, nullptr, done, s->ia);
     jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
     for (int pass = 0; pass < passes; ++pass) {
-      const pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      td.err = s->status_dev + 1;
       pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
                            ff_sweeps(s));
-      const pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
+      ta.err = s->status_dev + 1;
       pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done,
                             pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
     }
@@ -658,25 +668,27 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
       if (rc) return rc;
       pfc::count_launches((long long)s->graph_body * std::max(1, s->ctl_h->its));
     }
-    // basis V_0 = v0, V_i = Vbuf + i N (pointer table s->vtab); Z_i = Zbuf + i N (s->ztab)
+    // basis V_0 = v0, V_i = Vbuf + i vstride (pointer table s->vtab); Z_i = Zbuf + i vstride (s->ztab)
     int j = graph ? m : 0;
     const int chunk = 3;
     while (j < m) {
       const int jstart = j;
       const int jend = std::min(m, j + chunk);
       for (; j < jend; ++j) {
-        const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * N;
-        double* zj = s->Zbuf + (size_t)j * N;
-        double* w = s->Vbuf + (size_t)(j + 1) * N;
+        const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * s->vstride;
+        double* zj = s->Zbuf + (size_t)j * s->vstride;
+        double* w = s->Vbuf + (size_t)(j + 1) * s->vstride;
         if (s->prof) CU(cudaEventRecord(s->ev[2 * j], s->st));
         precond(s, vj, &s->ctl->scale[j], zj, done);
         if (s->prof) CU(cudaEventRecord(s->ev[2 * j + 1], s->st));
         jvp(s, zj, s->q, idt, w, done);
         for (int pass = 0; pass < passes; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
-          const pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
+          pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
+          td.err = s->status_dev + 1;
           pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
                                ff_sweeps(s));
-          const pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
+          pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
+          ta.err = s->status_dev + 1;
           pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
                                 pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
         }
@@ -700,7 +712,8 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     if (its > 0) {
       pfc::launch_gmres_solve(s->ctl, s->st);
       // red[8] = |S|^2, red[9] = sum S
-      const pfc::Tail tsum{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 8};
+      pfc::Tail tsum{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 8};
+      tsum.err = s->status_dev + 1;
       pfc::launch_multiaxpy(s->S, s->Zbuf, s->ztab, its, s->ctl->y, 1.0, N, s->partial, nullptr, nullptr, tsum,
                             s->st);
       CU(cudaGetLastError());
@@ -715,7 +728,8 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     // restart: r = -F - J S
     jvp(s, s->S, s->q, idt, s->W, nullptr);
     pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
-    const pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 10};
+    pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 10};
+    tnrm.err = s->status_dev + 1;
     pfc::launch_multidot(s->W, s->vtab, 1, s->W, N, s->partial, nullptr, nullptr, tnrm, s->st);
     pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, eta2, s->st);
     v0 = s->W;
@@ -925,6 +939,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->guess = (double*)at(pl.guess);
   s->Vbuf = (double*)at(pl.V);
   s->Zbuf = (double*)at(pl.Z);
+  s->vstride = basis_stride(s->g.n);
   s->fs.L = at(pl.L);
   s->fs.U = at(pl.U);
   s->fs.piv = (uint8_t*)at(pl.piv);
@@ -1056,8 +1071,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->vtab = (const double**)at(pl.tabs);
   s->ztab = s->vtab + pfc::kMaxVecs;
   std::vector<const double*> tabs(2 * pfc::kMaxVecs, nullptr);
-  for (int i = 0; i <= p->gmres_restart; ++i) tabs[i] = s->Vbuf + (size_t)i * s->g.n;
-  for (int i = 0; i < p->gmres_restart; ++i) tabs[pfc::kMaxVecs + i] = s->Zbuf + (size_t)i * s->g.n;
+  for (int i = 0; i <= p->gmres_restart; ++i) tabs[i] = s->Vbuf + (size_t)i * s->vstride;
+  for (int i = 0; i < p->gmres_restart; ++i) tabs[pfc::kMaxVecs + i] = s->Zbuf + (size_t)i * s->vstride;
   if (cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
                       s->st) != cudaSuccess ||
       cudaMemcpyAsync((void*)s->fs.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s->st) !=

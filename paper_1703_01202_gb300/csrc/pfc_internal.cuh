@@ -247,6 +247,7 @@ struct Tail {
   unsigned int* counter;
   double* out;              // kSums: reduced values
   const IterArgs* ia;       // when set, j comes from ia->j (graph mode)
+  int* err = nullptr;       // PFC_ETIMEOUT is stored here when a bounded wait runs out
 };
 
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).

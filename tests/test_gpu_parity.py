@@ -207,6 +207,21 @@ def test_chunked_apply_steps_match_oracle(pfc, prec, tol):
     assert [r["dt"] for r in recs] == pytest.approx([o.dt for o in orecs], rel=1e-9)
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
+@pytest.mark.parametrize("shape", [(27, 21), (45, 37)])
+def test_odd_point_count_steps_match_oracle(pfc, shape, prec, tol):
+    """Grids of 567 and 1665 points: every Krylov vector has odd length, so the last
+    tile of each streamed Gram-Schmidt sweep is partial and odd (1665 = 1024 + 641);
+    two adaptive steps against the oracle's."""
+    phi = inputs.noise_field(shape, 0.07, 0.07, 1040)
+    prm = dict(dt_min=1e-2, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, shape, (3, 3), prec=prec, overlap=1, **prm)
+    s.set_field(phi)
+    s.run(2)
+    ref, _ = O.run(phi, H, GAMMA, O.Params(parts=(3, 3), overlap=1, **prm), 2)
+    assert np.abs(s.get_field() - ref).max() <= tol
+
+
 def test_twenty_steps_noise64_match_oracle(pfc):
     """64^2 liquid from noise, fixed dt = 0.1, 20 steps, left-RAS 4x4 cores of 16^2 with
     one overlap cell per side (18^2 blocks): phi and energy per step against the oracle."""
