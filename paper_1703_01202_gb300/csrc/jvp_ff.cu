@@ -48,12 +48,12 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
   for (int i = tid; i < AX * AY; i += NT) {
     const int ly = i / AX, lx = i - ly * AX;
     const long long idx = wrap(x0 + lx - R, g.nx) + (long long)g.nx * wrap(y0 + ly - R, g.ny);
-    sV[ly][lx] = ff_of(vscale ? sc * v[idx] : v[idx]);
+    sV[ly][lx] = ff_split(vscale ? sc * v[idx] : v[idx]);
   }
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4), lx = i - ly * (AX - 4);
     const long long idx = wrap(x0 + lx - 1, g.nx) + (long long)g.nx * wrap(y0 + ly - 1, g.ny);
-    sQ[ly][lx] = ff_of(q[idx]);
+    sQ[ly][lx] = ff_split(q[idx]);
   }
   __syncthreads();
   for (int i = tid; i < (AX - 2) * (AY - 2); i += NT) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
     sL[ly - 1][lx - 1] = ff_lap(sV[ly][lx], sV[ly][lx + 1], sV[ly][lx - 1], sV[ly + 1][lx], sV[ly - 1][lx]);
   }
   __syncthreads();
-  const ff ih2 = ff_of(g.ih2), hih4 = ff_of(0.5 * g.ih2 * g.ih2), c0 = ff_of(0.5 * (1.0 - g.gamma));
+  const ff ih2 = ff_split(g.ih2), hih4 = ff_split(0.5 * g.ih2 * g.ih2), c0 = ff_split(0.5 * (1.0 - g.gamma));
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4) + 2, lx = i - (ly - 2) * (AX - 4) + 2;
     const int a = ly - 1, b = lx - 1;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
                                 ff_add(ff_mul(hih4, LLv), ff_mul(sQ[ly - 2][lx - 2], vv)));
   }
   __syncthreads();
-  const ff fidt = ff_of(idt);
+  const ff fidt = ff_split(idt);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int tx = threadIdx.x, ty = threadIdx.y + 8 * r;

@@ -122,7 +122,7 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
   if (!s_last) return;
   __threadfence();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int v = wid; v < nvals; v += NT / 32) {
+  for (int v = wid; v < nvals; v += (int)(blockDim.x / 32)) {
     double s = 0.0;
     for (int p = lane; p < nparts; p += 32) s += __ldcg(partial + (size_t)v * nparts + p);
     s = warp_sum(s);
@@ -145,36 +145,89 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
 }
 
 // ---- Streamed sweeps.  Each CTA takes tiles of kTile points round-robin and
-// brings every vector's tile into shared memory with one bulk copy (TMA,
-// completion on an mbarrier) through a ring of kStages buffers, so a CTA keeps
-// up to kStages x 8 KB in flight without holding them in registers; the threads
-// then work from shared memory (kPts points each).  Element q of a CTA's copy
-// sequence is (local tile q / per, vector q % per).
+// brings every vector's tile into shared memory with one bulk copy (TMA) through
+// a ring of kStages buffers.  One producer warp issues the copies; the NT
+// consumer threads wait for a buffer's "full" barrier (the copy's bytes), work
+// from shared memory (kPts points each) and release it warp by warp on its
+// "empty" barrier, so no CTA-wide barrier sits in the loop and a CTA keeps up to
+// kStages x 8 KB in flight.  Element q of a CTA's copy sequence is (local tile
+// q / per, vector q % per).
 constexpr int kTile = 1024;
 constexpr int kStages = 6;
 constexpr int kPts = kTile / NT;
-constexpr int kSweepMinCtas = 4;  // CTAs per SM the register budget allows (__launch_bounds__)
+constexpr int kSweepThreads = NT + 32;  // consumers + the producer warp
+constexpr int kSweepMinCtas = 4;        // CTAs per SM the register budget allows (__launch_bounds__)
 
 struct Ring {
-  double* buf;    // kStages x kTile
-  uint64_t* bar;  // kStages
+  double* buf;      // kStages x kTile
+  uint64_t* full;   // kStages: the copy landed (1 arrival + bytes)
+  uint64_t* empty;  // kStages: every consumer warp is done with it (NT / 32 arrivals)
 };
 
-// Thread 0: copy of sequence element q of this CTA (vector vp, local tile lt).
+__device__ __forceinline__ Ring ring_at(unsigned char* smem) {
+  double* buf = reinterpret_cast<double*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kTile * sizeof(double));
+  return Ring{buf, bars, bars + kStages};
+}
+
+// Producer lane: the copy of element q (vector vp, local tile lt) into buffer q % kStages.
 __device__ __forceinline__ void ring_issue(const Ring& rg, int q, const double* vp, long long n, int lt) {
   const int st = q % kStages;
   const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
   const long long cnt = min((long long)kTile, n - base);
   const uint32_t bytes = (uint32_t)((cnt * 8 + 15) & ~15ll);  // an odd count reads the 8-byte pad
   fence_proxy_async();
-  mbar_expect_tx(&rg.bar[st], bytes);
-  bulk_g2s(rg.buf + (size_t)st * kTile, vp + base, bytes, &rg.bar[st]);
+  mbar_expect_tx(&rg.full[st], bytes);
+  bulk_g2s(rg.buf + (size_t)st * kTile, vp + base, bytes, &rg.full[st]);
 }
 
-// Every thread waits for element q; false (all threads) when a wait ran out.
+// Producer (lane 0 of the last warp): issues elements 0 .. total-1, each once its buffer is
+// free; vec(q) gives the source vector.  On a wait that runs out it records the error and
+// waits for every copy it issued before returning.
+template <typename VecOf>
+__device__ __forceinline__ void ring_produce(const Ring& rg, int total, long long n, int per, VecOf vec, int* err) {
+  int issued = 0;
+  bool ok = true;
+  for (int q = 0; q < total; ++q) {
+    const int st = q % kStages;
+    if (q >= kStages && !(ok = mbar_wait_bounded(&rg.empty[st], (uint32_t)((q / kStages - 1) & 1)))) break;
+    ring_issue(rg, q, vec(q % per), n, q / per);
+    issued = q + 1;
+  }
+  if (!ok) {
+    if (err) atomicExch(err, PFC_ETIMEOUT);
+    for (int u = max(0, issued - kStages); u < issued; ++u)  // the last copy issued into each buffer
+      mbar_wait_bounded(&rg.full[u % kStages], (uint32_t)((u / kStages) & 1));
+  }
+}
+
+// The skip flags of a sweep (cycle done; second Gram-Schmidt pass not wanted), read by one
+// thread per CTA: a skipped sweep costs one load per CTA instead of one per thread.
+__device__ __forceinline__ bool sweep_skipped(const int* skip, const int* only_if) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (skip && *skip) || (only_if && !*only_if);
+  __syncthreads();
+  return s_skip != 0;
+}
+
+// Consumer side: wait for element q (false when the wait ran out) and release it.
 __device__ __forceinline__ bool ring_wait(const Ring& rg, int q) {
-  const bool ok = mbar_wait_bounded(&rg.bar[q % kStages], (uint32_t)((q / kStages) & 1));
-  return __syncthreads_and(ok) != 0;
+  return mbar_wait_bounded(&rg.full[q % kStages], (uint32_t)((q / kStages) & 1));
+}
+__device__ __forceinline__ void ring_release(const Ring& rg, int q) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&rg.empty[q % kStages]);
+}
+
+__device__ __forceinline__ void ring_init(const Ring& rg) {
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&rg.full[st], 1);
+      mbar_init(&rg.empty[st], NT / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
 }
 
 // The multi-dot of this CTA's group of up to G vectors against w.  FF: FP32 products.
@@ -196,33 +249,26 @@ __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const doubl
 
 // partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles.
 template <bool FF>
-__global__ void __launch_bounds__(NT, kSweepMinCtas)
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
                double* __restrict__ partial, const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
-  if ((skip && *skip) || (only_if && !*only_if)) return;
+  if (sweep_skipped(skip, only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nv = tail.ia->j + 2;
     w = tail.ia->w;
   }
   extern __shared__ __align__(128) unsigned char smem[];
-  const Ring rg{reinterpret_cast<double*>(smem),
-                reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kTile * sizeof(double))};
+  const Ring rg = ring_at(smem);
   __shared__ double red[NT / 32][G];
   __shared__ const double* sp[G + 1];
   const int g0 = blockIdx.y * G;
   const int cnt = max(0, min(G, nv - g0));  // 0 for spare groups of a graph-mode grid: they only take a ticket
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid <= G) sp[tid] = tid == 0 ? w : (tid - 1 < cnt ? vec_at(v0, tab, g0 + tid - 1) : w);
   const long long ntile = (n + kTile - 1) / kTile;
   const int my_tiles = cnt > 0 && blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
   const int per = 1 + cnt, total = my_tiles * per;
-  __syncthreads();
-  if (tid == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(&rg.bar[st], 1);
-    fence_mbar_init();
-    for (int q = 0; q < kStages && q < total; ++q) ring_issue(rg, q, sp[q % per], n, q / per);
-  }
-  __syncthreads();
+  ring_init(rg);  // also makes sp visible
   double acc[G];
   float af[G];
 #pragma unroll
@@ -230,81 +276,73 @@ __global__ void __launch_bounds__(NT, kSweepMinCtas)
     acc[k] = 0.0;
     af[k] = 0.0f;
   }
-  bool ok = true;
-  int q = 0;
-  for (int lt = 0; lt < my_tiles && ok; ++lt) {
-    const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
-    const int cntp = (int)min((long long)kTile, n - base);
-    double wv[kPts];
-    float wf[kPts];
-    if (!(ok = ring_wait(rg, q))) break;
+  if (wid == NT / 32) {  // producer warp
+    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err);
+  } else {
+    bool ok = true;
+    int q = 0;
+    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+      const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+      const int cntp = (int)min((long long)kTile, n - base);
+      double wv[kPts];
+      float wf[kPts];
+      if (!(ok = ring_wait(rg, q))) break;
+      {
+        const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          const int i = tid + p * NT;
+          wv[p] = i < cntp ? tb[i] : 0.0;
+          if (FF) wf[p] = f32_cut(wv[p]);
+        }
+      }
+      ring_release(rg, q++);
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        if (k < cnt) {  // block-uniform
+          if (!(ok = ring_wait(rg, q))) break;
+          dot_tile<FF>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wf, acc, af, k);
+          ring_release(rg, q++);
+        }
+      }
+    }
+    if (!ok && lane == 0 && tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
+    if (FF) {
+#pragma unroll
+      for (int k = 0; k < G; ++k) acc[k] = f2d_bits(af[k]);
+    }
+    // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
+    // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
+    // finishes one value over the remaining 4 lanes of its quarter (9 FP64 adds
+    // per lane instead of 8 full butterflies).  Lane l ends with the sum of value
+    // 4 b4 + 2 b3 + b2 (b_i = bit i of l).
+    static_assert(G == 8, "reduce-scatter written for 8 values");
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool up = lane & 16;
+      const double send = up ? acc[i] : acc[i + 4];
+      const double keep = up ? acc[i + 4] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const bool up = lane & 8;
+      const double send = up ? acc[i] : acc[i + 2];
+      const double keep = up ? acc[i + 2] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
     {
-      const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
-#pragma unroll
-      for (int p = 0; p < kPts; ++p) {
-        const int i = tid + p * NT;
-        wv[p] = i < cntp ? tb[i] : 0.0;
-        if (FF) wf[p] = f32_cut(wv[p]);
-      }
+      const bool up = lane & 4;
+      const double send = up ? acc[0] : acc[1];
+      const double keep = up ? acc[1] : acc[0];
+      acc[0] = keep + __shfl_xor_sync(FULL, send, 4);
     }
-    __syncthreads();  // the buffer is free
-    if (tid == 0 && q + kStages < total) ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
-    ++q;
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-      if (k < cnt) {  // block-uniform
-        if (!(ok = ring_wait(rg, q))) break;
-        dot_tile<FF>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wf, acc, af, k);
-        __syncthreads();
-        if (tid == 0 && q + kStages < total)
-          ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
-        ++q;
-      }
-    }
+    acc[0] += __shfl_xor_sync(FULL, acc[0], 2);
+    acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
+    if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
   }
-  if (!ok) {  // a copy never arrived: record, drain what is in flight, and still take the ticket
-    if (tid == 0) {
-      if (tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
-      for (int u = q; u < q + kStages && u < total; ++u)
-        mbar_wait_bounded(&rg.bar[u % kStages], (uint32_t)((u / kStages) & 1));
-    }
-  }
-  if (FF) {
-#pragma unroll
-    for (int k = 0; k < G; ++k) acc[k] = f2d_bits(af[k]);
-  }
-  // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
-  // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
-  // finishes one value over the remaining 4 lanes of its quarter (9 FP64 adds
-  // per lane instead of 8 full butterflies).  Lane l ends with the sum of value
-  // 4 b4 + 2 b3 + b2 (b_i = bit i of l).
-  static_assert(G == 8, "reduce-scatter written for 8 values");
-  const int lane = tid & 31, wid = tid >> 5;
-  const unsigned FULL = 0xffffffffu;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool up = lane & 16;
-    const double send = up ? acc[i] : acc[i + 4];
-    const double keep = up ? acc[i + 4] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(FULL, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool up = lane & 8;
-    const double send = up ? acc[i] : acc[i + 2];
-    const double keep = up ? acc[i + 2] : acc[i];
-    acc[i] = keep + __shfl_xor_sync(FULL, send, 8);
-  }
-  {
-    const bool up = lane & 4;
-    const double send = up ? acc[0] : acc[1];
-    const double keep = up ? acc[1] : acc[0];
-    acc[0] = keep + __shfl_xor_sync(FULL, send, 4);
-  }
-  acc[0] += __shfl_xor_sync(FULL, acc[0], 2);
-  acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
-  if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
-  __syncthreads();
+  __syncthreads();  // also keeps the CTA alive until the producer has drained its copies
   if (tid < cnt) {
     double s = 0.0;
     for (int qq = 0; qq < NT / 32; ++qq) s += red[qq][tid];
@@ -317,24 +355,23 @@ __global__ void __launch_bounds__(NT, kSweepMinCtas)
 // partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w.  FF: the sum over
 // k in float-float, one FP64 addition per point to store w.
 template <bool SUM, bool FF>
-__global__ void __launch_bounds__(NT, kSweepMinCtas)
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multiaxpy(double* __restrict__ w, const double* x0, const double* const* __restrict__ tab, int nx,
                 const double* __restrict__ coef, double sign, long long n, double* __restrict__ partial,
                 const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
-  if ((skip && *skip) || (only_if && !*only_if)) return;
+  if (sweep_skipped(skip, only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nx = tail.ia->j + 1;
     w = tail.ia->w;
   }
   extern __shared__ __align__(128) unsigned char smem[];
-  const Ring rg{reinterpret_cast<double*>(smem),
-                reinterpret_cast<uint64_t*>(smem + (size_t)kStages * kTile * sizeof(double))};
+  const Ring rg = ring_at(smem);
   __shared__ double red[2][NT / 32];
   __shared__ double c[kMaxVecs];
   __shared__ ff cf[kMaxVecs];
   __shared__ const double* sp[kMaxVecs + 1];
-  const int tid = threadIdx.x;
-  for (int k = tid; k <= nx; k += NT) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int k = tid; k <= nx; k += kSweepThreads) {
     if (k < nx) {
       c[k] = sign * coef[k];
       cf[k] = ff_of(sign * coef[k]);
@@ -344,74 +381,63 @@ __global__ void __launch_bounds__(NT, kSweepMinCtas)
   const long long ntile = (n + kTile - 1) / kTile;
   const int my_tiles = blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
   const int per = nx + 1, total = my_tiles * per;
-  __syncthreads();
-  if (tid == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(&rg.bar[st], 1);
-    fence_mbar_init();
-    for (int q = 0; q < kStages && q < total; ++q) ring_issue(rg, q, sp[q % per], n, q / per);
-  }
-  __syncthreads();
+  ring_init(rg);  // also makes c, cf, sp visible
   double s2 = 0.0, s1 = 0.0;
-  bool ok = true;
-  int q = 0;
-  for (int lt = 0; lt < my_tiles && ok; ++lt) {
-    const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
-    const int cntp = (int)min((long long)kTile, n - base);
-    double acc[kPts];
-    ff af[kPts];
+  if (wid == NT / 32) {  // producer warp
+    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err);
+  } else {
+    bool ok = true;
+    int q = 0;
+    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+      const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+      const int cntp = (int)min((long long)kTile, n - base);
+      double acc[kPts];
+      ff af[kPts];
 #pragma unroll
-    for (int p = 0; p < kPts; ++p) {
-      acc[p] = 0.0;
-      af[p] = {0.0f, 0.0f};
-    }
-    for (int k = 0; k <= nx; ++k) {
-      if (!(ok = ring_wait(rg, q))) break;
-      const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
-      if (k < nx) {
-        const double ck = c[k];
-        const ff cfk = cf[k];
-#pragma unroll
-        for (int p = 0; p < kPts; ++p) {
-          const int i = tid + p * NT;
-          if (i < cntp) {
-            if (FF)
-              af[p] = ff_acc(af[p], ff_prod(cfk, ff_split(tb[i])));
-            else
-              acc[p] = fma(ck, tb[i], acc[p]);
-          }
-        }
-      } else {  // the tile of w: add and store
-#pragma unroll
-        for (int p = 0; p < kPts; ++p) {
-          const int i = tid + p * NT;
-          if (i < cntp) {
-            const double wn = FF ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
-            w[base + i] = wn;
-            s2 = fma(wn, wn, s2);
-            if (SUM) s1 += wn;
-          }
-        }
+      for (int p = 0; p < kPts; ++p) {
+        acc[p] = 0.0;
+        af[p] = {0.0f, 0.0f};
       }
-      __syncthreads();  // the buffer is free
-      if (tid == 0 && q + kStages < total) ring_issue(rg, q + kStages, sp[(q + kStages) % per], n, (q + kStages) / per);
-      ++q;
+      for (int k = 0; k <= nx; ++k) {
+        if (!(ok = ring_wait(rg, q))) break;
+        const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
+        if (k < nx) {
+          const double ck = c[k];
+          const ff cfk = cf[k];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) {
+            const int i = tid + p * NT;
+            if (i < cntp) {
+              if (FF)
+                af[p] = ff_acc(af[p], ff_prod(cfk, ff_split(tb[i])));
+              else
+                acc[p] = fma(ck, tb[i], acc[p]);
+            }
+          }
+        } else {  // the tile of w: add and store
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) {
+            const int i = tid + p * NT;
+            if (i < cntp) {
+              const double wn = FF ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
+              w[base + i] = wn;
+              s2 = fma(wn, wn, s2);
+              if (SUM) s1 += wn;
+            }
+          }
+        }
+        ring_release(rg, q++);
+      }
+    }
+    if (!ok && lane == 0 && tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
+    s2 = warp_sum(s2);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
+      red[0][wid] = s2;
+      red[1][wid] = s1;
     }
   }
-  if (!ok) {  // a copy never arrived: record, drain what is in flight, and still take the ticket
-    if (tid == 0) {
-      if (tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
-      for (int u = q; u < q + kStages && u < total; ++u)
-        mbar_wait_bounded(&rg.bar[u % kStages], (uint32_t)((u / kStages) & 1));
-    }
-  }
-  const int lane = tid & 31, wid = tid >> 5;
-  s2 = warp_sum(s2);
-  s1 = warp_sum(s1);
-  if (lane == 0) {
-    red[0][wid] = s2;
-    red[1][wid] = s1;
-  }
-  __syncthreads();
+  __syncthreads();  // also keeps the CTA alive until the producer has drained its copies
   if (tid < (SUM ? 2 : 1)) {
     double s = 0.0;
     for (int qq = 0; qq < NT / 32; ++qq) s += red[tid][qq];
@@ -500,13 +526,13 @@ void launch_multidot(const double* v0, const double* const* tab, int nv, const d
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
   const dim3 grid(bx, gy);
-  const size_t smem = (size_t)kStages * kTile * sizeof(double) + kStages * 8;
+  const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
   if (ff) {
     cudaFuncSetAttribute(k_multidot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_multidot<true><<<grid, NT, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+    k_multidot<true><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
   } else {
     cudaFuncSetAttribute(k_multidot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_multidot<false><<<grid, NT, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
+    k_multidot<false><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
   }
   count_launches(1);
 }
@@ -516,13 +542,13 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
                       cudaStream_t st, bool ff) {
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)kRedCtas));
-  const size_t smem = (size_t)kStages * kTile * sizeof(double) + kStages * 8;
+  const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
   // the sum of w is read only by the kSums tail (and by callers of partials-only sweeps)
   const bool sum = !(tail.counter && tail.kind != Tail::kSums);
 #define PFC_AXPY(S, F)                                                                                  \
   do {                                                                                                  \
     cudaFuncSetAttribute(k_multiaxpy<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_multiaxpy<S, F><<<bx, NT, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail); \
+    k_multiaxpy<S, F><<<bx, kSweepThreads, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail); \
   } while (0)
   if (sum && ff)
     PFC_AXPY(true, true);
