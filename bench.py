@@ -33,9 +33,9 @@ METRIC = "PFC time steps/s (1024^2 2D crystal growth, adaptive dt)"
 
 
 # DRAM bytes (read + write) of one 2D Schwarz apply launch on this workload from one ncu capture
-# (profiles/ras_apply2d_hex1024_bf16.md), keyed by (factor precision, apply launch shape); a shape
-# or kernel not captured since its last change reports null.
-APPLY_TRAFFIC = {(2, 4): 456.238592e6 + 3.252992e6}
+# (profiles/ras_apply2d_hex1024_bf16.md, profiles/ras_apply2d_chunked_hex1024_bf16.md), keyed by
+# (factor precision, apply kernel); a kernel not captured since its last change reports null.
+APPLY_TRAFFIC = {(2, 4): 456.238592e6 + 3.252992e6, (2, 5): 540.646400e6 + 3.399424e6}
 
 
 def measured_peaks():
