@@ -280,6 +280,209 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
   }
 }
 
+// ---- Register-resident band LU (compute type float, kl <= 63).
+//
+// The same elimination as k_factor2d (same pivots, same multipliers, same rank-1
+// updates in the same order of operations, so the same factors), arranged for the
+// register file: thread t of the 128 owns ring column slot t and keeps that
+// column's entries for the 64 row slots of the window in registers.  Per step the
+// owner of column k publishes it to shared memory, warp 0 picks the pivot and
+// forms the multipliers, and every column applies its rank-1 update in registers;
+// the pivot row's entry a[slot] and the entering row's entry are reached through
+// a warp-uniform switch.  New rows are generated from per-column tables of the
+// q-dependent entries (evaluated in double as jac_entry does, then rounded).
+constexpr int kRegRows = 64;   // row slots (window of kl + 1 <= 64 rows)
+constexpr int kRegRing = 128;  // column slots (2 kl + 2 <= 128)
+
+#define PFC_CASES8(b) \
+  PFC_CASE(b + 0) PFC_CASE(b + 1) PFC_CASE(b + 2) PFC_CASE(b + 3) PFC_CASE(b + 4) PFC_CASE(b + 5) PFC_CASE(b + 6) PFC_CASE(b + 7)
+#define PFC_CASES64 \
+  PFC_CASES8(0) PFC_CASES8(8) PFC_CASES8(16) PFC_CASES8(24) PFC_CASES8(32) PFC_CASES8(40) PFC_CASES8(48) PFC_CASES8(56)
+__device__ __forceinline__ float reg_get(const float (&a)[kRegRows], int s) {
+  switch (s) {
+#define PFC_CASE(i) \
+  case i: return a[i];
+    PFC_CASES64
+#undef PFC_CASE
+  }
+  return 0.0f;
+}
+__device__ __forceinline__ void reg_set(float (&a)[kRegRows], int s, float v) {
+  switch (s) {
+#define PFC_CASE(i) \
+  case i: a[i] = v; break;
+    PFC_CASES64
+#undef PFC_CASE
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const BlockDesc* __restrict__ blocks,
+                                                         const double* __restrict__ q, double idt,
+                                                         const double* __restrict__ lin, FactorStore fs,
+                                                         int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float colbuf[kRegRows];     // column k by row slot
+  __shared__ __align__(16) float lslot[kRegRows];  // multipliers by row slot (0 off the window)
+  __shared__ int slot[kRegRows];         // window position & 63 -> row slot
+  __shared__ int posof[kRegRows];        // row slot -> window position (-1: free)
+  __shared__ float linf[49];             // the stencil table, rounded
+  __shared__ float s_dinv;
+  __shared__ int s_sk;
+  constexpr int PM = kRegRows - 1;
+  const BlockDesc B = blocks[blockIdx.x];
+  const int n = B.bx * B.by, bx = B.bx;
+  const int kl = min(3 * bx, n - 1);
+  const int ku2 = min(2 * kl, n - 1);
+  const int W = kl + 1;
+  const int lrow = fs.lrow, ucol = fs.ucol;
+  double* qb = reinterpret_cast<double*>(smem);              // q on the block
+  double* lin_s = qb + fs.n_max;                             // 7 x 7 stencil table
+  float* tabq = reinterpret_cast<float*>(lin_s + 49);        // per column: centre, -x, +x, -y, +y entries
+  TS* L = (TS*)fs.L + blockIdx.x * fs.strideL;
+  TS* U = (TS*)fs.U + blockIdx.x * fs.strideU;
+  uint8_t* piv = fs.piv + blockIdx.x * fs.strideP;
+  const int t = threadIdx.x, lane = t & 31;
+  const double ih2 = g.ih2;
+
+  for (int i = t; i < n; i += kRegRing)
+    qb[i] = q[wrap(B.x0 + i % bx, g.nx) + (long long)g.nx * wrap(B.y0 + i / bx, g.ny)];
+  for (int i = t; i < 49; i += kRegRing) {
+    lin_s[i] = lin[i];
+    linf[i] = (float)lin[i];
+  }
+  if (t < kRegRows) {
+    slot[t] = t;
+    posof[t] = t < W ? t : -1;
+  }
+  __syncthreads();
+  for (int i = t; i < n; i += kRegRing) {  // the entries jac_entry gives for ad <= 1, same expressions
+    const int dirs[5] = {24, 23, 25, 17, 31};  // (dx, dy) = (0,0), (-1,0), (1,0), (0,-1), (0,1)
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      double e = lin_s[dirs[d]];
+      e -= (d == 0 ? -4.0 * ih2 : ih2) * qb[i];
+      if (d == 0) e += idt;
+      tabq[5 * i + d] = (float)e;
+    }
+  }
+  float a[kRegRows];
+#pragma unroll
+  for (int r = 0; r < kRegRows; ++r)
+    a[r] = (r < W && r < n && t < n) ? (float)jac_entry(bx, ih2, qb, idt, lin_s, r, t) : 0.0f;
+  // block coordinates of this thread's column (column t, then t + 128, ...) and of the entering row
+  int ac = t % bx, bc = t / bx;
+  const int da = kRegRing % bx, db = kRegRing / bx;
+  int ar = (kl + 1) % bx, br = (kl + 1) / bx;
+  __syncthreads();
+
+  for (int k = 0; k < n; ++k) {
+    const int kw = k & (kRegRing - 1);
+    const int last = min(k + kl, n - 1);
+    if (t == kw)
+#pragma unroll
+      for (int r = 0; r < kRegRows; ++r) colbuf[r] = a[r];
+    __syncthreads();
+    if (t < 32) {  // partial pivoting: largest |a_ik| over the window, first on ties
+      float best = -1.0f;
+      int bp = k;
+      for (int pos = k + lane; pos <= last; pos += 32) {
+        const float v = fabsf(colbuf[slot[pos & PM]]);
+        if (v > best) {
+          best = v;
+          bp = pos;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ob > best || (ob == best && op < bp)) {
+          best = ob;
+          bp = op;
+        }
+      }
+      const int sk0 = slot[k & PM], sp = slot[bp & PM];
+      float d = colbuf[sp];
+      if (d == 0.0f) d = 1.0f;
+      const float dinv = 1.0f / d;
+      __syncwarp();
+      if (lane == 0) {
+        slot[k & PM] = sp;
+        slot[bp & PM] = sk0;
+        posof[sk0] = bp;
+        posof[sp] = k;
+        piv[k] = (uint8_t)(bp - k);
+        if (colbuf[sp] == 0.0f) atomicExch(status, PFC_ESINGULAR);
+        s_dinv = dinv;
+        s_sk = sp;
+      }
+      __syncwarp();
+      for (int r = lane; r < kRegRows; r += 32) {  // multipliers by slot: rows k+1 .. last
+        const int pos = posof[r];
+        lslot[r] = (pos > k && pos <= last) ? colbuf[r] * dinv : 0.0f;
+      }
+      __syncwarp();
+      for (int i = lane; i < lrow; i += 32)
+        L[(size_t)k * lrow + i] = to_store<TS>((double)(i < kl && k + 1 + i <= last ? lslot[slot[(k + 1 + i) & PM]] : 0.0f));
+    }
+    __syncthreads();
+    const int sk = s_sk;
+    const float u = reg_get(a, sk);  // the pivot row's entry in this column
+    const int j = (t - k) & (kRegRing - 1), c = k + j;
+    if (j <= ku2 && c < n) U[(size_t)c * ucol + j] = to_store<TS>((double)(j == 0 ? s_dinv : u));
+    if (j == 0)  // U column k's entries above the band stay zero for the bulk copies
+      for (int jj = ku2 + 1; jj < ucol; ++jj) U[(size_t)k * ucol + jj] = to_store<TS>(0.0);
+    if (j >= 1 && j <= ku2 && c < n) {  // rank-1 update of this column
+#pragma unroll
+      for (int r = 0; r < kRegRows; r += 4) {
+        const float4 l4 = *reinterpret_cast<const float4*>(&lslot[r]);
+        a[r] -= l4.x * u;
+        a[r + 1] -= l4.y * u;
+        a[r + 2] -= l4.z * u;
+        a[r + 3] -= l4.w * u;
+      }
+    }
+    if (j == ku2 + 1)  // the column entering the band starts at zero
+#pragma unroll
+      for (int r = 0; r < kRegRows; ++r) a[r] = 0.0f;
+    if (j == 0) {  // this slot now holds column k + 128
+      ac += da;
+      bc += db;
+      if (ac >= bx) {
+        ac -= bx;
+        ++bc;
+      }
+    }
+    const int rnew = k + 1 + kl;
+    if (rnew < n) {  // the next row of A_k enters the pivot row's slot
+      const int colw = k + 1 + ((t - k - 1) & (kRegRing - 1));
+      const int dx = ac - ar, dy = bc - br, ad = abs(dx) + abs(dy);
+      float v = 0.0f;
+      if (colw < n && ad <= 3) {
+        if (ad == 0)
+          v = tabq[5 * colw];
+        else if (ad == 1)
+          v = tabq[5 * colw + (dx == -1 ? 1 : dx == 1 ? 2 : dy == -1 ? 3 : 4)];
+        else
+          v = linf[(dy + 3) * 7 + dx + 3];
+      }
+      reg_set(a, sk, v);
+      if (t == 0) {
+        slot[rnew & PM] = sk;
+        posof[sk] = rnew;
+      }
+      if (++ar == bx) {
+        ar = 0;
+        ++br;
+      }
+    } else if (t == 0) {
+      posof[sk] = -1;
+    }
+  }
+}
+#undef PFC_CASES64
+#undef PFC_CASES8
+
 // Shared-memory carve-out of one warp of the apply kernel.
 struct ApplySmem {
   size_t stage, buf, piv, total;
@@ -834,6 +1037,13 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
+  if (sizeof(TC) == 4 && fs.kl_max + 1 <= kRegRows && 2 * fs.kl_max + 2 <= kRegRing) {
+    const size_t smem = (size_t)(fs.n_max + 49) * sizeof(double) + (size_t)fs.n_max * 5 * sizeof(float);
+    cudaFuncSetAttribute(k_factor2d_reg<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_factor2d_reg<TS><<<nblocks, kRegRing, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    count_launches(1);
+    return;
+  }
   const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max);
   if (2 * fs.kl_max + 2 <= 128) {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
