@@ -358,6 +358,46 @@ def run_bcc256(steps: int, warmup: int, prec: int):
             "dt_last": infos[-1]["dt"], "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
 
 
+def precond_sweep(args):
+    """The preconditioner and overlap sweep of Sec. 5 (Table 2's comparison) on the 1024^2 workload:
+    AS (Eq. invM), left-RAS (Eq. ras) and right-RAS (Eq. ash) with 0-3 overlap cells per side, BF16
+    factors, phi^n guess; steps `warmup`+1 .. `warmup`+`steps` timed (no bench line)."""
+    import torch
+
+    from paper_1703_01202_gb300 import build, inputs, pfc
+
+    build.build()
+    w = inputs.workload(WORKLOAD)
+    rows = []
+    for kind, name in ((pfc.PFC_AS, "as"), (pfc.PFC_LEFT_RAS, "left-ras"), (pfc.PFC_RIGHT_RAS, "right-ras")):
+        for ov in (0, 1, 2, 3):
+            params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=ov, factor_prec=pfc.PFC_BF16,
+                                        ras_kind=kind, dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"],
+                                        dt_halvings=4)
+            s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
+            s.set_field(w["phi"])
+            row = {"kind": name, "overlap_per_side": ov}
+            try:
+                s.run(args.warmup)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                infos = s.run(args.steps)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                row.update({"ms_per_step": 1e3 * el / args.steps,
+                            "newton_per_step": sum(i["newton_its"] for i in infos) / args.steps,
+                            "gmres_per_step": sum(i["gmres_its"] for i in infos) / args.steps,
+                            "dt_cuts": sum(i["dt_cuts"] for i in infos), "dt_last": infos[-1]["dt"],
+                            "apply_variant": s.tuning()["apply_variant"]})
+            except pfc.PfcError as e:
+                row["failed"] = str(e)
+            s.close()
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"precond_sweep": rows, "workload": WORKLOAD, "factor_prec": "bf16", "guess": "phi^n",
+                      "steps": args.steps, "warmup": args.warmup}))
+
+
 def kernel_loop(args):
     """Runs one kernel family `steps` times on the workload's initial field
     (each pfc_precond_apply factors and applies once), for ncu captures."""
@@ -403,11 +443,16 @@ def main():
                     help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
     ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
                     help="2D Schwarz apply kernel (-1: autotuned at the first factorisation)")
+    ap.add_argument("--precond-sweep", action="store_true",
+                    help="AS / left-RAS / right-RAS x overlap 0-3 on the workload (no bench line)")
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
                     help="profiling aid: run one kernel family repeatedly on the workload (no bench line)")
     args = ap.parse_args()
     if args.kernel_loop:
         kernel_loop(args)
+        return
+    if args.precond_sweep:
+        precond_sweep(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -76,7 +76,11 @@ typedef struct {
      cores one extra cell); overlap = cells added per side (Sec. 4). */
   int sub[3];
   int overlap;
-  int ras_kind;      /* PFC_LEFT_RAS (only kind built on the GPU)            */
+  int ras_kind;      /* Schwarz form (Sec. 4): PFC_LEFT_RAS (default, Eq. ras:
+                        solve on the overlapped block, keep the core), PFC_AS
+                        (Eq. invM: keep the whole block, overlaps summed) or
+                        PFC_RIGHT_RAS (Eq. ash: core of r in, whole block out).
+                        AS and right-RAS: 2D grids, apply_variant -1 or 5.   */
   int factor_prec;   /* PFC_F64 (plain path), PFC_F32 or PFC_BF16 storage    */
   int guess;         /* PFC_GUESS_*                                          */
   int mass_projection; /* 1: Newton update projected to zero mean            */

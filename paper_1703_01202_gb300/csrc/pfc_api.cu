@@ -45,6 +45,7 @@ struct pfc_state {
   BlockDesc* blocks_dev;
   int nblocks;
   pfc::FactorStore fs;
+  pfc::Decomp2 dc;  // 2D decomposition (AS / right-RAS overlap sums)
   double* lin_dev;
   // 3D: scratch fields of the three-pass stencils and the ILU(0) Schwarz data
   double *T1, *T2;
@@ -139,7 +140,10 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (g->dim == 2 && g->n[2] != 1) return PFC_EINVAL;
   if (p->gmres_restart < 1 || p->gmres_restart > pfc::kMaxRestart) return PFC_EINVAL;
   if (p->newton_max_it < 0 || p->gmres_max_it < 1 || p->overlap < 0) return PFC_EINVAL;
-  if (p->ras_kind != PFC_LEFT_RAS) return PFC_EINVAL;
+  // left-RAS everywhere; AS and right-RAS (full-block extension) on 2D grids, with the chunked apply
+  if (p->ras_kind != PFC_LEFT_RAS && p->ras_kind != PFC_AS && p->ras_kind != PFC_RIGHT_RAS) return PFC_EINVAL;
+  if (p->ras_kind != PFC_LEFT_RAS && (g->dim != 2 || (p->apply_variant != -1 && p->apply_variant != 5)))
+    return PFC_EINVAL;
   if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
   if (p->apply_variant < -1 || p->apply_variant >= pfc::kApplyVariants) return PFC_EINVAL;
   if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
@@ -293,7 +297,7 @@ size_t basis_stride(long long N) { return ((size_t)N + 31) / 32 * 32 + 17 * 32; 
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs, order, X;
+      tabs, feat, iargs, order, X, Yb;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -370,6 +374,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->U = L.take(pl->sU * es * pl->nblocks);
   pl->piv = L.take(pl->sP * pl->nblocks);
   pl->X = L.take((size_t)pl->xnc * pl->nblocks * (pl->xfw + pl->xbw));
+  pl->Yb = L.take(!d3 && p->ras_kind != PFC_LEFT_RAS ? sizeof(double) * (size_t)pl->n_max * pl->nblocks : 0);
   pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
   pl->lin = L.take(sizeof(double) * 343);
   pl->ctl = L.take(sizeof(GmresCtl));
@@ -475,7 +480,7 @@ void precond(pfc_state* s, const double* r, const double* rscale, double* z, con
              const pfc::IterArgs* ia = nullptr) {
   if (s->dim == 2)
     pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, rscale, z, skip, s->status_dev + 1, s->st,
-                            ia);
+                            ia, &s->dc);
   else
     pfc::launch_ras_apply3d(s->g, s->blocks_dev, s->nblocks, s->r3, r, rscale, z, skip, s->status_dev + 1, s->st);
 }
@@ -590,7 +595,7 @@ bool build_cycle_graph(pfc_state* s) {
   }
   // kernels of one body iteration: setup, apply, JVP, a multi-dot and a multi-axpy per pass, loop test
   // (counted here rather than from the process-wide counter, which other threads also move)
-  const int body = 4 + 2 * passes;
+  const int body = 4 + 2 * passes + (s->fs.ras_kind != PFC_LEFT_RAS ? 1 : 0);
   if (ok) ok = cudaStreamBeginCaptureToGraph(s->st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
@@ -949,6 +954,17 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.lrow = pl.lrow;
   s->fs.ucol = pl.ucol;
   s->fs.X = (unsigned char*)at(pl.X);
+  s->fs.ras_kind = p->ras_kind;
+  s->fs.Yb = (double*)at(pl.Yb);
+  if (g->dim == 2) {
+    s->dc.px = p->sub[0];
+    s->dc.py = p->sub[1];
+    s->dc.ov = p->overlap;
+    s->dc.base_x = (int)(g->n[0] / p->sub[0]);
+    s->dc.rem_x = (int)(g->n[0] % p->sub[0]);
+    s->dc.base_y = (int)(g->n[1] / p->sub[1]);
+    s->dc.rem_y = (int)(g->n[1] % p->sub[1]);
+  }
   s->fs.xfw = pl.xfw;
   s->fs.xbw = pl.xbw;
   s->fs.xnc = pl.xnc;
@@ -960,6 +976,10 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.n_max = pl.n_max;
   s->fs.variant = p->apply_variant >= 0 ? p->apply_variant : 0;
   s->tuned = false;
+  if (p->ras_kind != PFC_LEFT_RAS) {  // AS / right-RAS: the chunked apply only
+    s->fs.variant = pfc::kChunkedVariant;
+    s->tuned = true;
+  }
   s->ref_norm = -1.0;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     pfc_destroy(s);

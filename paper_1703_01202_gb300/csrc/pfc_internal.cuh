@@ -114,6 +114,17 @@ struct FactorStore {
   int nblk;         // blocks
   int xstage;       // bytes of the largest record (one TMA stage)
   int x_valid;      // X holds the chunks of the current factors
+  // Schwarz form (Sec. 4): PFC_LEFT_RAS writes block cores only; PFC_AS (Eq. invM) and
+  // PFC_RIGHT_RAS (Eq. ash) extend over the whole block, so the chunked apply writes every
+  // block's solution to Yb (n_max doubles per block) and k_schwarz_sum adds the overlapping
+  // parts point by point; PFC_RIGHT_RAS also restricts r to the core (R_k^0).
+  int ras_kind;
+  double* Yb;
+};
+// Axis splits of the 2D decomposition (the first n mod p cores one cell larger).
+struct Decomp2 {
+  int px, py, ov;
+  int base_x, rem_x, base_y, rem_y;
 };
 constexpr int kApplyVariants = 6;
 constexpr int kChunkedVariant = 5;
@@ -159,7 +170,7 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
-                        const IterArgs* ia = nullptr);
+                        const IterArgs* ia = nullptr, const Decomp2* dc = nullptr);
 size_t factor_smem_bytes(int prec, int kl, int n_max);
 // Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec
 // (xstage: bytes of the largest chunk record, n_max: rows of the largest block).

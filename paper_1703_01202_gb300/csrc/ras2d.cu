@@ -895,8 +895,10 @@ __global__ void __launch_bounds__(32 * WPC)
   const int da = 32 % B.bx, dc = 32 / B.bx, a0 = lane % B.bx, c0 = lane / B.bx;
   {
     int a = a0, c = c0;
-    for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta; zeros past n
-      y[t] = t < n ? (TC)r[wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny)] : (TC)0;
+    const bool core_only = fs.ras_kind == PFC_RIGHT_RAS;
+    for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta (R_k^0 for right-RAS); zeros past n
+      const bool in = t < n && (!core_only || (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy));
+      y[t] = in ? (TC)r[wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny)] : (TC)0;
       a += da;
       c += dc;
       if (a >= B.bx) {
@@ -996,6 +998,10 @@ __global__ void __launch_bounds__(32 * WPC)
     if (lane == 0 && t + STAGES < total) issue(t + STAGES);
   }
   const double sc = rscale ? *rscale : 1.0;
+  if (fs.ras_kind != PFC_LEFT_RAS) {  // extension over the whole block: to the block's scratch row
+    for (int t = lane; t < n; t += 32) fs.Yb[(size_t)b * fs.n_max + t] = sc * (double)y[t];
+    return;
+  }
   int a = a0, c = c0;
   for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
     if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
@@ -1006,6 +1012,42 @@ __global__ void __launch_bounds__(32 * WPC)
       a -= B.bx;
       ++c;
     }
+  }
+}
+
+// Core index along an axis of n cells in p cores (the first rem = n mod p hold base + 1).
+__device__ __forceinline__ int core_of(int x, int base, int rem) {
+  const int big = rem * (base + 1);
+  return x < big ? x / (base + 1) : rem + (x - big) / base;
+}
+__device__ __forceinline__ int core_start(int i, int base, int rem) { return i * base + min(i, rem); }
+
+// z(p) = sum over the blocks whose extended region holds p of their solution at p (Eq. invM /
+// Eq. ash extension (R_k^delta)^T), blocks visited in a fixed order: deterministic sums.
+__global__ void __launch_bounds__(256) k_schwarz_sum(Geo g, Decomp2 dc, const BlockDesc* __restrict__ blocks,
+                                                     FactorStore fs, double* __restrict__ z,
+                                                     const int* __restrict__ skip, const IterArgs* __restrict__ ia) {
+  if (skip && *skip) return;
+  if (ia) z = ia->z;
+  const long long n = (long long)g.nx * g.ny;
+  // cores within reach of a point (each distinct block once, in a fixed order)
+  const int kx = (dc.ov + dc.base_x - 1) / dc.base_x, ky = (dc.ov + dc.base_y - 1) / dc.base_y;
+  const int mx = min(2 * kx + 1, dc.px), my = min(2 * ky + 1, dc.py);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int ix = core_of(x, dc.base_x, dc.rem_x), iy = core_of(y, dc.base_y, dc.rem_y);
+    double s = 0.0;
+    for (int tj = 0; tj < my; ++tj) {
+      const int by = my == dc.py ? tj : ((iy - ky + tj) % dc.py + dc.py) % dc.py;
+      for (int ti = 0; ti < mx; ++ti) {
+        const int bxi = mx == dc.px ? ti : ((ix - kx + ti) % dc.px + dc.px) % dc.px;
+        const int b = by * dc.px + bxi;
+        const BlockDesc B = blocks[b];
+        const int a = ((x - B.x0) % g.nx + g.nx) % g.nx, c = ((y - B.y0) % g.ny + g.ny) % g.ny;
+        if (a < B.bx && c < B.by) s += fs.Yb[(size_t)b * fs.n_max + a + B.bx * c];
+      }
+    }
+    z[i] = s;
   }
 }
 
@@ -1135,7 +1177,7 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
-                        const IterArgs* ia) {
+                        const IterArgs* ia, const Decomp2* dc) {
   // Launch shapes (chunk length CH = steps per bulk copy, WPC = warps per CTA):
   // variant 0: stages of about 3.5 KB for every storage type, 4 warps per CTA;
   // 1: half the chunk (twice the resident warps per SM), 2: half the chunk and
@@ -1143,6 +1185,14 @@ void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, cons
   // 4: two subdomains per warp, 16 lanes each (5 + 9 window registers per lane);
   // 5: the chunked solves (one warp per block, records of kChunk steps).
   if (fs.variant == kChunkedVariant) {
+    if (fs.ras_kind != PFC_LEFT_RAS && dc) {  // solutions to the block scratch, then the overlap sums
+      launch_ras_apply2d(g, blocks, nblocks, fs, r, rscale, z, skip, err, st, ia, nullptr);
+      const long long n = (long long)g.nx * g.ny;
+      const int grid = (int)((n + 255) / 256 < 4 * 152 ? (n + 255) / 256 : 4 * 152);
+      k_schwarz_sum<<<grid, 256, 0, st>>>(g, *dc, blocks, fs, z, skip, ia);
+      count_launches(1);
+      return;
+    }
     if (fs.prec == PFC_F64)
       chunked_dispatch<double, double, kChunkWpcF64, kChunkStF64>(g, blocks, nblocks, fs, r, rscale, z, skip, err,
                                                                    st, ia);

@@ -64,3 +64,24 @@ def test_workspace_size_and_validation(libpfc):
     with pytest.raises(pfc.PfcError):
         pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4), gmres_restart=0))
     assert pfc.status_str(pfc.PFC_ESINGULAR).startswith("zero pivot")
+
+
+def test_schwarz_kind_validation(libpfc):
+    """AS and right-RAS take the chunked apply on 2D grids (plus one scratch row of n_max
+    doubles per block for the overlap sums); 3D grids and the per-step launch shapes refuse them."""
+    from paper_1703_01202_gb300 import pfc
+
+    left = pfc.workspace_size((1024, 1024), pfc.default_params(sub=(64, 64), overlap=1))
+    for kind in (pfc.PFC_AS, pfc.PFC_RIGHT_RAS):
+        size = pfc.workspace_size((1024, 1024), pfc.default_params(sub=(64, 64), overlap=1, ras_kind=kind))
+        assert size >= left + 4096 * 324 * 8
+        assert pfc.workspace_size((1024, 1024), pfc.default_params(sub=(64, 64), ras_kind=kind, apply_variant=5)) == size
+        for bad in (dict(apply_variant=0), dict(apply_variant=4)):
+            with pytest.raises(pfc.PfcError) as e:
+                pfc.workspace_size((1024, 1024), pfc.default_params(sub=(64, 64), ras_kind=kind, **bad))
+            assert e.value.status == pfc.PFC_EINVAL
+        with pytest.raises(pfc.PfcError) as e:
+            pfc.workspace_size((64, 64, 64), pfc.default_params(sub=(4, 4, 4), ras_kind=kind))
+        assert e.value.status == pfc.PFC_EINVAL
+    with pytest.raises(pfc.PfcError):
+        pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4), ras_kind=7))

@@ -207,6 +207,57 @@ def test_chunked_apply_steps_match_oracle(pfc, prec, tol):
     assert [r["dt"] for r in recs] == pytest.approx([o.dt for o in orecs], rel=1e-9)
 
 
+KINDS = {"as": 0, "right-ras": 2, "left-ras": 1}  # oracle name -> PFC_AS / PFC_RIGHT_RAS / PFC_LEFT_RAS
+
+
+@pytest.mark.parametrize("kind", ["as", "right-ras"])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4), (2, 0.25)])
+@pytest.mark.parametrize("shape,parts,dt", [((50, 37), (3, 2), 10.0), ((96, 80), (5, 6), 1.0)])
+def test_schwarz_kinds_match_oracle(pfc, shape, parts, dt, prec, tol, kind):
+    """Additive Schwarz (Eq. invM: solve on the overlapped block, add every block's whole
+    solution) and right-RAS (Eq. ash: the core of r in, the whole block out) against the
+    oracle's dense-LU forms, on ragged decompositions (overlap sums of 2 and 4 blocks)."""
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, parts, prec=prec, overlap=1, ras_kind=KINDS[kind])
+    z = s.precond_apply(Phi, phin, dt, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, dt, H, GAMMA)
+    ref = O.Schwarz(J, O.decompose(shape, parts, 1), kind, "lu").apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("kind", ["left-ras", "as", "right-ras"])
+@pytest.mark.parametrize("overlap", [0, 2, 3])
+def test_overlaps_match_oracle(pfc, kind, overlap):
+    """Overlaps of 0, 2 and 3 cells per side (blocks of 16, 20 and 22 cells: the last runs
+    kl = 66, past the narrow kernels) for the three Schwarz forms, FP64 factors."""
+    shape, parts = (96, 80), (5, 6)
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, parts, prec=0, overlap=overlap, ras_kind=KINDS[kind])
+    z = s.precond_apply(Phi, phin, 10.0, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, 10.0, H, GAMMA)
+    ref = O.Schwarz(J, O.decompose(shape, parts, overlap), kind, "lu").apply(r)
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= 1e-11
+
+
+@pytest.mark.parametrize("kind", ["as", "right-ras"])
+def test_schwarz_kinds_steps_match_oracle(pfc, kind):
+    """Two adaptive steps of the 48^2 noise field with AS and right-RAS, FP64 factors:
+    the Newton solutions against the oracle's with the same preconditioner."""
+    shape = (48, 48)
+    phi = inputs.noise_field(shape, 0.07, 0.07, 1050)
+    prm = dict(dt_min=1e-2, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, shape, (3, 3), prec=0, overlap=1, ras_kind=KINDS[kind], **prm)
+    s.set_field(phi)
+    s.run(2)
+    ref, _ = O.run(phi, H, GAMMA, O.Params(parts=(3, 3), overlap=1, ras_kind=kind, **prm), 2)
+    assert np.abs(s.get_field() - ref).max() <= 1e-8
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
 @pytest.mark.parametrize("shape", [(27, 21), (45, 37)])
 def test_odd_point_count_steps_match_oracle(pfc, shape, prec, tol):
