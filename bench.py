@@ -369,31 +369,33 @@ def precond_sweep(args):
     build.build()
     w = inputs.workload(WORKLOAD)
     rows = []
-    for kind, name in ((pfc.PFC_AS, "as"), (pfc.PFC_LEFT_RAS, "left-ras"), (pfc.PFC_RIGHT_RAS, "right-ras")):
-        for ov in (0, 1, 2, 3):
-            params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=ov, factor_prec=pfc.PFC_BF16,
-                                        ras_kind=kind, dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"],
-                                        dt_halvings=4)
-            s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
-            s.set_field(w["phi"])
-            row = {"kind": name, "overlap_per_side": ov}
-            try:
-                s.run(args.warmup)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                infos = s.run(args.steps)
-                torch.cuda.synchronize()
-                el = time.perf_counter() - t0
-                row.update({"ms_per_step": 1e3 * el / args.steps,
-                            "newton_per_step": sum(i["newton_its"] for i in infos) / args.steps,
-                            "gmres_per_step": sum(i["gmres_its"] for i in infos) / args.steps,
-                            "dt_cuts": sum(i["dt_cuts"] for i in infos), "dt_last": infos[-1]["dt"],
-                            "apply_variant": s.tuning()["apply_variant"]})
-            except pfc.PfcError as e:
-                row["failed"] = str(e)
-            s.close()
-            rows.append(row)
-            print(json.dumps(row), file=sys.stderr, flush=True)
+    cases = [(kind, name, ov, 0) for kind, name in ((pfc.PFC_AS, "as"), (pfc.PFC_LEFT_RAS, "left-ras"),
+                                                   (pfc.PFC_RIGHT_RAS, "right-ras")) for ov in (0, 1, 2, 3)]
+    cases += [(pfc.PFC_LEFT_RAS, "left-ras", 1, r) for r in (1, 3, 8)]  # factors kept across steps
+    for kind, name, ov, reuse in cases:
+        params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=ov, factor_prec=pfc.PFC_BF16,
+                                    ras_kind=kind, dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"],
+                                    dt_halvings=4, reuse_factor=reuse)
+        s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
+        s.set_field(w["phi"])
+        row = {"kind": name, "overlap_per_side": ov, "reuse_factor": reuse}
+        try:
+            s.run(args.warmup)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            infos = s.run(args.steps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            row.update({"ms_per_step": 1e3 * el / args.steps,
+                        "newton_per_step": sum(i["newton_its"] for i in infos) / args.steps,
+                        "gmres_per_step": sum(i["gmres_its"] for i in infos) / args.steps,
+                        "dt_cuts": sum(i["dt_cuts"] for i in infos), "dt_last": infos[-1]["dt"],
+                        "apply_variant": s.tuning()["apply_variant"]})
+        except pfc.PfcError as e:
+            row["failed"] = str(e)
+        s.close()
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
     print(json.dumps({"precond_sweep": rows, "workload": WORKLOAD, "factor_prec": "bf16", "guess": "phi^n",
                       "steps": args.steps, "warmup": args.warmup}))
 

@@ -115,6 +115,12 @@ typedef struct {
      than the legacy default stream and while pfc_profile is off; otherwise, or
      if the graph cannot be built, the host-driven loop runs. */
   int use_graph;
+  /* Factor reuse across time steps (extends the paper's reuse within a step,
+     Sec. 5.2): 0 (default) factors the subdomain matrices at the first Newton
+     iteration of every step; k > 0 keeps them for up to k further steps while
+     dt stays within 1e-3 (relative) of the dt they were made with.  Changes
+     the preconditioner only, not the converged phi^{n+1}. */
+  int reuse_factor;
 } pfc_params;
 
 typedef struct {

@@ -46,6 +46,10 @@ struct pfc_state {
   int nblocks;
   pfc::FactorStore fs;
   pfc::Decomp2 dc;  // 2D decomposition (AS / right-RAS overlap sums)
+  // factors kept across steps (reuse_factor): valid, the dt they were made with, steps reused since
+  bool factors_ok = false;
+  double factor_dt = 0.0;
+  int factor_age = 0;
   double* lin_dev;
   // 3D: scratch fields of the three-pass stencils and the ILU(0) Schwarz data
   double *T1, *T2;
@@ -149,6 +153,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
   if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
+  if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -762,11 +767,19 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
   double rnorm = r0;
   info->res_norm0 = r0;
   int m = 0, gm_total = 0, cuts_total = 0;
-  bool factored = false;
+  // factors of J(Phi_0) reused by every Newton iteration of the step, and (reuse_factor) by up to
+  // that many further steps at the same dt
+  bool factored = p.reuse_factor > 0 && s->factors_ok && s->factor_age < p.reuse_factor &&
+                  std::fabs(dt / s->factor_dt - 1.0) <= 1e-3;
+  if (factored) ++s->factor_age;
   while (rnorm > target && m < p.newton_max_it) {
-    if (!factored) {  // factors of J(Phi_0) reused by every Newton iteration of the step
+    if (!factored) {
+      s->factors_ok = false;
       if ((rc = factor_blocks(s, s->q, idt))) return rc;
       factored = true;
+      s->factors_ok = true;
+      s->factor_dt = dt;
+      s->factor_age = 0;
     }
     int its = 0;
     rc = gmres(s, idt, rnorm, std::max(p.gmres_rtol * rnorm, p.gmres_atol), &its);
@@ -893,6 +906,7 @@ int pfc_default_params(pfc_params* p) {
   p->apply_variant = -1;
   p->gmres_reorth_eta = 0.3;
   p->use_graph = 1;
+  p->reuse_factor = 0;
   return PFC_OK;
 }
 
@@ -1140,6 +1154,7 @@ int pfc_set_field(pfc_state* s, const double* phi, int on_device) {
   CU(cudaMemcpyAsync(s->phinm1, s->phin, b, cudaMemcpyDeviceToDevice, s->st));
   CU(cudaStreamSynchronize(s->st));
   s->have_E = s->have_Em1 = s->have_prev_dt = s->have_user_guess = false;
+  s->factors_ok = false;
   return PFC_OK;
 }
 
@@ -1207,6 +1222,7 @@ int pfc_load(pfc_state* s, const char* path) {
   CU(cudaMemcpyAsync(s->phin, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice, s->st));
   CU(cudaMemcpyAsync(s->phinm1, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, s->st));
   CU(cudaStreamSynchronize(s->st));
+  s->factors_ok = false;
   s->have_E = hd.have_E;
   s->have_Em1 = hd.have_Em1;
   s->have_prev_dt = hd.have_prev_dt;
@@ -1420,6 +1436,7 @@ int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v
 int pfc_precond_apply(pfc_state* s, const double* Phi, const double* phin, double dt, const double* r, double* z) {
   if (!s || !Phi || !phin || !r || !z || !(dt > 0.0)) return PFC_EINVAL;
   pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  s->factors_ok = false;  // the factors below belong to this call's arguments, not to a step
   int rc = factor_blocks(s, s->qt, 1.0 / dt);
   if (rc) return rc;
   precond(s, r, nullptr, z, nullptr);

@@ -259,6 +259,21 @@ def test_schwarz_kinds_steps_match_oracle(pfc, kind):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
+def test_factor_reuse_across_steps_keeps_the_solution(pfc, prec, tol):
+    """reuse_factor = 3: the subdomain factors of one step serve up to three more steps at the
+    same dt (the controller holds dt = dt_max on this field after its first steps); the
+    Newton solutions still match the oracle, which refactors every step."""
+    w = inputs.workload("noise64")
+    prm = dict(dt_min=1e-2, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, w["shape"], w["parts"], prec=prec, overlap=1, reuse_factor=3, **prm)
+    s.set_field(w["phi"])
+    recs = s.run(6)
+    ref, orecs = O.run(w["phi"], w["h"], w["gamma"], O.Params(parts=w["parts"], overlap=1, **prm), 6)
+    assert np.abs(s.get_field() - ref).max() <= tol
+    assert [r["dt"] for r in recs] == pytest.approx([o.dt for o in orecs], rel=1e-9)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
 @pytest.mark.parametrize("shape", [(27, 21), (45, 37)])
 def test_odd_point_count_steps_match_oracle(pfc, shape, prec, tol):
     """Grids of 567 and 1665 points: every Krylov vector has odd length, so the last
