@@ -43,6 +43,13 @@ __device__ __forceinline__ float to_store<float>(double v) { return (float)v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
 
+// Compute type -> storage type without a detour through double (double <-> float
+// conversions run on GB300's FP64 pipe).
+template <typename TS, typename TC>
+__device__ __forceinline__ TS to_store_t(TC v) { return (TS)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store_t<__nv_bfloat16, float>(float v) { return __float2bfloat16(v); }
+
 template <typename TC, typename TS>
 __device__ __forceinline__ TC from_store(TS v) { return (TC)v; }
 template <>
@@ -206,19 +213,19 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
         if (pos < n) l = A[off + kw] * dinv;
         lv[i] = l;
       }
-      L[(size_t)k * lrow + i] = to_store<TS>((double)l);
+      L[(size_t)k * lrow + i] = to_store_t<TS>(l);
     }
     for (int j = tid; j < ucol; j += nt) {
       const int col = k + j;
       TC u = (TC)0;
       if (j <= ku2 && col < n) {
         u = A[sk * RS + (col & (RING - 1))];
-        U[(size_t)col * ucol + j] = to_store<TS>((double)(j == 0 ? dinv : u));
+        U[(size_t)col * ucol + j] = to_store_t<TS>((TC)(j == 0 ? dinv : u));
       }
       if (j <= ku2) uv[j] = u;
     }
     // U column k's entries above the band (j > ku2) stay zero for the bulk copies
-    for (int j = ku2 + 1 + tid; j < ucol; j += nt) U[(size_t)k * ucol + j] = to_store<TS>(0.0);
+    for (int j = ku2 + 1 + tid; j < ucol; j += nt) U[(size_t)k * ucol + j] = to_store_t<TS>((TC)0);
     __syncthreads();
     // rank-1 update of the active window; multipliers and row offsets are read four at a time
     // (16-byte loads), so shared memory carries about half the traffic of one load per row
@@ -280,83 +287,71 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
   }
 }
 
-// ---- Register-resident band LU (compute type float, kl <= 63).
+// ---- Column-owned band LU (compute type float, kl <= 63).
 //
 // The same elimination as k_factor2d (same pivots, same multipliers, same rank-1
-// updates in the same order of operations, so the same factors), arranged for the
-// register file: thread t of the 128 owns ring column slot t and keeps that
-// column's entries for the 64 row slots of the window in registers.  Per step the
-// owner of column k publishes it to shared memory, warp 0 picks the pivot and
-// forms the multipliers, and every column applies its rank-1 update in registers;
-// the pivot row's entry a[slot] and the entering row's entry are reached through
-// a warp-uniform switch.  New rows are generated from per-column tables of the
-// q-dependent entries (evaluated in double as jac_entry does, then rounded).
-constexpr int kRegRows = 64;   // row slots (window of kl + 1 <= 64 rows)
-constexpr int kRegRing = 128;  // column slots (2 kl + 2 <= 128)
+// updates with the same operations, so the same factors), arranged by columns:
+// thread t of the 128 owns ring column slot t and keeps that column's entries for
+// the 64 row slots of the window in its own row of shared memory (68 floats apart,
+// so 16-byte accesses of 8 neighbouring threads hit distinct banks).  Per step warp
+// 0 reads column k, picks the pivot and forms the multipliers; every thread then
+// updates its column with 16-byte loads and stores (one load of its entries, one
+// of the multipliers, four FMAs, one store per four rows).  New rows come from
+// per-column tables of the q-dependent entries (evaluated in double as jac_entry
+// does, then rounded).
+constexpr int kColRows = 64;     // row slots (window of kl + 1 <= 64 rows)
+constexpr int kColRing = 128;    // column slots (2 kl + 2 <= 128)
+constexpr int kColStride = 68;   // floats per column row in shared memory
 
-#define PFC_CASES8(b) \
-  PFC_CASE(b + 0) PFC_CASE(b + 1) PFC_CASE(b + 2) PFC_CASE(b + 3) PFC_CASE(b + 4) PFC_CASE(b + 5) PFC_CASE(b + 6) PFC_CASE(b + 7)
-#define PFC_CASES64 \
-  PFC_CASES8(0) PFC_CASES8(8) PFC_CASES8(16) PFC_CASES8(24) PFC_CASES8(32) PFC_CASES8(40) PFC_CASES8(48) PFC_CASES8(56)
-__device__ __forceinline__ float reg_get(const float (&a)[kRegRows], int s) {
-  switch (s) {
-#define PFC_CASE(i) \
-  case i: return a[i];
-    PFC_CASES64
-#undef PFC_CASE
-  }
-  return 0.0f;
-}
-__device__ __forceinline__ void reg_set(float (&a)[kRegRows], int s, float v) {
-  switch (s) {
-#define PFC_CASE(i) \
-  case i: a[i] = v; break;
-    PFC_CASES64
-#undef PFC_CASE
-  }
+size_t factor_col_smem_bytes(int n_max) {
+  const size_t cols = (size_t)kColRing * kColStride * sizeof(float);
+  const size_t qtmp = (size_t)n_max * sizeof(double);  // q on the block, only while the tables are made
+  return (cols > qtmp ? cols : qtmp) + (size_t)n_max * 5 * sizeof(float) + 49 * sizeof(double);
 }
 
 template <typename TS>
-__global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(kColRing) k_factor2d_col(Geo g, const BlockDesc* __restrict__ blocks,
                                                          const double* __restrict__ q, double idt,
                                                          const double* __restrict__ lin, FactorStore fs,
                                                          int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float colbuf[kRegRows];     // column k by row slot
-  __shared__ __align__(16) float lslot[kRegRows];  // multipliers by row slot (0 off the window)
-  __shared__ int slot[kRegRows];         // window position & 63 -> row slot
-  __shared__ int posof[kRegRows];        // row slot -> window position (-1: free)
-  __shared__ float linf[49];             // the stencil table, rounded
+  __shared__ __align__(16) float lslot[kColRows];  // multipliers by row slot (0 off the window)
+  __shared__ int slot[kColRows];                   // window position & 63 -> row slot
+  __shared__ int posof[kColRows];                  // row slot -> window position (-1: free)
+  __shared__ float linf[49];                       // the stencil table, rounded
   __shared__ float s_dinv;
   __shared__ int s_sk;
-  constexpr int PM = kRegRows - 1;
+  constexpr int PM = kColRows - 1;
   const BlockDesc B = blocks[blockIdx.x];
   const int n = B.bx * B.by, bx = B.bx;
   const int kl = min(3 * bx, n - 1);
   const int ku2 = min(2 * kl, n - 1);
   const int W = kl + 1;
   const int lrow = fs.lrow, ucol = fs.ucol;
-  double* qb = reinterpret_cast<double*>(smem);              // q on the block
-  double* lin_s = qb + fs.n_max;                             // 7 x 7 stencil table
-  float* tabq = reinterpret_cast<float*>(lin_s + 49);        // per column: centre, -x, +x, -y, +y entries
+  const size_t cols = (size_t)kColRing * kColStride * sizeof(float);
+  const size_t qtmp = (size_t)fs.n_max * sizeof(double);
+  float* colA = reinterpret_cast<float*>(smem);  // column slot t: colA[t * kColStride + row slot]
+  double* qb = reinterpret_cast<double*>(smem);  // q on the block (before the columns are filled)
+  double* lin_s = reinterpret_cast<double*>(smem + (cols > qtmp ? cols : qtmp));  // 7 x 7 stencil table
+  float* tabq = reinterpret_cast<float*>(lin_s + 49);                            // per column: 5 entries
   TS* L = (TS*)fs.L + blockIdx.x * fs.strideL;
   TS* U = (TS*)fs.U + blockIdx.x * fs.strideU;
   uint8_t* piv = fs.piv + blockIdx.x * fs.strideP;
   const int t = threadIdx.x, lane = t & 31;
   const double ih2 = g.ih2;
 
-  for (int i = t; i < n; i += kRegRing)
+  for (int i = t; i < n; i += kColRing)
     qb[i] = q[wrap(B.x0 + i % bx, g.nx) + (long long)g.nx * wrap(B.y0 + i / bx, g.ny)];
-  for (int i = t; i < 49; i += kRegRing) {
+  for (int i = t; i < 49; i += kColRing) {
     lin_s[i] = lin[i];
     linf[i] = (float)lin[i];
   }
-  if (t < kRegRows) {
+  if (t < kColRows) {
     slot[t] = t;
     posof[t] = t < W ? t : -1;
   }
   __syncthreads();
-  for (int i = t; i < n; i += kRegRing) {  // the entries jac_entry gives for ad <= 1, same expressions
+  for (int i = t; i < n; i += kColRing) {  // the entries jac_entry gives for ad <= 1, same expressions
     const int dirs[5] = {24, 23, 25, 17, 31};  // (dx, dy) = (0,0), (-1,0), (1,0), (0,-1), (0,1)
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
@@ -366,45 +361,42 @@ __global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const Block
       tabq[5 * i + d] = (float)e;
     }
   }
-  float a[kRegRows];
-#pragma unroll
-  for (int r = 0; r < kRegRows; ++r)
-    a[r] = (r < W && r < n && t < n) ? (float)jac_entry(bx, ih2, qb, idt, lin_s, r, t) : 0.0f;
-  // block coordinates of this thread's column (column t, then t + 128, ...) and of the entering row
-  int ac = t % bx, bc = t / bx;
-  const int da = kRegRing % bx, db = kRegRing / bx;
-  int ar = (kl + 1) % bx, br = (kl + 1) / bx;
+  __syncthreads();  // qb is dead: its bytes become the columns
+  // entry (row r, column col) of A_k from the tables: (ar, br), (ac, bc) block coordinates
+  auto entry = [&](int ar, int br, int ac, int bc, int col) -> float {
+    const int dx = ac - ar, dy = bc - br, ad = abs(dx) + abs(dy);
+    if (ad > 3) return 0.0f;
+    if (ad == 0) return tabq[5 * col];
+    if (ad == 1) return tabq[5 * col + (dx == -1 ? 1 : dx == 1 ? 2 : dy == -1 ? 3 : 4)];
+    return linf[(dy + 3) * 7 + dx + 3];
+  };
+  float* mine = colA + (size_t)t * kColStride;
+  int ac = t % bx, bc = t / bx;  // block coordinates of this thread's column (t, then t + 128, ...)
+  for (int r = 0; r < kColRows; ++r)
+    mine[r] = (r < W && r < n && t < n) ? entry(r % bx, r / bx, ac, bc, t) : 0.0f;
+  const int da = kColRing % bx, db = kColRing / bx;
+  int ar = (kl + 1) % bx, br = (kl + 1) / bx;  // block coordinates of the entering row
   __syncthreads();
 
   for (int k = 0; k < n; ++k) {
-    const int kw = k & (kRegRing - 1);
+    const int kw = k & (kColRing - 1);
     const int last = min(k + kl, n - 1);
-    if (t == kw)
-#pragma unroll
-      for (int r = 0; r < kRegRows; ++r) colbuf[r] = a[r];
-    __syncthreads();
     if (t < 32) {  // partial pivoting: largest |a_ik| over the window, first on ties
-      float best = -1.0f;
-      int bp = k;
-      for (int pos = k + lane; pos <= last; pos += 32) {
-        const float v = fabsf(colbuf[slot[pos & PM]]);
-        if (v > best) {
-          best = v;
-          bp = pos;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (ob > best || (ob == best && op < bp)) {
-          best = ob;
-          bp = op;
-        }
-      }
+      const float* colk = colA + (size_t)kw * kColStride;
+      // lane candidates: positions k + lane and k + lane + 32 (window <= 64 rows); |a| compares as
+      // its bit pattern, a warp max of the bits and two ballots give the first maximal position
+      const int p0 = k + lane, p1 = k + lane + 32;
+      const unsigned b0 = p0 <= last ? __float_as_uint(fabsf(colk[slot[p0 & PM]])) : 0u;
+      const unsigned b1 = p1 <= last ? __float_as_uint(fabsf(colk[slot[p1 & PM]])) : 0u;
+      const bool second = b1 > b0 && p1 <= last;  // ties keep the earlier position
+      const unsigned bb = second ? b1 : b0;
+      const unsigned mx = __reduce_max_sync(0xffffffffu, bb);
+      const unsigned first_set = __ballot_sync(0xffffffffu, bb == mx && !second && p0 <= last);
+      const unsigned second_set = __ballot_sync(0xffffffffu, bb == mx && second);
+      const int bp = first_set ? k + __ffs(first_set) - 1 : k + 32 + __ffs(second_set) - 1;
       const int sk0 = slot[k & PM], sp = slot[bp & PM];
-      float d = colbuf[sp];
-      if (d == 0.0f) d = 1.0f;
-      const float dinv = 1.0f / d;
+      const float d0 = colk[sp];
+      const float dinv = 1.0f / (d0 == 0.0f ? 1.0f : d0);
       __syncwarp();
       if (lane == 0) {
         slot[k & PM] = sp;
@@ -412,39 +404,42 @@ __global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const Block
         posof[sk0] = bp;
         posof[sp] = k;
         piv[k] = (uint8_t)(bp - k);
-        if (colbuf[sp] == 0.0f) atomicExch(status, PFC_ESINGULAR);
+        if (d0 == 0.0f) atomicExch(status, PFC_ESINGULAR);
         s_dinv = dinv;
         s_sk = sp;
       }
       __syncwarp();
-      for (int r = lane; r < kRegRows; r += 32) {  // multipliers by slot: rows k+1 .. last
+      for (int r = lane; r < kColRows; r += 32) {  // multipliers by slot: rows k+1 .. last
         const int pos = posof[r];
-        lslot[r] = (pos > k && pos <= last) ? colbuf[r] * dinv : 0.0f;
+        lslot[r] = (pos > k && pos <= last) ? colk[r] * dinv : 0.0f;
       }
-      __syncwarp();
-      for (int i = lane; i < lrow; i += 32)
-        L[(size_t)k * lrow + i] = to_store<TS>((double)(i < kl && k + 1 + i <= last ? lslot[slot[(k + 1 + i) & PM]] : 0.0f));
     }
     __syncthreads();
+    if (t >= 32 && t < 64) {  // L row k (the multipliers in window order), off warp 0's path
+      const int ln = t - 32, last = min(k + kl, n - 1);
+      for (int i = ln; i < lrow; i += 32)
+        L[(size_t)k * lrow + i] = to_store_t<TS>(i < kl && k + 1 + i <= last ? lslot[slot[(k + 1 + i) & PM]] : 0.0f);
+    }
     const int sk = s_sk;
-    const float u = reg_get(a, sk);  // the pivot row's entry in this column
-    const int j = (t - k) & (kRegRing - 1), c = k + j;
-    if (j <= ku2 && c < n) U[(size_t)c * ucol + j] = to_store<TS>((double)(j == 0 ? s_dinv : u));
+    const float u = mine[sk];  // the pivot row's entry in this column
+    const int j = (t - k) & (kColRing - 1), c = k + j;
+    if (j <= ku2 && c < n) U[(size_t)c * ucol + j] = to_store_t<TS>(j == 0 ? s_dinv : u);
     if (j == 0)  // U column k's entries above the band stay zero for the bulk copies
-      for (int jj = ku2 + 1; jj < ucol; ++jj) U[(size_t)k * ucol + jj] = to_store<TS>(0.0);
+      for (int jj = ku2 + 1; jj < ucol; ++jj) U[(size_t)k * ucol + jj] = to_store_t<TS>(0.0f);
     if (j >= 1 && j <= ku2 && c < n) {  // rank-1 update of this column
-#pragma unroll
-      for (int r = 0; r < kRegRows; r += 4) {
+#pragma unroll 4
+      for (int r = 0; r < kColRows; r += 4) {
         const float4 l4 = *reinterpret_cast<const float4*>(&lslot[r]);
-        a[r] -= l4.x * u;
-        a[r + 1] -= l4.y * u;
-        a[r + 2] -= l4.z * u;
-        a[r + 3] -= l4.w * u;
+        float4 a4 = *reinterpret_cast<const float4*>(&mine[r]);
+        a4.x -= l4.x * u;
+        a4.y -= l4.y * u;
+        a4.z -= l4.z * u;
+        a4.w -= l4.w * u;
+        *reinterpret_cast<float4*>(&mine[r]) = a4;
       }
     }
     if (j == ku2 + 1)  // the column entering the band starts at zero
-#pragma unroll
-      for (int r = 0; r < kRegRows; ++r) a[r] = 0.0f;
+      for (int r = 0; r < kColRows; r += 4) *reinterpret_cast<float4*>(&mine[r]) = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j == 0) {  // this slot now holds column k + 128
       ac += da;
       bc += db;
@@ -455,18 +450,8 @@ __global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const Block
     }
     const int rnew = k + 1 + kl;
     if (rnew < n) {  // the next row of A_k enters the pivot row's slot
-      const int colw = k + 1 + ((t - k - 1) & (kRegRing - 1));
-      const int dx = ac - ar, dy = bc - br, ad = abs(dx) + abs(dy);
-      float v = 0.0f;
-      if (colw < n && ad <= 3) {
-        if (ad == 0)
-          v = tabq[5 * colw];
-        else if (ad == 1)
-          v = tabq[5 * colw + (dx == -1 ? 1 : dx == 1 ? 2 : dy == -1 ? 3 : 4)];
-        else
-          v = linf[(dy + 3) * 7 + dx + 3];
-      }
-      reg_set(a, sk, v);
+      const int colw = k + 1 + ((t - k - 1) & (kColRing - 1));
+      mine[sk] = colw < n ? entry(ar, br, ac, bc, colw) : 0.0f;
       if (t == 0) {
         slot[rnew & PM] = sk;
         posof[sk] = rnew;
@@ -478,10 +463,9 @@ __global__ void __launch_bounds__(kRegRing, 4) k_factor2d_reg(Geo g, const Block
     } else if (t == 0) {
       posof[sk] = -1;
     }
+    __syncthreads();
   }
 }
-#undef PFC_CASES64
-#undef PFC_CASES8
 
 // Shared-memory carve-out of one warp of the apply kernel.
 struct ApplySmem {
@@ -776,7 +760,7 @@ __global__ void __launch_bounds__(32 * WPC) k_chunk2d(const BlockDesc* __restric
       for (int r = 0; r < KC; ++r) E11[r * KC + lane] = e[r];
     }
     TS* L21 = reinterpret_cast<TS*>(rec + wp + KC * KC * sizeof(TC));
-    for (int idx = lane; idx < kl * KC; idx += 32) L21[idx] = to_store<TS>(-(double)X[KC * KC + idx]);
+    for (int idx = lane; idx < kl * KC; idx += 32) L21[idx] = to_store_t<TS>(-X[KC * KC + idx]);
     // backward: U11^{-1} (column lane by back substitution with the stored 1 / u_kk) and -U_a
     TC* U11i = reinterpret_cast<TC*>(fs.X + chunk_rec_off(fs, b, cg.nc, 2 * cg.nc - 1 - c));
     if (lane < KC) {
@@ -799,9 +783,9 @@ __global__ void __launch_bounds__(32 * WPC) k_chunk2d(const BlockDesc* __restric
     TS* Ua = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(U11i) + KC * KC * sizeof(TC));
     for (int idx = lane; idx < ku2 * KC; idx += 32) {
       const int i = idx / KC, j = idx % KC, jj = ku2 + j - i;  // u(k0 - ku2 + i, k0 + j) at U column k0 + j
-      double v = 0.0;
-      if (j < bc && jj <= ku2 && k0 - ku2 + i >= 0) v = -(double)from_store<TC, TS>(U[(size_t)(k0 + j) * fs.ucol + jj]);
-      Ua[idx] = to_store<TS>(v);
+      TC v = (TC)0;
+      if (j < bc && jj <= ku2 && k0 - ku2 + i >= 0) v = -from_store<TC, TS>(U[(size_t)(k0 + j) * fs.ucol + jj]);
+      Ua[idx] = to_store_t<TS>(v);
     }
     __syncwarp();
   }
@@ -1079,10 +1063,11 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
-  if (sizeof(TC) == 4 && fs.kl_max + 1 <= kRegRows && 2 * fs.kl_max + 2 <= kRegRing) {
-    const size_t smem = (size_t)(fs.n_max + 49) * sizeof(double) + (size_t)fs.n_max * 5 * sizeof(float);
-    cudaFuncSetAttribute(k_factor2d_reg<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d_reg<TS><<<nblocks, kRegRing, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+  if (sizeof(TC) == 4 && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
+      factor_col_smem_bytes(fs.n_max) <= 227 * 1024) {
+    const size_t smem = factor_col_smem_bytes(fs.n_max);
+    cudaFuncSetAttribute(k_factor2d_col<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_factor2d_col<TS><<<nblocks, kColRing, smem, st>>>(g, blocks, q, idt, lin, fs, status);
     count_launches(1);
     return;
   }
