@@ -49,20 +49,6 @@ __device__ __forceinline__ const double* vec_at(const double* v0, const double* 
 
 // ---- single-thread GMRES bookkeeping
 
-// After a multi-dot of V_0..V_j against w (c->red[0..j]) and w.w (c->red[j+1]).
-__device__ void gmres_after_dot(GmresCtl* c, int j, int pass) {
-  const int m1 = kMaxRestart + 1;
-  for (int i = 0; i <= j; ++i) {
-    const double h = c->scale[i] * c->red[i];
-    if (pass == 0)
-      c->H[i + m1 * j] = h;
-    else
-      c->H[i + m1 * j] += h;
-    c->coef[i] = h * c->scale[i];
-  }
-  if (pass == 0) c->wnorm2_before = c->red[j + 1];
-}
-
 __device__ void gmres_finalize(GmresCtl* c, int j, int m, double wn2) {
   const int m1 = kMaxRestart + 1;
   double* Hj = c->H + m1 * j;
@@ -129,13 +115,30 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
     if (lane == 0) s_sum[v] = s;
   }
   __syncthreads();
+  if (t.kind == Tail::kDot) {  // one thread per Hessenberg entry: the FP64 products run side by side
+    GmresCtl* c = t.ctl;
+    const int j = t.ia ? t.ia->j : t.j;
+    const int m1 = kMaxRestart + 1;
+    for (int i = threadIdx.x; i <= j + 1 && i < nvals; i += blockDim.x) c->red[i] = s_sum[i];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      const double sc = c->scale[i];
+      const double h = sc * s_sum[i];
+      if (t.pass == 0)
+        c->H[i + m1 * j] = h;
+      else
+        c->H[i + m1 * j] += h;
+      c->coef[i] = h * sc;
+    }
+    if (threadIdx.x == 0) {
+      if (t.pass == 0) c->wnorm2_before = s_sum[j + 1];
+      *t.counter = 0u;  // ready for the next kernel on this stream
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     GmresCtl* c = t.ctl;
     const int j = t.ia ? t.ia->j : t.j;
-    if (t.kind == Tail::kDot) {
-      for (int v = 0; v < nvals; ++v) c->red[v] = s_sum[v];
-      gmres_after_dot(c, j, t.pass);
-    } else if (t.kind == Tail::kAxpy) {
+    if (t.kind == Tail::kAxpy) {
       gmres_after_axpy(c, j, t.pass, t.m, s_sum[0]);
     } else {
       for (int v = 0; v < nvals; ++v) t.out[v] = s_sum[v];
