@@ -65,6 +65,9 @@ struct pfc_state {
   int* status_dev;
   // host mirrors (pinned)
   GmresCtl* ctl_h;
+  // host loop: control-block heads read back after every chunk of iterations, two in flight
+  GmresCtl* ctl_hb[2];
+  cudaEvent_t ctl_ev[2];
   double* red_h;
   int* status_h;
   // history for the adaptive step and the extrapolated guess
@@ -679,12 +682,18 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
       pfc::count_launches((long long)s->graph_body * std::max(1, s->ctl_h->its));
     }
     // basis V_0 = v0, V_i = Vbuf + i vstride (pointer table s->vtab); Z_i = Zbuf + i vstride (s->ztab)
+    // Host loop: iterations are queued a chunk at a time; after each chunk the head of the control
+    // block is copied back asynchronously, and the host waits for a chunk's head only once the next
+    // chunk is queued, so the GPU never idles on the host.  A chunk queued after the cycle ended runs
+    // its kernels as immediate returns (the done flag).
     int j = graph ? m : 0;
     const int chunk = 3;
-    while (j < m) {
-      const int jstart = j;
-      const int jend = std::min(m, j + chunk);
-      for (; j < jend; ++j) {
+    int c = 0, pend = -1, p0 = 0, p1 = 0;  // chunks queued; buffer and iterations of the pending chunk
+    bool stop = graph;
+    while (!stop) {
+      const int q0 = j, q1 = std::min(m, j + chunk);
+      const bool more = q0 < q1;
+      for (; j < q1; ++j) {
         const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * s->vstride;
         double* zj = s->Zbuf + (size_t)j * s->vstride;
         double* w = s->Vbuf + (size_t)(j + 1) * s->vstride;
@@ -703,19 +712,38 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
                                 pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
         }
       }
-      CU(cudaGetLastError());
+      if (more) {
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(s->ctl_hb[c & 1], s->ctl, offsetof(GmresCtl, H), cudaMemcpyDeviceToHost, s->st));
+        CU(cudaEventRecord(s->ctl_ev[c & 1], s->st));
+      }
+      if (pend >= 0) {  // the chunk before this one: did the cycle end there?
+        CU(cudaEventSynchronize(s->ctl_ev[pend]));
+        const GmresCtl* hb = s->ctl_hb[pend];
+        if (s->prof) {  // only applies that ran (not the ones skipped after convergence)
+          const int ran_to = hb->done ? std::min(hb->its, p1) : p1;
+          for (int t = p0; t < ran_to; ++t) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, s->ev[2 * t], s->ev[2 * t + 1]));
+            s->apply_ms += ms;
+            s->apply_launches += 1;
+          }
+        }
+        if (hb->done) stop = true;
+      }
+      if (more) {
+        pend = c & 1;
+        p0 = q0;
+        p1 = q1;
+        ++c;
+      } else {
+        pend = -1;
+        stop = true;
+      }
+    }
+    if (!graph) {  // the cycle's final head (every queued kernel has finished after this)
       int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
       if (rc) return rc;
-      if (s->prof) {  // only applies that ran (not the ones skipped after convergence)
-        const int ran_to = s->ctl_h->done ? std::min(s->ctl_h->its, jend) : jend;
-        for (int t = jstart; t < ran_to; ++t) {
-          float ms = 0.f;
-          CU(cudaEventElapsedTime(&ms, s->ev[2 * t], s->ev[2 * t + 1]));
-          s->apply_ms += ms;
-          s->apply_launches += 1;
-        }
-      }
-      if (s->ctl_h->done) break;
     }
     const int its = s->ctl_h->its;
     total += its;
@@ -1011,6 +1039,10 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->ia = (pfc::IterArgs*)at(pl.iargs);
   s->fs.order = (const int*)at(pl.order);
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->ctl_hb[0], sizeof(GmresCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->ctl_hb[1], sizeof(GmresCtl)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ctl_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ctl_ev[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&s->ia_h, sizeof(pfc::IterArgs)) != cudaSuccess) {
@@ -1139,6 +1171,10 @@ void pfc_destroy(pfc_state* s) {
   if (!s) return;
   pfc_profile(s, 0);
   if (s->ctl_h) cudaFreeHost(s->ctl_h);
+  for (int b = 0; b < 2; ++b) {
+    if (s->ctl_hb[b]) cudaFreeHost(s->ctl_hb[b]);
+    if (s->ctl_ev[b]) cudaEventDestroy(s->ctl_ev[b]);
+  }
   if (s->red_h) cudaFreeHost(s->red_h);
   if (s->status_h) cudaFreeHost(s->status_h);
   if (s->ia_h) cudaFreeHost(s->ia_h);
