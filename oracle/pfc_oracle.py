@@ -103,12 +103,36 @@ def mu_dvd(Phi: np.ndarray, phin: np.ndarray, h: float, gamma: float) -> np.ndar
     return L_gamma(0.5 * (Phi + phin), h, gamma) + cubic
 
 
-def residual(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float) -> np.ndarray:
-    """Nonlinear residual of the semi-implicit scheme Eq. (NSOP) with M = 1:
-    F(Phi) = (Phi - phi^n)/dt - Delta_d mu(Phi, phi^n).
+def mobility_nodes(Phi: np.ndarray, phin: np.ndarray) -> np.ndarray:
+    """M_d of Eq. (NSOP) for M(phi) = 1 - phi^2: M at the midpoint (Phi + phi^n)/2, node by node."""
+    s = 0.5 * (Phi + phin)
+    return 1.0 - s * s
+
+
+def div_m_grad(u: np.ndarray, Mn: np.ndarray, h: float) -> np.ndarray:
+    """(div M grad)_d u = sum over axes D(M D u) (Sec. 3): the mobility on the
+    midpoint of an edge is the average of its two end nodes, so the flux through
+    the edge i+1/2 is (M_i + M_{i+1})/2 (u_{i+1} - u_i)/h, and the divergence is
+    the difference of the fluxes through the two edges of a node, over h.  Periodic."""
+    out = np.zeros_like(u)
+    for ax in range(u.ndim):
+        edge = 0.5 * (Mn + np.roll(Mn, -1, axis=ax))
+        flux = edge * (np.roll(u, -1, axis=ax) - u) / (h * h)
+        out += flux - np.roll(flux, 1, axis=ax)
+    return out
+
+
+def residual(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
+             mobility: bool = False) -> np.ndarray:
+    """Nonlinear residual of the semi-implicit scheme Eq. (NSOP):
+    F(Phi) = (Phi - phi^n)/dt - (div M_d grad)_d mu(Phi, phi^n), with M = 1
+    (Delta_d) or, when `mobility`, M(phi) = 1 - phi^2 evaluated at (Phi + phi^n)/2.
     READING: sign and 1/dt scaling follow the commented-out form F = (Phi -
     Phi^n)/dt + E(Phi, Phi^n) printed before Eq. (NLS)."""
-    return (Phi - phin) / dt - lap(mu_dvd(Phi, phin, h, gamma), h)
+    mu = mu_dvd(Phi, phin, h, gamma)
+    if mobility:
+        return (Phi - phin) / dt - div_m_grad(mu, mobility_nodes(Phi, phin), h)
+    return (Phi - phin) / dt - lap(mu, h)
 
 
 def jac_coeff(Phi: np.ndarray, phin: np.ndarray) -> np.ndarray:
@@ -116,10 +140,19 @@ def jac_coeff(Phi: np.ndarray, phin: np.ndarray) -> np.ndarray:
     return (3.0 * Phi**2 + 2.0 * Phi * phin + phin**2) / 4.0
 
 
-def jvp(v: np.ndarray, Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float) -> np.ndarray:
-    """Jacobian-vector product of Eq. (Jacobi): J v = v/dt - Delta_d(1/2 L_gamma v + q v)."""
+def jvp(v: np.ndarray, Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
+        mobility: bool = False) -> np.ndarray:
+    """Jacobian-vector product of Eq. (Jacobi): J v = v/dt - Delta_d(1/2 L_gamma v + q v).
+    With `mobility` (M = 1 - phi^2 at the midpoint s = (Phi + phi^n)/2) the derivative
+    of F also differentiates M_d: dM/dPhi = -2 s * 1/2 = -s, so
+    J v = v/dt - (div M grad)_d(1/2 L_gamma v + q v) - (div (-s v) grad)_d mu."""
     q = jac_coeff(Phi, phin)
-    return v / dt - lap(0.5 * L_gamma(v, h, gamma) + q * v, h)
+    w = 0.5 * L_gamma(v, h, gamma) + q * v
+    if not mobility:
+        return v / dt - lap(w, h)
+    s = 0.5 * (Phi + phin)
+    mu = mu_dvd(Phi, phin, h, gamma)
+    return v / dt - div_m_grad(w, mobility_nodes(Phi, phin), h) - div_m_grad(mu, -s * v, h)
 
 
 def _lap_matrix(shape: Tuple[int, ...], h: float) -> sp.csr_matrix:
@@ -140,16 +173,40 @@ def _lap_matrix(shape: Tuple[int, ...], h: float) -> sp.csr_matrix:
     return out.tocsr()
 
 
-def assemble_jacobian(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float) -> sp.csr_matrix:
+def _shift_matrix(shape: Tuple[int, ...], ax: int) -> sp.csr_matrix:
+    """S with (S u)_i = u_{i+1} along axis ax (periodic), C-order unknowns."""
+    n = int(np.prod(shape))
+    idx = np.arange(n).reshape(shape)
+    return sp.csr_matrix((np.ones(n), (idx.ravel(), np.roll(idx, -1, axis=ax).ravel())), shape=(n, n))
+
+
+def assemble_jacobian(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
+                      mobility: bool = False) -> sp.csr_matrix:
     """Assembled Jacobian J = I/dt - Delta_d (1/2 L_gamma + diag q) as CSR
-    (Eq. Jacobi; L_gamma from Eq. discretedG)."""
+    (Eq. Jacobi; L_gamma from Eq. discretedG).  With `mobility`, Delta_d becomes
+    D_M = sum_ax (I - S^T) diag(M_edge) (S - I)/h^2 and the term of dM/dPhi is
+    added: B = sum_ax (I - S^T) diag((S - I) mu / h^2) (I + S)/2 diag(-s)."""
     shape = Phi.shape
     n = Phi.size
     lapm = _lap_matrix(shape, h)
     eye = sp.identity(n, format="csr")
     lg = (1.0 - gamma) * eye + 2.0 * lapm + lapm @ lapm
     q = sp.diags(jac_coeff(Phi, phin).ravel())
-    J = eye / dt - lapm @ (0.5 * lg + q)
+    if not mobility:
+        J = eye / dt - lapm @ (0.5 * lg + q)
+    else:
+        Mn = mobility_nodes(Phi, phin).ravel()
+        mu = mu_dvd(Phi, phin, h, gamma).ravel()
+        s = 0.5 * (Phi + phin).ravel()
+        DM = sp.csr_matrix((n, n))
+        B = sp.csr_matrix((n, n))
+        for ax in range(len(shape)):
+            S = _shift_matrix(shape, ax)
+            edge = 0.5 * (Mn + S @ Mn)
+            DM = DM + (eye - S.T) @ sp.diags(edge) @ (S - eye) / (h * h)
+            grad_mu = (S @ mu - mu) / (h * h)
+            B = B + (eye - S.T) @ sp.diags(grad_mu) @ (0.5 * (eye + S)) @ sp.diags(-s)
+        J = eye / dt - DM @ (0.5 * lg + q) - B
     J = J.tocsr()
     J.sum_duplicates()
     return J
@@ -480,6 +537,7 @@ class Params:
     eta: float = 5000.0
     energy_scaled: bool = True  # READING: controller uses F_d / |Omega|
     dt_halvings: int = 0  # READING: a step whose Newton iteration fails is retried with dt / 2
+    mobility: bool = False  # M(phi) = 1 - phi^2 (Eq. NSOP's M_d); False: M = 1
 
 
 @dataclass
@@ -510,7 +568,7 @@ def newton_solve(
     backtracking lam <- clamp(lam^2 f0 / (f(lam) - f0 + 2 lam f0) ... ) to
     [0.1 lam, 0.5 lam]; optional projection of S to zero mean (mass)."""
     Phi = (phin if guess is None else guess).copy()
-    F = residual(Phi, phin, dt, h, gamma)
+    F = residual(Phi, phin, dt, h, gamma, p.mobility)
     r0 = float(np.linalg.norm(F))
     target = max(p.newton_rtol * (r0 if ref_norm is None else ref_norm), p.newton_atol)
     rnorm = r0
@@ -519,7 +577,7 @@ def newton_solve(
     lambdas: List[float] = []
     pre = None
     while rnorm > target and m < p.newton_max_it:
-        J = assemble_jacobian(Phi, phin, dt, h, gamma)
+        J = assemble_jacobian(Phi, phin, dt, h, gamma, p.mobility)
         if p.precond and pre is None:
             pre = Schwarz(J, decompose(Phi.shape, p.parts, p.overlap), p.ras_kind, p.subdomain_solver,
                           p.ilu_shift)
@@ -536,7 +594,7 @@ def newton_solve(
         lam = 1.0
         for cut in range(p.ls_max_cuts + 1):
             trial = Phi + lam * S
-            Ft = residual(trial, phin, dt, h, gamma)
+            Ft = residual(trial, phin, dt, h, gamma, p.mobility)
             ft = 0.5 * float(np.dot(Ft.ravel(), Ft.ravel()))
             if ft <= (1.0 - 2.0 * p.ls_alpha * lam) * f0 or cut == p.ls_max_cuts:
                 break
@@ -585,8 +643,8 @@ def _step_with_guess(phin, phinm1, dt, dt_prev, h, gamma, p, guess):
         # is not larger than that of phi^n, the paper's own starting point (Sec. 4);
         # after a step-size jump dt/dt_prev is large and the extrapolation poor.
         g = extrapolated_guess(phin, phinm1, dt, dt_prev)
-        ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma)))
-        if ref < np.linalg.norm(residual(g, phin, dt, h, gamma)):
+        ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma, p.mobility)))
+        if ref < np.linalg.norm(residual(g, phin, dt, h, gamma, p.mobility)):
             g = None
         return newton_solve(phin, dt, h, gamma, p, g, ref_norm=ref)
     return newton_solve(phin, dt, h, gamma, p, None)

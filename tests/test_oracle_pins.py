@@ -421,3 +421,79 @@ def test_safeguarded_extrapolation_reaches_the_plain_solution():
     b, rb = O.run(phi0, h, gamma, p, 4, fixed_dt=0.5, guess="extrap")
     assert np.abs(a - b).max() <= 1e-9
     assert sum(r.newton_its for r in rb) <= sum(r.newton_its for r in ra)
+
+
+# ---------------------------------------------------------------- variable mobility M = 1 - phi^2
+def test_mobility_operator_is_conservative_symmetric_and_sums_by_parts():
+    """(div M grad)_d of Sec. 3 with edge-averaged M: sums to zero (mass), is symmetric, and
+    sum u (div M grad)_d u = -sum over edges M_edge (D^+ u)^2 (summation by parts, the
+    dissipation in the energy law); with M constant it is M Delta_d."""
+    shape = (12, 10)
+    u, v = rand_field(shape, 21, 0.0, 1.0), rand_field(shape, 22, 0.0, 1.0)
+    Mn = 0.5 + 0.4 * rand_field(shape, 23, 0.0, 1.0)
+    Du, Dv = O.div_m_grad(u, Mn, H2), O.div_m_grad(v, Mn, H2)
+    assert abs(float(np.sum(Du))) <= 1e-12 * float(np.abs(Du).sum())
+    assert float(np.sum(v * Du)) == pytest.approx(float(np.sum(u * Dv)), rel=1e-12)
+    edges = 0.0
+    for ax in range(2):
+        me = 0.5 * (Mn + np.roll(Mn, -1, axis=ax))
+        edges += float(np.sum(me * O.d_plus(u, ax, H2) ** 2))
+    assert float(np.sum(u * Du)) == pytest.approx(-edges, rel=1e-12)
+    np.testing.assert_allclose(O.div_m_grad(u, np.full(shape, 0.91), H2), 0.91 * O.lap(u, H2), rtol=0,
+                               atol=1e-13 * np.abs(O.lap(u, H2)).max())
+
+
+def test_mobility_jacobian_matches_finite_differences():
+    """With M = 1 - phi^2 at (Phi + phi^n)/2 the Jacobian gains the dM/dPhi term; the analytic
+    J v against central differences of F, and the assembled matrix against J v."""
+    shape = (12, 10)
+    Phi = rand_field(shape, 24, 0.2, 0.4)
+    phin = rand_field(shape, 25, 0.2, 0.4)
+    v = rand_field(shape, 26, 0.0, 1.0)
+    dt = 0.7
+    Jv = O.jvp(v, Phi, phin, dt, H2, GAMMA, mobility=True)
+    eps = 1e-5 * np.linalg.norm(Phi) / np.linalg.norm(v)
+    fd = (O.residual(Phi + eps * v, phin, dt, H2, GAMMA, mobility=True)
+          - O.residual(Phi - eps * v, phin, dt, H2, GAMMA, mobility=True)) / (2 * eps)
+    assert np.linalg.norm(Jv - fd) <= 1e-8 * np.linalg.norm(Jv)
+    J = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA, mobility=True)
+    np.testing.assert_allclose((J @ v.ravel()).reshape(shape), Jv, rtol=0, atol=1e-12 * np.abs(Jv).max())
+    # and it differs from the constant-mobility Jacobian (the term is not dropped)
+    assert np.linalg.norm(Jv - O.jvp(v, Phi, phin, dt, H2, GAMMA)) > 1e-3 * np.linalg.norm(Jv)
+
+
+@pytest.mark.parametrize("dt", [0.05, 1.0])
+def test_mobility_fourier_mode_multiplier(dt):
+    """Small mode on a uniform field phi_bar = 0.3: linearised, the scheme is Crank-Nicolson with
+    mobility M(phi_bar) = 1 - phi_bar^2 and the cubic term's slope 3 phi_bar^2 added to S:
+    phi1 - phi_bar = g (phi0 - phi_bar), g = (1 - dt M kappa S/2)/(1 + dt M kappa S/2)."""
+    shape = (16, 16)
+    h = 1.1
+    ks = (1, 2)
+    pbar = 0.3
+    d0 = 1e-6 * mode(shape, ks, h)
+    lam = kappa(ks, shape, h)
+    S = (1 - GAMMA) + 3 * pbar ** 2 - 2 * lam + lam * lam
+    M = 1 - pbar ** 2
+    g = (1 - 0.5 * dt * M * lam * S) / (1 + 0.5 * dt * M * lam * S)
+    p = O.Params(parts=(2, 2), newton_rtol=1e-13, gmres_rtol=1e-12, mobility=True)
+    phi1, info = O.newton_solve(pbar + d0, dt, h, GAMMA, p)
+    np.testing.assert_allclose(phi1 - pbar, g * d0, rtol=0, atol=1e-5 * 1e-6)
+    # the constant-mobility solve of the same step misses M (a plausible dropped term)
+    assert abs(g - (1 - 0.5 * dt * lam * S) / (1 + 0.5 * dt * lam * S)) > 1e-4
+
+
+def test_mobility_steps_conserve_mass_and_decrease_energy():
+    """Two Newton steps with M = 1 - phi^2 on a noisy field: mass to 1e-12 and a non-increasing
+    discrete energy (Sec. 3 energy law; the dissipation is sum M_edge (D^+ mu)^2 >= 0 while M > 0)."""
+    shape = (16, 16)
+    phi = 0.07 + 0.07 * rand_field(shape, 27, 0.0, 1.0)
+    p = O.Params(parts=(2, 2), mobility=True)
+    e0, m0 = O.energy(phi, H2, GAMMA), O.mass(phi, H2)
+    for _ in range(2):
+        phi, info = O.newton_solve(phi, 0.5, H2, GAMMA, p)
+        assert info.converged
+        e1 = O.energy(phi, H2, GAMMA)
+        assert e1 <= e0 + 1e-13 * abs(e0)
+        assert abs(O.mass(phi, H2) - m0) <= 1e-12 * max(1.0, abs(m0))
+        e0 = e1
