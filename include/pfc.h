@@ -121,6 +121,10 @@ typedef struct {
      dt stays within 1e-3 (relative) of the dt they were made with.  Changes
      the preconditioner only, not the converged phi^{n+1}. */
   int reuse_factor;
+  /* Mobility of Eq. (NSOP): 0 (default) M = 1; 1: M(phi) = 1 - phi^2 evaluated at
+     (Phi + phi^n)/2 and averaged onto edges (Sec. 3), with the Jacobian's
+     dM/dPhi term.  2D grids; the JVP then runs in FP64 on every path. */
+  int mobility;
 } pfc_params;
 
 typedef struct {

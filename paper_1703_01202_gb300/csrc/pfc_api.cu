@@ -46,6 +46,8 @@ struct pfc_state {
   int nblocks;
   pfc::FactorStore fs;
   pfc::Decomp2 dc;  // 2D decomposition (AS / right-RAS overlap sums)
+  // variable mobility: mu and s = (Phi + phi^n)/2 at the iterate of q (mu, sm) and of the trial q (mut, smt)
+  double *mu = nullptr, *mut = nullptr, *sm = nullptr, *smt = nullptr;
   // factors kept across steps (reuse_factor): valid, the dt they were made with, steps reused since
   bool factors_ok = false;
   double factor_dt = 0.0;
@@ -157,6 +159,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
   if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
+  if (p->mobility != 0 && (p->mobility != 1 || g->dim != 2)) return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -305,7 +308,7 @@ size_t basis_stride(long long N) { return ((size_t)N + 31) / 32 * 32 + 17 * 32; 
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs, order, X, Yb;
+      tabs, feat, iargs, order, X, Yb, mu, mut, smid, smidt;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -383,6 +386,11 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->piv = L.take(pl->sP * pl->nblocks);
   pl->X = L.take((size_t)pl->xnc * pl->nblocks * (pl->xfw + pl->xbw));
   pl->Yb = L.take(!d3 && p->ras_kind != PFC_LEFT_RAS ? sizeof(double) * (size_t)pl->n_max * pl->nblocks : 0);
+  const size_t mvec = p->mobility ? vec : 0;  // mu and s = (Phi + phi^n)/2 beside q and the trial q
+  pl->mu = L.take(mvec);
+  pl->mut = L.take(mvec);
+  pl->smid = L.take(mvec);
+  pl->smidt = L.take(mvec);
   pl->blocks = L.take(sizeof(BlockDesc) * pl->nblocks);
   pl->lin = L.take(sizeof(double) * 343);
   pl->ctl = L.take(sizeof(GmresCtl));
@@ -456,8 +464,12 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
                   double idt, double* F, double* Pout, double* qout, int slot) {
   int np = 0;
   if (s->dim == 2) {
+    // with variable mobility, mu and s go beside q: (mu, sm) with q, (mut, smt) with the trial q
+    const bool mob = s->p.mobility != 0;
+    double* muo = qout == s->q ? s->mu : s->mut;
+    double* so = qout == s->q ? s->sm : s->smt;
     pfc::launch_residual2d(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, phin, idt, F, Pout, qout, s->partial,
-                           &np, s->st);
+                           &np, s->st, mob, mob && qout ? muo : nullptr, mob && qout ? so : nullptr);
   } else {
     const double* P = Pb;
     if (S) {  // the trial point is needed at neighbours: materialise it first
@@ -476,7 +488,10 @@ bool ff_sweeps(const pfc_state* s) { return s->p.factor_prec != PFC_F64; }
 
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
          const pfc::IterArgs* ia = nullptr) {
-  if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
+  if (s->dim == 2 && s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
+    const bool trial = q != nullptr && q == s->qt;
+    pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu, trial ? s->smt : s->sm);
+  } else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
     pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
   else if (s->dim == 2)
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
@@ -549,11 +564,17 @@ int tune_apply(pfc_state* s) {
 }
 
 int factor_blocks(pfc_state* s, const double* q, double idt) {
+  if (s->p.mobility) {  // the mobility fields of q's iterate
+    const bool trial = q == s->qt;
+    s->fs.mob_mu = trial ? s->mut : s->mu;
+    s->fs.mob_s = trial ? s->smt : s->sm;
+  }
   if (s->dim == 2) {
     // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx: blocks at most 42 cells
     // wide in x); blocks wider than 21 cells run the wide-window apply kernel in its default shape or
     // the chunked apply
-    if (2 * s->fs.kl_max + 2 > 256 || pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max) > 227 * 1024)
+    if (2 * s->fs.kl_max + 2 > 256 ||
+        pfc::factor_smem_bytes(s->fs.prec, s->fs.kl_max, s->fs.n_max, s->p.mobility ? s->fs.ext_max : 0) > 227 * 1024)
       return PFC_EINVAL;
     if (s->p.apply_variant >= 0 && !variant_ok(s, s->p.apply_variant)) return PFC_EINVAL;
     if (s->p.apply_variant < 0 && !variant_ok(s, 0)) return PFC_EINVAL;
@@ -663,6 +684,8 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
   if (graph) {
     s->ia_h->q = s->q;
     s->ia_h->idt = idt;
+    s->ia_h->mu = s->mu;
+    s->ia_h->sm = s->sm;
     CU(cudaMemcpyAsync(s->ia, s->ia_h, sizeof(pfc::IterArgs), cudaMemcpyHostToDevice, s->st));
   }
   // first cycle: V_0 = F scaled by -1/||F||
@@ -836,6 +859,8 @@ int newton(pfc_state* s, double dt, pfc_step_info* info) {
     std::swap(s->Phi, s->Pt);
     std::swap(s->F, s->Ft);
     std::swap(s->q, s->qt);
+    std::swap(s->mu, s->mut);
+    std::swap(s->sm, s->smt);
     rnorm = std::sqrt(2.0 * ft);
     ++m;
   }
@@ -935,6 +960,7 @@ int pfc_default_params(pfc_params* p) {
   p->gmres_reorth_eta = 0.3;
   p->use_graph = 1;
   p->reuse_factor = 0;
+  p->mobility = 0;
   return PFC_OK;
 }
 
@@ -997,6 +1023,20 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->fs.ucol = pl.ucol;
   s->fs.X = (unsigned char*)at(pl.X);
   s->fs.ras_kind = p->ras_kind;
+  if (p->mobility) {
+    s->mu = (double*)at(pl.mu);
+    s->mut = (double*)at(pl.mut);
+    s->sm = (double*)at(pl.smid);
+    s->smt = (double*)at(pl.smidt);
+    int em = 0;
+    std::vector<BlockDesc> bl;
+    int nm0, km0;
+    build_blocks(g, p, &bl, &nm0, &km0);
+    for (const BlockDesc& b : bl) em = std::max(em, (b.bx + 2) * (b.by + 2));
+    s->fs.ext_max = em;
+  }
+  s->fs.mob_mu = nullptr;
+  s->fs.mob_s = nullptr;
   s->fs.Yb = (double*)at(pl.Yb);
   if (g->dim == 2) {
     s->dc.px = p->sub[0];
@@ -1462,7 +1502,12 @@ int pfc_residual(pfc_state* s, const double* Phi, const double* phin, double dt,
 
 int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v, double dt, double* Jv) {
   if (!s || !Phi || !phin || !v || !Jv || !(dt > 0.0)) return PFC_EINVAL;
-  pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  if (s->p.mobility) {  // q, mu and s of (Phi, phi^n) from the residual (F into scratch)
+    int rc = eval_residual(s, Phi, nullptr, 0.0, false, phin, 1.0 / dt, s->Ft, nullptr, s->qt, 2);
+    if (rc) return rc;
+  } else {
+    pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  }
   jvp(s, v, s->qt, 1.0 / dt, Jv, nullptr);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(s->st));
@@ -1471,7 +1516,12 @@ int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v
 
 int pfc_precond_apply(pfc_state* s, const double* Phi, const double* phin, double dt, const double* r, double* z) {
   if (!s || !Phi || !phin || !r || !z || !(dt > 0.0)) return PFC_EINVAL;
-  pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  if (s->p.mobility) {  // q, mu and s of (Phi, phi^n) from the residual (F into scratch)
+    int rc = eval_residual(s, Phi, nullptr, 0.0, false, phin, 1.0 / dt, s->Ft, nullptr, s->qt, 2);
+    if (rc) return rc;
+  } else {
+    pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
+  }
   s->factors_ok = false;  // the factors below belong to this call's arguments, not to a step
   int rc = factor_blocks(s, s->qt, 1.0 / dt);
   if (rc) return rc;

@@ -57,6 +57,8 @@ struct IterArgs {
   const double* scale;  // &scale[j]
   const double* q;      // Jacobian coefficient of this Newton iteration
   double idt;           // 1 / dt
+  const double* mu;     // variable mobility: mu and the midpoint s = (Phi + phi^n)/2 of this
+  const double* sm;     // Newton iteration (null with M = 1)
 };
 
 // Scalars the host reads back after a reduction.
@@ -79,11 +81,15 @@ void count_launches(long long n);
 long long launches_so_far();
 
 // ---- stencil kernels (stencil2d.cu)
+// mob: variable mobility M = 1 - s^2 at the midpoint s = (Phi + phi^n)/2 (Eq. NSOP's M_d); the
+// residual then also writes mu and s beside q (mu_out, s_out), and the JVP reads them (mu, sm).
 void launch_residual2d(const Geo& g, const double* Phi_base, const double* S, double lam, const double* smean,
                        const double* phin, double idt, double* F, double* Phi_out, double* q_out, double* partial,
-                       int* nparts, cudaStream_t st);
+                       int* nparts, cudaStream_t st, bool mob = false, double* mu_out = nullptr,
+                       double* s_out = nullptr);
 void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  const int* skip, cudaStream_t st, const IterArgs* ia = nullptr);
+                  const int* skip, cudaStream_t st, const IterArgs* ia = nullptr, const double* mu = nullptr,
+                  const double* sm = nullptr);
 void launch_energy2d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
 // The same JVP in float-float arithmetic on the FP32 pipe (jvp_ff.cu), for the mixed path.
 void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
@@ -120,6 +126,11 @@ struct FactorStore {
   // parts point by point; PFC_RIGHT_RAS also restricts r to the core (R_k^0).
   int ras_kind;
   double* Yb;
+  // variable mobility: mu and s = (Phi + phi^n)/2 at the factored iterate (null: M = 1), and the
+  // largest (bx + 2)(by + 2) of a block with its one-cell ring
+  const double* mob_mu;
+  const double* mob_s;
+  int ext_max;
 };
 // Axis splits of the 2D decomposition (the first n mod p cores one cell larger).
 struct Decomp2 {
@@ -171,7 +182,7 @@ void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
                         const IterArgs* ia = nullptr, const Decomp2* dc = nullptr);
-size_t factor_smem_bytes(int prec, int kl, int n_max);
+size_t factor_smem_bytes(int prec, int kl, int n_max, int ext_max = 0);
 // Whether apply variant v runs blocks of half-bandwidth kl_max at precision prec
 // (xstage: bytes of the largest chunk record, n_max: rows of the largest block).
 bool apply_variant_ok(int v, int prec, int kl_max, int xstage, int n_max);

@@ -123,6 +123,44 @@ __device__ __forceinline__ double jac_entry(int bx, double ih2, const double* qb
   return v;
 }
 
+// Entry (r, c) of A_k with variable mobility (the principal submatrix of J of the mobility
+// form): J = I/dt - D_M K - B, K = (1/2) L_gamma + diag q, D_M = (div M grad)_d with M = 1 - s^2
+// averaged onto edges, B = (div (-s v) grad)_d mu (derivative of M_d).  Row r collects, over
+// the 4 edges (r, nb): M_e (K(nb, c) - K(r, c)) for D_M K, and the two ends' dM terms for B.
+// sx, mx: s and mu on the block plus a one-cell ring ((bx+2) x (by+2), x fastest); l13: the 5 x 5
+// table of (1/2) L_gamma (offset (dx, dy) at (dy+2)*5 + dx+2).
+__device__ __forceinline__ double jac_entry_mob(int bx, int by, double ih2, const double* qb, double idt,
+                                                const double* l13, const double* sx, const double* mx, int r,
+                                                int c) {
+  const int ar = r % bx, br = r / bx, ac = c % bx, bc = c / bx;
+  const int dx = ac - ar, dy = bc - br;
+  if (abs(dx) + abs(dy) > 3) return 0.0;
+  const int ex = bx + 2;
+  auto ext = [&](int a, int b) { return (b + 1) * ex + (a + 1); };
+  auto K = [&](int a, int b) -> double {  // K(node (a, b), c): (1/2) L_gamma offset + q on the diagonal
+    const int ox = ac - a, oy = bc - b;
+    if (abs(ox) + abs(oy) > 2) return 0.0;
+    double v = l13[(oy + 2) * 5 + (ox + 2)];
+    if (ox == 0 && oy == 0) v += qb[c];
+    return v;
+  };
+  const double sr = sx[ext(ar, br)], mur = mx[ext(ar, br)];
+  const double Mr = 1.0 - sr * sr, Kr = K(ar, br);
+  const int nbx[4] = {-1, 1, 0, 0}, nby[4] = {0, 0, -1, 1};
+  double dmk = 0.0, bdiag = 0.0, boff = 0.0;
+  for (int e = 0; e < 4; ++e) {
+    const int na = ar + nbx[e], nb = br + nby[e];
+    const double sn = sx[ext(na, nb)], mun = mx[ext(na, nb)];
+    const double Me = 0.5 * (Mr + (1.0 - sn * sn));
+    dmk += Me * (K(na, nb) - Kr);
+    bdiag += mun - mur;
+    if (na == ac && nb == bc) boff += sn * (mun - mur);
+  }
+  double v = -ih2 * dmk + 0.5 * ih2 * boff;
+  if (dx == 0 && dy == 0) v += idt + 0.5 * ih2 * sr * bdiag;
+  return v;
+}
+
 template <typename TC, typename TS, int RING>
 __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
                                                   const double* __restrict__ q, double idt,
@@ -156,14 +194,40 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
   const double ih2 = g.ih2;
   const float inv_bx = 1.0f / (float)bx;
 
+  // variable mobility: s and mu on the block plus a ring, the (1/2) L_gamma table (after A)
+  const bool mob = fs.mob_mu != nullptr;
+  double* sx = reinterpret_cast<double*>(
+      smem + rup((size_t)(reinterpret_cast<unsigned char*>(A + (size_t)W * RS) - smem), 16));
+  double* mx = sx + fs.ext_max;
+  double* l13 = mx + fs.ext_max;
   for (int t = tid; t < n; t += nt)
     qb[t] = q[wrap(B.x0 + t % bx, g.nx) + (long long)g.nx * wrap(B.y0 + t / bx, g.ny)];
   for (int t = tid; t < 49; t += nt) lin_s[t] = lin[t];
   for (int w = tid; w < W; w += nt) slot[w] = w;
+  if (mob) {
+    const int ex = bx + 2, ne = ex * (by + 2);
+    for (int t = tid; t < ne; t += nt) {
+      const long long gi = wrap(B.x0 - 1 + t % ex, g.nx) + (long long)g.nx * wrap(B.y0 - 1 + t / ex, g.ny);
+      sx[t] = fs.mob_s[gi];
+      mx[t] = fs.mob_mu[gi];
+    }
+    if (tid < 25) {  // (1/2) L_gamma = (1/2) [(1 - gamma) + 2 Delta_d + Delta_d^2]
+      const int ox = tid % 5 - 2, oy = tid / 5 - 2, ad = abs(ox) + abs(oy);
+      const double ih4 = ih2 * ih2;
+      double v = 0.0;
+      if (ad == 0) v = 0.5 * ((1.0 - g.gamma) - 8.0 * ih2 + 20.0 * ih4);
+      else if (ad == 1) v = 0.5 * (2.0 * ih2 - 8.0 * ih4);
+      else if (ad == 2) v = (ox != 0 && oy != 0) ? ih4 : 0.5 * ih4;
+      l13[tid] = v;
+    }
+  }
   __syncthreads();
   for (int idx = tid; idx < W * RING; idx += nt) {
     const int pos = idx / RING, col = idx - pos * RING;
-    A[pos * RS + col] = (pos < n && col < n) ? (TC)jac_entry(bx, ih2, qb, idt, lin_s, pos, col) : (TC)0;
+    A[pos * RS + col] = (pos < n && col < n)
+                            ? (TC)(mob ? jac_entry_mob(bx, by, ih2, qb, idt, l13, sx, mx, pos, col)
+                                       : jac_entry(bx, ih2, qb, idt, lin_s, pos, col))
+                            : (TC)0;
   }
   __syncthreads();
 
@@ -264,7 +328,9 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
       for (int t = tid; t < RING; t += nt) {
         const int col = base + ((t - base) & (RING - 1));
         TC v = (TC)0;
-        if (col < n) {
+        if (col < n && mob) {
+          v = (TC)jac_entry_mob(bx, by, ih2, qb, idt, l13, sx, mx, rnew, col);
+        } else if (col < n) {
           if (bx >= 7) {  // col - rnew = dx + bx dy has a unique split with |dx| <= 3
             const int d = col - rnew;
             const int dy = __float2int_rn((float)d * inv_bx);
@@ -1063,7 +1129,7 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
-  if (sizeof(TC) == 4 && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
+  if (sizeof(TC) == 4 && !fs.mob_mu && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
       factor_col_smem_bytes(fs.n_max) <= 227 * 1024) {
     const size_t smem = factor_col_smem_bytes(fs.n_max);
     cudaFuncSetAttribute(k_factor2d_col<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1071,7 +1137,7 @@ void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const d
     count_launches(1);
     return;
   }
-  const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max);
+  const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max, fs.mob_mu ? fs.ext_max : 0);
   if (2 * fs.kl_max + 2 <= 128) {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_factor2d<TC, TS, 128><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status);
@@ -1143,11 +1209,13 @@ void launch_chunk2d(const BlockDesc* blocks, int nblocks, const FactorStore& fs,
 // Dynamic shared memory of the factor kernel: q on the block and the stencil
 // table (FP64), the (kl+1) x (RING+1) window plus the multiplier and U-row
 // buffers (compute type), the position map and the row offsets.
-size_t factor_smem_bytes(int prec, int kl, int n_max) {
+size_t factor_smem_bytes(int prec, int kl, int n_max, int ext_max) {
   const int ring = (2 * kl + 2 <= 128) ? 128 : 256;
   const size_t tc = prec == PFC_F64 ? 8 : 4;
-  return rup((size_t)(n_max + 49) * 8, 16) + (size_t)((kl + 1) * (ring + 1) + 2 * ring) * tc + ring * sizeof(int) +
-         16;
+  size_t b = rup((size_t)(n_max + 49) * 8, 16) + (size_t)((kl + 1) * (ring + 1) + 2 * ring) * tc +
+             ring * sizeof(int) + 16;
+  if (ext_max > 0) b = rup(b, 16) + 16 + (size_t)(2 * ext_max + 25) * 8;  // mobility: s, mu with ring, table
+  return b;
 }
 
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,

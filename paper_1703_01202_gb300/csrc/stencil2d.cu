@@ -35,15 +35,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // F(Phi) = (Phi - phi^n)/dt - Delta_d mu,  mu = L_gamma (Phi+phi^n)/2 + (Phi+phi^n)(Phi^2+phi^n^2)/4.
+// MOB: (div M grad)_d instead of Delta_d, M = 1 - s^2 at the midpoint s = (Phi+phi^n)/2 of each node
+// and the average of its two ends on an edge (Sec. 3); with qout also writes mu and s (muout, sout).
 // Phi = Pb + lam (S - mean S) when S != nullptr (line-search trial point, also written to Pout);
 // smean points at sum(S), or is null when the update is not projected.
 // Writes q = (3 Phi^2 + 2 Phi phi^n + phi^n^2)/4 when qout != nullptr, and the CTA's sum of F^2.
+template <bool MOB>
 __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restrict__ Pb,
                                                    const double* __restrict__ S, double lam,
                                                    const double* __restrict__ smean,
                                                    const double* __restrict__ phin, double idt,
                                                    double* __restrict__ F, double* __restrict__ Pout,
-                                                   double* __restrict__ qout, double* __restrict__ partial) {
+                                                   double* __restrict__ qout, double* __restrict__ partial,
+                                                   double* __restrict__ muout, double* __restrict__ sout) {
   __shared__ double sP[AY][AX], sN[AY][AX], sS[AY][AX];
   __shared__ double sL[AY - 2][AX - 2];
   __shared__ double sM[AY - 4][AX - 4];
@@ -88,13 +92,26 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
     if (gx < g.nx && gy < g.ny) {
       const int a = ty + 1, b = tx + 1;  // index into sM
       const double mu = sM[a][b];
-      const double Lmu = (sM[a][b - 1] + sM[a][b + 1]) + (sM[a - 1][b] + sM[a + 1][b]) - 4.0 * mu;
+      double Lmu;
+      if (MOB) {  // sum over the 4 edges of M_edge (mu_nb - mu), M_edge = (M_c + M_nb)/2, M = 1 - (sS/2)^2
+        const int ly = ty + R, lx = tx + R;
+        auto mob = [&](int y, int x) { const double h = 0.5 * sS[y][x]; return 1.0 - h * h; };
+        const double mc = mob(ly, lx);
+        Lmu = 0.5 * ((mc + mob(ly, lx - 1)) * (sM[a][b - 1] - mu) + (mc + mob(ly, lx + 1)) * (sM[a][b + 1] - mu)) +
+              0.5 * ((mc + mob(ly - 1, lx)) * (sM[a - 1][b] - mu) + (mc + mob(ly + 1, lx)) * (sM[a + 1][b] - mu));
+      } else {
+        Lmu = (sM[a][b - 1] + sM[a][b + 1]) + (sM[a - 1][b] + sM[a + 1][b]) - 4.0 * mu;
+      }
       const double p = sP[ty + R][tx + R], nn = sN[ty + R][tx + R];
       const double f = fma(-ih2, Lmu, (p - nn) * idt);
       const long long idx = gx + (long long)g.nx * gy;
       F[idx] = f;
       if (Pout) Pout[idx] = p;
       if (qout) qout[idx] = 0.25 * fma(3.0 * p, p, nn * fma(2.0, p, nn));
+      if (MOB && qout) {
+        muout[idx] = mu;
+        sout[idx] = 0.5 * sS[ty + R][tx + R];
+      }
       acc = fma(f, f, acc);
     }
   }
@@ -103,21 +120,28 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
 }
 
 // J v = v/dt - Delta_d w,  w = L_gamma v / 2 + q v (Eq. Jacobi).
+// J v = v/dt - Delta_d w, w = L_gamma v/2 + q v (Eq. Jacobi).  MOB: J v = v/dt - (div M grad)_d w
+// - (div dM grad)_d mu with M = 1 - s^2 and dM = -s v at the nodes, both averaged onto the edges.
+template <bool MOB>
 __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ v,
                                               const double* __restrict__ vscale, const double* __restrict__ q,
                                               double idt, double* __restrict__ Jv, const int* __restrict__ skip,
-                                              const IterArgs* __restrict__ ia) {
+                                              const IterArgs* __restrict__ ia, const double* __restrict__ mug,
+                                              const double* __restrict__ smg) {
   if (skip && *skip) return;
   if (ia) {  // graph mode: J Z_j into V_(j+1)
     v = ia->z;
     q = ia->q;
     idt = ia->idt;
     Jv = ia->w;
+    mug = ia->mu;
+    smg = ia->sm;
   }
   __shared__ double sV[AY][AX];
   __shared__ double sQ[AY - 4][AX - 4];
   __shared__ double sL[AY - 2][AX - 2];
   __shared__ double sW[AY - 4][AX - 4];
+  __shared__ double sMu[MOB ? AY - 4 : 1][MOB ? AX - 4 : 1], sSm[MOB ? AY - 4 : 1][MOB ? AX - 4 : 1];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int tid = threadIdx.x + threadIdx.y * 32;
   const double sc = vscale ? *vscale : 1.0;
@@ -130,6 +154,10 @@ __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ 
     const int ly = i / (AX - 4), lx = i - ly * (AX - 4);
     const long long idx = wrap(x0 + lx - 1, g.nx) + (long long)g.nx * wrap(y0 + ly - 1, g.ny);
     sQ[ly][lx] = q[idx];
+    if (MOB) {
+      sMu[ly][lx] = mug[idx];
+      sSm[ly][lx] = smg[idx];
+    }
   }
   __syncthreads();
   for (int i = tid; i < (AX - 2) * (AY - 2); i += NT) {
@@ -154,7 +182,18 @@ __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ 
     if (gx < g.nx && gy < g.ny) {
       const int a = ty + 1, b = tx + 1;
       const double w = sW[a][b];
-      const double Lw = (sW[a][b - 1] + sW[a][b + 1]) + (sW[a - 1][b] + sW[a + 1][b]) - 4.0 * w;
+      double Lw;
+      if (MOB) {  // edge (c, nb): M_e (w_nb - w_c) + dM_e (mu_nb - mu_c), averages of the two ends
+        const int ly = ty + R, lx = tx + R;
+        const double sc = sSm[a][b], mc = 1.0 - sc * sc, dc = -sc * sV[ly][lx], muc = sMu[a][b];
+        auto edge = [&](int ya, int xb, int vy, int vx) {
+          const double sn = sSm[ya][xb];
+          return 0.5 * ((mc + (1.0 - sn * sn)) * (sW[ya][xb] - w) + (dc - sn * sV[vy][vx]) * (sMu[ya][xb] - muc));
+        };
+        Lw = (edge(a, b - 1, ly, lx - 1) + edge(a, b + 1, ly, lx + 1)) + (edge(a - 1, b, ly - 1, lx) + edge(a + 1, b, ly + 1, lx));
+      } else {
+        Lw = (sW[a][b - 1] + sW[a][b + 1]) + (sW[a - 1][b] + sW[a + 1][b]) - 4.0 * w;
+      }
       Jv[gx + (long long)g.nx * gy] = fma(-ih2, Lw, sV[ty + R][tx + R] * idt);
     }
   }
@@ -200,17 +239,25 @@ __global__ void k_qcoef(long long n, const double* __restrict__ P, const double*
 
 void launch_residual2d(const Geo& g, const double* Pb, const double* S, double lam, const double* smean,
                        const double* phin, double idt, double* F, double* Pout, double* qout, double* partial,
-                       int* nparts, cudaStream_t st) {
+                       int* nparts, cudaStream_t st, bool mob, double* mu_out, double* s_out) {
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-  k_residual2d<<<grid, dim3(32, 8), 0, st>>>(g, Pb, S, lam, smean, phin, idt, F, Pout, qout, partial);
+  if (mob)
+    k_residual2d<true><<<grid, dim3(32, 8), 0, st>>>(g, Pb, S, lam, smean, phin, idt, F, Pout, qout, partial,
+                                                      mu_out, s_out);
+  else
+    k_residual2d<false><<<grid, dim3(32, 8), 0, st>>>(g, Pb, S, lam, smean, phin, idt, F, Pout, qout, partial,
+                                                       nullptr, nullptr);
   count_launches(1);
   *nparts = grid.x * grid.y;
 }
 
 void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  const int* skip, cudaStream_t st, const IterArgs* ia) {
+                  const int* skip, cudaStream_t st, const IterArgs* ia, const double* mu, const double* sm) {
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-  k_jvp2d<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia);
+  if (mu)
+    k_jvp2d<true><<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia, mu, sm);
+  else
+    k_jvp2d<false><<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia, nullptr, nullptr);
   count_launches(1);
 }
 

@@ -38,7 +38,7 @@ class pfc_params(ctypes.Structure):
         ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
         ("apply_variant", c_int), ("dt_halvings", c_int), ("gmres_reorth_eta", c_double),
-        ("use_graph", c_int), ("reuse_factor", c_int),
+        ("use_graph", c_int), ("reuse_factor", c_int), ("mobility", c_int),
     ]
 
 
