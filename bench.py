@@ -400,6 +400,35 @@ def precond_sweep(args):
                       "steps": args.steps, "warmup": args.warmup}))
 
 
+def run_mobility(steps: int, warmup: int, prec: int = 2):
+    """The 1024^2 workload with variable mobility M = 1 - phi^2 (the paper's Test B (c)); phi^n
+    guess, GMRES cycles as graphs, FP64 JVP (the mobility form's)."""
+    import torch
+
+    from paper_1703_01202_gb300 import inputs, pfc
+
+    w = inputs.workload(WORKLOAD)
+    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
+                                dt_max=w["dt_max"], eta=w["eta"], mobility=1)
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
+    s.set_field(w["phi"])
+    s.run(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    infos = s.run(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    return {"steps": steps, "steps_per_s": steps / (ms / 1e3),
+            "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
+            "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
+            "dt_last": infos[-1]["dt"], "energy_last": infos[-1]["energy"],
+            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec], "mobility": "1 - phi^2"}
+
+
 def kernel_loop(args):
     """Runs one kernel family `steps` times on the workload's initial field
     (each pfc_precond_apply factors and applies once), for ncu captures."""
@@ -527,6 +556,7 @@ def main():
         # (pfc_run_batch) and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
         line["workloads"] = {
             "batch32x256_bf16": run_batch32(max(2, args.steps // 2), 2),
+            "hex1024_mobility_bf16": run_mobility(max(4, args.steps // 4), 3),
             "bcc256_f32": run_bcc256(EXTRA_3D_STEPS, 1, 1),
             "bcc256_bf16": run_bcc256(EXTRA_3D_STEPS, 1, 2),
         }
