@@ -400,16 +400,25 @@ def precond_sweep(args):
                       "steps": args.steps, "warmup": args.warmup}))
 
 
-def run_mobility(steps: int, warmup: int, prec: int = 2):
+def guarded(fn, *a):
+    """An extra workload's record, or the error that stopped it (the bench line still prints)."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported in the line, not hidden
+        return {"failed": f"{type(e).__name__}: {e}"}
+
+
+def run_mobility(steps: int, warmup: int, prec: int = 1):
     """The 1024^2 workload with variable mobility M = 1 - phi^2 (the paper's Test B (c)); phi^n
-    guess, GMRES cycles as graphs, FP64 JVP (the mobility form's)."""
+    guess, GMRES cycles as graphs, FP64 JVP (the mobility form's).  F32 factors: the mobility
+    blocks are worse conditioned at dt = 10, and BF16 factors let GMRES(30) stall there."""
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
 
     w = inputs.workload(WORKLOAD)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], mobility=1)
+                                dt_max=w["dt_max"], eta=w["eta"], mobility=1, dt_halvings=6)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
     s.set_field(w["phi"])
     s.run(warmup)
@@ -555,10 +564,10 @@ def main():
         # the other workloads of the metric, each on this rank's GPU: the 32-run 256^2 ensemble
         # (pfc_run_batch) and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
         line["workloads"] = {
-            "batch32x256_bf16": run_batch32(max(2, args.steps // 2), 2),
-            "hex1024_mobility_bf16": run_mobility(max(4, args.steps // 4), 3),
-            "bcc256_f32": run_bcc256(EXTRA_3D_STEPS, 1, 1),
-            "bcc256_bf16": run_bcc256(EXTRA_3D_STEPS, 1, 2),
+            "batch32x256_bf16": guarded(run_batch32, max(2, args.steps // 2), 2),
+            "hex1024_mobility_f32": guarded(run_mobility, max(4, args.steps // 4), 3),
+            "bcc256_f32": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 1),
+            "bcc256_bf16": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 2),
         }
     if rank == 0 and not args.no_cpu_baseline:
         f64 = variants.get("f64")
