@@ -11,7 +11,8 @@ Conventions
 * Fields are numpy float64 arrays of shape ``(Ny, Nx)`` (2D) or ``(Nz, Ny, Nx)``
   (3D); the last axis is x, so a C-order flatten gives ``idx = i + Nx*(j + Ny*k)``.
 * Cell-centred periodic grid with isotropic spacing ``h`` (Sec. 3, grid
-  definition x_i = (i - 1/2) dx).
+  definition x_i = (i - 1/2) dx); with ``neumann`` the grid is closed by
+  Neumann-type walls (Sec. 2), as mirrors half a cell outside the end cells.
 * ``gamma`` is the quench depth of Eq. (GE); mobility M = 1 (Sec. 5, tests A, B, D).
 
 Every function cites the section / equation it follows.  Places where the paper
@@ -81,8 +82,12 @@ def local_energy(phi: np.ndarray, h: float, gamma: float) -> np.ndarray:
     return g
 
 
-def energy(phi: np.ndarray, h: float, gamma: float) -> float:
-    """Discrete free energy F_d = h^d * sum G_d (Eq. freeenergy)."""
+def energy(phi: np.ndarray, h: float, gamma: float, neumann: bool = False) -> float:
+    """Discrete free energy F_d = h^d * sum G_d (Eq. freeenergy); with `neumann`,
+    G_d of the evenly extended field (mirror ghosts), summed over the grid."""
+    if neumann:
+        g = restrict_to_grid(local_energy(even_extension(phi), h, gamma), phi.shape)
+        return float(np.sum(g) * h ** phi.ndim)
     return float(np.sum(local_energy(phi, h, gamma)) * h ** phi.ndim)
 
 
@@ -101,6 +106,22 @@ def mu_dvd(Phi: np.ndarray, phin: np.ndarray, h: float, gamma: float) -> np.ndar
     L_gamma (Phi + phi^n)/2 + (Phi^3 + Phi^2 phi^n + Phi phi^n^2 + phi^n^3)/4."""
     cubic = (Phi**3 + Phi**2 * phin + Phi * phin**2 + phin**3) / 4.0
     return L_gamma(0.5 * (Phi + phin), h, gamma) + cubic
+
+
+# Neumann-type boundaries (Sec. 2: n . grad phi = n . grad Delta phi = n . grad Delta^2 phi = 0).
+# READING: on the cell-centred grid the walls are mirrors halfway between a cell and its ghost
+# (ghost phi_0 = phi_1, phi_-1 = phi_2, ...).  The field extended evenly across every wall is
+# periodic on the doubled grid and stays even under every operator of the scheme, so each
+# Neumann operator is the periodic one on the doubled grid, restricted back to the grid.
+def even_extension(u: np.ndarray) -> np.ndarray:
+    """u mirrored across the far wall of every axis: a periodic field on the doubled grid."""
+    for ax in range(u.ndim):
+        u = np.concatenate([u, np.flip(u, axis=ax)], axis=ax)
+    return u
+
+
+def restrict_to_grid(u2: np.ndarray, shape: Tuple[int, ...]) -> np.ndarray:
+    return u2[tuple(slice(0, n) for n in shape)]
 
 
 def mobility_nodes(Phi: np.ndarray, phin: np.ndarray) -> np.ndarray:
@@ -123,12 +144,16 @@ def div_m_grad(u: np.ndarray, Mn: np.ndarray, h: float) -> np.ndarray:
 
 
 def residual(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
-             mobility: bool = False) -> np.ndarray:
+             mobility: bool = False, neumann: bool = False) -> np.ndarray:
     """Nonlinear residual of the semi-implicit scheme Eq. (NSOP):
     F(Phi) = (Phi - phi^n)/dt - (div M_d grad)_d mu(Phi, phi^n), with M = 1
     (Delta_d) or, when `mobility`, M(phi) = 1 - phi^2 evaluated at (Phi + phi^n)/2.
     READING: sign and 1/dt scaling follow the commented-out form F = (Phi -
-    Phi^n)/dt + E(Phi, Phi^n) printed before Eq. (NLS)."""
+    Phi^n)/dt + E(Phi, Phi^n) printed before Eq. (NLS).  `neumann`: the walls'
+    mirror images (see even_extension)."""
+    if neumann:
+        return restrict_to_grid(residual(even_extension(Phi), even_extension(phin), dt, h, gamma, mobility),
+                                Phi.shape)
     mu = mu_dvd(Phi, phin, h, gamma)
     if mobility:
         return (Phi - phin) / dt - div_m_grad(mu, mobility_nodes(Phi, phin), h)
@@ -141,11 +166,14 @@ def jac_coeff(Phi: np.ndarray, phin: np.ndarray) -> np.ndarray:
 
 
 def jvp(v: np.ndarray, Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
-        mobility: bool = False) -> np.ndarray:
+        mobility: bool = False, neumann: bool = False) -> np.ndarray:
     """Jacobian-vector product of Eq. (Jacobi): J v = v/dt - Delta_d(1/2 L_gamma v + q v).
     With `mobility` (M = 1 - phi^2 at the midpoint s = (Phi + phi^n)/2) the derivative
     of F also differentiates M_d: dM/dPhi = -2 s * 1/2 = -s, so
     J v = v/dt - (div M grad)_d(1/2 L_gamma v + q v) - (div (-s v) grad)_d mu."""
+    if neumann:
+        return restrict_to_grid(jvp(even_extension(v), even_extension(Phi), even_extension(phin), dt, h, gamma,
+                                    mobility), v.shape)
     q = jac_coeff(Phi, phin)
     w = 0.5 * L_gamma(v, h, gamma) + q * v
     if not mobility:
@@ -181,11 +209,24 @@ def _shift_matrix(shape: Tuple[int, ...], ax: int) -> sp.csr_matrix:
 
 
 def assemble_jacobian(Phi: np.ndarray, phin: np.ndarray, dt: float, h: float, gamma: float,
-                      mobility: bool = False) -> sp.csr_matrix:
+                      mobility: bool = False, neumann: bool = False) -> sp.csr_matrix:
     """Assembled Jacobian J = I/dt - Delta_d (1/2 L_gamma + diag q) as CSR
     (Eq. Jacobi; L_gamma from Eq. discretedG).  With `mobility`, Delta_d becomes
     D_M = sum_ax (I - S^T) diag(M_edge) (S - I)/h^2 and the term of dM/dPhi is
-    added: B = sum_ax (I - S^T) diag((S - I) mu / h^2) (I + S)/2 diag(-s)."""
+    added: B = sum_ax (I - S^T) diag((S - I) mu / h^2) (I + S)/2 diag(-s).
+    `neumann`: R J2 E with J2 the periodic Jacobian of the evenly extended fields on the doubled
+    grid, E the even extension (grid -> doubled grid) and R the restriction."""
+    if neumann:
+        shape = Phi.shape
+        n = Phi.size
+        src = even_extension(np.arange(n).reshape(shape)).ravel()
+        E = sp.csr_matrix((np.ones(src.size), (np.arange(src.size), src)), shape=(src.size, n))
+        J2 = assemble_jacobian(even_extension(Phi), even_extension(phin), dt, h, gamma, mobility)
+        rows = np.ravel_multi_index(np.indices(shape).reshape(len(shape), -1), tuple(2 * m for m in shape))
+        Rsel = sp.csr_matrix((np.ones(n), (np.arange(n), rows)), shape=(n, J2.shape[0]))
+        J = (Rsel @ J2 @ E).tocsr()
+        J.sum_duplicates()
+        return J
     shape = Phi.shape
     n = Phi.size
     lapm = _lap_matrix(shape, h)
@@ -237,37 +278,44 @@ class Block:
     core_n: Tuple[int, ...]  # per-axis core size
     overlap: int
     shape: Tuple[int, ...]  # global grid shape
+    neumann: bool = False  # walls instead of periodic wrap: the block is clipped to the grid
     block_idx: np.ndarray = field(default=None)  # global flat indices of Omega_k^delta (block C-order)
     core_mask: np.ndarray = field(default=None)  # True where the block point is in Omega_k
     core_idx: np.ndarray = field(default=None)  # global flat indices of Omega_k (block order)
 
     def __post_init__(self):
         axes = []
+        masks = []
         for lo, n, N in zip(self.core_lo, self.core_n, self.shape):
             if n + 2 * self.overlap > N:
                 raise ValueError("block wider than the periodic grid")
-            axes.append(np.arange(lo - self.overlap, lo + n + self.overlap) % N)
+            if self.neumann:  # READING: at a wall the overlapped block stops at the wall
+                a0, a1 = max(0, lo - self.overlap), min(N, lo + n + self.overlap)
+                axes.append(np.arange(a0, a1))
+                m = np.zeros(a1 - a0, dtype=bool)
+                m[lo - a0 : lo - a0 + n] = True
+            else:
+                axes.append(np.arange(lo - self.overlap, lo + n + self.overlap) % N)
+                m = np.zeros(n + 2 * self.overlap, dtype=bool)
+                m[self.overlap : self.overlap + n] = True
+            masks.append(m)
         grids = np.meshgrid(*axes, indexing="ij")
         self.block_idx = np.ravel_multi_index(tuple(g.ravel() for g in grids), self.shape)
-        masks = []
-        for n in self.core_n:
-            m = np.zeros(n + 2 * self.overlap, dtype=bool)
-            m[self.overlap : self.overlap + n] = True
-            masks.append(m)
         mg = np.meshgrid(*masks, indexing="ij")
         self.core_mask = np.logical_and.reduce([m.ravel() for m in mg])
         self.core_idx = self.block_idx[self.core_mask]
 
 
-def decompose(shape: Tuple[int, ...], parts: Tuple[int, ...], overlap: int) -> List[Block]:
+def decompose(shape: Tuple[int, ...], parts: Tuple[int, ...], overlap: int, neumann: bool = False) -> List[Block]:
     """Non-overlapping cores Omega_k extended by `overlap` cells per side with
-    periodic wrap (Sec. 4).  `parts` is given in array-axis order."""
+    periodic wrap (Sec. 4), or clipped at the walls with Neumann-type boundaries.
+    `parts` is given in array-axis order."""
     splits = [split_axis(N, p) for N, p in zip(shape, parts)]
     blocks = []
     for combo in np.ndindex(*parts):
         lo = tuple(splits[a][combo[a]][0] for a in range(len(shape)))
         n = tuple(splits[a][combo[a]][1] for a in range(len(shape)))
-        blocks.append(Block(lo, n, overlap, tuple(shape)))
+        blocks.append(Block(lo, n, overlap, tuple(shape), neumann))
     return blocks
 
 
@@ -538,6 +586,7 @@ class Params:
     energy_scaled: bool = True  # READING: controller uses F_d / |Omega|
     dt_halvings: int = 0  # READING: a step whose Newton iteration fails is retried with dt / 2
     mobility: bool = False  # M(phi) = 1 - phi^2 (Eq. NSOP's M_d); False: M = 1
+    neumann: bool = False  # Neumann-type walls (Sec. 2) instead of the periodic grid
 
 
 @dataclass
@@ -568,7 +617,7 @@ def newton_solve(
     backtracking lam <- clamp(lam^2 f0 / (f(lam) - f0 + 2 lam f0) ... ) to
     [0.1 lam, 0.5 lam]; optional projection of S to zero mean (mass)."""
     Phi = (phin if guess is None else guess).copy()
-    F = residual(Phi, phin, dt, h, gamma, p.mobility)
+    F = residual(Phi, phin, dt, h, gamma, p.mobility, p.neumann)
     r0 = float(np.linalg.norm(F))
     target = max(p.newton_rtol * (r0 if ref_norm is None else ref_norm), p.newton_atol)
     rnorm = r0
@@ -577,9 +626,9 @@ def newton_solve(
     lambdas: List[float] = []
     pre = None
     while rnorm > target and m < p.newton_max_it:
-        J = assemble_jacobian(Phi, phin, dt, h, gamma, p.mobility)
+        J = assemble_jacobian(Phi, phin, dt, h, gamma, p.mobility, p.neumann)
         if p.precond and pre is None:
-            pre = Schwarz(J, decompose(Phi.shape, p.parts, p.overlap), p.ras_kind, p.subdomain_solver,
+            pre = Schwarz(J, decompose(Phi.shape, p.parts, p.overlap, p.neumann), p.ras_kind, p.subdomain_solver,
                           p.ilu_shift)
         precond = (lambda v: pre.apply(v)) if p.precond else (lambda v: v)
         matvec = lambda v: (J @ v.ravel()).reshape(v.shape)
@@ -594,7 +643,7 @@ def newton_solve(
         lam = 1.0
         for cut in range(p.ls_max_cuts + 1):
             trial = Phi + lam * S
-            Ft = residual(trial, phin, dt, h, gamma, p.mobility)
+            Ft = residual(trial, phin, dt, h, gamma, p.mobility, p.neumann)
             ft = 0.5 * float(np.dot(Ft.ravel(), Ft.ravel()))
             if ft <= (1.0 - 2.0 * p.ls_alpha * lam) * f0 or cut == p.ls_max_cuts:
                 break
@@ -643,8 +692,8 @@ def _step_with_guess(phin, phinm1, dt, dt_prev, h, gamma, p, guess):
         # is not larger than that of phi^n, the paper's own starting point (Sec. 4);
         # after a step-size jump dt/dt_prev is large and the extrapolation poor.
         g = extrapolated_guess(phin, phinm1, dt, dt_prev)
-        ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma, p.mobility)))
-        if ref < np.linalg.norm(residual(g, phin, dt, h, gamma, p.mobility)):
+        ref = float(np.linalg.norm(residual(phin, phin, dt, h, gamma, p.mobility, p.neumann)))
+        if ref < np.linalg.norm(residual(g, phin, dt, h, gamma, p.mobility, p.neumann)):
             g = None
         return newton_solve(phin, dt, h, gamma, p, g, ref_norm=ref)
     return newton_solve(phin, dt, h, gamma, p, None)
@@ -665,7 +714,7 @@ def run(
     scale = 1.0 / area if p.energy_scaled else 1.0
     phin = phi0.copy()
     phinm1 = phi0.copy()
-    E_n = energy(phin, h, gamma)
+    E_n = energy(phin, h, gamma, p.neumann)
     E_nm1 = None
     dt_prev = None
     t = 0.0
@@ -685,7 +734,7 @@ def run(
         if not info.converged:
             raise RuntimeError(f"Newton did not converge at step {n}")
         phinm1, phin = phin, phi1
-        E_nm1, E_n = E_n, energy(phin, h, gamma)
+        E_nm1, E_n = E_n, energy(phin, h, gamma, p.neumann)
         dt_prev = dt
         t += dt
         recs.append(RunRecord(t, dt, E_n, mass(phin, h), info.newton_its, info.gmres_its))

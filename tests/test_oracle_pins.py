@@ -497,3 +497,203 @@ def test_mobility_steps_conserve_mass_and_decrease_energy():
         assert e1 <= e0 + 1e-13 * abs(e0)
         assert abs(O.mass(phi, H2) - m0) <= 1e-12 * max(1.0, abs(m0))
         e0 = e1
+
+
+# ---------------------------------------------------------------- Neumann-type walls (Sec. 2)
+def neumann_lap_matrix(shape, h):
+    """Textbook cell-centred Neumann Laplacian, built by hand: per axis the tridiagonal
+    (1, -2, 1)/h^2 with the ghost folded into the end rows (-1 instead of -2), then the
+    Kronecker sum over the axes.  Independent of the oracle's even-extension route."""
+    mats = []
+    for n in shape:
+        T = np.diag(np.full(n, -2.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+        T[0, 0] = T[-1, -1] = -1.0
+        mats.append(T / (h * h))
+    out = np.zeros((int(np.prod(shape)),) * 2)
+    for ax, T in enumerate(mats):
+        left = np.eye(int(np.prod(shape[:ax])))
+        right = np.eye(int(np.prod(shape[ax + 1:])))
+        out += np.kron(np.kron(left, T), right)
+    return out
+
+
+def neumann_parts(shape, h):
+    Lap = neumann_lap_matrix(shape, h)
+    Lg = (1 - GAMMA) * np.eye(Lap.shape[0]) + 2 * Lap + Lap @ Lap
+    return Lap, Lg
+
+
+def neumann_residual_by_hand(Phi, phin, dt, h):
+    Lap, Lg = neumann_parts(Phi.shape, h)
+    P, q = Phi.ravel(), phin.ravel()
+    mu = 0.5 * Lg @ (P + q) + (P**3 + P * P * q + P * q * q + q**3) / 4
+    return ((P - q) / dt - Lap @ mu).reshape(Phi.shape), mu.reshape(Phi.shape)
+
+
+def neumann_mode(shape, ks, h):
+    """prod_a cos(pi k_a x_a / L_a) on the cell centres: the half-wave cosines that satisfy
+    the mirror condition at both walls."""
+    out = 1.0
+    for c, k, n in zip(inputs.cell_centres(shape, h), ks, shape):
+        out = out * np.cos(math.pi * k * c / (n * h))
+    return out
+
+
+def neumann_kappa(ks, ns, h):
+    return sum(4.0 / h**2 * math.sin(math.pi * k / (2 * n)) ** 2 for k, n in zip(ks, ns))
+
+
+@pytest.mark.parametrize("shape", [(9, 12), (5, 6, 7)])
+def test_neumann_operators_match_the_ghost_folded_matrices(shape):
+    """Residual, J v and the assembled Jacobian with mirror walls against the hand-built
+    Neumann matrices: F = (Phi - phi^n)/dt - Lap_N mu, J = I/dt - Lap_N (1/2 L_N + diag q)."""
+    h = 0.8
+    Phi, phin, v = rand_field(shape, 31), rand_field(shape, 32), rand_field(shape, 33, 0.0, 1.0)
+    dt = 0.6
+    F_ref, _ = neumann_residual_by_hand(Phi, phin, dt, h)
+    F = O.residual(Phi, phin, dt, h, GAMMA, neumann=True)
+    np.testing.assert_allclose(F, F_ref, rtol=0, atol=1e-12 * np.abs(F_ref).max())
+    Lap, Lg = neumann_parts(shape, h)
+    q = O.jac_coeff(Phi, phin).ravel()
+    J_ref = np.eye(Lap.shape[0]) / dt - Lap @ (0.5 * Lg + np.diag(q))
+    J = O.assemble_jacobian(Phi, phin, dt, h, GAMMA, neumann=True).toarray()
+    np.testing.assert_allclose(J, J_ref, rtol=0, atol=1e-12 * np.abs(J_ref).max())
+    Jv = O.jvp(v, Phi, phin, dt, h, GAMMA, neumann=True)
+    np.testing.assert_allclose(Jv.ravel(), J_ref @ v.ravel(), rtol=0, atol=1e-12 * np.abs(Jv).max())
+    # and they are not the periodic operators
+    assert np.abs(F - O.residual(Phi, phin, dt, h, GAMMA)).max() > 1e-3 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("ks", [(1, 3), (2, 5)])
+def test_neumann_laplacian_half_wave_symbol(ks):
+    """Half-wave cosines are eigenvectors of the mirror-wall Laplacian with eigenvalue
+    -sum 4/h^2 sin^2(pi k/(2N)); odd k is no mode of the periodic grid."""
+    shape = (10, 12)
+    h = 0.7
+    u = neumann_mode(shape, ks, h)
+    lam = neumann_kappa(ks, shape, h)
+    np.testing.assert_allclose((neumann_lap_matrix(shape, h) @ u.ravel()).reshape(shape), -lam * u,
+                               rtol=0, atol=1e-12 * lam)
+    # the oracle's Jacobian at Phi = phi^n = 0 (q = 0) acts as 1/dt + kappa S/2 on the mode
+    S = (1 - GAMMA) - 2 * lam + lam * lam
+    zero = np.zeros(shape)
+    Jv = O.jvp(u, zero, zero, 0.5, h, GAMMA, neumann=True)
+    np.testing.assert_allclose(Jv, (1 / 0.5 + 0.5 * lam * S) * u, rtol=0, atol=1e-11 * (1 + lam**3))
+
+
+@pytest.mark.parametrize("dt", [0.05, 1.0, 20.0])
+def test_neumann_half_wave_crank_nicolson_multiplier(dt):
+    """Small half-wave mode between mirror walls: one NKS step multiplies it by
+    g = (1 - dt kappa S/2)/(1 + dt kappa S/2), kappa the Neumann symbol."""
+    shape = (16, 16)
+    h = 1.1
+    ks = (1, 3)
+    phi0 = 1e-6 * neumann_mode(shape, ks, h)
+    lam = neumann_kappa(ks, shape, h)
+    S = (1 - GAMMA) - 2 * lam + lam * lam
+    g = (1 - 0.5 * dt * lam * S) / (1 + 0.5 * dt * lam * S)
+    p = O.Params(parts=(2, 2), newton_rtol=1e-13, gmres_rtol=1e-12, neumann=True)
+    phi1, info = O.newton_solve(phi0, dt, h, GAMMA, p)
+    np.testing.assert_allclose(phi1, g * phi0, rtol=0, atol=1e-9 * 1e-6)
+
+
+def test_neumann_dvd_identity_and_energy_law():
+    """With mirror walls the DVD identity (Eq. DVD) and the energy balance of a step hold with
+    the sums over interior edges only: F1 - F0 = -dt h^2 sum_interior (D^+ mu)^2 + dt h^2 sum mu F."""
+    shape = (12, 10)
+    h = 0.8
+    p1, p0 = rand_field(shape, 34), rand_field(shape, 35)
+    _, mu = neumann_residual_by_hand(p1, p0, 1.0, h)
+    lhs = O.energy(p1, h, GAMMA, neumann=True) - O.energy(p0, h, GAMMA, neumann=True)
+    assert lhs == pytest.approx(float(np.sum(mu * (p1 - p0))) * h * h, rel=1e-12)
+    # the periodic energy does not satisfy it with the Neumann mu
+    lhs_p = O.energy(p1, h, GAMMA) - O.energy(p0, h, GAMMA)
+    assert abs(lhs_p - lhs) > 1e-6 * abs(lhs)
+    phin = inputs.noise_field((16, 16), 0.07, 0.07, 36)
+    dt = 1.0
+    p = O.Params(parts=(2, 2), newton_rtol=1e-12, neumann=True)
+    phi1, info = O.newton_solve(phin, dt, H2, GAMMA, p)
+    assert info.converged
+    F_by_hand, mu = neumann_residual_by_hand(phi1, phin, dt, H2)
+    diss = sum(float(np.sum(np.diff(mu, axis=ax) ** 2)) / H2**2 for ax in range(2))
+    F0, F1 = O.energy(phin, H2, GAMMA, neumann=True), O.energy(phi1, H2, GAMMA, neumann=True)
+    assert F1 - F0 == pytest.approx(-dt * H2**2 * diss + dt * H2**2 * float(np.sum(mu * F_by_hand)),
+                                    rel=1e-9, abs=1e-12 * abs(F0))
+    assert F1 <= F0
+    assert abs(O.mass(phi1, H2) - O.mass(phin, H2)) <= 1e-12 * max(1.0, abs(O.mass(phin, H2)))
+
+
+def test_neumann_decomposition_clips_blocks_at_the_walls():
+    """Cores partition the grid; overlapped blocks stop at the walls (no wrap), keep the
+    overlap inside; one block is the exact inverse of the Neumann Jacobian."""
+    shape, parts = (13, 10), (3, 2)
+    blocks = O.decompose(shape, parts, 1, neumann=True)
+    hits = np.zeros(int(np.prod(shape)), dtype=int)
+    for b in blocks:
+        hits[b.core_idx] += 1
+        iy, ix = np.unravel_index(b.block_idx, shape)
+        for c, lo, n, N in ((iy, b.core_lo[0], b.core_n[0], shape[0]), (ix, b.core_lo[1], b.core_n[1], shape[1])):
+            assert c.min() == max(0, lo - 1) and c.max() == min(N - 1, lo + n)
+    assert np.all(hits == 1)
+    Phi, phin = rand_field(shape, 37), rand_field(shape, 38)
+    J = O.assemble_jacobian(Phi, phin, 1.0, 0.8, GAMMA, neumann=True)
+    pre = O.Schwarz(J, O.decompose(shape, (1, 1), 0, neumann=True), "left-ras", "lu")
+    b = rand_field(shape, 39, 0.0, 1.0)
+    np.testing.assert_allclose(pre.apply(b).ravel(), np.linalg.solve(J.toarray(), b.ravel()), rtol=1e-10, atol=1e-12)
+
+
+def test_neumann_nks_matches_dense_direct_solve():
+    """NKS step with mirror walls (clipped left-RAS blocks) against Newton with the hand-built
+    Neumann residual and dense Jacobian solved by LAPACK, to 1e-12."""
+    shape = (10, 9)
+    phin = inputs.noise_field(shape, 0.07, 0.07, 40)
+    dt = 0.5
+    p = O.Params(newton_rtol=1e-13, gmres_rtol=1e-8, parts=(2, 3), overlap=1, neumann=True)
+    Phi, info = O.newton_solve(phin, dt, H2, GAMMA, p)
+    Lap, Lg = neumann_parts(shape, H2)
+    ref = phin.copy()
+    for _ in range(50):
+        F, _ = neumann_residual_by_hand(ref, phin, dt, H2)
+        if np.linalg.norm(F) <= 1e-14:
+            break
+        q = O.jac_coeff(ref, phin).ravel()
+        J = np.eye(Lap.shape[0]) / dt - Lap @ (0.5 * Lg + np.diag(q))
+        ref = ref - np.linalg.solve(J, F.ravel()).reshape(shape)
+    assert info.converged and info.newton_its >= 2
+    assert np.abs(Phi - ref).max() <= 1e-12
+
+
+def test_neumann_mobility_is_conservative_and_matches_finite_differences():
+    """M = 1 - phi^2 with mirror walls: sum F dt = mass change (no flux through the walls) and
+    the analytic J v against central differences of F."""
+    shape = (12, 10)
+    Phi, phin = rand_field(shape, 41, 0.2, 0.4), rand_field(shape, 42, 0.2, 0.4)
+    v = rand_field(shape, 43, 0.0, 1.0)
+    dt = 0.7
+    F = O.residual(Phi, phin, dt, H2, GAMMA, mobility=True, neumann=True)
+    assert abs(float(np.sum(F - (Phi - phin) / dt))) <= 1e-12 * float(np.abs(F).sum())
+    Jv = O.jvp(v, Phi, phin, dt, H2, GAMMA, mobility=True, neumann=True)
+    eps = 1e-5 * np.linalg.norm(Phi) / np.linalg.norm(v)
+    fd = (O.residual(Phi + eps * v, phin, dt, H2, GAMMA, mobility=True, neumann=True)
+          - O.residual(Phi - eps * v, phin, dt, H2, GAMMA, mobility=True, neumann=True)) / (2 * eps)
+    assert np.linalg.norm(Jv - fd) <= 1e-8 * np.linalg.norm(Jv)
+    J = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA, mobility=True, neumann=True)
+    np.testing.assert_allclose((J @ v.ravel()).reshape(shape), Jv, rtol=0, atol=1e-12 * np.abs(Jv).max())
+
+
+def test_neumann_pins_catch_a_whole_cell_mirror(monkeypatch):
+    """Mirroring about the wall cells (ghost u_{-1} = u_1) instead of the half-cell walls is a
+    plausible mistake; the hand-built matrices catch it."""
+    shape = (9, 12)
+    Phi, phin = rand_field(shape, 31), rand_field(shape, 32)
+    F_ref, _ = neumann_residual_by_hand(Phi, phin, 0.6, 0.8)
+
+    def whole_cell(u):
+        for ax in range(u.ndim):
+            inner = np.flip(np.take(u, np.arange(1, u.shape[ax] - 1), axis=ax), axis=ax)
+            u = np.concatenate([u, inner], axis=ax)
+        return u
+
+    monkeypatch.setattr(O, "even_extension", whole_cell)
+    F = O.residual(Phi, phin, 0.6, 0.8, GAMMA, neumann=True)
+    assert np.abs(F - F_ref).max() > 1e-3 * np.abs(F_ref).max()
