@@ -50,6 +50,8 @@ typedef enum {
 enum { PFC_F64 = 0, PFC_F32 = 1, PFC_BF16 = 2 };
 /* Schwarz variant (Sec. 4): Eq. invM, Eq. ras, Eq. ash. */
 enum { PFC_AS = 0, PFC_LEFT_RAS = 1, PFC_RIGHT_RAS = 2 };
+/* Domain boundary (pfc_params.boundary). */
+enum { PFC_PERIODIC = 0, PFC_NEUMANN = 1 };
 /* Newton initial guess: phi^n (Sec. 4), linear extrapolation, caller-supplied,
    or the learned network (pfc_set_guess_net).  EXTRAP and LEARNED are
    safeguarded: the residual norm of every candidate (phi^n, the extrapolation,
@@ -125,6 +127,14 @@ typedef struct {
      (Phi + phi^n)/2 and averaged onto edges (Sec. 3), with the Jacobian's
      dM/dPhi term.  2D grids; the JVP then runs in FP64 on every path. */
   int mobility;
+  /* Boundary of the domain: PFC_PERIODIC (0, default) or PFC_NEUMANN (1), the
+     homogeneous Neumann-type conditions of Sec. 2 (n.grad phi = n.grad Delta phi =
+     n.grad Delta^2 phi = 0) as mirror walls half a cell outside the end cells: every
+     stencil reads the mirror image of a cell beyond a wall.  The overlapped
+     subdomains stop at the walls and A_k is the principal submatrix of the Neumann
+     Jacobian (the mirror images folded into the block's own columns).  2D grids of
+     at least 4 x 4 cells, left-RAS, mobility 0; pfc_residual_static stays periodic. */
+  int boundary;
 } pfc_params;
 
 typedef struct {

@@ -17,11 +17,6 @@ constexpr int TX = 32, TY = 16, R = 3;
 constexpr int AX = TX + 2 * R, AY = TY + 2 * R;  // 38 x 22 staged points
 constexpr int NT = 256;                          // 32 x 8 threads, 2 outputs each
 
-__device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
-}
-
 // Unscaled 5-point Laplacian (e + w) + (n + s) - 4 c.
 __device__ __forceinline__ ff ff_lap(ff c, ff e, ff w, ff n, ff s) {
   return ff_add(ff_add(ff_add(e, w), ff_add(n, s)), ff_neg(ff_scale(c, 4.0f)));
@@ -47,12 +42,12 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
   const double sc = vscale ? *vscale : 1.0;
   for (int i = tid; i < AX * AY; i += NT) {
     const int ly = i / AX, lx = i - ly * AX;
-    const long long idx = wrap(x0 + lx - R, g.nx) + (long long)g.nx * wrap(y0 + ly - R, g.ny);
+    const long long idx = cell_index(x0 + lx - R, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - R, g.ny, g.neumann);
     sV[ly][lx] = ff_split(vscale ? sc * v[idx] : v[idx]);
   }
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4), lx = i - ly * (AX - 4);
-    const long long idx = wrap(x0 + lx - 1, g.nx) + (long long)g.nx * wrap(y0 + ly - 1, g.ny);
+    const long long idx = cell_index(x0 + lx - 1, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - 1, g.ny, g.neumann);
     sQ[ly][lx] = ff_split(q[idx]);
   }
   __syncthreads();

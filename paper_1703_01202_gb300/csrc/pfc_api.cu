@@ -160,6 +160,12 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
   if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
   if (p->mobility != 0 && (p->mobility != 1 || g->dim != 2)) return PFC_EINVAL;
+  // Neumann walls: 2D, left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then
+  // never see a second mirror image)
+  if (p->boundary != PFC_PERIODIC &&
+      (p->boundary != PFC_NEUMANN || g->dim != 2 || p->ras_kind != PFC_LEFT_RAS || p->mobility != 0 ||
+       g->n[0] < 4 || g->n[1] < 4))
+    return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
@@ -199,6 +205,15 @@ void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>
         b.cx = sx[bx].size;
         b.cy = sy[by].size;
         b.cz = sz[bz].size;
+        if (p->boundary == PFC_NEUMANN) {  // the overlap stops at the walls: blocks are clipped
+          const int x1 = std::min((int)g->n[0], b.x0 + b.bx), y1 = std::min((int)g->n[1], b.y0 + b.by);
+          b.x0 = std::max(0, b.x0);
+          b.y0 = std::max(0, b.y0);
+          b.bx = x1 - b.x0;
+          b.by = y1 - b.y0;
+          b.ox = sx[bx].start - b.x0;
+          b.oy = sy[by].start - b.y0;
+        }
         out->push_back(b);
         const int n = b.bx * b.by * b.bz;
         const int kl = std::min(3 * b.bx, n - 1);
@@ -997,6 +1012,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->g.ih2 = 1.0 / (h * h);
   s->g.gamma = eps;
   s->g.hd = g->dim == 3 ? h * h * h : h * h;
+  s->g.neumann = p->boundary == PFC_NEUMANN ? 1 : 0;
   char* base = (char*)ws;
   auto at = [&](size_t off) { return (void*)(base + off); };
   s->phin = (double*)at(pl.phin);

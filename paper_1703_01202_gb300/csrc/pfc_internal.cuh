@@ -19,7 +19,21 @@ struct Geo {
   double ih2;       // 1 / h^2
   double gamma;     // quench depth of Eq. (GE)
   double hd;        // h^d (cell volume)
+  int neumann;      // 0: periodic grid; 1: mirror walls half a cell outside the end cells (Sec. 2)
 };
+
+// Cell that index i (any integer) of an axis of n cells reads: the periodic image, or, between
+// mirror walls, the image in the evenly extended grid of period 2n (ghost -1 -> 0, n -> n - 1).
+__device__ __forceinline__ int cell_index(int i, int n, int neumann) {
+  if (!neumann) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  const int p = 2 * n;
+  i %= p;
+  if (i < 0) i += p;
+  return i < n ? i : p - 1 - i;
+}
 
 // One overlapped subdomain Omega_k^delta and its core Omega_k (Sec. 4).
 struct BlockDesc {

@@ -161,6 +161,30 @@ __device__ __forceinline__ double jac_entry_mob(int bx, int by, double ih2, cons
   return v;
 }
 
+// Entry (r, c) of A_k between Neumann walls: J of the evenly extended grid summed over the mirror
+// images of column c's cell (x images jx, -1 - jx, 2 nx - 1 - jx; likewise in y) that lie within
+// the radius-3 stencil of row r's cell; q of an image is q of the cell.  An image is never
+// nearer than the cell itself, so the band of A_k is that of the periodic case.
+__device__ __forceinline__ double jac_entry_neu(const BlockDesc& B, const Geo& g, double ih2, const double* qb,
+                                                double idt, const double* lin, int r, int c) {
+  const int bx = B.bx;
+  const int ar = r % bx, br = r / bx, ac = c % bx, bc = c / bx;
+  if (abs(ac - ar) + abs(bc - br) > 3) return 0.0;
+  const int gx = B.x0 + ar, gy = B.y0 + br, jx = B.x0 + ac, jy = B.y0 + bc;
+  const int xs[3] = {jx - gx, -1 - jx - gx, 2 * g.nx - 1 - jx - gx};
+  const int ys[3] = {jy - gy, -1 - jy - gy, 2 * g.ny - 1 - jy - gy};
+  double v = 0.0;
+  for (int iy = 0; iy < 3; ++iy)
+    for (int ix = 0; ix < 3; ++ix) {
+      const int dx = xs[ix], dy = ys[iy], ad = abs(dx) + abs(dy);
+      if (ad > 3) continue;
+      v += lin[(dy + 3) * 7 + (dx + 3)];
+      if (ad <= 1) v -= (ad == 0 ? -4.0 * ih2 : ih2) * qb[c];
+    }
+  if (r == c) v += idt;
+  return v;
+}
+
 template <typename TC, typename TS, int RING>
 __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
                                                   const double* __restrict__ q, double idt,
@@ -222,11 +246,13 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
     }
   }
   __syncthreads();
+  const bool neu = g.neumann != 0;
   for (int idx = tid; idx < W * RING; idx += nt) {
     const int pos = idx / RING, col = idx - pos * RING;
     A[pos * RS + col] = (pos < n && col < n)
-                            ? (TC)(mob ? jac_entry_mob(bx, by, ih2, qb, idt, l13, sx, mx, pos, col)
-                                       : jac_entry(bx, ih2, qb, idt, lin_s, pos, col))
+                            ? (TC)(mob   ? jac_entry_mob(bx, by, ih2, qb, idt, l13, sx, mx, pos, col)
+                                   : neu ? jac_entry_neu(B, g, ih2, qb, idt, lin_s, pos, col)
+                                         : jac_entry(bx, ih2, qb, idt, lin_s, pos, col))
                             : (TC)0;
   }
   __syncthreads();
@@ -330,6 +356,8 @@ __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __rest
         TC v = (TC)0;
         if (col < n && mob) {
           v = (TC)jac_entry_mob(bx, by, ih2, qb, idt, l13, sx, mx, rnew, col);
+        } else if (col < n && neu) {
+          v = (TC)jac_entry_neu(B, g, ih2, qb, idt, lin_s, rnew, col);
         } else if (col < n) {
           if (bx >= 7) {  // col - rnew = dx + bx dy has a unique split with |dx| <= 3
             const int d = col - rnew;
@@ -1129,7 +1157,7 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
-  if (sizeof(TC) == 4 && !fs.mob_mu && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
+  if (sizeof(TC) == 4 && !fs.mob_mu && !g.neumann && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
       factor_col_smem_bytes(fs.n_max) <= 227 * 1024) {
     const size_t smem = factor_col_smem_bytes(fs.n_max);
     cudaFuncSetAttribute(k_factor2d_col<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -4,7 +4,8 @@
 //
 // The residual and the JVP are radius-3 composed stencils, Delta_d applied to a
 // radius-2 operator.  Each CTA stages a (32+6) x (16+6) tile of its inputs in
-// shared memory (periodic wrap at the grid edges) and evaluates the stages in
+// shared memory (periodic wrap, or mirror images across Neumann walls, at the grid
+// edges: the operators are then those of the evenly extended grid) and evaluates the stages in
 // place: Laplacian of the halo-2 ring, then mu (or w) on the halo-1 ring, then
 // Delta_d of that on the tile.  All arithmetic is FP64; on GB300 these kernels
 // are bound by the FP64 issue rate, not by HBM (about 25 FP64 ops per 24 bytes).
@@ -16,11 +17,6 @@ namespace {
 constexpr int TX = 32, TY = 16, R = 3;
 constexpr int AX = TX + 2 * R, AY = TY + 2 * R;  // 38 x 22 staged points
 constexpr int NT = 256;                          // 32 x 8 threads, 2 outputs each
-
-__device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
-}
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -57,7 +53,7 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
   const double sm = (S && smean) ? *smean / (double)g.n : 0.0;  // mean of S (mass projection)
   for (int i = tid; i < AX * AY; i += NT) {
     const int ly = i / AX, lx = i - ly * AX;
-    const long long idx = wrap(x0 + lx - R, g.nx) + (long long)g.nx * wrap(y0 + ly - R, g.ny);
+    const long long idx = cell_index(x0 + lx - R, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - R, g.ny, g.neumann);
     double p = Pb[idx];
     if (S) p = p + lam * (S[idx] - sm);
     const double nn = phin[idx];
@@ -147,12 +143,12 @@ __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ 
   const double sc = vscale ? *vscale : 1.0;
   for (int i = tid; i < AX * AY; i += NT) {
     const int ly = i / AX, lx = i - ly * AX;
-    const long long idx = wrap(x0 + lx - R, g.nx) + (long long)g.nx * wrap(y0 + ly - R, g.ny);
+    const long long idx = cell_index(x0 + lx - R, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - R, g.ny, g.neumann);
     sV[ly][lx] = sc * v[idx];
   }
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4), lx = i - ly * (AX - 4);
-    const long long idx = wrap(x0 + lx - 1, g.nx) + (long long)g.nx * wrap(y0 + ly - 1, g.ny);
+    const long long idx = cell_index(x0 + lx - 1, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - 1, g.ny, g.neumann);
     sQ[ly][lx] = q[idx];
     if (MOB) {
       sMu[ly][lx] = mug[idx];
@@ -208,10 +204,10 @@ __global__ void __launch_bounds__(256) k_energy2d(Geo g, const double* __restric
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx), y = (int)(i / g.nx);
     const double p = phi[i];
-    const double pe = phi[wrap(x + 1, g.nx) + (long long)g.nx * y];
-    const double pw = phi[wrap(x - 1, g.nx) + (long long)g.nx * y];
-    const double pn = phi[x + (long long)g.nx * wrap(y + 1, g.ny)];
-    const double ps = phi[x + (long long)g.nx * wrap(y - 1, g.ny)];
+    const double pe = phi[cell_index(x + 1, g.nx, g.neumann) + (long long)g.nx * y];
+    const double pw = phi[cell_index(x - 1, g.nx, g.neumann) + (long long)g.nx * y];
+    const double pn = phi[x + (long long)g.nx * cell_index(y + 1, g.ny, g.neumann)];
+    const double ps = phi[x + (long long)g.nx * cell_index(y - 1, g.ny, g.neumann)];
     const double lap = ih2 * ((pe + pw) + (pn + ps) - 4.0 * p);
     const double grad = (pe - p) * (pe - p) + (p - pw) * (p - pw) + (pn - p) * (pn - p) + (p - ps) * (p - ps);
     const double p2 = p * p;

@@ -21,6 +21,7 @@ PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA = 0, -1, -2, -3
 PFC_ENEWTON, PFC_EGMRES, PFC_ESINGULAR, PFC_ENAN, PFC_ETIMEOUT = -4, -5, -6, -7, -8
 PFC_F64, PFC_F32, PFC_BF16 = 0, 1, 2
 PFC_AS, PFC_LEFT_RAS, PFC_RIGHT_RAS = 0, 1, 2
+PFC_PERIODIC, PFC_NEUMANN = 0, 1  # pfc_params.boundary
 PFC_GUESS_PREV, PFC_GUESS_EXTRAP, PFC_GUESS_USER, PFC_GUESS_LEARNED = 0, 1, 2, 3
 N_APPLY_VARIANTS = 6  # apply kernels 0-4 (per-step solves, bitwise equal) and 5 (chunked solves)
 APPLY_CHUNKED = 5
@@ -38,7 +39,7 @@ class pfc_params(ctypes.Structure):
         ("mass_projection", c_int), ("ls_alpha", c_double), ("ls_max_cuts", c_int),
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
         ("apply_variant", c_int), ("dt_halvings", c_int), ("gmres_reorth_eta", c_double),
-        ("use_graph", c_int), ("reuse_factor", c_int), ("mobility", c_int),
+        ("use_graph", c_int), ("reuse_factor", c_int), ("mobility", c_int), ("boundary", c_int),
     ]
 
 

@@ -99,3 +99,20 @@ def test_mobility_validation(libpfc):
             pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4), **bad))
     with pytest.raises(pfc.PfcError):
         pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), mobility=1))
+
+
+def test_boundary_validation(libpfc):
+    """Neumann-type walls (boundary = 1): 2D grids of at least 4 x 4 cells, left-RAS, M = 1."""
+    from paper_1703_01202_gb300 import pfc
+
+    assert pfc.workspace_size((64, 48), pfc.default_params(sub=(4, 4), boundary=pfc.PFC_NEUMANN)) > 0
+    for shape, bad in (((64, 64), dict(boundary=2)), ((64, 64), dict(boundary=-1)),
+                       ((64, 64), dict(boundary=1, ras_kind=pfc.PFC_AS, apply_variant=5)),
+                       ((64, 64), dict(boundary=1, mobility=1)), ((3, 64), dict(boundary=1, sub=(1, 1), overlap=0))):
+        prm = dict(sub=(4, 4))
+        prm.update(bad)
+        with pytest.raises(pfc.PfcError):
+            pfc.workspace_size(shape, pfc.default_params(**prm))
+    assert pfc.workspace_size((3, 64), pfc.default_params(sub=(1, 1), overlap=0)) > 0  # periodic: fine
+    with pytest.raises(pfc.PfcError):
+        pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), boundary=1))

@@ -433,3 +433,65 @@ def test_checkpoint_resume_continues_the_same_run(pfc, tmp_path):
     with pytest.raises(pfc.PfcError) as e:
         c.load(path)
     assert e.value.status == pfc.PFC_EINVAL
+
+
+# ---------------------------------------------------------------- Neumann-type walls (Sec. 2)
+NEU = 1  # PFC_NEUMANN
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("shape", [(64, 64), (40, 70), (9, 13), (48, 200)])
+def test_neumann_operators_match_oracle(pfc, shape, prec):
+    """Mirror walls: residual, J v (FP64 and float-float), energy and mass against the oracle's
+    even-extension operators; the fields differ most near the walls, where the stencils fold."""
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 1)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 2)
+    v = inputs.noise_field(shape, 0.0, 1.0, 3)
+    s = solver(pfc, shape, (1, 1), prec=prec, overlap=0, boundary=NEU)
+    F, nrm = s.residual(Phi, phin, 0.7)
+    ref = O.residual(Phi, phin, 0.7, H, GAMMA, neumann=True)
+    np.testing.assert_allclose(F.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert nrm == pytest.approx(np.linalg.norm(ref), rel=1e-12)
+    Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 2.5, H, GAMMA, neumann=True)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    s.set_field(Phi)
+    assert s.energy() == pytest.approx(O.energy(Phi, H, GAMMA, neumann=True), rel=1e-12)
+    assert s.mass() == pytest.approx(O.mass(Phi, H), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("variant", [0, 4, 5])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4), (2, 0.25)])
+@pytest.mark.parametrize("shape,parts,dt", [((50, 37), (3, 2), 10.0), ((96, 80), (5, 6), 1.0),
+                                            ((21, 27), (3, 3), 10.0)])
+def test_neumann_precond_matches_oracle(pfc, shape, parts, dt, prec, tol, variant):
+    """Left-RAS between mirror walls: the wall blocks are clipped (no wrap) and their matrices
+    carry the folded mirror entries; per-step and chunked solves against the oracle's dense-LU
+    Schwarz apply, with the periodic tests' rounding bounds."""
+    Phi = inputs.noise_field(shape, 0.285, 0.3, 8)
+    phin = inputs.noise_field(shape, 0.285, 0.3, 9)
+    r = inputs.noise_field(shape, 0.0, 1.0, 10)
+    s = solver(pfc, shape, parts, prec=prec, overlap=1, apply_variant=variant, boundary=NEU)
+    z = s.precond_apply(Phi, phin, dt, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, dt, H, GAMMA, neumann=True)
+    ref = O.Schwarz(J, O.decompose(shape, parts, 1, neumann=True), "left-ras", "lu").apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (2, 1e-7)])
+def test_neumann_steps_match_oracle(pfc, prec, tol):
+    """Three adaptive steps of a 48 x 40 noise field between mirror walls against the oracle;
+    mass conserved and the energy non-increasing."""
+    shape = (48, 40)
+    phi = inputs.noise_field(shape, 0.07, 0.07, 1070)
+    prm = dict(dt_min=1e-2, dt_max=10.0, eta=5000.0)
+    s = solver(pfc, shape, (3, 3), prec=prec, overlap=1, boundary=NEU, **prm)
+    s.set_field(phi)
+    recs = s.run(3)
+    ref, orecs = O.run(phi, H, GAMMA, O.Params(parts=(3, 3), overlap=1, neumann=True, **prm), 3)
+    assert np.abs(s.get_field() - ref).max() <= tol
+    for r, o in zip(recs, orecs):
+        assert abs(r["energy"] - o.energy) <= 1e-9 * abs(o.energy)
+        assert abs(r["mass"] - o.mass) <= 1e-12 * max(1.0, abs(o.mass))
+    assert all(b["energy"] <= a["energy"] + 1e-13 * abs(a["energy"]) for a, b in zip(recs, recs[1:]))
