@@ -412,13 +412,30 @@ def run_mobility(steps: int, warmup: int, prec: int = 1):
     """The 1024^2 workload with variable mobility M = 1 - phi^2 (the paper's Test B (c)); phi^n
     guess, GMRES cycles as graphs, FP64 JVP (the mobility form's).  F32 factors: the mobility
     blocks are worse conditioned at dt = 10, and BF16 factors let GMRES(30) stall there."""
+    out = run_form(steps, warmup, prec, mobility=1)
+    out["mobility"] = "1 - phi^2"
+    return out
+
+
+def run_neumann(steps: int, warmup: int, prec: int = 2):
+    """The 1024^2 workload between Neumann-type walls (Sec. 2): mirror-image stencils, wall-clipped
+    subdomains with folded block matrices (factored by the generic band LU), phi^n guess, GMRES
+    cycles as graphs, float-float JVP."""
+    out = run_form(steps, warmup, prec, boundary=1)
+    out["boundary"] = "neumann"
+    return out
+
+
+def run_form(steps: int, warmup: int, prec: int, **form):
+    """Adaptive steps of the 1024^2 workload with one of the scheme's other forms (mobility,
+    boundary), timed with CUDA events on the solver's stream."""
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
 
     w = inputs.workload(WORKLOAD)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], mobility=1, dt_halvings=6)
+                                dt_max=w["dt_max"], eta=w["eta"], dt_halvings=6, **form)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
     s.set_field(w["phi"])
     s.run(warmup)
@@ -435,7 +452,7 @@ def run_mobility(steps: int, warmup: int, prec: int = 1):
             "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
             "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
             "dt_last": infos[-1]["dt"], "energy_last": infos[-1]["energy"],
-            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec], "mobility": "1 - phi^2"}
+            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
 
 
 def kernel_loop(args):
@@ -566,6 +583,7 @@ def main():
         line["workloads"] = {
             "batch32x256_bf16": guarded(run_batch32, max(2, args.steps // 2), 2),
             "hex1024_mobility_f32": guarded(run_mobility, max(4, args.steps // 4), 3),
+            "hex1024_neumann_bf16": guarded(run_neumann, max(4, args.steps // 4), 3),
             "bcc256_f32": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 1),
             "bcc256_bf16": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 2),
         }
