@@ -426,14 +426,22 @@ def run_neumann(steps: int, warmup: int, prec: int = 2):
     return out
 
 
-def run_form(steps: int, warmup: int, prec: int, **form):
-    """Adaptive steps of the 1024^2 workload with one of the scheme's other forms (mobility,
-    boundary), timed with CUDA events on the solver's stream."""
+def run_crack(steps: int, warmup: int, prec: int = 1):
+    """Test C's crack-propagation workload: 4096 x 1024 cells of a stretched crystal with a liquid
+    notch, gamma = 1, dt in [1, 5], eta = 100; phi^n guess, GMRES cycles as graphs."""
+    out = run_form(steps, warmup, prec, workload="crack4096x1024")
+    out["workload"] = "crack4096x1024"
+    return out
+
+
+def run_form(steps: int, warmup: int, prec: int, workload: str = WORKLOAD, **form):
+    """Adaptive steps of a workload (by default the 1024^2 one) with one of the scheme's other
+    forms (mobility, boundary), timed with CUDA events on the solver's stream."""
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
 
-    w = inputs.workload(WORKLOAD)
+    w = inputs.workload(workload)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
                                 dt_max=w["dt_max"], eta=w["eta"], dt_halvings=6, **form)
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
@@ -578,12 +586,14 @@ def main():
         "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks", "e2e")} for k, v in variants.items()},
     }
     if not args.no_extras:
-        # the other workloads of the metric, each on this rank's GPU: the 32-run 256^2 ensemble
-        # (pfc_run_batch) and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
+        # the other workloads, each on this rank's GPU: the 32-run 256^2 ensemble (pfc_run_batch),
+        # the 1024^2 one with variable mobility and between Neumann walls, the 4096 x 1024 crack
+        # case and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
         line["workloads"] = {
             "batch32x256_bf16": guarded(run_batch32, max(2, args.steps // 2), 2),
             "hex1024_mobility_f32": guarded(run_mobility, max(4, args.steps // 4), 3),
             "hex1024_neumann_bf16": guarded(run_neumann, max(4, args.steps // 4), 3),
+            "crack4096x1024_bf16": guarded(run_crack, max(4, args.steps // 4), 3, 2),
             "bcc256_f32": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 1),
             "bcc256_bf16": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 2),
         }

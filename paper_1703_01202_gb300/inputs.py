@@ -163,6 +163,30 @@ def bcc_seeds_3d(
     return phi
 
 
+def crack_field(
+    shape: Tuple[int, int],
+    h: float,
+    mean: float = 0.49,
+    qx: float = math.sqrt(3.0) / 2.0,
+    stretch: float = 0.9,
+    notch_cells: Tuple[int, int] = (20, 40),
+    notch_value: float = 0.79,
+) -> np.ndarray:
+    """Test C's initial state: a stretched one-mode hexagonal lattice
+        mean + cos(qy y / sqrt3) cos(qx x) - cos(2 qy y / sqrt3) / 2,  qy = stretch * qx,
+    on every cell, with a centred notch of notch_cells (rows, columns) replaced by the
+    coexisting liquid density notch_value."""
+    ny, nx = shape
+    qy = stretch * qx
+    y, x = cell_centres(shape, h)
+    phi = mean + np.cos(qy * y / math.sqrt(3.0)) * np.cos(qx * x) - 0.5 * np.cos(2.0 * qy * y / math.sqrt(3.0))
+    phi = np.broadcast_to(phi, shape).copy()
+    ry, rx = notch_cells
+    y0, x0 = (ny - ry) // 2, (nx - rx) // 2
+    phi[y0 : y0 + ry, x0 : x0 + rx] = notch_value
+    return phi
+
+
 # Named workloads (shape in array-axis order, h, gamma, generator).  The sizes
 # and physical parameters are those of the crystal-growth workloads; the
 # solver settings live with the callers.
@@ -186,4 +210,12 @@ def workload(name: str) -> dict:
         return dict(shape=(256, 256), h=math.pi / 4, gammas=[float(g) for g in gammas],
                     phis=[noise_field((256, 256), 0.07, 0.07, 1004 + i) for i in range(32)],
                     parts=(16, 16), dt_min=1e-2, dt_max=10.0, eta=5000.0, steps=100)
+    if name == "crack4096x1024":  # crack propagation in a stretched crystal, gamma = 1, adaptive dt in [1, 5]
+        h = math.pi / 3.0
+        return dict(shape=(1024, 4096), h=h, gamma=1.0, phi=crack_field((1024, 4096), h),
+                    parts=(64, 256), dt_min=1.0, dt_max=5.0, eta=100.0, steps=3200)
+    if name == "crack128x48":  # the same recipe on a 128 x 48 grid (the notch keeps its 40 x 20 cells)
+        h = math.pi / 3.0
+        return dict(shape=(48, 128), h=h, gamma=1.0, phi=crack_field((48, 128), h),
+                    parts=(3, 8), dt_min=1.0, dt_max=5.0, eta=100.0, steps=20)
     raise KeyError(name)

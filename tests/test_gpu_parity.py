@@ -495,3 +495,23 @@ def test_neumann_steps_match_oracle(pfc, prec, tol):
         assert abs(r["energy"] - o.energy) <= 1e-9 * abs(o.energy)
         assert abs(r["mass"] - o.mass) <= 1e-12 * max(1.0, abs(o.mass))
     assert all(b["energy"] <= a["energy"] + 1e-13 * abs(a["energy"]) for a, b in zip(recs, recs[1:]))
+
+
+# ---------------------------------------------------------------- crack propagation (Test C)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (1, 1e-7)])
+def test_crack_steps_match_oracle(pfc, prec, tol):
+    """Test C's recipe (stretched lattice, liquid notch of 40 x 20 cells, gamma = 1, dt in [1, 5],
+    eta = 100) on a 128 x 48 grid: three adaptive steps against the oracle, the second one a hard
+    step (11 Newton iterations, line-search cuts, thousands of GMRES iterations in the oracle).
+    Tightening the oracle's tolerances moves its solution by 2e-12, loosening GMRES to 1e-3 by 2e-9."""
+    w = inputs.workload("crack128x48")
+    prm = dict(dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"])
+    params = pfc.default_params(sub=tuple(w["parts"][::-1]), factor_prec=prec, overlap=1, **prm)
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
+    s.set_field(w["phi"])
+    recs = s.run(3)
+    ref, orecs = O.run(w["phi"], w["h"], w["gamma"], O.Params(parts=w["parts"], overlap=1, **prm), 3)
+    assert np.abs(s.get_field() - ref).max() <= tol
+    assert [r["dt"] for r in recs] == pytest.approx([o.dt for o in orecs], rel=1e-9)
+    for r, o in zip(recs, orecs):
+        assert abs(r["energy"] - o.energy) <= 1e-9 * abs(o.energy)

@@ -697,3 +697,29 @@ def test_neumann_pins_catch_a_whole_cell_mirror(monkeypatch):
     monkeypatch.setattr(O, "even_extension", whole_cell)
     F = O.residual(Phi, phin, 0.6, 0.8, GAMMA, neumann=True)
     assert np.abs(F - F_ref).max() > 1e-3 * np.abs(F_ref).max()
+
+
+# ---------------------------------------------------------------- crack propagation recipe (Test C)
+def test_crack_recipe_and_first_step():
+    """Test C's initial state: lattice 0.49 + cos(qy y/sqrt3) cos(qx x) - cos(2 qy y/sqrt3)/2 with
+    qx = sqrt3/2, qy = 0.9 qx on the cell centres of h = pi/3 (4096 pi/3 over 4096 cells), a centred
+    notch of exactly 40 x 20 cells at 0.79; one oracle step at dt_min = 1 conserves mass and lowers
+    the energy."""
+    w = inputs.workload("crack128x48")
+    phi, h = w["phi"], w["h"]
+    assert h == pytest.approx(4096 * math.pi / 3 / 4096) and w["gamma"] == 1.0
+    notch = phi == 0.79
+    rows, cols = np.nonzero(notch)
+    assert notch.sum() == 40 * 20 and rows.min() == (48 - 20) // 2 and cols.min() == (128 - 40) // 2
+    assert rows.max() - rows.min() == 19 and cols.max() - cols.min() == 39
+    qx = math.sqrt(3) / 2
+    qy = 0.9 * qx
+    j, i = 3, 5  # a cell outside the notch
+    y, x = (j + 0.5) * h, (i + 0.5) * h
+    expect = 0.49 + math.cos(qy * y / math.sqrt(3)) * math.cos(qx * x) - 0.5 * math.cos(2 * qy * y / math.sqrt(3))
+    assert phi[j, i] == pytest.approx(expect, rel=1e-14)
+    p = O.Params(parts=w["parts"], overlap=1, dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"])
+    phi1, recs = O.run(phi, h, w["gamma"], p, 1)
+    assert recs[0].dt == 1.0
+    assert abs(recs[0].mass - O.mass(phi, h)) <= 1e-12 * abs(O.mass(phi, h))
+    assert recs[0].energy < O.energy(phi, h, w["gamma"])
