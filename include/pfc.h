@@ -3,7 +3,8 @@
  *
  * One call of pfc_step advances the density field phi^n by one time step of
  * the energy-stable DVDM semi-implicit scheme (Eq. NSOP with the discrete
- * variational derivative of Eq. discretedG, mobility M = 1, periodic grid),
+ * variational derivative of Eq. discretedG; mobility M = 1 or 1 - phi^2,
+ * periodic grid or Neumann-type walls, see pfc_params),
  * solving the nonlinear system F(Phi) = 0 (Eq. NLS) by inexact Newton
  * (Eq. newton) with right-preconditioned GMRES (Eq. hjacobi) and a restricted
  * additive Schwarz preconditioner with the paper's "improved" subdomain
@@ -11,8 +12,9 @@
  * step of Eq. (sencondt).
  *
  * Conventions shared by every entry point
- *  - Fields are float64, one value per cell of an Nx x Ny (x Nz) periodic
- *    cell-centred grid with isotropic spacing h, row-major with x fastest:
+ *  - Fields are float64, one value per cell of an Nx x Ny (x Nz) cell-centred
+ *    grid (periodic unless pfc_params.boundary says otherwise) with isotropic
+ *    spacing h, row-major with x fastest:
  *    idx = i + Nx * (j + Ny * k).
  *  - The library never allocates device memory.  The caller allocates one
  *    device workspace of pfc_workspace_size() bytes (256-byte aligned) and

@@ -12,7 +12,7 @@ constexpr int kMaxRestart = 60;   // GMRES restart length limit
 constexpr int kMaxVecs = kMaxRestart + 2;
 constexpr int kRedCtas = 4 * 152;  // CTAs of the grid-stride reduction kernels
 
-// Geometry of a periodic grid (x fastest) and the scheme's constants.
+// Geometry of the grid (x fastest; periodic or between mirror walls) and the scheme's constants.
 struct Geo {
   int nx, ny, nz;
   long long n;      // nx * ny * nz
@@ -37,7 +37,7 @@ __device__ __forceinline__ int cell_index(int i, int n, int neumann) {
 
 // One overlapped subdomain Omega_k^delta and its core Omega_k (Sec. 4).
 struct BlockDesc {
-  int x0, y0, z0;  // global cell of block-local (0,0,0); may be negative (periodic wrap)
+  int x0, y0, z0;  // global cell of block-local (0,0,0); may be negative (periodic wrap; >= 0 between walls)
   int bx, by, bz;  // block extent
   int ox, oy, oz;  // core offset inside the block (= overlap)
   int cx, cy, cz;  // core extent
