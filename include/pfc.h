@@ -167,6 +167,16 @@ int pfc_default_params(pfc_params* p);
    2*overlap, wider than the grid along an axis). */
 int pfc_workspace_size(const pfc_grid* g, const pfc_params* p, size_t* bytes);
 
+/* Host only (no device work): the overlapped subdomains Omega_k^delta of Sec. 4 that
+   a state with this grid and these parameters factors, in its block order (x
+   fastest, then y, then z).  Block k is 12 ints at out[12 k]: first cell x0, y0, z0
+   (negative, or reaching past the grid's end, where a periodic block wraps; never
+   between Neumann walls, where blocks stop at the walls), extent bx, by, bz, core
+   offset inside the block ox, oy, oz and core extent cx, cy, cz (2D: z0 = oz = 0,
+   bz = cz = 1).  Writes min(cap, count) blocks (out may be NULL when cap is 0) and
+   the count to *nblocks.  Errors: PFC_EINVAL as pfc_workspace_size, or cap < 0. */
+int pfc_block_layout(const pfc_grid* g, const pfc_params* p, int* out, int cap, int* nblocks);
+
 /* Creates a state on the current CUDA device.  h: grid spacing; eps: the
    quench depth gamma of Eq. (GE).  dev_workspace: caller-owned device buffer
    of `bytes` >= pfc_workspace_size (256-byte aligned); cuda_stream: a

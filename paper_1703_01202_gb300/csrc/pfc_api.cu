@@ -988,6 +988,19 @@ int pfc_workspace_size(const pfc_grid* g, const pfc_params* p, size_t* bytes) {
   return PFC_OK;
 }
 
+int pfc_block_layout(const pfc_grid* g, const pfc_params* p, int* out, int cap, int* nblocks) {
+  if (!nblocks || cap < 0 || (cap > 0 && !out)) return PFC_EINVAL;
+  int rc = validate(g, p);
+  if (rc) return rc;
+  std::vector<BlockDesc> blocks;
+  int n_max = 0, kl_max = 0;
+  build_blocks(g, p, &blocks, &n_max, &kl_max);
+  static_assert(sizeof(BlockDesc) == 12 * sizeof(int), "BlockDesc is 12 ints");
+  for (int k = 0; k < cap && k < (int)blocks.size(); ++k) memcpy(out + 12 * k, &blocks[k], sizeof(BlockDesc));
+  *nblocks = (int)blocks.size();
+  return PFC_OK;
+}
+
 int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, void* ws, size_t bytes,
                void* cuda_stream, pfc_state** out) {
   if (!out || !ws || !(h > 0.0) || !(eps == eps)) return PFC_EINVAL;

@@ -64,6 +64,7 @@ class PfcError(RuntimeError):
 _SIGNATURES = [
     ("pfc_default_params", c_int, [POINTER(pfc_params)]),
     ("pfc_workspace_size", c_int, [POINTER(pfc_grid), POINTER(pfc_params), POINTER(c_size_t)]),
+    ("pfc_block_layout", c_int, [POINTER(pfc_grid), POINTER(pfc_params), c_void_p, c_int, POINTER(c_int)]),
     ("pfc_create", c_int, [POINTER(pfc_grid), c_double, c_double, POINTER(pfc_params), c_void_p, c_size_t, c_void_p,
                            POINTER(c_void_p)]),
     ("pfc_destroy", None, [c_void_p]),
@@ -173,6 +174,19 @@ def workspace_size(shape: Sequence[int], params: pfc_params) -> int:
     _check(lib().pfc_workspace_size(ctypes.byref(make_grid(shape)), ctypes.byref(params), ctypes.byref(out)),
            "pfc_workspace_size")
     return out.value
+
+
+def block_layout(shape: Sequence[int], params: pfc_params) -> np.ndarray:
+    """The subdomains a state factors (host only): an (nblocks, 12) int32 array of rows
+    x0, y0, z0, bx, by, bz, ox, oy, oz, cx, cy, cz in the library's block order."""
+    count = c_int(0)
+    grid = make_grid(shape)
+    _check(lib().pfc_block_layout(ctypes.byref(grid), ctypes.byref(params), None, 0, ctypes.byref(count)),
+           "pfc_block_layout")
+    out = np.zeros((count.value, 12), dtype=np.int32)
+    _check(lib().pfc_block_layout(ctypes.byref(grid), ctypes.byref(params), out.ctypes.data_as(c_void_p),
+                                  count.value, ctypes.byref(count)), "pfc_block_layout")
+    return out
 
 
 class Solver:
