@@ -149,13 +149,15 @@ def test_single_block_ras_is_exact_inverse():
     np.testing.assert_allclose(res.x.ravel(), np.linalg.solve(J.toarray(), b.ravel()), rtol=1e-10, atol=1e-12)
 
 
-def test_ras_variants_match_definitions():
+@pytest.mark.parametrize("neumann", [False, True])
+def test_ras_variants_match_definitions(neumann):
     """AS / left-RAS / right-RAS (Eqs. invM, ras, ash) against explicit sums of
-    restriction matrices times dense block inverses."""
+    restriction matrices times dense block inverses; periodic, and between Neumann walls
+    (wall-clipped blocks of the Neumann Jacobian)."""
     shape = (12, 12)
     Phi, phin = rand_field(shape, 15), rand_field(shape, 16)
-    J = O.assemble_jacobian(Phi, phin, 0.5, H2, GAMMA)
-    blocks = O.decompose(shape, (2, 3), 1)
+    J = O.assemble_jacobian(Phi, phin, 0.5, H2, GAMMA, neumann=neumann)
+    blocks = O.decompose(shape, (2, 3), 1, neumann=neumann)
     n = Phi.size
     r = rand_field(shape, 17, 0.0, 1.0).ravel()
     for kind in ("as", "left-ras", "right-ras"):
