@@ -16,7 +16,7 @@ Conventions
 * ``gamma`` is the quench depth of Eq. (GE); mobility M = 1 (Sec. 5, tests A, B, D).
 
 Every function cites the section / equation it follows.  Places where the paper
-is silent are marked READING and follow the readings listed in the design doc.
+is silent are marked READING, each stating the reading taken.
 
 Pinning status: every function here is pinned by tests/test_oracle_pins.py
 (closed forms, identities, brute-force dense solves); none is "parity unpinned".
@@ -560,8 +560,8 @@ def gmres_right(
 
 @dataclass
 class Params:
-    """Solver parameters.  Defaults are the spec settings (Newton rtol
-    1e-10, GMRES rtol 1e-6, left-RAS); the paper's own are eps_r = 1e-8,
+    """Solver parameters.  Defaults are the settings the workloads here run with (Newton
+    rtol 1e-10, GMRES rtol 1e-6, left-RAS); the paper's own are eps_r = 1e-8,
     eps_a = 1e-10, xi_r = 1e-3, xi_a = 1e-11 (Sec. 5)."""
 
     newton_rtol: float = 1e-10
