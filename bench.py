@@ -3,8 +3,15 @@
 eta = 5000, left-RAS on 64 x 64 cores with one overlap cell per side).
 
 One bench step = one full time step of the scheme (Newton + GMRES + RAS,
-energy, mass, adaptive dt) through the C ABI.  Variants: plain FP64 NKS and
-the mixed path (FP32 / BF16 subdomain factors).  Prints one JSON line.
+energy, mass, adaptive dt) through the C ABI.  The headline is the mixed,
+learned-guess form (BF16 subdomain factors applied in FP32; float-float JVP,
+Gram-Schmidt dot products and multi-axpys; FP64 residual, Newton update, GMRES
+least squares, energy, mass and time step), timed with GMRES cycles as CUDA
+graphs.  Beside it: the plain FP64 NKS, the FP32 / BF16 factor forms with the
+phi^n guess, the same forms at 2048^2 and on the 256^3 BCC case, and the
+ensemble, mobility, Neumann and crack workloads.  Per form: iterations, the
+per-kernel rooflines of a separate profiled pass, and the errors against the
+FP64 oracle's trajectories (tests/golden).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -15,6 +22,7 @@ steps over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import importlib.util
 import json
 import math
 import os
@@ -28,23 +36,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "hex1024"
-EXTRA_3D_STEPS = 2
 METRIC = "PFC time steps/s (1024^2 2D crystal growth, adaptive dt)"
+PREC_NAME = {0: "f64", 1: "f32", 2: "bf16"}
 
-
-# DRAM bytes (read + write) of one 2D Schwarz apply launch on this workload from one ncu capture
-# (profiles/ras_apply2d_hex1024_bf16.md, profiles/ras_apply2d_chunked_hex1024_bf16.md), keyed by
-# (factor precision, apply kernel); a kernel not captured since its last change reports null.
-APPLY_TRAFFIC = {(2, 4): 456.238592e6 + 3.252992e6, (2, 5): 540.646400e6 + 3.399424e6}
+# DRAM bytes (read + write) of one launch from one ncu capture, keyed by (kernel family, factor
+# precision, 2D apply kernel); a kernel changed since its capture is left out (traffic null).
+TRAFFIC = {("apply", 2, 5): 540.646400e6 + 3.399424e6}
 
 
 def measured_peaks():
+    """HBM copy GB/s and dense BF16 TFLOP/s measured on the GB300s, else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return float(d.get("hbm_gbs", 6800.0)), "measured"
-    return 6800.0, "fallback"
+        return {"hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# FP32 and FP64 arithmetic peaks of one GB300 (152 SMs at 2070 MHz): 128 FP32 lanes per SM,
+# 2 flops per FMA; FP64 at 1/64 of the FP32 rate.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 
 
 class Clocks:
@@ -93,71 +106,117 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Per-step iteration counts of the FP64 path on this workload at the controller's dt (measured on a
-# GB300 with exact block LU, the oracle's preconditioner): the oracle sample below is scaled by them
-# when the bench has not measured them itself.
-ORACLE_NEWTON_PER_STEP = 4.0
-ORACLE_GMRES_PER_STEP = 146.0
-
-
-def oracle_sample(newton: float, gmres: float, blocks_sampled: int = 512) -> dict:
-    """Times the CPU oracle (one host thread) on a bounded sample of one time step
-    of the workload at dt = dt_max and scales it to seconds per step:
-      newton * (Jacobian assembly + 2 residuals) + Schwarz setup
-      + gmres * (Schwarz apply + CSR matvec + Gram-Schmidt against 15 vectors).
-    The Schwarz setup and apply are timed on the first `blocks_sampled` of the
-    equal-size blocks and scaled by the block count."""
-    code = f"""
-import json, sys, time
-import numpy as np
-sys.path.insert(0, {ROOT!r})
+# ---------------------------------------------------------------- the CPU oracle (cpu_baseline leg)
+ORACLE_STEP = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
 from oracle import pfc_oracle as O
 from paper_1703_01202_gb300 import inputs
-w = inputs.workload({WORKLOAD!r})
-phi, h, g, dt = w["phi"], w["h"], w["gamma"], w["dt_max"]
+w = inputs.workload({workload!r})
+p = O.Params(parts=w["parts"], overlap=1, dt_min=w["dt_min"], dt_max=w["dt_max"], eta=w["eta"])
 t0 = time.perf_counter()
-c = time.perf_counter(); F = O.residual(phi, phi, dt, h, g); t_res = time.perf_counter() - c
-c = time.perf_counter(); J = O.assemble_jacobian(phi, phi, dt, h, g); t_jac = time.perf_counter() - c
-blocks = O.decompose(phi.shape, w["parts"], 1)
-sub = blocks[:{blocks_sampled}]
-scale = len(blocks) / len(sub)
-c = time.perf_counter(); pre = O.Schwarz(J, sub, "left-ras", "lu"); t_sch = (time.perf_counter() - c) * scale
-c = time.perf_counter()
-for _ in range(3):
-    pre.apply(F)
-t_app = (time.perf_counter() - c) / 3 * scale
-v = F.ravel()
-c = time.perf_counter()
-for _ in range(3):
-    J @ v
-t_mv = (time.perf_counter() - c) / 3
-rng = np.random.default_rng(0)
-V = rng.standard_normal((15, v.size))
-c = time.perf_counter()
-x = v.copy()
-for i in range(15):
-    x -= (V[i] @ x) * V[i]
-nrm = np.linalg.norm(x)
-t_orth = time.perf_counter() - c
-step = {newton!r} * (t_jac + 2 * t_res) + t_sch + {gmres!r} * (t_app + t_mv + t_orth)
-print(json.dumps({{"seconds_per_step": step, "sample_seconds": time.perf_counter() - t0,
-                  "parts": {{"residual": t_res, "jacobian": t_jac, "schwarz_setup": t_sch, "apply": t_app,
-                            "matvec": t_mv, "gram_schmidt15": t_orth}}}}))
+phi1, info = O.newton_solve(w["phi"], w["dt_max"], w["h"], w["gamma"], p)
+el = time.perf_counter() - t0
+print(json.dumps({{"seconds": el, "newton_its": info.newton_its, "gmres_its": info.gmres_its,
+                  "converged": bool(info.converged), "dt": w["dt_max"]}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_whole_step(threads: int = 1) -> dict:
+    """One whole time step of the workload by the FP64 CPU oracle as it stands (Jacobian
+    assembly, Schwarz setup with dense block LU, right-preconditioned GMRES(30), line
+    search; its own Newton and GMRES counts) at dt = dt_max from the initial field, timed
+    in a fresh process with `threads` BLAS threads."""
+    code = ORACLE_STEP.format(root=ROOT, workload=WORKLOAD)
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
     if res.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
-    return json.loads(res.stdout.strip().splitlines()[-1])
+        raise RuntimeError("oracle step failed: " + res.stderr[-2000:])
+    r = json.loads(res.stdout.strip().splitlines()[-1])
+    r["threads"] = threads
+    return r
 
 
-def oracle_sample_text(r: dict, newton: float, gmres: float) -> str:
-    return (f"{WORKLOAD} step at dt = dt_max, FP64 oracle on 1 host thread: residual, Jacobian, Schwarz setup "
-            f"and apply on 512 of 4096 blocks (scaled), matvec and 15-vector Gram-Schmidt timed "
-            f"({r['sample_seconds']:.1f} s of CPU work), scaled by {newton:g} Newton and {gmres:g} GMRES "
-            f"iterations per step")
+def oracle_text(r: dict) -> str:
+    return (f"one whole {WORKLOAD} time step at dt = {r['dt']:g} from the initial field (FP64 oracle: "
+            f"{r['newton_its']} Newton, {r['gmres_its']} GMRES iterations, dense block LU, "
+            f"{r['threads']} BLAS thread(s)) in {r['seconds']:.1f} s on {cpu_model()} ({os.cpu_count()} cores)")
 
 
+def reference_arm(args):
+    """The base contract's reference arm: the oracle, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # Each timed step is one whole oracle time step (~1.5 min on one core); the oracle has no
+    # state to warm up.  At most two whole steps are timed so that the run ends within minutes.
+    nsteps = max(1, min(args.steps, args.reference_steps))
+    runs = [oracle_whole_step(1) for _ in range(nsteps)]
+    sec = sum(r["seconds"] for r in runs) / nsteps
+    v = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": nsteps, "warmup": 0, "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [1024, 1024], "subdomains": [64, 64], "overlap_per_side": 1},
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": oracle_text(runs[0]) + f"; {nsteps} whole step(s) timed, no warm-up"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    if args.reference_all_cores:
+        allc = oracle_whole_step(os.cpu_count() or 1)
+        line["cpu_baseline"]["all_cores"] = {"value": 1.0 / allc["seconds"], "unit": "steps/s",
+                                             "cores": allc["threads"], "sample": oracle_text(allc)}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- oracle trajectories (tests/golden)
+def _goldens():
+    spec = importlib.util.spec_from_file_location("goldens", os.path.join(ROOT, "tests", "golden", "goldens.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def golden_errors(case: str, prec: int, learned: bool, fast_dots: int) -> dict:
+    """Runs a fresh solver of the given form over the steps of an oracle trajectory (committed
+    record, written by tests/golden/make_goldens.py from the FP64 oracle) and states the errors
+    of the result: max |phi - phi_oracle| over the record's cells after the last step, and the
+    largest relative energy error and mass drift over the steps."""
+    import numpy as np
+
+    G = _goldens()
+    if not os.path.exists(G.path_of(case)):
+        return {"golden": case, "missing": True}
+    rec = G.load(case)
+    s, close = make_solver(rec["meta"]["workload"], prec, learned, fast_dots)
+    try:
+        infos = s.run(int(rec["meta"]["steps"]))
+        phi = s.get_field()
+    finally:
+        close()
+    e = np.array([i["energy"] for i in infos])
+    m = np.array([i["mass"] for i in infos])
+    return {"golden": case, "steps": len(infos), "cells": rec["meta"]["field"],
+            "max_abs_phi": G.field_error(rec, phi),
+            "max_rel_energy": float(np.max(np.abs(e - rec["energy"]) / np.abs(rec["energy"]))),
+            "max_rel_mass_drift": float(np.max(np.abs(m - rec["meta"]["mass0"])) / abs(rec["meta"]["mass0"])),
+            "max_rel_dt": float(np.max(np.abs(np.array([i["dt"] for i in infos]) - rec["dt"]) / rec["dt"])),
+            "newton_its": [int(i["newton_its"]) for i in infos], "oracle_newton_its": rec["newton_its"].tolist()}
+
+
+# ---------------------------------------------------------------- multi-GPU replicas
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -198,20 +257,20 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return units_per_rank * world / seconds_max
 
 
-def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, measure_e2e: bool,
-                apply_variant: int = -1, learned: bool = False, use_graph: int = 1):
-    import numpy as np
+# ---------------------------------------------------------------- solvers
+def make_solver(workload: str, prec: int, learned: bool = False, fast_dots: int = 0, stream=True, **form):
+    """A solver for a workload (fresh field set), its guess network and a close function."""
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
     from paper_1703_01202_gb300 import learned as lrn
 
-    w = inputs.workload(WORKLOAD)
+    w = inputs.workload(workload)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], apply_variant=apply_variant,
-                                guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV, use_graph=use_graph)
-    # a stream of its own: GMRES cycles run as captured graphs whenever per-apply timing is off
-    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
+                                dt_max=w["dt_max"], eta=w["eta"], gmres_fast_dots=fast_dots,
+                                guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV, **form)
+    # a stream of its own: GMRES cycles run as captured graphs whenever per-kernel timing is off
+    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream() if stream else None)
     net = None
     if learned:  # the committed network, trained on 512^2 trajectories of this workload's distribution
         theta, s_out = lrn.load()
@@ -219,13 +278,43 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
         net.set_params(theta)
         pfc.set_guess_net(s, net, s_out)
     s.set_field(w["phi"])
-    s.run(warmup)
-    tuning = s.tuning()
+
+    def close():
+        s.close()
+        if net is not None:
+            net.close()
+        torch.cuda.empty_cache()
+
+    return s, close
+
+
+def kernel_rooflines(pk: dict, hbm_gbs: float) -> dict:
+    """Per kernel family of the profiled pass: mean launch time, achieved algorithmic GB/s and
+    its fraction of the measured HBM copy rate (the factor: achieved TFLOP/s against the FP32 or
+    FP64 pipe's peak)."""
+    out = {}
+    for k, v in pk.items():
+        if v["launches"] == 0 or v["ms"] <= 0:
+            continue
+        sec = v["ms"] * 1e-3
+        r = {"launches": v["launches"], "us_per_launch": 1e3 * v["ms"] / v["launches"],
+             "achieved_gbs": v["bytes"] / sec / 1e9, "frac_hbm": v["bytes"] / sec / 1e9 / hbm_gbs,
+             "stored_over_algorithmic": v["bytes_stored"] / v["bytes"] if v["bytes"] else None}
+        if v["flops"] > 0:
+            r["achieved_tflops"] = v["flops"] / sec / 1e12
+        out[k] = r
+    return out
+
+
+def timed_steps(s, steps: int, world: int, local: int):
+    """`steps` adaptive steps of solver s between CUDA events on its stream (barrier and
+    synchronise on both sides); returns (ms, infos, clocks, launches)."""
+    import torch
+
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    s.profile(True)
     k0 = s.profile_read()["kernel_launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -236,30 +325,53 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
     barrier(world)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    prof = s.profile_read()
-    s.profile(False)
-    ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(world, ms)
+    launches = s.profile_read()["kernel_launches"] - k0
+    return max_over_ranks(world, e0.elapsed_time(e1)), infos, ck, launches
+
+
+def run_variant(workload: str, prec: int, steps: int, warmup: int, world: int, local: int, learned=False,
+                fast_dots=0, profile_steps=4, e2e=False, golden=None, hbm=6800.0):
+    """Warm-up, `steps` timed steps on the graph path, `profile_steps` more with per-kernel
+    events (host-driven GMRES loop), the end-to-end host-buffer steps when asked, and the
+    errors against an oracle trajectory."""
+    import numpy as np
+    import torch
+
+    s, close = make_solver(workload, prec, learned, fast_dots)
+    s.run(warmup)
+    tuning = s.tuning()
+    ms, infos, ck, launches = timed_steps(s, steps, world, local)
     out = {
         "ms_per_step": ms / steps,
         "steps_per_s": steps / (ms / 1e3),
         "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
         "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
-        "learned_guess_used": sum(1 for i in infos if i["guess_used"] == pfc.PFC_GUESS_LEARNED),
+        "learned_guess_used": sum(1 for i in infos if i["guess_used"] == 3),
         "dt_last": infos[-1]["dt"],
         "energy_last": infos[-1]["energy"],
-        "apply_launches": prof["apply_launches"],
-        "apply_ms_avg": prof["apply_ms"] / max(prof["apply_launches"], 1),
-        "apply_bytes": prof["apply_bytes"],
-        "gpu_launches": prof["kernel_launches"] - k0,
+        "gpu_launches": launches,
         "clocks": ck,
         "tuning": tuning,
+        "factor_prec": PREC_NAME[prec],
+        "phi_after": None,
     }
-    if measure_e2e:
-        # same metric through the C ABI with host buffers: every step copies phi^n in
-        # from pinned host memory and phi^{n+1} back out
-        pin_in = torch.empty(w["shape"], dtype=torch.float64).pin_memory()
-        pin_out = torch.empty(w["shape"], dtype=torch.float64).pin_memory()
+    if profile_steps > 0:
+        s.profile(True)
+        s.run(profile_steps)
+        pk = s.profile_kernels()
+        s.profile(False)
+        out["kernels"] = kernel_rooflines(pk, hbm)
+        out["profiled_steps"] = profile_steps
+        a = pk["apply"]
+        out["apply"] = {"launches": a["launches"], "ms_avg": a["ms"] / max(a["launches"], 1),
+                        "bytes_algorithmic": a["bytes"] / max(a["launches"], 1),
+                        "bytes_stored": a["bytes_stored"] / max(a["launches"], 1)}
+    if e2e:
+        # same metric through the C ABI with host buffers: every step copies phi^n in from
+        # pinned host memory and phi^{n+1} back out (GMRES cycles as graphs)
+        shape = tuple(s.shape)
+        pin_in = torch.empty(shape, dtype=torch.float64).pin_memory()
+        pin_out = torch.empty(shape, dtype=torch.float64).pin_memory()
         a_in, a_out = pin_in.numpy(), pin_out.numpy()
         a_in[...] = s.get_field()
         torch.cuda.synchronize()
@@ -273,11 +385,10 @@ def run_variant(prec: int, steps: int, warmup: int, world: int, local: int, meas
         el = max_over_ranks(world, time.perf_counter() - t0)
         out["e2e"] = {"value": steps * world / el, "unit": "steps/s", "h2d_bytes_per_step": int(a_in.nbytes),
                       "d2h_bytes_per_step": int(a_out.nbytes)}
-    s.close()
-    del s
-    if net is not None:
-        net.close()
-    torch.cuda.empty_cache()
+    out["phi_after"] = s.get_field()
+    close()
+    if golden:
+        out["errors_vs_oracle"] = golden_errors(golden, prec, learned, fast_dots)
     return out
 
 
@@ -325,21 +436,15 @@ def run_batch32(steps: int, warmup: int, prec: int = 2):
             "single_run_steps_per_s": steps / el1, "gpu_launches": launches,
             "newton_per_step": sum(r["newton_its"] for rr in recs for r in rr) / (len(recs) * steps),
             "gmres_per_step": sum(r["gmres_its"] for rr in recs for r in rr) / (len(recs) * steps),
-            "dt_cuts": sum(r["dt_cuts"] for rr in recs for r in rr),
-            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
+            "dt_cuts": sum(r["dt_cuts"] for rr in recs for r in rr), "factor_prec": PREC_NAME[prec]}
 
 
-def run_bcc256(steps: int, warmup: int, prec: int):
-    """The 3D workload: 256^3 BCC growth, 7 x 7 x 7 uneven cores, ILU(0) blocks."""
+def run_form(steps: int, warmup: int, prec: int, workload: str = WORKLOAD, **form):
+    """Adaptive steps of a workload with one of the scheme's other forms (mobility, boundary),
+    timed with CUDA events on the solver's stream (GMRES cycles as graphs in 2D)."""
     import torch
 
-    from paper_1703_01202_gb300 import inputs, pfc
-
-    w = inputs.workload("bcc256")
-    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"])
-    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
-    s.set_field(w["phi"])
+    s, close = make_solver(workload, prec, dt_halvings=6, **form)
     s.run(warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -349,13 +454,36 @@ def run_bcc256(steps: int, warmup: int, prec: int):
     e1.record(s.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    s.close()
-    del s
-    torch.cuda.empty_cache()
+    close()
     return {"steps": steps, "steps_per_s": steps / (ms / 1e3),
             "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
             "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
-            "dt_last": infos[-1]["dt"], "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
+            "dt_last": infos[-1]["dt"], "energy_last": infos[-1]["energy"], "factor_prec": PREC_NAME[prec]}
+
+
+def guarded(fn, *a, **kw):
+    """An extra workload's record, or the error that stopped it (the bench line still prints)."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the line, not hidden
+        return {"failed": f"{type(e).__name__}: {e}"}
+
+
+def strip(v: dict) -> dict:
+    return {k: x for k, x in v.items() if k not in ("clocks", "e2e", "phi_after")}
+
+
+def versus_f64(variants: dict) -> None:
+    """max |phi - phi_F64 GPU| after the same timed steps (same dt sequence up to the controller's
+    rounding), for every form of a grid that has a plain FP64 run."""
+    import numpy as np
+
+    ref = variants.get("f64", {}).get("phi_after")
+    if ref is None:
+        return
+    for k, v in variants.items():
+        if k != "f64" and v.get("phi_after") is not None:
+            v["max_abs_phi_vs_f64_gpu"] = float(np.abs(v["phi_after"] - ref).max())
 
 
 def precond_sweep(args):
@@ -400,69 +528,6 @@ def precond_sweep(args):
                       "steps": args.steps, "warmup": args.warmup}))
 
 
-def guarded(fn, *a):
-    """An extra workload's record, or the error that stopped it (the bench line still prints)."""
-    try:
-        return fn(*a)
-    except Exception as e:  # noqa: BLE001 - reported in the line, not hidden
-        return {"failed": f"{type(e).__name__}: {e}"}
-
-
-def run_mobility(steps: int, warmup: int, prec: int = 1):
-    """The 1024^2 workload with variable mobility M = 1 - phi^2 (the paper's Test B (c)); phi^n
-    guess, GMRES cycles as graphs, FP64 JVP (the mobility form's).  F32 factors: the mobility
-    blocks are worse conditioned at dt = 10, and BF16 factors let GMRES(30) stall there."""
-    out = run_form(steps, warmup, prec, mobility=1)
-    out["mobility"] = "1 - phi^2"
-    return out
-
-
-def run_neumann(steps: int, warmup: int, prec: int = 2):
-    """The 1024^2 workload between Neumann-type walls (Sec. 2): mirror-image stencils, wall-clipped
-    subdomains with folded block matrices (factored by the generic band LU), phi^n guess, GMRES
-    cycles as graphs, float-float JVP."""
-    out = run_form(steps, warmup, prec, boundary=1)
-    out["boundary"] = "neumann"
-    return out
-
-
-def run_crack(steps: int, warmup: int, prec: int = 1):
-    """Test C's crack-propagation workload: 4096 x 1024 cells of a stretched crystal with a liquid
-    notch, gamma = 1, dt in [1, 5], eta = 100; phi^n guess, GMRES cycles as graphs."""
-    out = run_form(steps, warmup, prec, workload="crack4096x1024")
-    out["workload"] = "crack4096x1024"
-    return out
-
-
-def run_form(steps: int, warmup: int, prec: int, workload: str = WORKLOAD, **form):
-    """Adaptive steps of a workload (by default the 1024^2 one) with one of the scheme's other
-    forms (mobility, boundary), timed with CUDA events on the solver's stream."""
-    import torch
-
-    from paper_1703_01202_gb300 import inputs, pfc
-
-    w = inputs.workload(workload)
-    params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], dt_halvings=6, **form)
-    s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream())
-    s.set_field(w["phi"])
-    s.run(warmup)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s.stream)
-    infos = s.run(steps)
-    e1.record(s.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    s.close()
-    return {"steps": steps, "steps_per_s": steps / (ms / 1e3),
-            "newton_per_step": sum(i["newton_its"] for i in infos) / steps,
-            "gmres_per_step": sum(i["gmres_its"] for i in infos) / steps,
-            "dt_last": infos[-1]["dt"], "energy_last": infos[-1]["energy"],
-            "factor_prec": {0: "f64", 1: "f32", 2: "bf16"}[prec]}
-
-
 def kernel_loop(args):
     """Runs one kernel family `steps` times on the workload's initial field
     (each pfc_precond_apply factors and applies once), for ncu captures."""
@@ -471,7 +536,7 @@ def kernel_loop(args):
     from paper_1703_01202_gb300 import build, inputs, pfc
 
     build.build()
-    w = inputs.workload(WORKLOAD)
+    w = inputs.workload(args.kernel_workload)
     prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2, "bf16_learned": 2}[args.variant]
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec,
                                 apply_variant=args.apply_variant)
@@ -490,6 +555,7 @@ def kernel_loop(args):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     print(json.dumps({"kernel_loop": args.kernel_loop, "variant": args.variant, "calls": args.steps,
+                      "workload": args.kernel_workload,
                       "ms_per_call": [round(1e3 * t, 3) for t in times], "tuning": s.tuning()}))
 
 
@@ -499,19 +565,26 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--reference-steps", type=int, default=1,
+                    help="reference arm: whole oracle time steps timed (at most --steps)")
+    ap.add_argument("--reference-all-cores", action="store_true",
+                    help="reference arm: also time one whole oracle step with one BLAS thread per host core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="all", choices=["all", "f64", "f32", "bf16", "bf16_learned"],
-                    help="run one factor-precision variant only (profiling runs)")
-    ap.add_argument("--no-graph", action="store_true",
-                    help="profiling aid: run GMRES cycles from the host loop (every launch visible to ncu)")
+    ap.add_argument("--profile-steps", type=int, default=4,
+                    help="steps after the timed region with per-kernel CUDA events (rooflines)")
+    ap.add_argument("--variant", default="all",
+                    choices=["all", "f64", "f32", "bf16", "bf16_learned", "bf16_learned_fastdots"],
+                    help="run one form only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the ensemble (32 x 256^2) and 3D (256^3) workloads")
-    ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
-                    help="2D Schwarz apply kernel (-1: autotuned at the first factorisation)")
+                    help="skip the 2048^2, 256^3, ensemble and other-form workloads")
+    ap.add_argument("--no-golden", action="store_true", help="skip the error runs against the oracle trajectories")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="AS / left-RAS / right-RAS x overlap 0-3 on the workload (no bench line)")
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
-                    help="profiling aid: run one kernel family repeatedly on the workload (no bench line)")
+                    help="profiling aid: run one kernel family repeatedly on a workload (no bench line)")
+    ap.add_argument("--kernel-workload", default=WORKLOAD)
+    ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
+                    help="2D Schwarz apply kernel for --kernel-loop (-1: autotuned)")
     args = ap.parse_args()
     if args.kernel_loop:
         kernel_loop(args)
@@ -519,29 +592,11 @@ def main():
     if args.precond_sweep:
         precond_sweep(args)
         return
-    if args.warmup < 3 and args.impl == "ours":
-        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-
     if args.impl == "reference":
-        rank = int(os.environ.get("RANK", "0"))
-        if rank != 0:
-            return
-        nw, gm = ORACLE_NEWTON_PER_STEP, ORACLE_GMRES_PER_STEP
-        for _ in range(min(args.warmup, 1)):
-            oracle_sample(nw, gm)
-        samples = [oracle_sample(nw, gm) for _ in range(max(1, args.steps))]
-        sec = statistics.median(r["seconds_per_step"] for r in samples)
-        v = 1.0 / sec
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": len(samples), "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * sec,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": oracle_sample_text(samples[0], nw, gm) + "; median over steps"},
-            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }))
+        reference_arm(args)
         return
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
     world, rank, local = dist_setup(args)
     from paper_1703_01202_gb300 import build
@@ -549,16 +604,24 @@ def main():
     if rank == 0:
         build.build()
     barrier(world)
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    golden = None if args.no_golden else "hex1024_s10"
+    forms = (("f64", 0, False, 0), ("f32", 1, False, 0), ("bf16", 2, False, 0), ("bf16_learned", 2, True, 0),
+             ("bf16_learned_fastdots", 2, True, 1))
     variants = {}
-    for name, prec, lg in (("f64", 0, False), ("f32", 1, False), ("bf16", 2, False), ("bf16_learned", 2, True)):
+    for name, prec, lg, fd in forms:
         if args.variant in ("all", name):
-            variants[name] = run_variant(prec, args.steps, args.warmup, world, local,
-                                         measure_e2e=(name == "bf16_learned" or args.variant != "all"),
-                                         apply_variant=args.apply_variant, learned=lg,
-                                         use_graph=0 if args.no_graph else 1)
-    head = variants["bf16_learned" if "bf16_learned" in variants else args.variant]
-    peak, peak_kind = measured_peaks()
-    achieved = head["apply_bytes"] / (head["apply_ms_avg"] * 1e-3) / 1e9
+            variants[name] = run_variant(WORKLOAD, prec, args.steps, args.warmup, world, local, learned=lg,
+                                         fast_dots=fd, profile_steps=args.profile_steps,
+                                         e2e=(name == "bf16_learned" or args.variant == name), golden=golden,
+                                         hbm=hbm)
+    versus_f64(variants)
+    head_name = "bf16_learned" if "bf16_learned" in variants else args.variant
+    head = variants[head_name]
+    ap_ = head.get("apply", {})
+    achieved = ap_["bytes_algorithmic"] / (ap_["ms_avg"] * 1e-3) / 1e9 if ap_.get("launches") else None
+    traffic = TRAFFIC.get(("apply", 2, head["tuning"]["apply_variant"])) if head_name.startswith("bf16") else None
     line = {
         "metric": METRIC,
         "value": whole_job_rate(args.steps, world, head["ms_per_step"] * args.steps / 1e3),
@@ -570,40 +633,59 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (subdomain factors stored bf16 and applied in f32; guess network bf16/f32)",
+        "dtype": ("f64 residual / Newton / GMRES least squares / energy / mass / dt; f32 subdomain LU stored "
+                  "bf16; float-float JVP and Gram-Schmidt sweeps; guess network bf16 with f32 accumulation"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [1024, 1024], "subdomains": [64, 64], "overlap_per_side": 1,
-                   "guess": "learned network (safeguarded by phi^n and the extrapolation)",
-                   "l2": "inputs larger than L2 (factors 0.45-1.7 GB per apply)", "replicas": world},
-        "roofline": {"bound": "hbm", "kernel": "ras_apply (left-RAS banded triangular solves)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind,
-                     "traffic": APPLY_TRAFFIC.get((2, head["tuning"]["apply_variant"]))},
+                   "form": head_name, "guess": "learned network (safeguarded by phi^n and the extrapolation)",
+                   "timed_path": "GMRES cycles as CUDA graphs, no per-kernel events in the timed region",
+                   "l2": "inputs larger than L2 (factors 0.4-0.6 GB per apply, Krylov basis 0.25 GB)",
+                   "replicas": world},
+        "roofline": {"bound": "hbm", "kernel": "Schwarz apply (left-RAS banded triangular solves, chunked records)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "peak_source": peaks["source"],
+                     "algorithmic_bytes_per_launch": ap_.get("bytes_algorithmic"),
+                     "stored_bytes_per_launch": ap_.get("bytes_stored"),
+                     "traffic": traffic,
+                     "traffic_over_algorithmic": traffic / ap_["bytes_algorithmic"] if traffic and ap_ else None,
+                     "tensor_pipe_frac": 0.0,
+                     "timing": f"CUDA events around each apply on the solver's stream over {args.profile_steps} "
+                               "profiled steps after the timed region"},
+        "rooflines": head.get("kernels"),
+        "peaks": {"hbm_gbs": hbm, "fp32_tflops": FP32_PEAK_TFLOPS, "fp64_tflops": FP64_PEAK_TFLOPS},
         "clocks": head["clocks"],
         "gpu_launches": head["gpu_launches"],
-        "e2e": head["e2e"],
+        "e2e": head.get("e2e"),
         "iterations": {"newton_per_step": head["newton_per_step"], "gmres_per_step": head["gmres_per_step"]},
-        "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks", "e2e")} for k, v in variants.items()},
+        "errors_vs_oracle": head.get("errors_vs_oracle"),
+        "variants": {k: strip(v) for k, v in variants.items()},
     }
     if not args.no_extras:
-        # the other workloads, each on this rank's GPU: the 32-run 256^2 ensemble (pfc_run_batch),
-        # the 1024^2 one with variable mobility and between Neumann walls, the 4096 x 1024 crack
-        # case and the 256^3 BCC case (F32 and BF16 ILU(0) factors)
+        # the other workloads, each on this rank's GPU
+        grid2048 = {}
+        for name, prec, lg, st in (("f64", 0, False, 4), ("f32", 1, False, 20), ("bf16", 2, False, 20),
+                                   ("bf16_learned", 2, True, 20)):
+            grid2048[name] = guarded(run_variant, "hex2048", prec, st, 3, world, local, learned=lg, profile_steps=2,
+                                     golden=None if args.no_golden else "hex2048_s3", hbm=hbm)
+        versus_f64(grid2048)
+        bcc = {}
+        for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
+            bcc[name] = guarded(run_variant, "bcc256", prec, 5, 1, world, local, profile_steps=1,
+                                golden=None if args.no_golden else "bcc64_s50", hbm=hbm)
+            if isinstance(bcc[name], dict) and "errors_vs_oracle" in bcc[name]:
+                bcc[name]["errors_vs_oracle"]["grid"] = "64^3 (the oracle trajectory's grid)"
         line["workloads"] = {
+            "hex2048": {k: strip(v) for k, v in grid2048.items()},
+            "bcc256": {k: strip(v) for k, v in bcc.items()},
             "batch32x256_bf16": guarded(run_batch32, max(2, args.steps // 2), 2),
-            "hex1024_mobility_f32": guarded(run_mobility, max(4, args.steps // 4), 3),
-            "hex1024_neumann_bf16": guarded(run_neumann, max(4, args.steps // 4), 3),
-            "crack4096x1024_bf16": guarded(run_crack, max(4, args.steps // 4), 3, 2),
-            "bcc256_f32": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 1),
-            "bcc256_bf16": guarded(run_bcc256, EXTRA_3D_STEPS, 1, 2),
+            "hex1024_mobility_f32": guarded(run_form, max(4, args.steps // 4), 3, 1, mobility=1),
+            "hex1024_neumann_bf16": guarded(run_form, max(4, args.steps // 4), 3, 2, boundary=1),
+            "crack4096x1024_bf16": guarded(run_form, max(4, args.steps // 4), 3, 2, workload="crack4096x1024"),
         }
     if rank == 0 and not args.no_cpu_baseline:
-        f64 = variants.get("f64")
-        nw = f64["newton_per_step"] if f64 else ORACLE_NEWTON_PER_STEP
-        gm = f64["gmres_per_step"] if f64 else ORACLE_GMRES_PER_STEP
-        r = oracle_sample(nw, gm)
-        line["cpu_baseline"] = {"value": 1.0 / r["seconds_per_step"], "unit": "steps/s", "cores": 1,
-                                "kind": "oracle", "sample": oracle_sample_text(r, nw, gm)}
+        r = oracle_whole_step(1)
+        line["cpu_baseline"] = {"value": 1.0 / r["seconds"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                "sample": oracle_text(r)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -111,7 +111,8 @@ typedef struct {
   /* Classical Gram-Schmidt re-orthogonalisation test (Daniel-Gragg-Kaufman-
      Stewart): a second pass when ||w'|| < gmres_reorth_eta ||w||; default 0.3
      (a second pass only under strong cancellation); 1/sqrt(2) is the classical
-     choice; 0 = one pass only.  Both sweeps are FP64. */
+     choice; 0 = one pass only.  Both sweeps have FP64-class accuracy (FP64 on
+     the plain path, float-float on the mixed path; see gmres_fast_dots). */
   double gmres_reorth_eta;
   /* 2D: run every GMRES cycle as one CUDA graph launch (default 1): a captured
      conditional while loop over the Arnoldi iterations, one host synchronisation
@@ -137,6 +138,13 @@ typedef struct {
      Jacobian (the mirror images folded into the block's own columns).  2D grids of
      at least 4 x 4 cells, left-RAS, mobility 0; pfc_residual_static stays periodic. */
   int boundary;
+  /* Arnoldi dot products of the mixed path (F32/BF16 factors): 0 (default)
+     float-float products and sums on the FP32 pipe (about 2^-46 relative, like
+     the multi-axpy, so the orthogonalisation keeps FP64-class accuracy); 1: FP32
+     products of the vectors cut to 24-bit significands (faster; the
+     re-orthogonalisation pass then carries more of the orthogonality).  The
+     plain path (F64 factors) always uses FP64 sweeps. */
+  int gmres_fast_dots;
 } pfc_params;
 
 typedef struct {
@@ -253,14 +261,54 @@ int pfc_next_dt(pfc_state* s, double* dt);
    phi^{n+1} back into out_host.  The copies run on the state's stream. */
 int pfc_step_host(pfc_state* s, const double* phin_host, double dt, double* out_host, pfc_step_info* info);
 
-/* Kernel timing for roofline reports.  pfc_profile(s, 1) creates CUDA events
-   and from then on brackets every executed Schwarz-apply launch with a pair of
-   events on the state's stream; pfc_profile(s, 0) releases them.
-   pfc_profile_read: launches and summed device milliseconds of the applies
-   since profiling was enabled, the algorithmic bytes one apply moves (factor
-   entries read + block gather + core write), and the number of kernels this
-   library launched in the process so far (all kinds). */
+/* Kernel timing for roofline reports.  pfc_profile(s, 1) creates a pool of CUDA
+   events and from then on brackets, with a pair of events on the state's
+   stream, every executed launch of the kernel families below; pfc_profile(s, 0)
+   releases them; both clear the sums.  While profiling is on, GMRES cycles run
+   from the host loop (event records cannot sit inside the cycle graph).
+   Families (index into the pfc_profile_kernels array):
+     PFC_PROF_APPLY     Schwarz apply (Eq. ras), one per GMRES iteration
+     PFC_PROF_JVP       Jacobian-vector product (Eq. Jacobi), one per GMRES iteration
+     PFC_PROF_DOT       first Gram-Schmidt pass, multi-dot of V_0..V_j against w
+     PFC_PROF_AXPY      first Gram-Schmidt pass, multi-axpy w -= sum c_i V_i
+     PFC_PROF_FACTOR    subdomain factorisation (Eq. Ak), once per time step
+     PFC_PROF_RESIDUAL  residual F (Eq. NSOP) with its norm and q
+     PFC_PROF_RECORDS   2D chunked records of the factors (chunked apply only)
+   Algorithmic work per launch: apply = the method's band factor entries (2D band
+   LU with partial pivoting, kl = 3 bx multipliers and 2 kl U entries per step,
+   shortened at the block's end; 3D: 63 ILU(0) entries per row) in the storage
+   precision, 1-byte pivots, the gather of r over the block and the write of z
+   on the core; JVP 24 bytes per point (v, q in, Jv out); multi-dot (j + 2) and
+   multi-axpy (j + 3) vectors of 8 bytes per point at Arnoldi column j; residual
+   3 vectors (+2 for a line-search trial point, +1 with q); factor: band factors
+   written plus q read, and 2 r c + r flops per elimination step (r multipliers,
+   c updated columns).  bytes_stored: what the kernels in use actually move
+   (padded rows, chunk records, scratch passes). */
+enum {
+  PFC_PROF_APPLY = 0,
+  PFC_PROF_JVP = 1,
+  PFC_PROF_DOT = 2,
+  PFC_PROF_AXPY = 3,
+  PFC_PROF_FACTOR = 4,
+  PFC_PROF_RESIDUAL = 5,
+  PFC_PROF_RECORDS = 6,
+  PFC_PROF_KINDS = 7
+};
+typedef struct {
+  long long launches;   /* timed launches                                         */
+  double ms;            /* summed device milliseconds between each launch's events */
+  double bytes;         /* summed algorithmic bytes                               */
+  double flops;         /* summed algorithmic floating-point operations           */
+  double bytes_stored;  /* summed bytes of the storage format in use              */
+} pfc_kernel_prof;
 int pfc_profile(pfc_state* s, int enable);
+/* Sums since profiling was enabled, one record per family for the first
+   min(cap, PFC_PROF_KINDS) families (out may be NULL when cap is 0).
+   Synchronises the state's stream when launches are still waiting. */
+int pfc_profile_kernels(pfc_state* s, pfc_kernel_prof* out, int cap);
+/* The apply family's launches and milliseconds, the algorithmic bytes of one
+   apply, and the number of kernels this library launched in the process so
+   far (all kinds, profiled or not). */
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches);
 
@@ -319,13 +367,28 @@ int pfc_set_guess_net(pfc_state* s, pfc_cnn* c, double s_out);
    fixed array inside the library (65,536 tiles, 512 KiB, held on every GPU
    that loads the library until the process exits), so grids with more than
    65,536 tiles (more than 33,554,432 cells) are rejected with PFC_EINVAL.
-   The first call on a device looks up the array's device address (with that
-   device current); make that first call before any stream capture.  All
-   calls share the one array: calls that overlap on the GPU (other streams,
-   other threads) race and must be serialised by the caller.  The call
-   synchronises its stream to return the norm. */
+   Every call looks up the array's address on the current device.  All calls
+   share the one array: calls that overlap on the GPU (other streams, other
+   threads) race and must be serialised by the caller.  The call synchronises
+   its stream to return the norm, so it cannot be used inside a stream
+   capture.  Errors: PFC_EINVAL for a grid or scalar pfc_create would refuse
+   (dim != 2, n[2] != 1, h or eps not finite, h <= 0), dt <= 0 or not finite,
+   null pointers, or too many tiles; PFC_ECUDA when a CUDA call fails. */
 int pfc_residual_static(const pfc_grid* g, double h, double eps, const double* Phi, const double* phin,
                         double dt, double* F_out, double* norm, void* cuda_stream);
+
+/* Failure-detection self-test of the bounded device-side wait that guards every
+   mbarrier wait of the library's TMA copy rings (a wait gives up after a cycle
+   limit, records PFC_ETIMEOUT and returns instead of hanging).  Launches one
+   CTA on cuda_stream that initialises an mbarrier with one expected arrival,
+   arrives on it when `arrive` is 1 (the wait then succeeds) or not at all (the
+   phase never completes and the wait runs out), and waits with a limit of
+   limit_cycles SM clock cycles (1 .. 4e9).  No copy is ever in flight, so the
+   kernel always returns.  The outcome (PFC_OK or PFC_ETIMEOUT) is written to
+   the caller's device int *dev_status and returned after the stream is
+   synchronised.  Not part of the paper's method.  Errors: PFC_EINVAL for a null
+   dev_status, arrive not 0/1 or a limit out of range; PFC_ECUDA. */
+int pfc_wait_selftest(int arrive, long long limit_cycles, int* dev_status, void* cuda_stream);
 
 /* Human-readable name of a status code (static string). */
 const char* pfc_status_str(int status);

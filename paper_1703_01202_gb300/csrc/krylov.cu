@@ -10,14 +10,17 @@
 // convergence flag).  So one Gram-Schmidt pass costs one kernel per vector
 // sweep, with no separate reduction launch.
 //
-// On the mixed path (F32/BF16 factors) the Arnoldi sweeps run on the FP32 pipe
-// (FF = true).  The multi-axpy w -= sum c_k V_k uses the float-float arithmetic of
-// ff.cuh (about 2^-46 relative) and stores w in FP64: the Arnoldi relation
+// On the mixed path (F32/BF16 factors) the Arnoldi sweeps run on the FP32 pipe.
+// The multi-axpy w -= sum c_k V_k uses the float-float arithmetic of ff.cuh
+// (about 2^-46 relative) and stores w in FP64: the Arnoldi relation
 // J Z_j = V H holds to that accuracy whatever the coefficients are.  The
-// coefficients themselves (the multi-dot products) then only decide how
-// orthogonal the new vector comes out, so they are summed in FP32 from the
-// vectors cut to 24-bit significands (about 2^-24 of |V_i| |w| per product);
-// the conditional second pass (DGKS) restores orthogonality where it matters.
+// coefficients (the multi-dot products) are float-float too by default
+// (Dot::kFF: both operands split into float pairs, products with their exact
+// rounding error and the cross terms, running sums with two-sum), so the
+// orthogonalisation keeps FP64-class accuracy.  Dot::kF32 -- FP32 products of
+// the vectors cut to 24-bit significands, about 2^-24 of |V_i| |w| per
+// product -- is a faster opt-in form (pfc_params.gmres_fast_dots) that leaves
+// the orthogonality of the new vector to the conditional second (DGKS) pass.
 //
 // The basis is kept unnormalised: V_i = scale_i * Vraw_i with scale_i held on
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
@@ -233,17 +236,23 @@ __device__ __forceinline__ void ring_init(const Ring& rg) {
   __syncthreads();
 }
 
-// The multi-dot of this CTA's group of up to G vectors against w.  FF: FP32 products.
-template <bool FF>
-__device__ __forceinline__ void dot_tile(const double* tb, int cntp, const double* wv, const float* wf, double* acc,
-                                         float* af, int k) {
+// Arithmetic of the multi-dot products: FP64, float-float, or FP32 from values cut to floats.
+enum Dot { kF64 = 0, kFF = 1, kF32 = 2 };
+
+// The multi-dot of this CTA's group of up to G vectors against w (wv: w in FP64,
+// wff: w split into float pairs, wf: w cut to floats).
+template <int D>
+__device__ __forceinline__ void dot_tile(const double* tb, int cntp, const double* wv, const ff* wff, const float* wf,
+                                         double* acc, ff* aff, float* af, int k) {
 #pragma unroll
   for (int p = 0; p < kPts; ++p) {
     const int i = threadIdx.x + p * NT;
     if (i < cntp) {
       const double v = tb[i];
-      if (FF)
+      if (D == kF32)
         af[k] = __fmaf_rn(f32_cut(v), wf[p], af[k]);
+      else if (D == kFF)
+        aff[k] = ff_acc(aff[k], ff_prod(ff_split(v), wff[p]));
       else
         acc[k] = fma(v, wv[p], acc[k]);
     }
@@ -251,7 +260,7 @@ __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const doubl
 }
 
 // partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles.
-template <bool FF>
+template <int D>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
                double* __restrict__ partial, const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
@@ -274,10 +283,12 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   ring_init(rg);  // also makes sp visible
   double acc[G];
   float af[G];
+  ff aff[G];
 #pragma unroll
   for (int k = 0; k < G; ++k) {
     acc[k] = 0.0;
     af[k] = 0.0f;
+    aff[k] = {0.0f, 0.0f};
   }
   if (wid == NT / 32) {  // producer warp
     if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err);
@@ -289,6 +300,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
       const int cntp = (int)min((long long)kTile, n - base);
       double wv[kPts];
       float wf[kPts];
+      ff wff[kPts];
       if (!(ok = ring_wait(rg, q))) break;
       {
         const double* tb = rg.buf + (size_t)(q % kStages) * kTile;
@@ -296,7 +308,8 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
         for (int p = 0; p < kPts; ++p) {
           const int i = tid + p * NT;
           wv[p] = i < cntp ? tb[i] : 0.0;
-          if (FF) wf[p] = f32_cut(wv[p]);
+          if (D == kF32) wf[p] = f32_cut(wv[p]);
+          if (D == kFF) wff[p] = ff_split(wv[p]);
         }
       }
       ring_release(rg, q++);
@@ -304,15 +317,19 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
       for (int k = 0; k < G; ++k) {
         if (k < cnt) {  // block-uniform
           if (!(ok = ring_wait(rg, q))) break;
-          dot_tile<FF>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wf, acc, af, k);
+          dot_tile<D>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wff, wf, acc, aff, af, k);
           ring_release(rg, q++);
         }
       }
     }
     if (!ok && lane == 0 && tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
-    if (FF) {
+    if (D == kF32) {
 #pragma unroll
       for (int k = 0; k < G; ++k) acc[k] = f2d_bits(af[k]);
+    }
+    if (D == kFF) {  // the pair's sum in FP64 (one FP64 add per value and thread)
+#pragma unroll
+      for (int k = 0; k < G; ++k) acc[k] = ff_to_double(aff[k]);
     }
     // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
     // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
@@ -523,20 +540,25 @@ int red_ctas(long long n) {
 
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     bool ff) {
+                     int dot) {
   // groups of G vectors in y; about kSweepMinCtas CTAs per SM in all
   const int gy = (nv + G - 1) / G;
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
   const dim3 grid(bx, gy);
   const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
-  if (ff) {
-    cudaFuncSetAttribute(k_multidot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_multidot<true><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
-  } else {
-    cudaFuncSetAttribute(k_multidot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_multidot<false><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail);
-  }
+#define PFC_DOT(D)                                                                                    \
+  do {                                                                                                \
+    cudaFuncSetAttribute(k_multidot<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    k_multidot<D><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail); \
+  } while (0)
+  if (dot == kDotFF)
+    PFC_DOT(kFF);
+  else if (dot == kDotF32)
+    PFC_DOT(kF32);
+  else
+    PFC_DOT(kF64);
+#undef PFC_DOT
   count_launches(1);
 }
 

@@ -8,13 +8,13 @@
 // total) lives in a file-scope __device__ array of fixed size instead of a
 // caller workspace.  Every GPU that loads this library holds the array until
 // the process exits.  In host code the array's name is only a host-side
-// stand-in for the symbol, never a device address: its device address is
-// fetched once per device with cudaGetSymbolAddress and passed to the kernels.
+// stand-in for the symbol, never a device address: every call looks up the
+// array's address on the current device with cudaGetSymbolAddress (cheap once
+// the module is loaded, and never stale after the context is torn down and
+// the module reloaded) and passes it to the kernels.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cmath>
-#include <mutex>
 
 #include "../../include/pfc.h"
 #include "pfc_internal.cuh"
@@ -22,25 +22,14 @@
 namespace {
 
 constexpr int kStaticTiles = 65536;  // 32 x 16 tiles: grids of up to 33,554,432 cells
-constexpr int kMaxDevices = 64;
-
 // [0, kStaticTiles): per-tile partial sums; [kStaticTiles]: the reduced sum of F^2.
 static __device__ __align__(256) double g_residual_scratch[kStaticTiles + 32];
 
-std::mutex g_setup_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.
 int scratch_on_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PFC_ECUDA;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_residual_scratch) != cudaSuccess || !p) return PFC_ECUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_residual_scratch) != cudaSuccess || !p) return PFC_ECUDA;
+  *out = static_cast<double*>(p);
   return PFC_OK;
 }
 
@@ -48,7 +37,9 @@ int scratch_on_current_device(double** out) {
 
 extern "C" int pfc_residual_static(const pfc_grid* grid, double h, double eps, const double* Phi,
                                    const double* phin, double dt, double* F_out, double* norm, void* cuda_stream) {
-  if (!grid || !Phi || !phin || !F_out || grid->dim != 2 || !(h > 0.0) || !(dt > 0.0) || !(eps == eps))
+  // the grid and scalar checks of pfc_create (an infinite h would zero the stencil silently)
+  if (!grid || !Phi || !phin || !F_out || grid->dim != 2 || grid->n[2] != 1 || !(h > 0.0) || !std::isfinite(h) ||
+      !std::isfinite(eps) || !(dt > 0.0) || !std::isfinite(dt))
     return PFC_EINVAL;
   if (grid->n[0] < 1 || grid->n[1] < 1 || grid->n[0] > (1 << 20) || grid->n[1] > (1 << 20)) return PFC_EINVAL;
   const long long tiles = ((grid->n[0] + 31) / 32) * ((grid->n[1] + 15) / 16);

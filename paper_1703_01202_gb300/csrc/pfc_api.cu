@@ -28,6 +28,14 @@ using pfc::Geo;
 using pfc::GmresCtl;
 using pfc::VecList;
 
+// One timed launch waiting for its events: its family, its Arnoldi column (-1: not part of a
+// GMRES cycle) and its algorithmic work.
+struct ProfPair {
+  int kind, j;
+  double bytes, flops, stored;
+};
+constexpr int kProfSlots = 256;
+
 struct pfc_state {
   pfc_grid grid;
   pfc_params p;
@@ -75,13 +83,18 @@ struct pfc_state {
   // history for the adaptive step and the extrapolated guess
   bool have_E, have_Em1, have_prev_dt, have_user_guess;
   double E_n, E_nm1, dt_prev;
-  // kernel timing (pfc_profile)
+  // kernel timing (pfc_profile): a pool of event pairs bracketing launches, resolved at
+  // synchronisation points into per-family sums
   bool prof;
-  cudaEvent_t ev[2 * pfc::kMaxRestart];
-  long long apply_launches;
-  double apply_ms;
-  double apply_bytes;        // per-step factors (apply variants 0-4)
-  double apply_bytes_chunk;  // chunked records (variant 5)
+  std::vector<cudaEvent_t> pev;  // 2 per slot
+  std::vector<ProfPair> ppend;   // slots in use, in record order
+  pfc_kernel_prof pk[PFC_PROF_KINDS];
+  double apply_bytes;        // the method's band factors + gather + core write (one apply)
+  double apply_bytes_step;   // what the per-step apply kernels (variants 0-4) read and write
+  double apply_bytes_chunk;  // what the chunked apply (variant 5) reads and writes
+  double factor_flops;       // one factorisation of every block (band LU with partial pivoting)
+  double factor_bytes;       // its band factors written + q read
+  double record_bytes;       // one chunk-record build: factors read + records written
   // apply kernel picked by timing at the first 2D factorisation (apply_variant = -1)
   bool tuned;
   float tune_ms[pfc::kApplyVariants];
@@ -158,6 +171,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
   if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
+  if (p->gmres_fast_dots != 0 && p->gmres_fast_dots != 1) return PFC_EINVAL;
   if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
   if (p->mobility != 0 && (p->mobility != 1 || g->dim != 2)) return PFC_EINVAL;
   // Neumann walls: 2D, left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then
@@ -474,10 +488,64 @@ int sync_read(pfc_state* s, void* dst, const void* src, size_t bytes) {
   return PFC_OK;
 }
 
+// ---- kernel timing (pfc_profile)
+// Adds every waiting pair whose launch ran to its family's sums (pairs of Arnoldi column
+// j >= its_run belong to iterations queued after the cycle converged: their kernels
+// returned at once) and empties the pool.  The stream must have passed every pair.
+int prof_resolve(pfc_state* s, int its_run) {
+  for (size_t i = 0; i < s->ppend.size(); ++i) {
+    const ProfPair& pp = s->ppend[i];
+    if (pp.j >= 0 && pp.j >= its_run) continue;
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, s->pev[2 * i], s->pev[2 * i + 1]));
+    pfc_kernel_prof& k = s->pk[pp.kind];
+    k.launches += 1;
+    k.ms += ms;
+    k.bytes += pp.bytes;
+    k.flops += pp.flops;
+    k.bytes_stored += pp.stored;
+  }
+  s->ppend.clear();
+  return PFC_OK;
+}
+// Opens a timed launch (returns its slot, -1 when profiling is off); a full pool is first
+// drained with a stream synchronisation.
+int prof_begin(pfc_state* s, int* slot) {
+  *slot = -1;
+  if (!s->prof) return PFC_OK;
+  if (s->ppend.size() >= (size_t)kProfSlots) {
+    CU(cudaStreamSynchronize(s->st));
+    int rc = prof_resolve(s, 1 << 30);
+    if (rc) return rc;
+  }
+  *slot = (int)s->ppend.size();
+  CU(cudaEventRecord(s->pev[2 * *slot], s->st));
+  s->ppend.push_back(ProfPair{-1, -1, 0.0, 0.0, 0.0});
+  return PFC_OK;
+}
+int prof_end(pfc_state* s, int slot, int kind, int j, double bytes, double flops = 0.0, double stored = -1.0) {
+  if (slot < 0) return PFC_OK;
+  CU(cudaEventRecord(s->pev[2 * slot + 1], s->st));
+  s->ppend[slot] = ProfPair{kind, j, bytes, flops, stored < 0.0 ? bytes : stored};
+  return PFC_OK;
+}
+#define PROF_BEGIN(slot)                \
+  do {                                  \
+    int rc_ = prof_begin(s, &(slot));   \
+    if (rc_) return rc_;                \
+  } while (0)
+#define PROF_END(...)                   \
+  do {                                  \
+    int rc_ = prof_end(s, __VA_ARGS__); \
+    if (rc_) return rc_;                \
+  } while (0)
+
 // F, q at Phi (or at the trial point Phi + lam (S - mean S)); returns ||F||^2 on the device in red[slot].
 int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, bool project, const double* phin,
                   double idt, double* F, double* Pout, double* qout, int slot) {
   int np = 0;
+  int ps;
+  PROF_BEGIN(ps);
   if (s->dim == 2) {
     // with variable mobility, mu and s go beside q: (mu, sm) with q, (mut, smt) with the trial q
     const bool mob = s->p.mobility != 0;
@@ -493,13 +561,24 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
     }
     pfc::launch_residual3d(s->g, P, phin, idt, F, qout, s->T1, s->T2, s->partial, &np, s->st);
   }
+  // reads Phi (or Phi_b and S), phi^n; writes F (and the trial Phi, q)
+  PROF_END(ps, PFC_PROF_RESIDUAL, -1, 8.0 * s->g.n * (3 + (S ? 2 : 0) + (qout ? 1 : 0)));
   pfc::launch_reduce(s->partial, 1, np, s->red + slot, s->st);
   CU(cudaGetLastError());
   return PFC_OK;
 }
 
-// The mixed path (F32/BF16 factors) runs the Arnoldi sweeps in float-float arithmetic.
+// The mixed path (F32/BF16 factors) runs the Arnoldi sweeps in float-float arithmetic
+// (the dot products too, unless gmres_fast_dots asks for FP32 ones).
 bool ff_sweeps(const pfc_state* s) { return s->p.factor_prec != PFC_F64; }
+// Bytes the apply kernel in use reads and writes per launch (its storage format).
+double apply_stored(const pfc_state* s) {
+  return s->dim == 2 && s->fs.variant == pfc::kChunkedVariant ? s->apply_bytes_chunk : s->apply_bytes_step;
+}
+int dot_mode(const pfc_state* s) {
+  if (!ff_sweeps(s)) return pfc::kDotF64;
+  return s->p.gmres_fast_dots ? pfc::kDotF32 : pfc::kDotFF;
+}
 
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
          const pfc::IterArgs* ia = nullptr) {
@@ -595,16 +674,21 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
     if (s->p.apply_variant < 0 && !variant_ok(s, 0)) return PFC_EINVAL;
   }
   CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
+  int ps;
+  PROF_BEGIN(ps);
   if (s->dim == 2)
     pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
   else
     pfc::launch_factor3d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->r3, s->status_dev, s->st);
+  PROF_END(ps, PFC_PROF_FACTOR, -1, s->factor_bytes, s->factor_flops);
   CU(cudaGetLastError());
   if (s->dim == 2) {  // chunked records for the chunked apply (in use, or about to be timed)
     const bool tuning = s->p.apply_variant < 0 && !s->tuned && variant_ok(s, pfc::kChunkedVariant);
     s->fs.x_valid = 0;
     if (tuning || s->fs.variant == pfc::kChunkedVariant) {
+      PROF_BEGIN(ps);
       pfc::launch_chunk2d(s->blocks_dev, s->nblocks, s->fs, s->st);
+      PROF_END(ps, PFC_PROF_RECORDS, -1, s->record_bytes);
       CU(cudaGetLastError());
       s->fs.x_valid = 1;
     }
@@ -653,7 +737,7 @@ bool build_cycle_graph(pfc_state* s) {
       pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
       td.err = s->status_dev + 1;
       pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                           ff_sweeps(s));
+                           dot_mode(s));
       pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
       ta.err = s->status_dev + 1;
       pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done,
@@ -726,7 +810,7 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     // its kernels as immediate returns (the done flag).
     int j = graph ? m : 0;
     const int chunk = 3;
-    int c = 0, pend = -1, p0 = 0, p1 = 0;  // chunks queued; buffer and iterations of the pending chunk
+    int c = 0, pend = -1;  // chunks queued; buffer of the pending chunk
     bool stop = graph;
     while (!stop) {
       const int q0 = j, q1 = std::min(m, j + chunk);
@@ -735,19 +819,28 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
         const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * s->vstride;
         double* zj = s->Zbuf + (size_t)j * s->vstride;
         double* w = s->Vbuf + (size_t)(j + 1) * s->vstride;
-        if (s->prof) CU(cudaEventRecord(s->ev[2 * j], s->st));
+        // (pfc_profile: apply, JVP and the first Gram-Schmidt pass are timed; the second pass
+        // runs only on the DGKS test, which the host does not see)
+        int ps;
+        PROF_BEGIN(ps);
         precond(s, vj, &s->ctl->scale[j], zj, done);
-        if (s->prof) CU(cudaEventRecord(s->ev[2 * j + 1], s->st));
+        PROF_END(ps, PFC_PROF_APPLY, j, s->apply_bytes, 0.0, apply_stored(s));
+        PROF_BEGIN(ps);
         jvp(s, zj, s->q, idt, w, done);
+        PROF_END(ps, PFC_PROF_JVP, j, 24.0 * N);  // reads v, q; writes Jv
         for (int pass = 0; pass < passes; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
           pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
           td.err = s->status_dev + 1;
+          if (pass == 0) PROF_BEGIN(ps);
           pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                               ff_sweeps(s));
+                               dot_mode(s));
+          if (pass == 0) PROF_END(ps, PFC_PROF_DOT, j, 8.0 * N * (j + 2));  // reads V_0..V_j and w
           pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
           ta.err = s->status_dev + 1;
+          if (pass == 0) PROF_BEGIN(ps);
           pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
                                 pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
+          if (pass == 0) PROF_END(ps, PFC_PROF_AXPY, j, 8.0 * N * (j + 3));  // reads V_0..V_j, w; writes w
         }
       }
       if (more) {
@@ -757,22 +850,10 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
       }
       if (pend >= 0) {  // the chunk before this one: did the cycle end there?
         CU(cudaEventSynchronize(s->ctl_ev[pend]));
-        const GmresCtl* hb = s->ctl_hb[pend];
-        if (s->prof) {  // only applies that ran (not the ones skipped after convergence)
-          const int ran_to = hb->done ? std::min(hb->its, p1) : p1;
-          for (int t = p0; t < ran_to; ++t) {
-            float ms = 0.f;
-            CU(cudaEventElapsedTime(&ms, s->ev[2 * t], s->ev[2 * t + 1]));
-            s->apply_ms += ms;
-            s->apply_launches += 1;
-          }
-        }
-        if (hb->done) stop = true;
+        if (s->ctl_hb[pend]->done) stop = true;
       }
       if (more) {
         pend = c & 1;
-        p0 = q0;
-        p1 = q1;
         ++c;
       } else {
         pend = -1;
@@ -782,6 +863,7 @@ int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
     if (!graph) {  // the cycle's final head (every queued kernel has finished after this)
       int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
       if (rc) return rc;
+      if (s->prof && (rc = prof_resolve(s, s->ctl_h->its))) return rc;
     }
     const int its = s->ctl_h->its;
     total += its;
@@ -1003,7 +1085,7 @@ int pfc_block_layout(const pfc_grid* g, const pfc_params* p, int* out, int cap, 
 
 int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, void* ws, size_t bytes,
                void* cuda_stream, pfc_state** out) {
-  if (!out || !ws || !(h > 0.0) || !(eps == eps)) return PFC_EINVAL;
+  if (!out || !ws || !(h > 0.0) || !std::isfinite(h) || !std::isfinite(eps)) return PFC_EINVAL;
   *out = nullptr;
   Plan pl;
   int rc = make_plan(g, p, &pl);
@@ -1138,24 +1220,47 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     }
   }
   s->fs.norder = (int)order.size();
-  {  // algorithmic bytes of one Schwarz apply: factors + pivots read, block gather, core write
+  {  // algorithmic work of the Schwarz kernels, per launch
     const double es = p->factor_prec == PFC_F64 ? 8.0 : (p->factor_prec == PFC_F32 ? 4.0 : 2.0);
-    double bytes = 0.0, bytes_chunk = 0.0;
+    double bytes = 0.0, bytes_step = 0.0, bytes_chunk = 0.0, fflops = 0.0, fbytes = 0.0, rbytes = 0.0;
+    std::vector<int> upd3, upd3_n;
+    if (g->dim == 3) update_lists(&upd3, &upd3_n);
     for (const BlockDesc& b : blocks) {
+      const double core = (double)b.cx * b.cy * b.cz * 8.0;
       if (g->dim == 2) {
-        const double n = (double)b.bx * b.by;
-        const int kl = std::min(3 * b.bx, b.bx * b.by - 1);
-        const int ku2 = std::min(2 * kl, b.bx * b.by - 1);
-        bytes += n * (kl + ku2 + 1) * es + n * 4.0 + n * 8.0 + (double)b.cx * b.cy * 8.0;
+        // the method's band LU with partial pivoting: step k has min(kl, n-1-k) multipliers and
+        // U row k min(ku2, n-1-k) entries right of the diagonal (ku2 = 2 kl with the pivots' fill)
+        const int n = b.bx * b.by;
+        const int kl = std::min(3 * b.bx, n - 1), ku2 = std::min(2 * kl, n - 1);
+        double entries = 0.0, fl = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const int r = std::min(kl, n - 1 - k), c = std::min(ku2, n - 1 - k);
+          entries += r + c + 1;
+          fl += r + 2.0 * r * c;  // multipliers, then the rank-1 update of the window
+        }
+        bytes += entries * es + n * 1.0 + n * 8.0 + core;  // band entries, pivots, gather of r, core of z
+        bytes_step += (double)n * (kl + ku2 + 1) * es + n * 1.0 + n * 8.0 + core;
         const pfc::ChunkGeom cg = pfc::chunk_geom(b.bx, b.by, (int)es, p->factor_prec == PFC_F64 ? 8 : 4);
-        bytes_chunk += (double)cg.nc * (cg.fwd + cg.bwd) + n * 8.0 + (double)b.cx * b.cy * 8.0;
-      } else {  // 63 ILU(0) entries per row, row tables, gather, core write
+        bytes_chunk += (double)cg.nc * (cg.fwd + cg.bwd) + n * 8.0 + core;
+        fflops += fl;
+        fbytes += entries * es + n * 1.0 + (double)(b.bx + 6) * (b.by + 6) * 8.0;  // factors out, q in
+        rbytes += (double)n * (pl.lrow + pl.ucol) * es + n + (double)cg.nc * (cg.fwd + cg.bwd);
+      } else {  // ILU(0): 63 entries per row (64 stored), gather, core write
         const double n = (double)b.bx * b.by * b.bz;
-        bytes += n * 63.0 * es + n * 8.0 + n * 8.0 + (double)b.cx * b.cy * b.cz * 8.0;
+        bytes += n * 63.0 * es + n * 8.0 + core;
+        bytes_step += n * 64.0 * es + n * 8.0 * 2 + core;
+        double per_row = 0.0;
+        for (int o = 0; o < 31; ++o) per_row += 1.0 + 2.0 * upd3_n[o];  // multiplier + row updates
+        fflops += n * per_row;
+        fbytes += n * 64.0 * es + (double)(b.bx + 6) * (b.by + 6) * (b.bz + 6) * 8.0;
       }
     }
     s->apply_bytes = bytes;
+    s->apply_bytes_step = bytes_step;
     s->apply_bytes_chunk = bytes_chunk;
+    s->factor_flops = fflops;
+    s->factor_bytes = fbytes;
+    s->record_bytes = rbytes;
   }
   if (g->dim == 3) {
     const Shapes3& S = pl.sh3;
@@ -1440,25 +1545,41 @@ int pfc_step_host(pfc_state* s, const double* phin_host, double dt, double* out_
 int pfc_profile(pfc_state* s, int enable) {
   if (!s) return PFC_EINVAL;
   if (enable && !s->prof) {
-    for (int i = 0; i < 2 * pfc::kMaxRestart; ++i) CU(cudaEventCreate(&s->ev[i]));
+    s->pev.assign(2 * kProfSlots, nullptr);
+    for (cudaEvent_t& e : s->pev) CU(cudaEventCreate(&e));
     s->prof = true;
   } else if (!enable && s->prof) {
     cudaStreamSynchronize(s->st);
-    for (int i = 0; i < 2 * pfc::kMaxRestart; ++i) cudaEventDestroy(s->ev[i]);
+    for (cudaEvent_t& e : s->pev)
+      if (e) cudaEventDestroy(e);
+    s->pev.clear();
     s->prof = false;
   }
-  s->apply_launches = 0;
-  s->apply_ms = 0.0;
+  s->ppend.clear();
+  memset(s->pk, 0, sizeof(s->pk));
+  return PFC_OK;
+}
+
+int pfc_profile_kernels(pfc_state* s, pfc_kernel_prof* out, int cap) {
+  if (!s || cap < 0 || (cap > 0 && !out)) return PFC_EINVAL;
+  if (s->prof && !s->ppend.empty()) {  // launches since the last GMRES cycle ended
+    CU(cudaStreamSynchronize(s->st));
+    int rc = prof_resolve(s, 1 << 30);
+    if (rc) return rc;
+  }
+  for (int k = 0; k < cap && k < PFC_PROF_KINDS; ++k) out[k] = s->pk[k];
   return PFC_OK;
 }
 
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches) {
   if (!s) return PFC_EINVAL;
-  if (apply_launches) *apply_launches = s->apply_launches;
-  if (apply_ms) *apply_ms = s->apply_ms;
-  if (apply_bytes)
-    *apply_bytes = s->dim == 2 && s->fs.variant == pfc::kChunkedVariant ? s->apply_bytes_chunk : s->apply_bytes;
+  pfc_kernel_prof pk[PFC_PROF_KINDS];
+  int rc = pfc_profile_kernels(s, pk, PFC_PROF_KINDS);
+  if (rc) return rc;
+  if (apply_launches) *apply_launches = pk[PFC_PROF_APPLY].launches;
+  if (apply_ms) *apply_ms = pk[PFC_PROF_APPLY].ms;
+  if (apply_bytes) *apply_bytes = s->apply_bytes;
   if (kernel_launches) *kernel_launches = pfc::launches_so_far();
   return PFC_OK;
 }

@@ -289,10 +289,13 @@ struct Tail {
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
 // With tail.ia set (graph mode) the vector count is ia->j + 2 (dot) / ia->j + 1 (axpy), w is
 // ia->w, and nv / nx only bound the grid.
-// ff: float-float arithmetic on the FP32 pipe (the mixed path's Arnoldi sweeps)
+// dot: arithmetic of the products -- kDotF64, kDotFF (float-float on the FP32 pipe, the mixed
+// path's default) or kDotF32 (FP32 products of values cut to floats, opt-in).
+// ff: float-float multi-axpy on the FP32 pipe (the mixed path's Arnoldi sweeps)
+constexpr int kDotF64 = 0, kDotFF = 1, kDotF32 = 2;
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     bool ff = false);
+                     int dot = kDotF64);
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st, bool ff = false);

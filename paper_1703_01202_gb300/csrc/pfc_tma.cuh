@@ -34,12 +34,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase with the given parity to complete; gives up after about
-// two seconds of SM clock and returns false (the caller records PFC_ETIMEOUT).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Default limit of a bounded wait: about two seconds of SM clock.
+constexpr long long kWaitCycles = 4000000000LL;
+
+// Waits for the phase with the given parity to complete; gives up after
+// `limit` SM clock cycles and returns false (the caller records PFC_ETIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > 4000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

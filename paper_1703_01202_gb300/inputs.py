@@ -205,6 +205,11 @@ def workload(name: str) -> dict:
         h = 80.0 * math.pi / 256.0
         return dict(shape=(256, 256, 256), h=h, gamma=0.3, phi=bcc_seeds_3d((256, 256, 256), h, seed=1003),
                     parts=(7, 7, 7), dt_min=0.5, dt_max=10.0, eta=500.0, steps=50)
+    if name == "bcc64":  # the 3D recipe on a 64^3 grid (same h, gamma, mean, taper; seed radius halved)
+        h = 80.0 * math.pi / 256.0
+        return dict(shape=(64, 64, 64), h=h, gamma=0.3,
+                    phi=bcc_seeds_3d((64, 64, 64), h, nseeds=4, d0=2.5 * math.pi, seed=1005),
+                    parts=(7, 7, 7), dt_min=0.5, dt_max=10.0, eta=500.0, steps=50)
     if name == "batch32x256":  # 32 independent 256^2 noise runs, gamma_i ~ U(0.1, 0.35), adaptive dt
         gammas = uniform(1004 * 7 + 3, 32, 0.1, 0.35)
         return dict(shape=(256, 256), h=math.pi / 4, gammas=[float(g) for g in gammas],

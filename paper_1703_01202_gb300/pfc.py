@@ -40,6 +40,7 @@ class pfc_params(ctypes.Structure):
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
         ("apply_variant", c_int), ("dt_halvings", c_int), ("gmres_reorth_eta", c_double),
         ("use_graph", c_int), ("reuse_factor", c_int), ("mobility", c_int), ("boundary", c_int),
+        ("gmres_fast_dots", c_int),
     ]
 
 
@@ -52,6 +53,14 @@ class pfc_step_info(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pfc_kernel_prof(ctypes.Structure):
+    _fields_ = [("launches", c_longlong), ("ms", c_double), ("bytes", c_double), ("flops", c_double),
+                ("bytes_stored", c_double)]
+
+
+PROF_KINDS = ["apply", "jvp", "dot", "axpy", "factor", "residual", "records"]  # PFC_PROF_* order
 
 
 class PfcError(RuntimeError):
@@ -87,8 +96,10 @@ _SIGNATURES = [
     ("pfc_get_tuning", c_int, [c_void_p, POINTER(c_int), POINTER(c_float), POINTER(c_int)]),
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
                                  POINTER(c_longlong)]),
+    ("pfc_profile_kernels", c_int, [c_void_p, POINTER(pfc_kernel_prof), c_int]),
     ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
                                     POINTER(c_double), c_void_p]),
+    ("pfc_wait_selftest", c_int, [c_int, c_longlong, c_void_p, c_void_p]),
     ("pfc_cnn_param_count", c_int, []),
     ("pfc_cnn_workspace_size", c_int, [c_int64, c_int64, POINTER(c_size_t)]),
     ("pfc_cnn_create", c_int, [c_int64, c_int64, c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
@@ -141,8 +152,10 @@ def default_params(**over) -> pfc_params:
         if k == "sub":
             for a, s in enumerate(v):
                 p.sub[a] = int(s)
-        else:
+        elif any(k == f for f, _ in pfc_params._fields_):
             setattr(p, k, v)
+        else:
+            raise KeyError(f"pfc_params has no field {k!r}")
     return p
 
 
@@ -312,6 +325,14 @@ class Solver:
         _check(lib().pfc_profile_read(self.handle, ctypes.byref(a), ctypes.byref(ms), ctypes.byref(b),
                                       ctypes.byref(k)), "pfc_profile_read")
         return {"apply_launches": a.value, "apply_ms": ms.value, "apply_bytes": b.value, "kernel_launches": k.value}
+
+    def profile_kernels(self) -> dict:
+        """Per kernel family (PROF_KINDS): timed launches, summed ms, algorithmic bytes and flops,
+        and the bytes of the storage format in use, since profiling was enabled."""
+        arr = (pfc_kernel_prof * len(PROF_KINDS))()
+        _check(lib().pfc_profile_kernels(self.handle, arr, len(PROF_KINDS)), "pfc_profile_kernels")
+        return {name: {k: getattr(arr[i], k) for k, _ in pfc_kernel_prof._fields_}
+                for i, name in enumerate(PROF_KINDS)}
 
     def tuning(self) -> dict:
         v, gr = c_int(), c_int()

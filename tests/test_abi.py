@@ -116,3 +116,31 @@ def test_boundary_validation(libpfc):
     assert pfc.workspace_size((3, 64), pfc.default_params(sub=(1, 1), overlap=0)) > 0  # periodic: fine
     with pytest.raises(pfc.PfcError):
         pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), boundary=1))
+
+
+def test_static_residual_and_wait_selftest_validation(libpfc):
+    """Arguments both entry points refuse before any device work (so no GPU is needed):
+    the static residual takes pfc_create's grid and scalar checks; the wait self-test
+    its flag and cycle-limit range."""
+    from paper_1703_01202_gb300 import pfc
+
+    L = libpfc
+    one = ctypes.c_void_p(8)  # never dereferenced: every call below fails validation first
+    nrm = ctypes.c_double()
+
+    def static(shape, h=0.78, eps=0.25, dt=1.0):
+        g = pfc.make_grid(shape)
+        return L.pfc_residual_static(ctypes.byref(g), h, eps, one, one, dt, one, ctypes.byref(nrm), None)
+
+    g3 = pfc.make_grid((4, 4))
+    g3.n[2] = 2  # a 2D grid with two planes
+    assert L.pfc_residual_static(ctypes.byref(g3), 0.78, 0.25, one, one, 1.0, one, None, None) == pfc.PFC_EINVAL
+    for kw in (dict(h=float("inf")), dict(h=0.0), dict(eps=float("inf")), dict(eps=float("nan")),
+               dict(dt=float("inf")), dict(dt=-1.0)):
+        assert static((64, 64), **kw) == pfc.PFC_EINVAL, kw
+    assert static((8, 8, 8)) == pfc.PFC_EINVAL
+    assert static((8192, 8192)) == pfc.PFC_EINVAL  # more tiles than the fixed scratch holds
+    assert L.pfc_wait_selftest(0, 1000, None, None) == pfc.PFC_EINVAL
+    assert L.pfc_wait_selftest(2, 1000, one, None) == pfc.PFC_EINVAL
+    assert L.pfc_wait_selftest(0, 0, one, None) == pfc.PFC_EINVAL
+    assert L.pfc_wait_selftest(0, 5_000_000_000, one, None) == pfc.PFC_EINVAL
