@@ -315,7 +315,9 @@ def timed_steps(s, steps: int, world: int, local: int):
     barrier(world)
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    k0 = s.profile_read()["kernel_launches"]
+    from paper_1703_01202_gb300 import pfc
+
+    c0 = pfc.launch_counts()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s.stream)
@@ -325,7 +327,8 @@ def timed_steps(s, steps: int, world: int, local: int):
     barrier(world)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    launches = s.profile_read()["kernel_launches"] - k0
+    c1 = pfc.launch_counts()
+    launches = {"kernels": c1["kernels"] - c0["kernels"], "graphs": c1["graphs"] - c0["graphs"]}
     return max_over_ranks(world, e0.elapsed_time(e1)), infos, ck, launches
 
 
@@ -349,7 +352,8 @@ def run_variant(workload: str, prec: int, steps: int, warmup: int, world: int, l
         "learned_guess_used": sum(1 for i in infos if i["guess_used"] == 3),
         "dt_last": infos[-1]["dt"],
         "energy_last": infos[-1]["energy"],
-        "gpu_launches": launches,
+        "gpu_launches": launches["kernels"],
+        "graph_launches": launches["graphs"],
         "clocks": ck,
         "tuning": tuning,
         "factor_prec": PREC_NAME[prec],
@@ -414,12 +418,13 @@ def run_batch32(steps: int, warmup: int, prec: int = 2):
         s.set_field(phi)
     pfc.run_batch(solvers, warmup)
     torch.cuda.synchronize()
-    k0 = solvers[0].profile_read()["kernel_launches"]
+    c0 = pfc.launch_counts()
     t0 = time.perf_counter()
     recs = pfc.run_batch(solvers, steps)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    launches = solvers[0].profile_read()["kernel_launches"] - k0
+    c1 = pfc.launch_counts()
+    launches = c1["kernels"] - c0["kernels"]
     for s in solvers:
         s.close()
     one = make(w["gammas"][0], None)
@@ -432,8 +437,13 @@ def run_batch32(steps: int, warmup: int, prec: int = 2):
     el1 = time.perf_counter() - t1
     one.close()
     torch.cuda.empty_cache()
-    return {"runs": len(solvers), "steps_per_run": steps, "steps_per_s": len(solvers) * steps / el,
+    member_steps = len(solvers) * steps
+    return {"runs": len(solvers), "steps_per_run": steps, "steps_per_s": member_steps / el,
             "single_run_steps_per_s": steps / el1, "gpu_launches": launches,
+            "kernels_per_member_step": launches / member_steps,
+            "graph_launches": c1["graphs"] - c0["graphs"],
+            "host_launch_calls_per_member_step": (c1["graphs"] - c0["graphs"]) / member_steps,
+            "form": "one captured graph per ensemble step (every run's whole step as a parallel branch)",
             "newton_per_step": sum(r["newton_its"] for rr in recs for r in rr) / (len(recs) * steps),
             "gmres_per_step": sum(r["gmres_its"] for rr in recs for r in rr) / (len(recs) * steps),
             "dt_cuts": sum(r["dt_cuts"] for rr in recs for r in rr), "factor_prec": PREC_NAME[prec]}
@@ -638,7 +648,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [1024, 1024], "subdomains": [64, 64], "overlap_per_side": 1,
                    "form": head_name, "guess": "learned network (safeguarded by phi^n and the extrapolation)",
-                   "timed_path": "GMRES cycles as CUDA graphs, no per-kernel events in the timed region",
+                   "timed_path": "every time step one CUDA graph launch (device-side Newton, GMRES and line-search "
+                                 "control), no per-kernel events in the timed region",
                    "l2": "inputs larger than L2 (factors 0.4-0.6 GB per apply, Krylov basis 0.25 GB)",
                    "replicas": world},
         "roofline": {"bound": "hbm", "kernel": "Schwarz apply (left-RAS banded triangular solves, chunked records)",
@@ -655,6 +666,7 @@ def main():
         "peaks": {"hbm_gbs": hbm, "fp32_tflops": FP32_PEAK_TFLOPS, "fp64_tflops": FP64_PEAK_TFLOPS},
         "clocks": head["clocks"],
         "gpu_launches": head["gpu_launches"],
+        "graph_launches": head["graph_launches"],
         "e2e": head.get("e2e"),
         "iterations": {"newton_per_step": head["newton_per_step"], "gmres_per_step": head["gmres_per_step"]},
         "errors_vs_oracle": head.get("errors_vs_oracle"),

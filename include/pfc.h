@@ -114,11 +114,17 @@ typedef struct {
      choice; 0 = one pass only.  Both sweeps have FP64-class accuracy (FP64 on
      the plain path, float-float on the mixed path; see gmres_fast_dots). */
   double gmres_reorth_eta;
-  /* 2D: run every GMRES cycle as one CUDA graph launch (default 1): a captured
-     conditional while loop over the Arnoldi iterations, one host synchronisation
-     per cycle instead of one per 3 iterations.  Used only on a stream other
-     than the legacy default stream and while pfc_profile is off; otherwise, or
-     if the graph cannot be built, the host-driven loop runs. */
+  /* 2D: run every time step as one CUDA graph launch (default 1).  The step --
+     Newton loop with its stop test, factor branch, GMRES restart loop, Arnoldi
+     loop, restart branch, backtracking line search and the commit of the new
+     field -- is captured once as nested conditional nodes whose conditions are
+     set by one-thread control kernels on the device; the host only writes the
+     step's inputs (dt, tolerances) and reads back one control block per step.
+     Used once the apply kernel is fixed (after the first factorisation when
+     apply_variant = -1), on a stream other than the legacy default stream and
+     while pfc_profile is off; otherwise, or if the graph cannot be built, the
+     host drives the same kernels, reading the control block after each
+     decision.  Both forms give identical results. */
   int use_graph;
   /* Factor reuse across time steps (extends the paper's reuse within a step,
      Sec. 5.2): 0 (default) factors the subdomain matrices at the first Newton
@@ -223,13 +229,21 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info);
 int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step);
 
 /* Batched form (independent runs, e.g. an ensemble of small grids): runs
-   pfc_run(states[i], nsteps, ...) for every i concurrently, one host thread per
-   state, so that states created on distinct streams overlap on the GPU.  The
-   paper runs one problem at a time; this entry point has no counterpart there.
+   pfc_run(states[i], nsteps, ...) for every i.  When every state is 2D with the
+   graph form on (use_graph), the phi^n guess, one device and streams of their
+   own, each ensemble step is one CUDA graph launch: a graph captured once that
+   holds every state's step graph as a parallel branch (each with its own dt,
+   convergence and line search), so the states' kernels overlap on the GPU with
+   no host work in between.  The first step of states that still have to tune
+   their apply kernel, and every other case, run on one host thread per state.
+   A state's failed step (PFC_ENEWTON, PFC_EGMRES) is retried alone with half the
+   time step (dt_halvings), as in pfc_run; a state that fails for good is left
+   unchanged by the later ensemble steps.  The paper runs one problem at a time;
+   this entry point has no counterpart there.
    per_step: count x nsteps records (state i at per_step[i * nsteps + n]) or
    NULL; status: count ints or NULL.  Returns PFC_OK when every run succeeded,
    else the status of the lowest-numbered failing state.  No two entries may be
-   the same state. */
+   the same state (PFC_EINVAL). */
 int pfc_run_batch(pfc_state** states, int count, int nsteps, pfc_step_info* per_step, int* status);
 
 /* F_d(phi^n) (Eq. freeenergy) and h^d sum phi^n. */
@@ -311,6 +325,11 @@ int pfc_profile_kernels(pfc_state* s, pfc_kernel_prof* out, int cap);
    far (all kinds, profiled or not). */
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches);
+
+/* Process-wide counts: kernels this library has run (a graph step's kernels are
+   counted from what its control kernels recorded) and CUDA graph launches (each a
+   whole time step of one state, or one step of a whole ensemble). */
+int pfc_launch_counts(long long* kernels, long long* graphs);
 
 /* Autotuner report (2D).  *apply_variant: the Schwarz apply kernel in use
    (pfc_params.apply_variant numbering).  apply_ms (optional, 6 floats): the

@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     nx = tail.ia->j + 1;
     w = tail.ia->w;
   }
+  if (tail.nx_dev) nx = *tail.nx_dev;  // graph mode: the count of a finished cycle
   extern __shared__ __align__(128) unsigned char smem[];
   const Ring rg = ring_at(smem);
   __shared__ double red[2][NT / 32];
@@ -540,9 +541,11 @@ int red_ctas(long long n) {
 
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     int dot) {
-  // groups of G vectors in y; about kSweepMinCtas CTAs per SM in all
-  const int gy = (nv + G - 1) / G;
+                     int dot, int nv_grid) {
+  // groups of G vectors in y; about kSweepMinCtas CTAs per SM in all.  The grid is sized for
+  // nv_grid vectors (>= nv): a sweep then splits the points over CTAs as the graph form's
+  // sweeps do (sized for the restart length), so both sum in the same order.
+  const int gy = (std::max(nv, nv_grid) + G - 1) / G;
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
   const dim3 grid(bx, gy);

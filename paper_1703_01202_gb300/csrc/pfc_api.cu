@@ -101,20 +101,29 @@ struct pfc_state {
   // ||F(phi^n)|| of the current step when a safeguarded guess was chosen (< 0: none)
   double ref_norm;
   int device;  // CUDA device current at pfc_create
-  // graph mode (2D): one captured GMRES cycle, a conditional while node over the Arnoldi iterations
-  pfc::IterArgs* ia;    // device
-  pfc::IterArgs* ia_h;  // pinned host copy of the host-set fields
-  cudaGraph_t graph;
-  cudaGraphExec_t gexec;
-  int graph_body;       // kernels in one iteration of the body
-  bool graph_failed;    // capture or instantiation failed once: keep the host-driven loop
+  // device-side control of a step and its graph form (2D): the whole step captured once
+  pfc::StepCtl* sc;     // device
+  pfc::StepCtl* sc_h;   // pinned host mirror
+  pfc::IterArgs* ia;    // Arnoldi iteration arguments (device): vectors of iteration j, q, 1/dt
+  pfc::IterArgs* ia2;   // the restart's J S -> W with this step's 1/dt (device)
+  pfc::StepHandles hs;  // conditional handles of the step graph
+  cudaStream_t cs[3];   // capture streams of the nested bodies (graph form)
+  cudaGraph_t sgraph;
+  cudaGraphExec_t sexec;
+  bool graph_failed;    // capture or instantiation failed once: keep the host-driven step
 };
 
 namespace pfc {
 namespace {
-long long g_launches = 0;  // host-side count; launches come from the calling thread
+long long g_launches = 0;        // host-side count; launches come from the calling thread
+thread_local bool g_paused = false;  // this thread is capturing a graph (nothing runs)
 }
-void count_launches(long long n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
+void count_launches(long long n) {
+  if (!g_paused) __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED);
+}
+void count_pause(bool on) { g_paused = on; }
+long long g_graph_launches = 0;  // graph launches (each a whole time step, or a whole ensemble step)
+void count_graph_launch() { __atomic_add_fetch(&g_graph_launches, 1, __ATOMIC_RELAXED); }
 long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 }  // namespace pfc
 
@@ -337,7 +346,7 @@ size_t basis_stride(long long N) { return ((size_t)N + 31) / 32 * 32 + 17 * 32; 
 
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs, order, X, Yb, mu, mut, smid, smidt;
+      tabs, feat, iargs, iargs2, sctl, order, X, Yb, mu, mut, smid, smidt;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -428,6 +437,8 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->status = L.take(sizeof(int) * 4);
   pl->tabs = L.take(sizeof(double*) * 2 * pfc::kMaxVecs);
   pl->iargs = L.take(sizeof(pfc::IterArgs));
+  pl->iargs2 = L.take(sizeof(pfc::IterArgs));
+  pl->sctl = L.take(sizeof(pfc::StepCtl));
   pl->order = L.take(sizeof(int) * (pl->nblocks + 16));
   pl->feat = d3 ? 0 : L.take(vec * 3);
   if (d3) {
@@ -541,8 +552,9 @@ int prof_end(pfc_state* s, int slot, int kind, int j, double bytes, double flops
   } while (0)
 
 // F, q at Phi (or at the trial point Phi + lam (S - mean S)); returns ||F||^2 on the device in red[slot].
+// dev (2D): 1/dt and the line-search step lam are read from the step's StepCtl on the device.
 int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, bool project, const double* phin,
-                  double idt, double* F, double* Pout, double* qout, int slot) {
+                  double idt, double* F, double* Pout, double* qout, int slot, bool dev = false) {
   int np = 0;
   int ps;
   PROF_BEGIN(ps);
@@ -552,7 +564,8 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
     double* muo = qout == s->q ? s->mu : s->mut;
     double* so = qout == s->q ? s->sm : s->smt;
     pfc::launch_residual2d(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, phin, idt, F, Pout, qout, s->partial,
-                           &np, s->st, mob, mob && qout ? muo : nullptr, mob && qout ? so : nullptr);
+                           &np, s->st, mob, mob && qout ? muo : nullptr, mob && qout ? so : nullptr,
+                           dev ? &s->sc->idt : nullptr, dev && S ? &s->sc->lam : nullptr);
   } else {
     const double* P = Pb;
     if (S) {  // the trial point is needed at neighbours: materialise it first
@@ -657,7 +670,8 @@ int tune_apply(pfc_state* s) {
   return PFC_OK;
 }
 
-int factor_blocks(pfc_state* s, const double* q, double idt) {
+// dev: 1/dt read from the step's StepCtl (a captured step graph).
+int factor_blocks(pfc_state* s, const double* q, double idt, bool dev = false) {
   if (s->p.mobility) {  // the mobility fields of q's iterate
     const bool trial = q == s->qt;
     s->fs.mob_mu = trial ? s->mut : s->mu;
@@ -677,7 +691,8 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
   int ps;
   PROF_BEGIN(ps);
   if (s->dim == 2)
-    pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st);
+    pfc::launch_factor2d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->fs, s->status_dev, s->st,
+                         dev ? &s->sc->idt : nullptr);
   else
     pfc::launch_factor3d(s->g, s->blocks_dev, s->nblocks, q, idt, s->lin_dev, s->r3, s->status_dev, s->st);
   PROF_END(ps, PFC_PROF_FACTOR, -1, s->factor_bytes, s->factor_flops);
@@ -697,276 +712,456 @@ int factor_blocks(pfc_state* s, const double* q, double idt) {
   return PFC_OK;
 }
 
-// Captures one GMRES cycle as a graph: a conditional while node whose body is one
-// Arnoldi iteration (iteration setup, Schwarz apply, JVP, the Gram-Schmidt
-// passes) and the loop test.  Every pointer and count that changes between
-// iterations or solves is read from s->ia, V_0 lives in Vbuf[0].  Returns false
-// (and leaves nothing captured) when the graph cannot be built.
-bool build_cycle_graph(pfc_state* s) {
-  const long long N = s->g.n;
-  const int m = s->p.gmres_restart;
-  const int passes = s->p.gmres_reorth_eta > 0.0 ? 2 : 1;
-  unsigned int* counter = reinterpret_cast<unsigned int*>(s->status_dev + 2);
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
-  cudaGraphConditionalHandle h;
-  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
-  bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
-  cudaGraphNodeParams cp = {};
-  cudaGraphNode_t node;
-  if (ok) {
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
-  }
-  // kernels of one body iteration: setup, apply, JVP, a multi-dot and a multi-axpy per pass, loop test
-  // (counted here rather than from the process-wide counter, which other threads also move)
-  const int body = 4 + 2 * passes + (s->fs.ras_kind != PFC_LEFT_RAS ? 1 : 0);
-  if (ok) ok = cudaStreamBeginCaptureToGraph(s->st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  if (ok) {
-    const double* v0 = s->Vbuf;
-    const int* reorth = &s->ctl->reorth;
-    const int* done = &s->ctl->done;  // a cycle that converged at its start runs the body once, all skipped
-    pfc::launch_iter_setup(s->ctl, s->vtab, s->ztab, s->ia, s->st);
-    precond(s, nullptr, nullptr, nullptr, done, s->ia);
-    jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
-    for (int pass = 0; pass < passes; ++pass) {
-      pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, counter, nullptr, s->ia};
-      td.err = s->status_dev + 1;
-      pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                           dot_mode(s));
-      pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, counter, nullptr, s->ia};
-      ta.err = s->status_dev + 1;
-      pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done,
-                            pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
-    }
-    pfc::launch_cycle_cond(s->ctl, m, h, s->st);
-    cudaGraph_t body = nullptr;
-    ok = cudaStreamEndCapture(s->st, &body) == cudaSuccess && cudaGetLastError() == cudaSuccess;
-  }
-  s->graph_body = body;
-  if (ok) pfc::count_launches(-(long long)body);  // the capture counted them once; replays count below
-  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    if (ge) cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-    return false;
-  }
-  s->graph = g;
-  s->gexec = ge;
-  return true;
+// ---------------------------------------------------------------- one time step
+// Every decision of a step is taken on the device by the control kernels of
+// newton.cu on the step's StepCtl (s->sc).  The emitters below queue the kernels of
+// each part of the step on s->st.  The host-driven form (step_host) reads StepCtl
+// back after each decision and runs the loops itself; the graph form captures the
+// same emitters once into the bodies of nested conditional nodes (Newton loop,
+// factor branch, GMRES restart loop, Arnoldi loop, restart branch, line-search
+// loop, commit branch), so that a whole step is one graph launch.  Both forms run
+// the same kernels in the same order on the same data.
+
+int read_ctl(pfc_state* s) { return sync_read(s, s->sc_h, s->sc, sizeof(pfc::StepCtl)); }
+
+unsigned int* ticket(pfc_state* s) { return reinterpret_cast<unsigned int*>(s->status_dev + 2); }
+
+// Factors of J(Phi_0) (Eq. Ak) at the first Newton iteration of a step, reused by the
+// later ones (Sec. 5.2).
+int emit_factor(pfc_state* s, double idt) {
+  int rc = factor_blocks(s, s->q, idt, s->dim == 2);
+  if (rc) return rc;
+  pfc::launch_factor_done(s->sc, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
 }
 
-// Right-preconditioned restarted GMRES for J S = -F, x0 = 0 (Eq. hjacobi).
-// V_0 = -F/||F||, Z_j = H^{-1} V_j, S = sum_j y_j Z_j.  Leaves sum(S) in red[9].
-int gmres(pfc_state* s, double idt, double fnorm, double tol, int* its_out) {
+// GMRES for J S = -F from S = 0 (Eq. hjacobi): S and the sums of S cleared, V_0 <- F
+// (scaled by -1/||F|| on the device), the cycle's tolerance and state.
+int emit_gmres_begin(pfc_state* s, int gm) {
+  pfc::launch_gmres_prep(s->S, s->red + 8, s->F, s->Vbuf, s->g.n, s->st);
+  pfc::launch_gmres_begin(s->sc, s->ctl, s->hs, gm, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+int gs_passes(const pfc_state* s) { return s->p.gmres_reorth_eta > 0.0 ? 2 : 1; }
+
+// Kernels of one Arnoldi iteration of the graph form.
+int arnoldi_body_kernels(const pfc_state* s) {
+  return 4 + 2 * gs_passes(s) + (s->fs.ras_kind != PFC_LEFT_RAS ? 1 : 0);
+}
+
+// One Arnoldi iteration (graph form): iteration setup, Schwarz apply, JVP, the
+// Gram-Schmidt passes and the loop test; the vectors of iteration j = its come from s->ia.
+void emit_arnoldi_body(pfc_state* s) {
+  const long long N = s->g.n;
+  const int m = s->p.gmres_restart;
+  const int* done = &s->ctl->done;  // a cycle that converged at its start runs the body once, all skipped
+  const int* reorth = &s->ctl->reorth;
+  const double* v0 = s->Vbuf;
+  pfc::launch_iter_setup(s->ctl, s->vtab, s->ztab, s->ia, s->st);
+  precond(s, nullptr, nullptr, nullptr, done, s->ia);
+  jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
+  for (int pass = 0; pass < gs_passes(s); ++pass) {
+    pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, ticket(s), nullptr, s->ia};
+    td.err = s->status_dev + 1;
+    pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
+                         dot_mode(s));
+    pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, ticket(s), nullptr, s->ia};
+    ta.err = s->status_dev + 1;
+    pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done, pass ? reorth : nullptr,
+                          ta, s->st, ff_sweeps(s));
+  }
+  pfc::launch_cycle_cond(s->ctl, m, s->hs.arnoldi, s->st);
+}
+
+// The Arnoldi iterations of one cycle driven by the host: iterations are queued a chunk at a
+// time; after each chunk the head of the control block is copied back asynchronously, and the
+// host waits for a chunk's head only once the next chunk is queued, so the GPU never idles on
+// the host.  A chunk queued after the cycle ended runs its kernels as immediate returns (the
+// done flag).  Basis V_0 = Vbuf, V_i = Vbuf + i vstride (s->vtab); Z_i = Zbuf + i vstride.
+int arnoldi_host(pfc_state* s, double idt) {
   const long long N = s->g.n;
   const int m = s->p.gmres_restart;
   const int* done = &s->ctl->done;
   const int* reorth = &s->ctl->reorth;
-  const double eta2 = s->p.gmres_reorth_eta * s->p.gmres_reorth_eta;
-  const int passes = eta2 > 0.0 ? 2 : 1;  // the second pass only exists with a DGKS threshold
-  unsigned int* counter = reinterpret_cast<unsigned int*>(s->status_dev + 2);  // last-CTA ticket
-  int total = 0;
-  CU(cudaMemsetAsync(s->S, 0, sizeof(double) * N, s->st));
-  CU(cudaMemsetAsync(s->red + 8, 0, 2 * sizeof(double), s->st));
-  // graph mode: 2D, a stream that can be captured, no per-apply event timing
-  bool graph = s->p.use_graph && s->dim == 2 && s->st != nullptr && !s->prof && !s->graph_failed;
-  if (graph && !s->gexec && !build_cycle_graph(s)) {
+  const double* v0 = s->Vbuf;
+  int j = 0;
+  const int chunk = 3;
+  int c = 0, pend = -1;  // chunks queued; buffer of the pending chunk
+  bool stop = false;
+  while (!stop) {
+    const int q0 = j, q1 = std::min(m, j + chunk);
+    const bool more = q0 < q1;
+    for (; j < q1; ++j) {
+      const double* vj = s->Vbuf + (size_t)j * s->vstride;
+      double* zj = s->Zbuf + (size_t)j * s->vstride;
+      double* w = s->Vbuf + (size_t)(j + 1) * s->vstride;
+      // (pfc_profile: apply, JVP and the first Gram-Schmidt pass are timed; the second pass
+      // runs only on the DGKS test, which the host does not see)
+      int ps;
+      PROF_BEGIN(ps);
+      precond(s, vj, &s->ctl->scale[j], zj, done);
+      PROF_END(ps, PFC_PROF_APPLY, j, s->apply_bytes, 0.0, apply_stored(s));
+      PROF_BEGIN(ps);
+      jvp(s, zj, s->q, idt, w, done);
+      PROF_END(ps, PFC_PROF_JVP, j, 24.0 * N);  // reads v, q; writes Jv
+      for (int pass = 0; pass < gs_passes(s); ++pass) {
+        pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, ticket(s), nullptr};
+        td.err = s->status_dev + 1;
+        if (pass == 0) PROF_BEGIN(ps);
+        pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
+                             dot_mode(s), m + 1);
+        if (pass == 0) PROF_END(ps, PFC_PROF_DOT, j, 8.0 * N * (j + 2));  // reads V_0..V_j and w
+        pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, ticket(s), nullptr};
+        ta.err = s->status_dev + 1;
+        if (pass == 0) PROF_BEGIN(ps);
+        pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
+                              pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
+        if (pass == 0) PROF_END(ps, PFC_PROF_AXPY, j, 8.0 * N * (j + 3));  // reads V_0..V_j, w; writes w
+      }
+    }
+    if (more) {
+      CU(cudaGetLastError());
+      CU(cudaMemcpyAsync(s->ctl_hb[c & 1], s->ctl, offsetof(GmresCtl, H), cudaMemcpyDeviceToHost, s->st));
+      CU(cudaEventRecord(s->ctl_ev[c & 1], s->st));
+    }
+    if (pend >= 0) {  // the chunk before this one: did the cycle end there?
+      CU(cudaEventSynchronize(s->ctl_ev[pend]));
+      if (s->ctl_hb[pend]->done) stop = true;
+    }
+    if (more) {
+      pend = c & 1;
+      ++c;
+    } else {
+      pend = -1;
+      stop = true;
+    }
+  }
+  // the cycle's final head (every queued kernel has finished after this)
+  int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
+  if (rc) return rc;
+  if (s->prof && (rc = prof_resolve(s, s->ctl_h->its))) return rc;
+  return PFC_OK;
+}
+
+// After a cycle: y from the rotated Hessenberg system, S += sum_j y_j Z_j over the cycle's
+// iterations (|S|^2 and sum S into red[8..9]), then converged / failed / restart.
+int emit_cycle_end(pfc_state* s, int gm) {
+  pfc::launch_gmres_solve(s->ctl, s->st);
+  pfc::Tail tsum{pfc::Tail::kSums, 0, 0, 0, s->ctl, ticket(s), s->red + 8};
+  tsum.err = s->status_dev + 1;
+  tsum.nx_dev = &s->ctl->its;
+  pfc::launch_multiaxpy(s->S, s->Zbuf, s->ztab, s->p.gmres_restart, s->ctl->y, 1.0, s->g.n, s->partial, nullptr,
+                        nullptr, tsum, s->st);
+  pfc::launch_cycle_decide(s->sc, s->ctl, s->hs, gm, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// Restart: r = -F - J S into W, ||r||^2 into red[10], V_0 <- r (scaled by 1/||r||).
+int emit_restart(pfc_state* s, double idt, int gm) {
+  const long long N = s->g.n;
+  if (gm)
+    jvp(s, nullptr, nullptr, 0.0, nullptr, nullptr, s->ia2);  // S -> W with this step's 1/dt
+  else
+    jvp(s, s->S, s->q, idt, s->W, nullptr);
+  pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
+  pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, ticket(s), s->red + 10};
+  tnrm.err = s->status_dev + 1;
+  pfc::launch_multidot(s->W, s->vtab, 1, s->W, N, s->partial, nullptr, nullptr, tnrm, s->st);
+  pfc::launch_gmres_restart(s->sc, s->ctl, s->red + 10, s->st);
+  pfc::CopyPairs cp{};
+  cp.src[0] = s->W;
+  cp.dst[0] = s->Vbuf;
+  cp.n = 1;
+  pfc::launch_copy_if_ok(s->sc, cp, N, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// One line-search trial Phi + lam (S - mean S) (Armijo backtracking on ||F||^2 / 2) and its decision.
+int emit_ls_trial(pfc_state* s, double lam, double idt, int gm) {
+  int rc = eval_residual(s, s->Phi, s->S, lam, s->p.mass_projection != 0, s->phin, idt, s->Ft, s->Pt, s->qt, 1,
+                         s->dim == 2);
+  if (rc) return rc;
+  pfc::launch_ls_decide(s->sc, s->red + 1, s->hs, gm, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// The accepted trial point becomes the Newton iterate (Phi, F, q and the mobility fields), then
+// the Newton stop test.
+int emit_accept(pfc_state* s, int gm) {
+  pfc::CopyPairs cp{};
+  cp.src[0] = s->Pt;
+  cp.dst[0] = s->Phi;
+  cp.src[1] = s->Ft;
+  cp.dst[1] = s->F;
+  cp.src[2] = s->qt;
+  cp.dst[2] = s->q;
+  cp.n = 3;
+  if (s->p.mobility) {
+    cp.src[3] = s->mut;
+    cp.dst[3] = s->mu;
+    cp.src[4] = s->smt;
+    cp.dst[4] = s->sm;
+    cp.n = 5;
+  }
+  pfc::launch_copy_if_ok(s->sc, cp, s->g.n, s->st);
+  pfc::launch_newton_next(s->sc, s->hs, gm, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// A converged step: phi^{n-1} <- phi^n, phi^n <- Phi, and the energy and mass of the new
+// phi^n (Eq. freeenergy; h^d sum phi) into red[4..5].
+int emit_commit(pfc_state* s) {
+  pfc::CopyPairs cp{};
+  cp.src[0] = s->phin;
+  cp.dst[0] = s->phinm1;
+  cp.src[1] = s->Phi;
+  cp.dst[1] = s->phin;
+  cp.n = 2;
+  pfc::launch_copy_if_ok(s->sc, cp, s->g.n, s->st);
+  int np = 0;
+  if (s->dim == 2)
+    pfc::launch_energy2d(s->g, s->phin, s->partial, &np, s->st);
+  else
+    pfc::launch_energy3d(s->g, s->phin, s->partial, &np, s->st);
+  pfc::launch_reduce(s->partial, 2, np, s->red + 4, s->st);
+  CU(cudaGetLastError());
+  return PFC_OK;
+}
+
+// One step driven by the host (3D, per-kernel profiling, the step that tunes the apply, no
+// capturable stream, or use_graph = 0): Newton from the guess in s->Phi.
+int step_host(pfc_state* s, double dt) {
+  const double idt = 1.0 / dt;
+  int rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->F, nullptr, s->q, 0, s->dim == 2);
+  if (rc) return rc;
+  pfc::launch_newton_begin(s->sc, s->red, s->ia, s->ia2, s->hs, 0, s->st);
+  if ((rc = read_ctl(s))) return rc;
+  const pfc::StepCtl* c = s->sc_h;
+  while (c->newton_go) {
+    if (c->factor_go && (rc = emit_factor(s, idt))) return rc;
+    if ((rc = emit_gmres_begin(s, 0)) || (rc = read_ctl(s))) return rc;
+    while (c->cycle_go) {
+      if ((rc = arnoldi_host(s, idt))) return rc;
+      if ((rc = emit_cycle_end(s, 0)) || (rc = read_ctl(s))) return rc;
+      if (c->restart_go && (rc = emit_restart(s, idt, 0))) return rc;
+    }
+    pfc::launch_gmres_end(s->sc, s->status_dev, s->hs, 0, s->st);
+    if ((rc = read_ctl(s))) return rc;
+    while (c->ls_go)
+      if ((rc = emit_ls_trial(s, c->lam, idt, 0)) || (rc = read_ctl(s))) return rc;
+    if ((rc = emit_accept(s, 0)) || (rc = read_ctl(s))) return rc;
+  }
+  pfc::launch_step_end(s->sc, s->hs, 0, s->st);
+  if ((rc = read_ctl(s))) return rc;
+  if (c->commit_go) rc = emit_commit(s);
+  return rc;
+}
+
+// ---- the graph form
+// A conditional handle on the graph being captured on st (the graph that will hold its node).
+bool new_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive || !g)
+    return false;
+  return cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+}
+
+// Adds a conditional node after the work captured so far on st; returns its body graph.
+bool add_cond(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive || !g)
+    return false;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &p) != cudaSuccess) return false;
+  if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return false;
+  *body = p.conditional.phGraph_out[0];
+  return true;
+}
+
+// Captures what `emit` queues into `body` on the helper stream cs (s->st is switched to cs
+// meanwhile, so that every emitter queues there).
+template <class F>
+bool capture_body(pfc_state* s, cudaGraph_t body, cudaStream_t cs, F emit) {
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return false;
+  cudaStream_t saved = s->st;
+  s->st = cs;
+  bool ok = emit();
+  s->st = saved;
+  cudaGraph_t out = nullptr;
+  ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && ok;
+  return ok;
+}
+
+// Queues the whole step of the graph form on s->st (which is being captured): every 1/dt
+// and line-search step is read from s->sc, every decision sets a conditional handle.
+bool emit_step_graph(pfc_state* s) {
+  pfc::StepHandles& h = s->hs;
+  const int m = s->p.gmres_restart;
+  cudaStream_t* cs = s->cs;
+  if (!new_handle(s->st, &h.newton) || !new_handle(s->st, &h.commit)) return false;
+  if (eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, 1.0, s->F, nullptr, s->q, 0, true)) return false;
+  pfc::launch_newton_begin(s->sc, s->red, s->ia, s->ia2, h, 1, s->st);
+  cudaGraph_t newton_body;
+  bool ok = add_cond(s->st, h.newton, cudaGraphCondTypeWhile, &newton_body) &&
+            capture_body(s, newton_body, cs[0], [&] {
+              if (!new_handle(s->st, &h.factor) || !new_handle(s->st, &h.cycle) || !new_handle(s->st, &h.ls))
+                return false;
+              pfc::launch_set_factor_cond(s->sc, h, 1, s->st);
+              cudaGraph_t factor_body, cycle_body, ls_body;
+              bool k = add_cond(s->st, h.factor, cudaGraphCondTypeIf, &factor_body) &&
+                       capture_body(s, factor_body, cs[1], [&] { return emit_factor(s, 1.0) == PFC_OK; });
+              k = k && emit_gmres_begin(s, 1) == PFC_OK;
+              k = k && add_cond(s->st, h.cycle, cudaGraphCondTypeWhile, &cycle_body) &&
+                  capture_body(s, cycle_body, cs[1], [&] {
+                    if (!new_handle(s->st, &h.arnoldi) || !new_handle(s->st, &h.restart)) return false;
+                    pfc::launch_arnoldi_begin(s->ctl, m, h, s->st);
+                    cudaGraph_t arnoldi_body, restart_body;
+                    bool q = add_cond(s->st, h.arnoldi, cudaGraphCondTypeWhile, &arnoldi_body) &&
+                             capture_body(s, arnoldi_body, cs[2], [&] {
+                               emit_arnoldi_body(s);
+                               return cudaGetLastError() == cudaSuccess;
+                             });
+                    q = q && emit_cycle_end(s, 1) == PFC_OK;
+                    q = q && add_cond(s->st, h.restart, cudaGraphCondTypeIf, &restart_body) &&
+                        capture_body(s, restart_body, cs[2], [&] { return emit_restart(s, 1.0, 1) == PFC_OK; });
+                    return q;
+                  });
+              pfc::launch_gmres_end(s->sc, s->status_dev, h, 1, s->st);
+              k = k && add_cond(s->st, h.ls, cudaGraphCondTypeWhile, &ls_body) &&
+                  capture_body(s, ls_body, cs[1], [&] { return emit_ls_trial(s, 1.0, 1.0, 1) == PFC_OK; });
+              k = k && emit_accept(s, 1) == PFC_OK;
+              return k;
+            });
+  pfc::launch_step_end(s->sc, h, 1, s->st);
+  cudaGraph_t commit_body;
+  ok = ok && add_cond(s->st, h.commit, cudaGraphCondTypeIf, &commit_body) &&
+       capture_body(s, commit_body, cs[0], [&] { return emit_commit(s) == PFC_OK; });
+  return ok && cudaGetLastError() == cudaSuccess;
+}
+
+// Kernels a graph step ran, from what the step's control kernels counted.
+long long graph_step_launches(const pfc_state* s, const pfc::StepCtl& c) {
+  const int m = c.m;
+  const bool chunked = s->dim == 2 && s->fs.variant == pfc::kChunkedVariant;
+  long long n = 4 + (c.commit_go ? 3 : 0);               // residual, reduce, begin, end; commit
+  n += 6LL * m;                                          // per Newton iteration
+  n += (long long)c.n_factor * (2 + (chunked ? 1 : 0));  // factor (+ records), done
+  n += 4LL * c.n_cycles + 5LL * c.n_restarts + 3LL * c.n_trials;
+  n += (long long)c.gm_total * arnoldi_body_kernels(s);
+  return n;
+}
+
+bool graph_ready(const pfc_state* s) {
+  return s->p.use_graph && s->dim == 2 && s->st != nullptr && !s->prof && !s->graph_failed &&
+         (s->tuned || s->p.apply_variant >= 0);
+}
+
+// Captures s's step graph (helper streams created on first use); false if it cannot be built.
+bool build_step_graph(pfc_state* s) {
+  for (cudaStream_t& c : s->cs)
+    if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) return false;
+  pfc::count_pause(true);  // the capture launches nothing; replays are counted from StepCtl
+  bool ok = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) ok = emit_step_graph(s);
+  cudaGraph_t g = nullptr;
+  ok = cudaStreamEndCapture(s->st, &g) == cudaSuccess && ok && g;
+  pfc::count_pause(false);
+  cudaGraphExec_t ge = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return false;
+  }
+  s->sgraph = g;
+  s->sexec = ge;
+  return true;
+}
+
+// The step's inputs in StepCtl: 1/dt, the stop-test reference, the tolerances, refactor.
+int write_ctl_inputs(pfc_state* s, double dt, bool refactor) {
+  pfc::StepCtl* c = s->sc_h;
+  const pfc_params& p = s->p;
+  c->idt = 1.0 / dt;
+  c->ref_norm = s->ref_norm;
+  c->newton_rtol = p.newton_rtol;
+  c->newton_atol = p.newton_atol;
+  c->gmres_rtol = p.gmres_rtol;
+  c->gmres_atol = p.gmres_atol;
+  c->ls_alpha = p.ls_alpha;
+  c->reorth_eta2 = p.gmres_reorth_eta * p.gmres_reorth_eta;
+  c->newton_max_it = p.newton_max_it;
+  c->ls_max_cuts = p.ls_max_cuts;
+  c->gmres_max_it = p.gmres_max_it;
+  c->refactor = refactor ? 1 : 0;
+  CU(cudaMemcpyAsync(s->sc, c, offsetof(pfc::StepCtl, r0), cudaMemcpyHostToDevice, s->st));
+  return PFC_OK;
+}
+
+// Whether this step factors the subdomain matrices (or reuses those of an earlier step at the
+// same dt, reuse_factor).
+bool needs_factor(pfc_state* s, double dt) {
+  const pfc_params& p = s->p;
+  return !(p.reuse_factor > 0 && s->factors_ok && s->factor_age < p.reuse_factor &&
+           std::fabs(dt / s->factor_dt - 1.0) <= 1e-3);
+}
+
+// One Newton solve from the guess in s->Phi, by the graph or by the host; on success phi^n and
+// phi^{n-1} have been advanced on the device and red[4..5] hold E and M of the new phi^n.
+int newton(pfc_state* s, double dt, pfc_step_info* info) {
+  const bool refactor = needs_factor(s, dt);
+  int rc = write_ctl_inputs(s, dt, refactor);
+  if (rc) return rc;
+  bool graph = graph_ready(s);
+  if (graph && !s->sexec && !build_step_graph(s)) {
     s->graph_failed = true;
     graph = false;
   }
   if (graph) {
-    s->ia_h->q = s->q;
-    s->ia_h->idt = idt;
-    s->ia_h->mu = s->mu;
-    s->ia_h->sm = s->sm;
-    CU(cudaMemcpyAsync(s->ia, s->ia_h, sizeof(pfc::IterArgs), cudaMemcpyHostToDevice, s->st));
+    CU(cudaGraphLaunch(s->sexec, s->st));
+    pfc::count_graph_launch();
+    CU(cudaMemcpyAsync(s->red_h + 4, s->red + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if ((rc = read_ctl(s))) return rc;
+    pfc::count_launches(graph_step_launches(s, *s->sc_h));
+  } else {
+    if ((rc = step_host(s, dt))) return rc;
+    if (s->sc_h->commit_go && (rc = sync_read(s, s->red_h + 4, s->red + 4, 2 * sizeof(double)))) return rc;
   }
-  // first cycle: V_0 = F scaled by -1/||F||
-  const double* v0 = s->F;
-  if (graph) {
-    CU(cudaMemcpyAsync(s->Vbuf, s->F, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
-    v0 = s->Vbuf;
+  const pfc::StepCtl& c = *s->sc_h;
+  if (refactor && c.n_factor > 0) {  // factors of this dt, reusable while it lasts
+    s->factors_ok = c.status != PFC_ESINGULAR;
+    s->factor_dt = dt;
+    s->factor_age = 0;
+  } else if (!refactor) {
+    ++s->factor_age;
   }
-  double f2 = fnorm * fnorm;
-  CU(cudaMemcpyAsync(s->red + 10, &f2, sizeof(double), cudaMemcpyHostToDevice, s->st));
-  pfc::launch_gmres_init(s->ctl, s->red + 10, -1.0, tol, eta2, s->st);
-  while (true) {
-    if (graph) {  // the whole cycle: one graph launch, one host synchronisation
-      CU(cudaGraphLaunch(s->gexec, s->st));
-      int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
-      if (rc) return rc;
-      pfc::count_launches((long long)s->graph_body * std::max(1, s->ctl_h->its));
-    }
-    // basis V_0 = v0, V_i = Vbuf + i vstride (pointer table s->vtab); Z_i = Zbuf + i vstride (s->ztab)
-    // Host loop: iterations are queued a chunk at a time; after each chunk the head of the control
-    // block is copied back asynchronously, and the host waits for a chunk's head only once the next
-    // chunk is queued, so the GPU never idles on the host.  A chunk queued after the cycle ended runs
-    // its kernels as immediate returns (the done flag).
-    int j = graph ? m : 0;
-    const int chunk = 3;
-    int c = 0, pend = -1;  // chunks queued; buffer of the pending chunk
-    bool stop = graph;
-    while (!stop) {
-      const int q0 = j, q1 = std::min(m, j + chunk);
-      const bool more = q0 < q1;
-      for (; j < q1; ++j) {
-        const double* vj = j == 0 ? v0 : s->Vbuf + (size_t)j * s->vstride;
-        double* zj = s->Zbuf + (size_t)j * s->vstride;
-        double* w = s->Vbuf + (size_t)(j + 1) * s->vstride;
-        // (pfc_profile: apply, JVP and the first Gram-Schmidt pass are timed; the second pass
-        // runs only on the DGKS test, which the host does not see)
-        int ps;
-        PROF_BEGIN(ps);
-        precond(s, vj, &s->ctl->scale[j], zj, done);
-        PROF_END(ps, PFC_PROF_APPLY, j, s->apply_bytes, 0.0, apply_stored(s));
-        PROF_BEGIN(ps);
-        jvp(s, zj, s->q, idt, w, done);
-        PROF_END(ps, PFC_PROF_JVP, j, 24.0 * N);  // reads v, q; writes Jv
-        for (int pass = 0; pass < passes; ++pass) {  // Gram-Schmidt pass; the second only on the DGKS test
-          pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, counter, nullptr};
-          td.err = s->status_dev + 1;
-          if (pass == 0) PROF_BEGIN(ps);
-          pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                               dot_mode(s));
-          if (pass == 0) PROF_END(ps, PFC_PROF_DOT, j, 8.0 * N * (j + 2));  // reads V_0..V_j and w
-          pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, counter, nullptr};
-          ta.err = s->status_dev + 1;
-          if (pass == 0) PROF_BEGIN(ps);
-          pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
-                                pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
-          if (pass == 0) PROF_END(ps, PFC_PROF_AXPY, j, 8.0 * N * (j + 3));  // reads V_0..V_j, w; writes w
-        }
-      }
-      if (more) {
-        CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(s->ctl_hb[c & 1], s->ctl, offsetof(GmresCtl, H), cudaMemcpyDeviceToHost, s->st));
-        CU(cudaEventRecord(s->ctl_ev[c & 1], s->st));
-      }
-      if (pend >= 0) {  // the chunk before this one: did the cycle end there?
-        CU(cudaEventSynchronize(s->ctl_ev[pend]));
-        if (s->ctl_hb[pend]->done) stop = true;
-      }
-      if (more) {
-        pend = c & 1;
-        ++c;
-      } else {
-        pend = -1;
-        stop = true;
-      }
-    }
-    if (!graph) {  // the cycle's final head (every queued kernel has finished after this)
-      int rc = sync_read(s, s->ctl_h, s->ctl, offsetof(GmresCtl, H));
-      if (rc) return rc;
-      if (s->prof && (rc = prof_resolve(s, s->ctl_h->its))) return rc;
-    }
-    const int its = s->ctl_h->its;
-    total += its;
-    if (its > 0) {
-      pfc::launch_gmres_solve(s->ctl, s->st);
-      // red[8] = |S|^2, red[9] = sum S
-      pfc::Tail tsum{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 8};
-      tsum.err = s->status_dev + 1;
-      pfc::launch_multiaxpy(s->S, s->Zbuf, s->ztab, its, s->ctl->y, 1.0, N, s->partial, nullptr, nullptr, tsum,
-                            s->st);
-      CU(cudaGetLastError());
-    }
-    const double est = s->ctl_h->est;
-    if (!(est == est)) return PFC_ENAN;
-    if (est <= s->ctl_h->tol || s->ctl_h->breakdown) break;
-    if (total >= s->p.gmres_max_it) {
-      *its_out = total;
-      return PFC_EGMRES;
-    }
-    // restart: r = -F - J S
-    jvp(s, s->S, s->q, idt, s->W, nullptr);
-    pfc::launch_axpby(s->W, s->F, -1.0, -1.0, N, s->st);
-    pfc::Tail tnrm{pfc::Tail::kSums, 0, 0, 0, s->ctl, counter, s->red + 10};
-    tnrm.err = s->status_dev + 1;
-    pfc::launch_multidot(s->W, s->vtab, 1, s->W, N, s->partial, nullptr, nullptr, tnrm, s->st);
-    pfc::launch_gmres_init(s->ctl, s->red + 10, 1.0, tol, eta2, s->st);
-    v0 = s->W;
-    if (graph) {
-      CU(cudaMemcpyAsync(s->Vbuf, s->W, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
-      v0 = s->Vbuf;
-    }
-    CU(cudaGetLastError());
-  }
-  *its_out = total;
-  return PFC_OK;
-}
-
-// One Newton solve of F(Phi) = 0 from the initial guess in s->Phi.  On success s->Phi holds phi^{n+1}.
-int newton(pfc_state* s, double dt, pfc_step_info* info) {
-  const double idt = 1.0 / dt;
-  const pfc_params& p = s->p;
-  int rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->F, nullptr, s->q, 0);
-  if (rc) return rc;
-  if ((rc = sync_read(s, s->red_h, s->red, sizeof(double)))) return rc;
-  const double r0 = std::sqrt(s->red_h[0]);
-  if (!(r0 == r0) || std::isinf(r0)) return PFC_ENAN;
-  // the plain method's tolerance (relative to ||F(phi^n)||) also for other initial guesses
-  const double target = std::max(p.newton_rtol * (s->ref_norm >= 0.0 ? s->ref_norm : r0), p.newton_atol);
-  double rnorm = r0;
-  info->res_norm0 = r0;
-  int m = 0, gm_total = 0, cuts_total = 0;
-  // factors of J(Phi_0) reused by every Newton iteration of the step, and (reuse_factor) by up to
-  // that many further steps at the same dt
-  bool factored = p.reuse_factor > 0 && s->factors_ok && s->factor_age < p.reuse_factor &&
-                  std::fabs(dt / s->factor_dt - 1.0) <= 1e-3;
-  if (factored) ++s->factor_age;
-  while (rnorm > target && m < p.newton_max_it) {
-    if (!factored) {
-      s->factors_ok = false;
-      if ((rc = factor_blocks(s, s->q, idt))) return rc;
-      factored = true;
-      s->factors_ok = true;
-      s->factor_dt = dt;
-      s->factor_age = 0;
-    }
-    int its = 0;
-    rc = gmres(s, idt, rnorm, std::max(p.gmres_rtol * rnorm, p.gmres_atol), &its);
-    gm_total += its;
-    if (rc) {
-      info->gmres_its = gm_total;
-      return rc;
-    }
-    if ((rc = sync_read(s, s->status_h, s->status_dev, 2 * sizeof(int)))) return rc;
-    if (s->status_h[0]) return s->status_h[0];
-    if (s->status_h[1]) return s->status_h[1];
-    // backtracking line search on f = ||F||^2 / 2 (Armijo, quadratic model)
-    const double f0 = 0.5 * rnorm * rnorm;
-    double lam = 1.0, ft = 0.0;
-    for (int cut = 0;; ++cut) {
-      if ((rc = eval_residual(s, s->Phi, s->S, lam, p.mass_projection != 0, s->phin, idt, s->Ft, s->Pt, s->qt, 1)))
-        return rc;
-      if ((rc = sync_read(s, s->red_h, s->red, 2 * sizeof(double)))) return rc;
-      ft = 0.5 * s->red_h[1];
-      if (!(ft == ft) || std::isinf(ft)) return PFC_ENAN;
-      if (ft <= (1.0 - 2.0 * p.ls_alpha * lam) * f0 || cut == p.ls_max_cuts) break;
-      const double lq = lam * lam * f0 / (ft - f0 + 2.0 * lam * f0);
-      lam = std::min(std::max(lq, 0.1 * lam), 0.5 * lam);
-      ++cuts_total;
-    }
-    std::swap(s->Phi, s->Pt);
-    std::swap(s->F, s->Ft);
-    std::swap(s->q, s->qt);
-    std::swap(s->mu, s->mut);
-    std::swap(s->sm, s->smt);
-    rnorm = std::sqrt(2.0 * ft);
-    ++m;
-  }
-  info->newton_its = m;
-  info->gmres_its = gm_total;
-  info->ls_cuts = cuts_total;
-  info->res_norm = rnorm;
-  if (rnorm > target) return PFC_ENEWTON;
-  return PFC_OK;
+  info->newton_its = c.m;
+  info->gmres_its = c.gm_total;
+  info->ls_cuts = c.cuts_total;
+  info->res_norm0 = c.r0;
+  info->res_norm = c.rnorm;
+  return c.status;
 }
 
 int energy_mass(pfc_state* s, const double* phi, double* E, double* M);
@@ -1007,8 +1202,164 @@ int safeguarded_guess(pfc_state* s, double dt, bool learned, int* used) {
     *used = PFC_GUESS_PREV;
   }
   if (rl == rl && rl < best) *used = PFC_GUESS_LEARNED;
-  if (*used == PFC_GUESS_LEARNED) std::swap(s->Phi, s->Pt);
+  if (*used == PFC_GUESS_LEARNED) CU(cudaMemcpyAsync(s->Phi, s->Pt, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
   if (*used == PFC_GUESS_PREV) CU(cudaMemcpyAsync(s->Phi, s->phin, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->st));
+  return PFC_OK;
+}
+
+// ---- batched steps of independent states (pfc_run_batch): one captured graph holds every
+// state's step graph as a parallel branch, so one graph launch steps the whole ensemble.
+struct BatchGraph {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+};
+
+// States that can share a batch graph: 2D, graph form on, the paper's phi^n guess, one device,
+// distinct streams other than the legacy default stream.
+bool batch_graph_ok(pfc_state** states, int count) {
+  if (count < 2) return false;
+  for (int i = 0; i < count; ++i) {
+    const pfc_state* s = states[i];
+    if (s->dim != 2 || !s->p.use_graph || s->st == nullptr || s->prof || s->graph_failed ||
+        s->p.guess != PFC_GUESS_PREV || s->device != states[0]->device)
+      return false;
+    for (int k = 0; k < i; ++k)
+      if (states[k]->st == s->st) return false;
+  }
+  return true;
+}
+
+bool all_graph_ready(pfc_state** states, int count, const std::vector<int>& rc) {
+  for (int i = 0; i < count; ++i)
+    if (rc[i] == PFC_OK && !graph_ready(states[i])) return false;
+  return true;
+}
+
+void destroy_batch_graph(BatchGraph* b) {
+  if (b->ge) cudaGraphExecDestroy(b->ge);
+  if (b->g) cudaGraphDestroy(b->g);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->st) cudaStreamDestroy(b->st);
+  *b = BatchGraph();
+}
+
+// Captures every state's step into one graph: the batch stream forks into each state's stream,
+// which records its step (nested bodies on its own helper streams), and joins back.
+int build_batch_graph(pfc_state** states, int count, BatchGraph* b) {
+  CU(cudaSetDevice(states[0]->device));
+  CU(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  b->join.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    CU(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+    CU(cudaStreamSynchronize(states[i]->st));
+    for (cudaStream_t& c : states[i]->cs)
+      if (!c) CU(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  }
+  pfc::count_pause(true);
+  bool ok = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess &&
+            cudaEventRecord(b->fork, b->st) == cudaSuccess;
+  for (int i = 0; i < count && ok; ++i) {
+    pfc_state* s = states[i];
+    ok = cudaStreamWaitEvent(s->st, b->fork, 0) == cudaSuccess && emit_step_graph(s) &&
+         cudaEventRecord(b->join[i], s->st) == cudaSuccess && cudaStreamWaitEvent(b->st, b->join[i], 0) == cudaSuccess;
+  }
+  cudaGraph_t g = nullptr;
+  ok = cudaStreamEndCapture(b->st, &g) == cudaSuccess && ok && g;
+  pfc::count_pause(false);
+  b->g = g;
+  if (ok) ok = cudaGraphInstantiate(&b->ge, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return PFC_ECUDA;
+  }
+  return PFC_OK;
+}
+
+// One step of every live state with one graph launch.  A state whose step fails with
+// PFC_ENEWTON / PFC_EGMRES is retried alone with half the time step (dt_halvings), as pfc_run
+// does; a state that failed for good keeps its branch in the graph with newton_max_it = 0,
+// which leaves its fields unchanged.  Records go to rec[i * stride].
+int batch_step(pfc_state** states, int count, BatchGraph* b, std::vector<int>& rc, pfc_step_info* rec, int stride) {
+  std::vector<double> dts(count, 0.0);
+  std::vector<char> refac(count, 0);
+  for (int i = 0; i < count; ++i) {
+    pfc_state* s = states[i];
+    pfc_next_dt(s, &dts[i]);
+    s->ref_norm = -1.0;
+    refac[i] = needs_factor(s, dts[i]);
+    pfc::StepCtl* c = s->sc_h;
+    c->idt = 1.0 / dts[i];
+    c->ref_norm = -1.0;
+    c->newton_rtol = s->p.newton_rtol;
+    c->newton_atol = s->p.newton_atol;
+    c->gmres_rtol = s->p.gmres_rtol;
+    c->gmres_atol = s->p.gmres_atol;
+    c->ls_alpha = s->p.ls_alpha;
+    c->reorth_eta2 = s->p.gmres_reorth_eta * s->p.gmres_reorth_eta;
+    c->newton_max_it = rc[i] == PFC_OK ? s->p.newton_max_it : 0;
+    c->ls_max_cuts = s->p.ls_max_cuts;
+    c->gmres_max_it = s->p.gmres_max_it;
+    c->refactor = refac[i];
+    CU(cudaMemcpyAsync(s->sc, c, offsetof(pfc::StepCtl, r0), cudaMemcpyHostToDevice, b->st));
+    CU(cudaMemcpyAsync(s->Phi, s->phin, sizeof(double) * s->g.n, cudaMemcpyDeviceToDevice, b->st));  // Phi_0 = phi^n
+  }
+  CU(cudaGraphLaunch(b->ge, b->st));
+  pfc::count_graph_launch();
+  for (int i = 0; i < count; ++i) {
+    pfc_state* s = states[i];
+    CU(cudaMemcpyAsync(s->sc_h, s->sc, sizeof(pfc::StepCtl), cudaMemcpyDeviceToHost, b->st));
+    CU(cudaMemcpyAsync(s->red_h + 4, s->red + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+  }
+  CU(cudaStreamSynchronize(b->st));
+  for (int i = 0; i < count; ++i) {
+    if (rc[i] != PFC_OK) continue;
+    pfc_state* s = states[i];
+    const pfc::StepCtl& c = *s->sc_h;
+    pfc::count_launches(graph_step_launches(s, c));
+    if (refac[i] && c.n_factor > 0) {
+      s->factors_ok = c.status != PFC_ESINGULAR;
+      s->factor_dt = dts[i];
+      s->factor_age = 0;
+    } else if (!refac[i]) {
+      ++s->factor_age;
+    }
+    pfc_step_info info{};
+    info.dt = dts[i];
+    info.guess_used = PFC_GUESS_PREV;
+    info.newton_its = c.m;
+    info.gmres_its = c.gm_total;
+    info.ls_cuts = c.cuts_total;
+    info.res_norm0 = c.r0;
+    info.res_norm = c.rnorm;
+    int st = c.status;
+    if (st == PFC_OK) {
+      const double E = s->red_h[4] * s->g.hd;
+      s->E_nm1 = s->E_n;
+      s->E_n = E;
+      s->have_Em1 = true;
+      s->dt_prev = dts[i];
+      s->have_prev_dt = true;
+      info.energy = E;
+      info.mass = s->red_h[5] * s->g.hd;
+    }
+    int cuts = 0;
+    double dt = dts[i];
+    while ((st == PFC_ENEWTON || st == PFC_EGMRES) && cuts < s->p.dt_halvings) {  // retry alone with dt / 2
+      dt *= 0.5;
+      ++cuts;
+      st = pfc_step(s, dt, &info);
+    }
+    info.status = st;
+    info.dt_cuts = cuts;
+    if (rec) rec[(size_t)i * stride] = info;
+    rc[i] = st;
+  }
   return PFC_OK;
 }
 
@@ -1188,6 +1539,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->status_dev = (int*)at(pl.status);
   s->feat = g->dim == 2 ? (double*)at(pl.feat) : nullptr;
   s->ia = (pfc::IterArgs*)at(pl.iargs);
+  s->ia2 = (pfc::IterArgs*)at(pl.iargs2);
+  s->sc = (pfc::StepCtl*)at(pl.sctl);
   s->fs.order = (const int*)at(pl.order);
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&s->ctl_hb[0], sizeof(GmresCtl)) != cudaSuccess ||
@@ -1196,7 +1549,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
       cudaEventCreateWithFlags(&s->ctl_ev[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost((void**)&s->red_h, 16 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&s->status_h, 4 * sizeof(int)) != cudaSuccess ||
-      cudaMallocHost((void**)&s->ia_h, sizeof(pfc::IterArgs)) != cudaSuccess) {
+      cudaMallocHost((void**)&s->sc_h, sizeof(pfc::StepCtl)) != cudaSuccess) {
     pfc_destroy(s);
     return PFC_ECUDA;
   }
@@ -1313,7 +1666,17 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   std::vector<const double*> tabs(2 * pfc::kMaxVecs, nullptr);
   for (int i = 0; i <= p->gmres_restart; ++i) tabs[i] = s->Vbuf + (size_t)i * s->vstride;
   for (int i = 0; i < p->gmres_restart; ++i) tabs[pfc::kMaxVecs + i] = s->Zbuf + (size_t)i * s->vstride;
-  if (cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
+  // iteration arguments whose pointers never change (q, the mobility fields; the restart's S -> W)
+  pfc::IterArgs ia0{}, ia20{};
+  ia0.q = ia20.q = s->q;
+  ia0.mu = ia20.mu = s->mu;
+  ia0.sm = ia20.sm = s->sm;
+  ia20.z = s->S;
+  ia20.w = s->W;
+  if (cudaMemcpyAsync(s->ia, &ia0, sizeof ia0, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemcpyAsync(s->ia2, &ia20, sizeof ia20, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+      cudaMemsetAsync(s->sc, 0, sizeof(pfc::StepCtl), s->st) != cudaSuccess ||
+      cudaMemcpyAsync(s->blocks_dev, blocks.data(), sizeof(BlockDesc) * blocks.size(), cudaMemcpyHostToDevice,
                       s->st) != cudaSuccess ||
       cudaMemcpyAsync((void*)s->fs.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, s->st) !=
           cudaSuccess ||
@@ -1335,7 +1698,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
 int pfc_get_tuning(const pfc_state* s, int* apply_variant, float* apply_ms, int* graph) {
   if (!s || !apply_variant) return PFC_EINVAL;
   *apply_variant = s->fs.variant;
-  if (graph) *graph = s->gexec != nullptr;
+  if (graph) *graph = s->sexec != nullptr;
   if (apply_ms)
     for (int v = 0; v < pfc::kApplyVariants; ++v) apply_ms[v] = s->tune_ms[v];
   return PFC_OK;
@@ -1351,9 +1714,11 @@ void pfc_destroy(pfc_state* s) {
   }
   if (s->red_h) cudaFreeHost(s->red_h);
   if (s->status_h) cudaFreeHost(s->status_h);
-  if (s->ia_h) cudaFreeHost(s->ia_h);
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->sc_h) cudaFreeHost(s->sc_h);
+  if (s->sexec) cudaGraphExecDestroy(s->sexec);
+  if (s->sgraph) cudaGraphDestroy(s->sgraph);
+  for (cudaStream_t c : s->cs)
+    if (c) cudaStreamDestroy(c);
   delete s;
 }
 
@@ -1477,6 +1842,11 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
     CU(cudaMemcpyAsync(s->Phi, s->phin, b, cudaMemcpyDeviceToDevice, s->st));
   }
   CU(cudaGetLastError());
+  if (!s->have_E) {  // E^n of the first field, for the time-step controller
+    if ((rc = energy_mass(s, s->phin, &s->E_n, nullptr))) return rc;
+    s->have_E = true;
+  }
+  // Newton on the device; a converged step also moves phi^n to phi^{n-1} and phi^{n+1} to phi^n
   rc = newton(s, dt, &info);
   s->have_user_guess = false;
   if (rc) {
@@ -1484,17 +1854,7 @@ int pfc_step(pfc_state* s, double dt, pfc_step_info* info_out) {
     if (info_out) *info_out = info;
     return rc;
   }
-  if (!s->have_E) {
-    if ((rc = energy_mass(s, s->phin, &s->E_n, nullptr))) return rc;
-    s->have_E = true;
-  }
-  // accept: phi^{n-1} <- phi^n, phi^n <- Phi
-  double* old = s->phinm1;
-  s->phinm1 = s->phin;
-  s->phin = s->Phi;
-  s->Phi = old;
-  double E = 0.0, M = 0.0;
-  if ((rc = energy_mass(s, s->phin, &E, &M))) return rc;
+  const double E = s->red_h[4] * s->g.hd, M = s->red_h[5] * s->g.hd;
   s->E_nm1 = s->E_n;
   s->E_n = E;
   s->have_Em1 = true;
@@ -1571,6 +1931,12 @@ int pfc_profile_kernels(pfc_state* s, pfc_kernel_prof* out, int cap) {
   return PFC_OK;
 }
 
+int pfc_launch_counts(long long* kernels, long long* graphs) {
+  if (kernels) *kernels = pfc::launches_so_far();
+  if (graphs) *graphs = __atomic_load_n(&pfc::g_graph_launches, __ATOMIC_RELAXED);
+  return PFC_OK;
+}
+
 int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, double* apply_bytes,
                      long long* kernel_launches) {
   if (!s) return PFC_EINVAL;
@@ -1609,20 +1975,50 @@ int pfc_run(pfc_state* s, int nsteps, pfc_step_info* per_step) {
 
 int pfc_run_batch(pfc_state** states, int count, int nsteps, pfc_step_info* per_step, int* status) {
   if (!states || count < 1 || nsteps < 0) return PFC_EINVAL;
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
     if (!states[i]) return PFC_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (states[k] == states[i]) return PFC_EINVAL;
+  }
   std::vector<int> rc(count, PFC_OK);
-  std::vector<std::thread> pool;
-  pool.reserve(count);
-  for (int i = 0; i < count; ++i)
-    pool.emplace_back([&, i]() {
-      if (cudaSetDevice(states[i]->device) != cudaSuccess) {
-        rc[i] = PFC_ECUDA;
-        return;
+  int n = 0;
+  // steps of every live state on host threads (one per state, each on its state's stream); the
+  // batch graph takes over once every state can run its step as a graph
+  auto threaded_steps = [&](int k) {
+    std::vector<std::thread> pool;
+    pool.reserve(count);
+    for (int i = 0; i < count; ++i)
+      pool.emplace_back([&, i]() {
+        if (rc[i] != PFC_OK) return;
+        if (cudaSetDevice(states[i]->device) != cudaSuccess) {
+          rc[i] = PFC_ECUDA;
+          return;
+        }
+        std::vector<pfc_step_info> rec(k);
+        rc[i] = pfc_run(states[i], k, rec.data());
+        if (per_step)
+          for (int t = 0; t < k; ++t) per_step[(size_t)i * nsteps + n + t] = rec[t];
+      });
+    for (std::thread& t : pool) t.join();
+    n += k;
+  };
+  if (!batch_graph_ok(states, count)) {
+    threaded_steps(nsteps);
+  } else {
+    while (n < nsteps && !all_graph_ready(states, count, rc)) threaded_steps(1);
+    if (n < nsteps) {
+      BatchGraph bg;
+      int brc = build_batch_graph(states, count, &bg);
+      if (brc == PFC_OK) {
+        for (; n < nsteps; ++n) {
+          brc = batch_step(states, count, &bg, rc, per_step ? per_step + n : nullptr, nsteps);
+          if (brc != PFC_OK) break;
+        }
       }
-      rc[i] = pfc_run(states[i], nsteps, per_step ? per_step + (size_t)i * nsteps : nullptr);
-    });
-  for (std::thread& t : pool) t.join();
+      destroy_batch_graph(&bg);
+      if (brc != PFC_OK) return brc;
+    }
+  }
   int first = PFC_OK;
   for (int i = 0; i < count; ++i) {
     if (status) status[i] = rc[i];

@@ -75,6 +75,30 @@ struct IterArgs {
   const double* sm;     // Newton iteration (null with M = 1)
 };
 
+// Device-side control of one time step (inexact Newton, Sec. 4): every decision of
+// the Newton loop, the GMRES restart loop and the backtracking line search is taken
+// by a one-thread kernel on these fields, so that a whole step can run as one CUDA
+// graph (conditional nodes driven by the *_go fields) or from the host, which reads
+// the same fields back; both execute the same kernels in the same order.
+struct StepCtl {
+  // set by the host before the step
+  double idt;       // 1 / dt
+  double ref_norm;  // ||F(phi^n)|| for the stop test with another guess (< 0: ||F(Phi_0)||)
+  double newton_rtol, newton_atol, gmres_rtol, gmres_atol, ls_alpha, reorth_eta2;
+  int newton_max_it, ls_max_cuts, gmres_max_it, refactor;
+  // state of the step
+  double r0, target, rnorm, f0, ft, lam, gtol;
+  int m, gm_total, gm_its, cuts_total, cut, status;
+  // branch and loop conditions
+  int newton_go, factor_go, cycle_go, restart_go, ls_go, commit_go;
+  // what ran (the host counts the launches of a graph step from these)
+  int n_factor, n_cycles, n_restarts, n_trials;
+};
+// Conditional handles of a step graph (unused when the host drives the step).
+struct StepHandles {
+  cudaGraphConditionalHandle newton, factor, cycle, arnoldi, restart, ls, commit;
+};
+
 // Scalars the host reads back after a reduction.
 struct Scalars {
   double sum[8];
@@ -92,15 +116,20 @@ struct LinStencil {
 
 // Process-wide count of kernels launched by this library (for launch reports).
 void count_launches(long long n);
+void count_pause(bool on);  // the calling thread is capturing a graph: its launches run later
+void count_graph_launch();
+extern long long g_graph_launches;
 long long launches_so_far();
 
 // ---- stencil kernels (stencil2d.cu)
 // mob: variable mobility M = 1 - s^2 at the midpoint s = (Phi + phi^n)/2 (Eq. NSOP's M_d); the
 // residual then also writes mu and s beside q (mu_out, s_out), and the JVP reads them (mu, sm).
+// idt_dev / lam_dev (optional): 1/dt and the line-search step read from device memory instead of
+// idt / lam (a captured step graph serves every time step).
 void launch_residual2d(const Geo& g, const double* Phi_base, const double* S, double lam, const double* smean,
                        const double* phin, double idt, double* F, double* Phi_out, double* q_out, double* partial,
                        int* nparts, cudaStream_t st, bool mob = false, double* mu_out = nullptr,
-                       double* s_out = nullptr);
+                       double* s_out = nullptr, const double* idt_dev = nullptr, const double* lam_dev = nullptr);
 void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
                   const int* skip, cudaStream_t st, const IterArgs* ia = nullptr, const double* mu = nullptr,
                   const double* sm = nullptr);
@@ -192,7 +221,8 @@ __host__ __device__ inline size_t chunk_rec_off(const FactorStore& fs, int b, in
 }
 void launch_chunk2d(const BlockDesc* blocks, int nblocks, const FactorStore& fs, cudaStream_t st);
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
-                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st);
+                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st,
+                     const double* idt_dev = nullptr);
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st,
                         const IterArgs* ia = nullptr, const Decomp2* dc = nullptr);
@@ -284,6 +314,7 @@ struct Tail {
   double* out;              // kSums: reduced values
   const IterArgs* ia;       // when set, j comes from ia->j (graph mode)
   int* err = nullptr;       // PFC_ETIMEOUT is stored here when a bounded wait runs out
+  const int* nx_dev = nullptr;  // multi-axpy: the vector count read from device memory (graph mode)
 };
 
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
@@ -295,7 +326,7 @@ struct Tail {
 constexpr int kDotF64 = 0, kDotFF = 1, kDotF32 = 2;
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     int dot = kDotF64);
+                     int dot = kDotF64, int nv_grid = 0);
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st, bool ff = false);
@@ -304,6 +335,28 @@ void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* c
                        cudaStream_t st);
 void launch_cycle_cond(const GmresCtl* ctl, int m, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st);
+// ---- step control (newton.cu); graph = 1 also sets the conditional handles in h
+void launch_newton_begin(StepCtl* c, const double* nrm2, IterArgs* ia, IterArgs* ia_restart, const StepHandles& h,
+                         int graph, cudaStream_t st);
+void launch_set_factor_cond(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
+void launch_factor_done(StepCtl* c, cudaStream_t st);
+void launch_gmres_begin(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st);
+void launch_arnoldi_begin(const GmresCtl* g, int m, const StepHandles& h, cudaStream_t st);
+void launch_cycle_decide(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st);
+void launch_gmres_restart(StepCtl* c, GmresCtl* g, const double* nrm2, cudaStream_t st);
+void launch_gmres_end(StepCtl* c, const int* status_dev, const StepHandles& h, int graph, cudaStream_t st);
+void launch_ls_decide(StepCtl* c, const double* nrm2, const StepHandles& h, int graph, cudaStream_t st);
+// Copies src[k] -> dst[k] (k < npairs, N doubles each) when the step's status is still PFC_OK.
+struct CopyPairs {
+  const double* src[5];
+  double* dst[5];
+  int n;
+};
+void launch_copy_if_ok(const StepCtl* c, const CopyPairs& cp, long long n, cudaStream_t st);
+// GMRES start: S = 0, red2[0..1] = 0 (|S|^2, sum S), V0 <- F.
+void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st);
+void launch_newton_next(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
+void launch_step_end(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
 void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, double reorth_eta2,
                        cudaStream_t st);
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st);

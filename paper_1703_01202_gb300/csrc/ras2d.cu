@@ -154,7 +154,8 @@ template <typename TC, typename TS, int RING>
 __global__ void __launch_bounds__(256) k_factor2d(Geo g, const BlockDesc* __restrict__ blocks,
                                                   const double* __restrict__ q, double idt,
                                                   const double* __restrict__ lin, FactorStore fs,
-                                                  int* __restrict__ status) {
+                                                  int* __restrict__ status, const double* __restrict__ idt_dev) {
+  if (idt_dev) idt = *idt_dev;  // a captured step graph: this step's 1/dt
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TC s_dinv;
   const BlockDesc B = blocks[blockIdx.x];
@@ -372,7 +373,9 @@ template <typename TS>
 __global__ void __launch_bounds__(kColRing) k_factor2d_col(Geo g, const BlockDesc* __restrict__ blocks,
                                                          const double* __restrict__ q, double idt,
                                                          const double* __restrict__ lin, FactorStore fs,
-                                                         int* __restrict__ status) {
+                                                         int* __restrict__ status,
+                                                         const double* __restrict__ idt_dev) {
+  if (idt_dev) idt = *idt_dev;  // a captured step graph: this step's 1/dt
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) float lslot[kColRows];  // multipliers by row slot (0 off the window)
   __shared__ int slot[kColRows];                   // window position & 63 -> row slot
@@ -1121,22 +1124,22 @@ void chunked_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 
 template <typename TC, typename TS>
 void factor_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
-                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
+                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st, const double* idt_dev) {
   if (sizeof(TC) == 4 && !fs.mob_mu && !g.neumann && fs.kl_max + 1 <= kColRows && 2 * fs.kl_max + 2 <= kColRing &&
       factor_col_smem_bytes(fs.n_max) <= 227 * 1024) {
     const size_t smem = factor_col_smem_bytes(fs.n_max);
     cudaFuncSetAttribute(k_factor2d_col<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d_col<TS><<<nblocks, kColRing, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    k_factor2d_col<TS><<<nblocks, kColRing, smem, st>>>(g, blocks, q, idt, lin, fs, status, idt_dev);
     count_launches(1);
     return;
   }
   const size_t smem = factor_smem_bytes(fs.prec, fs.kl_max, fs.n_max, fs.mob_mu ? fs.ext_max : 0);
   if (2 * fs.kl_max + 2 <= 128) {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d<TC, TS, 128><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    k_factor2d<TC, TS, 128><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status, idt_dev);
   } else {
     cudaFuncSetAttribute(k_factor2d<TC, TS, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_factor2d<TC, TS, 256><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status);
+    k_factor2d<TC, TS, 256><<<nblocks, 256, smem, st>>>(g, blocks, q, idt, lin, fs, status, idt_dev);
   }
   count_launches(1);
 }
@@ -1212,13 +1215,13 @@ size_t factor_smem_bytes(int prec, int kl, int n_max, int ext_max) {
 }
 
 void launch_factor2d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
-                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st) {
+                     const double* lin, const FactorStore& fs, int* status, cudaStream_t st, const double* idt_dev) {
   if (fs.prec == PFC_F64)
-    factor_dispatch<double, double>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+    factor_dispatch<double, double>(g, blocks, nblocks, q, idt, lin, fs, status, st, idt_dev);
   else if (fs.prec == PFC_F32)
-    factor_dispatch<float, float>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+    factor_dispatch<float, float>(g, blocks, nblocks, q, idt, lin, fs, status, st, idt_dev);
   else
-    factor_dispatch<float, __nv_bfloat16>(g, blocks, nblocks, q, idt, lin, fs, status, st);
+    factor_dispatch<float, __nv_bfloat16>(g, blocks, nblocks, q, idt, lin, fs, status, st, idt_dev);
 }
 
 void launch_ras_apply2d(const Geo& g, const BlockDesc* blocks, int nblocks, const FactorStore& fs, const double* r,

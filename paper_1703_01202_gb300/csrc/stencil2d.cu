@@ -43,8 +43,12 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
                                                    const double* __restrict__ phin, double idt,
                                                    double* __restrict__ F, double* __restrict__ Pout,
                                                    double* __restrict__ qout, double* __restrict__ partial,
-                                                   double* __restrict__ muout, double* __restrict__ sout) {
+                                                   double* __restrict__ muout, double* __restrict__ sout,
+                                                   const double* __restrict__ idt_dev,
+                                                   const double* __restrict__ lam_dev) {
   __shared__ double sP[AY][AX], sN[AY][AX], sS[AY][AX];
+  if (idt_dev) idt = *idt_dev;  // a captured step graph: this step's 1/dt and line-search step
+  if (lam_dev) lam = *lam_dev;
   __shared__ double sL[AY - 2][AX - 2];
   __shared__ double sM[AY - 4][AX - 4];
   __shared__ double red[NT / 32];
@@ -235,14 +239,15 @@ __global__ void k_qcoef(long long n, const double* __restrict__ P, const double*
 
 void launch_residual2d(const Geo& g, const double* Pb, const double* S, double lam, const double* smean,
                        const double* phin, double idt, double* F, double* Pout, double* qout, double* partial,
-                       int* nparts, cudaStream_t st, bool mob, double* mu_out, double* s_out) {
+                       int* nparts, cudaStream_t st, bool mob, double* mu_out, double* s_out, const double* idt_dev,
+                       const double* lam_dev) {
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
   if (mob)
     k_residual2d<true><<<grid, dim3(32, 8), 0, st>>>(g, Pb, S, lam, smean, phin, idt, F, Pout, qout, partial,
-                                                      mu_out, s_out);
+                                                      mu_out, s_out, idt_dev, lam_dev);
   else
     k_residual2d<false><<<grid, dim3(32, 8), 0, st>>>(g, Pb, S, lam, smean, phin, idt, F, Pout, qout, partial,
-                                                       nullptr, nullptr);
+                                                       nullptr, nullptr, idt_dev, lam_dev);
   count_launches(1);
   *nparts = grid.x * grid.y;
 }

@@ -97,6 +97,7 @@ _SIGNATURES = [
     ("pfc_profile_read", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_double), POINTER(c_double),
                                  POINTER(c_longlong)]),
     ("pfc_profile_kernels", c_int, [c_void_p, POINTER(pfc_kernel_prof), c_int]),
+    ("pfc_launch_counts", c_int, [POINTER(c_longlong), POINTER(c_longlong)]),
     ("pfc_residual_static", c_int, [POINTER(pfc_grid), c_double, c_double, c_void_p, c_void_p, c_double, c_void_p,
                                     POINTER(c_double), c_void_p]),
     ("pfc_wait_selftest", c_int, [c_int, c_longlong, c_void_p, c_void_p]),
@@ -170,6 +171,13 @@ def run_batch(solvers: Sequence["Solver"], nsteps: int) -> List[List[dict]]:
     out = [[infos[i * nsteps + k].as_dict() for k in range(nsteps)] for i in range(n)]
     _check(st, "pfc_run_batch")
     return out
+
+
+def launch_counts() -> dict:
+    """Process-wide: kernels the library has run and CUDA graph launches."""
+    k, g = c_longlong(), c_longlong()
+    _check(lib().pfc_launch_counts(ctypes.byref(k), ctypes.byref(g)), "pfc_launch_counts")
+    return {"kernels": k.value, "graphs": g.value}
 
 
 def make_grid(shape: Sequence[int]) -> pfc_grid:

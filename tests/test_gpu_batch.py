@@ -1,6 +1,7 @@
-"""GPU tests of the batched runner pfc_run_batch: independent states on their
-own streams, driven concurrently, give the same records and fields as the same
-states run one after another, and each agrees with the oracle."""
+"""GPU tests of the batched runner pfc_run_batch (independent states on their
+own streams stepped together by one captured graph per ensemble step) and of the
+graph form of a time step: both give the same records and fields as the
+host-driven steps, and each agrees with the oracle."""
 import math
 
 import numpy as np
@@ -41,8 +42,10 @@ def test_batch_equals_sequential_runs(env, prec):
     batch = [_make(P, torch, shape, g, prec, st) for g, st in zip(gammas, streams)]
     for s, phi in zip(batch, phis):
         s.set_field(phi)
+    g0 = P.launch_counts()["graphs"]
     recs = P.run_batch(batch, 3)
     torch.cuda.synchronize()
+    assert P.launch_counts()["graphs"] - g0 == 2  # step 1 tunes on threads; steps 2-3: one graph each
     for i, (g, phi) in enumerate(zip(gammas, phis)):
         s = _make(P, torch, shape, g, prec)
         s.set_field(phi)
@@ -105,22 +108,50 @@ def test_failed_steps_are_retried_with_half_the_step(env):
     assert e.value.status == P.PFC_EGMRES
 
 
-@pytest.mark.parametrize("prec", [0, 2])
-def test_graph_cycles_match_the_host_loop(env, prec):
-    """GMRES cycles captured as CUDA graphs (a conditional while loop over the Arnoldi
-    iterations, use_graph = 1, on a non-default stream) run the same kernels in the
-    same order as the host-driven loop: identical records and fields."""
-    P, torch = env
-    shape = (64, 64)
-    phi = inputs.noise_field(shape, 0.07, 0.07, 1030)
+def _graph_vs_host(P, torch, shape, sub, prec, steps, phi, gamma=0.25, **kw):
     out = {}
     for ug in (0, 1):
-        params = P.default_params(sub=(4, 4), overlap=1, factor_prec=prec, dt_min=0.01, dt_max=10.0, eta=5000.0,
-                                  use_graph=ug)
-        s = P.Solver(shape, H, 0.25, params, stream=torch.cuda.Stream())
+        params = P.default_params(sub=sub, overlap=1, factor_prec=prec, dt_min=0.01, dt_max=10.0, eta=5000.0,
+                                  use_graph=ug, **kw)
+        s = P.Solver(shape, H, gamma, params, stream=torch.cuda.Stream())
         s.set_field(phi)
-        recs = s.run(4)
-        out[ug] = (recs, s.get_field(), s.tuning()["graph"])
+        g0 = P.launch_counts()["graphs"]
+        recs = s.run(steps)
+        out[ug] = (recs, s.get_field(), s.tuning()["graph"], P.launch_counts()["graphs"] - g0)
+        s.close()
     assert out[1][2] == 1 and out[0][2] == 0
-    assert [r["gmres_its"] for r in out[0][0]] == [r["gmres_its"] for r in out[1][0]]
+    assert out[1][3] == steps - 1 and out[0][3] == 0  # one graph per step after the tuning step
+    for key in ("newton_its", "gmres_its", "ls_cuts", "dt", "energy", "res_norm"):
+        assert [r[key] for r in out[0][0]] == [r[key] for r in out[1][0]], key
     np.testing.assert_array_equal(out[0][1], out[1][1])
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_graph_steps_match_the_host_loop(env, prec):
+    """Whole time steps captured as CUDA graphs (use_graph = 1: Newton loop, factor branch,
+    GMRES restart and Arnoldi loops, line search and commit as conditional nodes driven by
+    device-side control kernels) run the same kernels in the same order as the host-driven
+    step: identical records and fields, bit for bit."""
+    P, torch = env
+    shape = (64, 64)
+    out = _graph_vs_host(P, torch, shape, (4, 4), prec, 4, inputs.noise_field(shape, 0.07, 0.07, 1030))
+    assert sum(r["gmres_its"] for r in out[1][0]) > 60  # GMRES(30) restarted within some Newton iterations
+
+
+def test_graph_steps_match_the_host_loop_at_512(env):
+    """The same at 512^2 (256 tiles per vector in the Gram-Schmidt sweeps, more than the CTAs of a
+    sweep), BF16 factors, 3 steps: the host loop sizes its sweeps like the graph's."""
+    P, torch = env
+    shape = (512, 512)
+    _graph_vs_host(P, torch, shape, (32, 32), 2, 3, inputs.hex_seeds_2d(shape, H, seed=2100))
+
+
+def test_graph_steps_with_line_search_cuts_match_the_host_loop(env):
+    """Variable mobility at dt = 10 needs damped Newton steps: the device-side line search
+    (Armijo test, quadratic backtracking) takes the same cuts in both forms."""
+    P, torch = env
+    shape = (48, 48)
+    phi = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=10, seed=3)
+    out = _graph_vs_host(P, torch, shape, (3, 3), 1, 4, phi, mobility=1)
+    assert sum(r["ls_cuts"] for r in out[1][0]) > 0
