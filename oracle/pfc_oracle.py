@@ -389,10 +389,22 @@ def ilu0(A: sp.csr_matrix) -> sp.csr_matrix:
     (IKJ) Gaussian elimination: for each row i and each k < i in row i's
     pattern, a_ik /= a_kk and a_ij -= a_ik a_kj for j > k in both patterns.
     Returns one CSR holding L (unit lower, strict part) and U (upper incl. diag)."""
-    A = sp.csr_matrix(A, dtype=np.float64, copy=True)
-    A.sort_indices()
-    n = A.shape[0]
-    indptr, indices, data = A.indptr, A.indices, A.data
+    return ilu0_batch([A])[0]
+
+
+def ilu0_batch(mats: Sequence[sp.csr_matrix]) -> List[sp.csr_matrix]:
+    """ilu0 of several matrices with one sparsity pattern (the blocks of one extent),
+    factored side by side: the same elimination steps, in the same order, on each
+    matrix's values (a stacked array, one row per matrix)."""
+    As = [sp.csr_matrix(A, dtype=np.float64, copy=True) for A in mats]
+    for A in As:
+        A.sort_indices()
+    indptr, indices = As[0].indptr, As[0].indices
+    for A in As[1:]:
+        if not (np.array_equal(A.indptr, indptr) and np.array_equal(A.indices, indices)):
+            raise ValueError("ilu0_batch: the matrices must share one pattern")
+    n = As[0].shape[0]
+    D = np.stack([A.data for A in As])  # D[b, p]: entry p of matrix b
     pos = [dict(zip(indices[indptr[i] : indptr[i + 1]], range(indptr[i], indptr[i + 1]))) for i in range(n)]
     diag_pos = np.array([pos[i][i] for i in range(n)])
     for i in range(n):
@@ -401,21 +413,31 @@ def ilu0(A: sp.csr_matrix) -> sp.csr_matrix:
             k = indices[p]
             if k >= i:
                 break
-            data[p] /= data[diag_pos[k]]
-            lik = data[p]
-            for pk in range(diag_pos[k] + 1, indptr[k + 1]):
-                j = indices[pk]
-                pj = row.get(j)
-                if pj is not None:
-                    data[pj] -= lik * data[pk]
-    return A
+            D[:, p] /= D[:, diag_pos[k]]  # l_ik = a_ik / a_kk
+            upper = range(diag_pos[k] + 1, indptr[k + 1])  # a_kj, j > k
+            pairs = [(row[indices[pk]], pk) for pk in upper if indices[pk] in row]
+            if pairs:
+                pj, pk = (np.array(v) for v in zip(*pairs))
+                D[:, pj] -= D[:, p : p + 1] * D[:, pk]  # a_ij -= l_ik a_kj (distinct j: independent)
+    for b, A in enumerate(As):
+        A.data = D[b].copy()
+    return As
+
+
+def ilu0_split(LU: sp.csr_matrix) -> Tuple[sp.csr_matrix, sp.csr_matrix]:
+    """The unit lower factor L (with its unit diagonal) and the upper factor U of an ILU(0)."""
+    L = sp.tril(LU, -1, format="csr") + sp.identity(LU.shape[0], format="csr")
+    return L, sp.triu(LU, 0, format="csr")
 
 
 def ilu0_solve(LU: sp.csr_matrix, b: np.ndarray) -> np.ndarray:
     """Forward substitution with the unit lower factor, then backward
     substitution with the upper factor of an ILU(0) (library triangular solves)."""
-    L = sp.tril(LU, -1, format="csr") + sp.identity(LU.shape[0], format="csr")
-    U = sp.triu(LU, 0, format="csr")
+    return ilu0_split_solve(ilu0_split(LU), b)
+
+
+def ilu0_split_solve(LU: Tuple[sp.csr_matrix, sp.csr_matrix], b: np.ndarray) -> np.ndarray:
+    L, U = LU
     y = spla.spsolve_triangular(L, b, lower=True, unit_diagonal=True)
     return spla.spsolve_triangular(U, y, lower=False)
 
@@ -438,25 +460,33 @@ class Schwarz:
         self.blocks = list(blocks)
         self.kind = kind
         self.solver = solver
-        self.factors = []
-        for blk in self.blocks:
-            if solver == "lu":
-                self.factors.append(scipy.linalg.lu_factor(subdomain_matrix(J, blk), check_finite=True))
-            elif solver == "ilu0":
-                A = subdomain_matrix(J, blk)
-                pattern = block_pattern(blk)
-                if np.any(A[~pattern] != 0.0):
-                    raise ValueError("block couples to itself across the periodic wrap; grid too small")
-                A = A + ilu_shift * np.mean(np.abs(np.diag(A))) * np.eye(A.shape[0])
+        self.factors = [None] * len(self.blocks)
+        if solver == "lu":
+            for k, blk in enumerate(self.blocks):
+                self.factors[k] = scipy.linalg.lu_factor(subdomain_matrix(J, blk), check_finite=True)
+        elif solver == "ilu0":
+            by_extent = {}  # blocks of one extent share their pattern: factored together
+            for k, blk in enumerate(self.blocks):
+                by_extent.setdefault(tuple(n + 2 * blk.overlap for n in blk.core_n), []).append(k)
+            for ks in by_extent.values():
+                pattern = block_pattern(self.blocks[ks[0]])
                 rows, cols = np.nonzero(pattern)
-                self.factors.append(ilu0(sp.csr_matrix((A[rows, cols], (rows, cols)), shape=A.shape)))
-            else:
-                raise ValueError(solver)
+                mats = []
+                for k in ks:
+                    A = subdomain_matrix(J, self.blocks[k])
+                    if np.any(A[~pattern] != 0.0):
+                        raise ValueError("block couples to itself across the periodic wrap; grid too small")
+                    A = A + ilu_shift * np.mean(np.abs(np.diag(A))) * np.eye(A.shape[0])
+                    mats.append(sp.csr_matrix((A[rows, cols], (rows, cols)), shape=A.shape))
+                for k, LU in zip(ks, ilu0_batch(mats)):
+                    self.factors[k] = ilu0_split(LU)
+        else:
+            raise ValueError(solver)
 
     def _solve(self, k: int, rhs: np.ndarray) -> np.ndarray:
         if self.solver == "lu":
             return scipy.linalg.lu_solve(self.factors[k], rhs)
-        return ilu0_solve(self.factors[k], rhs)
+        return ilu0_split_solve(self.factors[k], rhs)
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         flat = r.ravel()
