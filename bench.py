@@ -189,7 +189,7 @@ def _goldens():
     return mod
 
 
-def golden_errors(case: str, prec: int, learned: bool, fast_dots: int) -> dict:
+def golden_errors(case: str, prec: int, learned: bool, **extra) -> dict:
     """Runs a fresh solver of the given form over the steps of an oracle trajectory (committed
     record, written by tests/golden/make_goldens.py from the FP64 oracle) and states the errors
     of the result: max |phi - phi_oracle| over the record's cells after the last step, and the
@@ -200,7 +200,7 @@ def golden_errors(case: str, prec: int, learned: bool, fast_dots: int) -> dict:
     if not os.path.exists(G.path_of(case)):
         return {"golden": case, "missing": True}
     rec = G.load(case)
-    s, close = make_solver(rec["meta"]["workload"], prec, learned, fast_dots)
+    s, close = make_solver(rec["meta"]["workload"], prec, learned, **extra)
     try:
         infos = s.run(int(rec["meta"]["steps"]))
         phi = s.get_field()
@@ -258,8 +258,12 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 
 
 # ---------------------------------------------------------------- solvers
-def make_solver(workload: str, prec: int, learned: bool = False, fast_dots: int = 0, stream=True, **form):
+USE_GRAPH = [1]  # pfc_params.use_graph of every solver (--no-graph for ncu runs)
+
+
+def make_solver(workload: str, prec: int, learned: bool = False, stream=True, **form):
     """A solver for a workload (fresh field set), its guess network and a close function."""
+    form.setdefault("use_graph", USE_GRAPH[0])
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
@@ -267,7 +271,7 @@ def make_solver(workload: str, prec: int, learned: bool = False, fast_dots: int 
 
     w = inputs.workload(workload)
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
-                                dt_max=w["dt_max"], eta=w["eta"], gmres_fast_dots=fast_dots,
+                                dt_max=w["dt_max"], eta=w["eta"],
                                 guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV, **form)
     # a stream of its own: GMRES cycles run as captured graphs whenever per-kernel timing is off
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream() if stream else None)
@@ -333,14 +337,14 @@ def timed_steps(s, steps: int, world: int, local: int):
 
 
 def run_variant(workload: str, prec: int, steps: int, warmup: int, world: int, local: int, learned=False,
-                fast_dots=0, profile_steps=4, e2e=False, golden=None, hbm=6800.0):
+                profile_steps=4, e2e=False, golden=None, hbm=6800.0, **extra):
     """Warm-up, `steps` timed steps on the graph path, `profile_steps` more with per-kernel
     events (host-driven GMRES loop), the end-to-end host-buffer steps when asked, and the
     errors against an oracle trajectory."""
     import numpy as np
     import torch
 
-    s, close = make_solver(workload, prec, learned, fast_dots)
+    s, close = make_solver(workload, prec, learned, **extra)
     s.run(warmup)
     tuning = s.tuning()
     ms, infos, ck, launches = timed_steps(s, steps, world, local)
@@ -392,7 +396,7 @@ def run_variant(workload: str, prec: int, steps: int, warmup: int, world: int, l
     out["phi_after"] = s.get_field()
     close()
     if golden:
-        out["errors_vs_oracle"] = golden_errors(golden, prec, learned, fast_dots)
+        out["errors_vs_oracle"] = golden_errors(golden, prec, learned, **extra)
     return out
 
 
@@ -583,11 +587,15 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=4,
                     help="steps after the timed region with per-kernel CUDA events (rooflines)")
     ap.add_argument("--variant", default="all",
-                    choices=["all", "f64", "f32", "bf16", "bf16_learned", "bf16_learned_fastdots"],
+                    choices=["all", "f64", "f32", "bf16", "bf16_learned", "bf16_learned_fastdots",
+                             "bf16_learned_jvp32"],
                     help="run one form only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 2048^2, 256^3, ensemble and other-form workloads")
     ap.add_argument("--no-golden", action="store_true", help="skip the error runs against the oracle trajectories")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="profiling aid: host-driven steps (the same kernels; ncu cannot profile the kernel "
+                         "nodes of graphs with conditional nodes)")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="AS / left-RAS / right-RAS x overlap 0-3 on the workload (no bench line)")
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
@@ -596,6 +604,8 @@ def main():
     ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
                     help="2D Schwarz apply kernel for --kernel-loop (-1: autotuned)")
     args = ap.parse_args()
+    if args.no_graph:
+        USE_GRAPH[0] = 0
     if args.kernel_loop:
         kernel_loop(args)
         return
@@ -617,15 +627,17 @@ def main():
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"]
     golden = None if args.no_golden else "hex1024_s10"
-    forms = (("f64", 0, False, 0), ("f32", 1, False, 0), ("bf16", 2, False, 0), ("bf16_learned", 2, True, 0),
-             ("bf16_learned_fastdots", 2, True, 1))
+    # (name, factor precision, learned guess, opt-in forms)
+    forms = (("f64", 0, False, {}), ("f32", 1, False, {}), ("bf16", 2, False, {}), ("bf16_learned", 2, True, {}),
+             ("bf16_learned_fastdots", 2, True, {"gmres_fast_dots": 1}),
+             ("bf16_learned_jvp32", 2, True, {"jvp_fp32": 1}))
     variants = {}
-    for name, prec, lg, fd in forms:
+    for name, prec, lg, extra in forms:
         if args.variant in ("all", name):
             variants[name] = run_variant(WORKLOAD, prec, args.steps, args.warmup, world, local, learned=lg,
-                                         fast_dots=fd, profile_steps=args.profile_steps,
+                                         profile_steps=args.profile_steps,
                                          e2e=(name == "bf16_learned" or args.variant == name), golden=golden,
-                                         hbm=hbm)
+                                         hbm=hbm, **extra)
     versus_f64(variants)
     head_name = "bf16_learned" if "bf16_learned" in variants else args.variant
     head = variants[head_name]

@@ -92,3 +92,82 @@ void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const 
 }
 
 }  // namespace pfc
+
+// ---- The same product in plain FP32 (opt-in, pfc_params.jvp_fp32): v and q cut to floats, the
+// stencil in FP32, the result widened to FP64 by its bit pattern.  About 2^-24 of the largest
+// terms per point (the sixth-order stencil's cancellation makes that a larger part of J v for
+// smooth v); GMRES still solves to its own tolerance against this operator, and Newton's FP64
+// residual judges the step.
+namespace pfc {
+namespace {
+
+constexpr int FTX = 32, FTY = 16, FR = 3;
+constexpr int FAX = FTX + 2 * FR, FAY = FTY + 2 * FR;
+
+__global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restrict__ v, const double* __restrict__ q,
+                                                   double idt, double* __restrict__ Jv, const int* __restrict__ skip,
+                                                   const IterArgs* __restrict__ ia) {
+  if (skip && *skip) return;
+  if (ia) {  // graph mode: J Z_j into V_(j+1)
+    v = ia->z;
+    q = ia->q;
+    idt = ia->idt;
+    Jv = ia->w;
+  }
+  __shared__ float sV[FAY][FAX];
+  __shared__ float sQ[FAY - 4][FAX - 4];
+  __shared__ float sL[FAY - 2][FAX - 2];
+  __shared__ float sW[FAY - 4][FAX - 4];
+  const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+  const int tid = threadIdx.x + threadIdx.y * 32;
+  for (int i = tid; i < FAX * FAY; i += 256) {
+    const int ly = i / FAX, lx = i - ly * FAX;
+    const long long idx =
+        cell_index(x0 + lx - FR, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - FR, g.ny, g.neumann);
+    sV[ly][lx] = f32_cut(v[idx]);
+  }
+  for (int i = tid; i < (FAX - 4) * (FAY - 4); i += 256) {
+    const int ly = i / (FAX - 4), lx = i - ly * (FAX - 4);
+    const long long idx =
+        cell_index(x0 + lx - 1, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - 1, g.ny, g.neumann);
+    sQ[ly][lx] = f32_cut(q[idx]);
+  }
+  __syncthreads();
+  for (int i = tid; i < (FAX - 2) * (FAY - 2); i += 256) {
+    const int ly = i / (FAX - 2) + 1, lx = i - (ly - 1) * (FAX - 2) + 1;
+    sL[ly - 1][lx - 1] = (sV[ly][lx + 1] + sV[ly][lx - 1]) + (sV[ly + 1][lx] + sV[ly - 1][lx]) - 4.0f * sV[ly][lx];
+  }
+  __syncthreads();
+  const float ih2 = f32_cut(g.ih2), hih4 = f32_cut(0.5 * g.ih2 * g.ih2), c0 = f32_cut(0.5 * (1.0 - g.gamma));
+  for (int i = tid; i < (FAX - 4) * (FAY - 4); i += 256) {
+    const int ly = i / (FAX - 4) + 2, lx = i - (ly - 2) * (FAX - 4) + 2;
+    const int a = ly - 1, b = lx - 1;
+    const float Lv = sL[a][b];
+    const float LLv = (sL[a][b + 1] + sL[a][b - 1]) + (sL[a + 1][b] + sL[a - 1][b]) - 4.0f * Lv;
+    const float vv = sV[ly][lx];
+    sW[ly - 2][lx - 2] = fmaf(c0 + sQ[ly - 2][lx - 2], vv, fmaf(ih2, Lv, hih4 * LLv));  // w = (c0 + q) v + ih2 Lv + ih4/2 LLv
+  }
+  __syncthreads();
+  const float fidt = f32_cut(idt);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int tx = threadIdx.x, ty = threadIdx.y + 8 * r;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx < g.nx && gy < g.ny) {
+      const int a = ty + 1, b = tx + 1;
+      const float Lw = (sW[a][b + 1] + sW[a][b - 1]) + (sW[a + 1][b] + sW[a - 1][b]) - 4.0f * sW[a][b];
+      Jv[gx + (long long)g.nx * gy] = f2d_bits(fmaf(sV[ty + FR][tx + FR], fidt, -ih2 * Lw));
+    }
+  }
+}
+
+}  // namespace
+
+void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, const int* skip,
+                      cudaStream_t st, const IterArgs* ia) {
+  dim3 grid((g.nx + FTX - 1) / FTX, (g.ny + FTY - 1) / FTY);
+  k_jvp2d_f32<<<grid, dim3(32, 8), 0, st>>>(g, v, q, idt, Jv, skip, ia);
+  count_launches(1);
+}
+
+}  // namespace pfc

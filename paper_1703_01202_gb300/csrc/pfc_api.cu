@@ -181,6 +181,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
   if (p->gmres_fast_dots != 0 && p->gmres_fast_dots != 1) return PFC_EINVAL;
+  if (p->jvp_fp32 != 0 && p->jvp_fp32 != 1) return PFC_EINVAL;
   if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
   if (p->mobility != 0 && (p->mobility != 1 || g->dim != 2)) return PFC_EINVAL;
   // Neumann walls: 2D, left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then
@@ -598,7 +599,9 @@ void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out
   if (s->dim == 2 && s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
     const bool trial = q != nullptr && q == s->qt;
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu, trial ? s->smt : s->sm);
-  } else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
+  } else if (s->dim == 2 && s->fs.prec != PFC_F64 && s->p.jvp_fp32)  // mixed path, opt-in: plain FP32
+    pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia);
+  else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
     pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
   else if (s->dim == 2)
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);

@@ -137,6 +137,9 @@ void launch_energy2d(const Geo& g, const double* phi, double* partial, int* npar
 // The same JVP in float-float arithmetic on the FP32 pipe (jvp_ff.cu), for the mixed path.
 void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
                      const int* skip, cudaStream_t st, const IterArgs* ia = nullptr);
+// The same JVP in plain FP32 (opt-in on the mixed path, pfc_params.jvp_fp32).
+void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, const int* skip,
+                      cudaStream_t st, const IterArgs* ia = nullptr);
 void launch_qcoef(const Geo& g, const double* Phi, const double* phin, double* q, cudaStream_t st);
 
 // ---- Schwarz preconditioner (ras2d.cu)

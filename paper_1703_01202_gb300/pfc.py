@@ -40,7 +40,7 @@ class pfc_params(ctypes.Structure):
         ("dt_min", c_double), ("dt_max", c_double), ("eta", c_double), ("energy_scaled", c_int),
         ("apply_variant", c_int), ("dt_halvings", c_int), ("gmres_reorth_eta", c_double),
         ("use_graph", c_int), ("reuse_factor", c_int), ("mobility", c_int), ("boundary", c_int),
-        ("gmres_fast_dots", c_int),
+        ("gmres_fast_dots", c_int), ("jvp_fp32", c_int),
     ]
 
 

@@ -108,7 +108,9 @@ def test_failed_steps_are_retried_with_half_the_step(env):
     assert e.value.status == P.PFC_EGMRES
 
 
-def _graph_vs_host(P, torch, shape, sub, prec, steps, phi, gamma=0.25, **kw):
+def _graph_vs_host(P, torch, shape, sub, prec, steps, phi, gamma=0.25, fixed_dt=None, **kw):
+    """Both forms over `steps` steps (adaptive dt, or fixed_dt); with apply_variant = -1 the first
+    step tunes the apply kernel on the host, every later step is one graph launch."""
     out = {}
     for ug in (0, 1):
         params = P.default_params(sub=sub, overlap=1, factor_prec=prec, dt_min=0.01, dt_max=10.0, eta=5000.0,
@@ -116,11 +118,12 @@ def _graph_vs_host(P, torch, shape, sub, prec, steps, phi, gamma=0.25, **kw):
         s = P.Solver(shape, H, gamma, params, stream=torch.cuda.Stream())
         s.set_field(phi)
         g0 = P.launch_counts()["graphs"]
-        recs = s.run(steps)
+        recs = [s.step(fixed_dt) for _ in range(steps)] if fixed_dt else s.run(steps)
         out[ug] = (recs, s.get_field(), s.tuning()["graph"], P.launch_counts()["graphs"] - g0)
         s.close()
+    tuned_first = kw.get("apply_variant", -1) < 0
     assert out[1][2] == 1 and out[0][2] == 0
-    assert out[1][3] == steps - 1 and out[0][3] == 0  # one graph per step after the tuning step
+    assert out[1][3] == steps - tuned_first and out[0][3] == 0  # one graph per step
     for key in ("newton_its", "gmres_its", "ls_cuts", "dt", "energy", "res_norm"):
         assert [r[key] for r in out[0][0]] == [r[key] for r in out[1][0]], key
     np.testing.assert_array_equal(out[0][1], out[1][1])
@@ -148,10 +151,11 @@ def test_graph_steps_match_the_host_loop_at_512(env):
 
 
 def test_graph_steps_with_line_search_cuts_match_the_host_loop(env):
-    """Variable mobility at dt = 10 needs damped Newton steps: the device-side line search
-    (Armijo test, quadratic backtracking) takes the same cuts in both forms."""
+    """Variable mobility at dt = 10 from a crystal seed needs damped Newton steps: the
+    device-side line search (Armijo test, quadratic backtracking) takes the same cuts in both
+    forms.  A fixed apply kernel makes every step of the graph form a graph launch."""
     P, torch = env
     shape = (48, 48)
     phi = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=10, seed=3)
-    out = _graph_vs_host(P, torch, shape, (3, 3), 1, 4, phi, mobility=1)
+    out = _graph_vs_host(P, torch, shape, (3, 3), 1, 2, phi, fixed_dt=10.0, mobility=1, apply_variant=5)
     assert sum(r["ls_cuts"] for r in out[1][0]) > 0

@@ -82,16 +82,19 @@ def check_against(rec, infos, phi, tol):
     return err, rel_e.max()
 
 
-@pytest.mark.parametrize("prec,learned_guess", [(0, False), (1, False), (2, False), (2, True)])
-def test_hex1024_ten_steps_match_oracle(env, prec, learned_guess):
-    """The 1024^2 crystal-growth workload (64 x 64 cores), its first 10 adaptive steps."""
+@pytest.mark.parametrize("prec,learned_guess,form", [(0, False, {}), (1, False, {}), (2, False, {}), (2, True, {}),
+                                                     (2, True, {"gmres_fast_dots": 1}), (2, True, {"jvp_fp32": 1})])
+def test_hex1024_ten_steps_match_oracle(env, prec, learned_guess, form):
+    """The 1024^2 crystal-growth workload (64 x 64 cores), its first 10 adaptive steps; also the
+    opt-in mixed forms (FP32 Arnoldi dot products, FP32 JVP)."""
     P, torch, learned = env
     rec = G.load("hex1024_s10")
-    s, net, w = _solver(P, torch, learned, "hex1024", prec, learned_guess)
+    s, net, w = _solver(P, torch, learned, "hex1024", prec, learned_guess, **form)
     s.set_field(w["phi"])
     infos = s.run(rec["meta"]["steps"])
     err, rel_e = check_against(rec, infos, s.get_field(), TOL["f64" if prec == 0 and not learned_guess else "mixed"])
-    print(f"hex1024 prec {prec} learned {learned_guess}: max|dphi| {err:.2e}, energy {rel_e:.2e}")
+    print(f"hex1024 prec {prec} learned {learned_guess} {form}: max|dphi| {err:.2e}, energy {rel_e:.2e}, "
+          f"newton {[i['newton_its'] for i in infos]}")
     s.close()
     if net is not None:
         net.close()

@@ -45,6 +45,21 @@ def test_residual_matches_oracle(pfc, shape):
     assert nrm == pytest.approx(np.linalg.norm(ref), rel=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(64, 64), (40, 70), (33, 31)])
+def test_fp32_jvp_matches_oracle(pfc, shape):
+    """The opt-in plain FP32 JVP of the mixed path (jvp_fp32 = 1): inputs cut to floats and an
+    FP32 stencil whose terms reach ih2^3 |v| ~ 4 |v| times 20 in the radius-3 sum, so each entry
+    is within about 2^-24 x 100 of max |J v|; the bound asserted is 1e-5 of the largest entry."""
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 3)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 4)
+    v = inputs.noise_field(shape, 0.0, 1.0, 5)
+    s = solver(pfc, shape, (1, 1), prec=2, overlap=0, jvp_fp32=1)
+    Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 2.5, H, GAMMA)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    assert np.abs(Jv - ref).max() > 1e-12 * np.abs(ref).max()  # it is the FP32 kernel, not the float-float one
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("shape", [(64, 64), (40, 70), (33, 31)])
 def test_jvp_matches_oracle(pfc, shape, prec):
