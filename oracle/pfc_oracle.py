@@ -468,6 +468,7 @@ class Schwarz:
             by_extent = {}  # blocks of one extent share their pattern: factored together
             for k, blk in enumerate(self.blocks):
                 by_extent.setdefault(tuple(n + 2 * blk.overlap for n in blk.core_n), []).append(k)
+            self.groups = []  # (block numbers, block-diagonal L, block-diagonal U) per extent
             for ks in by_extent.values():
                 pattern = block_pattern(self.blocks[ks[0]])
                 rows, cols = np.nonzero(pattern)
@@ -480,6 +481,10 @@ class Schwarz:
                     mats.append(sp.csr_matrix((A[rows, cols], (rows, cols)), shape=A.shape))
                 for k, LU in zip(ks, ilu0_batch(mats)):
                     self.factors[k] = ilu0_split(LU)
+                # the blocks' triangular systems side by side: one block-diagonal solve per extent
+                # visits every block's rows and entries in the order its own solve would
+                self.groups.append((ks, sp.block_diag([self.factors[k][0] for k in ks], format="csr"),
+                                    sp.block_diag([self.factors[k][1] for k in ks], format="csr")))
         else:
             raise ValueError(solver)
 
@@ -488,14 +493,29 @@ class Schwarz:
             return scipy.linalg.lu_solve(self.factors[k], rhs)
         return ilu0_split_solve(self.factors[k], rhs)
 
+    def _solve_all(self, rhs: List[np.ndarray]) -> List[np.ndarray]:
+        if self.solver == "lu":
+            return [self._solve(k, b) for k, b in enumerate(rhs)]
+        sols = [None] * len(rhs)
+        for ks, L, U in self.groups:
+            y = spla.spsolve_triangular(L, np.concatenate([rhs[k] for k in ks]), lower=True, unit_diagonal=True)
+            x = spla.spsolve_triangular(U, y, lower=False)
+            o = 0
+            for k in ks:
+                sols[k] = x[o : o + rhs[k].size]
+                o += rhs[k].size
+        return sols
+
     def apply(self, r: np.ndarray) -> np.ndarray:
         flat = r.ravel()
         z = np.zeros_like(flat)
-        for k, blk in enumerate(self.blocks):
-            rhs = flat[blk.block_idx]
+        rhs = []
+        for blk in self.blocks:
+            b = flat[blk.block_idx]
             if self.kind == "right-ras":
-                rhs = np.where(blk.core_mask, rhs, 0.0)  # restriction R_k^0
-            sol = self._solve(k, rhs)
+                b = np.where(blk.core_mask, b, 0.0)  # restriction R_k^0
+            rhs.append(b)
+        for k, (blk, sol) in enumerate(zip(self.blocks, self._solve_all(rhs))):
             if self.kind == "left-ras":
                 z[blk.core_idx] += sol[blk.core_mask]  # extension (R_k^0)^T
             else:

@@ -20,7 +20,10 @@ LIB = os.path.join(HERE, "libpfc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}"]
+# -ffp-contract=off: host arithmetic rounds the same on x86 and Arm (no fused multiply-adds), so the
+# host's time-step controller matches the device's operation for operation
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
+         f"-I{INCLUDE}"]
 
 
 def nvcc() -> str:

@@ -115,4 +115,33 @@ __device__ __forceinline__ ff ff_acc(ff acc, ff x) {
   return {s.hi, __fadd_rn(__fadd_rn(acc.lo, x.lo), s.lo)};
 }
 
+// Sums of several float-float terms at the cost of one two-sum per term: the leading parts are
+// added with their exact rounding errors (two-sum), the trailing parts and those errors are summed
+// in plain FP32 (each far below the leading sum), and the result is renormalised once.  The
+// error stays near 2^-46 of the terms' magnitude, like ff_add's, at about half its instructions.
+// (e + w) + (n + s) - 4 c: the unscaled 5-point Laplacian.
+__device__ __forceinline__ ff ff_lap5(ff c, ff e, ff w, ff n, ff s) {
+  const ff a = two_sum(e.hi, w.hi), b = two_sum(n.hi, s.hi);
+  const ff t = two_sum(a.hi, b.hi);
+  const ff u = two_sum(t.hi, -4.0f * c.hi);  // times 4: exact
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e.lo, w.lo), __fadd_rn(n.lo, s.lo)),
+                             __fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(t.lo, __fmaf_rn(-4.0f, c.lo, u.lo))));
+  return fast_two_sum(u.hi, lo);
+}
+// a0 b0 + a1 b1 + a2 b2 + a3 b3 from the unnormalised products of ff_prod.
+__device__ __forceinline__ ff ff_dot4(ff a0, ff b0, ff a1, ff b1, ff a2, ff b2, ff a3, ff b3) {
+  const ff p0 = ff_prod(a0, b0), p1 = ff_prod(a1, b1), p2 = ff_prod(a2, b2), p3 = ff_prod(a3, b3);
+  const ff s01 = two_sum(p0.hi, p1.hi), s23 = two_sum(p2.hi, p3.hi);
+  const ff t = two_sum(s01.hi, s23.hi);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, p3.lo)),
+                             __fadd_rn(__fadd_rn(s01.lo, s23.lo), t.lo));
+  return fast_two_sum(t.hi, lo);
+}
+// a0 b0 - a1 b1.
+__device__ __forceinline__ ff ff_dot2m(ff a0, ff b0, ff a1, ff b1) {
+  const ff p0 = ff_prod(a0, b0), p1 = ff_prod(a1, b1);
+  const ff t = two_sum(p0.hi, -p1.hi);
+  return fast_two_sum(t.hi, __fadd_rn(__fsub_rn(p0.lo, p1.lo), t.lo));
+}
+
 }  // namespace pfc

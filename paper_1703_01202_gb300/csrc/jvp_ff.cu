@@ -17,10 +17,19 @@ constexpr int TX = 32, TY = 16, R = 3;
 constexpr int AX = TX + 2 * R, AY = TY + 2 * R;  // 38 x 22 staged points
 constexpr int NT = 256;                          // 32 x 8 threads, 2 outputs each
 
-// Unscaled 5-point Laplacian (e + w) + (n + s) - 4 c.
-__device__ __forceinline__ ff ff_lap(ff c, ff e, ff w, ff n, ff s) {
-  return ff_add(ff_add(ff_add(e, w), ff_add(n, s)), ff_neg(ff_scale(c, 4.0f)));
-}
+// Global index of staged point (lx, ly) of the tile at (x0, y0) with halo r: direct when the
+// whole staged region lies inside the grid (interior), else through the periodic or mirror image.
+struct Stage {
+  int x0, y0, r;
+  bool interior;
+  __device__ __forceinline__ Stage(const Geo& g, int x0_, int y0_, int tx, int ty, int r_)
+      : x0(x0_), y0(y0_), r(r_), interior(x0_ - r_ >= 0 && x0_ + tx + r_ <= g.nx && y0_ - r_ >= 0 && y0_ + ty + r_ <= g.ny) {}
+  __device__ __forceinline__ long long idx(const Geo& g, int lx, int ly) const {
+    const int x = x0 + lx - r, y = y0 + ly - r;
+    if (interior) return x + (long long)g.nx * y;
+    return cell_index(x, g.nx, g.neumann) + (long long)g.nx * cell_index(y, g.ny, g.neumann);
+  }
+};
 
 __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict__ v,
                                                  const double* __restrict__ vscale, const double* __restrict__ q,
@@ -40,20 +49,20 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int tid = threadIdx.x + threadIdx.y * 32;
   const double sc = vscale ? *vscale : 1.0;
+  const Stage sv(g, x0, y0, TX, TY, R), sq(g, x0, y0, TX, TY, 1);
   for (int i = tid; i < AX * AY; i += NT) {
     const int ly = i / AX, lx = i - ly * AX;
-    const long long idx = cell_index(x0 + lx - R, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - R, g.ny, g.neumann);
+    const long long idx = sv.idx(g, lx, ly);
     sV[ly][lx] = ff_split(vscale ? sc * v[idx] : v[idx]);
   }
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4), lx = i - ly * (AX - 4);
-    const long long idx = cell_index(x0 + lx - 1, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - 1, g.ny, g.neumann);
-    sQ[ly][lx] = ff_split(q[idx]);
+    sQ[ly][lx] = ff_split(q[sq.idx(g, lx, ly)]);
   }
   __syncthreads();
   for (int i = tid; i < (AX - 2) * (AY - 2); i += NT) {
     const int ly = i / (AX - 2) + 1, lx = i - (ly - 1) * (AX - 2) + 1;
-    sL[ly - 1][lx - 1] = ff_lap(sV[ly][lx], sV[ly][lx + 1], sV[ly][lx - 1], sV[ly + 1][lx], sV[ly - 1][lx]);
+    sL[ly - 1][lx - 1] = ff_lap5(sV[ly][lx], sV[ly][lx + 1], sV[ly][lx - 1], sV[ly + 1][lx], sV[ly - 1][lx]);
   }
   __syncthreads();
   const ff ih2 = ff_split(g.ih2), hih4 = ff_split(0.5 * g.ih2 * g.ih2), c0 = ff_split(0.5 * (1.0 - g.gamma));
@@ -61,11 +70,10 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
     const int ly = i / (AX - 4) + 2, lx = i - (ly - 2) * (AX - 4) + 2;
     const int a = ly - 1, b = lx - 1;
     const ff Lv = sL[a][b];
-    const ff LLv = ff_lap(Lv, sL[a][b + 1], sL[a][b - 1], sL[a + 1][b], sL[a - 1][b]);
+    const ff LLv = ff_lap5(Lv, sL[a][b + 1], sL[a][b - 1], sL[a + 1][b], sL[a - 1][b]);
     const ff vv = sV[ly][lx];
     // w = c0 v + ih2 Lv + (ih4/2) LLv + q v
-    sW[ly - 2][lx - 2] = ff_add(ff_add(ff_mul(c0, vv), ff_mul(ih2, Lv)),
-                                ff_add(ff_mul(hih4, LLv), ff_mul(sQ[ly - 2][lx - 2], vv)));
+    sW[ly - 2][lx - 2] = ff_dot4(c0, vv, ih2, Lv, hih4, LLv, sQ[ly - 2][lx - 2], vv);
   }
   __syncthreads();
   const ff fidt = ff_split(idt);
@@ -75,9 +83,8 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx < g.nx && gy < g.ny) {
       const int a = ty + 1, b = tx + 1;
-      const ff Lw = ff_lap(sW[a][b], sW[a][b + 1], sW[a][b - 1], sW[a + 1][b], sW[a - 1][b]);
-      const ff out = ff_add(ff_mul(sV[ty + R][tx + R], fidt), ff_neg(ff_mul(ih2, Lw)));
-      Jv[gx + (long long)g.nx * gy] = ff_to_double(out);
+      const ff Lw = ff_lap5(sW[a][b], sW[a][b + 1], sW[a][b - 1], sW[a + 1][b], sW[a - 1][b]);
+      Jv[gx + (long long)g.nx * gy] = ff_to_double(ff_dot2m(sV[ty + R][tx + R], fidt, ih2, Lw));
     }
   }
 }
@@ -120,17 +127,14 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
   __shared__ float sW[FAY - 4][FAX - 4];
   const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
   const int tid = threadIdx.x + threadIdx.y * 32;
+  const Stage sv(g, x0, y0, FTX, FTY, FR), sq(g, x0, y0, FTX, FTY, 1);
   for (int i = tid; i < FAX * FAY; i += 256) {
     const int ly = i / FAX, lx = i - ly * FAX;
-    const long long idx =
-        cell_index(x0 + lx - FR, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - FR, g.ny, g.neumann);
-    sV[ly][lx] = f32_cut(v[idx]);
+    sV[ly][lx] = f32_cut(v[sv.idx(g, lx, ly)]);
   }
   for (int i = tid; i < (FAX - 4) * (FAY - 4); i += 256) {
     const int ly = i / (FAX - 4), lx = i - ly * (FAX - 4);
-    const long long idx =
-        cell_index(x0 + lx - 1, g.nx, g.neumann) + (long long)g.nx * cell_index(y0 + ly - 1, g.ny, g.neumann);
-    sQ[ly][lx] = f32_cut(q[idx]);
+    sQ[ly][lx] = f32_cut(q[sq.idx(g, lx, ly)]);
   }
   __syncthreads();
   for (int i = tid; i < (FAX - 2) * (FAY - 2); i += 256) {

@@ -17,7 +17,8 @@
 // coefficients (the multi-dot products) are float-float too by default
 // (Dot::kFF: both operands split into float pairs, products with their exact
 // rounding error and the cross terms, running sums with two-sum), so the
-// orthogonalisation keeps FP64-class accuracy.  Dot::kF32 -- FP32 products of
+// orthogonalisation keeps FP64-class accuracy.  In both sweeps part of every
+// tile goes to the FP64 pipe instead (kPd below), which works beside the FP32 pipe.  Dot::kF32 -- FP32 products of
 // the vectors cut to 24-bit significands, about 2^-24 of |V_i| |w| per
 // product -- is a faster opt-in form (pfc_params.gmres_fast_dots) that leaves
 // the orthogonality of the new vector to the conditional second (DGKS) pass.
@@ -161,6 +162,11 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
 constexpr int kTile = 1024;
 constexpr int kStages = 6;
 constexpr int kPts = kTile / NT;
+// Float-float sweeps (the mixed path) send the first kPd of a thread's kPts points of every
+// tile to the FP64 pipe (one FMA each) and the rest to float-float on the FP32 pipe: both
+// give FP64-class sums, and the two pipes, each too slow alone for the HBM rate on GB300
+// (FP64 at 1/64 of FP32; float-float at ~30 instructions per element), run side by side.
+constexpr int kPd = 2;
 constexpr int kSweepThreads = NT + 32;  // consumers + the producer warp
 constexpr int kSweepMinCtas = 4;        // CTAs per SM the register budget allows (__launch_bounds__)
 
@@ -251,7 +257,7 @@ __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const doubl
       const double v = tb[i];
       if (D == kF32)
         af[k] = __fmaf_rn(f32_cut(v), wf[p], af[k]);
-      else if (D == kFF)
+      else if (D == kFF && p >= kPd)
         aff[k] = ff_acc(aff[k], ff_prod(ff_split(v), wff[p]));
       else
         acc[k] = fma(v, wv[p], acc[k]);
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
           const int i = tid + p * NT;
           wv[p] = i < cntp ? tb[i] : 0.0;
           if (D == kF32) wf[p] = f32_cut(wv[p]);
-          if (D == kFF) wff[p] = ff_split(wv[p]);
+          if (D == kFF && p >= kPd) wff[p] = ff_split(wv[p]);
         }
       }
       ring_release(rg, q++);
@@ -327,9 +333,9 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
 #pragma unroll
       for (int k = 0; k < G; ++k) acc[k] = f2d_bits(af[k]);
     }
-    if (D == kFF) {  // the pair's sum in FP64 (one FP64 add per value and thread)
+    if (D == kFF) {  // the FP64 part plus the pair's sum (two FP64 adds per value and thread)
 #pragma unroll
-      for (int k = 0; k < G; ++k) acc[k] = ff_to_double(aff[k]);
+      for (int k = 0; k < G; ++k) acc[k] += ff_to_double(aff[k]);
     }
     // Warp reduce-scatter of the G = 8 sums: each halving step sends the half of the
     // values a lane does not keep, so a lane adds 4 + 2 + 1 values and then
@@ -429,7 +435,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
           for (int p = 0; p < kPts; ++p) {
             const int i = tid + p * NT;
             if (i < cntp) {
-              if (FF)
+              if (FF && p >= kPd)
                 af[p] = ff_acc(af[p], ff_prod(cfk, ff_split(tb[i])));
               else
                 acc[p] = fma(ck, tb[i], acc[p]);
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
           for (int p = 0; p < kPts; ++p) {
             const int i = tid + p * NT;
             if (i < cntp) {
-              const double wn = FF ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
+              const double wn = FF && p >= kPd ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
               w[base + i] = wn;
               s2 = fma(wn, wn, s2);
               if (SUM) s1 += wn;

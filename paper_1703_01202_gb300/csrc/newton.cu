@@ -182,7 +182,76 @@ __global__ void k_step_end(StepCtl* c, StepHandles h, int graph) {
   set_cond(h.commit, graph, c->commit_go);
 }
 
+__global__ void k_mloop_begin(StepCtl* c, StepHandles h) {
+  c->loop_go = c->steps_done < c->steps_target && !c->failed;
+  c->cuts = 0;
+  c->dt = controller_dt(c->E_n, c->E_nm1, c->dt_prev, c->escale, c->dt_min, c->dt_max, c->eta,
+                        c->have_Em1 && c->have_prev_dt);
+  cudaGraphSetConditional(h.mloop, c->loop_go ? 1u : 0u);
+}
+
+__global__ void k_mstep_prep(StepCtl* c) {
+  c->idt = 1.0 / c->dt;
+  c->refactor = 1;
+}
+
+// After one attempt of a step (the graph step's status in c): keep it and go on, retry with
+// dt / 2 (Newton or GMRES failed and halvings remain), or stop the loop with the failure.
+__global__ void k_mstep_end(StepCtl* c, const double* red45, pfc_step_info* rec, StepHandles h) {
+  // kernels of the attempt (as the host counts a graph step) and this loop's own two per attempt
+  c->kernels += 2 + 4 + (c->commit_go ? 3 : 0) + 6LL * c->m + (long long)c->n_factor * (2 + c->chunked) +
+                4LL * c->n_cycles + 5LL * c->n_restarts + 3LL * c->n_trials + (long long)c->gm_total * c->body_kernels;
+  const int st = c->status;
+  if ((st == PFC_ENEWTON || st == PFC_EGMRES) && c->cuts < c->dt_halvings) {
+    c->dt *= 0.5;
+    c->cuts += 1;
+  } else {
+    pfc_step_info& r = rec[c->steps_done];
+    r.status = st;
+    r.newton_its = c->m;
+    r.gmres_its = c->gm_total;
+    r.ls_cuts = c->cuts_total;
+    r.dt = c->dt;
+    r.res_norm0 = c->r0;
+    r.res_norm = c->rnorm;
+    r.guess_used = PFC_GUESS_PREV;
+    r.dt_cuts = c->cuts;
+    r.energy = 0.0;
+    r.mass = 0.0;
+    if (st == PFC_OK) {
+      const double E = red45[0] * c->hd;
+      r.energy = E;
+      r.mass = red45[1] * c->hd;
+      c->E_nm1 = c->E_n;
+      c->E_n = E;
+      c->have_Em1 = 1;
+      c->dt_prev = c->dt;
+      c->have_prev_dt = 1;
+      c->steps_done += 1;
+      c->cuts = 0;
+      c->dt = controller_dt(c->E_n, c->E_nm1, c->dt_prev, c->escale, c->dt_min, c->dt_max, c->eta, true);
+    } else {
+      c->failed = st;
+    }
+  }
+  c->loop_go = c->steps_done < c->steps_target && !c->failed;
+  cudaGraphSetConditional(h.mloop, c->loop_go ? 1u : 0u);
+}
+
 }  // namespace
+
+void launch_mloop_begin(StepCtl* c, const StepHandles& h, cudaStream_t st) {
+  k_mloop_begin<<<1, 1, 0, st>>>(c, h);
+  count_launches(1);
+}
+void launch_mstep_prep(StepCtl* c, cudaStream_t st) {
+  k_mstep_prep<<<1, 1, 0, st>>>(c);
+  count_launches(1);
+}
+void launch_mstep_end(StepCtl* c, const double* red45, void* rec, const StepHandles& h, cudaStream_t st) {
+  k_mstep_end<<<1, 1, 0, st>>>(c, red45, static_cast<pfc_step_info*>(rec), h);
+  count_launches(1);
+}
 
 void launch_newton_begin(StepCtl* c, const double* nrm2, IterArgs* ia, IterArgs* ia2, const StepHandles& h,
                          int graph, cudaStream_t st) {

@@ -107,7 +107,8 @@ struct pfc_state {
   pfc::IterArgs* ia;    // Arnoldi iteration arguments (device): vectors of iteration j, q, 1/dt
   pfc::IterArgs* ia2;   // the restart's J S -> W with this step's 1/dt (device)
   pfc::StepHandles hs;  // conditional handles of the step graph
-  cudaStream_t cs[3];   // capture streams of the nested bodies (graph form)
+  cudaStream_t cs[4];   // capture streams of the nested bodies (graph form; one more level in a batch graph)
+  pfc_step_info* recs;  // device records of the batch form's time loop (kBatchRecs)
   cudaGraph_t sgraph;
   cudaGraphExec_t sexec;
   bool graph_failed;    // capture or instantiation failed once: keep the host-driven step
@@ -345,9 +346,12 @@ void update_lists(std::vector<int>* upd, std::vector<int>* upd_n) {
 // large power of two (the Gram-Schmidt sweeps read all of them at the same offsets).
 size_t basis_stride(long long N) { return ((size_t)N + 31) / 32 * 32 + 17 * 32; }
 
+// Steps the batch form's device time loop runs per graph launch (records kept on the device).
+constexpr int kBatchRecs = 64;
+
 struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
-      tabs, feat, iargs, iargs2, sctl, order, X, Yb, mu, mut, smid, smidt;
+      tabs, feat, iargs, iargs2, sctl, recs, order, X, Yb, mu, mut, smid, smidt;
   // 3D
   size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
   size_t total;
@@ -440,6 +444,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
   pl->iargs = L.take(sizeof(pfc::IterArgs));
   pl->iargs2 = L.take(sizeof(pfc::IterArgs));
   pl->sctl = L.take(sizeof(pfc::StepCtl));
+  pl->recs = L.take(sizeof(pfc_step_info) * kBatchRecs);
   pl->order = L.take(sizeof(int) * (pl->nblocks + 16));
   pl->feat = d3 ? 0 : L.take(vec * 3);
   if (d3) {
@@ -1017,10 +1022,10 @@ bool capture_body(pfc_state* s, cudaGraph_t body, cudaStream_t cs, F emit) {
 
 // Queues the whole step of the graph form on s->st (which is being captured): every 1/dt
 // and line-search step is read from s->sc, every decision sets a conditional handle.
-bool emit_step_graph(pfc_state* s) {
+bool emit_step_graph(pfc_state* s, int depth0 = 0) {
   pfc::StepHandles& h = s->hs;
   const int m = s->p.gmres_restart;
-  cudaStream_t* cs = s->cs;
+  cudaStream_t* cs = s->cs + depth0;  // nested bodies at depth d are captured on cs[d]
   if (!new_handle(s->st, &h.newton) || !new_handle(s->st, &h.commit)) return false;
   if (eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, 1.0, s->F, nullptr, s->q, 0, true)) return false;
   pfc::launch_newton_begin(s->sc, s->red, s->ia, s->ia2, h, 1, s->st);
@@ -1227,7 +1232,7 @@ bool batch_graph_ok(pfc_state** states, int count) {
   for (int i = 0; i < count; ++i) {
     const pfc_state* s = states[i];
     if (s->dim != 2 || !s->p.use_graph || s->st == nullptr || s->prof || s->graph_failed ||
-        s->p.guess != PFC_GUESS_PREV || s->device != states[0]->device)
+        s->p.guess != PFC_GUESS_PREV || s->p.reuse_factor != 0 || s->device != states[0]->device)
       return false;
     for (int k = 0; k < i; ++k)
       if (states[k]->st == s->st) return false;
@@ -1251,8 +1256,28 @@ void destroy_batch_graph(BatchGraph* b) {
   *b = BatchGraph();
 }
 
-// Captures every state's step into one graph: the batch stream forks into each state's stream,
-// which records its step (nested bodies on its own helper streams), and joins back.
+// One state's branch of a batch graph, queued on s->st (being captured): a while loop over its
+// time steps -- the step's dt from Eq. (sencondt) on the device, Phi_0 = phi^n, the whole step
+// graph, then record, retry with dt / 2 or stop -- so that every state advances through its
+// own steps, however long its Newton and GMRES iterations take, within one graph launch.
+bool emit_time_loop(pfc_state* s) {
+  if (!new_handle(s->st, &s->hs.mloop)) return false;
+  pfc::launch_mloop_begin(s->sc, s->hs, s->st);
+  cudaGraph_t body;
+  return add_cond(s->st, s->hs.mloop, cudaGraphCondTypeWhile, &body) &&
+         capture_body(s, body, s->cs[0], [&] {
+           pfc::launch_mstep_prep(s->sc, s->st);
+           if (cudaMemcpyAsync(s->Phi, s->phin, sizeof(double) * s->g.n, cudaMemcpyDeviceToDevice, s->st) !=
+               cudaSuccess)
+             return false;
+           if (!emit_step_graph(s, 1)) return false;
+           pfc::launch_mstep_end(s->sc, s->red + 4, s->recs, s->hs, s->st);
+           return cudaGetLastError() == cudaSuccess;
+         });
+}
+
+// Captures every state's time loop into one graph: the batch stream forks into each state's
+// stream, which records its loop (nested bodies on its own helper streams), and joins back.
 int build_batch_graph(pfc_state** states, int count, BatchGraph* b) {
   CU(cudaSetDevice(states[0]->device));
   CU(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
@@ -1269,7 +1294,7 @@ int build_batch_graph(pfc_state** states, int count, BatchGraph* b) {
             cudaEventRecord(b->fork, b->st) == cudaSuccess;
   for (int i = 0; i < count && ok; ++i) {
     pfc_state* s = states[i];
-    ok = cudaStreamWaitEvent(s->st, b->fork, 0) == cudaSuccess && emit_step_graph(s) &&
+    ok = cudaStreamWaitEvent(s->st, b->fork, 0) == cudaSuccess && emit_time_loop(s) &&
          cudaEventRecord(b->join[i], s->st) == cudaSuccess && cudaStreamWaitEvent(b->st, b->join[i], 0) == cudaSuccess;
   }
   cudaGraph_t g = nullptr;
@@ -1284,20 +1309,16 @@ int build_batch_graph(pfc_state** states, int count, BatchGraph* b) {
   return PFC_OK;
 }
 
-// One step of every live state with one graph launch.  A state whose step fails with
-// PFC_ENEWTON / PFC_EGMRES is retried alone with half the time step (dt_halvings), as pfc_run
-// does; a state that failed for good keeps its branch in the graph with newton_max_it = 0,
-// which leaves its fields unchanged.  Records go to rec[i * stride].
-int batch_step(pfc_state** states, int count, BatchGraph* b, std::vector<int>& rc, pfc_step_info* rec, int stride) {
-  std::vector<double> dts(count, 0.0);
-  std::vector<char> refac(count, 0);
+// k steps of every live state with one graph launch: each state's branch runs its own time loop
+// on the device (controller, retries with dt / 2 as pfc_run does, records).  The host uploads the
+// states' controller state and tolerances, launches once, and reads back the control blocks and
+// records.  Records of state i go to rec[i * stride + t], t < its steps done (and its failure).
+int batch_chunk(pfc_state** states, int count, BatchGraph* b, std::vector<int>& rc, pfc_step_info* rec, int stride,
+                int k) {
   for (int i = 0; i < count; ++i) {
     pfc_state* s = states[i];
-    pfc_next_dt(s, &dts[i]);
-    s->ref_norm = -1.0;
-    refac[i] = needs_factor(s, dts[i]);
     pfc::StepCtl* c = s->sc_h;
-    c->idt = 1.0 / dts[i];
+    memset(c, 0, sizeof(*c));
     c->ref_norm = -1.0;
     c->newton_rtol = s->p.newton_rtol;
     c->newton_atol = s->p.newton_atol;
@@ -1305,63 +1326,51 @@ int batch_step(pfc_state** states, int count, BatchGraph* b, std::vector<int>& r
     c->gmres_atol = s->p.gmres_atol;
     c->ls_alpha = s->p.ls_alpha;
     c->reorth_eta2 = s->p.gmres_reorth_eta * s->p.gmres_reorth_eta;
-    c->newton_max_it = rc[i] == PFC_OK ? s->p.newton_max_it : 0;
+    c->newton_max_it = s->p.newton_max_it;
     c->ls_max_cuts = s->p.ls_max_cuts;
     c->gmres_max_it = s->p.gmres_max_it;
-    c->refactor = refac[i];
-    CU(cudaMemcpyAsync(s->sc, c, offsetof(pfc::StepCtl, r0), cudaMemcpyHostToDevice, b->st));
-    CU(cudaMemcpyAsync(s->Phi, s->phin, sizeof(double) * s->g.n, cudaMemcpyDeviceToDevice, b->st));  // Phi_0 = phi^n
+    c->refactor = 1;
+    c->E_n = s->E_n;
+    c->E_nm1 = s->E_nm1;
+    c->dt_prev = s->dt_prev;
+    c->have_Em1 = s->have_Em1;
+    c->have_prev_dt = s->have_prev_dt;
+    c->dt_min = s->p.dt_min;
+    c->dt_max = s->p.dt_max;
+    c->eta = s->p.eta;
+    c->escale = s->p.energy_scaled ? 1.0 / (s->g.hd * (double)s->g.n) : 1.0;
+    c->hd = s->g.hd;
+    c->steps_target = rc[i] == PFC_OK ? k : 0;
+    c->dt_halvings = s->p.dt_halvings;
+    c->body_kernels = arnoldi_body_kernels(s);
+    c->chunked = s->fs.variant == pfc::kChunkedVariant;
+    CU(cudaMemcpyAsync(s->sc, c, sizeof(*c), cudaMemcpyHostToDevice, b->st));
   }
   CU(cudaGraphLaunch(b->ge, b->st));
   pfc::count_graph_launch();
+  std::vector<std::vector<pfc_step_info>> recs(count);
   for (int i = 0; i < count; ++i) {
     pfc_state* s = states[i];
+    recs[i].resize(k);
     CU(cudaMemcpyAsync(s->sc_h, s->sc, sizeof(pfc::StepCtl), cudaMemcpyDeviceToHost, b->st));
-    CU(cudaMemcpyAsync(s->red_h + 4, s->red + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    CU(cudaMemcpyAsync(recs[i].data(), s->recs, sizeof(pfc_step_info) * k, cudaMemcpyDeviceToHost, b->st));
   }
   CU(cudaStreamSynchronize(b->st));
   for (int i = 0; i < count; ++i) {
-    if (rc[i] != PFC_OK) continue;
     pfc_state* s = states[i];
     const pfc::StepCtl& c = *s->sc_h;
-    pfc::count_launches(graph_step_launches(s, c));
-    if (refac[i] && c.n_factor > 0) {
-      s->factors_ok = c.status != PFC_ESINGULAR;
-      s->factor_dt = dts[i];
-      s->factor_age = 0;
-    } else if (!refac[i]) {
-      ++s->factor_age;
-    }
-    pfc_step_info info{};
-    info.dt = dts[i];
-    info.guess_used = PFC_GUESS_PREV;
-    info.newton_its = c.m;
-    info.gmres_its = c.gm_total;
-    info.ls_cuts = c.cuts_total;
-    info.res_norm0 = c.r0;
-    info.res_norm = c.rnorm;
-    int st = c.status;
-    if (st == PFC_OK) {
-      const double E = s->red_h[4] * s->g.hd;
-      s->E_nm1 = s->E_n;
-      s->E_n = E;
-      s->have_Em1 = true;
-      s->dt_prev = dts[i];
-      s->have_prev_dt = true;
-      info.energy = E;
-      info.mass = s->red_h[5] * s->g.hd;
-    }
-    int cuts = 0;
-    double dt = dts[i];
-    while ((st == PFC_ENEWTON || st == PFC_EGMRES) && cuts < s->p.dt_halvings) {  // retry alone with dt / 2
-      dt *= 0.5;
-      ++cuts;
-      st = pfc_step(s, dt, &info);
-    }
-    info.status = st;
-    info.dt_cuts = cuts;
-    if (rec) rec[(size_t)i * stride] = info;
-    rc[i] = st;
+    pfc::count_launches(c.kernels + 1);  // the loop's kernels and its first loop test
+    if (rc[i] != PFC_OK) continue;
+    s->E_n = c.E_n;
+    s->E_nm1 = c.E_nm1;
+    s->dt_prev = c.dt_prev;
+    s->have_Em1 = c.have_Em1 != 0;
+    s->have_prev_dt = c.have_prev_dt != 0;
+    s->factors_ok = false;  // the loop refactors every step
+    const int done = c.steps_done + (c.failed ? 1 : 0);
+    if (rec)
+      for (int t = 0; t < done && t < k; ++t) rec[(size_t)i * stride + t] = recs[i][t];
+    if (c.failed) rc[i] = c.failed;
   }
   return PFC_OK;
 }
@@ -1544,6 +1553,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->ia = (pfc::IterArgs*)at(pl.iargs);
   s->ia2 = (pfc::IterArgs*)at(pl.iargs2);
   s->sc = (pfc::StepCtl*)at(pl.sctl);
+  s->recs = (pfc_step_info*)at(pl.recs);
   s->fs.order = (const int*)at(pl.order);
   if (cudaMallocHost((void**)&s->ctl_h, sizeof(GmresCtl)) != cudaSuccess ||
       cudaMallocHost((void**)&s->ctl_hb[0], sizeof(GmresCtl)) != cudaSuccess ||
@@ -1885,12 +1895,9 @@ int pfc_next_dt(pfc_state* s, double* dt_out) {
   if (!s || !dt_out) return PFC_EINVAL;
   const double area = s->g.hd * (double)s->g.n;
   const double scale = s->p.energy_scaled ? 1.0 / area : 1.0;
-  double dt = s->p.dt_min;
-  if (s->have_Em1 && s->have_prev_dt) {  // Eq. (sencondt)
-    const double fp = (s->E_n - s->E_nm1) * scale / s->dt_prev;
-    dt = std::max(s->p.dt_min, s->p.dt_max / std::sqrt(1.0 + s->p.eta * fp * fp));
-  }
-  *dt_out = dt;
+  // Eq. (sencondt); the same arithmetic as the batch form's device time loop
+  *dt_out = pfc::controller_dt(s->E_n, s->E_nm1, s->dt_prev, scale, s->p.dt_min, s->p.dt_max, s->p.eta,
+                               s->have_Em1 && s->have_prev_dt);
   return PFC_OK;
 }
 
@@ -2012,11 +2019,10 @@ int pfc_run_batch(pfc_state** states, int count, int nsteps, pfc_step_info* per_
     if (n < nsteps) {
       BatchGraph bg;
       int brc = build_batch_graph(states, count, &bg);
-      if (brc == PFC_OK) {
-        for (; n < nsteps; ++n) {
-          brc = batch_step(states, count, &bg, rc, per_step ? per_step + n : nullptr, nsteps);
-          if (brc != PFC_OK) break;
-        }
+      while (brc == PFC_OK && n < nsteps) {
+        const int k = std::min(kBatchRecs, nsteps - n);
+        brc = batch_chunk(states, count, &bg, rc, per_step ? per_step + n : nullptr, nsteps, k);
+        n += k;
       }
       destroy_batch_graph(&bg);
       if (brc != PFC_OK) return brc;

@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -93,10 +94,18 @@ struct StepCtl {
   int newton_go, factor_go, cycle_go, restart_go, ls_go, commit_go;
   // what ran (the host counts the launches of a graph step from these)
   int n_factor, n_cycles, n_restarts, n_trials;
+  // time loop of the batch form (pfc_run_batch): the adaptive step of Eq. (sencondt), retries
+  // with dt / 2, per-step records, all on the device
+  double dt, dt_prev, E_n, E_nm1;   // controller state
+  double dt_min, dt_max, eta, escale, hd;
+  int have_Em1, have_prev_dt;
+  int steps_target, steps_done, cuts, dt_halvings, failed, loop_go;
+  int body_kernels, chunked;        // kernels of one Arnoldi iteration; 1: factor + chunk records
+  long long kernels;                // kernels the time loop has run
 };
 // Conditional handles of a step graph (unused when the host drives the step).
 struct StepHandles {
-  cudaGraphConditionalHandle newton, factor, cycle, arnoldi, restart, ls, commit;
+  cudaGraphConditionalHandle newton, factor, cycle, arnoldi, restart, ls, commit, mloop;
 };
 
 // Scalars the host reads back after a reduction.
@@ -360,6 +369,25 @@ void launch_copy_if_ok(const StepCtl* c, const CopyPairs& cp, long long n, cudaS
 void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st);
 void launch_newton_next(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
 void launch_step_end(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
+// Batch form's device time loop: the loop test, the next step's dt (or the halved retry), and
+// the bookkeeping after a step (record into rec[steps_done], energy history, retry or stop).
+// rec points to pfc_step_info records (include/pfc.h).
+void launch_mloop_begin(StepCtl* c, const StepHandles& h, cudaStream_t st);
+void launch_mstep_prep(StepCtl* c, cudaStream_t st);
+void launch_mstep_end(StepCtl* c, const double* red45, void* rec, const StepHandles& h, cudaStream_t st);
+// The time step Eq. (sencondt) gives (the same arithmetic on host and device).
+__host__ __device__ inline double controller_dt(double E_n, double E_nm1, double dt_prev, double escale, double dt_min,
+                                                double dt_max, double eta, bool have) {
+  if (!have) return dt_min;
+#ifdef __CUDA_ARCH__
+  const double fp = __ddiv_rn(__dmul_rn(__dsub_rn(E_n, E_nm1), escale), dt_prev);
+  const double d = __ddiv_rn(dt_max, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(eta, fp), fp))));
+#else
+  const double fp = (E_n - E_nm1) * escale / dt_prev;
+  const double d = dt_max / std::sqrt(1.0 + eta * fp * fp);
+#endif
+  return d > dt_min ? d : dt_min;
+}
 void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double tol, double reorth_eta2,
                        cudaStream_t st);
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st);

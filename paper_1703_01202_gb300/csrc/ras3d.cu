@@ -15,6 +15,8 @@
 // neighbour outside the block reads zero and needs no bounds test.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "../../include/pfc.h"
 #include "pfc_internal.cuh"
 #include "pfc_tma.cuh"
@@ -160,14 +162,18 @@ __global__ void __launch_bounds__(NT) k_factor3d(Geo g, const BlockDesc* __restr
   }
 }
 
+// Levels of factor rows in flight per block (the ring's depth, at most kMaxStages3; the launch
+// picks it, see apply3d_dispatch).
+constexpr int kMaxStages3 = 8;
+
 template <typename TC, typename TS>
 __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __restrict__ blocks, Ras3D R,
                                                     const double* __restrict__ rin, const double* __restrict__ rscale,
                                                     double* __restrict__ z, const int* __restrict__ skip,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err, int stages) {
   if (skip && *skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[kMaxStages3];
   __shared__ int s_poff[kNOff];
   __shared__ int s_fail;
   const BlockDesc B = blocks[blockIdx.x];
@@ -179,27 +185,24 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   const TS* Lp = (const TS*)R.Lp + blockIdx.x * R.sLU;
   const TS* Up = (const TS*)R.Up + blockIdx.x * R.sLU;
   const size_t stage_elems = (size_t)R.max_level_rows * 32;
-  TS* stage0 = reinterpret_cast<TS*>(smem);
-  TS* stage1 = stage0 + stage_elems;
+  TS* stage_base = reinterpret_cast<TS*>(smem);
   if (threadIdx.x < kNOff) s_poff[threadIdx.x] = S.poff[threadIdx.x];
   const int nl = S.nlev;
   const int total = 2 * nl;  // forward levels 0..nl-1, then backward levels nl-1..0
-  auto issue = [&](int t) {
+  auto issue = [&](int t) {  // level copy t into stage t % stages
     const int l = t < nl ? t : 2 * nl - 1 - t;
     const TS* src = (t < nl ? Lp : Up) + (size_t)lev[l] * 32;
     const uint32_t bytes = (uint32_t)((lev[l + 1] - lev[l]) * 32 * sizeof(TS));
-    TS* dst = (t & 1) ? stage1 : stage0;
+    const int st = t % stages;
     fence_proxy_async();
-    mbar_expect_tx(&bar[t & 1], bytes);
-    bulk_g2s(dst, src, bytes, &bar[t & 1]);
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(stage_base + st * stage_elems, src, bytes, &bar[st]);
   };
   if (threadIdx.x == 0) {
     s_fail = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int st = 0; st < stages; ++st) mbar_init(&bar[st], 1);
     fence_mbar_init();
-    issue(0);
-    if (total > 1) issue(1);
+    for (int t = 0; t < stages && t < total; ++t) issue(t);
   }
   // restriction R_k^delta into the padded block (the ring stays zero)
   for (int r = threadIdx.x; r < S.nrows; r += NT) {
@@ -209,23 +212,21 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
                            (long long)g.nx * (wrap(B.y0 + b, g.ny) + (long long)g.ny * wrap(B.z0 + c, g.nz))];
   }
   __syncthreads();
-  uint32_t ph0 = 0, ph1 = 0;
   for (int t = 0; t < total; ++t) {
-    const int st = t & 1;
+    const int st = t % stages;
     if (threadIdx.x == 0) {
-      if (!mbar_wait_bounded(&bar[st], st ? ph1 : ph0)) s_fail = 1;
+      if (!mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
     }
-    if (st) ph1 ^= 1; else ph0 ^= 1;
     __syncthreads();
-    if (s_fail) {  // give up: record, drain the copies in flight, leave
+    if (s_fail) {  // give up: record, drain the copies in flight (levels t .. t + stages - 1), leave
       if (threadIdx.x == 0) {
         atomicExch(err, PFC_ETIMEOUT);
-        mbar_wait_bounded(&bar[st], st ? ph1 ^ 1 : ph0 ^ 1);
-        if (t + 1 < total) mbar_wait_bounded(&bar[st ^ 1], st ? ph0 : ph1);
+        for (int u = t; u < t + stages && u < total; ++u)
+          mbar_wait_bounded(&bar[u % stages], (uint32_t)((u / stages) & 1));
       }
       return;
     }
-    const TS* data = st ? stage1 : stage0;
+    const TS* data = stage_base + st * stage_elems;
     // every thread reads the stage the waiting thread saw complete
     if (t < nl) {  // forward: y_r = b_r - sum_lower l_ro y_(r+o)
       const int l = t;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
       }
     }
     __syncthreads();  // level done, stage free
-    if (threadIdx.x == 0 && t + 2 < total) issue(t + 2);
+    if (threadIdx.x == 0 && t + stages < total) issue(t + stages);
   }
   const double sc = rscale ? *rscale : 1.0;
   for (int r = threadIdx.x; r < S.nrows; r += NT) {  // extension (R_k^0)^T: core rows only
@@ -273,9 +274,14 @@ void factor3d_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const
 template <typename TC, typename TS>
 void apply3d_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                       const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)R.max_level_rows * 32 * sizeof(TS);
+  // Two levels in flight.  Deeper rings were slower on GB300 (256^3, BF16: 3.3 ms per apply with 2
+  // stages, 8.7 ms with 4, 6.4 ms with 7): the ring's shared memory comes out of the SM's L1, and
+  // the solve vector's neighbour reads, which live in global memory, depend on L1 hits.
+  const size_t stage = (size_t)R.max_level_rows * 32 * sizeof(TS);
+  const int stages = 2;
+  const size_t smem = stages * stage;
   cudaFuncSetAttribute(k_ras_apply3d<TC, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ras_apply3d<TC, TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err);
+  k_ras_apply3d<TC, TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err, stages);
   count_launches(1);
 }
 

@@ -10,9 +10,10 @@ mass, Newton and GMRES iterations) and its final field phi, either
   * whole: phi rounded to the nearest multiple of 2^-32 (2.3e-10, far below the
     1e-8 parity tolerance) and stored as int64 with its bytes regrouped by
     significance so that zlib finds the long runs, or
-  * sampled: phi at a fixed set of cells (exact float64 values), for grids
-    too large to store whole; plus sum, sum of squares, min and max of the
-    whole field.
+  * sampled: phi at a set of cells (exact float64 values), for grids too
+    large to store whole -- rows, columns and random cells spread over the
+    grid plus every cell the run moved; and sum, sum of squares, min and max
+    of the whole field.
 """
 from __future__ import annotations
 

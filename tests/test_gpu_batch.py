@@ -45,7 +45,7 @@ def test_batch_equals_sequential_runs(env, prec):
     g0 = P.launch_counts()["graphs"]
     recs = P.run_batch(batch, 3)
     torch.cuda.synchronize()
-    assert P.launch_counts()["graphs"] - g0 == 2  # step 1 tunes on threads; steps 2-3: one graph each
+    assert P.launch_counts()["graphs"] - g0 == 1  # step 1 tunes on threads; steps 2-3: one graph launch
     for i, (g, phi) in enumerate(zip(gammas, phis)):
         s = _make(P, torch, shape, g, prec)
         s.set_field(phi)
@@ -159,3 +159,33 @@ def test_graph_steps_with_line_search_cuts_match_the_host_loop(env):
     phi = inputs.hex_seeds_2d(shape, H, nseeds=1, radius_cells=10, seed=3)
     out = _graph_vs_host(P, torch, shape, (3, 3), 1, 2, phi, fixed_dt=10.0, mobility=1, apply_variant=5)
     assert sum(r["ls_cuts"] for r in out[1][0]) > 0
+
+
+def test_batch_time_loop_retries_like_pfc_run(env):
+    """States whose steps fail (GMRES capped at 8 iterations) retry with dt / 2 inside the batch
+    graph's device time loop exactly as pfc_run retries them on the host: the same records
+    (dt, halvings, iterations) and bit-identical fields."""
+    P, torch = env
+    shape = (48, 48)
+    gammas = [0.2, 0.33, 0.28]
+    phis = [inputs.noise_field(shape, 0.07, 0.07, 1050 + i) for i in range(3)]
+
+    def make(g, st):
+        prm = P.default_params(sub=(3, 3), overlap=1, dt_min=0.01, dt_max=10.0, eta=5000.0, gmres_max_it=8,
+                               dt_halvings=12)
+        return P.Solver(shape, H, g, prm, stream=st)
+
+    batch = [make(g, torch.cuda.Stream()) for g in gammas]
+    for s, phi in zip(batch, phis):
+        s.set_field(phi)
+    g0 = P.launch_counts()["graphs"]
+    recs = P.run_batch(batch, 5)
+    assert P.launch_counts()["graphs"] - g0 == 1  # steps 2-5 of every state in one graph launch
+    assert sum(r["dt_cuts"] for rr in recs for r in rr[1:]) > 0
+    for i, (g, phi) in enumerate(zip(gammas, phis)):
+        s = make(g, None)
+        s.set_field(phi)
+        ref = s.run(5)
+        for key in ("dt", "dt_cuts", "newton_its", "gmres_its", "energy"):
+            assert [r[key] for r in recs[i]] == [r[key] for r in ref], (i, key)
+        np.testing.assert_array_equal(batch[i].get_field(), s.get_field())
