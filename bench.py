@@ -258,12 +258,15 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 
 
 # ---------------------------------------------------------------- solvers
+EXTRAS = ("hex2048", "bcc256", "batch32x256", "forms")  # the workloads after the 1024^2 line
 USE_GRAPH = [1]  # pfc_params.use_graph of every solver (--no-graph for ncu runs)
+APPLY_VARIANT = [-1]  # pfc_params.apply_variant of every solver (-1: autotuned; pinned for ncu runs)
 
 
 def make_solver(workload: str, prec: int, learned: bool = False, stream=True, **form):
     """A solver for a workload (fresh field set), its guess network and a close function."""
     form.setdefault("use_graph", USE_GRAPH[0])
+    form.setdefault("apply_variant", APPLY_VARIANT[0])
     import torch
 
     from paper_1703_01202_gb300 import inputs, pfc
@@ -552,6 +555,12 @@ def kernel_loop(args):
 
     build.build()
     w = inputs.workload(args.kernel_workload)
+    if args.kernel_grid:  # the workload's recipe on another grid (3D: a case small enough for ncu)
+        nd = len(w["shape"])
+        w["shape"] = (args.kernel_grid,) * nd
+        w["parts"] = (args.kernel_parts,) * nd
+        w["phi"] = (inputs.bcc_seeds_3d(w["shape"], w["h"], nseeds=1, d0=5 * math.pi, seed=1003) if nd == 3
+                    else inputs.hex_seeds_2d(w["shape"], w["h"], seed=1001))
     prec = {"all": 2, "f64": 0, "f32": 1, "bf16": 2, "bf16_learned": 2}[args.variant]
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec,
                                 apply_variant=args.apply_variant)
@@ -594,6 +603,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 2048^2, 256^3, ensemble and other-form workloads")
     ap.add_argument("--no-golden", action="store_true", help="skip the error runs against the oracle trajectories")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of the other workloads to run: " + ",".join(EXTRAS) + " (default all)")
     ap.add_argument("--no-graph", action="store_true",
                     help="profiling aid: host-driven steps (the same kernels; ncu cannot profile the kernel "
                          "nodes of graphs with conditional nodes)")
@@ -602,11 +613,15 @@ def main():
     ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
                     help="profiling aid: run one kernel family repeatedly on a workload (no bench line)")
     ap.add_argument("--kernel-workload", default=WORKLOAD)
+    ap.add_argument("--kernel-grid", type=int, default=0, help="--kernel-loop: cells per axis instead of the workload's")
+    ap.add_argument("--kernel-parts", type=int, default=4, help="--kernel-loop with --kernel-grid: cores per axis")
     ap.add_argument("--apply-variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
-                    help="2D Schwarz apply kernel for --kernel-loop (-1: autotuned)")
+                    help="Schwarz apply kernel of every solver (-1: autotuned; ncu's serialised replay would "
+                         "otherwise tune to another kernel than a plain run)")
     args = ap.parse_args()
     if args.no_graph:
         USE_GRAPH[0] = 0
+    APPLY_VARIANT[0] = args.apply_variant
     if args.kernel_loop:
         kernel_loop(args)
         return
@@ -685,28 +700,34 @@ def main():
         "errors_vs_oracle": head.get("errors_vs_oracle"),
         "variants": {k: strip(v) for k, v in variants.items()},
     }
-    if not args.no_extras:
+    extras = set(EXTRAS) if args.extras == "all" else set(args.extras.split(","))
+    if not args.no_extras and extras:
         # the other workloads, each on this rank's GPU
-        grid2048 = {}
-        for name, prec, lg, st in (("f64", 0, False, 20), ("f32", 1, False, 20), ("bf16", 2, False, 20),
-                                   ("bf16_learned", 2, True, 20)):
-            grid2048[name] = guarded(run_variant, "hex2048", prec, st, 3, world, local, learned=lg, profile_steps=2,
-                                     golden=None if args.no_golden else "hex2048_s3", hbm=hbm)
-        versus_f64(grid2048)
-        bcc = {}
-        for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
-            bcc[name] = guarded(run_variant, "bcc256", prec, 5, 1, world, local, profile_steps=1,
-                                golden=None if args.no_golden else "bcc64_s50", hbm=hbm)
-            if isinstance(bcc[name], dict) and "errors_vs_oracle" in bcc[name]:
-                bcc[name]["errors_vs_oracle"]["grid"] = "64^3 (the oracle trajectory's grid)"
-        line["workloads"] = {
-            "hex2048": {k: strip(v) for k, v in grid2048.items()},
-            "bcc256": {k: strip(v) for k, v in bcc.items()},
-            "batch32x256_bf16": guarded(run_batch32, max(2, args.steps // 2), 2),
-            "hex1024_mobility_f32": guarded(run_form, max(4, args.steps // 4), 3, 1, mobility=1),
-            "hex1024_neumann_bf16": guarded(run_form, max(4, args.steps // 4), 3, 2, boundary=1),
-            "crack4096x1024_bf16": guarded(run_form, max(4, args.steps // 4), 3, 2, workload="crack4096x1024"),
-        }
+        work = {}
+        if "hex2048" in extras:
+            grid2048 = {}
+            for name, prec, lg, st in (("f64", 0, False, 20), ("f32", 1, False, 20), ("bf16", 2, False, 20),
+                                       ("bf16_learned", 2, True, 20)):
+                grid2048[name] = guarded(run_variant, "hex2048", prec, st, 3, world, local, learned=lg,
+                                         profile_steps=2, golden=None if args.no_golden else "hex2048_s3", hbm=hbm)
+            versus_f64(grid2048)
+            work["hex2048"] = {k: strip(v) for k, v in grid2048.items()}
+        if "bcc256" in extras:
+            bcc = {}
+            for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
+                bcc[name] = guarded(run_variant, "bcc256", prec, 5, 1, world, local, profile_steps=1,
+                                    golden=None if args.no_golden else "bcc64_s50", hbm=hbm)
+                if isinstance(bcc[name], dict) and "errors_vs_oracle" in bcc[name]:
+                    bcc[name]["errors_vs_oracle"]["grid"] = "64^3 (the oracle trajectory's grid)"
+            work["bcc256"] = {k: strip(v) for k, v in bcc.items()}
+        if "batch32x256" in extras:
+            work["batch32x256_bf16"] = guarded(run_batch32, max(2, args.steps // 2), 2)
+        if "forms" in extras:
+            work["hex1024_mobility_f32"] = guarded(run_form, max(4, args.steps // 4), 3, 1, mobility=1)
+            work["hex1024_neumann_bf16"] = guarded(run_form, max(4, args.steps // 4), 3, 2, boundary=1)
+            work["crack4096x1024_bf16"] = guarded(run_form, max(4, args.steps // 4), 3, 2,
+                                                  workload="crack4096x1024")
+        line["workloads"] = work
     if rank == 0 and not args.no_cpu_baseline:
         r = oracle_whole_step(1)
         line["cpu_baseline"] = {"value": 1.0 / r["seconds"], "unit": "steps/s", "cores": 1, "kind": "oracle",

@@ -102,7 +102,12 @@ typedef struct {
      to 0-4 up to rounding in the storage type).
      -1 (default) times every kernel on the first factorisation and keeps the
      fastest (pfc_get_tuning reports the pick).
-     Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0 and 5. */
+     Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0 and 5.
+     3D grids: 0 solves with the block's solve vector in global memory; 1 keeps
+     the 22 wavefront levels a solve reads in shared memory (F32/BF16 factors,
+     blocks at most 39 cells in y and z, at most 256 rows per level; otherwise
+     pfc_create fails with PFC_EINVAL); -1 takes 1 where it can run, else 0.
+     The two give bitwise identical results; 2..5 are refused in 3D. */
   int apply_variant;
   /* pfc_run only: a step whose Newton or GMRES iteration fails (PFC_ENEWTON,
      PFC_EGMRES) is retried with half the time step, at most dt_halvings times
@@ -263,7 +268,11 @@ int pfc_mass(pfc_state* s, double* m);
    *norm (may be NULL). */
 int pfc_residual(pfc_state* s, const double* Phi, const double* phin, double dt, double* F_out,
                  double* norm);
-/* J v = v/dt - Delta_d(L_gamma v / 2 + q v), q = (3 Phi^2 + 2 Phi phi^n + phi^n^2)/4 (Eq. Jacobi). */
+/* J v = v/dt - Delta_d(L_gamma v / 2 + q v), q = (3 Phi^2 + 2 Phi phi^n + phi^n^2)/4 (Eq. Jacobi).
+   On the 2D mixed path (F32/BF16 factors, M = 1) the product runs as GMRES takes it: v is
+   copied into the state's first Krylov scratch vector and interior tiles stage v and q by TMA
+   tensor copies; a staging wait that runs out returns PFC_ETIMEOUT.  The field and the time-step
+   state are untouched. */
 int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v, double dt,
             double* Jv);
 /* Builds the subdomain factors of J(Phi, phi^n, dt) (Eq. Ak, improved BC) and
@@ -339,8 +348,8 @@ int pfc_profile_read(pfc_state* s, long long* apply_launches, double* apply_ms, 
    whole time step of one state, or one step of a whole ensemble). */
 int pfc_launch_counts(long long* kernels, long long* graphs);
 
-/* Autotuner report (2D).  *apply_variant: the Schwarz apply kernel in use
-   (pfc_params.apply_variant numbering).  apply_ms (optional, 6 floats): the
+/* Autotuner report.  *apply_variant: the Schwarz apply kernel in use
+   (pfc_params.apply_variant numbering; 3D: 0 or 1, fixed at pfc_create).  apply_ms (optional, 6 floats): the
    mean device milliseconds of one apply measured per kernel at the first
    factorisation, -1 for kernels not timed (not tuned yet, an explicit variant,
    or one that cannot run the blocks).  *graph (optional): 1 once GMRES cycles

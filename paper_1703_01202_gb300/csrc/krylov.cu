@@ -182,10 +182,12 @@ __device__ __forceinline__ Ring ring_at(unsigned char* smem) {
   return Ring{buf, bars, bars + kStages};
 }
 
-// Producer lane: the copy of element q (vector vp, local tile lt) into buffer q % kStages.
-__device__ __forceinline__ void ring_issue(const Ring& rg, int q, const double* vp, long long n, int lt) {
+// Producer lane: the copy of element q (vector vp, local tile lt of CTA cta of P) into buffer
+// q % kStages.
+__device__ __forceinline__ void ring_issue(const Ring& rg, int q, const double* vp, long long n, int lt, int cta,
+                                           int P) {
   const int st = q % kStages;
-  const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+  const long long base = (long long)(cta + (long long)lt * P) * kTile;
   const long long cnt = min((long long)kTile, n - base);
   const uint32_t bytes = (uint32_t)((cnt * 8 + 15) & ~15ll);  // an odd count reads the 8-byte pad
   fence_proxy_async();
@@ -197,13 +199,14 @@ __device__ __forceinline__ void ring_issue(const Ring& rg, int q, const double* 
 // free; vec(q) gives the source vector.  On a wait that runs out it records the error and
 // waits for every copy it issued before returning.
 template <typename VecOf>
-__device__ __forceinline__ void ring_produce(const Ring& rg, int total, long long n, int per, VecOf vec, int* err) {
+__device__ __forceinline__ void ring_produce(const Ring& rg, int total, long long n, int per, VecOf vec, int* err,
+                                             int cta, int P) {
   int issued = 0;
   bool ok = true;
   for (int q = 0; q < total; ++q) {
     const int st = q % kStages;
     if (q >= kStages && !(ok = mbar_wait_bounded(&rg.empty[st], (uint32_t)((q / kStages - 1) & 1)))) break;
-    ring_issue(rg, q, vec(q % per), n, q / per);
+    ring_issue(rg, q, vec(q % per), n, q / per, cta, P);
     issued = q + 1;
   }
   if (!ok) {
@@ -265,7 +268,7 @@ __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const doubl
   }
 }
 
-// partial[(g0 + k) * gridDim.x + blockIdx.x] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles.
+// partial[(g0 + k) * P + cta] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles (P CTAs per group).
 template <int D>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
@@ -279,12 +282,17 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   const Ring rg = ring_at(smem);
   __shared__ double red[NT / 32][G];
   __shared__ const double* sp[G + 1];
-  const int g0 = blockIdx.y * G;
-  const int cnt = max(0, min(G, nv - g0));  // 0 for spare groups of a graph-mode grid: they only take a ticket
+  // The 1D grid is split evenly over the groups of G vectors this sweep has (however many
+  // the grid was sized for): P CTAs per group, CTA c of group g takes tiles c, c + P, ...;
+  // CTAs past gy * P only take a ticket.
+  const int gy = (nv + G - 1) / G, P = gridDim.x / gy;
+  const int grp = blockIdx.x / P, cta = blockIdx.x - grp * P;
+  const int g0 = grp * G;
+  const int cnt = grp < gy ? max(0, min(G, nv - g0)) : 0;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid <= G) sp[tid] = tid == 0 ? w : (tid - 1 < cnt ? vec_at(v0, tab, g0 + tid - 1) : w);
   const long long ntile = (n + kTile - 1) / kTile;
-  const int my_tiles = cnt > 0 && blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int my_tiles = cnt > 0 && cta < ntile ? (int)((ntile - 1 - cta) / P + 1) : 0;
   const int per = 1 + cnt, total = my_tiles * per;
   ring_init(rg);  // also makes sp visible
   double acc[G];
@@ -297,12 +305,12 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     aff[k] = {0.0f, 0.0f};
   }
   if (wid == NT / 32) {  // producer warp
-    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err);
+    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err, cta, P);
   } else {
     bool ok = true;
     int q = 0;
     for (int lt = 0; lt < my_tiles && ok; ++lt) {
-      const long long base = (long long)(blockIdx.x + (long long)lt * gridDim.x) * kTile;
+      const long long base = (long long)(cta + (long long)lt * P) * kTile;
       const int cntp = (int)min((long long)kTile, n - base);
       double wv[kPts];
       float wf[kPts];
@@ -372,9 +380,9 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   if (tid < cnt) {
     double s = 0.0;
     for (int qq = 0; qq < NT / 32; ++qq) s += red[qq][tid];
-    partial[(size_t)(g0 + tid) * gridDim.x + blockIdx.x] = s;
+    partial[(size_t)(g0 + tid) * P + cta] = s;
   }
-  if (tail.counter) last_cta_tail(tail, partial, nv, gridDim.x);
+  if (tail.counter) last_cta_tail(tail, partial, nv, P);
 }
 
 // w = w + sign * sum_k coef[k] X_k over this CTA's tiles (the tile of w comes last);
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   ring_init(rg);  // also makes c, cf, sp visible
   double s2 = 0.0, s1 = 0.0;
   if (wid == NT / 32) {  // producer warp
-    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err);
+    if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err, blockIdx.x, gridDim.x);
   } else {
     bool ok = true;
     int q = 0;
@@ -528,6 +536,7 @@ __global__ void k_iter_setup(const GmresCtl* __restrict__ ctl, const double* con
   ia->j = j;
   ia->v = vtab[j];
   ia->z = const_cast<double*>(ztab[j]);
+  ia->zplane = j;
   ia->w = const_cast<double*>(vtab[j + 1]);
   ia->scale = &ctl->scale[j];
 }
@@ -554,7 +563,7 @@ void launch_multidot(const double* v0, const double* const* tab, int nv, const d
   const int gy = (std::max(nv, nv_grid) + G - 1) / G;
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
-  const dim3 grid(bx, gy);
+  const dim3 grid(bx * gy);  // split over the groups the sweep has inside the kernel
   const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
 #define PFC_DOT(D)                                                                                    \
   do {                                                                                                \

@@ -53,6 +53,7 @@ struct pfc_state {
   BlockDesc* blocks_dev;
   int nblocks;
   pfc::FactorStore fs;
+  pfc::JvpMaps jmaps{};  // TMA maps of the basis Z and of q for the mixed path's JVP
   pfc::Decomp2 dc;  // 2D decomposition (AS / right-RAS overlap sums)
   // variable mobility: mu and s = (Phi + phi^n)/2 at the iterate of q (mu, sm) and of the trial q (mut, smt)
   double *mu = nullptr, *mut = nullptr, *sm = nullptr, *smt = nullptr;
@@ -178,6 +179,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
     return PFC_EINVAL;
   if (p->factor_prec < PFC_F64 || p->factor_prec > PFC_BF16) return PFC_EINVAL;
   if (p->apply_variant < -1 || p->apply_variant >= pfc::kApplyVariants) return PFC_EINVAL;
+  if (g->dim == 3 && p->apply_variant > 1) return PFC_EINVAL;
   if (p->dt_halvings < 0 || p->dt_halvings > 30) return PFC_EINVAL;
   if (!(p->gmres_reorth_eta >= 0.0 && p->gmres_reorth_eta < 1.0)) return PFC_EINVAL;
   if (p->use_graph != 0 && p->use_graph != 1) return PFC_EINVAL;
@@ -200,6 +202,7 @@ int validate(const pfc_grid* g, const pfc_params* p) {
       // 3D blocks: at least 7 cells per axis (offset order = row order), and the
       // block plus its 3-cell ring must not wrap onto itself (A_k = R J R^T pattern)
       if (core_min + 2 * p->overlap < 7 || core_max + 2 * p->overlap + 3 > g->n[a]) return PFC_EINVAL;
+      if (core_max + 2 * p->overlap > 1023) return PFC_EINVAL;  // row cells packed in 10 bits per axis
     }
   }
   return PFC_OK;
@@ -250,7 +253,7 @@ void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>
 // 3D shape tables: one entry per distinct block extent.
 struct Shapes3 {
   std::vector<pfc::Shape3> shapes;
-  std::vector<int> block_shape, lev_start, rowpad, rowlin, rowof;
+  std::vector<int> block_shape, lev_start, rowpad, rowabc;
   int nrows_max = 0, pad_max = 0, max_level_rows = 0;
 };
 
@@ -286,14 +289,12 @@ void build_shapes3(const std::vector<BlockDesc>& blocks, Shapes3* S) {
       sh.nlev = (b.bx - 1) + 3 * (b.by - 1) + 7 * (b.bz - 1) + 1;
       sh.lev_off = (int)S->lev_start.size();
       sh.row_off = (int)S->rowpad.size();
-      sh.pad_off = (int)S->rowof.size();
       for (int o = 0; o < 63; ++o) sh.poff[o] = off[o][0] + sh.px * (off[o][1] + sh.py * off[o][2]);
       // rows in level order, ascending linear index inside a level
       std::vector<std::vector<int>> bylev(sh.nlev);
       for (int c = 0; c < b.bz; ++c)
         for (int bb = 0; bb < b.by; ++bb)
           for (int a = 0; a < b.bx; ++a) bylev[a + 3 * bb + 7 * c].push_back(a + b.bx * (bb + b.by * c));
-      std::vector<int> rowof((size_t)sh.px * sh.py * sh.pz, -1);
       int r = 0;
       for (int l = 0; l < sh.nlev; ++l) {
         S->lev_start.push_back(r);
@@ -302,13 +303,11 @@ void build_shapes3(const std::vector<BlockDesc>& blocks, Shapes3* S) {
           const int a = li % b.bx, bb = (li / b.bx) % b.by, c = li / (b.bx * b.by);
           const int pp = (a + 3) + sh.px * ((bb + 3) + sh.py * (c + 3));
           S->rowpad.push_back(pp);
-          S->rowlin.push_back(li);
-          rowof[pp] = r;
+          S->rowabc.push_back(a | (bb << 10) | (c << 20));
           ++r;
         }
       }
       S->lev_start.push_back(r);
-      S->rowof.insert(S->rowof.end(), rowof.begin(), rowof.end());
       S->nrows_max = std::max(S->nrows_max, sh.nrows);
       S->pad_max = std::max(S->pad_max, sh.px * sh.py * sh.pz);
       found = (int)S->shapes.size();
@@ -353,7 +352,7 @@ struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
       tabs, feat, iargs, iargs2, sctl, recs, order, X, Yb, mu, mut, smid, smidt;
   // 3D
-  size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowlin, rowof, upd, upd_n, Lp, Up, work, ypad;
+  size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowabc, Lp, Up, work, ypad;
   size_t total;
   int nblocks, n_max, kl_max;
   size_t sL, sU, sP;
@@ -401,7 +400,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
     pl->xstage = 0;
     build_shapes3(blocks, &pl->sh3);
     pl->sLU3 = (size_t)pl->sh3.nrows_max * 32;
-    pl->sWork3 = (size_t)pl->sh3.nrows_max * 64;
+    pl->sWork3 = (size_t)pl->sh3.nrows_max * 32;  // U part of every block cell
     pl->sPad3 = ((size_t)pl->sh3.pad_max + 31) / 32 * 32;
   }
   const size_t vec = (size_t)N * 8;
@@ -455,10 +454,7 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
     pl->block_shape = L.take(sizeof(int) * S.block_shape.size());
     pl->lev_start = L.take(sizeof(int) * S.lev_start.size());
     pl->rowpad = L.take(sizeof(int) * S.rowpad.size());
-    pl->rowlin = L.take(sizeof(int) * S.rowlin.size());
-    pl->rowof = L.take(sizeof(int) * S.rowof.size());
-    pl->upd = L.take(sizeof(int) * 31 * 32);
-    pl->upd_n = L.take(sizeof(int) * 32);
+    pl->rowabc = L.take(sizeof(int) * S.rowabc.size());
     pl->Lp = L.take(pl->sLU3 * es * pl->nblocks);
     pl->Up = L.take(pl->sLU3 * es * pl->nblocks);
     pl->work = L.take(pl->sWork3 * tc * pl->nblocks);
@@ -599,17 +595,20 @@ int dot_mode(const pfc_state* s) {
   return s->p.gmres_fast_dots ? pfc::kDotF32 : pfc::kDotFF;
 }
 
+// zplane: v = Z_zplane of the basis and q = s->q, so the product may stage both by TMA (-1: not).
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
-         const pfc::IterArgs* ia = nullptr) {
+         const pfc::IterArgs* ia = nullptr, int zplane = -1) {
   if (s->dim == 2 && s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
     const bool trial = q != nullptr && q == s->qt;
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu, trial ? s->smt : s->sm);
   } else if (s->dim == 2 && s->fs.prec != PFC_F64 && s->p.jvp_fp32)  // mixed path, opt-in: plain FP32
-    pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia);
+    pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1);
   else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
-    pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
+    pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1);
   else if (s->dim == 2)
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
+  else if (s->fs.prec != PFC_F64)  // 3D mixed path: float-float passes on the FP32 pipe
+    pfc::launch_jvp3d_ff(s->g, v, q, idt, out, s->T1, s->T2, skip, s->st);
   else
     pfc::launch_jvp3d(s->g, v, nullptr, q, idt, out, s->T1, s->T2, skip, s->st);
 }
@@ -813,7 +812,7 @@ int arnoldi_host(pfc_state* s, double idt) {
       precond(s, vj, &s->ctl->scale[j], zj, done);
       PROF_END(ps, PFC_PROF_APPLY, j, s->apply_bytes, 0.0, apply_stored(s));
       PROF_BEGIN(ps);
-      jvp(s, zj, s->q, idt, w, done);
+      jvp(s, zj, s->q, idt, w, done, nullptr, j);
       PROF_END(ps, PFC_PROF_JVP, j, 24.0 * N);  // reads v, q; writes Jv
       for (int pass = 0; pass < gs_passes(s); ++pass) {
         pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, ticket(s), nullptr};
@@ -1637,10 +1636,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     R.block_shape = (const int*)at(pl.block_shape);
     R.lev_start = (const int*)at(pl.lev_start);
     R.rowpad = (const int*)at(pl.rowpad);
-    R.rowlin = (const int*)at(pl.rowlin);
-    R.rowof = (const int*)at(pl.rowof);
-    R.upd = (const int*)at(pl.upd);
-    R.upd_n = (const int*)at(pl.upd_n);
+    R.rowabc = (const int*)at(pl.rowabc);
     R.Lp = at(pl.Lp);
     R.Up = at(pl.Up);
     R.work = at(pl.work);
@@ -1650,9 +1646,18 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     R.sPad = pl.sPad3;
     R.prec = p->factor_prec;
     R.max_level_rows = S.max_level_rows;
+    R.max_byz = 0;
+    for (const pfc::Shape3& sh : S.shapes) R.max_byz = std::max(R.max_byz, std::max(sh.by, sh.bz));
+    R.window = 0;
+    if (p->apply_variant != 0) {  // -1: the window kernel where it fits; 1: only the window kernel
+      R.window = pfc::apply3d_window_ok(R) ? 1 : 0;
+      if (p->apply_variant == 1 && !R.window) {
+        pfc_destroy(s);
+        return PFC_EINVAL;
+      }
+    }
+    s->fs.variant = R.window;  // reported by pfc_get_tuning
     R.shift = 0.1;  // fraction of the block's mean |a_ii| added to the diagonal before ILU(0)
-    std::vector<int> upd, upd_n;
-    update_lists(&upd, &upd_n);
     const size_t tc = p->factor_prec == PFC_F64 ? 8 : 4;
     auto put = [&](const void* dst, const void* src, size_t bytes) {
       return cudaMemcpyAsync((void*)dst, src, bytes, cudaMemcpyHostToDevice, s->st) == cudaSuccess;
@@ -1661,9 +1666,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
         !put(R.block_shape, S.block_shape.data(), sizeof(int) * S.block_shape.size()) ||
         !put(R.lev_start, S.lev_start.data(), sizeof(int) * S.lev_start.size()) ||
         !put(R.rowpad, S.rowpad.data(), sizeof(int) * S.rowpad.size()) ||
-        !put(R.rowlin, S.rowlin.data(), sizeof(int) * S.rowlin.size()) ||
-        !put(R.rowof, S.rowof.data(), sizeof(int) * S.rowof.size()) ||
-        !put(R.upd, upd.data(), sizeof(int) * upd.size()) || !put(R.upd_n, upd_n.data(), sizeof(int) * upd_n.size()) ||
+        !put(R.rowabc, S.rowabc.data(), sizeof(int) * S.rowabc.size()) ||
         cudaMemsetAsync(R.ypad, 0, pl.sPad3 * tc * pl.nblocks, s->st) != cudaSuccess ||
         cudaStreamSynchronize(s->st) != cudaSuccess) {
       pfc_destroy(s);
@@ -1686,6 +1689,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   ia0.sm = ia20.sm = s->sm;
   ia20.z = s->S;
   ia20.w = s->W;
+  ia0.zplane = ia20.zplane = -1;
+  if (g->dim == 2 && !p->mobility) pfc::encode_jvp_maps(s->g, s->Zbuf, s->vstride, p->gmres_restart, s->q, &s->jmaps);
   if (cudaMemcpyAsync(s->ia, &ia0, sizeof ia0, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
       cudaMemcpyAsync(s->ia2, &ia20, sizeof ia20, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
       cudaMemsetAsync(s->sc, 0, sizeof(pfc::StepCtl), s->st) != cudaSuccess ||
@@ -2060,6 +2065,18 @@ int pfc_jvp(pfc_state* s, const double* Phi, const double* phin, const double* v
   if (s->p.mobility) {  // q, mu and s of (Phi, phi^n) from the residual (F into scratch)
     int rc = eval_residual(s, Phi, nullptr, 0.0, false, phin, 1.0 / dt, s->Ft, nullptr, s->qt, 2);
     if (rc) return rc;
+  } else if (s->dim == 2 && s->fs.prec != PFC_F64) {
+    // the mixed path's product as GMRES takes it: v as basis vector Z_0 and q in s->q, so that
+    // interior tiles stage by TMA (both are scratch between steps)
+    pfc::launch_qcoef(s->g, Phi, phin, s->q, s->st);
+    CU(cudaMemcpyAsync(s->Zbuf, v, sizeof(double) * (size_t)s->g.n, cudaMemcpyDeviceToDevice, s->st));
+    CU(cudaMemsetAsync(s->status_dev, 0, 2 * sizeof(int), s->st));
+    jvp(s, s->Zbuf, s->q, 1.0 / dt, Jv, nullptr, nullptr, 0);
+    CU(cudaGetLastError());
+    int st[2];
+    CU(cudaMemcpyAsync(st, s->status_dev, sizeof st, cudaMemcpyDeviceToHost, s->st));
+    CU(cudaStreamSynchronize(s->st));
+    return st[1] ? st[1] : PFC_OK;
   } else {
     pfc::launch_qcoef(s->g, Phi, phin, s->qt, s->st);
   }

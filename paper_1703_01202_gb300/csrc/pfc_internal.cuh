@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libpfc.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only; the driver's encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -74,6 +75,7 @@ struct IterArgs {
   double idt;           // 1 / dt
   const double* mu;     // variable mobility: mu and the midpoint s = (Phi + phi^n)/2 of this
   const double* sm;     // Newton iteration (null with M = 1)
+  int zplane;           // z = Z_zplane of the basis (the JVP may stage it by TMA); -1: z is not
 };
 
 // Device-side control of one time step (inexact Newton, Sec. 4): every decision of
@@ -143,12 +145,28 @@ void launch_jvp2d(const Geo& g, const double* v, const double* vscale, const dou
                   const int* skip, cudaStream_t st, const IterArgs* ia = nullptr, const double* mu = nullptr,
                   const double* sm = nullptr);
 void launch_energy2d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
-// The same JVP in float-float arithmetic on the FP32 pipe (jvp_ff.cu), for the mixed path.
+// Tensor maps of the mixed path's JVP (jvp_ff.cu): the basis Z_0..Z_(m-1) as an nx x ny x m
+// tensor (planes vstride doubles apart) and the Jacobian coefficient q as an nx x ny one.  An
+// interior tile stages its halo boxes of Z_j and q with two TMA tensor copies.
+struct JvpMaps {
+  CUtensorMap z;
+  CUtensorMap q;
+  int ok;
+};
+constexpr int kJvpBoxVX = 40, kJvpBoxVY = 22, kJvpBoxQX = 36, kJvpBoxQY = 18;
+// Encodes the two maps; maps->ok stays 0 (plain loads) when the grid is too small for the boxes,
+// nx is odd (row strides must be multiples of 16 bytes) or the driver's encoder is unavailable.
+void encode_jvp_maps(const Geo& g, const double* Zbuf, size_t vstride, int m, const double* q, JvpMaps* maps);
+// The same JVP in float-float arithmetic on the FP32 pipe (jvp_ff.cu), for the mixed path.  With
+// maps (ok) and v = Z_zj of the basis (zj >= 0, or ia->zplane in graph mode) and q the mapped
+// one, interior tiles stage by TMA; a staging wait that runs out records PFC_ETIMEOUT in *err.
 void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                     const int* skip, cudaStream_t st, const IterArgs* ia = nullptr);
+                     const int* skip, cudaStream_t st, const IterArgs* ia = nullptr, const JvpMaps* maps = nullptr,
+                     int zj = -1, int* err = nullptr);
 // The same JVP in plain FP32 (opt-in on the mixed path, pfc_params.jvp_fp32).
 void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, const int* skip,
-                      cudaStream_t st, const IterArgs* ia = nullptr);
+                      cudaStream_t st, const IterArgs* ia = nullptr, const JvpMaps* maps = nullptr, int zj = -1,
+                      int* err = nullptr);
 void launch_qcoef(const Geo& g, const double* Phi, const double* phin, double* q, cudaStream_t st);
 
 // ---- Schwarz preconditioner (ras2d.cu)
@@ -250,6 +268,9 @@ void launch_residual3d(const Geo& g, const double* P, const double* phin, double
                        double* T1, double* T2, double* partial, int* nparts, cudaStream_t st);
 void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
                   double* T1, double* T2, const int* skip, cudaStream_t st);
+// The same product in float-float arithmetic (the mixed path); T1, T2 hold float pairs.
+void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
+                     const int* skip, cudaStream_t st);
 void launch_energy3d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
 
 // ---- 3D Schwarz preconditioner with shifted ILU(0) subdomain solves (ras3d.cu)
@@ -262,8 +283,7 @@ struct Shape3 {
   int bx, by, bz, px, py, pz;
   int nrows, nlev;
   int lev_off;  // level starts: lev_start[lev_off .. lev_off + nlev]
-  int row_off;  // rowpad / rowlin: [row_off .. row_off + nrows)
-  int pad_off;  // rowof: [pad_off .. pad_off + px*py*pz)
+  int row_off;  // rowpad / rowabc: [row_off .. row_off + nrows)
   int poff[kNOff];
 };
 struct Ras3D {
@@ -271,19 +291,21 @@ struct Ras3D {
   const int* block_shape;
   const int* lev_start;
   const int* rowpad;  // padded linear position of each row
-  const int* rowlin;  // block-local linear index of each row
-  const int* rowof;   // padded position -> row (-1 on the ring)
-  const int* upd;     // update lists: upd[o1 * 32 + t] = o2 | (o3 << 8), count in upd_n[o1]
-  const int* upd_n;
+  const int* rowabc;  // block-local cell (a, b, c) of each row, packed a | b << 10 | c << 20
   void* Lp;           // per block nrows_max x 32: L multipliers of offsets 0..30 (storage type)
   void* Up;           // per block nrows_max x 32: [0] inverted diagonal, [1..31] offsets 32..62
-  void* work;         // per block nrows_max x 64 working rows (compute type)
+  void* work;         // per block nrows_max x 32: U parts of factored rows by block cell (compute type)
   void* ypad;         // per block pad_max (compute type): solve vector with zero ring
   size_t sLU, sWork, sPad;
   int prec;
   int max_level_rows;
+  int max_byz;        // largest block extent in y or z
+  int window;         // 1: FP32 solves in the shared-memory level window (apply3d_window_ok)
   double shift;       // diagonal shift, relative to the block's mean |a_ii|
 };
+// Whether the window apply can run these blocks: FP32/BF16 factors, blocks at most 39 cells in y
+// and z, levels of at most 256 rows, and the window plus two factor levels in shared memory.
+bool apply3d_window_ok(const Ras3D& R);
 void launch_factor3d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin343, const Ras3D& R, int* status, cudaStream_t st);
 void launch_ras_apply3d(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,

@@ -10,9 +10,23 @@
 // One CTA owns one block.  Rows are stored in level order, 32 factor entries
 // per row (L: offsets 0..30; U: the inverted diagonal then offsets 32..62),
 // so each level's factor data is one contiguous chunk that a TMA bulk copy
-// brings into shared memory while the previous level is being solved.  The
-// solve vector lives in a padded copy of the block (3-cell zero ring), so a
-// neighbour outside the block reads zero and needs no bounds test.
+// brings into shared memory while the previous level is being solved.  Inside
+// a level the entries are stored 16 bytes of a row at a time, row after row
+// (entry o of the level's row i at ((o / E) n_l + i) E + o % E, E entries per
+// 16 bytes, n_l rows), so that threads reading the same 16 bytes of
+// consecutive rows read consecutive addresses.
+//
+// Two apply kernels give identical results.  The general one keeps the solve
+// vector in a padded copy of the block in global memory (3-cell zero ring, so
+// a neighbour outside the block reads zero and needs no bounds test).  The
+// window kernel (FP32 solves of blocks at most 39 cells in y and z) keeps in
+// shared memory only the levels a row can still read: an offset moves at most
+// 21 levels (dc = -3), so 22 level slices, each the block's (b, c) plane with a
+// zero margin, hold every value the solve reads; the cell (a, b, c) of level l
+// sits at (b, c) of slice l mod 22, where a = l - 3b - 7c.  A (b, c) that has
+// no cell at a level holds zero there, which is what a neighbour outside the
+// block must read.  Both sum a row's 31 products as four partial sums of 8
+// entries, (s0 + s1) + (s2 + s3): four independent chains for the FMA pipeline.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -25,11 +39,6 @@ namespace pfc {
 namespace {
 
 constexpr int NT = 256;
-
-__device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
-}
 
 template <typename T>
 __device__ __forceinline__ T to_store(double v);
@@ -44,128 +53,217 @@ __device__ __forceinline__ TC from_store(TS v) { return (TC)v; }
 template <>
 __device__ __forceinline__ float from_store<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ void offset_of(int o, int* da, int* db, int* dc) {
-  // o-th entry of the lexicographic (dc, db, da) list of |d|_1 <= 3
+// o-th entry of the lexicographic (dc, db, da) list of the offsets with |d|_1 <= 3: 0..30 lower,
+// 31 the centre, 32..62 upper
+struct Off3 {
+  int a, b, c;
+};
+__host__ __device__ constexpr Off3 off63(int o) {
   int idx = 0;
   for (int c = -3; c <= 3; ++c)
     for (int b = -3; b <= 3; ++b)
-      for (int a = -3; a <= 3; ++a) {
-        if (abs(a) + abs(b) + abs(c) > 3) continue;
-        if (idx == o) {
-          *da = a;
-          *db = b;
-          *dc = c;
-          return;
+      for (int a = -3; a <= 3; ++a)
+        if ((a < 0 ? -a : a) + (b < 0 ? -b : b) + (c < 0 ? -c : c) <= 3) {
+          if (idx == o) return Off3{a, b, c};
+          ++idx;
         }
-        ++idx;
-      }
+  return Off3{0, 0, 0};
 }
 
+__device__ __forceinline__ void abc_of(int v, int* a, int* b, int* c) {
+  *a = v & 1023;
+  *b = (v >> 10) & 1023;
+  *c = v >> 20;
+}
+// Periodic image of a block cell's coordinate (blocks never reach a second period).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+__device__ __forceinline__ long long gidx(const Geo& g, const BlockDesc& B, int a, int b, int c) {
+  return wrap1(B.x0 + a, g.nx) + (long long)g.nx * (wrap1(B.y0 + b, g.ny) + (long long)g.ny * wrap1(B.z0 + c, g.nz));
+}
+// Element of entry o of row i (of n) inside a level's factor data (16-byte units row after row).
+template <typename TS>
+__device__ __forceinline__ int lev_elem(int o, int i, int n) {
+  constexpr int E = 16 / (int)sizeof(TS);
+  return ((o / E) * n + i) * E + (o % E);
+}
+
+template <typename TC>
+__device__ __forceinline__ TC fma_tc(TC a, TC b, TC c);
+template <>
+__device__ __forceinline__ float fma_tc<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_tc<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Conversions between the solve type and FP64 by integer operations on the bit patterns: the
+// hardware's FP64 <-> FP32 conversions run on GB300's FP64 pipe (1/64 of the FP32 rate), which the
+// level sweeps would otherwise wait on.  Both round as the hardware does (to nearest, ties to
+// even); zeros, subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if ((b << 1) == 0ull) return __uint_as_float(sign);  // +-0
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  if (e < -126 || e > 127) return (float)x;
+  const unsigned long long m = b & 0xfffffffffffffull;
+  unsigned f = sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
+  if (rem > half || (rem == half && (f & 1u))) ++f;  // a carry into the exponent is the correct rounding
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u && (u & 0x7fffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  if (ex == 0u || ex == 255u) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+template <typename TC>
+__device__ __forceinline__ TC tc_of(double x) { return (TC)x; }
+template <>
+__device__ __forceinline__ float tc_of<float>(double x) { return d2f_rn(x); }
+__device__ __forceinline__ double wide(double x) { return x; }
+__device__ __forceinline__ double wide(float x) { return f2d_exact(x); }
+
+// ILU(0) of one block, level by level (the rows of a level depend only on earlier levels), one
+// warp per row.  Row i's 63 pattern entries sit in the warp's shared-memory row; the U parts
+// (inverted diagonal, 31 upper entries) of finished rows sit in global memory by block cell, so
+// that lane j fetches entry j of every lower neighbour's U part at once before the eliminations.
+// Elimination by lower offset o1 (ascending, i.e. ascending neighbour row k = i + o1):
+// l_ik = a_ik / u_kk, then lane j takes the update a_io3 -= l_ik u_kj of its upper entry j,
+// o3 = o1 + o2(j) inside the pattern; the targets of one o1 are distinct, so one step is one
+// warp-wide update.
+template <typename TC>
+__host__ __device__ constexpr int factor_threads() { return sizeof(TC) == 8 ? 512 : 1024; }
+
 template <typename TC, typename TS>
-__global__ void __launch_bounds__(NT) k_factor3d(Geo g, const BlockDesc* __restrict__ blocks,
-                                                 const double* __restrict__ q, double idt,
-                                                 const double* __restrict__ lin343, Ras3D R,
-                                                 int* __restrict__ status) {
+__global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const BlockDesc* __restrict__ blocks,
+                                                                   const double* __restrict__ q, double idt,
+                                                                   const double* __restrict__ lin343, Ras3D R,
+                                                                   int* __restrict__ status) {
+  constexpr int FT = factor_threads<TC>(), FW = FT / 32;
   __shared__ int s_off[kNOff][3];
-  __shared__ double s_red[NT / 32];
+  __shared__ short s_idx[343];           // pattern index of offset (da, db, dc), -1 outside it
+  __shared__ signed char s_tgt[31][32];  // o3 of lower offset o1 and U entry j, -1: none
+  __shared__ double s_red[FW];
   __shared__ double s_sigma;
-  extern __shared__ __align__(16) unsigned char smem[];
-  TC* rowbuf = reinterpret_cast<TC*>(smem) + threadIdx.x * 64;  // this thread's working row
+  __shared__ TC s_row[FW][64];
   const BlockDesc B = blocks[blockIdx.x];
   const Shape3 S = R.shapes[R.block_shape[blockIdx.x]];
-  const int* rowpad = R.rowpad + S.row_off;
-  const int* rowlin = R.rowlin + S.row_off;
-  const int* rowof = R.rowof + S.pad_off;
+  const int* rowabc = R.rowabc + S.row_off;
   const int* lev = R.lev_start + S.lev_off;
-  TC* W = (TC*)R.work + blockIdx.x * R.sWork;
+  TC* WU = (TC*)R.work + blockIdx.x * R.sWork;  // 32 entries per block cell
   TS* Lp = (TS*)R.Lp + blockIdx.x * R.sLU;
   TS* Up = (TS*)R.Up + blockIdx.x * R.sLU;
-  if (threadIdx.x < kNOff) offset_of(threadIdx.x, &s_off[threadIdx.x][0], &s_off[threadIdx.x][1], &s_off[threadIdx.x][2]);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < 343; i += FT) s_idx[i] = -1;
+  if (tid < kNOff) {
+    const Off3 d = off63(tid);
+    s_off[tid][0] = d.a;
+    s_off[tid][1] = d.b;
+    s_off[tid][2] = d.c;
+  }
   __syncthreads();
+  if (tid < kNOff) s_idx[(s_off[tid][2] + 3) * 49 + (s_off[tid][1] + 3) * 7 + s_off[tid][0] + 3] = (short)tid;
+  __syncthreads();
+  for (int e = tid; e < 31 * 32; e += FT) {
+    const int o1 = e >> 5, j = e & 31;
+    int t3 = -1;
+    if (j > 0) {
+      const int a = s_off[o1][0] + s_off[31 + j][0], b = s_off[o1][1] + s_off[31 + j][1],
+                c = s_off[o1][2] + s_off[31 + j][2];
+      if (abs(a) + abs(b) + abs(c) <= 3) t3 = s_idx[(c + 3) * 49 + (b + 3) * 7 + a + 3];
+    }
+    s_tgt[o1][j] = (signed char)t3;
+  }
   const double ih2 = g.ih2;
-  auto qat = [&](int a, int b, int c) {
-    return q[wrap(B.x0 + a, g.nx) + (long long)g.nx * (wrap(B.y0 + b, g.ny) + (long long)g.ny * wrap(B.z0 + c, g.nz))];
-  };
+  auto qat = [&](int a, int b, int c) { return q[gidx(g, B, a, b, c)]; };
   // sigma = shift * mean |a_ii| of the block matrix
   double dsum = 0.0;
-  for (int r = threadIdx.x; r < S.nrows; r += NT) {
-    const int li = rowlin[r];
-    const int a = li % S.bx, b = (li / S.bx) % S.by, c = li / (S.bx * S.by);
+  for (int r = tid; r < S.nrows; r += FT) {
+    int a, b, c;
+    abc_of(rowabc[r], &a, &b, &c);
     dsum += fabs(idt + lin343[171] + 6.0 * ih2 * qat(a, b, c));
   }
   for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = dsum;
+  if (lane == 0) s_red[wid] = dsum;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+    for (int w = 0; w < FW; ++w) t += s_red[w];
     s_sigma = R.shift * t / (double)S.nrows;
   }
   __syncthreads();
   const double sigma = s_sigma;
-  // rows of A_k + sigma I (zero outside the block)
-  for (int r = threadIdx.x; r < S.nrows; r += NT) {
-    const int li = rowlin[r];
-    const int a = li % S.bx, b = (li / S.bx) % S.by, c = li / (S.bx * S.by);
-    for (int o = 0; o < 64; ++o) {
-      double v = 0.0;
-      if (o < kNOff) {
-        const int da = s_off[o][0], db = s_off[o][1], dc = s_off[o][2];
-        const int a2 = a + da, b2 = b + db, c2 = c + dc;
-        if (a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0 && c2 < S.bz) {
-          const int ad = abs(da) + abs(db) + abs(dc);
-          v = lin343[(dc + 3) * 49 + (db + 3) * 7 + (da + 3)];
-          if (ad <= 1) v -= (ad == 0 ? -6.0 * ih2 : ih2) * qat(a2, b2, c2);
-          if (ad == 0) v += idt + sigma;
-        }
-      }
-      W[(size_t)r * 64 + o] = (TC)v;
-    }
-  }
-  __syncthreads();
-  // ILU(0), row by row in level order: a_ik /= a_kk, a_ij -= a_ik a_kj on the pattern
+  TC* row = s_row[wid];
+  auto cell = [&](int a, int b, int c) { return a + S.bx * (b + S.by * c); };
   for (int l = 0; l < S.nlev; ++l) {
-    for (int r = lev[l] + threadIdx.x; r < lev[l + 1]; r += NT) {
-      for (int o = 0; o < 64; ++o) rowbuf[o] = W[(size_t)r * 64 + o];
-      const int p = rowpad[r];
-      for (int o1 = 0; o1 < 31; ++o1) {
-        TC lik = rowbuf[o1];
-        if (lik == (TC)0) continue;
-        const int k = rowof[p + S.poff[o1]];
-        if (k < 0) continue;
-        const TC* Wk = W + (size_t)k * 64;
-        lik *= Wk[31];  // inverted diagonal of the finished row k
-        rowbuf[o1] = lik;
-        const int cnt = R.upd_n[o1];
-        for (int t = 0; t < cnt; ++t) {
-          const int e = R.upd[o1 * 32 + t];
-          rowbuf[e >> 8] -= lik * Wk[e & 255];
+    const int r0 = lev[l], n = lev[l + 1] - r0;
+    for (int i = wid; i < n; i += FW) {
+      int a, b, c;
+      abc_of(rowabc[r0 + i], &a, &b, &c);
+      // row i of A_k + sigma I (zero outside the block): lane j builds entries j and 32 + j
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = lane + 32 * h;
+        double v = 0.0;
+        if (o < kNOff) {
+          const int da = s_off[o][0], db = s_off[o][1], dc = s_off[o][2];
+          const int a2 = a + da, b2 = b + db, c2 = c + dc;
+          if (a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0 && c2 < S.bz) {
+            const int ad = abs(da) + abs(db) + abs(dc);
+            v = lin343[(dc + 3) * 49 + (db + 3) * 7 + (da + 3)];
+            if (ad <= 1) v -= (ad == 0 ? -6.0 * ih2 : ih2) * qat(a2, b2, c2);
+            if (ad == 0) v += idt + sigma;
+          }
         }
+        row[o] = (TC)v;
       }
-      TC d = rowbuf[31];
+      // entry `lane` of the U part of every lower neighbour inside the block
+      TC u[31];
+#pragma unroll
+      for (int o1 = 0; o1 < 31; ++o1) {
+        const int a2 = a + s_off[o1][0], b2 = b + s_off[o1][1], c2 = c + s_off[o1][2];
+        const bool in = a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0;  // c2 <= c < bz
+        u[o1] = in ? WU[(size_t)cell(a2, b2, c2) * 32 + lane] : (TC)0;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int o1 = 0; o1 < 31; ++o1) {
+        const int a2 = a + s_off[o1][0], b2 = b + s_off[o1][1], c2 = c + s_off[o1][2];
+        if (!(a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0)) continue;  // k outside: no entry
+        TC lik = row[o1];
+        if (lik == (TC)0) continue;  // the same value in every lane
+        lik *= __shfl_sync(0xffffffffu, u[o1], 0);  // a_ik / u_kk
+        const int t3 = s_tgt[o1][lane];
+        __syncwarp();  // every lane has read a_ik
+        if (lane == 0) row[o1] = lik;
+        if (t3 >= 0) row[t3] = fma_tc<TC>(-lik, u[o1], row[t3]);
+        __syncwarp();
+      }
+      TC d = row[31];
       if (d == (TC)0) {
-        atomicExch(status, PFC_ESINGULAR);
+        if (lane == 0) atomicExch(status, PFC_ESINGULAR);
         d = (TC)1;
       }
-      rowbuf[31] = (TC)1 / d;
-      for (int o = 0; o < 64; ++o) W[(size_t)r * 64 + o] = rowbuf[o];
+      const TC inv = (TC)1 / d;
+      // the finished row: its U part for the rows below, L and U in the storage type
+      const TC uj = lane == 0 ? inv : row[31 + lane];
+      WU[(size_t)cell(a, b, c) * 32 + lane] = uj;
+      Lp[(size_t)r0 * 32 + lev_elem<TS>(lane, i, n)] = to_store<TS>(lane < 31 ? (double)row[lane] : 0.0);
+      Up[(size_t)r0 * 32 + lev_elem<TS>(lane, i, n)] = to_store<TS>((double)uj);
+      __syncwarp();  // the warp's row buffer is free for its next row
     }
-    __syncthreads();
-  }
-  // pack into the storage precision
-  for (int r = threadIdx.x; r < S.nrows; r += NT) {
-    const TC* Wr = W + (size_t)r * 64;
-    for (int o = 0; o < 32; ++o) {
-      Lp[(size_t)r * 32 + o] = to_store<TS>(o < 31 ? (double)Wr[o] : 0.0);
-      Up[(size_t)r * 32 + o] = to_store<TS>((double)Wr[31 + o]);
-    }
+    __syncthreads();  // level done: its U parts are visible to the next level's warps
   }
 }
 
-// Levels of factor rows in flight per block (the ring's depth, at most kMaxStages3; the launch
-// picks it, see apply3d_dispatch).
+// Levels of factor rows in flight per block (the ring's depth, at most kMaxStages3).
 constexpr int kMaxStages3 = 8;
 
+// General apply: the solve vector in a padded copy of the block in global memory, one thread per
+// row.
 template <typename TC, typename TS>
 __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __restrict__ blocks, Ras3D R,
                                                     const double* __restrict__ rin, const double* __restrict__ rscale,
@@ -179,7 +277,7 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   const BlockDesc B = blocks[blockIdx.x];
   const Shape3 S = R.shapes[R.block_shape[blockIdx.x]];
   const int* rowpad = R.rowpad + S.row_off;
-  const int* rowlin = R.rowlin + S.row_off;
+  const int* rowabc = R.rowabc + S.row_off;
   const int* lev = R.lev_start + S.lev_off;
   TC* Y = (TC*)R.ypad + blockIdx.x * R.sPad;
   const TS* Lp = (const TS*)R.Lp + blockIdx.x * R.sLU;
@@ -206,10 +304,9 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   }
   // restriction R_k^delta into the padded block (the ring stays zero)
   for (int r = threadIdx.x; r < S.nrows; r += NT) {
-    const int li = rowlin[r];
-    const int a = li % S.bx, b = (li / S.bx) % S.by, c = li / (S.bx * S.by);
-    Y[rowpad[r]] = (TC)rin[wrap(B.x0 + a, g.nx) +
-                           (long long)g.nx * (wrap(B.y0 + b, g.ny) + (long long)g.ny * wrap(B.z0 + c, g.nz))];
+    int a, b, c;
+    abc_of(rowabc[r], &a, &b, &c);
+    Y[rowpad[r]] = tc_of<TC>(rin[gidx(g, B, a, b, c)]);
   }
   __syncthreads();
   for (int t = 0; t < total; ++t) {
@@ -229,24 +326,39 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
     const TS* data = stage_base + st * stage_elems;
     // every thread reads the stage the waiting thread saw complete
     if (t < nl) {  // forward: y_r = b_r - sum_lower l_ro y_(r+o)
-      const int l = t;
-      for (int r = lev[l] + threadIdx.x; r < lev[l + 1]; r += NT) {
-        const TS* lr = data + (size_t)(r - lev[l]) * 32;
-        const int p = rowpad[r];
-        TC acc = Y[p];
+      const int l = t, n = lev[l + 1] - lev[l];
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const int p = rowpad[lev[l] + i];
+        TC part[4];
 #pragma unroll
-        for (int o = 0; o < 31; ++o) acc -= from_store<TC, TS>(lr[o]) * Y[p + s_poff[o]];
-        Y[p] = acc;
+        for (int qq = 0; qq < 4; ++qq) {  // entries 8 qq .. 8 qq + 7, as the window kernel sums them
+          TC acc = qq == 0 ? Y[p] : (TC)0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int o = 8 * qq + k;
+            if (o < 31) acc = fma_tc<TC>(-from_store<TC, TS>(data[lev_elem<TS>(o, i, n)]), Y[p + s_poff[o]], acc);
+          }
+          part[qq] = acc;
+        }
+        Y[p] = (part[0] + part[1]) + (part[2] + part[3]);
       }
     } else {  // backward: x_r = (y_r - sum_upper u_ro x_(r+o)) / u_rr
-      const int l = 2 * nl - 1 - t;
-      for (int r = lev[l] + threadIdx.x; r < lev[l + 1]; r += NT) {
-        const TS* ur = data + (size_t)(r - lev[l]) * 32;
-        const int p = rowpad[r];
-        TC acc = Y[p];
+      const int l = 2 * nl - 1 - t, n = lev[l + 1] - lev[l];
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const int p = rowpad[lev[l] + i];
+        TC part[4];
 #pragma unroll
-        for (int o = 0; o < 31; ++o) acc -= from_store<TC, TS>(ur[1 + o]) * Y[p + s_poff[32 + o]];
-        Y[p] = acc * from_store<TC, TS>(ur[0]);
+        for (int qq = 0; qq < 4; ++qq) {  // U entry e = 8 qq + k >= 1 is offset 31 + e; entry 0 is 1 / u_rr
+          TC acc = qq == 0 ? Y[p] : (TC)0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int e = 8 * qq + k;
+            if (e >= 1)
+              acc = fma_tc<TC>(-from_store<TC, TS>(data[lev_elem<TS>(e, i, n)]), Y[p + s_poff[31 + e]], acc);
+          }
+          part[qq] = acc;
+        }
+        Y[p] = ((part[0] + part[1]) + (part[2] + part[3])) * from_store<TC, TS>(data[lev_elem<TS>(0, i, n)]);
       }
     }
     __syncthreads();  // level done, stage free
@@ -254,34 +366,257 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   }
   const double sc = rscale ? *rscale : 1.0;
   for (int r = threadIdx.x; r < S.nrows; r += NT) {  // extension (R_k^0)^T: core rows only
-    const int li = rowlin[r];
-    const int a = li % S.bx, b = (li / S.bx) % S.by, c = li / (S.bx * S.by);
+    int a, b, c;
+    abc_of(rowabc[r], &a, &b, &c);
     if (a >= B.ox && a < B.ox + B.cx && b >= B.oy && b < B.oy + B.cy && c >= B.oz && c < B.oz + B.cz)
-      z[wrap(B.x0 + a, g.nx) + (long long)g.nx * (wrap(B.y0 + b, g.ny) + (long long)g.ny * wrap(B.z0 + c, g.nz))] =
-          sc * (double)Y[rowpad[r]];
+      z[gidx(g, B, a, b, c)] = sc * wide(Y[rowpad[r]]);
+  }
+}
+
+// ---- Window apply (FP32 solves).  Level slice l mod kWinLevels holds the solve values of level l
+// at (b, c), zero where (b, c) has no cell at that level; a margin of 3 zero cells after the last
+// b and c serves both sides (b - 3..b - 1 of one row of the slice reads the margin of the row
+// before; c - 3..c - 1 of slice s the margin rows of slice s - 1, or the lead margin of slice 0).
+constexpr int kWinPb = 42;                 // slice extent in b and c: 39 cells and the margin
+constexpr int kWinSlot = kWinPb * kWinPb;  // floats per slice
+constexpr int kWinLevels = 22;             // the level itself and the 21 an offset reaches
+constexpr int kWinLead = 4 * kWinPb;       // margin before slice 0 (c = -3 with b < 0 reaches row -4)
+constexpr int kWinFloats = kWinLead + kWinLevels * kWinSlot;
+constexpr int kWinMaxByz = kWinPb - 3;
+static_assert(kWinSlot % 4 == 0 && kWinLead % 4 == 0 && (kWinFloats * 4) % 128 == 0, "16-byte zeroing, aligned stages");
+
+// Levels an offset moves: a + 3b + 7c.
+__host__ __device__ constexpr int lev_shift(int o) { return off63(o).a + 3 * off63(o).b + 7 * off63(o).c; }
+
+// acc[O / 8] -= cf[O] y(cell + d_O) for the lower offsets O..30: the neighbour sits sft =
+// -lev_shift(O) in 1..21 levels back, in slice (lm - sft) mod kWinLevels.  `base` is the
+// cell's own window index.  Four accumulators (entries 8q..8q+7): the general kernel's order.
+template <int O>
+__device__ __forceinline__ void win_lower(float* acc, const float* __restrict__ win, int base, int lm,
+                                          const float* cf) {
+  if constexpr (O < 31) {
+    constexpr int sft = -lev_shift(O);
+    static_assert(sft >= 1 && sft < kWinLevels, "a lower offset reaches 1..21 levels back");
+    constexpr int d = off63(O).c * kWinPb + off63(O).b - sft * kWinSlot;
+    const int w = lm < sft ? kWinLevels * kWinSlot : 0;
+    acc[O / 8] = __fmaf_rn(-cf[O], win[base + w + d], acc[O / 8]);
+    win_lower<O + 1>(acc, win, base, lm, cf);
+  }
+}
+// acc[e / 8] -= cf[e] x(cell + d_O) for the upper offsets O..62, U entry e = O - 31 (cf[0] is
+// the inverted diagonal).
+template <int O>
+__device__ __forceinline__ void win_upper(float* acc, const float* __restrict__ win, int base, int lm,
+                                          const float* cf) {
+  if constexpr (O < 63) {
+    constexpr int sft = lev_shift(O);
+    static_assert(sft >= 1 && sft < kWinLevels, "an upper offset reaches 1..21 levels ahead");
+    constexpr int d = off63(O).c * kWinPb + off63(O).b + sft * kWinSlot;
+    constexpr int e = O - 31;
+    const int w = lm + sft >= kWinLevels ? kWinLevels * kWinSlot : 0;
+    acc[e / 8] = __fmaf_rn(-cf[e], win[base - w + d], acc[e / 8]);
+    win_upper<O + 1>(acc, win, base, lm, cf);
+  }
+}
+
+// The 32 entries of row i (of n) of a level's factor data, as floats.
+template <typename TS>
+__device__ __forceinline__ void load_row(const TS* data, int i, int n, float* cf);
+template <>
+__device__ __forceinline__ void load_row<__nv_bfloat16>(const __nv_bfloat16* data, int i, int n, float* cf) {
+  const uint4* u = reinterpret_cast<const uint4*>(data);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint4 v = u[k * n + i];
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cf[8 * k + 2 * j] = __uint_as_float(w[j] << 16);
+      cf[8 * k + 2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void load_row<float>(const float* data, int i, int n, float* cf) {
+  const float4* u = reinterpret_cast<const float4*>(data);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 v = u[k * n + i];
+    cf[4 * k] = v.x;
+    cf[4 * k + 1] = v.y;
+    cf[4 * k + 2] = v.z;
+    cf[4 * k + 3] = v.w;
+  }
+}
+
+// One thread per row of a level (levels of at most NT rows), one barrier per level.  Level l
+// writes slice l mod kWinLevels, which holds level l -+ 22 (forward / backward) and is read at
+// no level between; the cells that level held and level l does not are zeroed by the thread
+// that has the same place in that level's row list.
+template <typename TS>
+__global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDesc* __restrict__ blocks, Ras3D R,
+                                                           const double* __restrict__ rin,
+                                                           const double* __restrict__ rscale, double* __restrict__ z,
+                                                           const int* __restrict__ skip, int* __restrict__ err,
+                                                           int stages) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar[kMaxStages3];
+  __shared__ int s_fail;
+  float* win = reinterpret_cast<float*>(smem) + kWinLead;
+  float4* win4 = reinterpret_cast<float4*>(smem);
+  TS* stage_base = reinterpret_cast<TS*>(smem + (size_t)kWinFloats * sizeof(float));
+  const BlockDesc B = blocks[blockIdx.x];
+  const Shape3 S = R.shapes[R.block_shape[blockIdx.x]];
+  const int* rowabc = R.rowabc + S.row_off;
+  const int* lev = R.lev_start + S.lev_off;
+  float* ybuf = (float*)R.ypad + blockIdx.x * R.sPad;  // y of the forward solve, row order
+  const TS* Lp = (const TS*)R.Lp + blockIdx.x * R.sLU;
+  const TS* Up = (const TS*)R.Up + blockIdx.x * R.sLU;
+  const size_t stage_elems = (size_t)R.max_level_rows * 32;
+  const int nl = S.nlev, total = 2 * nl, tid = threadIdx.x;
+  auto level_of = [&](int t) { return t < nl ? t : 2 * nl - 1 - t; };
+  auto issue = [&](int t) {  // level copy t into stage t % stages
+    const int l = level_of(t);
+    const TS* src = (t < nl ? Lp : Up) + (size_t)lev[l] * 32;
+    const uint32_t bytes = (uint32_t)((lev[l + 1] - lev[l]) * 32 * sizeof(TS));
+    const int st = t % stages;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(stage_base + st * stage_elems, src, bytes, &bar[st]);
+  };
+  if (tid == 0) {
+    s_fail = 0;
+    for (int st = 0; st < stages; ++st) mbar_init(&bar[st], 1);
+    fence_mbar_init();
+    for (int t = 0; t < stages && t < total; ++t) issue(t);
+  }
+  for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // The thread's row of a level (r < 0: none), the level's row count, the row's cell, its input
+  // (r of the forward level, y of the backward one) and the slice cell to zero.  Loads run two
+  // levels ahead: the row list of level t + 2 and the input of level t + 1 are fetched while
+  // level t is solved.
+  struct Row {
+    int r, n, abc, ze;
+    float val;
+  };
+  auto rows = [&](int t, Row& w) {
+    const bool fwd = t < nl;
+    const int l = level_of(t), r0 = lev[l];
+    w.n = lev[l + 1] - r0;
+    w.r = tid < w.n ? r0 + tid : -1;
+    w.abc = w.r >= 0 ? rowabc[w.r] : 0;
+    w.ze = -1;
+    const int le = fwd ? l - kWinLevels : l + kWinLevels;  // the level the slice held
+    if (le >= 0 && le < nl && lev[le] + tid < lev[le + 1]) {
+      int a, b, c;
+      abc_of(rowabc[lev[le] + tid], &a, &b, &c);
+      if (fwd ? a + kWinLevels >= S.bx : a < kWinLevels) w.ze = c * kWinPb + b;
+    }
+  };
+  auto input = [&](int t, Row& w) {  // not for the first backward level (its y is computed just before)
+    if (w.r < 0) return;
+    if (t < nl) {
+      int a, b, c;
+      abc_of(w.abc, &a, &b, &c);
+      w.val = d2f_rn(rin[gidx(g, B, a, b, c)]);
+    } else if (t > nl) {
+      w.val = ybuf[w.r];
+    }
+  };
+  const double sc = rscale ? *rscale : 1.0;
+  Row w0{}, w1{}, w2{};
+  rows(0, w0);
+  input(0, w0);
+  if (total > 1) rows(1, w1);
+  for (int t = 0; t < total; ++t) {
+    const int st = t % stages;
+    const bool fwd = t < nl;
+    const int l = level_of(t);
+    if (t + 1 < total) input(t + 1, w1);
+    if (t + 2 < total) rows(t + 2, w2);
+    if (t == nl) {  // backward: the window starts from zero (no level above nl - 1)
+      __syncthreads();
+      for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid == 0 && !mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
+    __syncthreads();  // level t - 1 done: its slice written, its stage free
+    if (s_fail) {  // give up: record, drain the copies in flight (levels t .. last), leave
+      if (tid == 0) {
+        atomicExch(err, PFC_ETIMEOUT);
+        const int last = t == 0 ? stages - 1 : t - 2 + stages;
+        for (int u = t; u <= last && u < total; ++u)
+          mbar_wait_bounded(&bar[u % stages], (uint32_t)((u / stages) & 1));
+      }
+      return;
+    }
+    if (tid == 0 && t >= 1 && t - 1 + stages < total) issue(t - 1 + stages);
+    const int lm = l % kWinLevels;
+    if (w0.ze >= 0) win[lm * kWinSlot + w0.ze] = 0.f;
+    if (w0.r >= 0) {
+      float cf[32];
+      load_row<TS>(stage_base + st * stage_elems, tid, w0.n, cf);
+      int a, b, c;
+      abc_of(w0.abc, &a, &b, &c);
+      const int base = lm * kWinSlot + c * kWinPb + b;
+      float acc[4] = {w0.val, 0.f, 0.f, 0.f};
+      if (fwd) {  // y_r = b_r - sum_lower l_ro y_(r+o)
+        win_lower<0>(acc, win, base, lm, cf);
+        const float y = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        win[base] = y;
+        ybuf[w0.r] = y;
+        if (t == nl - 1) w1.val = y;  // the first backward level is this level: the same rows
+      } else {  // x_r = (y_r - sum_upper u_ro x_(r+o)) / u_rr; the core goes out (R_k^0)^T
+        win_upper<32>(acc, win, base, lm, cf);
+        const float x = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * cf[0];
+        win[base] = x;
+        if (a >= B.ox && a < B.ox + B.cx && b >= B.oy && b < B.oy + B.cy && c >= B.oz && c < B.oz + B.cz)
+          z[gidx(g, B, a, b, c)] = sc * f2d_exact(x);
+      }
+    }
+    w0 = w1;
+    w1 = w2;
   }
 }
 
 template <typename TC, typename TS>
 void factor3d_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                        const double* lin343, const Ras3D& R, int* status, cudaStream_t st) {
-  const size_t smem = (size_t)NT * 64 * sizeof(TC);
-  cudaFuncSetAttribute(k_factor3d<TC, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_factor3d<TC, TS><<<nblocks, NT, smem, st>>>(g, blocks, q, idt, lin343, R, status);
+  k_factor3d<TC, TS><<<nblocks, factor_threads<TC>(), 0, st>>>(g, blocks, q, idt, lin343, R, status);
   count_launches(1);
 }
 
 template <typename TC, typename TS>
 void apply3d_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                       const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
-  // Two levels in flight.  Deeper rings were slower on GB300 (256^3, BF16: 3.3 ms per apply with 2
-  // stages, 8.7 ms with 4, 6.4 ms with 7): the ring's shared memory comes out of the SM's L1, and
-  // the solve vector's neighbour reads, which live in global memory, depend on L1 hits.
+  // Two levels in flight: the ring's shared memory comes out of the SM's L1, on which this
+  // kernel's neighbour reads of the solve vector depend (deeper rings measured slower).
   const size_t stage = (size_t)R.max_level_rows * 32 * sizeof(TS);
   const int stages = 2;
   const size_t smem = stages * stage;
   cudaFuncSetAttribute(k_ras_apply3d<TC, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ras_apply3d<TC, TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err, stages);
+  count_launches(1);
+}
+
+constexpr size_t kSmemCap = 227 * 1024 - 1024;  // dynamic shared memory a CTA may take (static use aside)
+
+// Factor levels in flight for the window kernel: as many as fit beside the window (0: none).
+int win_stages(const Ras3D& R) {
+  if (R.prec == PFC_F64 || R.max_byz > kWinMaxByz || R.max_level_rows > NT) return 0;
+  const size_t stage = (size_t)R.max_level_rows * 32 * (R.prec == PFC_BF16 ? 2 : 4);
+  const size_t win = (size_t)kWinFloats * sizeof(float);
+  if (win + 2 * stage > kSmemCap) return 0;
+  return (int)std::min<size_t>(kMaxStages3, (kSmemCap - win) / stage);
+}
+
+template <typename TS>
+void apply3d_win_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
+                          const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
+  const int stages = win_stages(R);
+  const size_t smem = (size_t)kWinFloats * sizeof(float) + (size_t)stages * R.max_level_rows * 32 * sizeof(TS);
+  cudaFuncSetAttribute(k_ras_apply3d_win<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ras_apply3d_win<TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err, stages);
   count_launches(1);
 }
 
@@ -297,9 +632,15 @@ void launch_factor3d(const Geo& g, const BlockDesc* blocks, int nblocks, const d
     factor3d_dispatch<float, __nv_bfloat16>(g, blocks, nblocks, q, idt, lin343, R, status, st);
 }
 
+bool apply3d_window_ok(const Ras3D& R) { return win_stages(R) >= 2; }
+
 void launch_ras_apply3d(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                         const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
-  if (R.prec == PFC_F64)
+  if (R.window && R.prec == PFC_F32)
+    apply3d_win_dispatch<float>(g, blocks, nblocks, R, r, rscale, z, skip, err, st);
+  else if (R.window && R.prec == PFC_BF16)
+    apply3d_win_dispatch<__nv_bfloat16>(g, blocks, nblocks, R, r, rscale, z, skip, err, st);
+  else if (R.prec == PFC_F64)
     apply3d_dispatch<double, double>(g, blocks, nblocks, R, r, rscale, z, skip, err, st);
   else if (R.prec == PFC_F32)
     apply3d_dispatch<float, float>(g, blocks, nblocks, R, r, rscale, z, skip, err, st);

@@ -8,6 +8,7 @@
 // JVP's w) from it, and a final Laplacian pass that writes F (or J v).  Every
 // pass reads its neighbours through L1/L2; the FP64 issue rate, not HBM, bounds
 // them on GB300, so the extra passes cost little next to a fused 3D tile.
+#include "ff.cuh"
 #include "pfc_internal.cuh"
 
 namespace pfc {
@@ -197,6 +198,103 @@ void launch_energy3d(const Geo& g, const double* phi, double* partial, int* npar
   k_energy3d<<<b, NT, 0, st>>>(g, phi, partial);
   count_launches(1);
   *nparts = b;
+}
+
+}  // namespace pfc
+
+// ---- The Jacobian-vector product of the mixed path in float-float arithmetic (FP32 pipe): the
+// same three 7-point passes, with the scratch fields holding float pairs (8 bytes a point, as an
+// FP64 value).  J v is linear in v, so GMRES needs it only to its own stop test; float-float keeps
+// it to about 2^-44 of its terms, and GB300's FP64 pipe, which bounds the FP64 passes, idles.
+// One thread per point, CTAs of 32 x 8 points of one z plane (no index divisions).
+namespace pfc {
+namespace {
+
+constexpr int FX = 32, FY = 8;
+
+// ((xp + xm) + (yp + ym)) + (zp + zm) - 6 c, with one two-sum per leading part (as ff_lap5).
+__device__ __forceinline__ ff ff_lap7(ff c, ff xp, ff xm, ff yp, ff ym, ff zp, ff zm) {
+  const ff a = two_sum(xp.hi, xm.hi), b = two_sum(yp.hi, ym.hi), d = two_sum(zp.hi, zm.hi);
+  const ff t = two_sum(a.hi, b.hi);
+  const ff t2 = two_sum(t.hi, d.hi);
+  const float p = __fmul_rn(-6.0f, c.hi), pe = __fmaf_rn(-6.0f, c.hi, -p);  // -6 c.hi = p + pe exactly
+  const ff u = two_sum(t2.hi, p);
+  const float lo = __fadd_rn(
+      __fadd_rn(__fadd_rn(__fadd_rn(xp.lo, xm.lo), __fadd_rn(yp.lo, ym.lo)), __fadd_rn(zp.lo, zm.lo)),
+      __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(d.lo, t.lo)),
+                __fadd_rn(__fadd_rn(t2.lo, u.lo), __fadd_rn(pe, __fmul_rn(-6.0f, c.lo)))));
+  return fast_two_sum(u.hi, lo);
+}
+
+struct Nb {  // the point and its six periodic neighbours
+  long long c, xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ bool nb_of(const Geo& g, Nb* o) {
+  const int x = blockIdx.x * FX + threadIdx.x, y = blockIdx.y * FY + threadIdx.y, z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return false;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  o->c = x + sy * y + sz * z;
+  o->xp = o->c + (wrap_up(x, g.nx) - x);
+  o->xm = o->c + (wrap_dn(x, g.nx) - x);
+  o->yp = o->c + (wrap_up(y, g.ny) - y) * sy;
+  o->ym = o->c + (wrap_dn(y, g.ny) - y) * sy;
+  o->zp = o->c + (wrap_up(z, g.nz) - z) * sz;
+  o->zm = o->c + (wrap_dn(z, g.nz) - z) * sz;
+  return true;
+}
+__device__ __forceinline__ ff ldff(const float2* p, long long i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
+}
+
+// T1 = Lap v (unscaled)
+__global__ void __launch_bounds__(FX* FY) k_lap3d_ff(Geo g, const double* __restrict__ v, float2* __restrict__ T1,
+                                                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  const ff L = ff_lap7(ff_split(v[o.c]), ff_split(v[o.xp]), ff_split(v[o.xm]), ff_split(v[o.yp]),
+                       ff_split(v[o.ym]), ff_split(v[o.zp]), ff_split(v[o.zm]));
+  T1[o.c] = make_float2(L.hi, L.lo);
+}
+// T2 = w = c0 v + ih2 T1 + ih4/2 Lap T1 + q v
+__global__ void __launch_bounds__(FX* FY) k_mid3d_ff(Geo g, const double* __restrict__ v,
+                                                     const double* __restrict__ q, const float2* __restrict__ T1,
+                                                     float2* __restrict__ T2, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  const ff L1 = ldff(T1, o.c);
+  const ff LL = ff_lap7(L1, ldff(T1, o.xp), ldff(T1, o.xm), ldff(T1, o.yp), ldff(T1, o.ym), ldff(T1, o.zp),
+                        ldff(T1, o.zm));
+  const ff vv = ff_split(v[o.c]);
+  const ff ih2 = ff_split(g.ih2), hih4 = ff_split(0.5 * g.ih2 * g.ih2), c0 = ff_split(0.5 * (1.0 - g.gamma));
+  const ff w = ff_dot4(c0, vv, ih2, L1, hih4, LL, ff_split(q[o.c]), vv);
+  T2[o.c] = make_float2(w.hi, w.lo);
+}
+// J v = v idt - ih2 Lap w
+__global__ void __launch_bounds__(FX* FY) k_jvp_out3d_ff(Geo g, const double* __restrict__ v,
+                                                         const float2* __restrict__ T2, double idt,
+                                                         double* __restrict__ Jv, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  const ff Lw = ff_lap7(ldff(T2, o.c), ldff(T2, o.xp), ldff(T2, o.xm), ldff(T2, o.yp), ldff(T2, o.ym),
+                        ldff(T2, o.zp), ldff(T2, o.zm));
+  Jv[o.c] = ff_to_double(ff_dot2m(ff_split(v[o.c]), ff_split(idt), ff_split(g.ih2), Lw));
+}
+
+}  // namespace
+
+void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
+                     const int* skip, cudaStream_t st) {
+  const dim3 grid((g.nx + FX - 1) / FX, (g.ny + FY - 1) / FY, g.nz), blk(FX, FY);
+  float2* t1 = reinterpret_cast<float2*>(T1);
+  float2* t2 = reinterpret_cast<float2*>(T2);
+  k_lap3d_ff<<<grid, blk, 0, st>>>(g, v, t1, skip);
+  k_mid3d_ff<<<grid, blk, 0, st>>>(g, v, q, t1, t2, skip);
+  k_jvp_out3d_ff<<<grid, blk, 0, st>>>(g, v, t2, idt, Jv, skip);
+  count_launches(3);
 }
 
 }  // namespace pfc

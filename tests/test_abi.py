@@ -63,6 +63,12 @@ def test_workspace_size_and_validation(libpfc):
     assert e.value.status == pfc.PFC_EINVAL
     with pytest.raises(pfc.PfcError):
         pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4), gmres_restart=0))
+    # 3D grids have two apply kernels (0: global memory, 1: shared-memory window); 2..5 are 2D ones
+    for v in (-1, 0, 1):
+        assert pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), apply_variant=v)) > 0
+    for v in (2, 5):
+        with pytest.raises(pfc.PfcError):
+            pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), apply_variant=v))
     assert pfc.status_str(pfc.PFC_ESINGULAR).startswith("zero pivot")
 
 

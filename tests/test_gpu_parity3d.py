@@ -79,3 +79,48 @@ def test_steps_3d_match_oracle(pfc):
         assert abs(inf["energy"] - rec.energy) <= 1e-10 * abs(rec.energy)
     E = [i["energy"] for i in infos]
     assert all(b <= a for a, b in zip(E, E[1:]))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("shape,parts", [((74, 74, 74), (2, 2, 2)), ((17, 16, 15), (2, 2, 2)),
+                                         ((36, 30, 27), (3, 2, 2))])
+def test_window_apply_equals_global_apply(pfc, shape, parts, prec):
+    """The shared-memory level-window apply (variant 1) and the global-memory apply (variant 0)
+    take the same operations in the same order: bitwise equal outputs, on 39^3 blocks (the
+    window's largest: 218-row levels) as on small and uneven ones."""
+    Phi = inputs.noise_field(shape, -0.325, 0.3, 21)
+    phin = inputs.noise_field(shape, -0.325, 0.3, 22)
+    r = inputs.noise_field(shape, 0.0, 1.0, 23)
+    sw = solver3(pfc, shape, parts, prec=prec, apply_variant=1)
+    sg = solver3(pfc, shape, parts, prec=prec, apply_variant=0)
+    assert sw.tuning()["apply_variant"] == 1 and sg.tuning()["apply_variant"] == 0
+    assert solver3(pfc, shape, parts, prec=prec).tuning()["apply_variant"] == 1  # the default where it fits
+    zw = sw.precond_apply(Phi, phin, 1.5, r).cpu().numpy()
+    zg = sg.precond_apply(Phi, phin, 1.5, r).cpu().numpy()
+    assert np.array_equal(zw, zg)
+    assert np.isfinite(zw).all() and np.abs(zw).max() > 0
+
+
+def test_window_apply_refuses_blocks_it_cannot_hold(pfc):
+    """FP64 factors and blocks wider than 39 cells in y or z run only the global-memory apply:
+    asking for the window there fails at creation, and the default falls back."""
+    with pytest.raises(pfc.PfcError):
+        solver3(pfc, (16, 16, 16), (2, 2, 2), prec=0, apply_variant=1)
+    with pytest.raises(pfc.PfcError):
+        solver3(pfc, (80, 80, 80), (2, 2, 2), prec=2, apply_variant=1)  # 42-cell blocks
+    assert solver3(pfc, (80, 80, 80), (2, 2, 2), prec=2).tuning()["apply_variant"] == 0
+    assert solver3(pfc, (16, 16, 16), (2, 2, 2), prec=0).tuning()["apply_variant"] == 0
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 14, 18), (40, 37, 33)])
+def test_float_float_jvp_3d(pfc, shape, prec):
+    """The mixed path's 3D JVP (three float-float 7-point passes) against the oracle's FP64
+    product: float pairs keep about 2^-44 of the terms, within 1e-11 of the largest entry."""
+    Phi = inputs.noise_field(shape, -0.3, 0.4, 31)
+    phin = inputs.noise_field(shape, -0.3, 0.4, 32)
+    v = inputs.noise_field(shape, 0.0, 1.0, 33)
+    s = solver3(pfc, shape, (2, 2, 2), prec=prec)
+    Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 2.5, H3, GAMMA3)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
