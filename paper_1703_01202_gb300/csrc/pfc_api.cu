@@ -1647,7 +1647,11 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     R.prec = p->factor_prec;
     R.max_level_rows = S.max_level_rows;
     R.max_byz = 0;
-    for (const pfc::Shape3& sh : S.shapes) R.max_byz = std::max(R.max_byz, std::max(sh.by, sh.bz));
+    R.max_nlev = 0;
+    for (const pfc::Shape3& sh : S.shapes) {
+      R.max_byz = std::max(R.max_byz, std::max(sh.by, sh.bz));
+      R.max_nlev = std::max(R.max_nlev, sh.nlev);
+    }
     R.window = 0;
     if (p->apply_variant != 0) {  // -1: the window kernel where it fits; 1: only the window kernel
       R.window = pfc::apply3d_window_ok(R) ? 1 : 0;

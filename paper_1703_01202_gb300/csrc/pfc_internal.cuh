@@ -300,6 +300,7 @@ struct Ras3D {
   int prec;
   int max_level_rows;
   int max_byz;        // largest block extent in y or z
+  int max_nlev;       // most levels of a block
   int window;         // 1: FP32 solves in the shared-memory level window (apply3d_window_ok)
   double shift;       // diagonal shift, relative to the block's mean |a_ii|
 };

@@ -57,6 +57,7 @@ constexpr long long kWaitCycles = 4000000000LL;
 // Waits for the phase with the given parity to complete; gives up after
 // `limit` SM clock cycles and returns false (the caller records PFC_ETIMEOUT).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
+  if (mbar_try_wait(bar, parity)) return true;  // already complete: no clock read
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > limit) return false;

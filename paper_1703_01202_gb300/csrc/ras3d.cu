@@ -476,60 +476,60 @@ __global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDes
   const size_t stage_elems = (size_t)R.max_level_rows * 32;
   const int nl = S.nlev, total = 2 * nl, tid = threadIdx.x;
   auto level_of = [&](int t) { return t < nl ? t : 2 * nl - 1 - t; };
+  const int* lv = lev;  // the level starts: global memory until the shared copy is made
   auto issue = [&](int t) {  // level copy t into stage t % stages
     const int l = level_of(t);
-    const TS* src = (t < nl ? Lp : Up) + (size_t)lev[l] * 32;
-    const uint32_t bytes = (uint32_t)((lev[l + 1] - lev[l]) * 32 * sizeof(TS));
+    const TS* src = (t < nl ? Lp : Up) + (size_t)lv[l] * 32;
+    const uint32_t bytes = (uint32_t)((lv[l + 1] - lv[l]) * 32 * sizeof(TS));
     const int st = t % stages;
     fence_proxy_async();
     mbar_expect_tx(&bar[st], bytes);
     bulk_g2s(stage_base + st * stage_elems, src, bytes, &bar[st]);
   };
-  if (tid == 0) {
+  if (tid == NT - 1) {
     s_fail = 0;
     for (int st = 0; st < stages; ++st) mbar_init(&bar[st], 1);
     fence_mbar_init();
     for (int t = 0; t < stages && t < total; ++t) issue(t);
   }
+  // level starts in shared memory; the restriction R_k^delta r of every row, rounded to the solve
+  // type, into ybuf (row order) with all loads in flight at once: no level waits on a gather
+  int* lev_s = reinterpret_cast<int*>(smem + (size_t)kWinFloats * sizeof(float) + (size_t)stages * stage_elems * sizeof(TS));
+  for (int i = tid; i <= nl; i += NT) lev_s[i] = lev[i];
+  for (int r = tid; r < S.nrows; r += NT) {
+    int a, b, c;
+    abc_of(rowabc[r], &a, &b, &c);
+    ybuf[r] = d2f_rn(rin[gidx(g, B, a, b, c)]);
+  }
   for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  lv = lev_s;
   // The thread's row of a level (r < 0: none), the level's row count, the row's cell, its input
-  // (r of the forward level, y of the backward one) and the slice cell to zero.  Loads run two
-  // levels ahead: the row list of level t + 2 and the input of level t + 1 are fetched while
-  // level t is solved.
+  // (r of the forward level, y of the backward one; both in ybuf) and the cell of the level the
+  // slice held (ea < 0: none; zeroed if level l has no cell there).  Loads run ahead: the cells of
+  // level t + 2 and the input of level t + 1 are fetched while level t is solved, each a single
+  // load from a known address, and nothing reads them before their level: the loop body runs
+  // three times per iteration with the three rows' roles rotated, so no register is moved while
+  // its load is in flight.
   struct Row {
-    int r, n, abc, ze;
+    int r, n, abc, ea;
     float val;
   };
   auto rows = [&](int t, Row& w) {
     const bool fwd = t < nl;
-    const int l = level_of(t), r0 = lev[l];
-    w.n = lev[l + 1] - r0;
+    const int l = level_of(t), r0 = lev_s[l];
+    w.n = lev_s[l + 1] - r0;
     w.r = tid < w.n ? r0 + tid : -1;
     w.abc = w.r >= 0 ? rowabc[w.r] : 0;
-    w.ze = -1;
     const int le = fwd ? l - kWinLevels : l + kWinLevels;  // the level the slice held
-    if (le >= 0 && le < nl && lev[le] + tid < lev[le + 1]) {
-      int a, b, c;
-      abc_of(rowabc[lev[le] + tid], &a, &b, &c);
-      if (fwd ? a + kWinLevels >= S.bx : a < kWinLevels) w.ze = c * kWinPb + b;
-    }
+    w.ea = (le >= 0 && le < nl && lev_s[le] + tid < lev_s[le + 1]) ? rowabc[lev_s[le] + tid] : -1;
   };
   auto input = [&](int t, Row& w) {  // not for the first backward level (its y is computed just before)
-    if (w.r < 0) return;
-    if (t < nl) {
-      int a, b, c;
-      abc_of(w.abc, &a, &b, &c);
-      w.val = d2f_rn(rin[gidx(g, B, a, b, c)]);
-    } else if (t > nl) {
-      w.val = ybuf[w.r];
-    }
+    if (w.r >= 0 && t != nl) w.val = ybuf[w.r];
   };
   const double sc = rscale ? *rscale : 1.0;
-  Row w0{}, w1{}, w2{};
-  rows(0, w0);
-  input(0, w0);
-  if (total > 1) rows(1, w1);
-  for (int t = 0; t < total; ++t) {
+  // level t with its row in w0 (rows of t + 1 in w1, t + 2 in w2); false: give up
+  auto level = [&](int t, Row& w0, Row& w1, Row& w2) -> bool {
     const int st = t % stages;
     const bool fwd = t < nl;
     const int l = level_of(t);
@@ -539,20 +539,26 @@ __global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDes
       __syncthreads();
       for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (tid == 0 && !mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
+    // the ring is kept by the last thread: its warp has no row at the levels of 39^3 blocks (at
+    // most 218 rows), so the copies never hold up a row's work
+    if (tid == NT - 1 && !mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
     __syncthreads();  // level t - 1 done: its slice written, its stage free
     if (s_fail) {  // give up: record, drain the copies in flight (levels t .. last), leave
-      if (tid == 0) {
+      if (tid == NT - 1) {
         atomicExch(err, PFC_ETIMEOUT);
         const int last = t == 0 ? stages - 1 : t - 2 + stages;
         for (int u = t; u <= last && u < total; ++u)
           mbar_wait_bounded(&bar[u % stages], (uint32_t)((u / stages) & 1));
       }
-      return;
+      return false;
     }
-    if (tid == 0 && t >= 1 && t - 1 + stages < total) issue(t - 1 + stages);
+    if (tid == NT - 1 && t >= 1 && t - 1 + stages < total) issue(t - 1 + stages);
     const int lm = l % kWinLevels;
-    if (w0.ze >= 0) win[lm * kWinSlot + w0.ze] = 0.f;
+    if (w0.ea >= 0) {
+      int a, b, c;
+      abc_of(w0.ea, &a, &b, &c);
+      if (fwd ? a + kWinLevels >= S.bx : a < kWinLevels) win[lm * kWinSlot + c * kWinPb + b] = 0.f;
+    }
     if (w0.r >= 0) {
       float cf[32];
       load_row<TS>(stage_base + st * stage_elems, tid, w0.n, cf);
@@ -574,8 +580,16 @@ __global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDes
           z[gidx(g, B, a, b, c)] = sc * f2d_exact(x);
       }
     }
-    w0 = w1;
-    w1 = w2;
+    return true;
+  };
+  Row ra{}, rb{}, rc{};
+  rows(0, ra);
+  input(0, ra);
+  if (total > 1) rows(1, rb);
+  for (int t = 0; t < total; t += 3) {
+    if (!level(t, ra, rb, rc)) return;
+    if (t + 1 < total && !level(t + 1, rb, rc, ra)) return;
+    if (t + 2 < total && !level(t + 2, rc, ra, rb)) return;
   }
 }
 
@@ -601,20 +615,25 @@ void apply3d_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const 
 
 constexpr size_t kSmemCap = 227 * 1024 - 1024;  // dynamic shared memory a CTA may take (static use aside)
 
-// Factor levels in flight for the window kernel: as many as fit beside the window (0: none).
+// Bytes of the window kernel's level-start table (padded to 16).
+size_t win_lev_bytes(const Ras3D& R) { return ((size_t)(R.max_nlev + 1) * sizeof(int) + 15) / 16 * 16; }
+
+// Factor levels in flight for the window kernel: as many as fit beside the window and the level
+// table (0: none).
 int win_stages(const Ras3D& R) {
   if (R.prec == PFC_F64 || R.max_byz > kWinMaxByz || R.max_level_rows > NT) return 0;
   const size_t stage = (size_t)R.max_level_rows * 32 * (R.prec == PFC_BF16 ? 2 : 4);
-  const size_t win = (size_t)kWinFloats * sizeof(float);
-  if (win + 2 * stage > kSmemCap) return 0;
-  return (int)std::min<size_t>(kMaxStages3, (kSmemCap - win) / stage);
+  const size_t fixed = (size_t)kWinFloats * sizeof(float) + win_lev_bytes(R);
+  if (fixed + 2 * stage > kSmemCap) return 0;
+  return (int)std::min<size_t>(kMaxStages3, (kSmemCap - fixed) / stage);
 }
 
 template <typename TS>
 void apply3d_win_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                           const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
   const int stages = win_stages(R);
-  const size_t smem = (size_t)kWinFloats * sizeof(float) + (size_t)stages * R.max_level_rows * 32 * sizeof(TS);
+  const size_t smem = (size_t)kWinFloats * sizeof(float) + (size_t)stages * R.max_level_rows * 32 * sizeof(TS) +
+                      win_lev_bytes(R);
   cudaFuncSetAttribute(k_ras_apply3d_win<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ras_apply3d_win<TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err, stages);
   count_launches(1);
