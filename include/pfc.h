@@ -105,8 +105,8 @@ typedef struct {
      Blocks wider than 21 cells in x (kl = 3 bx > 64) accept only 0 and 5.
      3D grids: 0 solves with the block's solve vector in global memory; 1 keeps
      the 22 wavefront levels a solve reads in shared memory (F32/BF16 factors,
-     blocks at most 39 cells in y and z, at most 256 rows per level; otherwise
-     pfc_create fails with PFC_EINVAL); -1 takes 1 where it can run, else 0.
+     at most 255 rows per level; otherwise pfc_create fails with PFC_EINVAL);
+     -1 takes 1 where it can run, else 0.
      The two give bitwise identical results; 2..5 are refused in 3D. */
   int apply_variant;
   /* pfc_run only: a step whose Newton or GMRES iteration fails (PFC_ENEWTON,

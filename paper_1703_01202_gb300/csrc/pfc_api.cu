@@ -254,6 +254,9 @@ void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>
 struct Shapes3 {
   std::vector<pfc::Shape3> shapes;
   std::vector<int> block_shape, lev_start, rowpad, rowabc;
+  // per row, in each level's 16-bytes-per-row layout: the place of each lower (posL) / upper
+  // (posU) neighbour in its own level's row list, 255 where the neighbour is outside the block
+  std::vector<uint8_t> posL, posU;
   int nrows_max = 0, pad_max = 0, max_level_rows = 0;
 };
 
@@ -308,6 +311,40 @@ void build_shapes3(const std::vector<BlockDesc>& blocks, Shapes3* S) {
         }
       }
       S->lev_start.push_back(r);
+      {  // neighbour places for the compact-window apply (levels of at most 255 rows)
+        const int r0s = sh.row_off;
+        std::vector<int> place(sh.nrows);
+        std::vector<int> rowof_cell((size_t)sh.nrows);
+        for (int l = 0; l < sh.nlev; ++l)
+          for (int rr = S->lev_start[sh.lev_off + l]; rr < S->lev_start[sh.lev_off + l + 1]; ++rr) {
+            place[rr] = rr - S->lev_start[sh.lev_off + l];
+            const int v = S->rowabc[r0s + rr];
+            rowof_cell[(v & 1023) + b.bx * (((v >> 10) & 1023) + b.by * (v >> 20))] = rr;
+          }
+        S->posL.resize((size_t)(r0s + sh.nrows) * 32, 255);
+        S->posU.resize((size_t)(r0s + sh.nrows) * 32, 255);
+        for (int l = 0; l < sh.nlev; ++l) {
+          const int l0 = S->lev_start[sh.lev_off + l], n = S->lev_start[sh.lev_off + l + 1] - l0;
+          for (int i = 0; i < n; ++i) {
+            const int v = S->rowabc[r0s + l0 + i];
+            const int a = v & 1023, bb = (v >> 10) & 1023, c = v >> 20;
+            for (int e = 0; e < 32; ++e) {
+              const size_t at = (size_t)(r0s + l0) * 32 + (size_t)((e / 16) * n + i) * 16 + e % 16;
+              for (int pass = 0; pass < 2; ++pass) {
+                const int o = pass == 0 ? e : 31 + e;  // lower offset e (e < 31) / upper offset 31 + e (e >= 1)
+                if ((pass == 0 && e >= 31) || (pass == 1 && e < 1)) continue;
+                const int a2 = a + off[o][0], b2 = bb + off[o][1], c2 = c + off[o][2];
+                uint8_t pl = 255;
+                if (a2 >= 0 && a2 < b.bx && b2 >= 0 && b2 < b.by && c2 >= 0 && c2 < b.bz) {
+                  const int r2 = rowof_cell[a2 + b.bx * (b2 + b.by * c2)];
+                  if (place[r2] < 255) pl = (uint8_t)place[r2];
+                }
+                (pass == 0 ? S->posL : S->posU)[at] = pl;
+              }
+            }
+          }
+        }
+      }
       S->nrows_max = std::max(S->nrows_max, sh.nrows);
       S->pad_max = std::max(S->pad_max, sh.px * sh.py * sh.pz);
       found = (int)S->shapes.size();
@@ -352,7 +389,7 @@ struct Plan {
   size_t phin, phinm1, Phi, F, q, Pt, Ft, qt, S, W, guess, V, Z, L, U, piv, blocks, lin, ctl, partial, red, status,
       tabs, feat, iargs, iargs2, sctl, recs, order, X, Yb, mu, mut, smid, smidt;
   // 3D
-  size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowabc, Lp, Up, work, ypad;
+  size_t T1, T2, shapes, block_shape, lev_start, rowpad, rowabc, posL, posU, Lp, Up, work, ypad;
   size_t total;
   int nblocks, n_max, kl_max;
   size_t sL, sU, sP;
@@ -455,6 +492,8 @@ int make_plan(const pfc_grid* g, const pfc_params* p, Plan* pl) {
     pl->lev_start = L.take(sizeof(int) * S.lev_start.size());
     pl->rowpad = L.take(sizeof(int) * S.rowpad.size());
     pl->rowabc = L.take(sizeof(int) * S.rowabc.size());
+    pl->posL = L.take(S.posL.size());
+    pl->posU = L.take(S.posU.size());
     pl->Lp = L.take(pl->sLU3 * es * pl->nblocks);
     pl->Up = L.take(pl->sLU3 * es * pl->nblocks);
     pl->work = L.take(pl->sWork3 * tc * pl->nblocks);
@@ -1637,6 +1676,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     R.lev_start = (const int*)at(pl.lev_start);
     R.rowpad = (const int*)at(pl.rowpad);
     R.rowabc = (const int*)at(pl.rowabc);
+    R.posL = (const uint8_t*)at(pl.posL);
+    R.posU = (const uint8_t*)at(pl.posU);
     R.Lp = at(pl.Lp);
     R.Up = at(pl.Up);
     R.work = at(pl.work);
@@ -1646,12 +1687,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
     R.sPad = pl.sPad3;
     R.prec = p->factor_prec;
     R.max_level_rows = S.max_level_rows;
-    R.max_byz = 0;
     R.max_nlev = 0;
-    for (const pfc::Shape3& sh : S.shapes) {
-      R.max_byz = std::max(R.max_byz, std::max(sh.by, sh.bz));
-      R.max_nlev = std::max(R.max_nlev, sh.nlev);
-    }
+    for (const pfc::Shape3& sh : S.shapes) R.max_nlev = std::max(R.max_nlev, sh.nlev);
     R.window = 0;
     if (p->apply_variant != 0) {  // -1: the window kernel where it fits; 1: only the window kernel
       R.window = pfc::apply3d_window_ok(R) ? 1 : 0;
@@ -1671,6 +1708,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
         !put(R.lev_start, S.lev_start.data(), sizeof(int) * S.lev_start.size()) ||
         !put(R.rowpad, S.rowpad.data(), sizeof(int) * S.rowpad.size()) ||
         !put(R.rowabc, S.rowabc.data(), sizeof(int) * S.rowabc.size()) ||
+        !put(R.posL, S.posL.data(), S.posL.size()) || !put(R.posU, S.posU.data(), S.posU.size()) ||
         cudaMemsetAsync(R.ypad, 0, pl.sPad3 * tc * pl.nblocks, s->st) != cudaSuccess ||
         cudaStreamSynchronize(s->st) != cudaSuccess) {
       pfc_destroy(s);

@@ -299,13 +299,13 @@ struct Ras3D {
   size_t sLU, sWork, sPad;
   int prec;
   int max_level_rows;
-  int max_byz;        // largest block extent in y or z
   int max_nlev;       // most levels of a block
   int window;         // 1: FP32 solves in the shared-memory level window (apply3d_window_ok)
+  const uint8_t* posL;  // per row, 32 bytes in the level layout: place of each lower / upper
+  const uint8_t* posU;  // neighbour in its level's row list (255: outside the block)
   double shift;       // diagonal shift, relative to the block's mean |a_ii|
 };
-// Whether the window apply can run these blocks: FP32/BF16 factors, blocks at most 39 cells in y
-// and z, levels of at most 256 rows, and the window plus two factor levels in shared memory.
+// Whether the window apply can run these blocks: FP32/BF16 factors and levels of at most 255 rows.
 bool apply3d_window_ok(const Ras3D& R);
 void launch_factor3d(const Geo& g, const BlockDesc* blocks, int nblocks, const double* q, double idt,
                      const double* lin343, const Ras3D& R, int* status, cudaStream_t st);

@@ -19,13 +19,12 @@
 // Two apply kernels give identical results.  The general one keeps the solve
 // vector in a padded copy of the block in global memory (3-cell zero ring, so
 // a neighbour outside the block reads zero and needs no bounds test).  The
-// window kernel (FP32 solves of blocks at most 39 cells in y and z) keeps in
-// shared memory only the levels a row can still read: an offset moves at most
-// 21 levels (dc = -3), so 22 level slices, each the block's (b, c) plane with a
-// zero margin, hold every value the solve reads; the cell (a, b, c) of level l
-// sits at (b, c) of slice l mod 22, where a = l - 3b - 7c.  A (b, c) that has
-// no cell at a level holds zero there, which is what a neighbour outside the
-// block must read.  Both sum a row's 31 products as four partial sums of 8
+// window kernel (FP32 solves, levels of at most 255 rows) keeps in shared memory
+// only the levels a row can still read: an offset moves at most 21 levels
+// (dc = -3), so 22 level slots of 256 floats hold every value the solve reads,
+// row i of level l at place i of slot l mod 22, and each row's neighbours come
+// with their places from host tables (255, a place kept zero, for a neighbour
+// outside the block).  Both sum a row's 31 products as four partial sums of 8
 // entries, (s0 + s1) + (s2 + s3): four independent chains for the FMA pipeline.
 #include <cuda_bf16.h>
 
@@ -373,49 +372,53 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   }
 }
 
-// ---- Window apply (FP32 solves).  Level slice l mod kWinLevels holds the solve values of level l
-// at (b, c), zero where (b, c) has no cell at that level; a margin of 3 zero cells after the last
-// b and c serves both sides (b - 3..b - 1 of one row of the slice reads the margin of the row
-// before; c - 3..c - 1 of slice s the margin rows of slice s - 1, or the lead margin of slice 0).
-constexpr int kWinPb = 42;                 // slice extent in b and c: 39 cells and the margin
-constexpr int kWinSlot = kWinPb * kWinPb;  // floats per slice
-constexpr int kWinLevels = 22;             // the level itself and the 21 an offset reaches
-constexpr int kWinLead = 4 * kWinPb;       // margin before slice 0 (c = -3 with b < 0 reaches row -4)
-constexpr int kWinFloats = kWinLead + kWinLevels * kWinSlot;
-constexpr int kWinMaxByz = kWinPb - 3;
-static_assert(kWinSlot % 4 == 0 && kWinLead % 4 == 0 && (kWinFloats * 4) % 128 == 0, "16-byte zeroing, aligned stages");
+// ---- Window apply (FP32 solves).  The solve of a row reads rows of the 21 levels before it
+// (forward) or after it (backward) only, so 22 level slots hold every value it reads: level l in
+// slot l mod kWinLevels, row i of the level at place i.  Each row's neighbours come with their
+// places in their own levels (host tables, 255 for a neighbour outside the block: a place no
+// level writes, zero from the start).  A slot is rewritten at level l + 22 only, after the last
+// level that reads it; neither direction reads a slot it has not written in that direction.
+constexpr int kWinLevels = 22;   // the level itself and the 21 an offset reaches
+constexpr int kWinSlot = 256;    // floats per slot: places 0..254 and the zero place 255
+constexpr int kWinFloats = kWinLevels * kWinSlot;
 
 // Levels an offset moves: a + 3b + 7c.
 __host__ __device__ constexpr int lev_shift(int o) { return off63(o).a + 3 * off63(o).b + 7 * off63(o).c; }
 
-// acc[O / 8] -= cf[O] y(cell + d_O) for the lower offsets O..30: the neighbour sits sft =
-// -lev_shift(O) in 1..21 levels back, in slice (lm - sft) mod kWinLevels.  `base` is the
-// cell's own window index.  Four accumulators (entries 8q..8q+7): the general kernel's order.
+// Byte e of the 32 neighbour places of a row (two 16-byte words).
+__device__ __forceinline__ int place_of(const uint4& p0, const uint4& p1, int e) {
+  const uint4& p = e < 16 ? p0 : p1;
+  const int k = e & 15;
+  const uint32_t w = k < 4 ? p.x : k < 8 ? p.y : k < 12 ? p.z : p.w;
+  return (int)((w >> (8 * (k & 3))) & 0xffu);
+}
+
+// acc[O / 8] -= cf[O] y(neighbour O) for the lower offsets O..30: the neighbour sits sft =
+// -lev_shift(O) in 1..21 levels back, in slot (lm - sft) mod kWinLevels.  Four accumulators
+// (entries 8q..8q+7): the general kernel's order.
 template <int O>
-__device__ __forceinline__ void win_lower(float* acc, const float* __restrict__ win, int base, int lm,
-                                          const float* cf) {
+__device__ __forceinline__ void win_lower(float* acc, const float* __restrict__ win, int lm, const uint4& p0,
+                                          const uint4& p1, const float* cf) {
   if constexpr (O < 31) {
     constexpr int sft = -lev_shift(O);
     static_assert(sft >= 1 && sft < kWinLevels, "a lower offset reaches 1..21 levels back");
-    constexpr int d = off63(O).c * kWinPb + off63(O).b - sft * kWinSlot;
-    const int w = lm < sft ? kWinLevels * kWinSlot : 0;
-    acc[O / 8] = __fmaf_rn(-cf[O], win[base + w + d], acc[O / 8]);
-    win_lower<O + 1>(acc, win, base, lm, cf);
+    const int sl = lm < sft ? lm - sft + kWinLevels : lm - sft;
+    acc[O / 8] = __fmaf_rn(-cf[O], win[sl * kWinSlot + place_of(p0, p1, O)], acc[O / 8]);
+    win_lower<O + 1>(acc, win, lm, p0, p1, cf);
   }
 }
-// acc[e / 8] -= cf[e] x(cell + d_O) for the upper offsets O..62, U entry e = O - 31 (cf[0] is
-// the inverted diagonal).
+// acc[e / 8] -= cf[e] x(neighbour 31 + e) for the upper offsets, U entry e = O - 31 (cf[0] is the
+// inverted diagonal).
 template <int O>
-__device__ __forceinline__ void win_upper(float* acc, const float* __restrict__ win, int base, int lm,
-                                          const float* cf) {
+__device__ __forceinline__ void win_upper(float* acc, const float* __restrict__ win, int lm, const uint4& p0,
+                                          const uint4& p1, const float* cf) {
   if constexpr (O < 63) {
     constexpr int sft = lev_shift(O);
     static_assert(sft >= 1 && sft < kWinLevels, "an upper offset reaches 1..21 levels ahead");
-    constexpr int d = off63(O).c * kWinPb + off63(O).b + sft * kWinSlot;
     constexpr int e = O - 31;
-    const int w = lm + sft >= kWinLevels ? kWinLevels * kWinSlot : 0;
-    acc[e / 8] = __fmaf_rn(-cf[e], win[base - w + d], acc[e / 8]);
-    win_upper<O + 1>(acc, win, base, lm, cf);
+    const int sl = lm + sft >= kWinLevels ? lm + sft - kWinLevels : lm + sft;
+    acc[e / 8] = __fmaf_rn(-cf[e], win[sl * kWinSlot + place_of(p0, p1, e)], acc[e / 8]);
+    win_upper<O + 1>(acc, win, lm, p0, p1, cf);
   }
 }
 
@@ -449,44 +452,47 @@ __device__ __forceinline__ void load_row<float>(const float* data, int i, int n,
   }
 }
 
-// One thread per row of a level (levels of at most NT rows), one barrier per level.  Level l
-// writes slice l mod kWinLevels, which holds level l -+ 22 (forward / backward) and is read at
-// no level between; the cells that level held and level l does not are zeroed by the thread
-// that has the same place in that level's row list.
+// One thread per row of a level (levels of at most 255 rows), one barrier per level.  The small
+// window lets several blocks share an SM.  The last thread keeps the copy ring (its warp has no
+// row at levels of fewer than 225 rows).
 template <typename TS>
-__global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDesc* __restrict__ blocks, Ras3D R,
-                                                           const double* __restrict__ rin,
-                                                           const double* __restrict__ rscale, double* __restrict__ z,
-                                                           const int* __restrict__ skip, int* __restrict__ err,
-                                                           int stages) {
+__global__ void __launch_bounds__(NT) k_ras_apply3d_win(Geo g, const BlockDesc* __restrict__ blocks, Ras3D R,
+                                                        const double* __restrict__ rin,
+                                                        const double* __restrict__ rscale, double* __restrict__ z,
+                                                        const int* __restrict__ skip, int* __restrict__ err,
+                                                        int stages) {
   if (skip && *skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[kMaxStages3];
   __shared__ int s_fail;
-  float* win = reinterpret_cast<float*>(smem) + kWinLead;
-  float4* win4 = reinterpret_cast<float4*>(smem);
-  TS* stage_base = reinterpret_cast<TS*>(smem + (size_t)kWinFloats * sizeof(float));
   const BlockDesc B = blocks[blockIdx.x];
   const Shape3 S = R.shapes[R.block_shape[blockIdx.x]];
   const int* rowabc = R.rowabc + S.row_off;
+  const uint8_t* posL = R.posL + (size_t)S.row_off * 32;
+  const uint8_t* posU = R.posU + (size_t)S.row_off * 32;
   const int* lev = R.lev_start + S.lev_off;
-  float* ybuf = (float*)R.ypad + blockIdx.x * R.sPad;  // y of the forward solve, row order
+  float* ybuf = (float*)R.ypad + blockIdx.x * R.sPad;  // r, then the forward solution, row order
   const TS* Lp = (const TS*)R.Lp + blockIdx.x * R.sLU;
   const TS* Up = (const TS*)R.Up + blockIdx.x * R.sLU;
-  const size_t stage_elems = (size_t)R.max_level_rows * 32;
-  const int nl = S.nlev, total = 2 * nl, tid = threadIdx.x;
+  const size_t fbytes = (size_t)R.max_level_rows * 32 * sizeof(TS);  // factor part of a stage
+  const size_t sbytes = fbytes + (size_t)R.max_level_rows * 32;       // + the places
+  float* win = reinterpret_cast<float*>(smem);
+  unsigned char* stage_base = smem + (size_t)kWinFloats * sizeof(float);
+  int* lev_s = reinterpret_cast<int*>(stage_base + (size_t)stages * sbytes);
+  const int nl = S.nlev, total = 2 * nl, tid = threadIdx.x, ring = NT - 1;
   auto level_of = [&](int t) { return t < nl ? t : 2 * nl - 1 - t; };
   const int* lv = lev;  // the level starts: global memory until the shared copy is made
-  auto issue = [&](int t) {  // level copy t into stage t % stages
-    const int l = level_of(t);
-    const TS* src = (t < nl ? Lp : Up) + (size_t)lv[l] * 32;
-    const uint32_t bytes = (uint32_t)((lv[l + 1] - lv[l]) * 32 * sizeof(TS));
+  auto issue = [&](int t) {  // level copy t (factors and places) into stage t % stages
+    const int l = level_of(t), r0 = lv[l], n = lv[l + 1] - r0;
     const int st = t % stages;
+    unsigned char* dst = stage_base + (size_t)st * sbytes;
+    const uint32_t fb = (uint32_t)(n * 32 * sizeof(TS)), pb = (uint32_t)(n * 32);
     fence_proxy_async();
-    mbar_expect_tx(&bar[st], bytes);
-    bulk_g2s(stage_base + st * stage_elems, src, bytes, &bar[st]);
+    mbar_expect_tx(&bar[st], fb + pb);
+    bulk_g2s(dst, (t < nl ? Lp : Up) + (size_t)r0 * 32, fb, &bar[st]);
+    bulk_g2s(dst + fbytes, (t < nl ? posL : posU) + (size_t)r0 * 32, pb, &bar[st]);
   };
-  if (tid == NT - 1) {
+  if (tid == ring) {
     s_fail = 0;
     for (int st = 0; st < stages; ++st) mbar_init(&bar[st], 1);
     fence_mbar_init();
@@ -494,57 +500,43 @@ __global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDes
   }
   // level starts in shared memory; the restriction R_k^delta r of every row, rounded to the solve
   // type, into ybuf (row order) with all loads in flight at once: no level waits on a gather
-  int* lev_s = reinterpret_cast<int*>(smem + (size_t)kWinFloats * sizeof(float) + (size_t)stages * stage_elems * sizeof(TS));
   for (int i = tid; i <= nl; i += NT) lev_s[i] = lev[i];
   for (int r = tid; r < S.nrows; r += NT) {
     int a, b, c;
     abc_of(rowabc[r], &a, &b, &c);
     ybuf[r] = d2f_rn(rin[gidx(g, B, a, b, c)]);
   }
-  for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < kWinFloats; i += NT) win[i] = 0.f;
   __syncthreads();
   lv = lev_s;
-  // The thread's row of a level (r < 0: none), the level's row count, the row's cell, its input
-  // (r of the forward level, y of the backward one; both in ybuf) and the cell of the level the
-  // slice held (ea < 0: none; zeroed if level l has no cell there).  Loads run ahead: the cells of
-  // level t + 2 and the input of level t + 1 are fetched while level t is solved, each a single
-  // load from a known address, and nothing reads them before their level: the loop body runs
-  // three times per iteration with the three rows' roles rotated, so no register is moved while
-  // its load is in flight.
+  // The thread's row of a level (r < 0: none), the level's row count, its input (r of the
+  // forward level, y of the backward one; both in ybuf) and its cell (backward, for the output).
+  // Loads run ahead: the cell of level t + 2 and the input of level t + 1 are fetched while level t
+  // is solved; the loop body runs three times per iteration with the rows' roles rotated, so no
+  // register is moved while its load is in flight.
   struct Row {
-    int r, n, abc, ea;
+    int r, n, abc;
     float val;
   };
   auto rows = [&](int t, Row& w) {
-    const bool fwd = t < nl;
     const int l = level_of(t), r0 = lev_s[l];
     w.n = lev_s[l + 1] - r0;
     w.r = tid < w.n ? r0 + tid : -1;
-    w.abc = w.r >= 0 ? rowabc[w.r] : 0;
-    const int le = fwd ? l - kWinLevels : l + kWinLevels;  // the level the slice held
-    w.ea = (le >= 0 && le < nl && lev_s[le] + tid < lev_s[le + 1]) ? rowabc[lev_s[le] + tid] : -1;
+    w.abc = (w.r >= 0 && t >= nl) ? rowabc[w.r] : 0;
   };
   auto input = [&](int t, Row& w) {  // not for the first backward level (its y is computed just before)
     if (w.r >= 0 && t != nl) w.val = ybuf[w.r];
   };
   const double sc = rscale ? *rscale : 1.0;
-  // level t with its row in w0 (rows of t + 1 in w1, t + 2 in w2); false: give up
-  auto level = [&](int t, Row& w0, Row& w1, Row& w2) -> bool {
+  auto level = [&](int t, Row& w0, Row& w1, Row& w2) -> bool {  // false: give up
     const int st = t % stages;
     const bool fwd = t < nl;
-    const int l = level_of(t);
     if (t + 1 < total) input(t + 1, w1);
     if (t + 2 < total) rows(t + 2, w2);
-    if (t == nl) {  // backward: the window starts from zero (no level above nl - 1)
-      __syncthreads();
-      for (int i = tid; i < kWinFloats / 4; i += NT) win4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // the ring is kept by the last thread: its warp has no row at the levels of 39^3 blocks (at
-    // most 218 rows), so the copies never hold up a row's work
-    if (tid == NT - 1 && !mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
-    __syncthreads();  // level t - 1 done: its slice written, its stage free
+    if (tid == ring && !mbar_wait_bounded(&bar[st], (uint32_t)((t / stages) & 1))) s_fail = 1;
+    __syncthreads();  // level t - 1 done: its slot written, its stage free
     if (s_fail) {  // give up: record, drain the copies in flight (levels t .. last), leave
-      if (tid == NT - 1) {
+      if (tid == ring) {
         atomicExch(err, PFC_ETIMEOUT);
         const int last = t == 0 ? stages - 1 : t - 2 + stages;
         for (int u = t; u <= last && u < total; ++u)
@@ -552,30 +544,27 @@ __global__ void __launch_bounds__(NT, 1) k_ras_apply3d_win(Geo g, const BlockDes
       }
       return false;
     }
-    if (tid == NT - 1 && t >= 1 && t - 1 + stages < total) issue(t - 1 + stages);
-    const int lm = l % kWinLevels;
-    if (w0.ea >= 0) {
-      int a, b, c;
-      abc_of(w0.ea, &a, &b, &c);
-      if (fwd ? a + kWinLevels >= S.bx : a < kWinLevels) win[lm * kWinSlot + c * kWinPb + b] = 0.f;
-    }
+    if (tid == ring && t >= 1 && t - 1 + stages < total) issue(t - 1 + stages);
     if (w0.r >= 0) {
+      const unsigned char* data = stage_base + (size_t)st * sbytes;
       float cf[32];
-      load_row<TS>(stage_base + st * stage_elems, tid, w0.n, cf);
-      int a, b, c;
-      abc_of(w0.abc, &a, &b, &c);
-      const int base = lm * kWinSlot + c * kWinPb + b;
+      load_row<TS>(reinterpret_cast<const TS*>(data), tid, w0.n, cf);
+      const uint4* pu = reinterpret_cast<const uint4*>(data + fbytes);
+      const uint4 p0 = pu[tid], p1 = pu[w0.n + tid];
+      const int lm = level_of(t) % kWinLevels;
       float acc[4] = {w0.val, 0.f, 0.f, 0.f};
       if (fwd) {  // y_r = b_r - sum_lower l_ro y_(r+o)
-        win_lower<0>(acc, win, base, lm, cf);
+        win_lower<0>(acc, win, lm, p0, p1, cf);
         const float y = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        win[base] = y;
+        win[lm * kWinSlot + tid] = y;
         ybuf[w0.r] = y;
         if (t == nl - 1) w1.val = y;  // the first backward level is this level: the same rows
       } else {  // x_r = (y_r - sum_upper u_ro x_(r+o)) / u_rr; the core goes out (R_k^0)^T
-        win_upper<32>(acc, win, base, lm, cf);
+        win_upper<32>(acc, win, lm, p0, p1, cf);
         const float x = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * cf[0];
-        win[base] = x;
+        win[lm * kWinSlot + tid] = x;
+        int a, b, c;
+        abc_of(w0.abc, &a, &b, &c);
         if (a >= B.ox && a < B.ox + B.cx && b >= B.oy && b < B.oy + B.cy && c >= B.oz && c < B.oz + B.cz)
           z[gidx(g, B, a, b, c)] = sc * f2d_exact(x);
       }
@@ -617,23 +606,28 @@ constexpr size_t kSmemCap = 227 * 1024 - 1024;  // dynamic shared memory a CTA m
 
 // Bytes of the window kernel's level-start table (padded to 16).
 size_t win_lev_bytes(const Ras3D& R) { return ((size_t)(R.max_nlev + 1) * sizeof(int) + 15) / 16 * 16; }
+size_t win_stage_bytes(const Ras3D& R) {
+  return (size_t)R.max_level_rows * 32 * ((R.prec == PFC_BF16 ? 2 : 4) + 1);
+}
 
-// Factor levels in flight for the window kernel: as many as fit beside the window and the level
-// table (0: none).
+// Stages of the window kernel's copy ring: as many as fit while three blocks share an SM (two
+// levels at least), else while two do; 0 when the blocks' levels are too wide for it.
 int win_stages(const Ras3D& R) {
-  if (R.prec == PFC_F64 || R.max_byz > kWinMaxByz || R.max_level_rows > NT) return 0;
-  const size_t stage = (size_t)R.max_level_rows * 32 * (R.prec == PFC_BF16 ? 2 : 4);
-  const size_t fixed = (size_t)kWinFloats * sizeof(float) + win_lev_bytes(R);
-  if (fixed + 2 * stage > kSmemCap) return 0;
-  return (int)std::min<size_t>(kMaxStages3, (kSmemCap - fixed) / stage);
+  if (R.prec == PFC_F64 || R.max_level_rows > 255) return 0;
+  const size_t fixed = (size_t)kWinFloats * sizeof(float) + win_lev_bytes(R), stage = win_stage_bytes(R);
+  for (int per_sm = 3; per_sm >= 1; --per_sm) {
+    // the SM's 228 KB of shared memory, less each CTA's 1 KB reserve and its static arrays
+    const size_t cap = std::min<size_t>((size_t)228 * 1024 / per_sm - 1024 - 512, kSmemCap);
+    if (fixed + 2 * stage <= cap) return (int)std::min<size_t>(kMaxStages3, (cap - fixed) / stage);
+  }
+  return 0;
 }
 
 template <typename TS>
 void apply3d_win_dispatch(const Geo& g, const BlockDesc* blocks, int nblocks, const Ras3D& R, const double* r,
                           const double* rscale, double* z, const int* skip, int* err, cudaStream_t st) {
   const int stages = win_stages(R);
-  const size_t smem = (size_t)kWinFloats * sizeof(float) + (size_t)stages * R.max_level_rows * 32 * sizeof(TS) +
-                      win_lev_bytes(R);
+  const size_t smem = (size_t)kWinFloats * sizeof(float) + (size_t)stages * win_stage_bytes(R) + win_lev_bytes(R);
   cudaFuncSetAttribute(k_ras_apply3d_win<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ras_apply3d_win<TS><<<nblocks, NT, smem, st>>>(g, blocks, R, r, rscale, z, skip, err, stages);
   count_launches(1);

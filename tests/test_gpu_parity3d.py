@@ -82,12 +82,13 @@ def test_steps_3d_match_oracle(pfc):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("shape,parts", [((74, 74, 74), (2, 2, 2)), ((17, 16, 15), (2, 2, 2)),
-                                         ((36, 30, 27), (3, 2, 2))])
+@pytest.mark.parametrize("shape,parts", [((74, 74, 74), (2, 2, 2)), ((80, 80, 80), (2, 2, 2)),
+                                         ((17, 16, 15), (2, 2, 2)), ((36, 30, 27), (3, 2, 2))])
 def test_window_apply_equals_global_apply(pfc, shape, parts, prec):
     """The shared-memory level-window apply (variant 1) and the global-memory apply (variant 0)
-    take the same operations in the same order: bitwise equal outputs, on 39^3 blocks (the
-    window's largest: 218-row levels) as on small and uneven ones."""
+    take the same operations in the same order: bitwise equal outputs, on 39^3 blocks (the 256^3
+    workload's, 218-row levels), 42^3 blocks (252-row levels, near the window's 255) and small
+    and uneven ones."""
     Phi = inputs.noise_field(shape, -0.325, 0.3, 21)
     phin = inputs.noise_field(shape, -0.325, 0.3, 22)
     r = inputs.noise_field(shape, 0.0, 1.0, 23)
@@ -102,13 +103,13 @@ def test_window_apply_equals_global_apply(pfc, shape, parts, prec):
 
 
 def test_window_apply_refuses_blocks_it_cannot_hold(pfc):
-    """FP64 factors and blocks wider than 39 cells in y or z run only the global-memory apply:
-    asking for the window there fails at creation, and the default falls back."""
+    """FP64 factors and blocks with levels of more than 255 rows run only the global-memory
+    apply: asking for the window there fails at creation, and the default falls back."""
     with pytest.raises(pfc.PfcError):
         solver3(pfc, (16, 16, 16), (2, 2, 2), prec=0, apply_variant=1)
     with pytest.raises(pfc.PfcError):
-        solver3(pfc, (80, 80, 80), (2, 2, 2), prec=2, apply_variant=1)  # 42-cell blocks
-    assert solver3(pfc, (80, 80, 80), (2, 2, 2), prec=2).tuning()["apply_variant"] == 0
+        solver3(pfc, (90, 90, 90), (2, 2, 2), prec=2, apply_variant=1)  # 47^3 blocks: 316-row levels
+    assert solver3(pfc, (90, 90, 90), (2, 2, 2), prec=2).tuning()["apply_variant"] == 0
     assert solver3(pfc, (16, 16, 16), (2, 2, 2), prec=0).tuning()["apply_variant"] == 0
 
 
