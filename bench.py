@@ -6,8 +6,9 @@ One bench step = one full time step of the scheme (Newton + GMRES + RAS,
 energy, mass, adaptive dt) through the C ABI.  The headline is the mixed,
 learned-guess form (BF16 subdomain factors applied in FP32; float-float JVP,
 Gram-Schmidt dot products and multi-axpys; FP64 residual, Newton update, GMRES
-least squares, energy, mass and time step), timed with GMRES cycles as CUDA
-graphs.  Beside it: the plain FP64 NKS, the FP32 / BF16 factor forms with the
+least squares, energy, mass and time step), timed with every time step one
+captured CUDA graph (device-side Newton, GMRES and line-search control).
+Beside it: the plain FP64 NKS, the FP32 / BF16 factor forms with the
 phi^n guess, the same forms at 2048^2 and on the 256^3 BCC case, and the
 ensemble, mobility, Neumann and crack workloads.  Per form: iterations, the
 per-kernel rooflines of a separate profiled pass, and the errors against the
@@ -276,7 +277,7 @@ def make_solver(workload: str, prec: int, learned: bool = False, stream=True, **
     params = pfc.default_params(sub=tuple(w["parts"][::-1]), overlap=1, factor_prec=prec, dt_min=w["dt_min"],
                                 dt_max=w["dt_max"], eta=w["eta"],
                                 guess=pfc.PFC_GUESS_LEARNED if learned else pfc.PFC_GUESS_PREV, **form)
-    # a stream of its own: GMRES cycles run as captured graphs whenever per-kernel timing is off
+    # a stream of its own: every step runs as one captured graph whenever per-kernel timing is off
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params, stream=torch.cuda.Stream() if stream else None)
     net = None
     if learned:  # the committed network, trained on 512^2 trajectories of this workload's distribution
@@ -380,7 +381,7 @@ def run_variant(workload: str, prec: int, steps: int, warmup: int, world: int, l
     out["phi_after"] = s.get_field()  # after warm-up + timed + profiled steps (the same count for every form)
     if e2e:
         # same metric through the C ABI with host buffers: every step copies phi^n in from
-        # pinned host memory and phi^{n+1} back out (GMRES cycles as graphs)
+        # pinned host memory and phi^{n+1} back out (each step one graph)
         shape = tuple(s.shape)
         pin_in = torch.empty(shape, dtype=torch.float64).pin_memory()
         pin_out = torch.empty(shape, dtype=torch.float64).pin_memory()
