@@ -279,6 +279,7 @@ class Block:
     overlap: int
     shape: Tuple[int, ...]  # global grid shape
     neumann: bool = False  # walls instead of periodic wrap: the block is clipped to the grid
+    dims: Tuple[int, ...] = field(default=None)  # per-axis extent of Omega_k^delta (clipped at walls)
     block_idx: np.ndarray = field(default=None)  # global flat indices of Omega_k^delta (block C-order)
     core_mask: np.ndarray = field(default=None)  # True where the block point is in Omega_k
     core_idx: np.ndarray = field(default=None)  # global flat indices of Omega_k (block order)
@@ -299,6 +300,7 @@ class Block:
                 m = np.zeros(n + 2 * self.overlap, dtype=bool)
                 m[self.overlap : self.overlap + n] = True
             masks.append(m)
+        self.dims = tuple(len(ax) for ax in axes)
         grids = np.meshgrid(*axes, indexing="ij")
         self.block_idx = np.ravel_multi_index(tuple(g.ravel() for g in grids), self.shape)
         mg = np.meshgrid(*masks, indexing="ij")
@@ -377,7 +379,7 @@ def subdomain_matrix_improved_bc(
 def block_pattern(blk: Block, radius: int = 3) -> np.ndarray:
     """Structural pattern of A_k: block points whose local offsets satisfy
     |d|_1 <= 3, the support of Delta_d (1/2 L_gamma + q) (radius-3 composed stencil)."""
-    dims = [n + 2 * blk.overlap for n in blk.core_n]
+    dims = blk.dims
     coords = np.stack(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij"), -1).reshape(-1, len(dims))
     dist = np.abs(coords[:, None, :] - coords[None, :, :]).sum(-1)
     return dist <= radius
@@ -467,7 +469,7 @@ class Schwarz:
         elif solver == "ilu0":
             by_extent = {}  # blocks of one extent share their pattern: factored together
             for k, blk in enumerate(self.blocks):
-                by_extent.setdefault(tuple(n + 2 * blk.overlap for n in blk.core_n), []).append(k)
+                by_extent.setdefault(blk.dims, []).append(k)
             self.groups = []  # (block numbers, block-diagonal L, block-diagonal U) per extent
             for ks in by_extent.values():
                 pattern = block_pattern(self.blocks[ks[0]])

@@ -217,6 +217,28 @@ def test_shifted_ilu0_is_ilu0_of_the_shifted_block():
     np.testing.assert_allclose(z1.ravel()[blk.core_idx], sol[blk.core_mask], rtol=1e-13, atol=1e-15)
 
 
+def test_ilu0_schwarz_between_walls_is_per_block_ilu0():
+    """Between mirror walls the blocks stop at the walls (blocks of several extents): the
+    Schwarz 'ilu0' apply, which factors the blocks of one extent side by side, equals ILU(0) of
+    each block's own shifted matrix solved on its own, block by block (left-RAS: core rows)."""
+    shape = (12, 11, 10)
+    Phi, phin = rand_field(shape, 33), rand_field(shape, 34)
+    J = O.assemble_jacobian(Phi, phin, 0.5, 80 * math.pi / 256, 0.3, neumann=True)
+    blocks = O.decompose(shape, (2, 2, 2), 1, neumann=True)
+    assert len({b.dims for b in blocks}) > 1 and all(b.dims[0] == 7 for b in blocks)  # 6 + 1 at each wall
+    r = rand_field(shape, 35, 0.0, 1.0)
+    z = O.Schwarz(J, blocks, "left-ras", "ilu0", 0.1).apply(r)
+    ref = np.zeros(r.size)
+    for blk in blocks:
+        A = O.subdomain_matrix(J, blk)
+        As = A + 0.1 * np.mean(np.abs(np.diag(A))) * np.eye(A.shape[0])
+        rows, cols = np.nonzero(O.block_pattern(blk))
+        assert not np.any(As[~O.block_pattern(blk)])  # the folded wall rows stay in the radius-3 pattern
+        LU = O.ilu0(sp.csr_matrix((As[rows, cols], (rows, cols)), shape=As.shape))
+        ref[blk.core_idx] = O.ilu0_solve(LU, r.ravel()[blk.block_idx])[blk.core_mask]
+    np.testing.assert_allclose(z.ravel(), ref, rtol=1e-13, atol=1e-15)
+
+
 def test_gmres_unpreconditioned_matches_dense_solve():
     """GMRES with H = I to 1e-14 against a dense solve (restart exercised)."""
     shape = (8, 8)
