@@ -288,7 +288,7 @@ class Block:
         axes = []
         masks = []
         for lo, n, N in zip(self.core_lo, self.core_n, self.shape):
-            if n + 2 * self.overlap > N:
+            if n + 2 * self.overlap > N and not self.neumann:  # between walls the block is clipped
                 raise ValueError("block wider than the periodic grid")
             if self.neumann:  # READING: at a wall the overlapped block stops at the wall
                 a0, a1 = max(0, lo - self.overlap), min(N, lo + n + self.overlap)

@@ -190,18 +190,23 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   // Neumann walls: 2D, left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then
   // never see a second mirror image)
   if (p->boundary != PFC_PERIODIC &&
-      (p->boundary != PFC_NEUMANN || g->dim != 2 || p->ras_kind != PFC_LEFT_RAS || p->mobility != 0 ||
-       g->n[0] < 4 || g->n[1] < 4))
+      (p->boundary != PFC_NEUMANN || p->ras_kind != PFC_LEFT_RAS || p->mobility != 0 || g->n[0] < 4 ||
+       g->n[1] < 4 || (g->dim == 3 && g->n[2] < 4)))
     return PFC_EINVAL;
   for (int a = 0; a < g->dim; ++a) {
     if (p->sub[a] < 1 || p->sub[a] > g->n[a]) return PFC_EINVAL;
     const int core_max = (int)((g->n[a] + p->sub[a] - 1) / p->sub[a]);
     const int core_min = (int)(g->n[a] / p->sub[a]);
-    if (core_max + 2 * p->overlap > g->n[a]) return PFC_EINVAL;
+    // a periodic block must not reach its own image (3D blocks between walls are clipped instead)
+    if (core_max + 2 * p->overlap > g->n[a] && !(g->dim == 3 && p->boundary == PFC_NEUMANN)) return PFC_EINVAL;
     if (g->dim == 3) {
-      // 3D blocks: at least 7 cells per axis (offset order = row order), and the
-      // block plus its 3-cell ring must not wrap onto itself (A_k = R J R^T pattern)
-      if (core_min + 2 * p->overlap < 7 || core_max + 2 * p->overlap + 3 > g->n[a]) return PFC_EINVAL;
+      // 3D blocks: at least 7 cells per axis (offset order = row order); periodic blocks plus their
+      // 3-cell ring must not wrap onto themselves (A_k = R J R^T pattern); between walls a block at
+      // a wall has one overlap (or none, when one block spans the axis)
+      const int ext_min = p->boundary == PFC_NEUMANN ? (p->sub[a] == 1 ? (int)g->n[a] : core_min + p->overlap)
+                                                     : core_min + 2 * p->overlap;
+      if (ext_min < 7) return PFC_EINVAL;
+      if (p->boundary != PFC_NEUMANN && core_max + 2 * p->overlap + 3 > g->n[a]) return PFC_EINVAL;
       if (core_max + 2 * p->overlap > 1023) return PFC_EINVAL;  // row cells packed in 10 bits per axis
     }
   }
@@ -241,6 +246,12 @@ void build_blocks(const pfc_grid* g, const pfc_params* p, std::vector<BlockDesc>
           b.by = y1 - b.y0;
           b.ox = sx[bx].start - b.x0;
           b.oy = sy[by].start - b.y0;
+          if (g->dim == 3) {
+            const int z1 = std::min((int)g->n[2], b.z0 + b.bz);
+            b.z0 = std::max(0, b.z0);
+            b.bz = z1 - b.z0;
+            b.oz = sz[bz].start - b.z0;
+          }
         }
         out->push_back(b);
         const int n = b.bx * b.by * b.bz;
