@@ -146,8 +146,9 @@ typedef struct {
      n.grad Delta^2 phi = 0) as mirror walls half a cell outside the end cells: every
      stencil reads the mirror image of a cell beyond a wall.  The overlapped
      subdomains stop at the walls and A_k is the principal submatrix of the Neumann
-     Jacobian (the mirror images folded into the block's own columns).  2D grids of
-     at least 4 x 4 cells, left-RAS, mobility 0; pfc_residual_static stays periodic. */
+     Jacobian (the mirror images folded into the block's own columns).  Grids of
+     at least 4 cells per axis (2D and 3D), left-RAS, mobility 0; 3D blocks at least
+     7 cells per axis; pfc_residual_static stays periodic. */
   int boundary;
   /* Arnoldi dot products of the mixed path (F32/BF16 factors): 0 (default)
      float-float products and sums on the FP32 pipe (about 2^-46 relative, like

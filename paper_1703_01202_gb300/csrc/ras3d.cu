@@ -178,12 +178,38 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
   }
   const double ih2 = g.ih2;
   auto qat = [&](int a, int b, int c) { return q[gidx(g, B, a, b, c)]; };
+  // Between mirror walls (Sec. 2) a row within 3 cells of a wall has stencil entries beyond it;
+  // the Neumann Jacobian folds each onto the column of its mirror image (the image of global
+  // cell -1 - i is i, of n + i is n - 1 - i), and A_k keeps the folded entries whose columns lie
+  // in the block.
+  auto mir = [](int i, int n) { return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i); };
+  auto wall_row = [&](int a, int b, int c) {
+    return g.neumann && (B.x0 + a < 3 || B.x0 + a + 3 >= g.nx || B.y0 + b < 3 || B.y0 + b + 3 >= g.ny ||
+                         B.z0 + c < 3 || B.z0 + c + 3 >= g.nz);
+  };
+  // entry of row (a, b, c) of the wall-folded J (without the diagonal's 1/dt and shift) in the
+  // column of block cell (a2, b2, c2): the sum, in offset order, of the stencil entries whose
+  // mirror images land there
+  auto folded = [&](int a, int b, int c, int a2, int b2, int c2) {
+    double v = 0.0;
+    for (int d = 0; d < kNOff; ++d) {
+      const int X = mir(B.x0 + a + s_off[d][0], g.nx), Y = mir(B.y0 + b + s_off[d][1], g.ny),
+                Z = mir(B.z0 + c + s_off[d][2], g.nz);
+      if (X - B.x0 != a2 || Y - B.y0 != b2 || Z - B.z0 != c2) continue;
+      const int ad = abs(s_off[d][0]) + abs(s_off[d][1]) + abs(s_off[d][2]);
+      double t = lin343[(s_off[d][2] + 3) * 49 + (s_off[d][1] + 3) * 7 + (s_off[d][0] + 3)];
+      if (ad <= 1) t -= (ad == 0 ? -6.0 * ih2 : ih2) * q[X + (long long)g.nx * (Y + (long long)g.ny * Z)];
+      v += t;
+    }
+    return v;
+  };
   // sigma = shift * mean |a_ii| of the block matrix
   double dsum = 0.0;
   for (int r = tid; r < S.nrows; r += FT) {
     int a, b, c;
     abc_of(rowabc[r], &a, &b, &c);
-    dsum += fabs(idt + lin343[171] + 6.0 * ih2 * qat(a, b, c));
+    dsum += wall_row(a, b, c) ? fabs(folded(a, b, c, a, b, c) + idt)
+                              : fabs(idt + lin343[171] + 6.0 * ih2 * qat(a, b, c));
   }
   for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
   if (lane == 0) s_red[wid] = dsum;
@@ -203,6 +229,7 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
       int a, b, c;
       abc_of(rowabc[r0 + i], &a, &b, &c);
       // row i of A_k + sigma I (zero outside the block): lane j builds entries j and 32 + j
+      const bool wall = wall_row(a, b, c);  // the same for the whole warp
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int o = lane + 32 * h;
@@ -212,8 +239,12 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
           const int a2 = a + da, b2 = b + db, c2 = c + dc;
           if (a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0 && c2 < S.bz) {
             const int ad = abs(da) + abs(db) + abs(dc);
-            v = lin343[(dc + 3) * 49 + (db + 3) * 7 + (da + 3)];
-            if (ad <= 1) v -= (ad == 0 ? -6.0 * ih2 : ih2) * qat(a2, b2, c2);
+            if (wall) {
+              v = folded(a, b, c, a2, b2, c2);
+            } else {
+              v = lin343[(dc + 3) * 49 + (db + 3) * 7 + (da + 3)];
+              if (ad <= 1) v -= (ad == 0 ? -6.0 * ih2 : ih2) * qat(a2, b2, c2);
+            }
             if (ad == 0) v += idt + sigma;
           }
         }

@@ -1,7 +1,9 @@
 // FP64 stencil kernels of the 3D scheme: the DVDM residual (Eq. NSOP with the
 // variational derivative of Eq. discretedG), the Jacobian-vector product (Eq.
 // Jacobi), the discrete energy (Eqs. relations, freeenergy) and mass, on a
-// periodic nx x ny x nz grid (x fastest).
+// periodic nx x ny x nz grid (x fastest), or between mirror walls (Sec. 2: each
+// pass reads the mirror image of a cell beyond a wall, which makes the composed
+// operators those of the evenly extended fields).
 //
 // The radius-3 composed operators are evaluated in three 7-point passes with
 // two scratch fields (T1, T2): a Laplacian pass, a pass that forms mu (or the
@@ -16,17 +18,19 @@ namespace {
 
 constexpr int NT = 256;
 
-__device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
-__device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+// Neighbour index along an axis: the periodic image, or between mirror walls the cell itself
+// (the mirror image of the cell beyond the wall).
+__device__ __forceinline__ int wrap_up(int i, int n, int neu) { return i + 1 == n ? (neu ? i : 0) : i + 1; }
+__device__ __forceinline__ int wrap_dn(int i, int n, int neu) { return i == 0 ? (neu ? 0 : n - 1) : i - 1; }
 
 // unscaled 7-point Laplacian of u (+ u2 if given) at point idx = (x, y, z)
 __device__ __forceinline__ double lap7(const double* __restrict__ u, const double* __restrict__ u2, const Geo& g,
                                        int x, int y, int z) {
   const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long c = x + sy * y + sz * z;
-  const long long xp = c + (wrap_up(x, g.nx) - x) * sx, xm = c + (wrap_dn(x, g.nx) - x) * sx;
-  const long long yp = c + (wrap_up(y, g.ny) - y) * sy, ym = c + (wrap_dn(y, g.ny) - y) * sy;
-  const long long zp = c + (wrap_up(z, g.nz) - z) * sz, zm = c + (wrap_dn(z, g.nz) - z) * sz;
+  const long long xp = c + (wrap_up(x, g.nx, g.neumann) - x) * sx, xm = c + (wrap_dn(x, g.nx, g.neumann) - x) * sx;
+  const long long yp = c + (wrap_up(y, g.ny, g.neumann) - y) * sy, ym = c + (wrap_dn(y, g.ny, g.neumann) - y) * sy;
+  const long long zp = c + (wrap_up(z, g.nz, g.neumann) - z) * sz, zm = c + (wrap_dn(z, g.nz, g.neumann) - z) * sz;
   if (u2) {
     const double cc = u[c] + u2[c];
     return ((u[xp] + u2[xp]) + (u[xm] + u2[xm])) + ((u[yp] + u2[yp]) + (u[ym] + u2[ym])) +
@@ -141,9 +145,9 @@ __global__ void __launch_bounds__(NT) k_energy3d(Geo g, const double* __restrict
     int x, y, z;
     coords(g, i, &x, &y, &z);
     const double p = phi[i];
-    const double xp = phi[i + (wrap_up(x, g.nx) - x)], xm = phi[i + (wrap_dn(x, g.nx) - x)];
-    const double yp = phi[i + (wrap_up(y, g.ny) - y) * sy], ym = phi[i + (wrap_dn(y, g.ny) - y) * sy];
-    const double zp = phi[i + (wrap_up(z, g.nz) - z) * sz], zm = phi[i + (wrap_dn(z, g.nz) - z) * sz];
+    const double xp = phi[i + (wrap_up(x, g.nx, g.neumann) - x)], xm = phi[i + (wrap_dn(x, g.nx, g.neumann) - x)];
+    const double yp = phi[i + (wrap_up(y, g.ny, g.neumann) - y) * sy], ym = phi[i + (wrap_dn(y, g.ny, g.neumann) - y) * sy];
+    const double zp = phi[i + (wrap_up(z, g.nz, g.neumann) - z) * sz], zm = phi[i + (wrap_dn(z, g.nz, g.neumann) - z) * sz];
     const double lap = ih2 * ((xp + xm) + (yp + ym) + (zp + zm) - 6.0 * p);
     const double grad = (xp - p) * (xp - p) + (p - xm) * (p - xm) + (yp - p) * (yp - p) + (p - ym) * (p - ym) +
                         (zp - p) * (zp - p) + (p - zm) * (p - zm);
@@ -234,12 +238,12 @@ __device__ __forceinline__ bool nb_of(const Geo& g, Nb* o) {
   if (x >= g.nx || y >= g.ny) return false;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   o->c = x + sy * y + sz * z;
-  o->xp = o->c + (wrap_up(x, g.nx) - x);
-  o->xm = o->c + (wrap_dn(x, g.nx) - x);
-  o->yp = o->c + (wrap_up(y, g.ny) - y) * sy;
-  o->ym = o->c + (wrap_dn(y, g.ny) - y) * sy;
-  o->zp = o->c + (wrap_up(z, g.nz) - z) * sz;
-  o->zm = o->c + (wrap_dn(z, g.nz) - z) * sz;
+  o->xp = o->c + (wrap_up(x, g.nx, g.neumann) - x);
+  o->xm = o->c + (wrap_dn(x, g.nx, g.neumann) - x);
+  o->yp = o->c + (wrap_up(y, g.ny, g.neumann) - y) * sy;
+  o->ym = o->c + (wrap_dn(y, g.ny, g.neumann) - y) * sy;
+  o->zp = o->c + (wrap_up(z, g.nz, g.neumann) - z) * sz;
+  o->zm = o->c + (wrap_dn(z, g.nz, g.neumann) - z) * sz;
   return true;
 }
 __device__ __forceinline__ ff ldff(const float2* p, long long i) {

@@ -108,7 +108,8 @@ def test_mobility_validation(libpfc):
 
 
 def test_boundary_validation(libpfc):
-    """Neumann-type walls (boundary = 1): 2D grids of at least 4 x 4 cells, left-RAS, M = 1."""
+    """Neumann-type walls (boundary = 1): at least 4 cells per axis (2D and 3D), left-RAS, M = 1;
+    3D blocks at least 7 cells per axis (a block at a wall has one overlap)."""
     from paper_1703_01202_gb300 import pfc
 
     assert pfc.workspace_size((64, 48), pfc.default_params(sub=(4, 4), boundary=pfc.PFC_NEUMANN)) > 0
@@ -120,8 +121,14 @@ def test_boundary_validation(libpfc):
         with pytest.raises(pfc.PfcError):
             pfc.workspace_size(shape, pfc.default_params(**prm))
     assert pfc.workspace_size((3, 64), pfc.default_params(sub=(1, 1), overlap=0)) > 0  # periodic: fine
+    assert pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), boundary=1)) > 0
+    assert pfc.workspace_size((8, 8, 8), pfc.default_params(sub=(1, 1, 1), overlap=0, boundary=1)) > 0
+    for shape, sub in (((10, 10, 10), (2, 2, 2)),  # wall blocks of 5 + 1 cells
+                       ((6, 6, 6), (1, 1, 1))):    # a block of 6 cells per axis
+        with pytest.raises(pfc.PfcError):
+            pfc.workspace_size(shape, pfc.default_params(sub=sub, overlap=1 if sub[0] > 1 else 0, boundary=1))
     with pytest.raises(pfc.PfcError):
-        pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), boundary=1))
+        pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), boundary=1, mobility=1))
 
 
 def test_static_residual_and_wait_selftest_validation(libpfc):

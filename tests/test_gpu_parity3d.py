@@ -128,3 +128,54 @@ def test_float_float_jvp_3d(pfc, shape, prec):
     Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
     ref = O.jvp(v, Phi, phin, 2.5, H3, GAMMA3)
     np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 14, 18)])
+def test_neumann_operators_3d(pfc, shape):
+    """Mirror walls in 3D (Sec. 2): residual, FP64 and float-float JVP and energy against the
+    oracle's operators of the evenly extended fields."""
+    Phi = inputs.noise_field(shape, -0.3, 0.4, 41)
+    phin = inputs.noise_field(shape, -0.3, 0.4, 42)
+    v = inputs.noise_field(shape, 0.0, 1.0, 43)
+    s = solver3(pfc, shape, (2, 2, 2), boundary=pfc.PFC_NEUMANN)
+    F, nrm = s.residual(Phi, phin, 0.7)
+    ref = O.residual(Phi, phin, 0.7, H3, GAMMA3, neumann=True)
+    np.testing.assert_allclose(F.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    refj = O.jvp(v, Phi, phin, 2.5, H3, GAMMA3, neumann=True)
+    np.testing.assert_allclose(s.jvp(Phi, phin, v, 2.5).cpu().numpy(), refj, rtol=0, atol=1e-12 * np.abs(refj).max())
+    s2 = solver3(pfc, shape, (2, 2, 2), prec=2, boundary=pfc.PFC_NEUMANN)
+    np.testing.assert_allclose(s2.jvp(Phi, phin, v, 2.5).cpu().numpy(), refj, rtol=0, atol=1e-11 * np.abs(refj).max())
+    s.set_field(Phi)
+    assert s.energy() == pytest.approx(O.energy(Phi, H3, GAMMA3, neumann=True), rel=1e-12)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (2, 0.05)])
+@pytest.mark.parametrize("shape,parts", [((16, 16, 16), (2, 2, 2)), ((17, 15, 18), (2, 2, 2)), ((14, 8, 9), (2, 1, 1))])
+def test_neumann_precond_3d(pfc, shape, parts, prec, tol):
+    """Left-RAS between mirror walls: blocks stop at the walls and A_k is the principal submatrix
+    of the Neumann Jacobian (mirror images folded into the block's columns), against the oracle's
+    blocks of its assembled Neumann Jacobian."""
+    Phi = inputs.noise_field(shape, -0.325, 0.3, 44)
+    phin = inputs.noise_field(shape, -0.325, 0.3, 45)
+    r = inputs.noise_field(shape, 0.0, 1.0, 46)
+    s = solver3(pfc, shape, parts, prec=prec, boundary=pfc.PFC_NEUMANN)
+    z = s.precond_apply(Phi, phin, 2.0, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, 2.0, H3, GAMMA3, neumann=True)
+    ref = O.Schwarz(J, O.decompose(shape, parts, 1, neumann=True), "left-ras", "ilu0", 0.1).apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol_phi,tol_e", [(0, 1e-8, 1e-10), (2, 1e-7, 1e-9)])
+def test_neumann_steps_3d(pfc, prec, tol_phi, tol_e):
+    """Three fixed steps at dt = 0.5 between mirror walls on a 16^3 BCC-seeded field."""
+    shape = (16, 16, 16)
+    phi0 = inputs.bcc_seeds_3d(shape, H3, nseeds=1, d0=4 * H3, seed=5)
+    s = solver3(pfc, shape, (2, 2, 2), prec=prec, boundary=pfc.PFC_NEUMANN)
+    s.set_field(phi0)
+    infos = [s.step(0.5) for _ in range(3)]
+    ref, recs = O.run(phi0, H3, GAMMA3, O.Params(parts=(2, 2, 2), overlap=1, subdomain_solver="ilu0", neumann=True),
+                      3, fixed_dt=0.5)
+    assert np.abs(s.get_field() - ref).max() <= tol_phi
+    for inf, rec in zip(infos, recs):
+        assert abs(inf["energy"] - rec.energy) <= tol_e * abs(rec.energy)
