@@ -84,6 +84,7 @@ __device__ void gmres_after_axpy(GmresCtl* c, int j, int pass, int m, double wn2
   if (pass == 0) {
     if (wn2 < c->reorth_eta2 * c->wnorm2_before) {  // ||w'|| < eta ||w||: orthogonalise once more
       c->reorth = 1;
+      c->n_reorth += 1;
       return;
     }
     c->reorth = 0;
@@ -144,6 +145,7 @@ __device__ __noinline__ void last_cta_tail(const Tail& t, const double* __restri
     const int j = t.ia ? t.ia->j : t.j;
     if (t.kind == Tail::kAxpy) {
       gmres_after_axpy(c, j, t.pass, t.m, s_sum[0]);
+      if (t.set_reorth) cudaGraphSetConditional(t.h_reorth, c->reorth ? 1u : 0u);
     } else {
       for (int v = 0; v < nvals; ++v) t.out[v] = s_sum[v];
     }
@@ -282,13 +284,16 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   const Ring rg = ring_at(smem);
   __shared__ double red[NT / 32][G];
   __shared__ const double* sp[G + 1];
-  // The 1D grid is split evenly over the groups of G vectors this sweep has (however many
-  // the grid was sized for): P CTAs per group, CTA c of group g takes tiles c, c + P, ...;
-  // CTAs past gy * P only take a ticket.
+  // The 1D grid is split evenly over the gy = ceil(nv / G) groups this sweep has (however
+  // many the grid was sized for): P CTAs per group, CTA c of group g takes tiles c, c + P, ...;
+  // CTAs past gy * P only take a ticket.  The nv vectors are dealt to the groups in sizes that
+  // differ by at most one (9 vectors as 5 + 4, not 8 + 1), so that no group's CTAs wait idle
+  // on the others.
   const int gy = (nv + G - 1) / G, P = gridDim.x / gy;
   const int grp = blockIdx.x / P, cta = blockIdx.x - grp * P;
-  const int g0 = grp * G;
-  const int cnt = grp < gy ? max(0, min(G, nv - g0)) : 0;
+  const int gbase = nv / gy, grem = nv - gbase * gy;
+  const int g0 = grp * gbase + min(grp, grem);
+  const int cnt = grp < gy ? gbase + (grp < grem ? 1 : 0) : 0;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid <= G) sp[tid] = tid == 0 ? w : (tid - 1 < cnt ? vec_at(v0, tab, g0 + tid - 1) : w);
   const long long ntile = (n + kTile - 1) / kTile;
@@ -530,21 +535,21 @@ __global__ void k_extrapolate(double* __restrict__ out, const double* __restrict
     out[i] = fma(ratio, a[i] - b[i], a[i]);
 }
 
-__global__ void k_iter_setup(const GmresCtl* __restrict__ ctl, const double* const* __restrict__ vtab,
-                             const double* const* __restrict__ ztab, IterArgs* __restrict__ ia) {
+// The Arnoldi loop's condition, and the vectors of the iteration it lets run.
+__global__ void k_arnoldi_next(const GmresCtl* __restrict__ ctl, const double* const* __restrict__ vtab,
+                               const double* const* __restrict__ ztab, IterArgs* __restrict__ ia, int m,
+                               cudaGraphConditionalHandle h) {
   const int j = ctl->its;
-  ia->j = j;
-  ia->v = vtab[j];
-  ia->z = const_cast<double*>(ztab[j]);
-  ia->zplane = j;
-  ia->w = const_cast<double*>(vtab[j + 1]);
-  ia->scale = &ctl->scale[j];
-}
-
-// Keeps the graph's while loop running until the cycle is done (converged, broken
-// down or at the restart length).
-__global__ void k_cycle_cond(const GmresCtl* __restrict__ ctl, int m, cudaGraphConditionalHandle h) {
-  cudaGraphSetConditional(h, (!ctl->done && ctl->its < m) ? 1u : 0u);
+  const bool go = !ctl->done && j < m;
+  if (go) {
+    ia->j = j;
+    ia->v = vtab[j];
+    ia->z = const_cast<double*>(ztab[j]);
+    ia->zplane = j;
+    ia->w = const_cast<double*>(vtab[j + 1]);
+    ia->scale = &ctl->scale[j];
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 int red_ctas(long long n) {
@@ -605,14 +610,9 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
   count_launches(1);
 }
 
-void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
-                       cudaStream_t st) {
-  k_iter_setup<<<1, 1, 0, st>>>(ctl, vtab, ztab, ia);
-  count_launches(1);
-}
-
-void launch_cycle_cond(const GmresCtl* ctl, int m, cudaGraphConditionalHandle h, cudaStream_t st) {
-  k_cycle_cond<<<1, 1, 0, st>>>(ctl, m, h);
+void launch_arnoldi_next(const GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
+                         int m, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_arnoldi_next<<<1, 1, 0, st>>>(ctl, vtab, ztab, ia, m, h);
   count_launches(1);
 }
 

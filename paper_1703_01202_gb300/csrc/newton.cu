@@ -38,7 +38,7 @@ __global__ void k_newton_begin(StepCtl* c, const double* nrm2, IterArgs* ia, Ite
   c->newton_go = c->status == PFC_OK && r0 > c->target && c->newton_max_it > 0;
   c->factor_go = c->refactor;
   c->commit_go = 0;
-  c->n_factor = c->n_cycles = c->n_restarts = c->n_trials = 0;
+  c->n_factor = c->n_cycles = c->n_restarts = c->n_trials = c->n_reorth = 0;
   set_cond(h.newton, graph, c->newton_go);
 }
 
@@ -59,6 +59,7 @@ __global__ void k_gmres_begin(StepCtl* c, GmresCtl* g, StepHandles h, int graph)
   g->its = 0;
   g->reorth = 0;
   g->breakdown = 0;
+  g->n_reorth = 0;
   g->tol = tol;
   g->reorth_eta2 = c->reorth_eta2;
   g->beta = beta;
@@ -71,13 +72,10 @@ __global__ void k_gmres_begin(StepCtl* c, GmresCtl* g, StepHandles h, int graph)
   set_cond(h.cycle, graph, c->cycle_go);
 }
 
-__global__ void k_arnoldi_begin(const GmresCtl* g, int m, StepHandles h) {
-  cudaGraphSetConditional(h.arnoldi, (!g->done && g->its < m) ? 1u : 0u);
-}
-
 // After a cycle (its iterations, S updated): converged, failed, or restart.
 __global__ void k_cycle_decide(StepCtl* c, GmresCtl* g, StepHandles h, int graph) {
   c->gm_its += g->its;
+  c->n_reorth += g->n_reorth;
   const double est = g->est;
   int go = 0;
   if (!(est == est)) {
@@ -104,6 +102,7 @@ __global__ void k_gmres_restart(StepCtl* c, GmresCtl* g, const double* nrm2) {
   g->its = 0;
   g->reorth = 0;
   g->breakdown = 0;
+  g->n_reorth = 0;
   g->tol = c->gtol;
   g->reorth_eta2 = c->reorth_eta2;
   g->beta = beta;
@@ -200,7 +199,8 @@ __global__ void k_mstep_prep(StepCtl* c) {
 __global__ void k_mstep_end(StepCtl* c, const double* red45, pfc_step_info* rec, StepHandles h) {
   // kernels of the attempt (as the host counts a graph step) and this loop's own two per attempt
   c->kernels += 2 + 4 + (c->commit_go ? 3 : 0) + 6LL * c->m + (long long)c->n_factor * (2 + c->chunked) +
-                4LL * c->n_cycles + 5LL * c->n_restarts + 3LL * c->n_trials + (long long)c->gm_total * c->body_kernels;
+                4LL * c->n_cycles + 5LL * c->n_restarts + 3LL * c->n_trials + (long long)c->gm_total * c->body_kernels +
+                2LL * c->n_reorth;
   const int st = c->status;
   if ((st == PFC_ENEWTON || st == PFC_EGMRES) && c->cuts < c->dt_halvings) {
     c->dt *= 0.5;
@@ -268,10 +268,6 @@ void launch_factor_done(StepCtl* c, cudaStream_t st) {
 }
 void launch_gmres_begin(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st) {
   k_gmres_begin<<<1, 1, 0, st>>>(c, g, h, graph);
-  count_launches(1);
-}
-void launch_arnoldi_begin(const GmresCtl* g, int m, const StepHandles& h, cudaStream_t st) {
-  k_arnoldi_begin<<<1, 1, 0, st>>>(g, m, h);
   count_launches(1);
 }
 void launch_cycle_decide(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st) {

@@ -108,7 +108,7 @@ struct pfc_state {
   pfc::IterArgs* ia;    // Arnoldi iteration arguments (device): vectors of iteration j, q, 1/dt
   pfc::IterArgs* ia2;   // the restart's J S -> W with this step's 1/dt (device)
   pfc::StepHandles hs;  // conditional handles of the step graph
-  cudaStream_t cs[4];   // capture streams of the nested bodies (graph form; one more level in a batch graph)
+  cudaStream_t cs[5];   // capture streams of the nested bodies (graph form; one more level in a batch graph)
   pfc_step_info* recs;  // device records of the batch form's time loop (kBatchRecs)
   cudaGraph_t sgraph;
   cudaGraphExec_t sexec;
@@ -804,35 +804,6 @@ int emit_gmres_begin(pfc_state* s, int gm) {
 
 int gs_passes(const pfc_state* s) { return s->p.gmres_reorth_eta > 0.0 ? 2 : 1; }
 
-// Kernels of one Arnoldi iteration of the graph form.
-int arnoldi_body_kernels(const pfc_state* s) {
-  return 4 + 2 * gs_passes(s) + (s->fs.ras_kind != PFC_LEFT_RAS ? 1 : 0);
-}
-
-// One Arnoldi iteration (graph form): iteration setup, Schwarz apply, JVP, the
-// Gram-Schmidt passes and the loop test; the vectors of iteration j = its come from s->ia.
-void emit_arnoldi_body(pfc_state* s) {
-  const long long N = s->g.n;
-  const int m = s->p.gmres_restart;
-  const int* done = &s->ctl->done;  // a cycle that converged at its start runs the body once, all skipped
-  const int* reorth = &s->ctl->reorth;
-  const double* v0 = s->Vbuf;
-  pfc::launch_iter_setup(s->ctl, s->vtab, s->ztab, s->ia, s->st);
-  precond(s, nullptr, nullptr, nullptr, done, s->ia);
-  jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
-  for (int pass = 0; pass < gs_passes(s); ++pass) {
-    pfc::Tail td{pfc::Tail::kDot, 0, pass, m, s->ctl, ticket(s), nullptr, s->ia};
-    td.err = s->status_dev + 1;
-    pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                         dot_mode(s));
-    pfc::Tail ta{pfc::Tail::kAxpy, 0, pass, m, s->ctl, ticket(s), nullptr, s->ia};
-    ta.err = s->status_dev + 1;
-    pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done, pass ? reorth : nullptr,
-                          ta, s->st, ff_sweeps(s));
-  }
-  pfc::launch_cycle_cond(s->ctl, m, s->hs.arnoldi, s->st);
-}
-
 // The Arnoldi iterations of one cycle driven by the host: iterations are queued a chunk at a
 // time; after each chunk the head of the control block is copied back asynchronously, and the
 // host waits for a chunk's head only once the next chunk is queued, so the GPU never idles on
@@ -1069,6 +1040,48 @@ bool capture_body(pfc_state* s, cudaGraph_t body, cudaStream_t cs, F emit) {
   return ok;
 }
 
+// Kernels of one Arnoldi iteration of the graph form without a second Gram-Schmidt pass (each
+// second pass adds its two sweeps; StepCtl counts them).
+int arnoldi_body_kernels(const pfc_state* s) { return 5 + (s->fs.ras_kind != PFC_LEFT_RAS ? 1 : 0); }
+
+// One Arnoldi iteration (graph form): Schwarz apply, JVP, the first Gram-Schmidt pass, the
+// second pass inside an IF node that the first pass's last CTA sets (DGKS test), and the loop
+// test, which also writes the next iteration's vectors to s->ia.  The IF body is captured on
+// cs_if.
+bool emit_arnoldi_body(pfc_state* s, cudaStream_t cs_if) {
+  const long long N = s->g.n;
+  const int m = s->p.gmres_restart;
+  const int* done = &s->ctl->done;
+  const int* reorth = &s->ctl->reorth;
+  const double* v0 = s->Vbuf;
+  const bool two = gs_passes(s) == 2;
+  if (two && !new_handle(s->st, &s->hs.reorth)) return false;
+  precond(s, nullptr, nullptr, nullptr, done, s->ia);
+  jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
+  auto pass = [&](int p) {
+    pfc::Tail td{pfc::Tail::kDot, 0, p, m, s->ctl, ticket(s), nullptr, s->ia};
+    td.err = s->status_dev + 1;
+    pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, p ? reorth : nullptr, td, s->st,
+                         dot_mode(s));
+    pfc::Tail ta{pfc::Tail::kAxpy, 0, p, m, s->ctl, ticket(s), nullptr, s->ia};
+    ta.err = s->status_dev + 1;
+    if (two && p == 0) {
+      ta.h_reorth = s->hs.reorth;
+      ta.set_reorth = 1;
+    }
+    pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done, p ? reorth : nullptr,
+                          ta, s->st, ff_sweeps(s));
+    return cudaGetLastError() == cudaSuccess;
+  };
+  bool ok = pass(0);
+  if (ok && two) {
+    cudaGraph_t body;
+    ok = add_cond(s->st, s->hs.reorth, cudaGraphCondTypeIf, &body) && capture_body(s, body, cs_if, [&] { return pass(1); });
+  }
+  pfc::launch_arnoldi_next(s->ctl, s->vtab, s->ztab, s->ia, m, s->hs.arnoldi, s->st);
+  return ok && cudaGetLastError() == cudaSuccess;
+}
+
 // Queues the whole step of the graph form on s->st (which is being captured): every 1/dt
 // and line-search step is read from s->sc, every decision sets a conditional handle.
 bool emit_step_graph(pfc_state* s, int depth0 = 0) {
@@ -1091,13 +1104,10 @@ bool emit_step_graph(pfc_state* s, int depth0 = 0) {
               k = k && add_cond(s->st, h.cycle, cudaGraphCondTypeWhile, &cycle_body) &&
                   capture_body(s, cycle_body, cs[1], [&] {
                     if (!new_handle(s->st, &h.arnoldi) || !new_handle(s->st, &h.restart)) return false;
-                    pfc::launch_arnoldi_begin(s->ctl, m, h, s->st);
+                    pfc::launch_arnoldi_next(s->ctl, s->vtab, s->ztab, s->ia, m, h.arnoldi, s->st);
                     cudaGraph_t arnoldi_body, restart_body;
                     bool q = add_cond(s->st, h.arnoldi, cudaGraphCondTypeWhile, &arnoldi_body) &&
-                             capture_body(s, arnoldi_body, cs[2], [&] {
-                               emit_arnoldi_body(s);
-                               return cudaGetLastError() == cudaSuccess;
-                             });
+                             capture_body(s, arnoldi_body, cs[2], [&] { return emit_arnoldi_body(s, cs[3]); });
                     q = q && emit_cycle_end(s, 1) == PFC_OK;
                     q = q && add_cond(s->st, h.restart, cudaGraphCondTypeIf, &restart_body) &&
                         capture_body(s, restart_body, cs[2], [&] { return emit_restart(s, 1.0, 1) == PFC_OK; });
@@ -1124,7 +1134,7 @@ long long graph_step_launches(const pfc_state* s, const pfc::StepCtl& c) {
   n += 6LL * m;                                          // per Newton iteration
   n += (long long)c.n_factor * (2 + (chunked ? 1 : 0));  // factor (+ records), done
   n += 4LL * c.n_cycles + 5LL * c.n_restarts + 3LL * c.n_trials;
-  n += (long long)c.gm_total * arnoldi_body_kernels(s);
+  n += (long long)c.gm_total * arnoldi_body_kernels(s) + 2LL * c.n_reorth;
   return n;
 }
 

@@ -51,6 +51,7 @@ struct GmresCtl {
   int its;       // iterations completed in this cycle
   int reorth;    // second Gram-Schmidt pass requested for the current column
   int breakdown;
+  int n_reorth;  // second passes run in this cycle
   double tol, beta, est;
   double wnorm2_before;
   double reorth_eta2;  // second pass when ||w'||^2 < reorth_eta2 ||w||^2 (0: never)
@@ -63,7 +64,7 @@ struct GmresCtl {
 
 // Arguments of one Arnoldi iteration read from device memory, so that a captured
 // CUDA graph can loop over iterations: j and the vectors of step j are written by
-// k_iter_setup at the start of every iteration; q and idt by the host once per
+// the loop-condition kernel before every iteration; q and idt by the host once per
 // GMRES solve.
 struct IterArgs {
   int j;
@@ -95,7 +96,7 @@ struct StepCtl {
   // branch and loop conditions
   int newton_go, factor_go, cycle_go, restart_go, ls_go, commit_go;
   // what ran (the host counts the launches of a graph step from these)
-  int n_factor, n_cycles, n_restarts, n_trials;
+  int n_factor, n_cycles, n_restarts, n_trials, n_reorth;
   // time loop of the batch form (pfc_run_batch): the adaptive step of Eq. (sencondt), retries
   // with dt / 2, per-step records, all on the device
   double dt, dt_prev, E_n, E_nm1;   // controller state
@@ -107,7 +108,7 @@ struct StepCtl {
 };
 // Conditional handles of a step graph (unused when the host drives the step).
 struct StepHandles {
-  cudaGraphConditionalHandle newton, factor, cycle, arnoldi, restart, ls, commit, mloop;
+  cudaGraphConditionalHandle newton, factor, cycle, arnoldi, restart, ls, commit, mloop, reorth;
 };
 
 // Scalars the host reads back after a reduction.
@@ -350,6 +351,10 @@ struct Tail {
   const IterArgs* ia;       // when set, j comes from ia->j (graph mode)
   int* err = nullptr;       // PFC_ETIMEOUT is stored here when a bounded wait runs out
   const int* nx_dev = nullptr;  // multi-axpy: the vector count read from device memory (graph mode)
+  // graph mode, first Gram-Schmidt pass: the kAxpy tail sets this conditional handle to
+  // "second pass wanted" (the IF node around the second pass's sweeps)
+  cudaGraphConditionalHandle h_reorth = 0;
+  int set_reorth = 0;
 };
 
 // Vector lists: entry 0 is v0 (x0), entry i > 0 is tab[i] (a device array of pointers).
@@ -366,9 +371,11 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
                       cudaStream_t st, bool ff = false);
 // Graph-mode helpers: ia <- the vectors of iteration j = ctl->its; loop condition of a GMRES cycle.
-void launch_iter_setup(GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
-                       cudaStream_t st);
-void launch_cycle_cond(const GmresCtl* ctl, int m, cudaGraphConditionalHandle h, cudaStream_t st);
+// Graph mode, before the Arnoldi loop and at the end of each iteration: the loop's
+// conditional handle h = (cycle not done and fewer than m iterations), and when it goes on,
+// the next iteration's vectors in ia (j = its; V_j, Z_j, V_{j+1} from the pointer tables).
+void launch_arnoldi_next(const GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
+                         int m, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_reduce(const double* partial, int nvals, int nparts, double* out, cudaStream_t st);
 // ---- step control (newton.cu); graph = 1 also sets the conditional handles in h
 void launch_newton_begin(StepCtl* c, const double* nrm2, IterArgs* ia, IterArgs* ia_restart, const StepHandles& h,
@@ -376,7 +383,6 @@ void launch_newton_begin(StepCtl* c, const double* nrm2, IterArgs* ia, IterArgs*
 void launch_set_factor_cond(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
 void launch_factor_done(StepCtl* c, cudaStream_t st);
 void launch_gmres_begin(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st);
-void launch_arnoldi_begin(const GmresCtl* g, int m, const StepHandles& h, cudaStream_t st);
 void launch_cycle_decide(StepCtl* c, GmresCtl* g, const StepHandles& h, int graph, cudaStream_t st);
 void launch_gmres_restart(StepCtl* c, GmresCtl* g, const double* nrm2, cudaStream_t st);
 void launch_gmres_end(StepCtl* c, const int* status_dev, const StepHandles& h, int graph, cudaStream_t st);
