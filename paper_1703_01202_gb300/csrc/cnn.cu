@@ -22,6 +22,7 @@
 
 #include "../../include/pfc.h"
 #include "pfc_internal.cuh"
+#include "pfc_tma.cuh"
 
 namespace pfc {
 
@@ -119,107 +120,158 @@ __global__ void __launch_bounds__(NT) k_conv_fwd(int nx, int ny, const TI* __res
   }
 }
 
-// The 32 -> 32 convolutions of the forward pass as an implicit GEMM on the tensor
-// cores: per 16 x 16 tile, D (256 pixels x 32 channels) = sum over the 9 taps of
-// A_tap (256 x 32 input channels, the tile shifted by the tap) times W_tap (32 x 32),
-// in BF16 with FP32 accumulation (mma.sync m16n8k16).  Warp w owns tile rows 2w and
-// 2w+1 (two 16-pixel M tiles) and all 32 output channels (four N tiles); K runs over
-// tap x 32 channels in 18 steps of 16.  The input tile with its periodic halo sits in
-// shared memory pixel-major with channels contiguous (pixel stride 40 elements = 80
-// bytes, so the eight rows of an ldmatrix phase fall on distinct banks); the weights
-// sit tap-major [tap][co][ci] with the same stride.  z and GELU(z) are staged back
-// through shared memory and written as coalesced 16-pixel rows of each channel plane.
-constexpr int kMmaStride = 40;  // BF16 elements per pixel row / per weight row in shared memory
+// The 32 -> 32 convolutions of the forward pass as an implicit GEMM on the fifth-generation
+// tensor cores (tcgen05): per 16 x 16 tile, D (256 pixels x 32 channels) = sum over the 9 taps
+// of A_tap (the tile shifted by the tap, 32 input channels) times W_tap^T (32 x 32), BF16
+// operands from shared memory, FP32 accumulators in tensor memory (TMEM).  The 256 pixels
+// are two M = 128 halves: half h holds pixel columns 8h .. 8h + 7 of all 16 rows, so row i of
+// the half (TMEM lane i) is pixel (i / 8, 8h + i % 8).  K runs over tap x channel in 18 steps
+// of 16; one thread issues the 36 MMAs (N = 32) and commits them to an mbarrier.
+//
+// Shared-memory operands in the no-swizzle K-major layout of UMMA: 8 x 16-byte core matrices
+// (8 rows of 8 BF16 channels).  The input tile with its periodic halo is stored
+// [channel group g (4)][halo row (18)][halo column (18)][8 channels], so 8 consecutive pixels
+// of a row are one core matrix wherever the tap shifts them; the next 8 rows of M (the next
+// pixel row) lie 18 x 16 bytes further (stride-dimension offset), the next 8 channels of K
+// 18 x 18 x 16 bytes further (leading-dimension offset).  The weights are stored
+// [tap][g][co (32)][8 channels]: N-direction offset 128 bytes, K-direction 512 bytes.
+//
+// Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of half w / 4 (32 columns = the 32
+// output channels of its 32 pixels), adds the bias, stages z and GELU(z) in shared memory and
+// writes coalesced 16-pixel rows of each channel plane.  The MMA completion wait is bounded:
+// when it runs out the kernel stores nothing, records PFC_ETIMEOUT in *err and still frees
+// its TMEM.
+constexpr int kTcCols = 64;                       // TMEM columns: two halves x 32 channels (FP32)
+constexpr int kTcInBytes = 4 * TH * TH * 16;      // input tile: 20,736 bytes
+constexpr int kTcWBytes = 9 * 4 * 32 * 16;        // weights: 18,432 bytes
+constexpr int kTcSmem = kTcInBytes + kTcWBytes + 32 * 4 + 16;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4
+// at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension (K) and
+// stride-dimension (M/N) byte offsets, each >> 4 in 14 bits; bits 46-48 hold the fixed
+// descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
 }
-__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 consecutive FP32 columns of the calling thread's TMEM lane (warp-quarter lanes).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(NT) k_conv32_fwd_mma(int nx, int ny, const __nv_bfloat16* __restrict__ in,
-                                                       const __nv_bfloat16* __restrict__ W,
-                                                       const float* __restrict__ b, __nv_bfloat16* __restrict__ z,
-                                                       __nv_bfloat16* __restrict__ a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __nv_bfloat16* s_in = reinterpret_cast<__nv_bfloat16*>(smraw);      // [TH][TH][kMmaStride]
-  __nv_bfloat16* s_w = s_in + TH * TH * kMmaStride;                   // [9][32][kMmaStride]
-  float* s_b = reinterpret_cast<float*>(s_w + 9 * 32 * kMmaStride);    // [32]
+__global__ void __launch_bounds__(NT) k_conv32_fwd_tc(int nx, int ny, const __nv_bfloat16* __restrict__ in,
+                                                      const __nv_bfloat16* __restrict__ W,
+                                                      const float* __restrict__ b, __nv_bfloat16* __restrict__ z,
+                                                      __nv_bfloat16* __restrict__ a, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __nv_bfloat16* s_in = reinterpret_cast<__nv_bfloat16*>(smraw);                 // [4][TH][TH][8]
+  __nv_bfloat16* s_w = reinterpret_cast<__nv_bfloat16*>(smraw + kTcInBytes);    // [9][4][32][8]
+  float* s_b = reinterpret_cast<float*>(smraw + kTcInBytes + kTcWBytes);         // [32]
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smraw + kTcInBytes + kTcWBytes + 128);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smraw + kTcInBytes + kTcWBytes + 136);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc_alloc(s_tmem, kTcCols);
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
   const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
   const long long N = (long long)nx * ny;
-  for (int i = threadIdx.x; i < 32 * TH * TH; i += NT) {  // input planes -> pixel-major tile
+  for (int i = tid; i < 32 * TH * TH; i += NT) {  // input planes -> [g][row][col][8]
     const int c = i / (TH * TH), r = i - c * TH * TH;
     const int ly = r / TH, lx = r - ly * TH;
     const long long p = wrapi(x0 + lx - 1, nx) + (long long)nx * wrapi(y0 + ly - 1, ny);
-    s_in[(ly * TH + lx) * kMmaStride + c] = in[c * N + p];
+    s_in[((c >> 3) * TH * TH + r) * 8 + (c & 7)] = in[c * N + p];
   }
-  for (int i = threadIdx.x; i < 32 * 32 * 9; i += NT) {  // W[co][ci][tap] -> s_w[tap][co][ci]
+  for (int i = tid; i < 32 * 32 * 9; i += NT) {  // W[co][ci][tap] -> [tap][ci / 8][co][ci % 8]
     const int co = i / (32 * 9), r = i - co * 32 * 9;
     const int ci = r / 9, tap = r - ci * 9;
-    s_w[(tap * 32 + co) * kMmaStride + ci] = W[i];
+    s_w[((tap * 4 + (ci >> 3)) * 32 + co) * 8 + (ci & 7)] = W[i];
   }
-  if (threadIdx.x < 32) s_b[threadIdx.x] = b[threadIdx.x];
+  if (tid < 32) s_b[tid] = b[tid];
+  fence_proxy_async();  // the operands are read by the tensor cores (async proxy)
+  tc_fence_before();
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-    for (int kc = 0; kc < 2; ++kc) {  // input channels 16 kc .. 16 kc + 15
-      uint32_t bf[4][2];
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {  // two N tiles per ldmatrix.x4
-        const int co = 16 * np + (lane & 7) + ((lane >> 4) << 3);
-        const int ci = 16 * kc + ((lane >> 3) & 1) * 8;
-        ldsm_x4(smem_addr(s_w + (tap * 32 + co) * kMmaStride + ci), bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0],
-                bf[2 * np + 1][1]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int ty = 2 * warp + mt;  // tile row of this M tile; pixel x = row of the fragment
-        const int px = lane & 15, ci = 16 * kc + (lane >> 4) * 8;
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(smem_addr(s_in + ((ty + 1 + dy) * TH + (px + 1 + dx)) * kMmaStride + ci), a0, a1, a2, a3);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  if (tid == 0) {
+    const uint32_t in0 = smem_u32(s_in), w0 = smem_u32(s_w);
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      for (int kc = 0; kc < 2; ++kc) {  // channels 16 kc .. 16 kc + 15: groups 2 kc, 2 kc + 1
+        const uint64_t bd = umma_desc(w0 + (uint32_t)((tap * 4 + 2 * kc) * 32 * 16), 32 * 16, 8 * 16);
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t a_at = in0 + (uint32_t)(((2 * kc) * TH * TH + (1 + dy) * TH + 8 * h + 1 + dx) * 16);
+          tc_mma(tmem + 32u * h, umma_desc(a_at, TH * TH * 16, TH * 16), bd, (tap | kc) ? 1u : 0u);
+        }
       }
     }
+    tc_commit(s_bar);
   }
-  __syncthreads();  // the input tile is done: reuse it for the output staging
-  __nv_bfloat16* s_z = s_in;                // [32][256]
-  __nv_bfloat16* s_a = s_in + 32 * NT;      // [32][256]
-  const int gid = lane >> 2, tig = lane & 3;
+  if (!mbar_wait_bounded(s_bar, 0)) s_fail = 1;
+  tc_fence_after();
+  __syncthreads();  // every warp past the wait: the operand tiles are free for the output staging
+  const bool ok = s_fail == 0;
+  __nv_bfloat16* s_z = s_in;            // [32][256], over the input and weight tiles
+  __nv_bfloat16* s_a = s_in + 32 * NT;  // [32][256]
+  if (ok) {
+    const int q = warp & 3, h = warp >> 2;
+    uint32_t r[32];
+    tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32u * h, r);
+    const int i = 32 * q + lane;
+    const int pix = (i >> 3) * T + 8 * h + (i & 7);
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int ty = 2 * warp + mt;
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int px = gid + (e >> 1) * 8, co = 8 * nt + 2 * tig + (e & 1);
-        const float v = acc[mt][nt][e] + s_b[co];
-        s_z[co * NT + ty * T + px] = __float2bfloat16(v);
-        s_a[co * NT + ty * T + px] = __float2bfloat16(gelu_f(v));
-      }
+    for (int co = 0; co < 32; ++co) {
+      const float v = __uint_as_float(r[co]) + s_b[co];
+      s_z[co * NT + pix] = __float2bfloat16(v);
+      s_a[co * NT + pix] = __float2bfloat16(gelu_f(v));
+    }
   }
+  tc_fence_before();
   __syncthreads();
-  for (int i = threadIdx.x; i < 32 * NT; i += NT) {  // coalesced 16-pixel rows of every plane
+  if (warp == 0) {
+    tc_fence_after();
+    tc_dealloc(tmem, kTcCols);
+  }
+  if (!ok) {
+    if (tid == 0 && err) atomicExch(err, PFC_ETIMEOUT);
+    return;
+  }
+  for (int i = tid; i < 32 * NT; i += NT) {  // coalesced 16-pixel rows of every plane
     const int co = i / NT, r = i - co * NT;
     const int ty = r / T, tx = r - ty * T;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -394,11 +446,10 @@ void conv_fwd(int nx, int ny, const TI* in, const __nv_bfloat16* W, const float*
   count_launches(1);
 }
 
-void conv32_fwd_mma(int nx, int ny, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* b,
-                    __nv_bfloat16* z, __nv_bfloat16* a, cudaStream_t st) {
-  const size_t smem = sizeof(__nv_bfloat16) * (TH * TH + 9 * 32) * kMmaStride + sizeof(float) * 32;
-  cudaFuncSetAttribute(k_conv32_fwd_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_conv32_fwd_mma<<<dim3((nx + T - 1) / T, (ny + T - 1) / T), NT, smem, st>>>(nx, ny, in, W, b, z, a);
+void conv32_fwd_tc(int nx, int ny, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* b,
+                   __nv_bfloat16* z, __nv_bfloat16* a, int* err, cudaStream_t st) {
+  cudaFuncSetAttribute(k_conv32_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  k_conv32_fwd_tc<<<dim3((nx + T - 1) / T, (ny + T - 1) / T), NT, kTcSmem, st>>>(nx, ny, in, W, b, z, a, err);
   count_launches(1);
 }
 
@@ -442,6 +493,7 @@ struct Cnn {
   float* d2;
   float* partial;          // kGradCtas x (largest layer's parameter count)
   double* red;             // reduction partials of the loss
+  int* err;                // PFC_ETIMEOUT when a bounded wait of a kernel ran out (0: none)
 };
 
 size_t cnn_workspace_bytes(long long n) {
@@ -454,6 +506,7 @@ size_t cnn_workspace_bytes(long long n) {
   t += 2 * r(sizeof(float) * 32 * n);
   t += r(sizeof(float) * (size_t)kGradCtas * (32 * 32 * 9 + 32));
   t += r(sizeof(double) * 1024);
+  t += r(sizeof(int));
   return t;
 }
 
@@ -477,6 +530,18 @@ void cnn_bind(Cnn* c, void* ws) {
   c->d2 = (float*)take(sizeof(float) * 32 * n);
   c->partial = (float*)take(sizeof(float) * (size_t)kGradCtas * (32 * 32 * 9 + 32));
   c->red = (double*)take(sizeof(double) * 1024);
+  c->err = (int*)take(sizeof(int));
+}
+
+// The error flag of the network's kernels (PFC_ETIMEOUT when a bounded wait ran out), cleared
+// once read; waits for the work queued on the network's stream.
+int cnn_status(Cnn* c) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return PFC_ECUDA;
+  if (e && cudaMemsetAsync(c->err, 0, sizeof(int), c->st) != cudaSuccess) return PFC_ECUDA;
+  return e;
 }
 
 // Forward pass on 3 FP64 feature planes (3 x n, planar); result in c->out (FP32).
@@ -486,8 +551,10 @@ void cnn_forward(Cnn* c, const double* feat) {
   const float* th = c->theta;
   conv_fwd<3, 32, true, double, __nv_bfloat16>(nx, ny, feat, W + layer_offset(0), th + layer_offset(0) + 32 * 3 * 9,
                                                c->z[0], c->a[0], c->st);
-  conv32_fwd_mma(nx, ny, c->a[0], W + layer_offset(1), th + layer_offset(1) + 32 * 32 * 9, c->z[1], c->a[1], c->st);
-  conv32_fwd_mma(nx, ny, c->a[1], W + layer_offset(2), th + layer_offset(2) + 32 * 32 * 9, c->z[2], c->a[2], c->st);
+  conv32_fwd_tc(nx, ny, c->a[0], W + layer_offset(1), th + layer_offset(1) + 32 * 32 * 9, c->z[1], c->a[1], c->err,
+                c->st);
+  conv32_fwd_tc(nx, ny, c->a[1], W + layer_offset(2), th + layer_offset(2) + 32 * 32 * 9, c->z[2], c->a[2], c->err,
+                c->st);
   conv_fwd<32, 1, false, __nv_bfloat16, float>(nx, ny, c->a[2], W + layer_offset(3), th + layer_offset(3) + 32 * 9,
                                                c->out, nullptr, c->st);
 }
@@ -709,7 +776,7 @@ int pfc_cnn_forward(pfc_cnn* h, const double* feat, double* out) {
   pfc::cnn_forward(&h->c, feat);
   pfc::cnn_out_to_f64(&h->c, out);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->c.st) != cudaSuccess) return PFC_ECUDA;
-  return PFC_OK;
+  return pfc::cnn_status(&h->c);
 }
 
 static int cnn_loss(pfc_cnn* h, int nparts, double* loss) {
@@ -725,7 +792,7 @@ static int cnn_loss(pfc_cnn* h, int nparts, double* loss) {
     *loss = s / (double)h->c.n;
   }
   free(part);
-  return rc;
+  return rc ? rc : pfc::cnn_status(&h->c);
 }
 
 int pfc_cnn_loss_grad(pfc_cnn* h, const double* feat, const double* target, double* loss, float* grad) {
@@ -758,7 +825,7 @@ int pfc_cnn_train_step(pfc_cnn* h, const double* feat, const double* target, dou
   int rc = pfc::cnn_backward(&h->c, feat, target, &np);
   if (rc) return rc;
   pfc::cnn_adam(&h->c, (float)lr, t);
-  if (!loss) return cudaGetLastError() == cudaSuccess ? PFC_OK : PFC_ECUDA;
+  if (!loss) return cudaGetLastError() == cudaSuccess ? pfc::cnn_status(&h->c) : PFC_ECUDA;
   return cnn_loss(h, np, loss);
 }
 

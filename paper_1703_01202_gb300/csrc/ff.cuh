@@ -46,6 +46,17 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
+// Vectors stored as float pairs: element i of an FP64-sized array holds (hi, lo) of a
+// normalised pair (|lo| <= ulp(hi) / 2) in its 8 bytes.  The mixed path keeps its Krylov
+// basis this way, so the Arnoldi sweeps need no split per element.
+__device__ __forceinline__ ff ld_pair(const double* p, long long i) {
+  const float2 t = reinterpret_cast<const float2*>(p)[i];
+  return {t.x, t.y};
+}
+__device__ __forceinline__ void st_pair(double* p, long long i, ff a) {
+  reinterpret_cast<float2*>(p)[i] = make_float2(a.hi, a.lo);
+}
+
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ ff two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
@@ -65,6 +76,11 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// x as a normalised float pair (hi = x rounded to a float, lo = the rest rounded): 2^-48 relative.
+__device__ __forceinline__ ff ff_pair_of(double x) {
+  const ff a = ff_of(x);
+  return fast_two_sum(a.hi, a.lo);
+}
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product

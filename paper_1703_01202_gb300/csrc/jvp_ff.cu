@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
                                                  const double* __restrict__ vscale, const double* __restrict__ q,
                                                  double idt, double* __restrict__ Jv, const int* __restrict__ skip,
                                                  const IterArgs* __restrict__ ia, const __grid_constant__ JvpMaps maps,
-                                                 int zj, int* __restrict__ err) {
+                                                 int zj, int* __restrict__ err, int pout) {
   if (skip && *skip) return;
   if (ia) {  // graph mode: J Z_j into V_(j+1)
     v = ia->z;
@@ -137,7 +137,11 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
     if (gx < g.nx && gy < g.ny) {
       const int a = ty + 1, b = tx + 1;
       const ff Lw = ff_lap5(sW[a][b], sW[a][b + 1], sW[a][b - 1], sW[a + 1][b], sW[a - 1][b]);
-      Jv[gx + (long long)g.nx * gy] = ff_to_double(ff_dot2m(sV[ty + R][tx + R], fidt, ih2, Lw));
+      const ff jv = ff_dot2m(sV[ty + R][tx + R], fidt, ih2, Lw);
+      if (pout)
+        st_pair(Jv, gx + (long long)g.nx * gy, jv);
+      else
+        Jv[gx + (long long)g.nx * gy] = ff_to_double(jv);
     }
   }
 }
@@ -179,11 +183,12 @@ void encode_jvp_maps(const Geo& g, const double* Zbuf, size_t vstride, int m, co
 }
 
 void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                     const int* skip, cudaStream_t st, const IterArgs* ia, const JvpMaps* maps, int zj, int* err) {
+                     const int* skip, cudaStream_t st, const IterArgs* ia, const JvpMaps* maps, int zj, int* err,
+                     int pout) {
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
   JvpMaps m{};
   if (maps) m = *maps;
-  k_jvp2d_ff<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia, m, zj, err);
+  k_jvp2d_ff<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia, m, zj, err, pout);
   count_launches(1);
 }
 
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
                                                    double idt, double* __restrict__ Jv, const int* __restrict__ skip,
                                                    const IterArgs* __restrict__ ia,
                                                    const __grid_constant__ JvpMaps maps, int zj,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err, int pout) {
   if (skip && *skip) return;
   if (ia) {  // graph mode: J Z_j into V_(j+1)
     v = ia->z;
@@ -268,7 +273,11 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
     if (gx < g.nx && gy < g.ny) {
       const int a = ty + 1, b = tx + 1;
       const float Lw = (sW[a][b + 1] + sW[a][b - 1]) + (sW[a + 1][b] + sW[a - 1][b]) - 4.0f * sW[a][b];
-      Jv[gx + (long long)g.nx * gy] = f2d_bits(fmaf(sV[ty + FR][tx + FR], fidt, -ih2 * Lw));
+      const float jv = fmaf(sV[ty + FR][tx + FR], fidt, -ih2 * Lw);
+      if (pout)
+        st_pair(Jv, gx + (long long)g.nx * gy, ff{jv, 0.0f});
+      else
+        Jv[gx + (long long)g.nx * gy] = f2d_bits(jv);
     }
   }
 }
@@ -276,11 +285,11 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
 }  // namespace
 
 void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, const int* skip,
-                      cudaStream_t st, const IterArgs* ia, const JvpMaps* maps, int zj, int* err) {
+                      cudaStream_t st, const IterArgs* ia, const JvpMaps* maps, int zj, int* err, int pout) {
   dim3 grid((g.nx + FTX - 1) / FTX, (g.ny + FTY - 1) / FTY);
   JvpMaps m{};
   if (maps) m = *maps;
-  k_jvp2d_f32<<<grid, dim3(32, 8), 0, st>>>(g, v, q, idt, Jv, skip, ia, m, zj, err);
+  k_jvp2d_f32<<<grid, dim3(32, 8), 0, st>>>(g, v, q, idt, Jv, skip, ia, m, zj, err, pout);
   count_launches(1);
 }
 

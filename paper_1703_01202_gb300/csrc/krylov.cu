@@ -11,23 +11,27 @@
 // sweep, with no separate reduction launch.
 //
 // On the mixed path (F32/BF16 factors) the Arnoldi sweeps run on the FP32 pipe.
-// The multi-axpy w -= sum c_k V_k uses the float-float arithmetic of ff.cuh
-// (about 2^-46 relative) and stores w in FP64: the Arnoldi relation
-// J Z_j = V H holds to that accuracy whatever the coefficients are.  The
-// coefficients (the multi-dot products) are float-float too by default
-// (Dot::kFF: both operands split into float pairs, products with their exact
-// rounding error and the cross terms, running sums with two-sum), so the
-// orthogonalisation keeps FP64-class accuracy.  In both sweeps part of every
-// tile goes to the FP64 pipe instead (kPd below), which works beside the FP32 pipe.  Dot::kF32 -- FP32 products of
-// the vectors cut to 24-bit significands, about 2^-24 of |V_i| |w| per
-// product -- is a faster opt-in form (pfc_params.gmres_fast_dots) that leaves
-// the orthogonality of the new vector to the conditional second (DGKS) pass.
+// There the Krylov basis V is stored as normalised float pairs (hi, lo) in the
+// 8 bytes of each element (the JVP writes them, the sweeps and the Schwarz apply
+// read them), so no sweep splits an FP64 value.  The multi-axpy w -= sum c_k V_k
+// uses the float-float arithmetic of ff.cuh (about 2^-46 relative) and stores w
+// as a pair: the Arnoldi relation J Z_j = V H holds to that accuracy whatever
+// the coefficients are.  The coefficients (the multi-dot products) are
+// float-float too by default (Dot::kFF: products with their exact rounding error
+// and the cross terms, running sums with two-sum), so the orthogonalisation keeps
+// FP64-class accuracy.  (The same sweeps over FP64-stored vectors, for the
+// mobility form whose JVP stays FP64, split each element and send part of every
+// tile to the FP64 pipe, kPd below.)  Dot::kF32 -- FP32 products of the leading
+// floats, about 2^-24 of |V_i| |w| per product -- is a faster opt-in form
+// (pfc_params.gmres_fast_dots) that leaves the orthogonality of the new vector
+// to the conditional second (DGKS) pass.
 //
 // The basis is kept unnormalised: V_i = scale_i * Vraw_i with scale_i held on
 // the device, so no kernel pass is spent on normalising.  Every kernel takes
 // the cycle's "done" flag and returns at once when it is set, which lets the
 // host queue several iterations ahead and synchronise rarely.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include "../../include/pfc.h"
@@ -252,13 +256,23 @@ enum Dot { kF64 = 0, kFF = 1, kF32 = 2 };
 
 // The multi-dot of this CTA's group of up to G vectors against w (wv: w in FP64,
 // wff: w split into float pairs, wf: w cut to floats).
-template <int D>
+// PR: the vectors are stored as float pairs (the mixed path's basis): every point in
+// float-float (or FP32 from the leading floats), no split and no FP64 part.
+template <int D, bool PR>
 __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const double* wv, const ff* wff, const float* wf,
                                          double* acc, ff* aff, float* af, int k) {
 #pragma unroll
   for (int p = 0; p < kPts; ++p) {
     const int i = threadIdx.x + p * NT;
     if (i < cntp) {
+      if (PR) {
+        const ff v = ld_pair(tb, i);
+        if (D == kF32)
+          af[k] = __fmaf_rn(v.hi, wf[p], af[k]);
+        else
+          aff[k] = ff_acc(aff[k], ff_prod(v, wff[p]));
+        continue;
+      }
       const double v = tb[i];
       if (D == kF32)
         af[k] = __fmaf_rn(f32_cut(v), wf[p], af[k]);
@@ -271,7 +285,8 @@ __device__ __forceinline__ void dot_tile(const double* tb, int cntp, const doubl
 }
 
 // partial[(g0 + k) * P + cta] = sum_i V_{g0+k}[i] * w[i] over this CTA's tiles (P CTAs per group).
-template <int D>
+// PR: V and w stored as float pairs (D = kFF or kF32).
+template <int D, bool PR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
                double* __restrict__ partial, const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
@@ -326,6 +341,11 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
 #pragma unroll
         for (int p = 0; p < kPts; ++p) {
           const int i = tid + p * NT;
+          if (PR) {
+            wff[p] = i < cntp ? ld_pair(tb, i) : ff{0.0f, 0.0f};
+            wf[p] = wff[p].hi;
+            continue;
+          }
           wv[p] = i < cntp ? tb[i] : 0.0;
           if (D == kF32) wf[p] = f32_cut(wv[p]);
           if (D == kFF && p >= kPd) wff[p] = ff_split(wv[p]);
@@ -336,7 +356,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
       for (int k = 0; k < G; ++k) {
         if (k < cnt) {  // block-uniform
           if (!(ok = ring_wait(rg, q))) break;
-          dot_tile<D>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wff, wf, acc, aff, af, k);
+          dot_tile<D, PR>(rg.buf + (size_t)(q % kStages) * kTile, cntp, wv, wff, wf, acc, aff, af, k);
           ring_release(rg, q++);
         }
       }
@@ -392,8 +412,10 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
 
 // w = w + sign * sum_k coef[k] X_k over this CTA's tiles (the tile of w comes last);
 // partial[0..] = sum w^2, and with SUM partial[gridDim..] = sum w.  FF: the sum over
-// k in float-float, one FP64 addition per point to store w.
-template <bool SUM, bool FF>
+// k in float-float, one FP64 addition per point to store w.  PR (with FF, without SUM): X
+// and w stored as float pairs, every point in float-float, w stored as a normalised pair and
+// sum w^2 taken in float-float.
+template <bool SUM, bool FF, bool PR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multiaxpy(double* __restrict__ w, const double* x0, const double* const* __restrict__ tab, int nx,
                 const double* __restrict__ coef, double sign, long long n, double* __restrict__ partial,
@@ -423,6 +445,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
   const int per = nx + 1, total = my_tiles * per;
   ring_init(rg);  // also makes c, cf, sp visible
   double s2 = 0.0, s1 = 0.0;
+  ff s2f = {0.0f, 0.0f};
   if (wid == NT / 32) {  // producer warp
     if (lane == 0) ring_produce(rg, total, n, per, [&](int k) { return sp[k]; }, tail.err, blockIdx.x, gridDim.x);
   } else {
@@ -448,7 +471,9 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
           for (int p = 0; p < kPts; ++p) {
             const int i = tid + p * NT;
             if (i < cntp) {
-              if (FF && p >= kPd)
+              if (PR)
+                af[p] = ff_acc(af[p], ff_prod(cfk, ld_pair(tb, i)));
+              else if (FF && p >= kPd)
                 af[p] = ff_acc(af[p], ff_prod(cfk, ff_split(tb[i])));
               else
                 acc[p] = fma(ck, tb[i], acc[p]);
@@ -459,6 +484,13 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
           for (int p = 0; p < kPts; ++p) {
             const int i = tid + p * NT;
             if (i < cntp) {
+              if (PR) {
+                const ff a = ff_acc(ld_pair(tb, i), af[p]);
+                const ff wn = fast_two_sum(a.hi, a.lo);
+                st_pair(w, base + i, wn);
+                s2f = ff_acc(s2f, ff_prod(wn, wn));
+                continue;
+              }
               const double wn = FF && p >= kPd ? ff_to_double(ff_acc(ff_split(tb[i]), af[p])) : tb[i] + acc[p];
               w[base + i] = wn;
               s2 = fma(wn, wn, s2);
@@ -470,6 +502,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
       }
     }
     if (!ok && lane == 0 && tail.err) atomicExch(tail.err, PFC_ETIMEOUT);
+    if (PR) s2 = ff_to_double(s2f);
     s2 = warp_sum(s2);
     s1 = warp_sum(s1);
     if (lane == 0) {
@@ -561,7 +594,7 @@ int red_ctas(long long n) {
 
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     int dot, int nv_grid) {
+                     int dot, int nv_grid, bool pairs) {
   // groups of G vectors in y; about kSweepMinCtas CTAs per SM in all.  The grid is sized for
   // nv_grid vectors (>= nv): a sweep then splits the points over CTAs as the graph form's
   // sweeps do (sized for the restart length), so both sum in the same order.
@@ -570,42 +603,53 @@ void launch_multidot(const double* v0, const double* const* tab, int nv, const d
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)(kRedCtas / gy)));
   const dim3 grid(bx * gy);  // split over the groups the sweep has inside the kernel
   const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
-#define PFC_DOT(D)                                                                                    \
-  do {                                                                                                \
-    cudaFuncSetAttribute(k_multidot<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-    k_multidot<D><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail); \
+#define PFC_DOT(D, PR)                                                                                    \
+  do {                                                                                                    \
+    cudaFuncSetAttribute(k_multidot<D, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    k_multidot<D, PR><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail); \
   } while (0)
-  if (dot == kDotFF)
-    PFC_DOT(kFF);
+  if (dot == kDotFF && pairs)
+    PFC_DOT(kFF, true);
+  else if (dot == kDotF32 && pairs)
+    PFC_DOT(kF32, true);
+  else if (dot == kDotFF)
+    PFC_DOT(kFF, false);
   else if (dot == kDotF32)
-    PFC_DOT(kF32);
+    PFC_DOT(kF32, false);
   else
-    PFC_DOT(kF64);
+    PFC_DOT(kF64, false);
 #undef PFC_DOT
   count_launches(1);
 }
 
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
-                      cudaStream_t st, bool ff) {
+                      cudaStream_t st, bool ff, bool pairs) {
   const long long ntile = (n + kTile - 1) / kTile;
   const int bx = (int)std::max(1ll, std::min(ntile, (long long)kRedCtas));
   const size_t smem = (size_t)kStages * kTile * sizeof(double) + 2 * kStages * 8;
   // the sum of w is read only by the kSums tail (and by callers of partials-only sweeps)
   const bool sum = !(tail.counter && tail.kind != Tail::kSums);
-#define PFC_AXPY(S, F)                                                                                  \
+#define PFC_AXPY(S, F, PR)                                                                              \
   do {                                                                                                  \
-    cudaFuncSetAttribute(k_multiaxpy<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    k_multiaxpy<S, F><<<bx, kSweepThreads, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, tail); \
+    cudaFuncSetAttribute(k_multiaxpy<S, F, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_multiaxpy<S, F, PR><<<bx, kSweepThreads, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, \
+                                                           tail);                                      \
   } while (0)
-  if (sum && ff)
-    PFC_AXPY(true, true);
+  if (pairs && sum) {  // float-pair vectors come with no sum of w (the Gram-Schmidt sweeps)
+    fprintf(stderr, "libpfc: float-pair multi-axpy with the sum of w\n");
+    return;
+  }
+  if (pairs)
+    PFC_AXPY(false, true, true);
+  else if (sum && ff)
+    PFC_AXPY(true, true, false);
   else if (sum)
-    PFC_AXPY(true, false);
+    PFC_AXPY(true, false, false);
   else if (ff)
-    PFC_AXPY(false, true);
+    PFC_AXPY(false, true, false);
   else
-    PFC_AXPY(false, false);
+    PFC_AXPY(false, false, false);
 #undef PFC_AXPY
   count_launches(1);
 }

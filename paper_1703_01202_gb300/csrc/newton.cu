@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "../../include/pfc.h"
+#include "ff.cuh"
 #include "pfc_internal.cuh"
 
 namespace pfc {
@@ -149,6 +150,11 @@ __global__ void k_copy_if_ok(const StepCtl* c, CopyPairs cp, long long n) {
   if (c->status != PFC_OK) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (int k = 0; k < cp.n; ++k) {
+    if ((cp.to_pairs >> k) & 1u) {
+      for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+        st_pair(cp.dst[k], i, ff_pair_of(cp.src[k][i]));
+      continue;
+    }
     const double2* __restrict__ s = reinterpret_cast<const double2*>(cp.src[k]);
     double2* __restrict__ d = reinterpret_cast<double2*>(cp.dst[k]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n / 2; i += stride) d[i] = s[i];
@@ -157,11 +163,14 @@ __global__ void k_copy_if_ok(const StepCtl* c, CopyPairs cp, long long n) {
 }
 
 __global__ void k_gmres_prep(double* __restrict__ S, double* __restrict__ red2, const double* __restrict__ F,
-                             double* __restrict__ V0, long long n) {
+                             double* __restrict__ V0, long long n, int pairs) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
     S[i] = 0.0;
-    V0[i] = F[i];
+    if (pairs)
+      st_pair(V0, i, ff_pair_of(F[i]));
+    else
+      V0[i] = F[i];
   }
   if (blockIdx.x == 0 && threadIdx.x < 2) red2[threadIdx.x] = 0.0;
 }
@@ -291,9 +300,10 @@ void launch_copy_if_ok(const StepCtl* c, const CopyPairs& cp, long long n, cudaS
   k_copy_if_ok<<<(int)(b < kRedCtas ? (b < 1 ? 1 : b) : kRedCtas), 256, 0, st>>>(c, cp, n);
   count_launches(1);
 }
-void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st) {
+void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st,
+                       bool pairs) {
   const long long b = (n + 255) / 256;
-  k_gmres_prep<<<(int)(b < kRedCtas ? (b < 1 ? 1 : b) : kRedCtas), 256, 0, st>>>(S, red2, F, V0, n);
+  k_gmres_prep<<<(int)(b < kRedCtas ? (b < 1 ? 1 : b) : kRedCtas), 256, 0, st>>>(S, red2, F, V0, n, pairs ? 1 : 0);
   count_launches(1);
 }
 void launch_newton_next(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st) {

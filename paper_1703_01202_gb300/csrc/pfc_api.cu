@@ -636,6 +636,10 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
 // The mixed path (F32/BF16 factors) runs the Arnoldi sweeps in float-float arithmetic
 // (the dot products too, unless gmres_fast_dots asks for FP32 ones).
 bool ff_sweeps(const pfc_state* s) { return s->p.factor_prec != PFC_F64; }
+// The mixed path keeps its Krylov basis V as float pairs (ff.cuh): the JVP writes them, the
+// sweeps and the Schwarz apply read them without a split.  Not with variable mobility, whose JVP
+// stays FP64.
+bool pair_basis(const pfc_state* s) { return ff_sweeps(s) && !s->p.mobility; }
 // Bytes the apply kernel in use reads and writes per launch (its storage format).
 double apply_stored(const pfc_state* s) {
   return s->dim == 2 && s->fs.variant == pfc::kChunkedVariant ? s->apply_bytes_chunk : s->apply_bytes_step;
@@ -646,25 +650,30 @@ int dot_mode(const pfc_state* s) {
 }
 
 // zplane: v = Z_zplane of the basis and q = s->q, so the product may stage both by TMA (-1: not).
+// pout: out (or ia->w) is a basis vector stored as float pairs (pair_basis).
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
-         const pfc::IterArgs* ia = nullptr, int zplane = -1) {
+         const pfc::IterArgs* ia = nullptr, int zplane = -1, bool pout = false) {
   if (s->dim == 2 && s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
     const bool trial = q != nullptr && q == s->qt;
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu, trial ? s->smt : s->sm);
   } else if (s->dim == 2 && s->fs.prec != PFC_F64 && s->p.jvp_fp32)  // mixed path, opt-in: plain FP32
-    pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1);
+    pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1, pout);
   else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
-    pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1);
+    pfc::launch_jvp2d_ff(s->g, v, nullptr, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1,
+                         pout);
   else if (s->dim == 2)
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
   else if (s->fs.prec != PFC_F64)  // 3D mixed path: float-float passes on the FP32 pipe
-    pfc::launch_jvp3d_ff(s->g, v, q, idt, out, s->T1, s->T2, skip, s->st);
+    pfc::launch_jvp3d_ff(s->g, v, q, idt, out, s->T1, s->T2, skip, s->st, pout);
   else
     pfc::launch_jvp3d(s->g, v, nullptr, q, idt, out, s->T1, s->T2, skip, s->st);
 }
 
+// pin: r (or ia->v) is a basis vector stored as float pairs (pair_basis).
 void precond(pfc_state* s, const double* r, const double* rscale, double* z, const int* skip,
-             const pfc::IterArgs* ia = nullptr) {
+             const pfc::IterArgs* ia = nullptr, bool pin = false) {
+  s->fs.pin = pin ? 1 : 0;
+  s->r3.pin = pin ? 1 : 0;
   if (s->dim == 2)
     pfc::launch_ras_apply2d(s->g, s->blocks_dev, s->nblocks, s->fs, r, rscale, z, skip, s->status_dev + 1, s->st,
                             ia, &s->dc);
@@ -796,7 +805,7 @@ int emit_factor(pfc_state* s, double idt) {
 // GMRES for J S = -F from S = 0 (Eq. hjacobi): S and the sums of S cleared, V_0 <- F
 // (scaled by -1/||F|| on the device), the cycle's tolerance and state.
 int emit_gmres_begin(pfc_state* s, int gm) {
-  pfc::launch_gmres_prep(s->S, s->red + 8, s->F, s->Vbuf, s->g.n, s->st);
+  pfc::launch_gmres_prep(s->S, s->red + 8, s->F, s->Vbuf, s->g.n, s->st, pair_basis(s));
   pfc::launch_gmres_begin(s->sc, s->ctl, s->hs, gm, s->st);
   CU(cudaGetLastError());
   return PFC_OK;
@@ -815,6 +824,7 @@ int arnoldi_host(pfc_state* s, double idt) {
   const int* done = &s->ctl->done;
   const int* reorth = &s->ctl->reorth;
   const double* v0 = s->Vbuf;
+  const bool pairs = pair_basis(s);
   int j = 0;
   const int chunk = 3;
   int c = 0, pend = -1;  // chunks queued; buffer of the pending chunk
@@ -830,23 +840,23 @@ int arnoldi_host(pfc_state* s, double idt) {
       // runs only on the DGKS test, which the host does not see)
       int ps;
       PROF_BEGIN(ps);
-      precond(s, vj, &s->ctl->scale[j], zj, done);
+      precond(s, vj, &s->ctl->scale[j], zj, done, nullptr, pairs);
       PROF_END(ps, PFC_PROF_APPLY, j, s->apply_bytes, 0.0, apply_stored(s));
       PROF_BEGIN(ps);
-      jvp(s, zj, s->q, idt, w, done, nullptr, j);
+      jvp(s, zj, s->q, idt, w, done, nullptr, j, pairs);
       PROF_END(ps, PFC_PROF_JVP, j, 24.0 * N);  // reads v, q; writes Jv
       for (int pass = 0; pass < gs_passes(s); ++pass) {
         pfc::Tail td{pfc::Tail::kDot, j, pass, m, s->ctl, ticket(s), nullptr};
         td.err = s->status_dev + 1;
         if (pass == 0) PROF_BEGIN(ps);
         pfc::launch_multidot(v0, s->vtab, j + 2, w, N, s->partial, done, pass ? reorth : nullptr, td, s->st,
-                             dot_mode(s), m + 1);
+                             dot_mode(s), m + 1, pairs);
         if (pass == 0) PROF_END(ps, PFC_PROF_DOT, j, 8.0 * N * (j + 2));  // reads V_0..V_j and w
         pfc::Tail ta{pfc::Tail::kAxpy, j, pass, m, s->ctl, ticket(s), nullptr};
         ta.err = s->status_dev + 1;
         if (pass == 0) PROF_BEGIN(ps);
         pfc::launch_multiaxpy(w, v0, s->vtab, j + 1, s->ctl->coef, -1.0, N, s->partial, done,
-                              pass ? reorth : nullptr, ta, s->st, ff_sweeps(s));
+                              pass ? reorth : nullptr, ta, s->st, ff_sweeps(s), pairs);
         if (pass == 0) PROF_END(ps, PFC_PROF_AXPY, j, 8.0 * N * (j + 3));  // reads V_0..V_j, w; writes w
       }
     }
@@ -904,6 +914,7 @@ int emit_restart(pfc_state* s, double idt, int gm) {
   cp.src[0] = s->W;
   cp.dst[0] = s->Vbuf;
   cp.n = 1;
+  cp.to_pairs = pair_basis(s) ? 1u : 0u;
   pfc::launch_copy_if_ok(s->sc, cp, N, s->st);
   CU(cudaGetLastError());
   return PFC_OK;
@@ -1055,14 +1066,15 @@ bool emit_arnoldi_body(pfc_state* s, cudaStream_t cs_if) {
   const int* reorth = &s->ctl->reorth;
   const double* v0 = s->Vbuf;
   const bool two = gs_passes(s) == 2;
+  const bool pairs = pair_basis(s);
   if (two && !new_handle(s->st, &s->hs.reorth)) return false;
-  precond(s, nullptr, nullptr, nullptr, done, s->ia);
-  jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia);
+  precond(s, nullptr, nullptr, nullptr, done, s->ia, pairs);
+  jvp(s, nullptr, nullptr, 0.0, nullptr, done, s->ia, -1, pairs);
   auto pass = [&](int p) {
     pfc::Tail td{pfc::Tail::kDot, 0, p, m, s->ctl, ticket(s), nullptr, s->ia};
     td.err = s->status_dev + 1;
     pfc::launch_multidot(v0, s->vtab, m + 1, nullptr, N, s->partial, done, p ? reorth : nullptr, td, s->st,
-                         dot_mode(s));
+                         dot_mode(s), 0, pairs);
     pfc::Tail ta{pfc::Tail::kAxpy, 0, p, m, s->ctl, ticket(s), nullptr, s->ia};
     ta.err = s->status_dev + 1;
     if (two && p == 0) {
@@ -1070,7 +1082,7 @@ bool emit_arnoldi_body(pfc_state* s, cudaStream_t cs_if) {
       ta.set_reorth = 1;
     }
     pfc::launch_multiaxpy(nullptr, v0, s->vtab, m, s->ctl->coef, -1.0, N, s->partial, done, p ? reorth : nullptr,
-                          ta, s->st, ff_sweeps(s));
+                          ta, s->st, ff_sweeps(s), pairs);
     return cudaGetLastError() == cudaSuccess;
   };
   bool ok = pass(0);
@@ -1260,6 +1272,13 @@ int safeguarded_guess(pfc_state* s, double dt, bool learned, int* used) {
   if ((rc = eval_residual(s, s->Phi, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 3))) return rc;
   if ((rc = eval_residual(s, s->phin, nullptr, 0.0, false, s->phin, idt, s->Ft, nullptr, nullptr, 6))) return rc;
   if ((rc = sync_read(s, s->red_h + 2, s->red + 2, 5 * sizeof(double)))) return rc;
+  if (learned) {
+    pfc::Cnn* c = reinterpret_cast<pfc::Cnn*>(s->cnn);
+    const cudaStream_t own = pfc::cnn_swap_stream(c, s->st);
+    rc = pfc::cnn_status(c);
+    pfc::cnn_swap_stream(c, own);
+    if (rc) return rc;
+  }
   const double rl = learned ? s->red_h[2] : NAN, re = s->red_h[3], rp = s->red_h[6];
   s->ref_norm = std::sqrt(rp);
   double best = re;

@@ -163,11 +163,12 @@ void encode_jvp_maps(const Geo& g, const double* Zbuf, size_t vstride, int m, co
 // one, interior tiles stage by TMA; a staging wait that runs out records PFC_ETIMEOUT in *err.
 void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
                      const int* skip, cudaStream_t st, const IterArgs* ia = nullptr, const JvpMaps* maps = nullptr,
-                     int zj = -1, int* err = nullptr);
+                     int zj = -1, int* err = nullptr, int pout = 0);
 // The same JVP in plain FP32 (opt-in on the mixed path, pfc_params.jvp_fp32).
+// pout (both): Jv is stored as float pairs (ff.cuh), the form of the mixed path's Krylov basis.
 void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, const int* skip,
                       cudaStream_t st, const IterArgs* ia = nullptr, const JvpMaps* maps = nullptr, int zj = -1,
-                      int* err = nullptr);
+                      int* err = nullptr, int pout = 0);
 void launch_qcoef(const Geo& g, const double* Phi, const double* phin, double* q, cudaStream_t st);
 
 // ---- Schwarz preconditioner (ras2d.cu)
@@ -200,6 +201,7 @@ struct FactorStore {
   // parts point by point; PFC_RIGHT_RAS also restricts r to the core (R_k^0).
   int ras_kind;
   double* Yb;
+  int pin;  // the apply's input r is stored as float pairs (the mixed path's Krylov basis)
   // variable mobility: mu and s = (Phi + phi^n)/2 at the factored iterate (null: M = 1), and the
   // largest (bx + 2)(by + 2) of a block with its one-cell ring
   const double* mob_mu;
@@ -271,7 +273,7 @@ void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const dou
                   double* T1, double* T2, const int* skip, cudaStream_t st);
 // The same product in float-float arithmetic (the mixed path); T1, T2 hold float pairs.
 void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
-                     const int* skip, cudaStream_t st);
+                     const int* skip, cudaStream_t st, int pout = 0);  // pout: Jv as float pairs
 void launch_energy3d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
 
 // ---- 3D Schwarz preconditioner with shifted ILU(0) subdomain solves (ras3d.cu)
@@ -305,6 +307,7 @@ struct Ras3D {
   const uint8_t* posL;  // per row, 32 bytes in the level layout: place of each lower / upper
   const uint8_t* posU;  // neighbour in its level's row list (255: outside the block)
   double shift;       // diagonal shift, relative to the block's mean |a_ii|
+  int pin;            // the apply's input r is stored as float pairs (the mixed path's Krylov basis)
 };
 // Whether the window apply can run these blocks: FP32/BF16 factors and levels of at most 255 rows.
 bool apply3d_window_ok(const Ras3D& R);
@@ -318,6 +321,7 @@ struct Cnn;
 size_t cnn_workspace_bytes(long long n);
 void cnn_bind(Cnn* c, void* ws);
 void cnn_forward(Cnn* c, const double* feat);
+int cnn_status(Cnn* c);  // PFC_ETIMEOUT if a bounded wait of the network's kernels ran out (then cleared)
 int cnn_backward(Cnn* c, const double* feat, const double* target, int* nparts);
 void cnn_adam(Cnn* c, float lr, int t);
 void cnn_refresh_bf16(Cnn* c);
@@ -363,13 +367,15 @@ struct Tail {
 // dot: arithmetic of the products -- kDotF64, kDotFF (float-float on the FP32 pipe, the mixed
 // path's default) or kDotF32 (FP32 products of values cut to floats, opt-in).
 // ff: float-float multi-axpy on the FP32 pipe (the mixed path's Arnoldi sweeps)
+// pairs: the vectors (and w) are stored as float pairs (ff.cuh), the mixed path's Krylov
+// basis; with dot = kDotFF / kDotF32 and, for the multi-axpy, ff and a tail other than kSums
 constexpr int kDotF64 = 0, kDotFF = 1, kDotF32 = 2;
 void launch_multidot(const double* v0, const double* const* tab, int nv, const double* w, long long n,
                      double* partial, const int* skip, const int* only_if, const Tail& tail, cudaStream_t st,
-                     int dot = kDotF64, int nv_grid = 0);
+                     int dot = kDotF64, int nv_grid = 0, bool pairs = false);
 void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int nx, const double* coef, double sign,
                       long long n, double* partial, const int* skip, const int* only_if, const Tail& tail,
-                      cudaStream_t st, bool ff = false);
+                      cudaStream_t st, bool ff = false, bool pairs = false);
 // Graph-mode helpers: ia <- the vectors of iteration j = ctl->its; loop condition of a GMRES cycle.
 // Graph mode, before the Arnoldi loop and at the end of each iteration: the loop's
 // conditional handle h = (cycle not done and fewer than m iterations), and when it goes on,
@@ -388,14 +394,17 @@ void launch_gmres_restart(StepCtl* c, GmresCtl* g, const double* nrm2, cudaStrea
 void launch_gmres_end(StepCtl* c, const int* status_dev, const StepHandles& h, int graph, cudaStream_t st);
 void launch_ls_decide(StepCtl* c, const double* nrm2, const StepHandles& h, int graph, cudaStream_t st);
 // Copies src[k] -> dst[k] (k < npairs, N doubles each) when the step's status is still PFC_OK.
+// Bit k of to_pairs: dst[k] receives src[k] as float pairs (ff.cuh) instead of a copy.
 struct CopyPairs {
   const double* src[5];
   double* dst[5];
   int n;
+  unsigned to_pairs;
 };
 void launch_copy_if_ok(const StepCtl* c, const CopyPairs& cp, long long n, cudaStream_t st);
-// GMRES start: S = 0, red2[0..1] = 0 (|S|^2, sum S), V0 <- F.
-void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st);
+// GMRES start: S = 0, red2[0..1] = 0 (|S|^2, sum S), V0 <- F (as float pairs with pairs).
+void launch_gmres_prep(double* S, double* red2, const double* F, double* V0, long long n, cudaStream_t st,
+                       bool pairs = false);
 void launch_newton_next(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
 void launch_step_end(StepCtl* c, const StepHandles& h, int graph, cudaStream_t st);
 // Batch form's device time loop: the loop test, the next step's dt (or the halved retry), and

@@ -30,6 +30,17 @@
 namespace pfc {
 namespace {
 
+// Element i of the apply's input in the compute type; pin: r is stored as float pairs (the mixed
+// path's Krylov basis), read as the float nearest their sum.
+template <typename TC>
+__device__ __forceinline__ TC ld_r(const double* __restrict__ r, long long i, int pin) {
+  if (pin) {
+    const float2 t = reinterpret_cast<const float2*>(r)[i];
+    return (TC)__fadd_rn(t.x, t.y);
+  }
+  return (TC)r[i];
+}
+
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(32 * WPC) k_ras_apply2d(Geo g, const BlockDesc
   }
   for (int t = li; t < n; t += LB) {  // restriction R_k^delta (periodic wrap) and pivots
     const int a = t % bx, c = t / bx;
-    buf[t] = valid ? (TC)r[wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny)] : (TC)0;
+    buf[t] = valid ? ld_r<TC>(r, wrap(B.x0 + a, g.nx) + (long long)g.nx * wrap(B.y0 + c, g.ny), fs.pin) : (TC)0;
     pv[t] = valid ? piv[t] : (uint8_t)0;
   }
   __syncwarp();
@@ -944,7 +955,7 @@ __global__ void __launch_bounds__(32 * WPC)
     const bool core_only = fs.ras_kind == PFC_RIGHT_RAS;
     for (int t = lane; t < nc * KC; t += 32) {  // restriction R_k^delta (R_k^0 for right-RAS); zeros past n
       const bool in = t < n && (!core_only || (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy));
-      y[t] = in ? (TC)r[wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny)] : (TC)0;
+      y[t] = in ? ld_r<TC>(r, wrap1(B.x0 + a, g.nx) + (long long)g.nx * wrap1(B.y0 + c, g.ny), fs.pin) : (TC)0;
       a += da;
       c += dc;
       if (a >= B.bx) {

@@ -86,6 +86,13 @@ __device__ __forceinline__ int lev_elem(int o, int i, int n) {
   return ((o / E) * n + i) * E + (o % E);
 }
 
+// Element i of an input stored as float pairs (the mixed path's Krylov basis): the float nearest
+// their sum.
+__device__ __forceinline__ float pair_sum(const double* __restrict__ r, long long i) {
+  const float2 t = reinterpret_cast<const float2*>(r)[i];
+  return __fadd_rn(t.x, t.y);
+}
+
 template <typename TC>
 __device__ __forceinline__ TC fma_tc(TC a, TC b, TC c);
 template <>
@@ -336,7 +343,8 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d(Geo g, const BlockDesc* __re
   for (int r = threadIdx.x; r < S.nrows; r += NT) {
     int a, b, c;
     abc_of(rowabc[r], &a, &b, &c);
-    Y[rowpad[r]] = tc_of<TC>(rin[gidx(g, B, a, b, c)]);
+    const long long gi = gidx(g, B, a, b, c);
+    Y[rowpad[r]] = R.pin ? (TC)pair_sum(rin, gi) : tc_of<TC>(rin[gi]);
   }
   __syncthreads();
   for (int t = 0; t < total; ++t) {
@@ -535,7 +543,8 @@ __global__ void __launch_bounds__(NT) k_ras_apply3d_win(Geo g, const BlockDesc* 
   for (int r = tid; r < S.nrows; r += NT) {
     int a, b, c;
     abc_of(rowabc[r], &a, &b, &c);
-    ybuf[r] = d2f_rn(rin[gidx(g, B, a, b, c)]);
+    const long long gi = gidx(g, B, a, b, c);
+    ybuf[r] = R.pin ? pair_sum(rin, gi) : d2f_rn(rin[gi]);
   }
   for (int i = tid; i < kWinFloats; i += NT) win[i] = 0.f;
   __syncthreads();

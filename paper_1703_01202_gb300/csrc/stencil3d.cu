@@ -279,25 +279,29 @@ __global__ void __launch_bounds__(FX* FY) k_mid3d_ff(Geo g, const double* __rest
 // J v = v idt - ih2 Lap w
 __global__ void __launch_bounds__(FX* FY) k_jvp_out3d_ff(Geo g, const double* __restrict__ v,
                                                          const float2* __restrict__ T2, double idt,
-                                                         double* __restrict__ Jv, const int* __restrict__ skip) {
+                                                         double* __restrict__ Jv, const int* __restrict__ skip, int pout) {
   if (skip && *skip) return;
   Nb o;
   if (!nb_of(g, &o)) return;
   const ff Lw = ff_lap7(ldff(T2, o.c), ldff(T2, o.xp), ldff(T2, o.xm), ldff(T2, o.yp), ldff(T2, o.ym),
                         ldff(T2, o.zp), ldff(T2, o.zm));
-  Jv[o.c] = ff_to_double(ff_dot2m(ff_split(v[o.c]), ff_split(idt), ff_split(g.ih2), Lw));
+  const ff jv = ff_dot2m(ff_split(v[o.c]), ff_split(idt), ff_split(g.ih2), Lw);
+  if (pout)
+    st_pair(Jv, o.c, jv);
+  else
+    Jv[o.c] = ff_to_double(jv);
 }
 
 }  // namespace
 
 void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
-                     const int* skip, cudaStream_t st) {
+                     const int* skip, cudaStream_t st, int pout) {
   const dim3 grid((g.nx + FX - 1) / FX, (g.ny + FY - 1) / FY, g.nz), blk(FX, FY);
   float2* t1 = reinterpret_cast<float2*>(T1);
   float2* t2 = reinterpret_cast<float2*>(T2);
   k_lap3d_ff<<<grid, blk, 0, st>>>(g, v, t1, skip);
   k_mid3d_ff<<<grid, blk, 0, st>>>(g, v, q, t1, t2, skip);
-  k_jvp_out3d_ff<<<grid, blk, 0, st>>>(g, v, t2, idt, Jv, skip);
+  k_jvp_out3d_ff<<<grid, blk, 0, st>>>(g, v, t2, idt, Jv, skip, pout);
   count_launches(3);
 }
 

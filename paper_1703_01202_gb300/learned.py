@@ -4,9 +4,10 @@ Trajectories come from the solver itself (plain NKS, F32 factors) on
 hexagonal-seed crystal-growth fields like the 1024^2 workload's, on a smaller
 grid; every step after the first gives one sample (features of phi^n, phi^{n-1},
 dt and the target correction toward phi^{n+1}), built on the device by
-pfc_cnn_sample.  Training runs pfc_cnn_train_step (the library's forward,
-backward and Adam kernels), one sample per Adam step.  All arithmetic runs in
-libpfc; this module only sequences calls and keeps samples in device memory.
+pfc_cnn_sample when the sample is used (only the trajectories' fields are kept).
+Training runs pfc_cnn_train_step (the library's forward, backward and Adam
+kernels), one sample per Adam step.  All arithmetic runs in libpfc; this module
+only sequences calls and keeps the fields in device memory.
 """
 from __future__ import annotations
 
@@ -28,7 +29,8 @@ DT_MIN, DT_MAX, ETA = 1e-2, 10.0, 5000.0
 def generate(n_traj: int, steps: int, shape=(512, 512), seed0: int = 2000, s_out: Optional[float] = None,
              sub: Optional[Tuple[int, int]] = None) -> Dict:
     """Runs n_traj trajectories of `steps` adaptive steps from seeded hexagonal
-    crystal fields and returns the device samples and the output scale."""
+    crystal fields and returns their device fields (one sample per step after the
+    first) and the output scale."""
     import torch
 
     ny, nx = shape
@@ -36,8 +38,6 @@ def generate(n_traj: int, steps: int, shape=(512, 512), seed0: int = 2000, s_out
     params = pfc.default_params(sub=sub, overlap=1, factor_prec=pfc.PFC_F32, dt_min=DT_MIN, dt_max=DT_MAX, eta=ETA)
     solver = pfc.Solver(shape, H, GAMMA, params)
     net = pfc.GuessNet(shape)
-    feats: List = []
-    targets: List = []
     raw: List[Tuple] = []
     t0 = time.perf_counter()
     for tr in range(n_traj):
@@ -47,7 +47,14 @@ def generate(n_traj: int, steps: int, shape=(512, 512), seed0: int = 2000, s_out
         dts = []
         for _ in range(steps):
             dt = solver.next_dt()
-            solver.step(dt)
+            for cut in range(4):  # a failed step leaves phi^n as it was: retry with dt / 2
+                try:
+                    solver.step(dt)
+                    break
+                except pfc.PfcError:
+                    if cut == 3:
+                        raise
+                    dt *= 0.5
             dts.append(dt)
             hist.append(solver.get_field_device())
         for k in range(1, steps):  # sample: phi^{k-1}, phi^k -> phi^{k+1}, dt_k, dt_{k-1}
@@ -58,14 +65,27 @@ def generate(n_traj: int, steps: int, shape=(512, 512), seed0: int = 2000, s_out
             e = (c - b - r * (b - a)).cpu().numpy()
             errs.append(float(np.sqrt(np.mean(e * e))))
         s_out = float(np.mean(errs)) or 1e-3
-    for a, b, c, r, c2 in raw:
-        f = torch.empty((3,) + tuple(shape), dtype=torch.float64, device="cuda")
-        t = torch.empty(tuple(shape), dtype=torch.float64, device="cuda")
-        net.sample(a, b, c, r, c2, s_out, f, t)
-        feats.append(f)
-        targets.append(t)
-    return {"feat": feats, "target": targets, "s_out": s_out, "shape": tuple(shape), "gen_seconds":
-            time.perf_counter() - t0, "net": net}
+    solver.close()
+    return {"raw": raw, "s_out": s_out, "shape": tuple(shape), "gen_seconds": time.perf_counter() - t0, "net": net}
+
+
+class _Samples:
+    """Sample i of a generate() result, built on the device into two reused buffers."""
+
+    def __init__(self, data: Dict):
+        import torch
+
+        self.data = data
+        self.f = torch.empty((3,) + tuple(data["shape"]), dtype=torch.float64, device="cuda")
+        self.t = torch.empty(tuple(data["shape"]), dtype=torch.float64, device="cuda")
+
+    def __len__(self) -> int:
+        return len(self.data["raw"])
+
+    def __getitem__(self, i: int):
+        a, b, c, r, c2 = self.data["raw"][i]
+        self.data["net"].sample(a, b, c, r, c2, self.data["s_out"], self.f, self.t)
+        return self.f, self.t
 
 
 def _init_params(seed: int) -> np.ndarray:
@@ -94,7 +114,8 @@ def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
     net: pfc.GuessNet = data["net"]
     net.set_params(theta0 if theta0 is not None else _init_params(seed))
     rng = np.random.default_rng(seed)
-    n = len(data["feat"]) - holdout
+    samples = _Samples(data)
+    n = len(samples) - holdout
     total = epochs * n
     t = 0
     history = []
@@ -104,17 +125,17 @@ def train_net(data: Dict, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
         for i in order:
             t += 1
             a = lr if lr_min is None else lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * (t - 1) / total))
-            tot += net.train_step(data["feat"][i], data["target"][i], a, t)
+            tot += net.train_step(*samples[i], a, t)
         rec = {"train": tot / max(n, 1)}
         if holdout:
-            rec["holdout"] = sum(net.loss_grad(data["feat"][i], data["target"][i])[0]
-                                 for i in range(n, n + holdout)) / holdout
+            rec["holdout"] = sum(net.loss_grad(*samples[i])[0] for i in range(n, n + holdout)) / holdout
         history.append(rec)
     return net.get_params(), history
 
 
-# The committed network: trajectories of the 1024^2 workload's distribution
-# (three hexagonal seeds, gamma 0.25, adaptive dt) on 512^2 grids.
+# The committed network: trajectories of the 1024^2 workload's distribution (three hexagonal
+# seeds, gamma 0.25, adaptive dt) on 512^2 grids, their first 25 steps (the growth stage the
+# 1024^2 workload's timed steps are in).
 DEFAULT_RECIPE = dict(n_traj=96, steps=25, size=512, epochs=20, lr=3e-4, lr_min=3e-5, seed=0, seed0=2000)
 WEIGHTS = "guess_net.npz"
 
@@ -129,8 +150,8 @@ def train_default(out_path: str, **over) -> Dict:
     hold = rc["steps"] - 1  # the last trajectory's samples
     theta, hist = train_net(data, epochs=rc["epochs"], lr=rc["lr"], lr_min=rc["lr_min"], seed=rc["seed"],
                             holdout=hold)
-    info = {"recipe": rc, "s_out": data["s_out"], "history": hist, "samples": len(data["feat"]) - hold,
-            "seconds": time.perf_counter() - t0}
+    info = {"recipe": rc, "s_out": data["s_out"], "history": hist, "samples": len(data["raw"]) - hold,
+            "gen_seconds": data["gen_seconds"], "seconds": time.perf_counter() - t0}
     np.savez(out_path, theta=theta.astype(np.float32), s_out=np.array([data["s_out"]]),
              info=np.array(json.dumps(info)))
     data["net"].close()
