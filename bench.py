@@ -549,7 +549,8 @@ def precond_sweep(args):
 
 def kernel_loop(args):
     """Runs one kernel family `steps` times on the workload's initial field
-    (each pfc_precond_apply factors and applies once), for ncu captures."""
+    (each pfc_precond_apply factors and applies once; cnn: the guess network's
+    forward pass), for ncu captures."""
     import torch
 
     from paper_1703_01202_gb300 import build, inputs, pfc
@@ -568,10 +569,19 @@ def kernel_loop(args):
     s = pfc.Solver(w["shape"], w["h"], w["gamma"], params)
     phi = torch.from_numpy(w["phi"]).cuda()
     r = torch.from_numpy(inputs.noise_field(w["shape"], 0.0, 1.0, 7)).cuda()
+    net = None
+    if args.kernel_loop == "cnn":  # the committed guess network's forward pass on the workload's features
+        from paper_1703_01202_gb300 import learned
+
+        net = pfc.GuessNet(w["shape"])
+        net.set_params(learned.load()[0])
+        feat = torch.stack([phi - phi.mean(), 0.01 * r, torch.full_like(phi, 1.0)])
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        if args.kernel_loop == "apply":
+        if net is not None:
+            net.forward(feat)
+        elif args.kernel_loop == "apply":
             s.precond_apply(phi, phi, 10.0, r)
         elif args.kernel_loop == "jvp":
             s.jvp(phi, phi, r, 10.0)
@@ -611,7 +621,7 @@ def main():
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="AS / left-RAS / right-RAS x overlap 0-3 on the workload (no bench line)")
-    ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual"],
+    ap.add_argument("--kernel-loop", default=None, choices=["apply", "jvp", "residual", "cnn"],
                     help="profiling aid: run one kernel family repeatedly on a workload (no bench line)")
     ap.add_argument("--kernel-workload", default=WORKLOAD)
     ap.add_argument("--kernel-grid", type=int, default=0, help="--kernel-loop: cells per axis instead of the workload's")

@@ -211,17 +211,45 @@ __global__ void __launch_bounds__(NT) k_conv32_fwd_tc(int nx, int ny, const __nv
   }
   const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
   const long long N = (long long)nx * ny;
-  for (int i = tid; i < 32 * TH * TH; i += NT) {  // input planes -> [g][row][col][8]
-    const int c = i / (TH * TH), r = i - c * TH * TH;
-    const int ly = r / TH, lx = r - ly * TH;
-    const long long p = wrapi(x0 + lx - 1, nx) + (long long)nx * wrapi(y0 + ly - 1, ny);
-    s_in[((c >> 3) * TH * TH + r) * 8 + (c & 7)] = in[c * N + p];
+  // Input planes -> [g][row][col][8]: one 16-byte row of the layout (8 channels of a pixel) per
+  // item, gathered from the 8 planes (consecutive threads take consecutive pixels).
+  // All of a thread's loads are issued before its stores (the item loops are unrolled), so the
+  // gathers of a tile are in flight together.
+  const bool inner = x0 >= 1 && y0 >= 1 && x0 + T + 1 <= nx && y0 + T + 1 <= ny;  // no periodic wrap
+  constexpr int kInItems = 4 * TH * TH, kInPer = (kInItems + NT - 1) / NT;
+  constexpr int kWItems = 9 * 4 * 32, kWPer = (kWItems + NT - 1) / NT;
+  uint4 vin[kInPer], vw[kWPer];
+#pragma unroll
+  for (int u = 0; u < kInPer; ++u) {
+    const int it = tid + u * NT;
+    if (it < kInItems) {
+      const int g = it / (TH * TH), r = it - g * (TH * TH);
+      const int ly = r / TH, lx = r - ly * TH;
+      const int gx = inner ? x0 + lx - 1 : wrapi(x0 + lx - 1, nx), gy = inner ? y0 + ly - 1 : wrapi(y0 + ly - 1, ny);
+      const __nv_bfloat16* src = in + (long long)(8 * g) * N + gx + (long long)nx * gy;
+      __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(&vin[u]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) e[k] = src[k * N];
+    }
   }
-  for (int i = tid; i < 32 * 32 * 9; i += NT) {  // W[co][ci][tap] -> [tap][ci / 8][co][ci % 8]
-    const int co = i / (32 * 9), r = i - co * 32 * 9;
-    const int ci = r / 9, tap = r - ci * 9;
-    s_w[((tap * 4 + (ci >> 3)) * 32 + co) * 8 + (ci & 7)] = W[i];
+  // W[co][ci][tap] -> [tap][ci / 8][co][ci % 8], one 16-byte row (8 input channels) per item.
+#pragma unroll
+  for (int u = 0; u < kWPer; ++u) {
+    const int it = tid + u * NT;
+    if (it < kWItems) {
+      const int tap = it >> 7, g = (it >> 5) & 3, co = it & 31;
+      const __nv_bfloat16* src = W + co * 288 + (8 * g) * 9 + tap;
+      __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(&vw[u]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) e[k] = src[9 * k];
+    }
   }
+#pragma unroll
+  for (int u = 0; u < kInPer; ++u)
+    if (tid + u * NT < kInItems) reinterpret_cast<uint4*>(s_in)[tid + u * NT] = vin[u];
+#pragma unroll
+  for (int u = 0; u < kWPer; ++u)
+    if (tid + u * NT < kWItems) reinterpret_cast<uint4*>(s_w)[tid + u * NT] = vw[u];
   if (tid < 32) s_b[tid] = b[tid];
   fence_proxy_async();  // the operands are read by the tensor cores (async proxy)
   tc_fence_before();
@@ -271,7 +299,16 @@ __global__ void __launch_bounds__(NT) k_conv32_fwd_tc(int nx, int ny, const __nv
     if (tid == 0 && err) atomicExch(err, PFC_ETIMEOUT);
     return;
   }
-  for (int i = tid; i < 32 * NT; i += NT) {  // coalesced 16-pixel rows of every plane
+  if (x0 + T <= nx && y0 + T <= ny && (nx & 7) == 0) {  // whole tile, 16-byte aligned rows: 8 pixels a store
+    for (int i = tid; i < 32 * NT / 8; i += NT) {
+      const int co = i >> 5, ty = (i >> 1) & 15, h = i & 1;
+      const long long p = co * N + x0 + 8 * h + (long long)nx * (y0 + ty);
+      reinterpret_cast<uint4*>(z + p)[0] = reinterpret_cast<const uint4*>(s_z)[i];
+      reinterpret_cast<uint4*>(a + p)[0] = reinterpret_cast<const uint4*>(s_a)[i];
+    }
+    return;
+  }
+  for (int i = tid; i < 32 * NT; i += NT) {  // ragged tile: 16-pixel rows of every plane
     const int co = i / NT, r = i - co * NT;
     const int ty = r / T, tx = r - ty * T;
     const int gx = x0 + tx, gy = y0 + ty;
