@@ -260,6 +260,11 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 
 # ---------------------------------------------------------------- solvers
 EXTRAS = ("hex2048", "bcc256", "batch32x256", "forms")  # the workloads after the 1024^2 line
+# The stopping tolerances of the paper's experiments (Sec. 5: eps_r = 1e-8, eps_a = 1e-10 for Newton,
+# xi_r = 1e-3, xi_a = 1e-11 for GMRES).  The other forms use the tighter 1e-10 / 1e-6 of the 64^2
+# workload, under which the oracle trajectories were written; these two forms report the same
+# workload at the paper's own settings.
+PAPER_TOL = {"newton_rtol": 1e-8, "newton_atol": 1e-10, "gmres_rtol": 1e-3, "gmres_atol": 1e-11}
 USE_GRAPH = [1]  # pfc_params.use_graph of every solver (--no-graph for ncu runs)
 APPLY_VARIANT = [-1]  # pfc_params.apply_variant of every solver (-1: autotuned; pinned for ncu runs)
 
@@ -497,11 +502,10 @@ def versus_f64(variants: dict) -> None:
     up to the controller's rounding), for every form of a grid that has a plain FP64 run."""
     import numpy as np
 
-    ref = variants.get("f64", {}).get("phi_after")
-    if ref is None:
-        return
-    for k, v in variants.items():
-        if k != "f64" and v.get("phi_after") is not None:
+    for k, v in variants.items():  # the paper-tolerance forms against the FP64 run at the same tolerances
+        base = "f64_paper_tol" if k.endswith("_paper_tol") else "f64"
+        ref = variants.get(base, {}).get("phi_after")
+        if k != base and ref is not None and v.get("phi_after") is not None:
             v["max_abs_phi_vs_f64_gpu"] = float(np.abs(v["phi_after"] - ref).max())
 
 
@@ -609,7 +613,7 @@ def main():
                     help="steps after the timed region with per-kernel CUDA events (rooflines)")
     ap.add_argument("--variant", default="all",
                     choices=["all", "f64", "f32", "bf16", "bf16_learned", "bf16_learned_fastdots",
-                             "bf16_learned_jvp32"],
+                             "bf16_learned_jvp32", "f64_paper_tol", "bf16_learned_paper_tol"],
                     help="run one form only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 2048^2, 256^3, ensemble and other-form workloads")
@@ -657,14 +661,18 @@ def main():
     # (name, factor precision, learned guess, opt-in forms)
     forms = (("f64", 0, False, {}), ("f32", 1, False, {}), ("bf16", 2, False, {}), ("bf16_learned", 2, True, {}),
              ("bf16_learned_fastdots", 2, True, {"gmres_fast_dots": 1}),
-             ("bf16_learned_jvp32", 2, True, {"jvp_fp32": 1}))
+             ("bf16_learned_jvp32", 2, True, {"jvp_fp32": 1}),
+             ("f64_paper_tol", 0, False, PAPER_TOL), ("bf16_learned_paper_tol", 2, True, PAPER_TOL))
     variants = {}
     for name, prec, lg, extra in forms:
         if args.variant in ("all", name):
+            paper = name.endswith("_paper_tol")  # the oracle trajectory was written at the tighter tolerances
             variants[name] = run_variant(WORKLOAD, prec, args.steps, args.warmup, world, local, learned=lg,
-                                         profile_steps=args.profile_steps,
-                                         e2e=(name == "bf16_learned" or args.variant == name), golden=golden,
-                                         hbm=hbm, **extra)
+                                         profile_steps=0 if paper and args.variant == "all" else args.profile_steps,
+                                         e2e=(name == "bf16_learned" or args.variant == name),
+                                         golden=None if paper else golden, hbm=hbm, **extra)
+            if paper:
+                variants[name]["tolerances"] = dict(PAPER_TOL)
     versus_f64(variants)
     head_name = "bf16_learned" if "bf16_learned" in variants else args.variant
     head = variants[head_name]
