@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
                                                  double idt, double* __restrict__ Jv, const int* __restrict__ skip,
                                                  const IterArgs* __restrict__ ia, const __grid_constant__ JvpMaps maps,
                                                  int zj, int* __restrict__ err, int pout) {
+  pdl_wait();
   if (skip && *skip) return;
   if (ia) {  // graph mode: J Z_j into V_(j+1)
     v = ia->z;
@@ -188,7 +189,7 @@ void launch_jvp2d_ff(const Geo& g, const double* v, const double* vscale, const 
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
   JvpMaps m{};
   if (maps) m = *maps;
-  k_jvp2d_ff<<<grid, dim3(32, 8), 0, st>>>(g, v, vscale, q, idt, Jv, skip, ia, m, zj, err, pout);
+  launch_pdl(k_jvp2d_ff, grid, dim3(32, 8), 0, st, g, v, vscale, q, idt, Jv, skip, ia, m, zj, err, pout);
   count_launches(1);
 }
 
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
                                                    const IterArgs* __restrict__ ia,
                                                    const __grid_constant__ JvpMaps maps, int zj,
                                                    int* __restrict__ err, int pout) {
+  pdl_wait();
   if (skip && *skip) return;
   if (ia) {  // graph mode: J Z_j into V_(j+1)
     v = ia->z;
@@ -289,7 +291,7 @@ void launch_jvp2d_f32(const Geo& g, const double* v, const double* q, double idt
   dim3 grid((g.nx + FTX - 1) / FTX, (g.ny + FTY - 1) / FTY);
   JvpMaps m{};
   if (maps) m = *maps;
-  k_jvp2d_f32<<<grid, dim3(32, 8), 0, st>>>(g, v, q, idt, Jv, skip, ia, m, zj, err, pout);
+  launch_pdl(k_jvp2d_f32, grid, dim3(32, 8), 0, st, g, v, q, idt, Jv, skip, ia, m, zj, err, pout);
   count_launches(1);
 }
 

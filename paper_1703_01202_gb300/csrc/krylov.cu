@@ -290,6 +290,7 @@ template <int D, bool PR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multidot(const double* v0, const double* const* __restrict__ tab, int nv, const double* w, long long n,
                double* __restrict__ partial, const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
+  pdl_wait();
   if (sweep_skipped(skip, only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nv = tail.ia->j + 2;
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
     if ((lane & 3) == 0) red[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = acc[0];
   }
+  pdl_trigger();
   __syncthreads();  // also keeps the CTA alive until the producer has drained its copies
   if (tid < cnt) {
     double s = 0.0;
@@ -420,6 +422,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
     k_multiaxpy(double* __restrict__ w, const double* x0, const double* const* __restrict__ tab, int nx,
                 const double* __restrict__ coef, double sign, long long n, double* __restrict__ partial,
                 const int* __restrict__ skip, const int* __restrict__ only_if, Tail tail) {
+  pdl_wait();
   if (sweep_skipped(skip, only_if)) return;
   if (tail.ia) {  // graph mode: this iteration's vector count and w
     nx = tail.ia->j + 1;
@@ -510,6 +513,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinCtas)
       red[1][wid] = s1;
     }
   }
+  pdl_trigger();
   __syncthreads();  // also keeps the CTA alive until the producer has drained its copies
   if (tid < (SUM ? 2 : 1)) {
     double s = 0.0;
@@ -572,6 +576,7 @@ __global__ void k_extrapolate(double* __restrict__ out, const double* __restrict
 __global__ void k_arnoldi_next(const GmresCtl* __restrict__ ctl, const double* const* __restrict__ vtab,
                                const double* const* __restrict__ ztab, IterArgs* __restrict__ ia, int m,
                                cudaGraphConditionalHandle h) {
+  pdl_wait();
   const int j = ctl->its;
   const bool go = !ctl->done && j < m;
   if (go) {
@@ -606,7 +611,8 @@ void launch_multidot(const double* v0, const double* const* tab, int nv, const d
 #define PFC_DOT(D, PR)                                                                                    \
   do {                                                                                                    \
     cudaFuncSetAttribute(k_multidot<D, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-    k_multidot<D, PR><<<grid, kSweepThreads, smem, st>>>(v0, tab, nv, w, n, partial, skip, only_if, tail); \
+    launch_pdl(k_multidot<D, PR>, grid, dim3(kSweepThreads), smem, st, v0, tab, nv, w, n, partial, skip, only_if, \
+               tail);                                                                                       \
   } while (0)
   if (dot == kDotFF && pairs)
     PFC_DOT(kFF, true);
@@ -633,8 +639,8 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
 #define PFC_AXPY(S, F, PR)                                                                              \
   do {                                                                                                  \
     cudaFuncSetAttribute(k_multiaxpy<S, F, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_multiaxpy<S, F, PR><<<bx, kSweepThreads, smem, st>>>(w, x0, tab, nx, coef, sign, n, partial, skip, only_if, \
-                                                           tail);                                      \
+    launch_pdl(k_multiaxpy<S, F, PR>, dim3(bx), dim3(kSweepThreads), smem, st, w, x0, tab, nx, coef, sign, n,   \
+               partial, skip, only_if, tail);                                                           \
   } while (0)
   if (pairs && sum) {  // float-pair vectors come with no sum of w (the Gram-Schmidt sweeps)
     fprintf(stderr, "libpfc: float-pair multi-axpy with the sum of w\n");
@@ -656,7 +662,7 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
 
 void launch_arnoldi_next(const GmresCtl* ctl, const double* const* vtab, const double* const* ztab, IterArgs* ia,
                          int m, cudaGraphConditionalHandle h, cudaStream_t st) {
-  k_arnoldi_next<<<1, 1, 0, st>>>(ctl, vtab, ztab, ia, m, h);
+  launch_pdl(k_arnoldi_next, dim3(1), dim3(1), 0, st, ctl, vtab, ztab, ia, m, h);
   count_launches(1);
 }
 

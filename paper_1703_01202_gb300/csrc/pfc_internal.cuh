@@ -14,6 +14,30 @@ constexpr int kMaxRestart = 60;   // GMRES restart length limit
 constexpr int kMaxVecs = kMaxRestart + 2;
 constexpr int kRedCtas = 4 * 152;  // CTAs of the grid-stride reduction kernels
 
+// Programmatic dependent launch between the kernels of an Arnoldi iteration: a kernel launched
+// with launch_pdl may be scheduled while the kernel before it on the stream drains; it calls
+// pdl_wait() before reading anything (every earlier kernel has then completed and its writes are
+// visible).  A kernel calls pdl_trigger() once its main work is done, so that the next one can be
+// scheduled during its tail (the last CTA's reduction).  Both are no-ops for kernels launched
+// without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Geometry of the grid (x fastest; periodic or between mirror walls) and the scheme's constants.
 struct Geo {
   int nx, ny, nz;

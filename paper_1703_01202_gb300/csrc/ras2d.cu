@@ -1059,6 +1059,7 @@ __global__ void __launch_bounds__(32 * WPC)
     for (int t = lane; t < n; t += 32) fs.Yb[(size_t)b * fs.n_max + t] = sc * (double)y[t];
     return;
   }
+  pdl_trigger();  // the solves are done: the next kernel (the JVP) may be scheduled
   int a = a0, c = c0;
   for (int t = lane; t < n; t += 32) {  // extension (R_k^0)^T: core points only
     if (a >= B.ox && a < B.ox + B.cx && c >= B.oy && c < B.oy + B.cy)
