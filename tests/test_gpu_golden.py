@@ -100,16 +100,18 @@ def test_hex1024_ten_steps_match_oracle(env, prec, learned_guess, form):
         net.close()
 
 
-@pytest.mark.parametrize("prec,learned_guess", [(0, False), (1, False), (2, False), (2, True)])
-def test_hex2048_three_steps_match_oracle(env, prec, learned_guess):
-    """The 2048^2 precision workload (128 x 128 cores, 16,384 blocks), its first 3 steps."""
+@pytest.mark.parametrize("prec,learned_guess,form", [(0, False, {}), (1, False, {}), (2, False, {}), (2, True, {}),
+                                                     (2, True, {"jvp_fp32": 1})])
+def test_hex2048_three_steps_match_oracle(env, prec, learned_guess, form):
+    """The 2048^2 precision workload (128 x 128 cores, 16,384 blocks), its first 3 steps; also the
+    bench's headline form (FP32 JVP)."""
     P, torch, learned = env
     rec = G.load("hex2048_s3")
-    s, net, w = _solver(P, torch, learned, "hex2048", prec, learned_guess)
+    s, net, w = _solver(P, torch, learned, "hex2048", prec, learned_guess, **form)
     s.set_field(w["phi"])
     infos = s.run(rec["meta"]["steps"])
     err, rel_e = check_against(rec, infos, s.get_field(), TOL["f64" if prec == 0 and not learned_guess else "mixed"])
-    print(f"hex2048 prec {prec} learned {learned_guess}: max|dphi| {err:.2e}, energy {rel_e:.2e}")
+    print(f"hex2048 prec {prec} learned {learned_guess} {form}: max|dphi| {err:.2e}, energy {rel_e:.2e}")
     s.close()
     if net is not None:
         net.close()
