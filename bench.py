@@ -741,9 +741,10 @@ def main():
             work["hex2048"] = {k: strip(v) for k, v in grid2048.items()}
         if "bcc256" in extras:
             bcc = {}
-            for name, prec in (("f64", 0), ("f32", 1), ("bf16", 2)):
+            for name, prec, form in (("f64", 0, {}), ("f32", 1, {}), ("bf16", 2, {}),
+                                     ("bf16_jvp32", 2, {"jvp_fp32": 1})):
                 bcc[name] = guarded(run_variant, "bcc256", prec, 5, 1, world, local, profile_steps=1,
-                                    golden=None if args.no_golden else "bcc64_s50", hbm=hbm)
+                                    golden=None if args.no_golden else "bcc64_s50", hbm=hbm, **form)
                 if isinstance(bcc[name], dict) and "errors_vs_oracle" in bcc[name]:
                     bcc[name]["errors_vs_oracle"]["grid"] = "64^3 (the oracle trajectory's grid)"
             work["bcc256"] = {k: strip(v) for k, v in bcc.items()}

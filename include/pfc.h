@@ -157,10 +157,10 @@ typedef struct {
      re-orthogonalisation pass then carries more of the orthogonality).  The
      plain path (F64 factors) always uses FP64 sweeps. */
   int gmres_fast_dots;
-  /* JVP of the mixed path (F32/BF16 factors, M = 1, 2D): 0 (default) float-float
-     on the FP32 pipe (about 2^-46 relative, so GMRES sees the FP64 operator);
-     1: plain FP32 (v and q cut to floats; much cheaper, about 2^-24 of the
-     largest stencil terms per point).  The Newton residual stays FP64, so the
+  /* JVP of the mixed path (F32/BF16 factors, M = 1, 2D and 3D): 0 (default)
+     float-float on the FP32 pipe (about 2^-46 relative, so GMRES sees the FP64
+     operator); 1: plain FP32 (v and q cut to floats; much cheaper, about 2^-24 of
+     the largest stencil terms per point).  The Newton residual stays FP64, so the
      converged phi^{n+1} meets the same tolerance either way; the iteration
      counts tell whether the cheaper operator pays.  The plain path (F64
      factors) and variable mobility always use the FP64 JVP. */

@@ -113,13 +113,20 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
       sQ[ly][lx] = ff_split(q[sq.idx(g, lx, ly)]);
     }
   }
+  __shared__ ff s_k[4];  // the scheme's constants, split once per CTA
+  if (tid == 0) {
+    s_k[0] = ff_split(g.ih2);
+    s_k[1] = ff_split(g.hih4);
+    s_k[2] = ff_split(g.c0);
+    s_k[3] = ff_split(idt);
+  }
   __syncthreads();
   for (int i = tid; i < (AX - 2) * (AY - 2); i += NT) {
     const int ly = i / (AX - 2) + 1, lx = i - (ly - 1) * (AX - 2) + 1;
     sL[ly - 1][lx - 1] = ff_lap5(sV[ly][lx], sV[ly][lx + 1], sV[ly][lx - 1], sV[ly + 1][lx], sV[ly - 1][lx]);
   }
   __syncthreads();
-  const ff ih2 = ff_split(g.ih2), hih4 = ff_split(0.5 * g.ih2 * g.ih2), c0 = ff_split(0.5 * (1.0 - g.gamma));
+  const ff ih2 = s_k[0], hih4 = s_k[1], c0 = s_k[2];
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4) + 2, lx = i - (ly - 2) * (AX - 4) + 2;
     const int a = ly - 1, b = lx - 1;
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d_ff(Geo g, const double* __restrict
     sW[ly - 2][lx - 2] = ff_dot4(c0, vv, ih2, Lv, hih4, LLv, sQ[ly - 2][lx - 2], vv);
   }
   __syncthreads();
-  const ff fidt = ff_split(idt);
+  const ff fidt = s_k[3];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int tx = threadIdx.x, ty = threadIdx.y + 8 * r;
@@ -251,13 +258,20 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
       sQ[ly][lx] = f32_cut(q[sq.idx(g, lx, ly)]);
     }
   }
+  __shared__ float s_k[4];  // the scheme's constants, cut to floats once per CTA
+  if (tid == 0) {
+    s_k[0] = f32_cut(g.ih2);
+    s_k[1] = f32_cut(g.hih4);
+    s_k[2] = f32_cut(g.c0);
+    s_k[3] = f32_cut(idt);
+  }
   __syncthreads();
   for (int i = tid; i < (FAX - 2) * (FAY - 2); i += 256) {
     const int ly = i / (FAX - 2) + 1, lx = i - (ly - 1) * (FAX - 2) + 1;
     sL[ly - 1][lx - 1] = (sV[ly][lx + 1] + sV[ly][lx - 1]) + (sV[ly + 1][lx] + sV[ly - 1][lx]) - 4.0f * sV[ly][lx];
   }
   __syncthreads();
-  const float ih2 = f32_cut(g.ih2), hih4 = f32_cut(0.5 * g.ih2 * g.ih2), c0 = f32_cut(0.5 * (1.0 - g.gamma));
+  const float ih2 = s_k[0], hih4 = s_k[1], c0 = s_k[2];
   for (int i = tid; i < (FAX - 4) * (FAY - 4); i += 256) {
     const int ly = i / (FAX - 4) + 2, lx = i - (ly - 2) * (FAX - 4) + 2;
     const int a = ly - 1, b = lx - 1;
@@ -267,7 +281,7 @@ __global__ void __launch_bounds__(256) k_jvp2d_f32(Geo g, const double* __restri
     sW[ly - 2][lx - 2] = fmaf(c0 + sQ[ly - 2][lx - 2], vv, fmaf(ih2, Lv, hih4 * LLv));  // w = (c0 + q) v + ih2 Lv + ih4/2 LLv
   }
   __syncthreads();
-  const float fidt = f32_cut(idt);
+  const float fidt = s_k[3];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int tx = threadIdx.x, ty = threadIdx.y + 8 * r;

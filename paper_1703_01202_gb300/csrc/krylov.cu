@@ -551,13 +551,21 @@ __global__ void k_gmres_init(GmresCtl* c, const double* __restrict__ nrm2, doubl
 }
 
 // y = R^{-1} g over the completed iterations (R = rotated Hessenberg).
-__global__ void k_gmres_solve(GmresCtl* c) {
+// Back substitution R y = g of the rotated Hessenberg system (k <= kMaxRestart = 60 rows), by
+// one warp, column by column: lane l keeps rows l and l + 32 of g and subtracts H(i, j) y_j from
+// them as each y_j becomes final (FP64).
+__global__ void __launch_bounds__(32) k_gmres_solve(GmresCtl* c) {
+  static_assert(kMaxRestart <= 64, "two rows per lane");
   const int m1 = kMaxRestart + 1;
   const int k = c->its;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = c->g[i];
-    for (int l = i + 1; l < k; ++l) s -= c->H[i + m1 * l] * c->y[l];
-    c->y[i] = s / c->H[i + m1 * i];
+  const int lane = threadIdx.x;
+  double g0 = lane < k ? c->g[lane] : 0.0, g1 = lane + 32 < k ? c->g[lane + 32] : 0.0;
+  for (int j = k - 1; j >= 0; --j) {
+    const double gj = __shfl_sync(0xffffffffu, j < 32 ? g0 : g1, j & 31);
+    const double yj = gj / c->H[j + m1 * j];
+    if (lane == (j & 31)) c->y[j] = yj;
+    if (lane < j) g0 = fma(-c->H[lane + m1 * j], yj, g0);
+    if (lane + 32 < j) g1 = fma(-c->H[lane + 32 + m1 * j], yj, g1);
   }
 }
 
@@ -677,7 +685,7 @@ void launch_gmres_init(GmresCtl* ctl, const double* nrm2, double sign, double to
   count_launches(1);
 }
 void launch_gmres_solve(GmresCtl* ctl, cudaStream_t st) {
-  k_gmres_solve<<<1, 1, 0, st>>>(ctl);
+  k_gmres_solve<<<1, 32, 0, st>>>(ctl);
   count_launches(1);
 }
 

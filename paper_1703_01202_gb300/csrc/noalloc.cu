@@ -55,6 +55,7 @@ extern "C" int pfc_residual_static(const pfc_grid* grid, double h, double eps, c
   g.ih2 = 1.0 / (h * h);
   g.gamma = eps;
   g.hd = h * h;
+  pfc::geo_constants(&g);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int np = 0;
   // every tile writes its own partial and the reduction overwrites the total, so

@@ -663,6 +663,8 @@ void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out
                          pout);
   else if (s->dim == 2)
     pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia);
+  else if (s->fs.prec != PFC_F64 && s->p.jvp_fp32)  // 3D mixed path, opt-in: plain FP32 passes
+    pfc::launch_jvp3d_f32(s->g, v, q, idt, out, s->T1, s->T2, skip, s->st, pout);
   else if (s->fs.prec != PFC_F64)  // 3D mixed path: float-float passes on the FP32 pipe
     pfc::launch_jvp3d_ff(s->g, v, q, idt, out, s->T1, s->T2, skip, s->st, pout);
   else
@@ -1549,6 +1551,7 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   s->g.gamma = eps;
   s->g.hd = g->dim == 3 ? h * h * h : h * h;
   s->g.neumann = p->boundary == PFC_NEUMANN ? 1 : 0;
+  pfc::geo_constants(&s->g);
   char* base = (char*)ws;
   auto at = [&](size_t off) { return (void*)(base + off); };
   s->phin = (double*)at(pl.phin);

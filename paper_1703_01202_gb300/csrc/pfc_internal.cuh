@@ -46,7 +46,16 @@ struct Geo {
   double gamma;     // quench depth of Eq. (GE)
   double hd;        // h^d (cell volume)
   int neumann;      // 0: periodic grid; 1: mirror walls half a cell outside the end cells (Sec. 2)
+  // derived on the host by geo_constants (kernels read them instead of computing them per thread)
+  double ih4;       // ih2 * ih2
+  double hih4;      // 0.5 * ih2 * ih2
+  double c0;        // 0.5 * (1 - gamma)
 };
+inline void geo_constants(Geo* g) {
+  g->ih4 = g->ih2 * g->ih2;
+  g->hih4 = 0.5 * g->ih2 * g->ih2;
+  g->c0 = 0.5 * (1.0 - g->gamma);
+}
 
 // Cell that index i (any integer) of an axis of n cells reads: the periodic image, or, between
 // mirror walls, the image in the evenly extended grid of period 2n (ghost -1 -> 0, n -> n - 1).
@@ -298,6 +307,9 @@ void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const dou
 // The same product in float-float arithmetic (the mixed path); T1, T2 hold float pairs.
 void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
                      const int* skip, cudaStream_t st, int pout = 0);  // pout: Jv as float pairs
+// The same product in plain FP32 (opt-in on the mixed path, pfc_params.jvp_fp32); T1, T2 hold floats.
+void launch_jvp3d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
+                      const int* skip, cudaStream_t st, int pout = 0);
 void launch_energy3d(const Geo& g, const double* phi, double* partial, int* nparts, cudaStream_t st);
 
 // ---- 3D Schwarz preconditioner with shifted ILU(0) subdomain solves (ras3d.cu)

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NT) k_residual2d(Geo g, const double* __restri
     sL[ly - 1][lx - 1] = (sS[ly][lx - 1] + sS[ly][lx + 1]) + (sS[ly - 1][lx] + sS[ly + 1][lx]) - 4.0 * sS[ly][lx];
   }
   __syncthreads();
-  const double ih2 = g.ih2, ih4 = g.ih2 * g.ih2, c0 = 0.5 * (1.0 - g.gamma);
+  const double ih2 = g.ih2, ih4 = g.ih4, c0 = g.c0;
   // mu on the halo-1 region
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4) + 2, lx = i - (ly - 2) * (AX - 4) + 2;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ 
     sL[ly - 1][lx - 1] = (sV[ly][lx - 1] + sV[ly][lx + 1]) + (sV[ly - 1][lx] + sV[ly + 1][lx]) - 4.0 * sV[ly][lx];
   }
   __syncthreads();
-  const double ih2 = g.ih2, ih4 = g.ih2 * g.ih2, c0 = 0.5 * (1.0 - g.gamma);
+  const double ih2 = g.ih2, ih4 = g.ih4, c0 = g.c0;
   for (int i = tid; i < (AX - 4) * (AY - 4); i += NT) {
     const int ly = i / (AX - 4) + 2, lx = i - (ly - 2) * (AX - 4) + 2;
     const int a = ly - 1, b = lx - 1;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(NT) k_jvp2d(Geo g, const double* __restrict__ 
 __global__ void __launch_bounds__(256) k_energy2d(Geo g, const double* __restrict__ phi,
                                                   double* __restrict__ partial) {
   __shared__ double red[8];
-  const double c0 = 0.5 * (1.0 - g.gamma), ih2 = g.ih2;
+  const double c0 = g.c0, ih2 = g.ih2;
   double e = 0.0, m = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx), y = (int)(i / g.nx);

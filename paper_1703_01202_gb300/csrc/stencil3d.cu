@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(NT) k_mid3d(Geo g, int mode, const double* __r
                                               const double* __restrict__ T1, double* __restrict__ out,
                                               const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const double ih2 = g.ih2, ih4 = g.ih2 * g.ih2, c0 = 0.5 * (1.0 - g.gamma);
+  const double ih2 = g.ih2, ih4 = g.ih4, c0 = g.c0;
   const double sc = vscale ? *vscale : 1.0;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
     int x, y, z;
@@ -138,7 +138,7 @@ __global__ void k_trial(long long n, const double* __restrict__ Pb, const double
 __global__ void __launch_bounds__(NT) k_energy3d(Geo g, const double* __restrict__ phi,
                                                  double* __restrict__ partial) {
   __shared__ double red[NT / 32];
-  const double c0 = 0.5 * (1.0 - g.gamma), ih2 = g.ih2;
+  const double c0 = g.c0, ih2 = g.ih2;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   double e = 0.0, m = 0.0;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(FX* FY) k_mid3d_ff(Geo g, const double* __rest
   const ff LL = ff_lap7(L1, ldff(T1, o.xp), ldff(T1, o.xm), ldff(T1, o.yp), ldff(T1, o.ym), ldff(T1, o.zp),
                         ldff(T1, o.zm));
   const ff vv = ff_split(v[o.c]);
-  const ff ih2 = ff_split(g.ih2), hih4 = ff_split(0.5 * g.ih2 * g.ih2), c0 = ff_split(0.5 * (1.0 - g.gamma));
+  const ff ih2 = ff_split(g.ih2), hih4 = ff_split(g.hih4), c0 = ff_split(g.c0);
   const ff w = ff_dot4(c0, vv, ih2, L1, hih4, LL, ff_split(q[o.c]), vv);
   T2[o.c] = make_float2(w.hi, w.lo);
 }
@@ -292,7 +292,73 @@ __global__ void __launch_bounds__(FX* FY) k_jvp_out3d_ff(Geo g, const double* __
     Jv[o.c] = ff_to_double(jv);
 }
 
+// The same three passes in plain FP32 (opt-in on the mixed path, pfc_params.jvp_fp32): inputs cut
+// to floats, FP32 scratch fields, the 2D FP32 JVP's arithmetic with 7-point Laplacians.  The
+// scheme's constants are cut once per CTA.
+__device__ __forceinline__ float lap7f(float c, float xp, float xm, float yp, float ym, float zp, float zm) {
+  return ((xp + xm) + (yp + ym)) + (zp + zm) - 6.0f * c;
+}
+__device__ __forceinline__ void consts_f32(const Geo& g, double idt, float* k) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    k[0] = f32_cut(g.ih2);
+    k[1] = f32_cut(g.hih4);
+    k[2] = f32_cut(g.c0);
+    k[3] = f32_cut(idt);
+  }
+  __syncthreads();
+}
+// T1 = Lap v (unscaled)
+__global__ void __launch_bounds__(FX* FY) k_lap3d_f32(Geo g, const double* __restrict__ v, float* __restrict__ T1,
+                                                      const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  T1[o.c] = lap7f(f32_cut(v[o.c]), f32_cut(v[o.xp]), f32_cut(v[o.xm]), f32_cut(v[o.yp]), f32_cut(v[o.ym]),
+                  f32_cut(v[o.zp]), f32_cut(v[o.zm]));
+}
+// T2 = w = (c0 + q) v + ih2 T1 + ih4/2 Lap T1
+__global__ void __launch_bounds__(FX* FY) k_mid3d_f32(Geo g, const double* __restrict__ v,
+                                                      const double* __restrict__ q, const float* __restrict__ T1,
+                                                      float* __restrict__ T2, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float k[4];
+  consts_f32(g, 0.0, k);
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  const float L1 = T1[o.c];
+  const float LL = lap7f(L1, T1[o.xp], T1[o.xm], T1[o.yp], T1[o.ym], T1[o.zp], T1[o.zm]);
+  T2[o.c] = fmaf(k[2] + f32_cut(q[o.c]), f32_cut(v[o.c]), fmaf(k[0], L1, k[1] * LL));
+}
+// J v = v idt - ih2 Lap w
+__global__ void __launch_bounds__(FX* FY) k_jvp_out3d_f32(Geo g, const double* __restrict__ v,
+                                                          const float* __restrict__ T2, double idt,
+                                                          double* __restrict__ Jv, const int* __restrict__ skip,
+                                                          int pout) {
+  if (skip && *skip) return;
+  __shared__ float k[4];
+  consts_f32(g, idt, k);
+  Nb o;
+  if (!nb_of(g, &o)) return;
+  const float Lw = lap7f(T2[o.c], T2[o.xp], T2[o.xm], T2[o.yp], T2[o.ym], T2[o.zp], T2[o.zm]);
+  const float jv = fmaf(f32_cut(v[o.c]), k[3], -k[0] * Lw);
+  if (pout)
+    st_pair(Jv, o.c, ff{jv, 0.0f});
+  else
+    Jv[o.c] = f2d_bits(jv);
+}
+
 }  // namespace
+
+void launch_jvp3d_f32(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
+                      const int* skip, cudaStream_t st, int pout) {
+  const dim3 grid((g.nx + FX - 1) / FX, (g.ny + FY - 1) / FY, g.nz), blk(FX, FY);
+  float* t1 = reinterpret_cast<float*>(T1);
+  float* t2 = reinterpret_cast<float*>(T2);
+  k_lap3d_f32<<<grid, blk, 0, st>>>(g, v, t1, skip);
+  k_mid3d_f32<<<grid, blk, 0, st>>>(g, v, q, t1, t2, skip);
+  k_jvp_out3d_f32<<<grid, blk, 0, st>>>(g, v, t2, idt, Jv, skip, pout);
+  count_launches(3);
+}
 
 void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
                      const int* skip, cudaStream_t st, int pout) {

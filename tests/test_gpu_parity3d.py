@@ -130,6 +130,36 @@ def test_float_float_jvp_3d(pfc, shape, prec):
     np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 14, 18), (40, 37, 33)])
+def test_fp32_jvp_3d(pfc, shape):
+    """The opt-in FP32 3D JVP (jvp_fp32 = 1; inputs cut to floats, FP32 passes) against the oracle's
+    FP64 product: FP32 rounding of terms up to ih4 |v| in size, bounded at 1e-5 of the largest
+    entry (as the 2D FP32 JVP)."""
+    Phi = inputs.noise_field(shape, -0.3, 0.4, 31)
+    phin = inputs.noise_field(shape, -0.3, 0.4, 32)
+    v = inputs.noise_field(shape, 0.0, 1.0, 33)
+    s = solver3(pfc, shape, (2, 2, 2), prec=2, jvp_fp32=1)
+    Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+    ref = O.jvp(v, Phi, phin, 2.5, H3, GAMMA3)
+    np.testing.assert_allclose(Jv, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    assert np.abs(Jv - ref).max() > 1e-12 * np.abs(ref).max()  # it is the FP32 kernel, not the float-float one
+
+
+def test_steps_3d_fp32_jvp_match_oracle(pfc):
+    """Three fixed steps at dt = 0.5 on the 16^3 BCC-seeded field with BF16 factors and the FP32 JVP,
+    at the mixed tolerances."""
+    shape = (16, 16, 16)
+    phi0 = inputs.bcc_seeds_3d(shape, H3, nseeds=1, d0=4 * H3, seed=5)
+    s = solver3(pfc, shape, (2, 2, 2), prec=2, jvp_fp32=1)
+    s.set_field(phi0)
+    infos = [s.step(0.5) for _ in range(3)]
+    ref, recs = O.run(phi0, H3, GAMMA3, O.Params(parts=(2, 2, 2), overlap=1, subdomain_solver="ilu0"), 3,
+                      fixed_dt=0.5)
+    assert np.abs(s.get_field() - ref).max() <= 1e-7
+    for inf, rec in zip(infos, recs):
+        assert abs(inf["energy"] - rec.energy) <= 1e-9 * abs(rec.energy)
+
+
 @pytest.mark.parametrize("shape", [(16, 16, 16), (12, 14, 18)])
 def test_neumann_operators_3d(pfc, shape):
     """Mirror walls in 3D (Sec. 2): residual, FP64 and float-float JVP and energy against the
