@@ -400,6 +400,9 @@ __global__ void __launch_bounds__(kColRing) k_factor2d_col(Geo g, const BlockDes
   const int kl = min(3 * bx, n - 1);
   const int ku2 = min(2 * kl, n - 1);
   const int W = kl + 1;
+  // A row enters the slot its pivot row leaves, so only row slots 0 .. W - 1 ever hold rows: the
+  // column updates stop at W rounded up to whole 16-byte groups.
+  const int Wp = (W + 3) & ~3;
   const int lrow = fs.lrow, ucol = fs.ucol;
   const size_t cols = (size_t)kColRing * kColStride * sizeof(float);
   const size_t qtmp = (size_t)fs.n_max * sizeof(double);
@@ -499,9 +502,9 @@ __global__ void __launch_bounds__(kColRing) k_factor2d_col(Geo g, const BlockDes
     if (j <= ku2 && c < n) U[(size_t)c * ucol + j] = to_store_t<TS>(j == 0 ? s_dinv : u);
     if (j == 0)  // U column k's entries above the band stay zero for the bulk copies
       for (int jj = ku2 + 1; jj < ucol; ++jj) U[(size_t)k * ucol + jj] = to_store_t<TS>(0.0f);
-    if (j >= 1 && j <= ku2 && c < n) {  // rank-1 update of this column
+    if (j >= 1 && j <= ku2 && c < n) {  // rank-1 update of this column (row slots < W hold the rows)
 #pragma unroll 4
-      for (int r = 0; r < kColRows; r += 4) {
+      for (int r = 0; r < Wp; r += 4) {
         const float4 l4 = *reinterpret_cast<const float4*>(&lslot[r]);
         float4 a4 = *reinterpret_cast<const float4*>(&mine[r]);
         a4.x -= l4.x * u;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(kColRing) k_factor2d_col(Geo g, const BlockDes
       }
     }
     if (j == ku2 + 1)  // the column entering the band starts at zero
-      for (int r = 0; r < kColRows; r += 4) *reinterpret_cast<float4*>(&mine[r]) = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int r = 0; r < Wp; r += 4) *reinterpret_cast<float4*>(&mine[r]) = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j == 0) {  // this slot now holds column k + 128
       ac += da;
       bc += db;
