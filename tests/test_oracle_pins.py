@@ -523,6 +523,85 @@ def test_mobility_steps_conserve_mass_and_decrease_energy():
         e0 = e1
 
 
+# ---------------------------------------------------------------- variable mobility in 3D
+def test_mobility_3d_on_a_field_constant_along_one_axis_is_the_2d_operator():
+    """A 3D field constant along one axis has no flux across that axis: the 3D residual and JVP
+    with M = 1 - phi^2 equal the 2D ones of the remaining two axes, for each choice of the constant
+    axis (so every axis of the 3D operator is exercised against the pinned 2D one)."""
+    rng_shape2 = (10, 12)
+    Phi2 = rand_field(rng_shape2, 61, 0.2, 0.4)
+    phin2 = rand_field(rng_shape2, 62, 0.2, 0.4)
+    v2 = rand_field(rng_shape2, 63, 0.0, 1.0)
+    dt = 0.6
+    F2 = O.residual(Phi2, phin2, dt, H2, GAMMA, mobility=True)
+    J2 = O.jvp(v2, Phi2, phin2, dt, H2, GAMMA, mobility=True)
+    for ax in range(3):
+        rep = lambda a: np.repeat(np.expand_dims(a, ax), 5, axis=ax)  # noqa: E731
+        F3 = O.residual(rep(Phi2), rep(phin2), dt, H2, GAMMA, mobility=True)
+        J3 = O.jvp(rep(v2), rep(Phi2), rep(phin2), dt, H2, GAMMA, mobility=True)
+        np.testing.assert_allclose(F3, rep(F2), rtol=0, atol=1e-12 * np.abs(F2).max())
+        np.testing.assert_allclose(J3, rep(J2), rtol=0, atol=1e-12 * np.abs(J2).max())
+
+
+def test_mobility_3d_jacobian_matches_finite_differences():
+    """3D, M = 1 - phi^2: the analytic J v against central differences of F, the assembled
+    matrix against J v, and the dM/dPhi term present."""
+    shape = (6, 7, 8)
+    Phi = rand_field(shape, 64, 0.2, 0.4)
+    phin = rand_field(shape, 65, 0.2, 0.4)
+    v = rand_field(shape, 66, 0.0, 1.0)
+    dt = 0.7
+    Jv = O.jvp(v, Phi, phin, dt, H2, GAMMA, mobility=True)
+    eps = 1e-5 * np.linalg.norm(Phi) / np.linalg.norm(v)
+    fd = (O.residual(Phi + eps * v, phin, dt, H2, GAMMA, mobility=True)
+          - O.residual(Phi - eps * v, phin, dt, H2, GAMMA, mobility=True)) / (2 * eps)
+    assert np.linalg.norm(Jv - fd) <= 1e-8 * np.linalg.norm(Jv)
+    J = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA, mobility=True)
+    np.testing.assert_allclose((J @ v.ravel()).reshape(shape), Jv, rtol=0, atol=1e-12 * np.abs(Jv).max())
+    assert np.linalg.norm(Jv - O.jvp(v, Phi, phin, dt, H2, GAMMA)) > 1e-3 * np.linalg.norm(Jv)
+    # the block matrices keep the 63-point pattern of the constant-mobility Jacobian
+    J1 = O.assemble_jacobian(Phi, phin, dt, H2, GAMMA)
+    assert set(zip(*J.nonzero())) <= set(zip(*J1.nonzero()))
+
+
+@pytest.mark.parametrize("dt", [0.05, 1.0])
+def test_mobility_3d_fourier_mode_multiplier(dt):
+    """3D small mode on phi_bar = 0.3 with M = 1 - phi^2: Crank-Nicolson with M(phi_bar) and the cubic
+    slope 3 phi_bar^2, g = (1 - dt M kappa S/2)/(1 + dt M kappa S/2), solved with the shifted-ILU(0)
+    Schwarz blocks of the 3D path."""
+    shape = (16, 16, 16)
+    h = 1.1
+    ks = (1, 2, 1)
+    pbar = 0.3
+    d0 = 1e-6 * mode(shape, ks, h)
+    lam = kappa(ks, shape, h)
+    S = (1 - GAMMA) + 3 * pbar ** 2 - 2 * lam + lam * lam
+    M = 1 - pbar ** 2
+    g = (1 - 0.5 * dt * M * lam * S) / (1 + 0.5 * dt * M * lam * S)
+    p = O.Params(parts=(2, 2, 2), newton_rtol=1e-13, gmres_rtol=1e-12, mobility=True, subdomain_solver="ilu0")
+    phi1, info = O.newton_solve(pbar + d0, dt, h, GAMMA, p)
+    np.testing.assert_allclose(phi1 - pbar, g * d0, rtol=0, atol=1e-5 * 1e-6)
+    # a solve that dropped M would give the constant-mobility multiplier
+    assert abs(g - (1 - 0.5 * dt * lam * S) / (1 + 0.5 * dt * lam * S)) > 1e-4
+
+
+def test_mobility_3d_steps_conserve_mass_and_decrease_energy():
+    """Two 3D Newton steps with M = 1 - phi^2 and shifted-ILU(0) blocks: mass to 1e-12 and a
+    non-increasing discrete energy."""
+    shape = (16, 16, 16)
+    h = 80 * math.pi / 256
+    phi = -0.325 + 0.07 * rand_field(shape, 67, 0.0, 1.0)
+    p = O.Params(parts=(2, 2, 2), mobility=True, subdomain_solver="ilu0")
+    e0, m0 = O.energy(phi, h, 0.3), O.mass(phi, h)
+    for _ in range(2):
+        phi, info = O.newton_solve(phi, 0.5, h, 0.3, p)
+        assert info.converged
+        e1 = O.energy(phi, h, 0.3)
+        assert e1 <= e0 + 1e-13 * abs(e0)
+        assert abs(O.mass(phi, h) - m0) <= 1e-12 * max(1.0, abs(m0))
+        e0 = e1
+
+
 # ---------------------------------------------------------------- Neumann-type walls (Sec. 2)
 def neumann_lap_matrix(shape, h):
     """Textbook cell-centred Neumann Laplacian, built by hand: per axis the tridiagonal
