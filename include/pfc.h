@@ -139,7 +139,8 @@ typedef struct {
   int reuse_factor;
   /* Mobility of Eq. (NSOP): 0 (default) M = 1; 1: M(phi) = 1 - phi^2 evaluated at
      (Phi + phi^n)/2 and averaged onto edges (Sec. 3), with the Jacobian's
-     dM/dPhi term.  2D grids; the JVP then runs in FP64 on every path. */
+     dM/dPhi term.  2D and 3D periodic grids; the JVP then runs in FP64 on every
+     path. */
   int mobility;
   /* Boundary of the domain: PFC_PERIODIC (0, default) or PFC_NEUMANN (1), the
      homogeneous Neumann-type conditions of Sec. 2 (n.grad phi = n.grad Delta phi =

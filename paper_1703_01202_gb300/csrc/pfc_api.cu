@@ -186,9 +186,9 @@ int validate(const pfc_grid* g, const pfc_params* p) {
   if (p->gmres_fast_dots != 0 && p->gmres_fast_dots != 1) return PFC_EINVAL;
   if (p->jvp_fp32 != 0 && p->jvp_fp32 != 1) return PFC_EINVAL;
   if (p->reuse_factor < 0 || p->reuse_factor > 1000000) return PFC_EINVAL;
-  if (p->mobility != 0 && (p->mobility != 1 || g->dim != 2)) return PFC_EINVAL;
-  // Neumann walls: 2D, left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then
-  // never see a second mirror image)
+  if (p->mobility != 0 && p->mobility != 1) return PFC_EINVAL;
+  // Neumann walls: left-RAS, M = 1, at least 4 cells per axis (the radius-3 stencils then never
+  // see a second mirror image)
   if (p->boundary != PFC_PERIODIC &&
       (p->boundary != PFC_NEUMANN || p->ras_kind != PFC_LEFT_RAS || p->mobility != 0 || g->n[0] < 4 ||
        g->n[1] < 4 || (g->dim == 3 && g->n[2] < 4)))
@@ -624,7 +624,11 @@ int eval_residual(pfc_state* s, const double* Pb, const double* S, double lam, b
       pfc::launch_trial(s->g, Pb, S, lam, project ? s->red + 9 : nullptr, Pout, s->st);
       P = Pout;
     }
-    pfc::launch_residual3d(s->g, P, phin, idt, F, qout, s->T1, s->T2, s->partial, &np, s->st);
+    const bool mob = s->p.mobility != 0;  // mu and s beside q, as in 2D
+    double* muo = qout == s->q ? s->mu : s->mut;
+    double* so = qout == s->q ? s->sm : s->smt;
+    pfc::launch_residual3d(s->g, P, phin, idt, F, qout, s->T1, s->T2, s->partial, &np, s->st, mob,
+                           mob && qout ? muo : nullptr, mob && qout ? so : nullptr);
   }
   // reads Phi (or Phi_b and S), phi^n; writes F (and the trial Phi, q)
   PROF_END(ps, PFC_PROF_RESIDUAL, -1, 8.0 * s->g.n * (3 + (S ? 2 : 0) + (qout ? 1 : 0)));
@@ -653,9 +657,14 @@ int dot_mode(const pfc_state* s) {
 // pout: out (or ia->w) is a basis vector stored as float pairs (pair_basis).
 void jvp(pfc_state* s, const double* v, const double* q, double idt, double* out, const int* skip,
          const pfc::IterArgs* ia = nullptr, int zplane = -1, bool pout = false) {
-  if (s->dim == 2 && s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
+  if (s->p.mobility) {  // variable mobility: FP64 on every path; mu, s of q's iterate
     const bool trial = q != nullptr && q == s->qt;
-    pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu, trial ? s->smt : s->sm);
+    if (s->dim == 2)
+      pfc::launch_jvp2d(s->g, v, nullptr, q, idt, out, skip, s->st, ia, trial ? s->mut : s->mu,
+                        trial ? s->smt : s->sm);
+    else
+      pfc::launch_jvp3d(s->g, v, nullptr, q, idt, out, s->T1, s->T2, skip, s->st, trial ? s->mut : s->mu,
+                        trial ? s->smt : s->sm);
   } else if (s->dim == 2 && s->fs.prec != PFC_F64 && s->p.jvp_fp32)  // mixed path, opt-in: plain FP32
     pfc::launch_jvp2d_f32(s->g, v, q, idt, out, skip, s->st, ia, &s->jmaps, zplane, s->status_dev + 1, pout);
   else if (s->dim == 2 && s->fs.prec != PFC_F64)  // mixed path: float-float JVP on the FP32 pipe
@@ -742,8 +751,8 @@ int tune_apply(pfc_state* s) {
 int factor_blocks(pfc_state* s, const double* q, double idt, bool dev = false) {
   if (s->p.mobility) {  // the mobility fields of q's iterate
     const bool trial = q == s->qt;
-    s->fs.mob_mu = trial ? s->mut : s->mu;
-    s->fs.mob_s = trial ? s->smt : s->sm;
+    s->fs.mob_mu = s->r3.mob_mu = trial ? s->mut : s->mu;
+    s->fs.mob_s = s->r3.mob_s = trial ? s->smt : s->sm;
   }
   if (s->dim == 2) {
     // the sliding factor window holds 2 kl + 2 <= 256 column slots (kl = 3 bx: blocks at most 42 cells
@@ -1592,6 +1601,8 @@ int pfc_create(const pfc_grid* g, double h, double eps, const pfc_params* p, voi
   }
   s->fs.mob_mu = nullptr;
   s->fs.mob_s = nullptr;
+  s->r3.mob_mu = nullptr;
+  s->r3.mob_s = nullptr;
   s->fs.Yb = (double*)at(pl.Yb);
   if (g->dim == 2) {
     s->dc.px = p->sub[0];

@@ -300,10 +300,14 @@ bool apply_variant_ok(int v, int prec, int kl_max, int xstage, int n_max);
 // ---- 3D stencils (stencil3d.cu)
 void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, const double* ssum, double* Pout,
                   cudaStream_t st);
+// mob: variable mobility M = 1 - s^2, s = (P + phin)/2; mu and s written to mu_out, s_out when given.
 void launch_residual3d(const Geo& g, const double* P, const double* phin, double idt, double* F, double* q_out,
-                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st);
+                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st, bool mob = false,
+                       double* mu_out = nullptr, double* s_out = nullptr);
+// mu, sm (variable mobility): mu and s of the iterate q belongs to; null: M = 1.
 void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  double* T1, double* T2, const int* skip, cudaStream_t st);
+                  double* T1, double* T2, const int* skip, cudaStream_t st, const double* mu = nullptr,
+                  const double* sm = nullptr);
 // The same product in float-float arithmetic (the mixed path); T1, T2 hold float pairs.
 void launch_jvp3d_ff(const Geo& g, const double* v, const double* q, double idt, double* Jv, double* T1, double* T2,
                      const int* skip, cudaStream_t st, int pout = 0);  // pout: Jv as float pairs
@@ -344,6 +348,8 @@ struct Ras3D {
   const uint8_t* posU;  // neighbour in its level's row list (255: outside the block)
   double shift;       // diagonal shift, relative to the block's mean |a_ii|
   int pin;            // the apply's input r is stored as float pairs (the mixed path's Krylov basis)
+  const double* mob_mu;  // variable mobility: mu and s = (Phi + phi^n)/2 at the factored iterate
+  const double* mob_s;   // (null: M = 1)
 };
 // Whether the window apply can run these blocks: FP32/BF16 factors and levels of at most 255 rows.
 bool apply3d_window_ok(const Ras3D& R);

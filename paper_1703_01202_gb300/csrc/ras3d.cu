@@ -210,13 +210,79 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
     }
     return v;
   };
+  // Variable mobility (Sec. 3, M = 1 - s^2 at s = (Phi + phi^n)/2): row i of
+  // J = I/dt - D_M (L_gamma/2 + Q) - B, with D_M the 7-point (div M grad)_d (edge M the average of
+  // its end nodes) and B the term of dM/dPhi = -s.  mob_row gathers what the row's entries need
+  // (the 7-point coefficients of D_M, q at the 7 nodes, B's three kinds of entry); mob_entry gives
+  // the entry in the column of offset (da, db, dc), without 1/dt and the shift.
+  const bool mob = R.mob_mu != nullptr;
+  struct MobRow {
+    double cf[7];  // D_M coefficients of the centre and of +x, -x, +y, -y, +z, -z
+    double qn[7];  // q at those nodes
+    double bd;     // -B(i, i)
+    double bn[6];  // -B(i, i + n_k)
+  };
+  auto lgh = [&](int da, int db, int dc) -> double {  // L_gamma / 2 at offset (da, db, dc)
+    const int ad = abs(da) + abs(db) + abs(dc), nz = (da != 0) + (db != 0) + (dc != 0);
+    if (ad == 0) return g.c0 - 6.0 * ih2 + 21.0 * g.ih4;
+    if (ad == 1) return ih2 - 6.0 * g.ih4;
+    if (ad == 2) return nz == 1 ? 0.5 * g.ih4 : g.ih4;
+    return 0.0;
+  };
+  constexpr int kNb[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  auto mob_row = [&](int a, int b, int c, MobRow* m) {
+    double sn[7], mn[7], un[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const long long i = gidx(g, B, a + kNb[k][0], b + kNb[k][1], c + kNb[k][2]);
+      sn[k] = R.mob_s[i];
+      un[k] = R.mob_mu[i];
+      m->qn[k] = q[i];
+      mn[k] = 1.0 - sn[k] * sn[k];
+    }
+    double c0 = 0.0, bd = 0.0;
+#pragma unroll
+    for (int k = 1; k < 7; ++k) {
+      m->cf[k] = ih2 * 0.5 * (mn[0] + mn[k]);
+      c0 -= m->cf[k];
+      // the gradient of mu on the edge to neighbour k, oriented along +axis
+      const double gk = (k & 1) ? (un[k] - un[0]) * ih2 : (un[0] - un[k]) * ih2;
+      bd += (k & 1) ? 0.5 * gk : -0.5 * gk;
+      m->bn[k - 1] = (k & 1) ? 0.5 * gk * sn[k] : -0.5 * gk * sn[k];
+    }
+    m->cf[0] = c0;
+    m->bd = bd * sn[0];
+  };
+  auto mob_entry = [&](const MobRow& m, int da, int db, int dc) -> double {
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int ea = da - kNb[k][0], eb = db - kNb[k][1], ec = dc - kNb[k][2];
+      double t = lgh(ea, eb, ec);
+      if (ea == 0 && eb == 0 && ec == 0) t += m.qn[k];
+      v = fma(-m.cf[k], t, v);
+    }
+    const int ad = abs(da) + abs(db) + abs(dc);
+    if (ad == 0) v += m.bd;
+    if (ad == 1) {
+      const int k = da == 1 ? 1 : da == -1 ? 2 : db == 1 ? 3 : db == -1 ? 4 : dc == 1 ? 5 : 6;
+      v += m.bn[k - 1];
+    }
+    return v;
+  };
   // sigma = shift * mean |a_ii| of the block matrix
   double dsum = 0.0;
   for (int r = tid; r < S.nrows; r += FT) {
     int a, b, c;
     abc_of(rowabc[r], &a, &b, &c);
-    dsum += wall_row(a, b, c) ? fabs(folded(a, b, c, a, b, c) + idt)
-                              : fabs(idt + lin343[171] + 6.0 * ih2 * qat(a, b, c));
+    if (mob) {
+      MobRow m;
+      mob_row(a, b, c, &m);
+      dsum += fabs(mob_entry(m, 0, 0, 0) + idt);
+    } else {
+      dsum += wall_row(a, b, c) ? fabs(folded(a, b, c, a, b, c) + idt)
+                                : fabs(idt + lin343[171] + 6.0 * ih2 * qat(a, b, c));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
   if (lane == 0) s_red[wid] = dsum;
@@ -237,6 +303,8 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
       abc_of(rowabc[r0 + i], &a, &b, &c);
       // row i of A_k + sigma I (zero outside the block): lane j builds entries j and 32 + j
       const bool wall = wall_row(a, b, c);  // the same for the whole warp
+      MobRow mr;
+      if (mob) mob_row(a, b, c, &mr);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int o = lane + 32 * h;
@@ -246,7 +314,9 @@ __global__ void __launch_bounds__(factor_threads<TC>()) k_factor3d(Geo g, const 
           const int a2 = a + da, b2 = b + db, c2 = c + dc;
           if (a2 >= 0 && a2 < S.bx && b2 >= 0 && b2 < S.by && c2 >= 0 && c2 < S.bz) {
             const int ad = abs(da) + abs(db) + abs(dc);
-            if (wall) {
+            if (mob) {
+              v = mob_entry(mr, da, db, dc);
+            } else if (wall) {
               v = folded(a, b, c, a2, b2, c2);
             } else {
               v = lin343[(dc + 3) * 49 + (db + 3) * 7 + (da + 3)];

@@ -94,17 +94,59 @@ __global__ void __launch_bounds__(NT) k_mid3d(Geo g, int mode, const double* __r
   }
 }
 
+// The six neighbours of (x, y, z) in the order +x, -x, +y, -y, +z, -z (periodic grid).
+__device__ __forceinline__ void nbrs6(const Geo& g, int x, int y, int z, long long c, long long* nb) {
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  nb[0] = c + (wrap_up(x, g.nx, g.neumann) - x);
+  nb[1] = c + (wrap_dn(x, g.nx, g.neumann) - x);
+  nb[2] = c + (wrap_up(y, g.ny, g.neumann) - y) * sy;
+  nb[3] = c + (wrap_dn(y, g.ny, g.neumann) - y) * sy;
+  nb[4] = c + (wrap_up(z, g.nz, g.neumann) - z) * sz;
+  nb[5] = c + (wrap_dn(z, g.nz, g.neumann) - z) * sz;
+}
+// Variable mobility (Sec. 3, M = 1 - s^2 at the midpoint s = (Phi + phi^n)/2, node by node):
+// (div M grad)_d u at c = ih2 sum over the six edges M_edge (u_nb - u_c), M_edge the average of
+// the edge's two end nodes.  m[k] are the nodal M of the neighbours, mc that of c.
+__device__ __forceinline__ double div_m_grad6(const double* __restrict__ u, long long c, const long long* nb,
+                                              double mc, const double* m, double ih2) {
+  const double uc = u[c];
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc = fma(0.5 * (mc + m[k]), u[nb[k]] - uc, acc);
+  return ih2 * acc;
+}
+
 // F = (P - N) idt - ih2 Lap(mu); q = (3P^2 + 2PN + N^2)/4; per-CTA sum of F^2.
+// MOB: F = (P - N) idt - (div M grad)_d mu with M = 1 - s^2, s = (P + N)/2; mu and s of every node
+// written to mu_out, s_out when given (the JVP and the factor of this iterate read them).
+template <bool MOB>
 __global__ void __launch_bounds__(NT) k_res_out3d(Geo g, const double* __restrict__ P, const double* __restrict__ N,
                                                   const double* __restrict__ mu, double idt, double* __restrict__ F,
-                                                  double* __restrict__ qout, double* __restrict__ partial) {
+                                                  double* __restrict__ qout, double* __restrict__ partial,
+                                                  double* __restrict__ mu_out, double* __restrict__ s_out) {
   __shared__ double red[NT / 32];
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
     int x, y, z;
     coords(g, i, &x, &y, &z);
     const double p = P[i], nn = N[i];
-    const double f = fma(-g.ih2, lap7(mu, nullptr, g, x, y, z), (p - nn) * idt);
+    double f;
+    if (MOB) {
+      long long nb[6];
+      nbrs6(g, x, y, z, i, nb);
+      double m[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double sk = 0.5 * (P[nb[k]] + N[nb[k]]);
+        m[k] = 1.0 - sk * sk;
+      }
+      const double sc = 0.5 * (p + nn);
+      f = (p - nn) * idt - div_m_grad6(mu, i, nb, 1.0 - sc * sc, m, g.ih2);
+      if (mu_out) mu_out[i] = mu[i];
+      if (s_out) s_out[i] = sc;
+    } else {
+      f = fma(-g.ih2, lap7(mu, nullptr, g, x, y, z), (p - nn) * idt);
+    }
     F[i] = f;
     if (qout) qout[i] = 0.25 * fma(3.0 * p, p, nn * fma(2.0, p, nn));
     acc = fma(f, f, acc);
@@ -114,15 +156,34 @@ __global__ void __launch_bounds__(NT) k_res_out3d(Geo g, const double* __restric
 }
 
 // J v = sc v idt - ih2 Lap(w)
+// MOB: J v = sc v idt - (div M grad)_d w - (div dM grad)_d mu, with M = 1 - s^2 and its derivative
+// dM = -s (sc v) at the nodes (edge values the averages), mu and s of the iterate.
+template <bool MOB>
 __global__ void __launch_bounds__(NT) k_jvp_out3d(Geo g, const double* __restrict__ v,
                                                   const double* __restrict__ vscale, const double* __restrict__ w,
-                                                  double idt, double* __restrict__ Jv, const int* __restrict__ skip) {
+                                                  double idt, double* __restrict__ Jv, const int* __restrict__ skip,
+                                                  const double* __restrict__ mu, const double* __restrict__ sm) {
   if (skip && *skip) return;
   const double sc = vscale ? *vscale : 1.0;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < g.n; i += (long long)gridDim.x * NT) {
     int x, y, z;
     coords(g, i, &x, &y, &z);
-    Jv[i] = fma(-g.ih2, lap7(w, nullptr, g, x, y, z), sc * v[i] * idt);
+    if (MOB) {
+      long long nb[6];
+      nbrs6(g, x, y, z, i, nb);
+      double m[6], dm[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double sk = sm[nb[k]];
+        m[k] = 1.0 - sk * sk;
+        dm[k] = -sk * (sc * v[nb[k]]);
+      }
+      const double s0 = sm[i];
+      const double vi = sc * v[i];
+      Jv[i] = vi * idt - div_m_grad6(w, i, nb, 1.0 - s0 * s0, m, g.ih2) - div_m_grad6(mu, i, nb, -s0 * vi, dm, g.ih2);
+    } else {
+      Jv[i] = fma(-g.ih2, lap7(w, nullptr, g, x, y, z), sc * v[i] * idt);
+    }
   }
 }
 
@@ -179,21 +240,28 @@ void launch_trial(const Geo& g, const double* Pb, const double* S, double lam, c
 }
 
 void launch_residual3d(const Geo& g, const double* P, const double* phin, double idt, double* F, double* q_out,
-                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st) {
+                       double* T1, double* T2, double* partial, int* nparts, cudaStream_t st, bool mob,
+                       double* mu_out, double* s_out) {
   const int b = ctas(g.n);
   k_lap3d<<<b, NT, 0, st>>>(g, P, phin, nullptr, T1, nullptr);
   k_mid3d<<<b, NT, 0, st>>>(g, 0, P, phin, nullptr, T1, T2, nullptr);
-  k_res_out3d<<<b, NT, 0, st>>>(g, P, phin, T2, idt, F, q_out, partial);
+  if (mob)
+    k_res_out3d<true><<<b, NT, 0, st>>>(g, P, phin, T2, idt, F, q_out, partial, mu_out, s_out);
+  else
+    k_res_out3d<false><<<b, NT, 0, st>>>(g, P, phin, T2, idt, F, q_out, partial, nullptr, nullptr);
   count_launches(3);
   *nparts = b;
 }
 
 void launch_jvp3d(const Geo& g, const double* v, const double* vscale, const double* q, double idt, double* Jv,
-                  double* T1, double* T2, const int* skip, cudaStream_t st) {
+                  double* T1, double* T2, const int* skip, cudaStream_t st, const double* mu, const double* sm) {
   const int b = ctas(g.n);
   k_lap3d<<<b, NT, 0, st>>>(g, v, nullptr, vscale, T1, skip);
   k_mid3d<<<b, NT, 0, st>>>(g, 1, v, q, vscale, T1, T2, skip);
-  k_jvp_out3d<<<b, NT, 0, st>>>(g, v, vscale, T2, idt, Jv, skip);
+  if (mu)
+    k_jvp_out3d<true><<<b, NT, 0, st>>>(g, v, vscale, T2, idt, Jv, skip, mu, sm);
+  else
+    k_jvp_out3d<false><<<b, NT, 0, st>>>(g, v, vscale, T2, idt, Jv, skip, nullptr, nullptr);
   count_launches(3);
 }
 

@@ -94,8 +94,8 @@ def test_schwarz_kind_validation(libpfc):
 
 
 def test_mobility_validation(libpfc):
-    """M = 1 - phi^2 (mobility = 1): 2D only; four more fields in the workspace (mu and the
-    midpoint s beside q and the trial q)."""
+    """M = 1 - phi^2 (mobility = 1): 2D and 3D periodic grids; four more fields in the workspace
+    (mu and the midpoint s beside q and the trial q)."""
     from paper_1703_01202_gb300 import pfc
 
     base = pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4)))
@@ -103,8 +103,8 @@ def test_mobility_validation(libpfc):
     for bad in (dict(mobility=2), dict(mobility=-1)):
         with pytest.raises(pfc.PfcError):
             pfc.workspace_size((64, 64), pfc.default_params(sub=(4, 4), **bad))
-    with pytest.raises(pfc.PfcError):
-        pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), mobility=1))
+    base3 = pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2)))
+    assert pfc.workspace_size((32, 32, 32), pfc.default_params(sub=(2, 2, 2), mobility=1)) >= base3 + 4 * 32 ** 3 * 8
 
 
 def test_boundary_validation(libpfc):

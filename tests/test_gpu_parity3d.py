@@ -209,3 +209,55 @@ def test_neumann_steps_3d(pfc, prec, tol_phi, tol_e):
     assert np.abs(s.get_field() - ref).max() <= tol_phi
     for inf, rec in zip(infos, recs):
         assert abs(inf["energy"] - rec.energy) <= tol_e * abs(rec.energy)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 14, 18)])
+def test_mobility_operators_3d(pfc, shape):
+    """Variable mobility M = 1 - phi^2 in 3D (Sec. 3): residual (edge-averaged M of the midpoint)
+    and the FP64 JVP with the dM/dPhi term against the oracle, on every path (the mixed path's
+    JVP is FP64 too with mobility)."""
+    Phi = inputs.noise_field(shape, 0.2, 0.4, 51)
+    phin = inputs.noise_field(shape, 0.2, 0.4, 52)
+    v = inputs.noise_field(shape, 0.0, 1.0, 53)
+    ref = O.residual(Phi, phin, 0.7, H3, GAMMA3, mobility=True)
+    refj = O.jvp(v, Phi, phin, 2.5, H3, GAMMA3, mobility=True)
+    for prec in (0, 2):
+        s = solver3(pfc, shape, (2, 2, 2), prec=prec, mobility=1)
+        F, nrm = s.residual(Phi, phin, 0.7)
+        np.testing.assert_allclose(F.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+        assert nrm == pytest.approx(np.linalg.norm(ref), rel=1e-12)
+        Jv = s.jvp(Phi, phin, v, 2.5).cpu().numpy()
+        np.testing.assert_allclose(Jv, refj, rtol=0, atol=1e-12 * np.abs(refj).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (2, 0.05)])
+@pytest.mark.parametrize("shape,parts", [((16, 16, 16), (2, 2, 2)), ((17, 16, 15), (2, 2, 2))])
+def test_mobility_precond_3d(pfc, shape, parts, prec, tol):
+    """Left-RAS with shifted ILU(0) blocks of the mobility Jacobian (the 63-point pattern, entries
+    of D_M (L_gamma/2 + Q) and of the dM/dPhi term) against the oracle's blocks of its assembled
+    mobility Jacobian."""
+    Phi = inputs.noise_field(shape, 0.2, 0.3, 54)
+    phin = inputs.noise_field(shape, 0.2, 0.3, 55)
+    r = inputs.noise_field(shape, 0.0, 1.0, 56)
+    s = solver3(pfc, shape, parts, prec=prec, mobility=1)
+    z = s.precond_apply(Phi, phin, 2.0, r).cpu().numpy()
+    J = O.assemble_jacobian(Phi, phin, 2.0, H3, GAMMA3, mobility=True)
+    ref = O.Schwarz(J, O.decompose(shape, parts, 1), "left-ras", "ilu0", 0.1).apply(r)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol_phi,tol_e", [(0, 1e-8, 1e-10), (2, 1e-7, 1e-9)])
+def test_mobility_steps_3d(pfc, prec, tol_phi, tol_e):
+    """Three fixed steps at dt = 0.5 with M = 1 - phi^2 on a 16^3 noisy liquid (|phi| < 1, so M > 0)
+    against the oracle (plain FP64 and mixed tolerances)."""
+    shape = (16, 16, 16)
+    phi0 = inputs.noise_field(shape, -0.325, 0.07, 57)
+    s = solver3(pfc, shape, (2, 2, 2), prec=prec, mobility=1)
+    s.set_field(phi0)
+    infos = [s.step(0.5) for _ in range(3)]
+    ref, recs = O.run(phi0, H3, GAMMA3, O.Params(parts=(2, 2, 2), overlap=1, subdomain_solver="ilu0", mobility=True),
+                      3, fixed_dt=0.5)
+    assert np.abs(s.get_field() - ref).max() <= tol_phi
+    for inf, rec in zip(infos, recs):
+        assert abs(inf["energy"] - rec.energy) <= tol_e * abs(rec.energy)
