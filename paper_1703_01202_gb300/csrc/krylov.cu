@@ -650,8 +650,10 @@ void launch_multiaxpy(double* w, const double* x0, const double* const* tab, int
     launch_pdl(k_multiaxpy<S, F, PR>, dim3(bx), dim3(kSweepThreads), smem, st, w, x0, tab, nx, coef, sign, n,   \
                partial, skip, only_if, tail);                                                           \
   } while (0)
-  if (pairs && sum) {  // float-pair vectors come with no sum of w (the Gram-Schmidt sweeps)
+  if (pairs && sum) {  // float-pair vectors come with no sum of w (the Gram-Schmidt sweeps only)
     fprintf(stderr, "libpfc: float-pair multi-axpy with the sum of w\n");
+    static const int kInvalid = PFC_EINVAL;  // the step then fails with this status
+    if (tail.err) cudaMemcpyAsync(tail.err, &kInvalid, sizeof kInvalid, cudaMemcpyHostToDevice, st);
     return;
   }
   if (pairs)
